@@ -1,0 +1,248 @@
+"""Seeded synthetic workloads for the adaptive-particle-refinement (APR) SPH hot path.
+
+This module only *places particles* and states run parameters.  It holds none of
+the method's arithmetic (no kernel, no density, no split/merge rule), so both the
+FP64 CPU oracle and the CUDA library can take their inputs from here without
+sharing any code with each other.
+
+Every workload is a plain ``dict``:
+
+``cfg``        run parameters (box, quantisation unit, EOS, viscosity, APR limits)
+``regions``    refinement regions (centre, nested boundaries, shape, optional sink to track)
+``sinks``      point masses (position, velocity, mass, accretion radius)
+``p``          particle arrays (float64 positions/velocities/u/h, uint8 level/flags, uint64 id)
+
+The paper's own problems (the HD 142527 circumbinary disc, the planet-in-disc and
+flyby runs of Section 3) need initial conditions that are not available here; the
+generators below stand in for them with the same geometry, profiles and particle
+counts (surface density Sigma ~ 1/R on R in [1, 10], H/R = 0.05 at R = 1,
+c_s ~ R^-1/4, Keplerian rotation, a sink-tracking refinement sphere), and the
+shock tube and lattices are the usual SPH test set-ups.  All randomness comes from
+``numpy.random.default_rng(seed)`` with ``seed = 20240917 + index``.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED_BASE = 20240917
+
+# particle flag bits (shared vocabulary of the state, not arithmetic)
+FLAG_CHANGED = 1   # split or merged during the current split/merge pass
+FLAG_FIXED = 2     # boundary particle: never moved, split or merged
+FLAG_DEAD = 4      # removed (merged away or accreted) until the next compaction
+
+SHAPE_SPHERE = 0
+SHAPE_SLAB = 1
+
+EOS_ADIABATIC = 0
+EOS_LOCALLY_ISOTHERMAL = 1
+
+
+def _cfg(**kw):
+    base = dict(
+        box_lo=[0.0, 0.0, 0.0], box_hi=[1.0, 1.0, 1.0], periodic=[1, 1, 1],
+        delta=2.0 ** -30,
+        hfact=1.2, gamma=5.0 / 3.0, eos=EOS_ADIABATIC, cs0=1.0, qcs=0.0,
+        alpha_av=1.0, beta_av=2.0, alpha_u=0.0,
+        rsep_fac=0.2, dnn_cap=0.35,
+        m0=1.0, lmax=1, seed=SEED_BASE,
+        ccour=0.3, cforce=0.25, G=1.0,
+    )
+    base.update(kw)
+    return base
+
+
+def _particles(x, y, z, vx, vy, vz, u, h, flags=None, level=None):
+    n = len(x)
+    p = dict(
+        x=np.ascontiguousarray(x, dtype=np.float64),
+        y=np.ascontiguousarray(y, dtype=np.float64),
+        z=np.ascontiguousarray(z, dtype=np.float64),
+        vx=np.ascontiguousarray(vx, dtype=np.float64),
+        vy=np.ascontiguousarray(vy, dtype=np.float64),
+        vz=np.ascontiguousarray(vz, dtype=np.float64),
+        u=np.ascontiguousarray(u, dtype=np.float64),
+        h=np.ascontiguousarray(h, dtype=np.float64),
+        level=np.zeros(n, np.uint8) if level is None else np.ascontiguousarray(level, np.uint8),
+        flags=np.zeros(n, np.uint8) if flags is None else np.ascontiguousarray(flags, np.uint8),
+        id=np.arange(n, dtype=np.uint64),
+    )
+    return p
+
+
+def lattice_box(n_side=16, jitter=0.05, seed=SEED_BASE, sphere_R=(0.25,), gamma=5.0 / 3.0,
+                u0=1.0, rho0=1.0, hfact=1.2, name=None):
+    """Cubic lattice of ``n_side**3`` particles in the periodic unit box.
+
+    Positions are cell centres ``(i + 1/2)/n_side`` moved by ``U(-jitter, jitter)``
+    lattice spacings per axis; equal masses ``rho0/n_side**3``; ``u = u0``; ``v = 0``;
+    ``h = hfact * spacing``.  A refinement sphere at the box centre with nested radii
+    ``sphere_R`` (one level per radius, outermost first).
+    """
+    rng = np.random.default_rng(seed)
+    s = 1.0 / n_side
+    g = (np.arange(n_side) + 0.5) * s
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    pos = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    if jitter:
+        pos = pos + rng.uniform(-jitter, jitter, size=pos.shape) * s
+    pos = np.mod(pos, 1.0)
+    n = len(pos)
+    zeros = np.zeros(n)
+    p = _particles(pos[:, 0], pos[:, 1], pos[:, 2], zeros, zeros, zeros,
+                   np.full(n, u0), np.full(n, hfact * s))
+    cfg = _cfg(gamma=gamma, hfact=hfact, m0=rho0 * s ** 3, lmax=max(1, len(sphere_R)), seed=seed)
+    regions = [dict(shape=SHAPE_SPHERE, axis=0, track_sink=-1, centre=[0.5, 0.5, 0.5],
+                    R=list(sphere_R))] if sphere_R else []
+    return dict(name=name or f"lattice{n_side}", cfg=cfg, regions=regions, sinks=[], p=p,
+                rho0=rho0, spacing=s)
+
+
+def c1_lattice():
+    """16^3 = 4096-particle jittered lattice, periodic unit box, one refinement sphere r = 0.25."""
+    return lattice_box(16, 0.05, SEED_BASE + 0, sphere_R=(0.25,), name="c1_lattice4096")
+
+
+def sod(nL=28, gamma=1.4, slab=(0.15, 0.10), seed=SEED_BASE + 1, jitter=0.05, name=None):
+    """Three-dimensional Sod shock tube.
+
+    x in [-0.5, 0.5], y and z periodic with width 0.1.  Left state rho = 1, P = 1 on a
+    lattice of spacing 0.1/nL; right state rho = 0.125, P = 0.1 on spacing 0.2/nL (equal
+    particle masses).  Each particle is moved by U(-jitter, jitter) local spacings per
+    axis: a perfect cubic lattice cannot rearrange sideways under the one-dimensional
+    expansion and its rarefied part ends up stretched along x only, which biases the
+    SPH estimates behind the rarefaction.  Particles within 4*hfact spacings of
+    x = +-0.5 are FIXED.  The refinement region is a slab |x| < slab[k] for level k + 1.
+    """
+    assert nL % 2 == 0
+    w = 0.1
+    hfact = 1.2
+    sL = w / nL
+    sR = 2.0 * sL
+    gyz_L = (np.arange(nL) + 0.5) * sL
+    gyz_R = (np.arange(nL // 2) + 0.5) * sR
+    xL = (np.arange(5 * nL) + 0.5) * sL - 0.5
+    xR = (np.arange(5 * nL // 2) + 0.5) * sR
+    XL, YL, ZL = np.meshgrid(xL, gyz_L, gyz_L, indexing="ij")
+    XR, YR, ZR = np.meshgrid(xR, gyz_R, gyz_R, indexing="ij")
+    x = np.concatenate([XL.ravel(), XR.ravel()])
+    y = np.concatenate([YL.ravel(), YR.ravel()])
+    z = np.concatenate([ZL.ravel(), ZR.ravel()])
+    nl = XL.size
+    n = len(x)
+    rho = np.where(np.arange(n) < nl, 1.0, 0.125)
+    P = np.where(np.arange(n) < nl, 1.0, 0.1)
+    u = P / ((gamma - 1.0) * rho)
+    spacing = np.where(np.arange(n) < nl, sL, sR)
+    h = hfact * spacing
+    flags = np.zeros(n, np.uint8)
+    fixed = (x < -0.5 + 4 * hfact * sL) | (x > 0.5 - 4 * hfact * sR)
+    flags[fixed] = FLAG_FIXED
+    if jitter:
+        rng = np.random.default_rng(seed)
+        x = x + rng.uniform(-jitter, jitter, n) * spacing
+        y = np.mod(y + rng.uniform(-jitter, jitter, n) * spacing, w)
+        z = np.mod(z + rng.uniform(-jitter, jitter, n) * spacing, w)
+    zeros = np.zeros(n)
+    p = _particles(x, y, z, zeros, zeros, zeros, u, h, flags=flags)
+    cfg = _cfg(box_lo=[-0.6, 0.0, 0.0], box_hi=[0.6, w, w], periodic=[0, 1, 1],
+               delta=w * 2.0 ** -26, gamma=gamma, hfact=hfact, m0=sL ** 3,
+               alpha_av=1.0, beta_av=2.0, alpha_u=1.0, lmax=len(slab), seed=seed)
+    regions = [dict(shape=SHAPE_SLAB, axis=0, track_sink=-1, centre=[0.0, 0.05, 0.05],
+                    R=list(slab))] if slab else []
+    return dict(name=name or f"sod_nL{nL}", cfg=cfg, regions=regions, sinks=[], p=p,
+                sod=dict(rhoL=1.0, PL=1.0, rhoR=0.125, PR=0.1, gamma=gamma, x0=0.0))
+
+
+def c2_sod():
+    """The full-size Sod tube: 140x28x28 + 70x14x14 = 123,480 particles, 2-level slab."""
+    return sod(28, name="c2_sod123480")
+
+
+def _disc(n, seed, Rin=1.0, Rout=10.0, mdisc=0.05, H0=0.05, q=0.25, hfact=1.2):
+    rng = np.random.default_rng(seed)
+    R = rng.uniform(Rin, Rout, n)          # Sigma ~ 1/R  =>  dM/dR = const
+    phi = rng.uniform(0.0, 2.0 * math.pi, n)
+    H = H0 * R ** (1.5 - q)                # H = c_s/Omega, c_s = H0 R^-q, Omega = R^-3/2
+    z = rng.normal(0.0, 1.0, n) * H
+    x = R * np.cos(phi)
+    y = R * np.sin(phi)
+    vphi = np.sqrt(1.0 / R)
+    vx = -vphi * np.sin(phi)
+    vy = vphi * np.cos(phi)
+    vz = np.zeros(n)
+    m = mdisc / n
+    sigma0 = mdisc / (2.0 * math.pi * (Rout - Rin))
+    rho = sigma0 / R / (math.sqrt(2.0 * math.pi) * H) * np.exp(-0.5 * (z / H) ** 2)
+    rho = np.maximum(rho, 1e-6 * rho.max())
+    h = hfact * (m / rho) ** (1.0 / 3.0)
+    h = np.minimum(h, 1.0)
+    u = np.zeros(n)
+    p = _particles(x, y, z, vx, vy, vz, u, h)
+    cfg = _cfg(box_lo=[-12.0, -12.0, -12.0], box_hi=[12.0, 12.0, 12.0], periodic=[0, 0, 0],
+               delta=2.0 ** -25, gamma=1.0, eos=EOS_LOCALLY_ISOTHERMAL, cs0=H0, qcs=q,
+               hfact=hfact, m0=m, alpha_av=0.1, beta_av=2.0, alpha_u=0.0, seed=seed)
+    return p, cfg
+
+
+def disc_planet(n=1_000_000, seed=SEED_BASE + 2, name=None):
+    """Locally isothermal disc around M = 1 with a q = 1e-3 planet at R = 5 and a 3-level
+    refinement sphere R = (2.0, 1.5, 1.0) that tracks the planet."""
+    p, cfg = _disc(n, seed)
+    cfg["lmax"] = 3
+    mp = 1e-3
+    vp = math.sqrt((1.0 + mp) / 5.0)
+    sinks = [dict(x=[0.0, 0.0, 0.0], v=[0.0, -mp * vp, 0.0], m=1.0, racc=0.5),
+             dict(x=[5.0, 0.0, 0.0], v=[0.0, vp, 0.0], m=mp, racc=0.25)]
+    regions = [dict(shape=SHAPE_SPHERE, axis=0, track_sink=1, centre=[5.0, 0.0, 0.0],
+                    R=[2.0, 1.5, 1.0])]
+    return dict(name=name or f"c3_disc_planet{n}", cfg=cfg, regions=regions, sinks=sinks, p=p)
+
+
+def c3_disc_planet():
+    return disc_planet(1_000_000)
+
+
+def flyby(n=8_000_000, seed=SEED_BASE + 3, name=None):
+    """Disc as above (no planet) plus a unit-mass perturber on a parabolic orbit with
+    periastron 20, started at true anomaly -120 degrees; a 2-level refinement sphere
+    R = (7.5, 5.0) follows it."""
+    p, cfg = _disc(n, seed)
+    cfg["lmax"] = 2
+    f = -2.0 * math.pi / 3.0
+    qperi = 20.0
+    ptot = 2.0 * qperi
+    mtot = 2.0
+    r = ptot / (1.0 + math.cos(f))
+    pos = [r * math.cos(f), r * math.sin(f), 0.0]
+    k = math.sqrt(mtot / ptot)
+    vr, vt = k * math.sin(f), k * (1.0 + math.cos(f))
+    vel = [vr * math.cos(f) - vt * math.sin(f), vr * math.sin(f) + vt * math.cos(f), 0.0]
+    sinks = [dict(x=[0.0, 0.0, 0.0], v=[0.0, 0.0, 0.0], m=1.0, racc=0.5),
+             dict(x=pos, v=vel, m=1.0, racc=1.0)]
+    regions = [dict(shape=SHAPE_SPHERE, axis=0, track_sink=1, centre=list(pos), R=[7.5, 5.0])]
+    return dict(name=name or f"c4_flyby{n}", cfg=cfg, regions=regions, sinks=sinks, p=p)
+
+
+def c5_adjoint_lattice(n_side=126):
+    """126^3 = 2,000,376-particle jittered lattice with a 2-level sphere R = (0.35, 0.25)."""
+    return lattice_box(n_side, 0.05, SEED_BASE + 4, sphere_R=(0.35, 0.25),
+                       name=f"c5_lattice{n_side ** 3}")
+
+
+def copy_workload(w, capacity=None):
+    """Deep copy with particle arrays grown to ``capacity`` (new slots zeroed)."""
+    import copy
+    out = copy.deepcopy({k: v for k, v in w.items() if k != "p"})
+    n = len(w["p"]["x"])
+    cap = max(capacity or n, n)
+    p = {}
+    for k, a in w["p"].items():
+        b = np.zeros(cap, dtype=a.dtype)
+        b[:n] = a
+        p[k] = b
+    out["p"] = p
+    out["n"] = n
+    return out

@@ -1,0 +1,1334 @@
+/*
+ * FP64 CPU oracle for adaptive particle refinement (APR) in compressible SPH.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant generator with the CUDA library, and the CUDA
+ * library never calls it.
+ *
+ * What it computes, and where each piece comes from (Nealon & Price,
+ * "Adaptive particle refinement for compressible SPH", arXiv 2409.11470):
+ *
+ *   refinement level from position ............ Sec. 2.1 rules 1-3, Table 1 caption
+ *   mass per level m(l) = m0 / 2^l ............. Sec. 2.1 rule 5, Eq. 1
+ *   split: 1 parent -> 2 children, h scaled by (1/2)^(1/3), children at
+ *          +-r_sep along a direction tangential to the zone boundary, rotated
+ *          by a random angle, r_sep = min(0.2 h, 0.35 d_nn) ..... Sec. 2.2, Eq. 2
+ *   merge: pairing by a k-d tree cut through the centre of mass with an even
+ *          count on each side, leaves of exactly two; merge if the leaf's
+ *          centre of mass lies at a lower level; survivor at the pair's centre
+ *          of mass and velocity, h scaled by 2^(1/3); an odd particle is left
+ *          for the next step ........................... Sec. 2.3, Eq. 3, Eq. 4
+ *   per-step order: split levels ascending, then merge levels descending,
+ *          one level change per particle per step ............... Sec. 2.6
+ *   density / smoothing length: the paper cites the iterative h-rho solve of
+ *          the Phantom code (Sec. 2.2) without printing it; this oracle takes
+ *          the standard grad-h SPH definition: h is the unique root of
+ *          sum_b m_b W(r_ab, h) = m_a (h_fact/h)^3 (self included), found by
+ *          bisection to machine precision; M4 kernel, h_fact = 1.2 (Table 2)
+ *   forces: standard grad-h SPH momentum/energy equations with the
+ *          signal-velocity artificial viscosity and (optionally) artificial
+ *          conductivity (the paper cites them, Sec. 3 and Sec. 4) -- a proposed
+ *          reading, pinned by conservation laws, a lattice, a linear pressure
+ *          gradient and the Sod shock tube closed form.
+ *
+ * Decisions (neighbour membership, nearest-neighbour distance, the pairing
+ * tree's cuts) are taken on a quantised integer lattice x_int = floor((x-lo)/D)
+ * so that they are exact and independent of summation order; all physical
+ * values use the plain float64 coordinates.
+ *
+ * Build: gcc -O2 -std=c11 -fopenmp -ffp-contract=off -fPIC -shared.
+ * -ffp-contract=off keeps every float64 operation a separately rounded IEEE
+ * operation (no fused multiply-add), which the bit-exact split/merge
+ * geometry relies on.
+ */
+#define _GNU_SOURCE
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_FLAG_CHANGED 1u
+#define ORC_FLAG_FIXED 2u
+#define ORC_FLAG_DEAD 4u
+
+#define ORC_MAXLEV 8
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+#define ORC_COORD_BITS 30
+#define ORC_COORD_MAX ((1LL << ORC_COORD_BITS) - 1)
+
+/* (1/2)^(1/3) and 2^(1/3) as float64 literals (Eq. 2 and Eq. 3) */
+#define ORC_SPLIT_HFAC 0.7937005259840998
+#define ORC_MERGE_HFAC 1.2599210498948732
+
+typedef struct {
+    double lo[3], hi[3];
+    int periodic[3];
+    double delta;
+    double hfact, gamma;
+    int eos; /* 0 adiabatic, 1 locally isothermal */
+    double cs0, qcs;
+    double alpha_av, beta_av, alpha_u;
+    double rsep_fac, dnn_cap;
+    double m0;
+    int lmax;
+    unsigned long long seed;
+    double ccour, cforce, G;
+    int nthreads;
+    int enumerate; /* 0 brute force, 1 uniform cell list (same sets, sorted) */
+} orc_cfg;
+
+typedef struct {
+    int shape; /* 0 sphere, 1 slab */
+    int axis;
+    int track_sink; /* -1 fixed */
+    int nlev;
+    double centre[3];
+    double R[ORC_MAXLEV];
+} orc_region;
+
+typedef struct {
+    double x[3], v[3], a[3];
+    double m, racc;
+} orc_sink;
+
+typedef struct {
+    long long n, cap, next_id;
+    double *x, *y, *z, *vx, *vy, *vz, *u, *h;
+    double *rho, *omega, *ax, *ay, *az, *dudt, *vsig, *dnn, *pres, *cs;
+    unsigned char *level, *flags;
+    unsigned long long *id;
+} orc_state;
+
+typedef struct {
+    long long n_split[ORC_MAXLEV], n_merge[ORC_MAXLEV], n_spare[ORC_MAXLEV];
+    long long n_accreted, n_dead;
+} orc_counts;
+
+typedef struct {
+    double mass, mom[3], ang[3], ekin, etherm;
+} orc_stats;
+
+/* ------------------------------------------------------------------ basics */
+
+int orc_threads(const orc_cfg* c)
+{
+#ifdef _OPENMP
+    if (c && c->nthreads > 0) return c->nthreads;
+    return omp_get_max_threads();
+#else
+    (void)c;
+    return 1;
+#endif
+}
+
+static void set_threads(const orc_cfg* c)
+{
+#ifdef _OPENMP
+    if (c->nthreads > 0) omp_set_num_threads(c->nthreads);
+#else
+    (void)c;
+#endif
+}
+
+/* particle mass from its refinement level: m(l) = m0 / 2^l (Eq. 1) */
+static double mass_of(const orc_cfg* c, int level) { return ldexp(c->m0, -level); }
+
+static double box_len(const orc_cfg* c, int k) { return c->hi[k] - c->lo[k]; }
+
+long long orc_lattice_len(const orc_cfg* c, int k)
+{
+    return (long long)llround(box_len(c, k) / c->delta);
+}
+
+/* integer lattice coordinate of one component */
+static long long quant1(const orc_cfg* c, int k, double x)
+{
+    long long q = (long long)floor((x - c->lo[k]) / c->delta);
+    if (c->periodic[k]) {
+        long long L = orc_lattice_len(c, k);
+        q %= L;
+        if (q < 0) q += L;
+    } else {
+        if (q < 0) q = 0;
+        if (q > ORC_COORD_MAX) q = ORC_COORD_MAX;
+    }
+    return q;
+}
+
+void orc_quantise(const orc_cfg* c, long long n, const double* x, const double* y,
+                  const double* z, long long* xi)
+{
+    for (long long i = 0; i < n; ++i) {
+        xi[3 * i + 0] = quant1(c, 0, x[i]);
+        xi[3 * i + 1] = quant1(c, 1, y[i]);
+        xi[3 * i + 2] = quant1(c, 2, z[i]);
+    }
+}
+
+/* squared lattice separation with the minimum image on periodic axes (exact) */
+static unsigned long long r2_lattice(const orc_cfg* c, const long long* a, const long long* b)
+{
+    unsigned long long r2 = 0;
+    for (int k = 0; k < 3; ++k) {
+        long long d = a[k] - b[k];
+        if (c->periodic[k]) {
+            long long L = orc_lattice_len(c, k);
+            if (2 * d > L) d -= L;
+            else if (2 * d < -L) d += L;
+        }
+        r2 += (unsigned long long)(d * d);
+    }
+    return r2;
+}
+
+/* neighbour threshold: b is within the kernel radius 2h of a iff r2_lattice < thr(h) */
+unsigned long long orc_threshold(const orc_cfg* c, double h)
+{
+    double t = (2.0 * h) / c->delta;
+    double t2 = t * t;
+    if (!(t2 < 4.6e18)) return 4611686018427387904ULL;
+    return (unsigned long long)ceil(t2);
+}
+
+/* float64 minimum-image separation a - b */
+static void sep64(const orc_cfg* c, const orc_state* s, long long a, long long b, double d[3])
+{
+    d[0] = s->x[a] - s->x[b];
+    d[1] = s->y[a] - s->y[b];
+    d[2] = s->z[a] - s->z[b];
+    for (int k = 0; k < 3; ++k) {
+        if (c->periodic[k]) {
+            double L = box_len(c, k);
+            if (d[k] > 0.5 * L) d[k] -= L;
+            else if (d[k] < -0.5 * L) d[k] += L;
+        }
+    }
+}
+
+static int is_live(const orc_state* s, long long i) { return !(s->flags[i] & ORC_FLAG_DEAD); }
+
+/* --------------------------------------------------------- M4 cubic spline */
+
+/* f(q) and f'(q) of the M4 kernel, W = f(q)/(pi h^3), q = r/h, support 2h */
+static void m4(double q, double* f, double* df)
+{
+    if (q < 1.0) {
+        *f = 1.0 - 1.5 * q * q + 0.75 * q * q * q;
+        *df = -3.0 * q + 2.25 * q * q;
+    } else if (q < 2.0) {
+        double t = 2.0 - q;
+        *f = 0.25 * t * t * t;
+        *df = -0.75 * t * t;
+    } else {
+        *f = 0.0;
+        *df = 0.0;
+    }
+}
+
+void orc_kernel_m4(double q, double* out2) { m4(q, &out2[0], &out2[1]); }
+
+/* ------------------------------------------------ candidate enumeration */
+
+typedef struct {
+    int nc[3];
+    double cw[3];
+    long long* head; /* first particle of each cell (CSR over cells) */
+    long long* items;
+    long long ncell;
+} cellgrid;
+
+static long long cell_coord(const orc_cfg* c, const cellgrid* g, int k, double x)
+{
+    long long i = (long long)floor((x - c->lo[k]) / g->cw[k]);
+    if (c->periodic[k]) {
+        i %= g->nc[k];
+        if (i < 0) i += g->nc[k];
+    } else {
+        if (i < 0) i = 0;
+        if (i >= g->nc[k]) i = g->nc[k] - 1;
+    }
+    return i;
+}
+
+static void grid_build(const orc_cfg* c, const orc_state* s, double width, cellgrid* g)
+{
+    long long n = s->n;
+    for (int k = 0; k < 3; ++k) {
+        double L = box_len(c, k);
+        int m = (int)floor(L / width);
+        if (m < 1) m = 1;
+        if (m > 256) m = 256;
+        g->nc[k] = m;
+        g->cw[k] = L / m;
+    }
+    g->ncell = (long long)g->nc[0] * g->nc[1] * g->nc[2];
+    g->head = (long long*)calloc((size_t)g->ncell + 1, sizeof(long long));
+    g->items = (long long*)malloc(sizeof(long long) * (size_t)(n > 0 ? n : 1));
+    long long* cid = (long long*)malloc(sizeof(long long) * (size_t)(n > 0 ? n : 1));
+    for (long long i = 0; i < n; ++i) {
+        long long cx = cell_coord(c, g, 0, s->x[i]);
+        long long cy = cell_coord(c, g, 1, s->y[i]);
+        long long cz = cell_coord(c, g, 2, s->z[i]);
+        cid[i] = (cx * g->nc[1] + cy) * g->nc[2] + cz;
+        g->head[cid[i] + 1]++;
+    }
+    for (long long k = 0; k < g->ncell; ++k) g->head[k + 1] += g->head[k];
+    long long* fill = (long long*)malloc(sizeof(long long) * (size_t)g->ncell);
+    for (long long k = 0; k < g->ncell; ++k) fill[k] = g->head[k];
+    for (long long i = 0; i < n; ++i) g->items[fill[cid[i]]++] = i;
+    free(fill);
+    free(cid);
+}
+
+static void grid_free(cellgrid* g)
+{
+    free(g->head);
+    free(g->items);
+}
+
+typedef struct {
+    long long* idx;
+    double* r2;
+    long long n, cap;
+} blist;
+
+static void bl_push(blist* L, long long b, double r2)
+{
+    if (L->n == L->cap) {
+        L->cap = L->cap ? 2 * L->cap : 256;
+        L->idx = (long long*)realloc(L->idx, sizeof(long long) * (size_t)L->cap);
+        L->r2 = (double*)realloc(L->r2, sizeof(double) * (size_t)L->cap);
+    }
+    L->idx[L->n] = b;
+    L->r2[L->n] = r2;
+    L->n++;
+}
+
+static int cmp_ll(const void* a, const void* b)
+{
+    long long x = *(const long long*)a, y = *(const long long*)b;
+    return (x > y) - (x < y);
+}
+
+/* all live b (b may equal a) with |x_a - x_b| < R, sorted by index */
+static void gather_within(const orc_cfg* c, const orc_state* s, const cellgrid* g, long long a,
+                          double R, blist* out)
+{
+    out->n = 0;
+    double R2 = R * R;
+    if (!g) {
+        for (long long b = 0; b < s->n; ++b) {
+            if (!is_live(s, b)) continue;
+            double d[3];
+            sep64(c, s, a, b, d);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 < R2) bl_push(out, b, r2);
+        }
+        return;
+    }
+    long long ca[3] = {cell_coord(c, g, 0, s->x[a]), cell_coord(c, g, 1, s->y[a]),
+                       cell_coord(c, g, 2, s->z[a])};
+    long long lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+        long long m = (long long)ceil(R / g->cw[k]);
+        if (c->periodic[k]) {
+            if (2 * m + 1 >= g->nc[k]) {
+                lo[k] = 0;
+                hi[k] = g->nc[k] - 1;
+            } else {
+                lo[k] = ca[k] - m;
+                hi[k] = ca[k] + m;
+            }
+        } else {
+            lo[k] = ca[k] - m < 0 ? 0 : ca[k] - m;
+            hi[k] = ca[k] + m >= g->nc[k] ? g->nc[k] - 1 : ca[k] + m;
+        }
+    }
+    for (long long i = lo[0]; i <= hi[0]; ++i)
+        for (long long j = lo[1]; j <= hi[1]; ++j)
+            for (long long k = lo[2]; k <= hi[2]; ++k) {
+                long long ii = (i % g->nc[0] + g->nc[0]) % g->nc[0];
+                long long jj = (j % g->nc[1] + g->nc[1]) % g->nc[1];
+                long long kk = (k % g->nc[2] + g->nc[2]) % g->nc[2];
+                long long cell = (ii * g->nc[1] + jj) * g->nc[2] + kk;
+                for (long long t = g->head[cell]; t < g->head[cell + 1]; ++t) {
+                    long long b = g->items[t];
+                    if (!is_live(s, b)) continue;
+                    double d[3];
+                    sep64(c, s, a, b, d);
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (r2 < R2) bl_push(out, b, r2);
+                }
+            }
+    /* sort by particle index so that sums do not depend on the enumeration */
+    long long* key = (long long*)malloc(sizeof(long long) * (size_t)(out->n ? out->n : 1));
+    for (long long t = 0; t < out->n; ++t) key[t] = out->idx[t];
+    qsort(key, (size_t)out->n, sizeof(long long), cmp_ll);
+    for (long long t = 0; t < out->n; ++t) {
+        long long b = key[t];
+        double d[3];
+        sep64(c, s, a, b, d);
+        out->idx[t] = b;
+        out->r2[t] = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    }
+    free(key);
+}
+
+static double max_live_h(const orc_state* s)
+{
+    double m = 0.0;
+    for (long long i = 0; i < s->n; ++i)
+        if (is_live(s, i) && s->h[i] > m) m = s->h[i];
+    return m;
+}
+
+/* ------------------------------------------------------ neighbour lists */
+
+/*
+ * Neighbour lists on the quantised lattice.  mode 0 (gather): b != a with
+ * r2 < thr(h_a).  mode 1 (symmetric): r2 < max(thr(h_a), thr(h_b)).  Lists are
+ * in ascending index order.  Returns the total number of entries, or -1 if it
+ * exceeds cap (offsets are still complete).
+ */
+long long orc_neighbours(const orc_cfg* c, const orc_state* s, int mode, long long* offsets,
+                         int* idx, long long cap)
+{
+    long long n = s->n;
+    long long* xi = (long long*)malloc(sizeof(long long) * 3 * (size_t)(n ? n : 1));
+    orc_quantise(c, n, s->x, s->y, s->z, xi);
+    unsigned long long* thr =
+        (unsigned long long*)malloc(sizeof(unsigned long long) * (size_t)(n ? n : 1));
+    for (long long i = 0; i < n; ++i) thr[i] = orc_threshold(c, s->h[i]);
+    long long* cnt = (long long*)calloc((size_t)n + 1, sizeof(long long));
+    set_threads(c);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long long a = 0; a < n; ++a) {
+        if (!is_live(s, a)) continue;
+        long long k = 0;
+        for (long long b = 0; b < n; ++b) {
+            if (b == a || !is_live(s, b)) continue;
+            unsigned long long r2 = r2_lattice(c, &xi[3 * a], &xi[3 * b]);
+            unsigned long long t = thr[a];
+            if (mode == 1 && thr[b] > t) t = thr[b];
+            if (r2 < t) ++k;
+        }
+        cnt[a] = k;
+    }
+    offsets[0] = 0;
+    for (long long a = 0; a < n; ++a) offsets[a + 1] = offsets[a] + cnt[a];
+    long long total = offsets[n];
+    if (total > cap) {
+        free(xi);
+        free(thr);
+        free(cnt);
+        return -1;
+    }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long long a = 0; a < n; ++a) {
+        if (!is_live(s, a)) continue;
+        long long k = offsets[a];
+        for (long long b = 0; b < n; ++b) {
+            if (b == a || !is_live(s, b)) continue;
+            unsigned long long r2 = r2_lattice(c, &xi[3 * a], &xi[3 * b]);
+            unsigned long long t = thr[a];
+            if (mode == 1 && thr[b] > t) t = thr[b];
+            if (r2 < t) idx[k++] = (int)b;
+        }
+    }
+    free(xi);
+    free(thr);
+    free(cnt);
+    return total;
+}
+
+/* -------------------------------------------------------------- density */
+
+/*
+ * pi h^3 (rho_sum(h) - rho_h(h)) and its h-derivative over a candidate list of
+ * (r, m_b); non-decreasing in h with a single sign change.
+ */
+static double g_of_h(const orc_cfg* c, const double* r, const double* mb, long long n, double ma,
+                     double h, double* dg)
+{
+    double sum = 0.0, d = 0.0;
+    for (long long t = 0; t < n; ++t) {
+        double q = r[t] / h, f, df;
+        m4(q, &f, &df);
+        sum += mb[t] * f;
+        d += mb[t] * df * (-q / h);
+    }
+    if (dg) *dg = d;
+    return sum - M_PI * ma * c->hfact * c->hfact * c->hfact;
+}
+
+static void eos(const orc_cfg* c, const orc_state* s, long long a, double rho, double* P,
+                double* cs)
+{
+    if (c->eos == 0) {
+        *P = (c->gamma - 1.0) * rho * s->u[a];
+        *cs = sqrt(c->gamma * (*P) / rho);
+    } else {
+        double R = sqrt(s->x[a] * s->x[a] + s->y[a] * s->y[a]);
+        *cs = c->cs0 * pow(R, -c->qcs);
+        *P = (*cs) * (*cs) * rho;
+    }
+}
+
+/* density, h, Omega, nearest-neighbour distance, pressure and sound speed of particle a */
+static int density_one(const orc_cfg* c, orc_state* s, const cellgrid* g, const long long* xi,
+                       long long a, blist* L, double** rbuf, double** mbuf, long long* bufcap)
+{
+    double ma = mass_of(c, s->level[a]);
+    double hi = s->h[a] > 0.0 ? s->h[a] : c->delta * 1024.0;
+    /* find an upper bracket: enough mass within 2*hi */
+    long long n = 0;
+    double *r = NULL, *mb = NULL;
+    for (int it = 0;; ++it) {
+        gather_within(c, s, g, a, 2.0 * hi, L);
+        n = L->n;
+        if (n > *bufcap) {
+            *bufcap = 2 * n;
+            *rbuf = (double*)realloc(*rbuf, sizeof(double) * (size_t)*bufcap);
+            *mbuf = (double*)realloc(*mbuf, sizeof(double) * (size_t)*bufcap);
+        }
+        r = *rbuf;
+        mb = *mbuf;
+        for (long long t = 0; t < n; ++t) {
+            r[t] = sqrt(L->r2[t]);
+            mb[t] = mass_of(c, s->level[L->idx[t]]);
+        }
+        if (g_of_h(c, r, mb, n, ma, hi, NULL) > 0.0) break;
+        hi *= 1.5;
+        if (it > 200) return -1;
+    }
+    double lo = hi;
+    for (int it = 0; g_of_h(c, r, mb, n, ma, lo, NULL) >= 0.0; ++it) {
+        lo /= 1.5;
+        if (it > 400) return -1;
+    }
+    /* the root of g in (lo, hi): Newton steps kept inside the bracket, else bisection */
+    double h = 0.5 * (lo + hi);
+    for (int it = 0; it < 400; ++it) {
+        double dg;
+        double gv = g_of_h(c, r, mb, n, ma, h, &dg);
+        if (gv > 0.0) hi = h;
+        else lo = h;
+        double hn = (dg > 0.0) ? h - gv / dg : 0.5 * (lo + hi);
+        if (!(hn > lo && hn < hi)) hn = 0.5 * (lo + hi);
+        if (!(hn > lo && hn < hi) || hn == h) break;
+        if (fabs(hn - h) <= 4.0 * 2.220446049250313e-16 * h) {
+            h = hn;
+            break;
+        }
+        h = hn;
+    }
+    double hr = c->hfact / h;
+    double rho = ma * hr * hr * hr;
+    double dwdh = 0.0;
+    for (long long t = 0; t < n; ++t) {
+        double q = r[t] / h, f, df;
+        m4(q, &f, &df);
+        dwdh += mb[t] * (-(3.0 * f + q * df) / (M_PI * h * h * h * h));
+    }
+    s->h[a] = h;
+    s->rho[a] = rho;
+    s->omega[a] = 1.0 + h / (3.0 * rho) * dwdh;
+    /* nearest neighbour on the lattice among b != a with r2 < thr(h) */
+    unsigned long long thr = orc_threshold(c, h);
+    unsigned long long best = ~0ULL;
+    gather_within(c, s, g, a, 2.0 * h + 4.0 * c->delta, L);
+    for (long long t = 0; t < L->n; ++t) {
+        long long b = L->idx[t];
+        if (b == a) continue;
+        unsigned long long r2 = r2_lattice(c, &xi[3 * a], &xi[3 * b]);
+        if (r2 < thr && r2 < best) best = r2;
+    }
+    s->dnn[a] = best == ~0ULL ? INFINITY : sqrt((double)best) * c->delta;
+    double P, cs;
+    eos(c, s, a, rho, &P, &cs);
+    s->pres[a] = P;
+    s->cs[a] = cs;
+    return 0;
+}
+
+/*
+ * Solve for h, rho, Omega (and d_nn, P, c_s) of every live particle, or of the
+ * listed sample only (the others are read, not written).  Returns the number
+ * of particles whose bracket could not be found.
+ */
+long long orc_density(const orc_cfg* c, orc_state* s, const long long* sample, long long nsample)
+{
+    long long n = s->n;
+    long long* xi = (long long*)malloc(sizeof(long long) * 3 * (size_t)(n ? n : 1));
+    orc_quantise(c, n, s->x, s->y, s->z, xi);
+    cellgrid grid, *g = NULL;
+    if (c->enumerate == 1 && n > 0) {
+        grid_build(c, s, 0.5 * max_live_h(s), &grid);
+        g = &grid;
+    }
+    long long m = sample ? nsample : n;
+    long long bad = 0;
+    set_threads(c);
+#pragma omp parallel reduction(+ : bad)
+    {
+        blist L = {0};
+        double *rbuf = NULL, *mbuf = NULL;
+        long long bufcap = 0;
+#pragma omp for schedule(dynamic, 16)
+        for (long long t = 0; t < m; ++t) {
+            long long a = sample ? sample[t] : t;
+            if (!is_live(s, a)) continue;
+            if (density_one(c, s, g, xi, a, &L, &rbuf, &mbuf, &bufcap) != 0) ++bad;
+        }
+        free(rbuf);
+        free(mbuf);
+        free(L.idx);
+        free(L.r2);
+    }
+    if (g) grid_free(g);
+    free(xi);
+    return bad;
+}
+
+/* rho_sum(h) and sum_b m_b dW/dh(h) of particle a at a given h (self included) */
+void orc_rho_sum(const orc_cfg* c, const orc_state* s, long long a, double h, double* out2)
+{
+    blist L = {0};
+    gather_within(c, s, NULL, a, 2.0 * h, &L);
+    double rho = 0.0, dwdh = 0.0;
+    for (long long t = 0; t < L.n; ++t) {
+        double q = sqrt(L.r2[t]) / h, f, df;
+        m4(q, &f, &df);
+        double mb = mass_of(c, s->level[L.idx[t]]);
+        rho += mb * f / (M_PI * h * h * h);
+        dwdh += mb * (-(3.0 * f + q * df) / (M_PI * h * h * h * h));
+    }
+    out2[0] = rho;
+    out2[1] = dwdh;
+    free(L.idx);
+    free(L.r2);
+}
+
+/* ---------------------------------------------------------------- force */
+
+/* sum over the symmetric neighbour set nb[0..nn) (ascending index) of particle a */
+static void force_sum(const orc_cfg* c, orc_state* s, long long a, const long long* nb,
+                      long long nn)
+{
+    double axa = 0.0, aya = 0.0, aza = 0.0, du = 0.0, vsig = 0.0;
+    double ha = s->h[a], rhoa = s->rho[a], Oa = s->omega[a], Pa = s->pres[a], ca = s->cs[a];
+    for (long long t = 0; t < nn; ++t) {
+        long long b = nb[t];
+        if (b == a) continue;
+        double d[3];
+        sep64(c, s, a, b, d);
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double hb = s->h[b];
+        double qa = r / ha, qb = r / hb;
+        if (!(qa < 2.0 || qb < 2.0)) continue;
+        double rx = d[0] / r, ry = d[1] / r, rz = d[2] / r;
+        double fa, dfa, fb, dfb;
+        m4(qa, &fa, &dfa);
+        m4(qb, &fb, &dfb);
+        double Fa = dfa / (M_PI * ha * ha * ha * ha);
+        double Fb = dfb / (M_PI * hb * hb * hb * hb);
+        double vx = s->vx[a] - s->vx[b], vy = s->vy[a] - s->vy[b], vz = s->vz[a] - s->vz[b];
+        double vr = vx * rx + vy * ry + vz * rz;
+        double mb = mass_of(c, s->level[b]);
+        double rhob = s->rho[b], Ob = s->omega[b], Pb = s->pres[b], cb = s->cs[b];
+        /* artificial viscosity: approaching pairs only, signal speed alpha c_s + beta |v.r| */
+        double qava = 0.0, qavb = 0.0;
+        if (vr < 0.0) {
+            double vsa = c->alpha_av * ca + c->beta_av * (-vr);
+            double vsb = c->alpha_av * cb + c->beta_av * (-vr);
+            qava = -0.5 * rhoa * vsa * vr;
+            qavb = -0.5 * rhob * vsb * vr;
+        }
+        double ta = (Pa + qava) / (Oa * rhoa * rhoa) * Fa;
+        double tb = (Pb + qavb) / (Ob * rhob * rhob) * Fb;
+        double fac = -mb * (ta + tb);
+        axa += fac * rx;
+        aya += fac * ry;
+        aza += fac * rz;
+        if (c->eos == 0) {
+            du += mb * (Pa + qava) / (Oa * rhoa * rhoa) * vr * Fa;
+            if (c->alpha_u > 0.0) {
+                double vsu = sqrt(fabs(Pa - Pb) / (0.5 * (rhoa + rhob)));
+                du += mb * c->alpha_u * vsu * (s->u[a] - s->u[b]) * 0.5 *
+                      (Fa / (Oa * rhoa) + Fb / (Ob * rhob));
+            }
+        }
+        double vs = ca + c->beta_av * (vr < 0.0 ? -vr : 0.0);
+        if (vs > vsig) vsig = vs;
+    }
+    s->ax[a] = axa;
+    s->ay[a] = aya;
+    s->az[a] = aza;
+    s->dudt[a] = du;
+    s->vsig[a] = vsig > ca ? vsig : ca;
+}
+
+/*
+ * Hydrodynamic acceleration, du/dt and signal speed of every live particle
+ * (or of the sample).  Requires h, rho, omega, pres, cs of all neighbours.
+ * The symmetric set of a is {b : |r_ab| < 2 h_a} U {b : |r_ab| < 2 h_b}: built
+ * as the union of a's own gather list and the lists that contain a.
+ */
+void orc_force(const orc_cfg* c, orc_state* s, const long long* sample, long long nsample)
+{
+    long long n = s->n;
+    double hmax = max_live_h(s);
+    cellgrid grid, *g = NULL;
+    if (c->enumerate == 1 && n > 0) {
+        grid_build(c, s, 0.5 * hmax, &grid);
+        g = &grid;
+    }
+    set_threads(c);
+    if (sample) {
+#pragma omp parallel
+        {
+            blist L = {0};
+#pragma omp for schedule(dynamic, 16)
+            for (long long t = 0; t < nsample; ++t) {
+                long long a = sample[t];
+                if (!is_live(s, a)) continue;
+                gather_within(c, s, g, a, 2.0 * (s->h[a] > hmax ? s->h[a] : hmax), &L);
+                force_sum(c, s, a, L.idx, L.n);
+            }
+            free(L.idx);
+            free(L.r2);
+        }
+        if (g) grid_free(g);
+        return;
+    }
+    /* gather lists G_a (ascending), then reverse lists R_b = {a : b in G_a} (ascending) */
+    long long* gcnt = (long long*)calloc((size_t)n + 1, sizeof(long long));
+    long long** glist = (long long**)calloc((size_t)(n ? n : 1), sizeof(long long*));
+#pragma omp parallel
+    {
+        blist L = {0};
+#pragma omp for schedule(dynamic, 16)
+        for (long long a = 0; a < n; ++a) {
+            if (!is_live(s, a)) continue;
+            gather_within(c, s, g, a, 2.0 * s->h[a], &L);
+            glist[a] = (long long*)malloc(sizeof(long long) * (size_t)(L.n ? L.n : 1));
+            memcpy(glist[a], L.idx, sizeof(long long) * (size_t)L.n);
+            gcnt[a] = L.n;
+        }
+        free(L.idx);
+        free(L.r2);
+    }
+    long long* roff = (long long*)calloc((size_t)n + 1, sizeof(long long));
+    for (long long a = 0; a < n; ++a)
+        for (long long t = 0; t < gcnt[a]; ++t) roff[glist[a][t] + 1]++;
+    for (long long b = 0; b < n; ++b) roff[b + 1] += roff[b];
+    long long* rlist = (long long*)malloc(sizeof(long long) * (size_t)(roff[n] ? roff[n] : 1));
+    long long* fill = (long long*)malloc(sizeof(long long) * (size_t)(n ? n : 1));
+    for (long long b = 0; b < n; ++b) fill[b] = roff[b];
+    for (long long a = 0; a < n; ++a)
+        for (long long t = 0; t < gcnt[a]; ++t) rlist[fill[glist[a][t]]++] = a;
+#pragma omp parallel
+    {
+        long long* u = NULL;
+        long long ucap = 0;
+#pragma omp for schedule(dynamic, 16)
+        for (long long a = 0; a < n; ++a) {
+            if (!is_live(s, a)) continue;
+            long long na = gcnt[a], nr = roff[a + 1] - roff[a];
+            if (na + nr > ucap) {
+                ucap = 2 * (na + nr);
+                u = (long long*)realloc(u, sizeof(long long) * (size_t)ucap);
+            }
+            const long long* A = glist[a];
+            const long long* B = rlist + roff[a];
+            long long i = 0, j = 0, k = 0;
+            while (i < na || j < nr) {
+                long long v;
+                if (j >= nr || (i < na && A[i] < B[j])) v = A[i++];
+                else if (i >= na || B[j] < A[i]) v = B[j++];
+                else {
+                    v = A[i++];
+                    ++j;
+                }
+                u[k++] = v;
+            }
+            force_sum(c, s, a, u, k);
+        }
+        free(u);
+    }
+    for (long long a = 0; a < n; ++a) free(glist[a]);
+    free(glist);
+    free(gcnt);
+    free(roff);
+    free(rlist);
+    free(fill);
+    if (g) grid_free(g);
+}
+
+/* point-mass gravity: sinks on gas (added to a), gas and sinks on sinks */
+void orc_sink_gravity(const orc_cfg* c, orc_state* s, orc_sink* k, int nk)
+{
+    for (int j = 0; j < nk; ++j) k[j].a[0] = k[j].a[1] = k[j].a[2] = 0.0;
+    for (long long i = 0; i < s->n; ++i) {
+        if (!is_live(s, i)) continue;
+        double mi = mass_of(c, s->level[i]);
+        for (int j = 0; j < nk; ++j) {
+            double dx = s->x[i] - k[j].x[0], dy = s->y[i] - k[j].x[1], dz = s->z[i] - k[j].x[2];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            double r = sqrt(r2);
+            double f = c->G / (r2 * r);
+            s->ax[i] -= f * k[j].m * dx;
+            s->ay[i] -= f * k[j].m * dy;
+            s->az[i] -= f * k[j].m * dz;
+            k[j].a[0] += f * mi * dx;
+            k[j].a[1] += f * mi * dy;
+            k[j].a[2] += f * mi * dz;
+        }
+    }
+    for (int j = 0; j < nk; ++j)
+        for (int l = 0; l < nk; ++l) {
+            if (l == j) continue;
+            double dx = k[j].x[0] - k[l].x[0], dy = k[j].x[1] - k[l].x[1],
+                   dz = k[j].x[2] - k[l].x[2];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            double r = sqrt(r2);
+            double f = c->G * k[l].m / (r2 * r);
+            k[j].a[0] -= f * dx;
+            k[j].a[1] -= f * dy;
+            k[j].a[2] -= f * dz;
+        }
+}
+
+/* ----------------------------------------------------- refinement levels */
+
+/* level a region asks for at point p (Sec. 2.1 rule 1; nested boundaries, Table 1) */
+static int region_level(const orc_region* r, const double p[3])
+{
+    int lev = 0;
+    for (int k = 0; k < r->nlev; ++k) {
+        int inside;
+        if (r->shape == 0) {
+            double dx = p[0] - r->centre[0], dy = p[1] - r->centre[1], dz = p[2] - r->centre[2];
+            double d2 = dx * dx + dy * dy + dz * dz;
+            inside = d2 < r->R[k] * r->R[k];
+        } else {
+            double d = p[r->axis] - r->centre[r->axis];
+            inside = fabs(d) < r->R[k];
+        }
+        if (inside) lev = k + 1;
+    }
+    return lev;
+}
+
+/* target level: maximum over regions, default 0, capped at lmax; *which = deciding region */
+static int target_level(const orc_cfg* c, const orc_region* rg, int nr, const double p[3],
+                        int* which)
+{
+    int best = 0, w = -1;
+    for (int j = 0; j < nr; ++j) {
+        int l = region_level(&rg[j], p);
+        if (l > best) {
+            best = l;
+            w = j;
+        }
+    }
+    if (best > c->lmax) best = c->lmax;
+    if (which) *which = w;
+    return best;
+}
+
+void orc_target_levels(const orc_cfg* c, const orc_region* rg, int nr, long long n,
+                       const double* x, const double* y, const double* z, unsigned char* out)
+{
+    for (long long i = 0; i < n; ++i) {
+        double p[3] = {x[i], y[i], z[i]};
+        out[i] = (unsigned char)target_level(c, rg, nr, p, NULL);
+    }
+}
+
+void orc_track_regions(orc_region* rg, int nr, const orc_sink* k, int nk)
+{
+    for (int j = 0; j < nr; ++j) {
+        int t = rg[j].track_sink;
+        if (t >= 0 && t < nk)
+            for (int d = 0; d < 3; ++d) rg[j].centre[d] = k[t].x[d];
+    }
+}
+
+/* --------------------------------------------------------------- split */
+
+/* SplitMix64 output function (Steele, Lea & Flood 2014) */
+static unsigned long long splitmix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+unsigned long long orc_splitmix64(unsigned long long z) { return splitmix64(z); }
+
+/* the split's random number in [-1, 1) from (seed, particle id, step) */
+double orc_split_uniform(unsigned long long seed, unsigned long long id, unsigned long long step)
+{
+    unsigned long long z = splitmix64(splitmix64(splitmix64(seed) ^ id) ^ step);
+    return (double)(z >> 11) * 2.220446049250313e-16 - 1.0;
+}
+
+static double wrap1(const orc_cfg* c, int k, double x)
+{
+    if (c->periodic[k]) {
+        double L = box_len(c, k);
+        if (x >= c->hi[k]) x -= L;
+        else if (x < c->lo[k]) x += L;
+    }
+    return x;
+}
+
+/*
+ * Unit direction w along which the two children are placed: perpendicular to
+ * the vector v from the zone centre to the parent (so tangential to a sphere;
+ * in the plane of a slab), rotated about v by a random angle (Sec. 2.2).
+ * The angle enters through t in [-1,1): cos = (1-t^2)/(1+t^2), sin = 2t/(1+t^2).
+ */
+void orc_split_direction(const orc_region* r, const double p[3], double t, double w[3])
+{
+    double v[3];
+    if (r->shape == 0) {
+        v[0] = p[0] - r->centre[0];
+        v[1] = p[1] - r->centre[1];
+        v[2] = p[2] - r->centre[2];
+        double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (vn > 0.0) {
+            v[0] = v[0] / vn;
+            v[1] = v[1] / vn;
+            v[2] = v[2] / vn;
+        } else {
+            v[0] = 1.0;
+            v[1] = 0.0;
+            v[2] = 0.0;
+        }
+    } else {
+        v[0] = v[1] = v[2] = 0.0;
+        v[r->axis] = p[r->axis] - r->centre[r->axis] >= 0.0 ? 1.0 : -1.0;
+    }
+    /* axis least aligned with v (lowest index on a tie) */
+    int k = 0;
+    for (int j = 1; j < 3; ++j)
+        if (fabs(v[j]) < fabs(v[k])) k = j;
+    double e[3] = {0.0, 0.0, 0.0};
+    e[k] = 1.0;
+    double w1[3] = {v[1] * e[2] - v[2] * e[1], v[2] * e[0] - v[0] * e[2], v[0] * e[1] - v[1] * e[0]};
+    double n1 = sqrt(w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2]);
+    w1[0] = w1[0] / n1;
+    w1[1] = w1[1] / n1;
+    w1[2] = w1[2] / n1;
+    double w2[3] = {v[1] * w1[2] - v[2] * w1[1], v[2] * w1[0] - v[0] * w1[2],
+                    v[0] * w1[1] - v[1] * w1[0]};
+    double den = 1.0 + t * t;
+    double cs = (1.0 - t * t) / den;
+    double sn = (2.0 * t) / den;
+    for (int j = 0; j < 3; ++j) w[j] = cs * w1[j] + sn * w2[j];
+}
+
+static void copy_particle(orc_state* s, long long dst, long long src)
+{
+#define CP(f) s->f[dst] = s->f[src]
+    CP(x); CP(y); CP(z); CP(vx); CP(vy); CP(vz); CP(u); CP(h);
+    CP(rho); CP(omega); CP(ax); CP(ay); CP(az); CP(dudt); CP(vsig); CP(dnn); CP(pres); CP(cs);
+    CP(level); CP(flags); CP(id);
+#undef CP
+}
+
+/*
+ * One split pass over level l (Sec. 2.2, Sec. 2.6): every live, unchanged,
+ * non-fixed particle at level l whose target level exceeds l is split.  In
+ * ascending index order the k-th split parent keeps its slot (child at +r_sep w)
+ * and the new child goes to slot n + k (at -r_sep w) with id next_id + k.
+ * Returns the number of splits, or -1 (state untouched) if capacity is short.
+ */
+long long orc_split_pass(const orc_cfg* c, orc_state* s, const orc_region* rg, int nr, int l,
+                         unsigned long long step)
+{
+    long long n = s->n, ns = 0;
+    for (long long i = 0; i < n; ++i) {
+        if (s->level[i] != l || (s->flags[i] & (ORC_FLAG_CHANGED | ORC_FLAG_FIXED | ORC_FLAG_DEAD)))
+            continue;
+        double p[3] = {s->x[i], s->y[i], s->z[i]};
+        if (target_level(c, rg, nr, p, NULL) > l) ++ns;
+    }
+    if (n + ns > s->cap) return -1;
+    long long k = 0;
+    for (long long i = 0; i < n; ++i) {
+        if (s->level[i] != l || (s->flags[i] & (ORC_FLAG_CHANGED | ORC_FLAG_FIXED | ORC_FLAG_DEAD)))
+            continue;
+        double p[3] = {s->x[i], s->y[i], s->z[i]};
+        int which;
+        if (target_level(c, rg, nr, p, &which) <= l) continue;
+        double t = orc_split_uniform(c->seed, s->id[i], step);
+        double w[3];
+        orc_split_direction(&rg[which], p, t, w);
+        double rsep = c->rsep_fac * s->h[i];
+        double cap = c->dnn_cap * s->dnn[i];
+        if (cap < rsep) rsep = cap;
+        long long j = n + k;
+        copy_particle(s, j, i);
+        s->x[i] = wrap1(c, 0, p[0] + rsep * w[0]);
+        s->y[i] = wrap1(c, 1, p[1] + rsep * w[1]);
+        s->z[i] = wrap1(c, 2, p[2] + rsep * w[2]);
+        s->x[j] = wrap1(c, 0, p[0] - rsep * w[0]);
+        s->y[j] = wrap1(c, 1, p[1] - rsep * w[1]);
+        s->z[j] = wrap1(c, 2, p[2] - rsep * w[2]);
+        double hn = s->h[i] * ORC_SPLIT_HFAC;
+        s->h[i] = s->h[j] = hn;
+        s->level[i] = s->level[j] = (unsigned char)(l + 1);
+        s->flags[i] |= ORC_FLAG_CHANGED;
+        s->flags[j] |= ORC_FLAG_CHANGED;
+        s->id[j] = (unsigned long long)(s->next_id + k);
+        ++k;
+    }
+    s->n = n + ns;
+    s->next_id += ns;
+    return ns;
+}
+
+/* --------------------------------------------------------------- merge */
+
+static int cmp_u64(const void* a, const void* b)
+{
+    unsigned long long x = *(const unsigned long long*)a, y = *(const unsigned long long*)b;
+    return (x > y) - (x < y);
+}
+
+/*
+ * Pairing tree (Sec. 2.3).  set[0..m) holds particle indices (m even); xi are
+ * their lattice coordinates indexed by particle.  A node with more than two
+ * particles is cut through its centre of mass (all masses equal within a
+ * level, so the mean lattice coordinate, floored) along the axis of largest
+ * extent; the cut count is kept even by moving the cut across one particle
+ * towards the more balanced side.  On return set is reordered so that
+ * (set[2j], set[2j+1]) are the leaves.  Returns 0, or -1 on bad input.
+ */
+int orc_pair_tree(const long long* xi, long long* set, long long m)
+{
+    if (m % 2) return -1;
+    if (m == 0) return 0;
+    unsigned long long* key = (unsigned long long*)malloc(sizeof(unsigned long long) * (size_t)m);
+    long long* stk = (long long*)malloc(sizeof(long long) * 2 * (size_t)(m + 2));
+    long long sp = 0;
+    stk[sp++] = 0;
+    stk[sp++] = m;
+    while (sp > 0) {
+        long long n = stk[--sp];
+        long long off = stk[--sp];
+        if (n <= 2) continue;
+        long long* S = set + off;
+        long long lo[3], hi[3];
+        for (int k = 0; k < 3; ++k) lo[k] = hi[k] = xi[3 * S[0] + k];
+        for (long long t = 1; t < n; ++t)
+            for (int k = 0; k < 3; ++k) {
+                long long v = xi[3 * S[t] + k];
+                if (v < lo[k]) lo[k] = v;
+                if (v > hi[k]) hi[k] = v;
+            }
+        int ax = 0;
+        for (int k = 1; k < 3; ++k)
+            if (hi[k] - lo[k] > hi[ax] - lo[ax]) ax = k;
+        unsigned long long sum = 0;
+        for (long long t = 0; t < n; ++t) sum += (unsigned long long)xi[3 * S[t] + ax];
+        long long com = (long long)(sum / (unsigned long long)n);
+        for (long long t = 0; t < n; ++t)
+            key[t] = ((unsigned long long)xi[3 * S[t] + ax] << 32) | (unsigned long long)S[t];
+        qsort(key, (size_t)n, sizeof(unsigned long long), cmp_u64);
+        for (long long t = 0; t < n; ++t) S[t] = (long long)(key[t] & 0xffffffffULL);
+        long long k = 0;
+        while (k < n && xi[3 * S[k] + ax] < com) ++k;
+        if (k == 0)
+            while (k < n && xi[3 * S[k] + ax] <= com) ++k;
+        if (k == n) {
+            k = 2 * (n / 4);
+        } else if (k % 2) {
+            long long a = k - 1, b = k + 1;
+            long long da = 2 * a - n, db = 2 * b - n;
+            if (da < 0) da = -da;
+            if (db < 0) db = -db;
+            k = (da <= db) ? a : b;
+        }
+        stk[sp++] = off;
+        stk[sp++] = k;
+        stk[sp++] = off + k;
+        stk[sp++] = n - k;
+    }
+    free(key);
+    free(stk);
+    return 0;
+}
+
+/*
+ * One merge pass over level l >= 1 (Sec. 2.3).  Candidates: live, unchanged,
+ * non-fixed particles at level l in ascending index order; with an odd count
+ * the last one is left out (*spare = its index, else -1).  For each leaf pair
+ * whose centre of mass lies at a target level below l, the lower index
+ * survives at the centre of mass with the mean velocity and thermal energy,
+ * h * 2^(1/3), level l-1; the other is marked dead.  Returns merges done.
+ */
+long long orc_merge_pass(const orc_cfg* c, orc_state* s, const orc_region* rg, int nr, int l,
+                         long long* spare)
+{
+    long long n = s->n, m = 0;
+    *spare = -1;
+    long long* set = (long long*)malloc(sizeof(long long) * (size_t)(n ? n : 1));
+    for (long long i = 0; i < n; ++i)
+        if (s->level[i] == l &&
+            !(s->flags[i] & (ORC_FLAG_CHANGED | ORC_FLAG_FIXED | ORC_FLAG_DEAD)))
+            set[m++] = i;
+    if (m % 2) {
+        *spare = set[m - 1];
+        --m;
+    }
+    long long nm = 0;
+    if (m >= 2) {
+        long long* xi = (long long*)malloc(sizeof(long long) * 3 * (size_t)n);
+        orc_quantise(c, n, s->x, s->y, s->z, xi);
+        orc_pair_tree(xi, set, m);
+        for (long long j = 0; j < m; j += 2) {
+            long long a = set[j], b = set[j + 1];
+            if (b < a) {
+                long long t = a;
+                a = b;
+                b = t;
+            }
+            double pa[3] = {s->x[a], s->y[a], s->z[a]}, pb[3] = {s->x[b], s->y[b], s->z[b]};
+            double com[3];
+            for (int k = 0; k < 3; ++k) {
+                double d = pb[k] - pa[k];
+                if (c->periodic[k]) {
+                    double L = box_len(c, k);
+                    if (d > 0.5 * L) d -= L;
+                    else if (d < -0.5 * L) d += L;
+                }
+                com[k] = wrap1(c, k, pa[k] + 0.5 * d);
+            }
+            if (target_level(c, rg, nr, com, NULL) >= l) continue;
+            s->x[a] = com[0];
+            s->y[a] = com[1];
+            s->z[a] = com[2];
+            s->vx[a] = 0.5 * (s->vx[a] + s->vx[b]);
+            s->vy[a] = 0.5 * (s->vy[a] + s->vy[b]);
+            s->vz[a] = 0.5 * (s->vz[a] + s->vz[b]);
+            s->u[a] = 0.5 * (s->u[a] + s->u[b]);
+            s->h[a] = s->h[a] * ORC_MERGE_HFAC;
+            s->level[a] = (unsigned char)(l - 1);
+            s->flags[a] |= ORC_FLAG_CHANGED;
+            s->flags[b] |= ORC_FLAG_DEAD;
+            ++nm;
+        }
+        free(xi);
+    }
+    free(set);
+    return nm;
+}
+
+/* stable removal of dead particles; returns the number removed */
+long long orc_compact(orc_state* s)
+{
+    long long k = 0, n = s->n;
+    for (long long i = 0; i < n; ++i) {
+        if (s->flags[i] & ORC_FLAG_DEAD) continue;
+        if (k != i) copy_particle(s, k, i);
+        ++k;
+    }
+    s->n = k;
+    return n - k;
+}
+
+/*
+ * Full split/merge pass of one step (Sec. 2.6): clear the changed marks, split
+ * level by level from 0 up, merge level by level from lmax down, then compact.
+ * Returns 0, or -1 if capacity ran out (splits done so far are kept).
+ */
+int orc_split_merge(const orc_cfg* c, orc_state* s, const orc_region* rg, int nr,
+                    unsigned long long step, orc_counts* cnt)
+{
+    memset(cnt, 0, sizeof(*cnt));
+    for (long long i = 0; i < s->n; ++i) s->flags[i] &= (unsigned char)~ORC_FLAG_CHANGED;
+    for (int l = 0; l < c->lmax; ++l) {
+        long long ns = orc_split_pass(c, s, rg, nr, l, step);
+        if (ns < 0) return -1;
+        cnt->n_split[l] = ns;
+    }
+    for (int l = c->lmax; l >= 1; --l) {
+        long long spare;
+        cnt->n_merge[l] = orc_merge_pass(c, s, rg, nr, l, &spare);
+        cnt->n_spare[l] = spare >= 0 ? 1 : 0;
+    }
+    cnt->n_dead = orc_compact(s);
+    return 0;
+}
+
+/* ------------------------------------------------------ sinks / stepping */
+
+/* accretion: a live gas particle inside a sink's radius is absorbed (first sink wins) */
+long long orc_accrete(const orc_cfg* c, orc_state* s, orc_sink* k, int nk)
+{
+    long long na = 0;
+    for (int j = 0; j < nk; ++j) {
+        double M = 0.0, P[3] = {0, 0, 0}, X[3] = {0, 0, 0};
+        for (long long i = 0; i < s->n; ++i) {
+            if (s->flags[i] & (ORC_FLAG_DEAD | ORC_FLAG_FIXED)) continue;
+            double dx = s->x[i] - k[j].x[0], dy = s->y[i] - k[j].x[1], dz = s->z[i] - k[j].x[2];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (!(r2 < k[j].racc * k[j].racc)) continue;
+            double mi = mass_of(c, s->level[i]);
+            M += mi;
+            P[0] += mi * s->vx[i];
+            P[1] += mi * s->vy[i];
+            P[2] += mi * s->vz[i];
+            X[0] += mi * s->x[i];
+            X[1] += mi * s->y[i];
+            X[2] += mi * s->z[i];
+            s->flags[i] |= ORC_FLAG_DEAD;
+            ++na;
+        }
+        if (M > 0.0) {
+            double mt = k[j].m + M;
+            for (int d = 0; d < 3; ++d) {
+                k[j].v[d] = (k[j].m * k[j].v[d] + P[d]) / mt;
+                k[j].x[d] = (k[j].m * k[j].x[d] + X[d]) / mt;
+            }
+            k[j].m = mt;
+        }
+    }
+    return na;
+}
+
+void orc_stats_compute(const orc_cfg* c, const orc_state* s, const orc_sink* k, int nk,
+                       orc_stats* st)
+{
+    memset(st, 0, sizeof(*st));
+    for (long long i = 0; i < s->n; ++i) {
+        if (!is_live(s, i)) continue;
+        double m = mass_of(c, s->level[i]);
+        st->mass += m;
+        st->mom[0] += m * s->vx[i];
+        st->mom[1] += m * s->vy[i];
+        st->mom[2] += m * s->vz[i];
+        st->ang[0] += m * (s->y[i] * s->vz[i] - s->z[i] * s->vy[i]);
+        st->ang[1] += m * (s->z[i] * s->vx[i] - s->x[i] * s->vz[i]);
+        st->ang[2] += m * (s->x[i] * s->vy[i] - s->y[i] * s->vx[i]);
+        st->ekin += 0.5 * m * (s->vx[i] * s->vx[i] + s->vy[i] * s->vy[i] + s->vz[i] * s->vz[i]);
+        if (c->eos == 0) st->etherm += m * s->u[i];
+    }
+    for (int j = 0; j < nk; ++j) {
+        double m = k[j].m;
+        st->mass += m;
+        for (int d = 0; d < 3; ++d) st->mom[d] += m * k[j].v[d];
+        st->ang[0] += m * (k[j].x[1] * k[j].v[2] - k[j].x[2] * k[j].v[1]);
+        st->ang[1] += m * (k[j].x[2] * k[j].v[0] - k[j].x[0] * k[j].v[2]);
+        st->ang[2] += m * (k[j].x[0] * k[j].v[1] - k[j].x[1] * k[j].v[0]);
+        st->ekin += 0.5 * m * (k[j].v[0] * k[j].v[0] + k[j].v[1] * k[j].v[1] + k[j].v[2] * k[j].v[2]);
+    }
+}
+
+/* next time step: min over moving particles of C_cour h / v_sig and C_force sqrt(h/|a|) */
+double orc_timestep(const orc_cfg* c, const orc_state* s)
+{
+    double dt = INFINITY;
+    for (long long i = 0; i < s->n; ++i) {
+        if (s->flags[i] & (ORC_FLAG_DEAD | ORC_FLAG_FIXED)) continue;
+        if (s->vsig[i] > 0.0) {
+            double t = c->ccour * s->h[i] / s->vsig[i];
+            if (t < dt) dt = t;
+        }
+        double a = sqrt(s->ax[i] * s->ax[i] + s->ay[i] * s->ay[i] + s->az[i] * s->az[i]);
+        if (a > 0.0) {
+            double t = c->cforce * sqrt(s->h[i] / a);
+            if (t < dt) dt = t;
+        }
+    }
+    return dt;
+}
+
+/* density, then hydro forces, then point-mass gravity */
+long long orc_density_force(const orc_cfg* c, orc_state* s, orc_sink* k, int nk)
+{
+    long long bad = orc_density(c, s, NULL, 0);
+    orc_force(c, s, NULL, 0);
+    if (nk > 0) orc_sink_gravity(c, s, k, nk);
+    return bad;
+}
+
+/*
+ * Initial refinement: repeat (density; one split/merge pass) until no particle
+ * changes level, so that particles reach the full depth of nested zones; then
+ * density and forces.  Returns passes used, or -1 on capacity shortage.
+ */
+int orc_init(const orc_cfg* c, orc_state* s, orc_region* rg, int nr, orc_sink* k, int nk,
+             unsigned long long* step)
+{
+    orc_track_regions(rg, nr, k, nk);
+    int passes = 0;
+    for (;;) {
+        orc_density(c, s, NULL, 0);
+        orc_counts cnt;
+        if (orc_split_merge(c, s, rg, nr, *step, &cnt) != 0) return -1;
+        (*step)++;
+        ++passes;
+        long long changed = 0;
+        for (int l = 0; l < ORC_MAXLEV; ++l) changed += cnt.n_split[l] + cnt.n_merge[l];
+        if (changed == 0 || passes > 4 * ORC_MAXLEV) break;
+    }
+    for (long long i = 0; i < s->n; ++i) s->flags[i] &= (unsigned char)~ORC_FLAG_CHANGED;
+    orc_density_force(c, s, k, nk);
+    return passes;
+}
+
+/*
+ * One kick-drift-kick step: half kick (gas and sinks), drift, accretion,
+ * regions follow their sinks, split/merge + compaction, density, forces,
+ * half kick.  Fixed particles are not moved.
+ */
+int orc_step(const orc_cfg* c, orc_state* s, orc_region* rg, int nr, orc_sink* k, int nk,
+             double dt, unsigned long long step, orc_counts* cnt, orc_stats* st)
+{
+    double hdt = 0.5 * dt;
+    for (long long i = 0; i < s->n; ++i) {
+        if (s->flags[i] & (ORC_FLAG_FIXED | ORC_FLAG_DEAD)) continue;
+        s->vx[i] += hdt * s->ax[i];
+        s->vy[i] += hdt * s->ay[i];
+        s->vz[i] += hdt * s->az[i];
+        if (c->eos == 0) s->u[i] += hdt * s->dudt[i];
+    }
+    for (int j = 0; j < nk; ++j)
+        for (int d = 0; d < 3; ++d) k[j].v[d] += hdt * k[j].a[d];
+    for (long long i = 0; i < s->n; ++i) {
+        if (s->flags[i] & (ORC_FLAG_FIXED | ORC_FLAG_DEAD)) continue;
+        s->x[i] = wrap1(c, 0, s->x[i] + dt * s->vx[i]);
+        s->y[i] = wrap1(c, 1, s->y[i] + dt * s->vy[i]);
+        s->z[i] = wrap1(c, 2, s->z[i] + dt * s->vz[i]);
+    }
+    for (int j = 0; j < nk; ++j)
+        for (int d = 0; d < 3; ++d) k[j].x[d] += dt * k[j].v[d];
+    long long na = nk > 0 ? orc_accrete(c, s, k, nk) : 0;
+    orc_track_regions(rg, nr, k, nk);
+    if (orc_split_merge(c, s, rg, nr, step, cnt) != 0) return -1;
+    cnt->n_accreted = na;
+    orc_density_force(c, s, k, nk);
+    for (long long i = 0; i < s->n; ++i) {
+        if (s->flags[i] & (ORC_FLAG_FIXED | ORC_FLAG_DEAD)) continue;
+        s->vx[i] += hdt * s->ax[i];
+        s->vy[i] += hdt * s->ay[i];
+        s->vz[i] += hdt * s->az[i];
+        if (c->eos == 0) s->u[i] += hdt * s->dudt[i];
+    }
+    for (int j = 0; j < nk; ++j)
+        for (int d = 0; d < 3; ++d) k[j].v[d] += hdt * k[j].a[d];
+    orc_stats_compute(c, s, k, nk, st);
+    return 0;
+}

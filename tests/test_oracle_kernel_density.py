@@ -1,0 +1,150 @@
+"""Pins of the oracle's kernel and density solve (not GPU).
+
+The paper fixes the kernel radius and the h_fact convention only through
+Table 2 (M4, h_fact = 1.2, N_neigh = 57.9); the density itself is the standard
+grad-h SPH relation it cites.  Each test checks the oracle against something
+other than its own formulas: quadrature, finite differences, a lattice, an
+independent float distance computation, Table 2.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import apr_synth
+import oracle
+from conftest import read_golden
+
+
+def test_m4_normalised_to_unity():
+    # W = f(q)/(pi h^3): integral over the sphere of radius 2h is 4 int_0^2 q^2 f(q) dq
+    val, _ = integrate.quad(lambda q: 4.0 * q * q * oracle.kernel_m4(q)[0], 0.0, 2.0,
+                            points=[1.0])
+    assert abs(val - 1.0) < 1e-12
+
+
+def test_m4_derivative_matches_finite_difference():
+    e = 1e-6
+    for q in np.linspace(0.05, 1.95, 39):
+        fd = (oracle.kernel_m4(q + e)[0] - oracle.kernel_m4(q - e)[0]) / (2 * e)
+        assert abs(fd - oracle.kernel_m4(q)[1]) < 1e-8
+
+
+def test_m4_continuous_and_compact():
+    for q in (1.0, 2.0):
+        lo, hi = oracle.kernel_m4(q - 1e-12), oracle.kernel_m4(q + 1e-12)
+        assert abs(lo[0] - hi[0]) < 1e-10 and abs(lo[1] - hi[1]) < 1e-10
+    assert tuple(oracle.kernel_m4(2.0)) == (0.0, 0.0)
+    assert oracle.kernel_m4(0.0)[0] == 1.0
+
+
+def test_table2_neighbour_number():
+    rows = {r[0]: (float(r[1]), float(r[2])) for r in read_golden("table2_kernels.txt")}
+    nn, hfact = rows["M4"]
+    # closed form for a kernel of radius 2h
+    assert round(4.0 * math.pi / 3.0 * (2.0 * hfact) ** 3, 1) == nn
+    # the oracle's solved h on the jittered lattice gives that many neighbours (self included)
+    w = apr_synth.c1_lattice()
+    assert w["cfg"]["hfact"] == hfact
+    o = oracle.Oracle(w)
+    o.density()
+    off, _ = o.neighbours(0)
+    assert abs(np.diff(off).mean() + 1.0 - nn) < 2.0
+
+
+def test_lattice_density_uniform_and_rho0():
+    w = apr_synth.lattice_box(16, jitter=0.0, sphere_R=())
+    o = oracle.Oracle(w)
+    assert o.density() == 0
+    rho = o["rho"]
+    assert rho.max() / rho.min() - 1.0 < 1e-12
+    assert abs(rho.mean() / w["rho0"] - 1.0) < 1e-2
+    h = o["h"]
+    assert np.allclose(h, w["cfg"]["hfact"] * (o.mass() / rho) ** (1 / 3), rtol=1e-14, atol=0)
+
+
+def test_solved_h_is_root_of_density_relation():
+    o = oracle.Oracle(apr_synth.c1_lattice())
+    o.density()
+    m = o.mass()
+    for a in range(0, o.n, 257):
+        rs, _ = o.rho_sum(a, o["h"][a])
+        rh = m[a] * (o.cfg.hfact / o["h"][a]) ** 3
+        assert abs(rs / rh - 1.0) < 1e-12
+        assert abs(o["rho"][a] / rs - 1.0) < 1e-12
+
+
+def test_omega_matches_finite_difference_of_density_sum():
+    o = oracle.Oracle(apr_synth.c1_lattice())
+    o.density()
+    for a in range(0, o.n, 511):
+        h = o["h"][a]
+        e = 1e-6 * h
+        drho_dh = (o.rho_sum(a, h + e)[0] - o.rho_sum(a, h - e)[0]) / (2 * e)
+        rho = o["rho"][a]
+        omega_fd = 1.0 + h / (3.0 * rho) * drho_dh
+        assert abs(omega_fd - o["omega"][a]) < 1e-7
+
+
+def test_enumeration_modes_give_identical_results():
+    w = apr_synth.c1_lattice()
+    res = []
+    for mode in (0, 1):
+        o = oracle.Oracle(w, enumerate=mode)
+        o.density()
+        o.force()
+        res.append({f: o[f].copy() for f in ("h", "rho", "omega", "dnn", "ax", "ay", "dudt")})
+    for f in res[0]:
+        assert np.array_equal(res[0][f], res[1][f]), f
+
+
+def _float_pairs(x, y, z, h, L=1.0):
+    d = np.stack([x[:, None] - x[None, :], y[:, None] - y[None, :], z[:, None] - z[None, :]])
+    d -= L * np.round(d / L)
+    r = np.sqrt((d ** 2).sum(0))
+    return r
+
+
+def test_neighbour_lists_match_float_distances():
+    o = oracle.Oracle(apr_synth.c1_lattice())
+    o.density()
+    off, idx = o.neighbours(0)
+    r = _float_pairs(o["x"], o["y"], o["z"], o["h"])
+    twoh = 2.0 * o["h"][:, None]
+    delta = o.cfg.delta
+    inside = (r < twoh) & ~np.eye(o.n, dtype=bool)
+    margin = np.abs(r - twoh) > 8 * delta
+    for a in range(0, o.n, 37):
+        got = np.zeros(o.n, bool)
+        got[idx[off[a]:off[a + 1]]] = True
+        assert np.array_equal(got[margin[a]], inside[a][margin[a]])
+    # symmetric lists contain the gather lists and are symmetric
+    offs, idxs = o.neighbours(1)
+    pairs = set()
+    for a in range(o.n):
+        for b in idxs[offs[a]:offs[a + 1]]:
+            pairs.add((a, int(b)))
+    assert all((b, a) in pairs for (a, b) in pairs)
+
+
+def test_nearest_neighbour_distance():
+    o = oracle.Oracle(apr_synth.c1_lattice())
+    o.density()
+    r = _float_pairs(o["x"], o["y"], o["z"], o["h"])
+    np.fill_diagonal(r, np.inf)
+    dmin = r.min(1)
+    assert np.all(np.abs(o["dnn"] - dmin) < 4 * o.cfg.delta)
+
+
+def test_mixed_masses_keep_density():
+    # split every particle once (zone covers the box): twice the particles, half the mass
+    w = apr_synth.lattice_box(12, jitter=0.05, sphere_R=(5.0,))
+    o = oracle.Oracle(w, capacity=4 * 12 ** 3)
+    o.density()
+    m_before = o.mass().sum()
+    ns = o.split_pass(0, 0)
+    assert ns == 12 ** 3 and o.n == 2 * 12 ** 3
+    assert o.mass().sum() == m_before
+    o.density()
+    assert abs(o["rho"].mean() / w["rho0"] - 1.0) < 0.03
