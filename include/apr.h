@@ -1,0 +1,224 @@
+/*
+ * apr.h -- C ABI of the GB300 adaptive particle refinement (APR) SPH library.
+ *
+ * Method: Nealon & Price, "Adaptive particle refinement for compressible
+ * smoothed particle hydrodynamics" (arXiv 2409.11470).  The library runs the
+ * data-parallel hot path of one time step on one GPU: refinement zones
+ * (Sec. 2.1), split (Sec. 2.2, Eq. 2), pairing tree and merge (Sec. 2.3,
+ * Eq. 3, Eq. 4) in the per-step order of Sec. 2.6, the neighbour search, the
+ * h-rho density solve and the force / energy sums over particles of mixed
+ * mass (Eq. 1) and smoothing length, point-mass gravity with accretion, and a
+ * kick-drift-kick update.
+ *
+ * Conventions (all entry points):
+ *  - Plain C types only.  Particle arrays and the workspace are DEVICE
+ *    pointers owned by the caller; the library owns only the opaque context
+ *    and a few bytes of pinned host memory for status read-back.
+ *  - All GPU work is ordered on the stream given to apr_create; calls return
+ *    after the host has read whatever counts it reports (a short
+ *    device-to-host copy), so the particle count is always current on return.
+ *  - Nothing is allocated on the device after apr_bind.
+ *  - Errors are status codes; no exception crosses the ABI.  apr_last_error
+ *    returns a text for the last failing call on that context.
+ *  - Particle order is the caller's: indices are stable except that split
+ *    children are appended at the end (slot n + rank) and merged-away or
+ *    accreted particles are removed by a stable compaction.
+ */
+#ifndef APR_H
+#define APR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define APR_MAXLEV 8
+#define APR_MAXREG 8
+#define APR_MAXSINK 8
+
+typedef enum {
+    APR_OK = 0,
+    APR_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, bad config) */
+    APR_ERR_CAPACITY = 2,       /* a split would exceed the bound capacity; state unchanged */
+    APR_ERR_NR_NOCONV = 3,      /* some h-rho iterations did not converge (best effort kept) */
+    APR_ERR_NEIGH_OVERFLOW = 4, /* a neighbour or candidate list exceeded its capacity */
+    APR_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+    APR_ERR_STATE = 6,          /* call out of order (e.g. before apr_bind) */
+    APR_ERR_WORKSPACE = 7       /* workspace too small for the bound capacity */
+} apr_status;
+
+/* particle flag bits */
+enum { APR_FLAG_CHANGED = 1, APR_FLAG_FIXED = 2, APR_FLAG_DEAD = 4 };
+enum { APR_SHAPE_SPHERE = 0, APR_SHAPE_SLAB = 1 };
+enum { APR_EOS_ADIABATIC = 0, APR_EOS_LOCALLY_ISOTHERMAL = 1 };
+enum { APR_PREC_FP32_MIXED = 0, APR_PREC_FP64 = 1 };
+
+/*
+ * Run configuration.  box_lo/box_hi: domain; periodic axes wrap.  delta: the
+ * quantisation unit D of the integer lattice x_int = floor((x - lo)/D) on
+ * which all decisions (neighbour membership, nearest-neighbour distance,
+ * pairing-tree cuts) are taken; (hi - lo)/D must be <= 2^30 and an exact
+ * integer on periodic axes.  hfact: h = hfact (m/rho)^(1/3) (Table 2).
+ * m0: mass at level 0 (Eq. 1).  lmax: deepest level.  rsep_fac, dnn_cap: the
+ * split separation min(rsep_fac h, dnn_cap d_nn) (Sec. 2.2; 0.2 and 0.35).
+ * alpha_av, beta_av: artificial viscosity; alpha_u: artificial conductivity.
+ * precision: APR_PREC_FP32_MIXED (pair sums in float on relative lattice
+ * coordinates, compensated; state, integration and global sums in double) or
+ * APR_PREC_FP64.  nr_tol, nr_maxit: h-rho Newton-Raphson stopping rule.
+ * max_neigh: capacity of one particle's neighbour list (0 = default 256).
+ */
+typedef struct {
+    double box_lo[3], box_hi[3];
+    int periodic[3];
+    double delta;
+    double hfact, gamma;
+    int eos;
+    double cs0, qcs;
+    double alpha_av, beta_av, alpha_u;
+    double rsep_fac, dnn_cap;
+    double m0;
+    int lmax;
+    unsigned long long seed;
+    double ccour, cforce, G;
+    int precision;
+    double nr_tol;
+    int nr_maxit;
+    int max_neigh;
+} apr_config;
+
+/*
+ * A refinement zone (Sec. 2.1, Table 1): nested boundaries R[0] > R[1] > ...,
+ * a point strictly inside R[k] asks for level k + 1.  shape sphere:
+ * |x - centre| < R; slab: |x[axis] - centre[axis]| < R.  track_sink >= 0 makes
+ * the centre follow that sink every step (co-moving zone, Sec. 2.1).
+ */
+typedef struct {
+    int shape, axis, track_sink, nlev;
+    double centre[3];
+    double R[APR_MAXLEV];
+} apr_region;
+
+/* a point mass: position, velocity, acceleration, mass, accretion radius */
+typedef struct {
+    double x[3], v[3], a[3];
+    double m, racc;
+} apr_sink;
+
+/*
+ * Particle state: caller-owned DEVICE arrays of length >= capacity, in the
+ * caller's order.  Inputs: x..h, level, flags, id.  Outputs written by the
+ * library: rho, omega (grad-h term), ax..az, dudt, vsig (signal speed), dnn
+ * (nearest-neighbour distance on the lattice, +inf if none within 2h), pres,
+ * cs.  Mass is m0 / 2^level (Eq. 1) and is not stored.
+ */
+typedef struct {
+    double *x, *y, *z, *vx, *vy, *vz, *u, *h;
+    double *rho, *omega, *ax, *ay, *az, *dudt, *vsig, *dnn, *pres, *cs;
+    unsigned char *level, *flags;
+    unsigned long long *id;
+} apr_particles;
+
+typedef struct {
+    long long n_split[APR_MAXLEV], n_merge[APR_MAXLEV], n_spare[APR_MAXLEV];
+    long long n_accreted, n_dead;
+} apr_counts;
+
+/* float64 conservation sums over live gas particles and sinks */
+typedef struct {
+    double mass, mom[3], ang[3], ekin, etherm;
+} apr_stats;
+
+typedef struct apr_ctx apr_ctx;
+
+/* Create a context on the current CUDA device; stream may be NULL (legacy default). */
+apr_status apr_create(apr_ctx** ctx, const apr_config* cfg, void* stream);
+void apr_destroy(apr_ctx* ctx);
+const char* apr_last_error(const apr_ctx* ctx);
+
+/* Bytes of device workspace needed for `capacity` particles. */
+apr_status apr_workspace_size(const apr_config* cfg, long long capacity, size_t* bytes);
+
+/*
+ * Attach particle arrays (n live particles, room for `capacity`), the next id
+ * to hand to a split child, and a caller-owned device workspace of at least
+ * apr_workspace_size bytes (256-byte aligned).
+ */
+apr_status apr_bind(apr_ctx* ctx, const apr_particles* p, long long n, long long capacity,
+                    long long next_id, void* workspace, size_t bytes);
+
+/* Refinement zones and point masses (host arrays, copied). */
+apr_status apr_set_regions(apr_ctx* ctx, const apr_region* r, int nregions);
+apr_status apr_set_sinks(apr_ctx* ctx, const apr_sink* s, int nsinks);
+apr_status apr_get_sinks(apr_ctx* ctx, apr_sink* s, int nsinks);
+
+/* Current particle count, next id and split/merge step counter. */
+apr_status apr_get_count(apr_ctx* ctx, long long* n, long long* next_id,
+                         unsigned long long* step);
+
+/*
+ * Initial refinement (Sec. 2.6 applied until no particle changes level):
+ * repeat {density; split/merge pass} until nothing changes, then density and
+ * forces.  *passes receives the number of split/merge passes.
+ */
+apr_status apr_init(apr_ctx* ctx, int* passes);
+
+/*
+ * One split/merge pass (Sec. 2.6): clear the changed marks; split levels
+ * 0..lmax-1 ascending (Sec. 2.2, Eq. 2); merge levels lmax..1 descending
+ * through the pairing tree (Sec. 2.3, Eq. 3; an odd candidate is left over);
+ * compact.  Each particle changes level at most once.  APR_ERR_CAPACITY is
+ * detected before any particle is written.
+ */
+apr_status apr_split_merge(apr_ctx* ctx, long long* n_out, apr_counts* counts);
+
+/*
+ * Density solve: h, rho, omega, dnn, pres, cs of every live particle from
+ * the h-rho relation rho = m (hfact/h)^3 = sum_b m_b W(r_ab, h) (cited in
+ * Sec. 2.2) by Newton-Raphson from the current h.  *n_unconverged (may be
+ * NULL) receives the count still unconverged after nr_maxit iterations.
+ */
+apr_status apr_sph_density(apr_ctx* ctx, long long* n_unconverged);
+
+/* Hydrodynamic acceleration, du/dt, signal speed, plus point-mass gravity. */
+apr_status apr_sph_force(apr_ctx* ctx);
+
+/*
+ * One kick-drift-kick step of length dt (dt <= 0: the Courant/force limit
+ * from the last force pass): half kick, drift, accretion, zones follow their
+ * sinks, split/merge, density, forces, half kick.  dt_used, stats, counts may
+ * be NULL.
+ */
+apr_status apr_step(apr_ctx* ctx, double dt, double* dt_used, apr_stats* stats,
+                    apr_counts* counts);
+
+/* Time-step limit from the last force pass: min(ccour h/vsig, cforce sqrt(h/|a|)). */
+apr_status apr_timestep(apr_ctx* ctx, double* dt);
+
+/* Conservation sums of the current state. */
+apr_status apr_stats_compute(apr_ctx* ctx, apr_stats* stats);
+
+/*
+ * Debug / parity: neighbour lists on the quantised lattice at the current h,
+ * into HOST buffers in CSR form (offsets[n+1], idx[total]; particle indices
+ * in the caller's order; order within a list unspecified).  mode 0: b != a
+ * with |r_ab| < 2 h_a; mode 1: |r_ab| < 2 max(h_a, h_b).  Returns
+ * APR_ERR_NEIGH_OVERFLOW with *total set if cap is too small.
+ */
+apr_status apr_neighbour_lists(apr_ctx* ctx, int mode, long long* offsets, int* idx,
+                               long long cap, long long* total);
+
+/*
+ * Debug / parity: the pairing tree (Sec. 2.3) of the merge candidates of
+ * `level` in the current state, without merging.  pairs: HOST buffer of
+ * 2*cap particle indices; *npairs receives the pair count, *spare the index
+ * left out for an odd count (-1 if none).
+ */
+apr_status apr_merge_pairs(apr_ctx* ctx, int level, long long* pairs, long long cap,
+                           long long* npairs, long long* spare);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APR_H */

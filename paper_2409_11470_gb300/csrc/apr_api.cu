@@ -1,0 +1,547 @@
+// C ABI of the GB300 APR SPH library (declared in include/apr.h): argument
+// checks, the caller-owned workspace layout, and the host-side order of the
+// passes of one step (Sec. 2.6: zones -> split ascending -> merge descending
+// -> density -> forces, inside a kick-drift-kick update).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "apr_internal.cuh"
+
+namespace apr {
+
+apr_status fail(apr_ctx* c, apr_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+apr_status cuda_check(apr_ctx* c, cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return APR_OK;
+    return fail(c, APR_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+DevRegions dev_regions(const apr_ctx* c)
+{
+    DevRegions r;
+    memset(&r, 0, sizeof(r));
+    r.n = c->nreg;
+    for (int j = 0; j < c->nreg; ++j) {
+        const apr_region& s = c->regions[j];
+        r.r[j].shape = s.shape;
+        r.r[j].axis = s.axis;
+        r.r[j].nlev = s.nlev;
+        for (int k = 0; k < 3; ++k) r.r[j].centre[k] = s.centre[k];
+        for (int k = 0; k < APR_MAXLEV; ++k) r.r[j].R[k] = s.R[k];
+    }
+    return r;
+}
+
+DevSinks dev_sinks(const apr_ctx* c)
+{
+    DevSinks s;
+    memset(&s, 0, sizeof(s));
+    s.n = c->nsink;
+    for (int j = 0; j < c->nsink; ++j) {
+        for (int k = 0; k < 3; ++k) s.x[j][k] = c->sinks[j].x[k];
+        s.m[j] = c->sinks[j].m;
+        s.racc[j] = c->sinks[j].racc;
+    }
+    return s;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Workspace* W)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void* {
+        off = align256(off);
+        void* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    const size_t C = (size_t)(cap > 0 ? cap : 1);
+    const size_t K = (size_t)(cfg.max_neigh > 0 ? cfg.max_neigh : DEFAULT_MAX_NEIGH);
+    const size_t ntiles = (C + RADIX_TILE - 1) / RADIX_TILE;
+    const size_t scan_n = C > 256 * ntiles ? C : 256 * ntiles;
+    const bool f64 = cfg.precision == APR_PREC_FP64;
+    Workspace w;
+    memset(&w, 0, sizeof(w));
+    w.xi = (int4*)take(16 * C);
+    w.key[0] = (unsigned long long*)take(8 * C);
+    w.key[1] = (unsigned long long*)take(8 * C);
+    w.val[0] = (unsigned int*)take(4 * C);
+    w.val[1] = (unsigned int*)take(4 * C);
+    w.hist = (unsigned int*)take(4 * 256 * ntiles * 2);
+    w.scan_tmp = (unsigned int*)take(4 * (scan_n / 256 + 8192));
+    w.pk = (int4*)take(16 * C);
+    w.sthr = (unsigned long long*)take(8 * C);
+    w.sh = (double*)take(8 * C);
+    if (f64) {
+        w.sx = (double*)take(8 * C);
+        w.sy = (double*)take(8 * C);
+        w.sz = (double*)take(8 * C);
+        w.dA = (double*)take(32 * C);
+        w.dV = (double*)take(32 * C);
+        w.dB = (double*)take(32 * C);
+    } else {
+        w.fA = (float4*)take(16 * C);
+        w.fV = (float4*)take(16 * C);
+        w.fB = (float4*)take(16 * C);
+    }
+    w.left = (int*)take(4 * C);
+    w.right = (int*)take(4 * C);
+    w.parent_int = (int*)take(4 * C);
+    w.parent_leaf = (int*)take(4 * C);
+    w.visit = (int*)take(4 * C);
+    w.nlo = (int4*)take(16 * C);
+    w.nhi = (int4*)take(16 * C);
+    w.nhmax = (double*)take(8 * C);
+    w.cflag = (unsigned int*)take(4 * C);
+    w.cscan = (unsigned int*)take(4 * C);
+    w.cell_first = (int*)take(4 * C);
+    w.cell_cnt = (int*)take(4 * C);
+    w.cell_node = (int*)take(4 * C);
+    w.cmark = (int*)take(4 * C);
+    w.cand = (int2*)take(8 * (size_t)MAX_CAND * C);
+    w.ncand = (int*)take(4 * C);
+    w.nbr = (unsigned int*)take(4 * K * C);
+    w.ncnt = (int*)take(4 * C);
+    w.status = (int*)take(4 * 64);
+    w.tgt = (unsigned char*)take(C);
+    w.uflag = (unsigned int*)take(4 * C);
+    w.uscan = (unsigned int*)take(4 * C);
+    w.tmp8 = (double*)take(8 * C);
+    w.mset[0] = (unsigned int*)take(4 * C);
+    w.mset[1] = (unsigned int*)take(4 * C);
+    w.seg_lo[0] = (int*)take(4 * C);
+    w.seg_lo[1] = (int*)take(4 * C);
+    w.seg_hi[0] = (int*)take(4 * C);
+    w.seg_hi[1] = (int*)take(4 * C);
+    w.acc_lo = (int4*)take(16 * C * 2);
+    w.acc_hi = (int4*)take(16 * C * 2);
+    w.acc_sum = (unsigned long long*)take(8 * C * 2);
+    w.acc_k = (unsigned int*)take(4 * C * 2);
+    w.acc_k2 = (unsigned int*)take(4 * C * 2);
+    w.acc_key = (unsigned long long*)take(8 * C * 4);
+    w.lflag = (unsigned int*)take(4 * C);
+    w.red = (double*)take(8 * 32 * (size_t)RED_BLOCKS);
+    w.redout = (double*)take(8 * 32);
+    w.bytes = align256(off);
+    if (W) *W = w;
+    return w.bytes;
+}
+
+static apr_status check_cfg(const apr_config* cfg, DevCfg* dc, std::string* why)
+{
+    if (!cfg) {
+        *why = "null config";
+        return APR_ERR_ARG;
+    }
+    if (!(cfg->delta > 0.0) || !(cfg->hfact > 0.0) || !(cfg->m0 > 0.0)) {
+        *why = "delta, hfact and m0 must be positive";
+        return APR_ERR_ARG;
+    }
+    if (cfg->lmax < 0 || cfg->lmax >= APR_MAXLEV) {
+        *why = "lmax out of range";
+        return APR_ERR_ARG;
+    }
+    if (cfg->precision != APR_PREC_FP32_MIXED && cfg->precision != APR_PREC_FP64) {
+        *why = "unknown precision";
+        return APR_ERR_ARG;
+    }
+    memset(dc, 0, sizeof(*dc));
+    for (int k = 0; k < 3; ++k) {
+        double L = cfg->box_hi[k] - cfg->box_lo[k];
+        if (!(L > 0.0)) {
+            *why = "empty box";
+            return APR_ERR_ARG;
+        }
+        double units = L / cfg->delta;
+        if (units > (double)(1LL << COORD_BITS)) {
+            *why = "box / delta exceeds 2^30 lattice units";
+            return APR_ERR_ARG;
+        }
+        long long Li = llround(units);
+        if (cfg->periodic[k] && (double)Li != units) {
+            *why = "periodic length is not a whole number of lattice units";
+            return APR_ERR_ARG;
+        }
+        dc->lo[k] = cfg->box_lo[k];
+        dc->hi[k] = cfg->box_hi[k];
+        dc->L[k] = L;
+        dc->periodic[k] = cfg->periodic[k] ? 1 : 0;
+        dc->Lint[k] = Li;
+    }
+    dc->delta = cfg->delta;
+    dc->deltaf = (float)cfg->delta;
+    dc->hfact = cfg->hfact;
+    dc->gamma = cfg->gamma;
+    dc->eos = cfg->eos;
+    dc->cs0 = cfg->cs0;
+    dc->qcs = cfg->qcs;
+    dc->alpha_av = cfg->alpha_av;
+    dc->beta_av = cfg->beta_av;
+    dc->alpha_u = cfg->alpha_u;
+    dc->rsep_fac = cfg->rsep_fac;
+    dc->dnn_cap = cfg->dnn_cap;
+    dc->m0 = cfg->m0;
+    dc->lmax = cfg->lmax;
+    dc->seed = cfg->seed;
+    dc->ccour = cfg->ccour;
+    dc->cforce = cfg->cforce;
+    dc->G = cfg->G;
+    dc->nr_tol = cfg->nr_tol > 0.0 ? cfg->nr_tol
+                                   : (cfg->precision == APR_PREC_FP64 ? 1e-12 : 1e-6);
+    dc->nr_maxit = cfg->nr_maxit > 0 ? cfg->nr_maxit : 50;
+    dc->max_neigh = cfg->max_neigh > 0 ? cfg->max_neigh : DEFAULT_MAX_NEIGH;
+    return APR_OK;
+}
+
+// ------------------------------------------------------------ pass drivers
+
+static apr_status read_status(apr_ctx* c, int first, int count, int* out)
+{
+    cudaMemcpyAsync(c->hbuf, &c->W.status[first], sizeof(int) * count, cudaMemcpyDeviceToHost,
+                    c->stream);
+    apr_status s = cuda_check(c, cudaStreamSynchronize(c->stream), "status");
+    if (s == APR_OK) memcpy(out, c->hbuf, sizeof(int) * count);
+    return s;
+}
+
+static apr_status check_overflow(apr_ctx* c)
+{
+    int st[8];
+    apr_status s = read_status(c, 0, 8, st);
+    if (s != APR_OK) return s;
+    if (st[ST_TREE_BAD]) return fail(c, APR_ERR_STATE, "internal error: malformed radix tree");
+    if (st[0]) return fail(c, APR_ERR_NEIGH_OVERFLOW, "a neighbour list exceeded max_neigh");
+    if (st[1]) return fail(c, APR_ERR_NEIGH_OVERFLOW, "a candidate-cell list overflowed");
+    return APR_OK;
+}
+
+static apr_status run_density(apr_ctx* c, long long* noconv_out)
+{
+    apr_status s = index_sort(c);
+    if (s != APR_OK) return s;
+    long long unc = 0, noconv = 0;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        cudaMemsetAsync(c->W.status, 0, 2 * sizeof(int), c->stream);
+        s = index_lists(c, 0, DENSITY_REACH);
+        if (s != APR_OK) return s;
+        s = check_overflow(c);
+        if (s != APR_OK) return s;
+        s = density_pass(c, &unc, &noconv);
+        if (s != APR_OK) return s;
+        if (unc == 0) break;
+        s = index_refresh_h(c);
+        if (s != APR_OK) return s;
+    }
+    if (noconv_out) *noconv_out = noconv + unc;
+    if (unc) return fail(c, APR_ERR_NR_NOCONV, "smoothing lengths kept outgrowing their lists");
+    if (noconv) return fail(c, APR_ERR_NR_NOCONV, "h-rho iteration did not converge everywhere");
+    return APR_OK;
+}
+
+static apr_status run_force(apr_ctx* c)
+{
+    apr_status s = index_refresh_h(c);
+    if (s != APR_OK) return s;
+    cudaMemsetAsync(c->W.status, 0, 2 * sizeof(int), c->stream);
+    s = index_lists(c, 1, 1.0);
+    if (s != APR_OK) return s;
+    s = gather_force_data(c);
+    if (s != APR_OK) return s;
+    s = force_pass(c);
+    if (s != APR_OK) return s;
+    s = check_overflow(c);
+    if (s != APR_OK) return s;
+    s = sink_gravity(c);
+    if (s != APR_OK) return s;
+    c->have_force = true;
+    return APR_OK;
+}
+
+static void track_regions(apr_ctx* c)
+{
+    for (int j = 0; j < c->nreg; ++j) {
+        int t = c->regions[j].track_sink;
+        if (t >= 0 && t < c->nsink)
+            for (int k = 0; k < 3; ++k) c->regions[j].centre[k] = c->sinks[t].x[k];
+    }
+}
+
+}  // namespace apr
+
+using namespace apr;
+
+// ---------------------------------------------------------------- the ABI
+
+extern "C" {
+
+apr_status apr_create(apr_ctx** out, const apr_config* cfg, void* stream)
+{
+    if (!out) return APR_ERR_ARG;
+    *out = nullptr;
+    DevCfg dc;
+    std::string why;
+    apr_status s = check_cfg(cfg, &dc, &why);
+    if (s != APR_OK) return s;
+    apr_ctx* c = new (std::nothrow) apr_ctx();
+    if (!c) return APR_ERR_ARG;
+    c->cfg = *cfg;
+    c->dc = dc;
+    c->stream = (cudaStream_t)stream;
+    c->bound = false;
+    c->have_force = false;
+    c->n = c->cap = c->next_id = 0;
+    c->step = 0;
+    c->nreg = c->nsink = 0;
+    c->ncell = 0;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaMallocHost((void**)&c->hbuf, 4096) != cudaSuccess) {
+        delete c;
+        return APR_ERR_CUDA;
+    }
+    *out = c;
+    return APR_OK;
+}
+
+void apr_destroy(apr_ctx* c)
+{
+    if (!c) return;
+    if (c->hbuf) cudaFreeHost(c->hbuf);
+    delete c;
+}
+
+const char* apr_last_error(const apr_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+apr_status apr_workspace_size(const apr_config* cfg, long long capacity, size_t* bytes)
+{
+    if (!cfg || !bytes || capacity < 0) return APR_ERR_ARG;
+    *bytes = workspace_layout(*cfg, capacity, nullptr, nullptr);
+    return APR_OK;
+}
+
+apr_status apr_bind(apr_ctx* c, const apr_particles* p, long long n, long long capacity,
+                    long long next_id, void* workspace, size_t bytes)
+{
+    if (!c || !p) return APR_ERR_ARG;
+    if (n < 0 || capacity < n || capacity >= (1LL << 31))
+        return fail(c, APR_ERR_ARG, "need 0 <= n <= capacity < 2^31");
+    const void* ptrs[] = {p->x,  p->y,    p->z,  p->vx,   p->vy,   p->vz,   p->u,
+                          p->h,  p->rho,  p->omega, p->ax, p->ay,   p->az,   p->dudt,
+                          p->vsig, p->dnn, p->pres, p->cs, p->level, p->flags, p->id};
+    for (const void* q : ptrs)
+        if (!q) return fail(c, APR_ERR_ARG, "null particle array");
+    size_t need = workspace_layout(c->cfg, capacity, nullptr, nullptr);
+    if (!workspace || bytes < need) return fail(c, APR_ERR_WORKSPACE, "workspace too small");
+    if (((uintptr_t)workspace) & 255) return fail(c, APR_ERR_ARG, "workspace not 256-byte aligned");
+    c->p = *p;
+    c->n = n;
+    c->cap = capacity;
+    c->next_id = next_id;
+    c->ws = (char*)workspace;
+    c->ws_bytes = bytes;
+    workspace_layout(c->cfg, capacity, c->ws, &c->W);
+    apr_status s =
+        cuda_check(c, cudaMemsetAsync(c->W.status, 0, 4 * 64, c->stream), "bind");
+    if (s != APR_OK) return s;
+    c->bound = true;
+    c->have_force = false;
+    return APR_OK;
+}
+
+apr_status apr_set_regions(apr_ctx* c, const apr_region* r, int nregions)
+{
+    if (!c || nregions < 0 || nregions > APR_MAXREG || (nregions > 0 && !r)) return APR_ERR_ARG;
+    for (int j = 0; j < nregions; ++j) {
+        if (r[j].nlev < 0 || r[j].nlev > APR_MAXLEV || r[j].axis < 0 || r[j].axis > 2 ||
+            (r[j].shape != APR_SHAPE_SPHERE && r[j].shape != APR_SHAPE_SLAB))
+            return fail(c, APR_ERR_ARG, "bad region");
+        c->regions[j] = r[j];
+    }
+    c->nreg = nregions;
+    return APR_OK;
+}
+
+apr_status apr_set_sinks(apr_ctx* c, const apr_sink* s, int nsinks)
+{
+    if (!c || nsinks < 0 || nsinks > APR_MAXSINK || (nsinks > 0 && !s)) return APR_ERR_ARG;
+    for (int j = 0; j < nsinks; ++j) c->sinks[j] = s[j];
+    c->nsink = nsinks;
+    return APR_OK;
+}
+
+apr_status apr_get_sinks(apr_ctx* c, apr_sink* s, int nsinks)
+{
+    if (!c || nsinks < 0 || nsinks > c->nsink || (nsinks > 0 && !s)) return APR_ERR_ARG;
+    for (int j = 0; j < nsinks; ++j) s[j] = c->sinks[j];
+    return APR_OK;
+}
+
+apr_status apr_get_count(apr_ctx* c, long long* n, long long* next_id, unsigned long long* step)
+{
+    if (!c) return APR_ERR_ARG;
+    if (n) *n = c->n;
+    if (next_id) *next_id = c->next_id;
+    if (step) *step = c->step;
+    return APR_OK;
+}
+
+apr_status apr_sph_density(apr_ctx* c, long long* n_unconverged)
+{
+    if (!c) return APR_ERR_ARG;
+    if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    return run_density(c, n_unconverged);
+}
+
+apr_status apr_sph_force(apr_ctx* c)
+{
+    if (!c) return APR_ERR_ARG;
+    if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    return run_force(c);
+}
+
+apr_status apr_split_merge(apr_ctx* c, long long* n_out, apr_counts* counts)
+{
+    if (!c) return APR_ERR_ARG;
+    if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    apr_counts cnt;
+    track_regions(c);
+    apr_status s = split_merge_pass(c, &cnt);
+    if (n_out) *n_out = c->n;
+    if (counts) *counts = cnt;
+    return s;
+}
+
+apr_status apr_init(apr_ctx* c, int* passes)
+{
+    if (!c) return APR_ERR_ARG;
+    if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    track_regions(c);
+    int np = 0;
+    apr_status s;
+    for (;;) {
+        s = run_density(c, nullptr);
+        if (s != APR_OK && s != APR_ERR_NR_NOCONV) return s;
+        apr_counts cnt;
+        s = split_merge_pass(c, &cnt);
+        if (s != APR_OK) return s;
+        ++np;
+        long long changed = 0;
+        for (int l = 0; l < APR_MAXLEV; ++l) changed += cnt.n_split[l] + cnt.n_merge[l];
+        if (changed == 0 || np > 4 * APR_MAXLEV) break;
+    }
+    s = clear_changed(c);
+    if (s != APR_OK) return s;
+    s = run_density(c, nullptr);
+    if (s != APR_OK) return s;
+    s = run_force(c);
+    if (passes) *passes = np;
+    return s;
+}
+
+apr_status apr_timestep(apr_ctx* c, double* dt)
+{
+    if (!c || !dt) return APR_ERR_ARG;
+    if (!c->bound || !c->have_force) return fail(c, APR_ERR_STATE, "no force pass yet");
+    return compute_timestep(c, dt);
+}
+
+apr_status apr_stats_compute(apr_ctx* c, apr_stats* st)
+{
+    if (!c || !st) return APR_ERR_ARG;
+    if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    return compute_stats(c, st);
+}
+
+apr_status apr_step(apr_ctx* c, double dt, double* dt_used, apr_stats* stats,
+                    apr_counts* counts)
+{
+    if (!c) return APR_ERR_ARG;
+    if (!c->bound || !c->have_force) return fail(c, APR_ERR_STATE, "apr_init or a force pass first");
+    apr_status s;
+    if (!(dt > 0.0)) {
+        s = compute_timestep(c, &dt);
+        if (s != APR_OK) return s;
+    }
+    const double hdt = 0.5 * dt;
+    s = kick(c, hdt);
+    if (s != APR_OK) return s;
+    s = drift(c, dt);
+    if (s != APR_OK) return s;
+    long long na = 0;
+    s = accrete(c, &na);
+    if (s != APR_OK) return s;
+    track_regions(c);
+    apr_counts cnt;
+    s = split_merge_pass(c, &cnt);
+    if (s != APR_OK) return s;
+    cnt.n_accreted = na;
+    s = run_density(c, nullptr);
+    if (s != APR_OK) return s;
+    s = run_force(c);
+    if (s != APR_OK) return s;
+    s = kick(c, hdt);
+    if (s != APR_OK) return s;
+    if (dt_used) *dt_used = dt;
+    if (counts) *counts = cnt;
+    if (stats) {
+        s = compute_stats(c, stats);
+        if (s != APR_OK) return s;
+    }
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "step");
+}
+
+apr_status apr_neighbour_lists(apr_ctx* c, int mode, long long* offsets, int* idx, long long cap,
+                               long long* total)
+{
+    if (!c || !offsets || (mode != 0 && mode != 1)) return APR_ERR_ARG;
+    if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    const long long n = c->n;
+    apr_status s = index_sort(c);
+    if (s != APR_OK) return s;
+    cudaMemsetAsync(c->W.status, 0, 2 * sizeof(int), c->stream);
+    s = index_lists(c, mode, 1.0);
+    if (s != APR_OK) return s;
+    s = check_overflow(c);
+    if (s != APR_OK) return s;
+    const int K = c->dc.max_neigh;
+    std::vector<unsigned> perm(n), nb((size_t)K * n);
+    std::vector<int> cnt(n);
+    if (n > 0) {
+        cudaMemcpyAsync(perm.data(), c->W.perm, 4 * n, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(cnt.data(), c->W.ncnt, 4 * n, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpy2DAsync(nb.data(), 4 * n, c->W.nbr, 4 * c->cap, 4 * n, K, cudaMemcpyDeviceToHost,
+                          c->stream);
+    }
+    s = cuda_check(c, cudaStreamSynchronize(c->stream), "neighbour lists");
+    if (s != APR_OK) return s;
+    std::vector<long long> cnt_can(n, 0);
+    for (long long sl = 0; sl < n; ++sl) cnt_can[perm[sl]] = cnt[sl];
+    offsets[0] = 0;
+    for (long long a = 0; a < n; ++a) offsets[a + 1] = offsets[a] + cnt_can[a];
+    const long long tot = n > 0 ? offsets[n] : 0;
+    if (total) *total = tot;
+    if (tot > cap || (tot > 0 && !idx)) return fail(c, APR_ERR_NEIGH_OVERFLOW, "idx too small");
+    for (long long sl = 0; sl < n; ++sl) {
+        long long a = perm[sl], o = offsets[a];
+        for (int k = 0; k < cnt[sl]; ++k) idx[o + k] = (int)perm[nb[(size_t)k * n + sl]];
+    }
+    return APR_OK;
+}
+
+apr_status apr_merge_pairs(apr_ctx* c, int level, long long* pairs, long long cap,
+                           long long* npairs, long long* spare)
+{
+    if (!c || !pairs || !npairs || !spare || level < 1) return APR_ERR_ARG;
+    if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    return merge_pairs_debug(c, level, pairs, cap, npairs, spare);
+}
+
+}  // extern "C"

@@ -1,0 +1,615 @@
+// Neighbour index of the APR SPH hot path on sm_103a.
+//
+// The paper finds neighbours with Phantom's k-d tree (cited in Sec. 2.2 and
+// Sec. 2.3); on the GPU the index is rebuilt every density pass instead:
+//   1. positions -> integer lattice coordinates -> 63-bit Morton keys;
+//   2. stable LSD radix sort of (key, index), 8 passes of 8 bits;
+//   3. a binary radix tree over the sorted keys (Karras 2012 construction);
+//   4. bottom-up node boxes, particle counts and max h;
+//   5. cells = the largest subtrees with <= 32 particles (one warp each);
+//   6. per cell, the candidate cells whose box is within kernel reach;
+//   7. per particle, the exact neighbour list on the integer lattice,
+//      one warp per cell with candidates broadcast lane to lane.
+// Every membership decision is an exact integer comparison, so the lists are
+// bit-identical to a brute-force search on the same lattice.
+#include <cstdio>
+
+#include "apr_internal.cuh"
+
+namespace apr {
+
+// ------------------------------------------------------------------- scan
+
+__global__ void k_scan_block(const unsigned int* __restrict__ in, unsigned int* __restrict__ out,
+                             unsigned int* __restrict__ bsum, long long n)
+{
+    __shared__ unsigned int wsum[8];
+    const long long base = (long long)blockIdx.x * SCAN_BLOCK + 4 * threadIdx.x;
+    unsigned int v[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0u;
+        s += v[k];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned int w = lane < 8 ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            unsigned int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        if (lane < 8) wsum[lane] = w;
+    }
+    __syncthreads();
+    unsigned int run = incl - s + (wid > 0 ? wsum[wid - 1] : 0u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 255 && bsum) bsum[blockIdx.x] = wsum[7];
+}
+
+__global__ void k_scan_add(unsigned int* __restrict__ out, const unsigned int* __restrict__ boff,
+                           long long n)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += boff[i / SCAN_BLOCK];
+}
+
+__global__ void k_scan_total(const unsigned int* in, const unsigned int* out, long long n,
+                             unsigned int* total)
+{
+    *total = n > 0 ? out[n - 1] + in[n - 1] : 0u;
+}
+
+static void scan_rec(cudaStream_t st, const unsigned int* in, unsigned int* out, long long n,
+                     unsigned int* tmp)
+{
+    const long long nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    if (nb <= 1) {
+        k_scan_block<<<1, 256, 0, st>>>(in, out, nullptr, n);
+        return;
+    }
+    unsigned int* sums = tmp;
+    unsigned int* offs = tmp + nb;
+    k_scan_block<<<(unsigned)nb, 256, 0, st>>>(in, out, sums, n);
+    scan_rec(st, sums, offs, nb, tmp + 2 * nb);
+    k_scan_add<<<nblocks(n, 256), 256, 0, st>>>(out, offs, n);
+}
+
+apr_status scan_u32(apr_ctx* c, const unsigned int* in, unsigned int* out, long long n,
+                    unsigned int* total_dev)
+{
+    if (n > 0) scan_rec(c->stream, in, out, n, c->W.scan_tmp);
+    if (total_dev) k_scan_total<<<1, 1, 0, c->stream>>>(in, out, n, total_dev);
+    return cuda_check(c, cudaGetLastError(), "scan");
+}
+
+// --------------------------------------------------- lattice and Morton keys
+
+__device__ __forceinline__ long long quant1(const DevCfg& dc, int k, double x)
+{
+    long long q = (long long)floor((x - dc.lo[k]) / dc.delta);
+    if (dc.periodic[k]) {
+        long long L = dc.Lint[k];
+        q %= L;
+        if (q < 0) q += L;
+    } else {
+        if (q < 0) q = 0;
+        if (q > COORD_MAX) q = COORD_MAX;
+    }
+    return q;
+}
+
+// spread the low 21 bits of v so that bit k lands on bit 3k
+__device__ __forceinline__ unsigned long long spread21(unsigned int v)
+{
+    unsigned long long x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x001f00000000ffffULL;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffULL;
+    x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
+    x = (x | (x << 2)) & 0x1249249249249249ULL;
+    return x;
+}
+
+__global__ void k_quantise(DevCfg dc, const double* __restrict__ x, const double* __restrict__ y,
+                           const double* __restrict__ z, const unsigned char* __restrict__ level,
+                           long long n, int4* __restrict__ xi, unsigned long long* __restrict__ key,
+                           unsigned int* __restrict__ val)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    long long qx = quant1(dc, 0, x[i]), qy = quant1(dc, 1, y[i]), qz = quant1(dc, 2, z[i]);
+    xi[i] = make_int4((int)qx, (int)qy, (int)qz, (int)level[i]);
+    if (key) {
+        const int sh = COORD_BITS - 21;
+        key[i] = (spread21((unsigned)(qx >> sh)) << 2) | (spread21((unsigned)(qy >> sh)) << 1) |
+                 spread21((unsigned)(qz >> sh));
+        val[i] = (unsigned)i;
+    }
+}
+
+apr_status quantise(apr_ctx* c)
+{
+    k_quantise<<<nblocks(c->n, 256), 256, 0, c->stream>>>(c->dc, c->p.x, c->p.y, c->p.z,
+                                                          c->p.level, c->n, c->W.xi, nullptr,
+                                                          nullptr);
+    return cuda_check(c, cudaGetLastError(), "quantise");
+}
+
+// ------------------------------------------------------------- radix sort
+
+__global__ void k_radix_hist(const unsigned long long* __restrict__ keys, long long n, int shift,
+                             unsigned int* __restrict__ hist, int ntiles)
+{
+    __shared__ unsigned int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * RADIX_TILE;
+#pragma unroll
+    for (int r = 0; r < RADIX_TILE / 256; ++r) {
+        long long i = base + r * 256 + threadIdx.x;
+        if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(long long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// stable scatter: rank of an item = items of the same digit before it in the tile
+__global__ void k_radix_scatter(const unsigned long long* __restrict__ kin,
+                                const unsigned int* __restrict__ vin,
+                                unsigned long long* __restrict__ kout, unsigned int* __restrict__ vout,
+                                long long n, int shift, const unsigned int* __restrict__ hoff,
+                                int ntiles)
+{
+    __shared__ unsigned int run[256];
+    __shared__ unsigned int wcnt[8][256];
+    __shared__ unsigned int goff[256];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    run[t] = 0;
+    goff[t] = hoff[(long long)t * ntiles + blockIdx.x];
+    for (int w = 0; w < 8; ++w) wcnt[w][t] = 0;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    const long long base = (long long)blockIdx.x * RADIX_TILE;
+    for (int r = 0; r < RADIX_TILE / 256; ++r) {
+        long long i = base + r * 256 + t;
+        bool valid = i < n;
+        unsigned long long k = valid ? kin[i] : 0ULL;
+        unsigned int v = valid ? vin[i] : 0u;
+        unsigned d = valid ? (unsigned)(k >> shift) & 255u : 256u + lane;  // invalid: unique
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned rank = __popc(peers & lt);
+        if (valid && (peers & lt) == 0) wcnt[wid][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            unsigned pos = goff[d] + run[d] + rank;
+            for (int w = 0; w < wid; ++w) pos += wcnt[w][d];
+            kout[pos] = k;
+            vout[pos] = v;
+        }
+        __syncthreads();
+        unsigned tot = 0;
+        for (int w = 0; w < 8; ++w) {
+            tot += wcnt[w][t];
+            wcnt[w][t] = 0;
+        }
+        run[t] += tot;
+        __syncthreads();
+    }
+}
+
+static apr_status radix_sort(apr_ctx* c, long long n)
+{
+    Workspace& W = c->W;
+    const int ntiles = nblocks(n, RADIX_TILE);
+    int cur = 0;
+    for (int shift = 0; shift < 64; shift += 8) {
+        k_radix_hist<<<ntiles, 256, 0, c->stream>>>(W.key[cur], n, shift, W.hist, ntiles);
+        scan_u32(c, W.hist, W.hist + (size_t)256 * ntiles, (long long)256 * ntiles, nullptr);
+        k_radix_scatter<<<ntiles, 256, 0, c->stream>>>(W.key[cur], W.val[cur], W.key[cur ^ 1],
+                                                       W.val[cur ^ 1], n, shift,
+                                                       W.hist + (size_t)256 * ntiles, ntiles);
+        cur ^= 1;
+    }
+    W.skey = W.key[cur];
+    W.perm = W.val[cur];
+    return cuda_check(c, cudaGetLastError(), "radix sort");
+}
+
+// ------------------------------------------------------- gather sorted data
+
+__global__ void k_gather_index(long long n, const unsigned int* __restrict__ perm,
+                               const int4* __restrict__ xi, const double* __restrict__ h,
+                               const double* __restrict__ x, const double* __restrict__ y,
+                               const double* __restrict__ z, int4* __restrict__ pk,
+                               double* __restrict__ sh, double* __restrict__ sx,
+                               double* __restrict__ sy, double* __restrict__ sz)
+{
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    unsigned i = perm[s];
+    pk[s] = xi[i];
+    sh[s] = h[i];
+    if (sx) {
+        sx[s] = x[i];
+        sy[s] = y[i];
+        sz[s] = z[i];
+    }
+}
+
+__global__ void k_gather_h(long long n, const unsigned int* __restrict__ perm,
+                           const double* __restrict__ h, double* __restrict__ sh)
+{
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) sh[s] = h[perm[s]];
+}
+
+// ------------------------------------------------------------ radix tree
+
+__device__ __forceinline__ int prefix_len(const unsigned long long* __restrict__ k, int n, int i,
+                                          int j)
+{
+    if (j < 0 || j >= n) return -1;
+    unsigned long long a = k[i], b = k[j];
+    if (a == b) return 64 + __clz((unsigned)i ^ (unsigned)j);
+    return __clzll(a ^ b);
+}
+
+__global__ void k_tree_internal(const unsigned long long* __restrict__ k, int n,
+                                int* __restrict__ left, int* __restrict__ right,
+                                int* __restrict__ parent_int, int* __restrict__ parent_leaf)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (prefix_len(k, n, i, i + 1) - prefix_len(k, n, i, i - 1)) > 0 ? 1 : -1;
+    int dmin = prefix_len(k, n, i, i - d);
+    int lmax = 2;
+    while (prefix_len(k, n, i, i + lmax * d) > dmin) lmax *= 2;
+    int l = 0;
+    for (int t = lmax / 2; t >= 1; t /= 2)
+        if (prefix_len(k, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = prefix_len(k, n, i, j);
+    int s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (prefix_len(k, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int g = i + s * d + (d < 0 ? -1 : 0);
+    int lo = min(i, j), hi = max(i, j);
+    int L = (lo == g) ? ~g : g;
+    int R = (hi == g + 1) ? ~(g + 1) : g + 1;
+    left[i] = L;
+    right[i] = R;
+    if (L >= 0) parent_int[L] = i;
+    else parent_leaf[~L] = i;
+    if (R >= 0) parent_int[R] = i;
+    else parent_leaf[~R] = i;
+}
+
+struct NodeData {
+    int lo[3], hi[3], count, first;
+    double hmax;
+};
+
+__device__ __forceinline__ NodeData node_data(int c, const int4* pk, const double* sh,
+                                              const int4* nlo, const int4* nhi, const double* nhmax)
+{
+    NodeData r;
+    if (c < 0) {
+        int s = ~c;
+        int4 p = pk[s];
+        r.lo[0] = r.hi[0] = p.x;
+        r.lo[1] = r.hi[1] = p.y;
+        r.lo[2] = r.hi[2] = p.z;
+        r.count = 1;
+        r.first = s;
+        r.hmax = sh[s];
+    } else {
+        int4 a = __ldcg(&nlo[c]), b = __ldcg(&nhi[c]);
+        r.lo[0] = a.x;
+        r.lo[1] = a.y;
+        r.lo[2] = a.z;
+        r.count = a.w;
+        r.hi[0] = b.x;
+        r.hi[1] = b.y;
+        r.hi[2] = b.z;
+        r.first = b.w;
+        r.hmax = __ldcg(&nhmax[c]);
+    }
+    return r;
+}
+
+// bottom-up: the second child to arrive at a node merges both children
+__global__ void k_tree_up(int n, const int4* __restrict__ pk, const double* __restrict__ sh,
+                          const int* __restrict__ left, const int* __restrict__ right,
+                          const int* __restrict__ parent_int, const int* __restrict__ parent_leaf,
+                          int* __restrict__ visit, int4* nlo, int4* nhi, double* nhmax,
+                          int* status)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n || n < 2) return;
+    int node = parent_leaf[s];
+    for (int depth = 0;; ++depth) {
+        if (depth > 4 * 64 || node < 0 || node >= n - 1) {  // a valid tree is < 96 deep
+            atomicOr(&status[ST_TREE_BAD], 1);
+            return;
+        }
+        __threadfence();
+        if (atomicAdd(&visit[node], 1) == 0) return;
+        __threadfence();
+        NodeData a = node_data(left[node], pk, sh, nlo, nhi, nhmax);
+        NodeData b = node_data(right[node], pk, sh, nlo, nhi, nhmax);
+        int4 lo = make_int4(min(a.lo[0], b.lo[0]), min(a.lo[1], b.lo[1]), min(a.lo[2], b.lo[2]),
+                            a.count + b.count);
+        int4 hi = make_int4(max(a.hi[0], b.hi[0]), max(a.hi[1], b.hi[1]), max(a.hi[2], b.hi[2]),
+                            min(a.first, b.first));
+        __stcg(&nlo[node], lo);
+        __stcg(&nhi[node], hi);
+        __stcg(&nhmax[node], fmax(a.hmax, b.hmax));
+        if (node == 0) return;
+        node = parent_int[node];
+    }
+}
+
+static apr_status tree_up(apr_ctx* c)
+{
+    Workspace& W = c->W;
+    int n = (int)c->n;
+    if (n < 2) return APR_OK;
+    cudaMemsetAsync(W.visit, 0, sizeof(int) * (size_t)(n - 1), c->stream);
+    k_tree_up<<<nblocks(n, 256), 256, 0, c->stream>>>(n, W.pk, W.sh, W.left, W.right,
+                                                      W.parent_int, W.parent_leaf, W.visit, W.nlo,
+                                                      W.nhi, W.nhmax, W.status);
+    return cuda_check(c, cudaGetLastError(), "tree up");
+}
+
+apr_status index_sort(apr_ctx* c)
+{
+    Workspace& W = c->W;
+    long long n = c->n;
+    if (n <= 0) return APR_OK;
+    k_quantise<<<nblocks(n, 256), 256, 0, c->stream>>>(c->dc, c->p.x, c->p.y, c->p.z, c->p.level,
+                                                       n, W.xi, W.key[0], W.val[0]);
+    apr_status s = radix_sort(c, n);
+    if (s != APR_OK) return s;
+    const bool f64 = c->cfg.precision == APR_PREC_FP64;
+    k_gather_index<<<nblocks(n, 256), 256, 0, c->stream>>>(n, W.perm, W.xi, c->p.h, c->p.x, c->p.y,
+                                                           c->p.z, W.pk, W.sh, f64 ? W.sx : nullptr,
+                                                           W.sy, W.sz);
+    if (n >= 2)
+        k_tree_internal<<<nblocks(n - 1, 256), 256, 0, c->stream>>>(W.skey, (int)n, W.left, W.right,
+                                                                     W.parent_int, W.parent_leaf);
+    s = cuda_check(c, cudaGetLastError(), "index sort");
+    if (s != APR_OK) return s;
+    return tree_up(c);
+}
+
+apr_status index_refresh_h(apr_ctx* c)
+{
+    if (c->n <= 0) return APR_OK;
+    k_gather_h<<<nblocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->W.perm, c->p.h, c->W.sh);
+    apr_status s = cuda_check(c, cudaGetLastError(), "refresh h");
+    if (s != APR_OK) return s;
+    return tree_up(c);
+}
+
+// ------------------------------------------------------------------ cells
+
+__device__ __forceinline__ int node_count(int c, const int4* nlo) { return c < 0 ? 1 : nlo[c].w; }
+__device__ __forceinline__ int node_first(int c, const int4* nhi) { return c < 0 ? ~c : nhi[c].w; }
+
+__global__ void k_cells_mark(int n, const int* __restrict__ left, const int* __restrict__ right,
+                             const int4* __restrict__ nlo, const int4* __restrict__ nhi,
+                             unsigned int* __restrict__ cflag, int* __restrict__ cmark)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    if (nlo[i].w <= CELL_MAX) return;
+    int ch[2] = {left[i], right[i]};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        int cc = ch[k];
+        if (node_count(cc, nlo) <= CELL_MAX) {
+            int f = node_first(cc, nhi);
+            if (f >= 0 && f < n) {
+                cflag[f] = 1u;
+                cmark[f] = cc;
+            }
+        }
+    }
+}
+
+__global__ void k_cells_root(int n, unsigned int* cflag, int* cmark)
+{
+    cflag[0] = 1u;
+    cmark[0] = n >= 2 ? 0 : ~0;
+}
+
+__global__ void k_cells_compact(int n, const unsigned int* __restrict__ cflag,
+                                const unsigned int* __restrict__ cscan,
+                                const int* __restrict__ cmark, const int4* __restrict__ nlo,
+                                int* __restrict__ cell_first, int* __restrict__ cell_cnt,
+                                int* __restrict__ cell_node)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n || !cflag[s]) return;
+    int id = (int)cscan[s];
+    int node = cmark[s];
+    cell_first[id] = s;
+    cell_cnt[id] = node_count(node, nlo);
+    cell_node[id] = node;
+}
+
+// squared lattice distance between two boxes (minimum image on periodic axes)
+__device__ __forceinline__ unsigned long long box_dist2(const DevCfg& dc, const int* alo,
+                                                        const int* ahi, const int* blo,
+                                                        const int* bhi)
+{
+    unsigned long long d2 = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        long long g = max(0LL, max((long long)blo[k] - ahi[k], (long long)alo[k] - bhi[k]));
+        if (dc.periodic[k]) {
+            long long L = dc.Lint[k];
+            long long g1 = max(0LL, max((long long)blo[k] + L - ahi[k], (long long)alo[k] - bhi[k] - L));
+            long long g2 = max(0LL, max((long long)blo[k] - L - ahi[k], (long long)alo[k] - bhi[k] + L));
+            g = min(g, min(g1, g2));
+        }
+        d2 += (unsigned long long)(g * g);
+    }
+    return d2;
+}
+
+// candidate cells: traverse the tree from the root, keep cells within reach
+__global__ void k_candidates(DevCfg dc, int mode, double reach, int ncell, int n,
+                             const int* __restrict__ cell_node, const int* __restrict__ left,
+                             const int* __restrict__ right, const int4* __restrict__ pk,
+                             const double* __restrict__ sh, const int4* __restrict__ nlo,
+                             const int4* __restrict__ nhi, const double* __restrict__ nhmax,
+                             int2* __restrict__ cand, int* __restrict__ ncand, int* status)
+{
+    int cid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cid >= ncell) return;
+    NodeData me = node_data(cell_node[cid], pk, sh, nlo, nhi, nhmax);
+    const unsigned long long thr_self = neighbour_threshold(reach * me.hmax, dc.delta);
+    int stack[128];
+    int sp = 0;
+    stack[sp++] = n >= 2 ? 0 : ~0;
+    int k = 0;
+    bool overflow = false;
+    while (sp > 0) {
+        int node = stack[--sp];
+        NodeData o = node_data(node, pk, sh, nlo, nhi, nhmax);
+        unsigned long long thr =
+            mode == 0 ? thr_self : neighbour_threshold(reach * fmax(me.hmax, o.hmax), dc.delta);
+        if (box_dist2(dc, me.lo, me.hi, o.lo, o.hi) >= thr) continue;
+        if (o.count <= CELL_MAX) {
+            if (k < MAX_CAND) cand[(long long)cid * MAX_CAND + k] = make_int2(o.first, o.count);
+            else overflow = true;
+            ++k;
+        } else if (sp + 2 <= 128) {
+            stack[sp++] = right[node];
+            stack[sp++] = left[node];
+        } else {
+            overflow = true;
+        }
+    }
+    ncand[cid] = min(k, MAX_CAND);
+    if (overflow) atomicOr(&status[ST_CAND_OVERFLOW], 1);
+}
+
+__global__ void k_thresholds(DevCfg dc, long long n, double reach, const double* __restrict__ sh,
+                             unsigned long long* __restrict__ thr)
+{
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) thr[s] = neighbour_threshold(reach * sh[s], dc.delta);
+}
+
+// exact lists: warp per cell; candidate particles broadcast lane to lane
+__global__ void __launch_bounds__(128) k_lists(DevCfg dc, int mode, int ncell, int n, long long cap,
+                                               const int* __restrict__ cell_first,
+                                               const int* __restrict__ cell_cnt,
+                                               const int2* __restrict__ cand,
+                                               const int* __restrict__ ncand,
+                                               const int4* __restrict__ pk,
+                                               const unsigned long long* __restrict__ thr,
+                                               unsigned int* __restrict__ nbr, int* __restrict__ ncnt,
+                                               int* status)
+{
+    const int lane = threadIdx.x & 31;
+    const int cid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (cid >= ncell) return;
+    const int first = cell_first[cid], cnt = cell_cnt[cid];
+    if (first < 0 || cnt < 1 || cnt > CELL_MAX || first + cnt > n) return;
+    const bool own = lane < cnt;
+    const int a = first + (own ? lane : 0);
+    const int4 pa = pk[a];
+    const unsigned long long ta = thr[a];
+    const int Lx = (int)dc.Lint[0], Ly = (int)dc.Lint[1], Lz = (int)dc.Lint[2];
+    const int px = dc.periodic[0], py = dc.periodic[1], pz = dc.periodic[2];
+    const int K = dc.max_neigh;
+    int m = 0;
+    const int nc = ncand[cid];
+    for (int j = 0; j < nc; ++j) {
+        int2 cb = cand[(long long)cid * MAX_CAND + j];
+        if (cb.x < 0 || cb.y < 0 || cb.y > CELL_MAX || cb.x + cb.y > n) continue;
+        int4 pb = make_int4(0, 0, 0, 0);
+        unsigned long long tb = 0;
+        if (lane < cb.y) {
+            pb = pk[cb.x + lane];
+            tb = thr[cb.x + lane];
+        }
+        for (int l = 0; l < cb.y; ++l) {
+            int bx = __shfl_sync(0xffffffffu, pb.x, l);
+            int by = __shfl_sync(0xffffffffu, pb.y, l);
+            int bz = __shfl_sync(0xffffffffu, pb.z, l);
+            unsigned long long t = __shfl_sync(0xffffffffu, tb, l);
+            int b = cb.x + l;
+            if (!own || b == a) continue;
+            int dx = min_image32(pa.x - bx, px, Lx);
+            int dy = min_image32(pa.y - by, py, Ly);
+            int dz = min_image32(pa.z - bz, pz, Lz);
+            unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
+                                    (unsigned long long)((long long)dy * dy) +
+                                    (unsigned long long)((long long)dz * dz);
+            unsigned long long th = (mode == 1 && t > ta) ? t : ta;
+            if (r2 < th) {
+                if (m < K) nbr[(long long)m * cap + a] = (unsigned)b;
+                ++m;
+            }
+        }
+    }
+    if (own) {
+        ncnt[a] = min(m, K);
+        if (m > K) atomicOr(&status[ST_NEIGH_OVERFLOW], 1);
+    }
+}
+
+apr_status index_lists(apr_ctx* c, int mode, double reach)
+{
+    Workspace& W = c->W;
+    int n = (int)c->n;
+    if (n <= 0) {
+        c->ncell = 0;
+        return APR_OK;
+    }
+    cudaStream_t st = c->stream;
+    cudaMemsetAsync(W.cflag, 0, sizeof(unsigned) * (size_t)n, st);
+    if (n <= CELL_MAX)
+        k_cells_root<<<1, 1, 0, st>>>(n, W.cflag, W.cmark);
+    else
+        k_cells_mark<<<nblocks(n - 1, 256), 256, 0, st>>>(n, W.left, W.right, W.nlo, W.nhi, W.cflag,
+                                                           W.cmark);
+    scan_u32(c, W.cflag, W.cscan, n, (unsigned*)&W.status[ST_COUNT_A]);
+    k_cells_compact<<<nblocks(n, 256), 256, 0, st>>>(n, W.cflag, W.cscan, W.cmark, W.nlo,
+                                                     W.cell_first, W.cell_cnt, W.cell_node);
+    cudaMemcpyAsync(c->hbuf, &W.status[ST_COUNT_A], sizeof(int), cudaMemcpyDeviceToHost, st);
+    apr_status s = cuda_check(c, cudaStreamSynchronize(st), "cells");
+    if (s != APR_OK) return s;
+    int ncell = ((int*)c->hbuf)[0];
+    c->ncell = ncell;
+    k_candidates<<<nblocks(ncell, 128), 128, 0, st>>>(c->dc, mode, mode == 0 ? reach : 1.0, ncell, n,
+                                                       W.cell_node, W.left, W.right, W.pk, W.sh,
+                                                       W.nlo, W.nhi, W.nhmax, W.cand,
+                                                       W.ncand, W.status);
+    k_thresholds<<<nblocks(n, 256), 256, 0, st>>>(c->dc, n, mode == 0 ? reach : 1.0, W.sh, W.sthr);
+    k_lists<<<nblocks((long long)ncell * 32, 128), 128, 0, st>>>(
+        c->dc, mode, ncell, n, c->cap, W.cell_first, W.cell_cnt, W.cand, W.ncand, W.pk, W.sthr,
+        W.nbr, W.ncnt, W.status);
+    return cuda_check(c, cudaGetLastError(), "lists");
+}
+
+}  // namespace apr

@@ -1,0 +1,243 @@
+// Internal declarations of the GB300 APR SPH library: device configuration,
+// the opaque context, the workspace layout and small device helpers shared by
+// the translation units.  Nothing here is part of the C ABI (include/apr.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "apr.h"
+
+namespace apr {
+
+constexpr int COORD_BITS = 30;               // lattice coordinates are in [0, 2^30)
+constexpr long long COORD_MAX = (1LL << COORD_BITS) - 1;
+constexpr int CELL_MAX = 32;                 // particles per cell (one warp)
+constexpr int MAX_CAND = 128;                // candidate cells per cell
+constexpr int RADIX_TILE = 2048;             // items per radix-sort block (256 x 8)
+constexpr int SCAN_BLOCK = 1024;             // items per scan block (256 x 4)
+constexpr int RED_BLOCKS = 1216;             // 8 x 152 SMs: fixed-shape f64 reductions
+constexpr int DEFAULT_MAX_NEIGH = 256;
+constexpr float DENSITY_REACH = 1.125f;      // density lists cover r < 2 * 1.125 * h
+
+// status words written by kernels (device, read back by the host)
+enum {
+    ST_NEIGH_OVERFLOW = 0,   // a particle's list exceeded max_neigh
+    ST_CAND_OVERFLOW = 1,    // a cell's candidate list exceeded MAX_CAND
+    ST_UNCOVERED = 2,        // density: h grew beyond the list's reach
+    ST_NOCONV = 3,           // density: Newton-Raphson not converged
+    ST_COUNT_A = 4,          // generic counters for split/merge passes
+    ST_COUNT_B = 5,
+    ST_MAXSEG = 6,           // merge tree: largest open segment
+    ST_TREE_BAD = 7,         // radix tree walk left its bounds (must never happen)
+    ST_NSTATUS = 16
+};
+
+// configuration as the kernels see it (passed by value)
+struct DevCfg {
+    double lo[3], hi[3], L[3];
+    int periodic[3];
+    long long Lint[3];
+    double delta;
+    float deltaf;
+    double hfact, gamma;
+    int eos;
+    double cs0, qcs;
+    double alpha_av, beta_av, alpha_u;
+    double rsep_fac, dnn_cap;
+    double m0;
+    int lmax;
+    unsigned long long seed;
+    double ccour, cforce, G;
+    double nr_tol;
+    int nr_maxit;
+    int max_neigh;
+};
+
+struct DevRegion {
+    int shape, axis, nlev, pad;
+    double centre[3];
+    double R[APR_MAXLEV];
+};
+
+struct DevRegions {
+    int n;
+    DevRegion r[APR_MAXREG];
+};
+
+struct DevSinks {
+    int n;
+    double x[APR_MAXSINK][3];
+    double m[APR_MAXSINK];
+    double racc[APR_MAXSINK];
+};
+
+// pointers into the caller's workspace
+struct Workspace {
+    // index build
+    int4* xi;                 // canonical-order lattice coordinates + level
+    unsigned long long* key[2];
+    unsigned int* val[2];
+    unsigned int* hist;
+    unsigned int* scan_tmp;
+    unsigned int* perm;       // sorted slot -> canonical index
+    unsigned long long* skey; // sorted keys (aliases key[0] or key[1])
+    int4* pk;                 // sorted lattice coordinates + level
+    unsigned long long* sthr; // sorted neighbour thresholds of the current list
+    double* sh;               // sorted h (float64)
+    float4* fA;               // FP32 force data: hinv, P/(Omega rho^2), cs, rho
+    float4* fV;               // FP32 velocities + u
+    float4* fB;               // FP32 P, 1/(Omega rho), h, level-mass factor
+    double* sx;               // FP64 sorted positions
+    double* sy;
+    double* sz;
+    double* dA;               // FP64 force data (4 per particle)
+    double* dV;
+    double* dB;
+    // radix tree over sorted keys
+    int* left;
+    int* right;
+    int* parent_int;
+    int* parent_leaf;
+    int* visit;
+    int4* nlo;                // node bbox min (x,y,z) + count
+    int4* nhi;                // node bbox max (x,y,z) + first sorted slot
+    double* nhmax;            // node max h
+    // cells
+    unsigned int* cflag;
+    unsigned int* cscan;
+    int* cell_first;
+    int* cell_cnt;
+    int* cell_node;
+    int* cmark;               // node of the cell starting at a sorted slot
+    int2* cand;               // MAX_CAND (first slot, count) per cell
+    int* ncand;
+    // neighbour lists, transposed: nbr[k * cap + sorted slot]
+    unsigned int* nbr;
+    int* ncnt;
+    // status words
+    int* status;
+    // split / merge / compaction scratch
+    unsigned char* tgt;
+    unsigned int* uflag;
+    unsigned int* uscan;
+    double* tmp8;             // one field's worth of compaction scratch
+    unsigned int* mset[2];    // merge tree: particle order within segments
+    int* seg_lo[2];
+    int* seg_hi[2];
+    int4* acc_lo;             // per segment (indexed by its first position)
+    int4* acc_hi;
+    unsigned long long* acc_sum;
+    unsigned int* acc_k;
+    unsigned int* acc_k2;
+    unsigned long long* acc_key;
+    unsigned int* lflag;
+    // reductions
+    double* red;              // RED_BLOCKS x 32 partial sums
+    double* redout;           // 32 final sums
+    size_t bytes;
+};
+
+size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Workspace* W);
+
+}  // namespace apr
+
+struct apr_ctx {
+    apr_config cfg;
+    apr::DevCfg dc;
+    cudaStream_t stream;
+    int device;
+    apr_particles p;
+    long long n, cap, next_id;
+    unsigned long long step;
+    char* ws;
+    size_t ws_bytes;
+    apr::Workspace W;
+    apr_region regions[APR_MAXREG];
+    int nreg;
+    apr_sink sinks[APR_MAXSINK];
+    int nsink;
+    long long* hbuf;          // pinned host read-back buffer
+    std::string err;
+    bool bound;
+    bool have_force;
+    int ncell;
+};
+
+namespace apr {
+
+// ---------------------------------------------------------------- helpers
+
+__host__ __device__ inline unsigned long long neighbour_threshold(double h, double delta)
+{
+    // b is within the kernel radius 2h of a iff r2_lattice(a, b) < thr(h)
+    double t = (2.0 * h) / delta;
+    double t2 = t * t;
+    if (!(t2 < 4.6e18)) return 4611686018427387904ULL;
+    return (unsigned long long)ceil(t2);
+}
+
+__device__ __forceinline__ long long min_image(long long d, int periodic, long long L)
+{
+    if (periodic) {
+        if (2 * d > L) d -= L;
+        else if (2 * d < -L) d += L;
+    }
+    return d;
+}
+
+__device__ __forceinline__ int min_image32(int d, int periodic, int L)
+{
+    if (periodic) {
+        if (2 * d > L) d -= L;
+        else if (2 * d < -L) d += L;
+    }
+    return d;
+}
+
+// relative mass 2^-level as an exact float
+__device__ __forceinline__ float level_mass_f(int level) { return __int_as_float((127 - level) << 23); }
+__device__ __forceinline__ double level_mass_d(int level)
+{
+    return __longlong_as_double((long long)(1023 - level) << 52);
+}
+
+// ------------------------------------------------------ launch plumbing
+
+// host-side helpers (apr_api.cu)
+apr_status fail(apr_ctx* c, apr_status s, const std::string& msg);
+apr_status cuda_check(apr_ctx* c, cudaError_t e, const char* what);
+DevRegions dev_regions(const apr_ctx* c);
+DevSinks dev_sinks(const apr_ctx* c);
+
+// index build (apr_index.cu)
+apr_status scan_u32(apr_ctx* c, const unsigned int* in, unsigned int* out, long long n,
+                    unsigned int* total_dev);
+apr_status quantise(apr_ctx* c);
+apr_status index_sort(apr_ctx* c);           // quantise, Morton sort, gather, tree, node data
+apr_status index_refresh_h(apr_ctx* c);      // re-gather h and node hmax after a density pass
+apr_status index_lists(apr_ctx* c, int mode, double reach);  // cells, candidates, lists
+
+// SPH passes (apr_sph.cu)
+apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv);
+apr_status force_pass(apr_ctx* c);
+apr_status gather_force_data(apr_ctx* c);
+
+// refinement, sinks, integration (apr_refine.cu)
+apr_status split_merge_pass(apr_ctx* c, apr_counts* cnt);
+apr_status clear_changed(apr_ctx* c);
+apr_status merge_pairs_debug(apr_ctx* c, int level, long long* pairs, long long cap,
+                             long long* npairs, long long* spare);
+apr_status sink_gravity(apr_ctx* c);
+apr_status accrete(apr_ctx* c, long long* naccreted);
+apr_status kick(apr_ctx* c, double hdt);
+apr_status drift(apr_ctx* c, double dt);
+apr_status compute_stats(apr_ctx* c, apr_stats* st);
+apr_status compute_timestep(apr_ctx* c, double* dt);
+apr_status compact(apr_ctx* c, long long* removed);
+
+inline int nblocks(long long n, int bs) { return (int)((n + bs - 1) / bs); }
+
+}  // namespace apr

@@ -1,0 +1,103 @@
+"""GPU steps of the whole hot path against the oracle: initial refinement and
+kick-drift-kick steps on a shock tube with a two-level slab and on a disc with
+a planet; conservation on the GPU; sampled checks at the full shock-tube size."""
+import numpy as np
+import pytest
+
+import apr_synth
+import oracle
+from gpu_util import rel, sim, with_velocities
+
+pytestmark = pytest.mark.gpu
+
+
+def _compare_by_id(o, g, fields, tol):
+    io, ig = o["id"], g.get("id")
+    so, sg = np.argsort(io), np.argsort(ig)
+    assert np.array_equal(io[so], ig[sg])
+    for f, t in zip(fields, tol):
+        a, b = g.get(f)[sg], o[f][so]
+        assert np.max(np.abs(a - b) / (np.abs(b) + t[1])) < t[0], f
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_sod_init_and_steps(precision):
+    w = apr_synth.sod(10)
+    cap = 4 * len(w["p"]["x"])
+    o = oracle.Oracle(w, capacity=cap)
+    g = sim(w, precision, capacity=cap)
+    po, pg = o.init(), g.init()
+    assert g.n == o.n and po == pg
+    assert np.array_equal(np.bincount(g.get("level")), np.bincount(o["level"]))
+    tol = 1e-9 if precision == "fp64" else 2e-5
+    _compare_by_id(o, g, ("x", "rho", "h"), [(tol, 0.0)] * 3)
+    dt = 0.5 * o.timestep()
+    for k in range(3):
+        co, so = o.step(dt)
+        _, sg, cg = g.step(dt)
+        assert list(cg.n_split) == list(co.n_split) and list(cg.n_merge) == list(co.n_merge)
+        assert g.n == o.n
+        assert sg.mass == pytest.approx(so.mass, rel=1e-13)
+    _compare_by_id(o, g, ("x", "vx", "rho", "u"), [(10 * tol, 0.01), (100 * tol, 0.05),
+                                                  (10 * tol, 0.0), (10 * tol, 0.0)])
+
+
+def test_disc_planet_steps_with_accretion():
+    w = apr_synth.disc_planet(20000)
+    cap = 4 * 20000
+    o = oracle.Oracle(w, capacity=cap)
+    g = sim(w, "fp64", capacity=cap)
+    o.init()
+    g.init()
+    assert g.n == o.n
+    dt = 0.02
+    for _ in range(2):
+        co, so = o.step(dt)
+        _, sg, cg = g.step(dt)
+        assert cg.n_accreted == co.n_accreted
+        assert g.n == o.n
+        assert sg.mass == pytest.approx(so.mass, rel=1e-13)
+        for k in range(3):
+            assert sg.mom[k] == pytest.approx(so.mom[k], rel=1e-9, abs=1e-15)
+    ks, kg = o.sinks_state(), g.sinks()
+    for a, b in zip(ks, kg):
+        assert np.allclose(a["x"], b["x"], rtol=1e-12, atol=1e-14)
+        assert a["m"] == pytest.approx(b["m"], rel=1e-14)
+
+
+def test_gpu_step_conserves_mass_and_momentum_fp32():
+    w = with_velocities(apr_synth.lattice_box(12, 0.1, sphere_R=(0.3,), seed=4), 0.2)
+    w["cfg"]["alpha_u"] = 1.0
+    g = sim(w, "fp32", capacity=8 * 12 ** 3)
+    g.init()
+    s0 = g.stats()
+    for _ in range(5):
+        _, s, _ = g.step(0.0)
+    assert s.mass == pytest.approx(s0.mass, rel=1e-14)
+    scale = s0.mass * 0.2
+    for k in range(3):
+        assert abs(s.mom[k] - s0.mom[k]) < 1e-6 * scale
+    assert abs((s.ekin + s.etherm) / (s0.ekin + s0.etherm) - 1) < 1e-3
+
+
+@pytest.mark.slow
+def test_full_size_sod_sampled():
+    """The full 123,480-particle tube after the initial refinement (the bench's
+    state): density and force of sampled particles against the oracle."""
+    w = apr_synth.c2_sod()
+    cap = 3 * len(w["p"]["x"])
+    g = sim(w, "fp32", capacity=cap)
+    g.init()
+    o = oracle.Oracle(w, capacity=cap)
+    o.init()
+    assert g.n == o.n
+    io, ig = o["id"], g.get("id")
+    so, sg = np.argsort(io), np.argsort(ig)
+    assert np.array_equal(io[so], ig[sg])
+    rng = np.random.default_rng(0)
+    pick = rng.choice(o.n, 300, replace=False)
+    a_o, a_g = so[pick], sg[pick]
+    assert rel(g.get("rho")[a_g], o["rho"][a_o]).max() < 2e-5
+    scale = o["pres"][a_o] / (o["rho"][a_o] * o["h"][a_o])
+    err = np.abs(g.get("ax")[a_g] - o["ax"][a_o]) / (np.abs(o["ax"][a_o]) + scale)
+    assert err.max() < 2e-4
