@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the APR SPH hot path on one GB300 (replicas on N GPUs).
+
+Workload: the full three-dimensional Sod shock tube (140x28x28 + 70x14x14 =
+123,480 equal-mass particles, ~210k after the initial two-level refinement of
+the slab |x| < 0.15 / 0.10).  A step is one whole pass of the hot path
+(kick, drift, accretion, zones, split/merge, neighbour index, density solve,
+forces, kick) through the C ABI.  Metric: particle-steps per second, counting
+the particles the density and force passes ran on.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(density + force on a bounded sample of the same state) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "APR particle-steps/s (density+force), FP32-mixed vs FP64 GPU, at stated error"
+UNIT = "particle-steps/s"
+WORKLOAD = "sod_shock_tube_3d_123480p_2level_slab"
+
+# Algorithmic FP32 work per pair, counted once from the kernel source (FMA = 2):
+# density, per pair inside 2h per Newton-Raphson iteration: relative coords 3,
+# r^2 5, sqrt 1, q 1, M4 f and f' 8, two compensated sums 11  -> 29;
+# force, per pair inside max(2h_a, 2h_b): coords/r^2/rsqrt/r/q 12, two M4
+# derivatives 8, F_a F_b 5, v.r 9, viscosity on approaching pairs (half) 6,
+# pressure term 5, three compensated components 15, energy 7, conductivity 13,
+# signal speed 3  -> 83.
+FLOPS_PER_PAIR = {"density": 29.0, "force": 83.0}
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nL", type=int, default=28, help="shock-tube resolution (28 = full size)")
+    return ap.parse_args()
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def workload(nL):
+    import apr_synth
+    return apr_synth.c2_sod() if nL == 28 else apr_synth.sod(nL)
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if bus_id:
+            cmd += ["-i", bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [l.strip().split(", ") for l in self.file.read().splitlines() if l.strip()]
+        os.unlink(self.file.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in rows if len(r) >= 9 for k in range(4)
+                          if r[5 + k].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------- our arm
+
+def timed_steps(sim, torch, k, flush):
+    """Device time of k steps (CUDA events on the library's stream), L2 flushed
+    (256 MB written) before each step, outside the events."""
+    st = sim.stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(k)]
+    psteps = 0
+    for i in range(k):
+        with torch.cuda.stream(st):
+            flush.zero_()
+        ev[i][0].record(st)
+        sim.step(0.0)
+        ev[i][1].record(st)
+        psteps += sim.n
+    st.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    return ms, psteps
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    src = os.path.join(ROOT, "paper_2409_11470_gb300", "csrc", "apr_sph.cu")
+    with open(src, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()[:16]
+    return rec if rec.get("source_sha256_16") == digest else None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import apr_synth  # noqa: F401
+    from paper_2409_11470_gb300.binding import F64_FIELDS, Simulation
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = workload(args.nL)
+    n0 = len(w["p"]["x"])
+    cap = 3 * n0
+    sim = Simulation(w, capacity=cap, precision="fp32")
+    sim.init()
+    n_init = sim.n
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        sim.step(0.0)
+    props = torch.cuda.get_device_properties(local)
+    bus = getattr(props, "pci_bus_id", None)
+    sim.profile_enable(True)
+    launches0 = sim.profile()["launches"]  # kernels launched before the timed region
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(bus)
+    t_wall = time.perf_counter()
+    ms, psteps = timed_steps(sim, torch, args.steps, flush)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    prof = sim.profile()
+    sim.profile_enable(False)
+    launches = prof["launches"] - launches0
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    ps_t = torch.tensor([float(psteps)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(ps_t, op=dist.ReduceOp.SUM)
+    ms_max, ps_all = float(ms_t.item()), float(ps_t.item())
+    value = ps_all / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (live events on the library's stream)
+    groups = {g: prof[g] for g in ("sort", "tree", "lists", "density", "force", "refine", "other")}
+    dom = max(("density", "force"), key=lambda g: groups[g]["ms"])
+    gd = groups[dom]
+    sm_max = clocks["sm_max_mhz"] or 2070.0
+    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flops_launch = gd["pairs"] * FLOPS_PER_PAIR[dom] / max(gd["calls"], 1)
+    ms_launch = gd["ms"] / max(gd["calls"], 1)
+    achieved = flops_launch / (ms_launch / 1e3) / 1e12
+    tr = traffic_record(f"k_{dom}_f32")
+    roofline = {"bound": "alu", "kernel": f"k_{dom}<float>", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": tr["dram_bytes_per_launch"] * (n_init / tr["n"]) if tr else None,
+                "peak_note": f"FP32 FMA pipes: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                             f"{sm_max:.0f} MHz (derived, no measured FP32 peak)",
+                "pairs_per_launch": gd["pairs"] / max(gd["calls"], 1),
+                "flops_per_pair": FLOPS_PER_PAIR[dom], "ms_per_launch": ms_launch}
+    breakdown = {g: round(v["ms"] / args.steps, 4) for g, v in groups.items()}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD if args.nL == 28 else f"sod_nL{args.nL}",
+                      "n_initial": n0, "n_after_init": n_init, "n_last": sim.n,
+                      "precision": "fp32-mixed (pair sums f32 compensated; state, integration, "
+                                   "reductions f64)",
+                      "l2": "flushed by a 256 MB write before every timed step",
+                      "parallelism": "replicas" if world > 1 else "single GPU",
+                      "wall_s_timed": t_wall, "launches_before_timed": launches0},
+           "roofline": roofline, "breakdown_ms_per_step": breakdown,
+           "gpu_launches": launches, "clocks": clocks}
+
+    if rank == 0 and not args.no_fp64:
+        s64 = Simulation(w, capacity=cap, precision="fp64")
+        s64.init()
+        for _ in range(max(1, args.warmup // 2)):
+            s64.step(0.0)
+        ms64, ps64 = timed_steps(s64, torch, args.fp64_steps, flush)
+        v64 = ps64 / (ms64 / 1e3)
+        out["fp64"] = {"value": v64, "ms_per_step": ms64 / args.fp64_steps,
+                       "steps": args.fp64_steps}
+        out["fp32_over_fp64"] = value / v64
+        s64.close()
+
+    if rank == 0 and not args.no_e2e:
+        # the same steps through the public API with host buffers: pinned host state
+        # is copied in before and read back after every step
+        fields = list(F64_FIELDS) + ["level", "flags", "id"]
+        host = {f: torch.empty_like(sim.t[f], device="cpu").pin_memory() for f in fields}
+        for f in fields:
+            host[f].copy_(sim.t[f])
+        st = sim.stream
+        evs = []
+        bi = bo = 0
+        ps_e = 0
+        for _ in range(args.steps):
+            n = sim.n
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(st):
+                flush.zero_()
+            e0.record(st)
+            with torch.cuda.stream(st):
+                for f in fields:
+                    sim.t[f][:n].copy_(host[f][:n], non_blocking=True)
+            sim.step(0.0)
+            n2 = sim.n
+            with torch.cuda.stream(st):
+                for f in fields:
+                    host[f][:n2].copy_(sim.t[f][:n2], non_blocking=True)
+            e1.record(st)
+            st.synchronize()
+            evs.append(e0.elapsed_time(e1))
+            bi += sum(n * host[f].element_size() for f in fields)
+            bo += sum(n2 * host[f].element_size() for f in fields)
+            ps_e += n2
+        out["e2e"] = {"value": ps_e / (sum(evs) / 1e3), "unit": UNIT,
+                      "h2d_bytes_per_step": bi // args.steps, "d2h_bytes_per_step": bo // args.steps}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = oracle_baseline(w, cap, args.cpu_seconds)
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    sim.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------ the oracle
+
+def oracle_baseline(w, cap, seconds):
+    """Density + force of the FP64 oracle (as it stands) on a bounded sample of the
+    initialised state; returns particle-steps/s and how it was measured."""
+    import numpy as np
+
+    import oracle
+    o = oracle.Oracle(w, capacity=cap)
+    o.init()
+    rng = np.random.default_rng(0)
+    m = 256
+    t = 0.0
+    while True:
+        sample = rng.choice(o.n, m, replace=False)
+        t0 = time.perf_counter()
+        o.density(sample)
+        o.force(sample)
+        t = time.perf_counter() - t0
+        if t * 4 > seconds or m >= o.n:
+            break
+        m = min(o.n, int(m * max(2.0, 0.5 * seconds / max(t, 1e-3))))
+    total = 0.0
+    done = 0
+    steps = max(1, int(round(seconds / max(t, 1e-3))))
+    for _ in range(steps):
+        sample = rng.choice(o.n, m, replace=False)
+        t0 = time.perf_counter()
+        o.density(sample)
+        o.force(sample)
+        total += time.perf_counter() - t0
+        done += m
+    return {"value": done / total, "unit": UNIT, "cores": o.threads(), "kind": "oracle",
+            "sample": f"density+force of {m} random particles of the initialised "
+                      f"{o.n}-particle shock tube, cell-list enumeration, "
+                      f"{steps} sample(s), {total:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    w = workload(args.nL)
+    n0 = len(w["p"]["x"])
+    import numpy as np
+
+    import oracle
+    o = oracle.Oracle(w, capacity=3 * n0)
+    o.init()
+    rng = np.random.default_rng(0)
+    per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))  # whole run within minutes
+    m = 256
+    while True:
+        sample = rng.choice(o.n, m, replace=False)
+        t0 = time.perf_counter()
+        o.density(sample)
+        o.force(sample)
+        t = time.perf_counter() - t0
+        if t * 2 > per_step or m >= o.n:
+            break
+        m = min(o.n, int(m * max(2.0, 0.8 * per_step / max(t, 1e-3))))
+    for _ in range(args.warmup):
+        s = rng.choice(o.n, m, replace=False)
+        o.density(s)
+        o.force(s)
+    total = 0.0
+    for _ in range(args.steps):
+        s = rng.choice(o.n, m, replace=False)
+        t0 = time.perf_counter()
+        o.density(s)
+        o.force(s)
+        total += time.perf_counter() - t0
+    value = args.steps * m / total
+    sample = (f"each step: density+force of {m} random particles of the initialised "
+              f"{o.n}-particle shock tube (FP64 oracle, cell-list enumeration)")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD if args.nL == 28 else f"sod_nL{args.nL}",
+                      "n_initial": n0, "n_after_init": o.n},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": o.threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

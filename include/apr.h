@@ -66,7 +66,7 @@ enum { APR_PREC_FP32_MIXED = 0, APR_PREC_FP64 = 1 };
  * precision: APR_PREC_FP32_MIXED (pair sums in float on relative lattice
  * coordinates, compensated; state, integration and global sums in double) or
  * APR_PREC_FP64.  nr_tol, nr_maxit: h-rho Newton-Raphson stopping rule.
- * max_neigh: capacity of one particle's neighbour list (0 = default 256).
+ * max_neigh: capacity of one particle's neighbour list (0 = default 512).
  */
 typedef struct {
     double box_lo[3], box_hi[3];
@@ -128,6 +128,33 @@ typedef struct {
 typedef struct {
     double mass, mom[3], ang[3], ekin, etherm;
 } apr_stats;
+
+/* kernel groups timed by the profiler (apr_profile_enable) */
+enum {
+    APR_PROF_SORT = 0,      /* lattice quantisation, Morton keys, radix sort, gathers */
+    APR_PROF_TREE = 1,      /* radix tree construction and bottom-up node boxes */
+    APR_PROF_LISTS = 2,     /* cells, candidate cells, neighbour lists */
+    APR_PROF_DENSITY = 3,   /* the h-rho Newton-Raphson kernel */
+    APR_PROF_FORCE = 4,     /* the force / energy kernel */
+    APR_PROF_REFINE = 5,    /* split / merge pass */
+    APR_PROF_OTHER = 6,     /* force-data gathers, gravity, accretion, integration, sums */
+    APR_NPROF = 8
+};
+
+/*
+ * Profile counters.  ms/calls: device time (CUDA events recorded on the
+ * library's stream around each group) and number of timed calls per group,
+ * accumulated while profiling is enabled.  pairs: pair evaluations done by
+ * the density kernel (pairs inside 2h, summed over Newton-Raphson iterations)
+ * and by the force kernel (pairs inside max(2h_a, 2h_b)).  launches: every
+ * kernel the library launched since the context was created (always counted).
+ */
+typedef struct {
+    double ms[APR_NPROF];
+    long long calls[APR_NPROF];
+    double pairs[APR_NPROF];
+    long long launches;
+} apr_profile;
 
 typedef struct apr_ctx apr_ctx;
 
@@ -216,6 +243,17 @@ apr_status apr_neighbour_lists(apr_ctx* ctx, int mode, long long* offsets, int* 
  */
 apr_status apr_merge_pairs(apr_ctx* ctx, int level, long long* pairs, long long cap,
                            long long* npairs, long long* spare);
+
+/*
+ * Profiling (not part of the method): on != 0 starts timing kernel groups with
+ * CUDA events on the bound stream and counting pair evaluations, and clears
+ * the counters; on == 0 stops.  The event pool is created here, not in the
+ * hot calls.
+ */
+apr_status apr_profile_enable(apr_ctx* ctx, int on);
+
+/* Read (and with reset != 0 clear) the profile counters; synchronises the stream. */
+apr_status apr_profile_read(apr_ctx* ctx, apr_profile* out, int reset);
 
 #ifdef __cplusplus
 }

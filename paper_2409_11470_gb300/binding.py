@@ -63,6 +63,15 @@ class Stats(C.Structure):
                 ("ekin", C.c_double), ("etherm", C.c_double)]
 
 
+NPROF = 8
+PROF_GROUPS = ("sort", "tree", "lists", "density", "force", "refine", "other")
+
+
+class Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * NPROF), ("calls", C.c_longlong * NPROF),
+                ("pairs", C.c_double * NPROF), ("launches", C.c_longlong)]
+
+
 class AprError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -95,6 +104,8 @@ def _load():
         "apr_stats_compute": [vp, P(Stats)],
         "apr_neighbour_lists": [vp, i32, P(ll), P(i32), ll, P(ll)],
         "apr_merge_pairs": [vp, i32, P(ll), ll, P(ll), P(ll)],
+        "apr_profile_enable": [vp, i32],
+        "apr_profile_read": [vp, P(Profile), i32],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -306,6 +317,18 @@ class Simulation:
                 continue
             self._check(st, "neighbour_lists")
             return off, idx[: tot.value]
+
+    def profile_enable(self, on=True):
+        self._check(lib.apr_profile_enable(self.ctx, 1 if on else 0), "profile_enable")
+
+    def profile(self, reset=False):
+        """Per-group device ms, timed calls and pair evaluations, plus the launch count."""
+        pr = Profile()
+        self._check(lib.apr_profile_read(self.ctx, C.byref(pr), 1 if reset else 0), "profile")
+        out = {g: dict(ms=pr.ms[k], calls=pr.calls[k], pairs=pr.pairs[k])
+               for k, g in enumerate(PROF_GROUPS)}
+        out["launches"] = pr.launches
+        return out
 
     def merge_pairs(self, level):
         n = self.n

@@ -53,6 +53,37 @@ DevSinks dev_sinks(const apr_ctx* c)
     return s;
 }
 
+// ---------------------------------------------------------------- profiling
+
+static void prof_drain(apr_ctx* c)
+{
+    if (c->ev_used == 0) return;
+    cudaStreamSynchronize(c->stream);
+    for (int s = 0; s < c->ev_used; ++s) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[2 * s], c->ev[2 * s + 1]) == cudaSuccess) {
+            c->prof_ms[c->ev_group[s]] += ms;
+            c->prof_calls[c->ev_group[s]] += 1;
+        }
+    }
+    c->ev_used = 0;
+}
+
+int prof_begin(apr_ctx* c, int group)
+{
+    if (!c->prof) return -1;
+    if (c->ev_used == PROF_POOL) prof_drain(c);
+    int s = c->ev_used++;
+    c->ev_group[s] = group;
+    cudaEventRecord(c->ev[2 * s], c->stream);
+    return s;
+}
+
+void prof_end(apr_ctx* c, int slot)
+{
+    if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], c->stream);
+}
+
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Workspace* W)
@@ -112,6 +143,7 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.nbr = (unsigned int*)take(4 * K * C);
     w.ncnt = (int*)take(4 * C);
     w.status = (int*)take(4 * 64);
+    w.counters = (unsigned long long*)take(8 * 16);
     w.tgt = (unsigned char*)take(C);
     w.uflag = (unsigned int*)take(4 * C);
     w.uscan = (unsigned int*)take(4 * C);
@@ -228,20 +260,24 @@ static apr_status run_density(apr_ctx* c, long long* noconv_out)
 {
     apr_status s = index_sort(c);
     if (s != APR_OK) return s;
-    long long unc = 0, noconv = 0;
-    for (int attempt = 0; attempt < 8; ++attempt) {
+    long long unc = 0, noconv = 0, shrinks = 0;
+    for (int attempt = 0; attempt < 64; ++attempt) {
         cudaMemsetAsync(c->W.status, 0, 2 * sizeof(int), c->stream);
-        s = index_lists(c, 0, DENSITY_REACH);
+        s = index_lists(c, 0, DENSITY_REACH, true);
         if (s != APR_OK) return s;
         s = check_overflow(c);
         if (s != APR_OK) return s;
         s = density_pass(c, &unc, &noconv);
         if (s != APR_OK) return s;
+        shrinks += c->last_shrink;
         if (unc == 0) break;
         s = index_refresh_h(c);
         if (s != APR_OK) return s;
     }
     if (noconv_out) *noconv_out = noconv + unc;
+    if (unc && shrinks)
+        return fail(c, APR_ERR_NEIGH_OVERFLOW,
+                    "neighbour lists cannot hold the particles within reach: raise max_neigh");
     if (unc) return fail(c, APR_ERR_NR_NOCONV, "smoothing lengths kept outgrowing their lists");
     if (noconv) return fail(c, APR_ERR_NR_NOCONV, "h-rho iteration did not converge everywhere");
     return APR_OK;
@@ -254,13 +290,17 @@ static apr_status run_force(apr_ctx* c)
     cudaMemsetAsync(c->W.status, 0, 2 * sizeof(int), c->stream);
     s = index_lists(c, 1, 1.0);
     if (s != APR_OK) return s;
+    int ps = prof_begin(c, APR_PROF_OTHER);
     s = gather_force_data(c);
+    prof_end(c, ps);
     if (s != APR_OK) return s;
     s = force_pass(c);
     if (s != APR_OK) return s;
     s = check_overflow(c);
     if (s != APR_OK) return s;
+    ps = prof_begin(c, APR_PROF_OTHER);
     s = sink_gravity(c);
+    prof_end(c, ps);
     if (s != APR_OK) return s;
     c->have_force = true;
     return APR_OK;
@@ -302,6 +342,15 @@ apr_status apr_create(apr_ctx** out, const apr_config* cfg, void* stream)
     c->step = 0;
     c->nreg = c->nsink = 0;
     c->ncell = 0;
+    c->last_shrink = 0;
+    c->launches = 0;
+    c->prof = false;
+    c->ev_used = 0;
+    for (int g = 0; g < APR_NPROF; ++g) {
+        c->prof_ms[g] = 0.0;
+        c->prof_calls[g] = 0;
+    }
+    for (int k = 0; k < 2 * PROF_POOL; ++k) c->ev[k] = nullptr;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaMallocHost((void**)&c->hbuf, 4096) != cudaSuccess) {
         delete c;
@@ -314,6 +363,8 @@ apr_status apr_create(apr_ctx** out, const apr_config* cfg, void* stream)
 void apr_destroy(apr_ctx* c)
 {
     if (!c) return;
+    for (int k = 0; k < 2 * PROF_POOL; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->hbuf) cudaFreeHost(c->hbuf);
     delete c;
 }
@@ -349,7 +400,7 @@ apr_status apr_bind(apr_ctx* c, const apr_particles* p, long long n, long long c
     c->ws_bytes = bytes;
     workspace_layout(c->cfg, capacity, c->ws, &c->W);
     apr_status s =
-        cuda_check(c, cudaMemsetAsync(c->W.status, 0, 4 * 64, c->stream), "bind");
+        cuda_check(c, cudaMemsetAsync(c->W.status, 0, 4 * 64 + 8 * 16 + 256, c->stream), "bind");
     if (s != APR_OK) return s;
     c->bound = true;
     c->have_force = false;
@@ -471,12 +522,14 @@ apr_status apr_step(apr_ctx* c, double dt, double* dt_used, apr_stats* stats,
         if (s != APR_OK) return s;
     }
     const double hdt = 0.5 * dt;
+    int ps = prof_begin(c, APR_PROF_OTHER);
     s = kick(c, hdt);
     if (s != APR_OK) return s;
     s = drift(c, dt);
     if (s != APR_OK) return s;
     long long na = 0;
     s = accrete(c, &na);
+    prof_end(c, ps);
     if (s != APR_OK) return s;
     track_regions(c);
     apr_counts cnt;
@@ -487,7 +540,9 @@ apr_status apr_step(apr_ctx* c, double dt, double* dt_used, apr_stats* stats,
     if (s != APR_OK) return s;
     s = run_force(c);
     if (s != APR_OK) return s;
+    ps = prof_begin(c, APR_PROF_OTHER);
     s = kick(c, hdt);
+    prof_end(c, ps);
     if (s != APR_OK) return s;
     if (dt_used) *dt_used = dt;
     if (counts) *counts = cnt;
@@ -533,6 +588,54 @@ apr_status apr_neighbour_lists(apr_ctx* c, int mode, long long* offsets, int* id
         long long a = perm[sl], o = offsets[a];
         for (int k = 0; k < cnt[sl]; ++k) idx[o + k] = (int)perm[nb[(size_t)k * n + sl]];
     }
+    return APR_OK;
+}
+
+apr_status apr_profile_enable(apr_ctx* c, int on)
+{
+    if (!c) return APR_ERR_ARG;
+    if (on) {
+        for (int k = 0; k < 2 * PROF_POOL; ++k)
+            if (!c->ev[k] && cudaEventCreate(&c->ev[k]) != cudaSuccess)
+                return fail(c, APR_ERR_CUDA, "event pool");
+        prof_drain(c);
+        for (int g = 0; g < APR_NPROF; ++g) {
+            c->prof_ms[g] = 0.0;
+            c->prof_calls[g] = 0;
+        }
+        if (c->bound) cudaMemsetAsync(c->W.counters, 0, 8 * 16, c->stream);
+    } else {
+        prof_drain(c);
+    }
+    c->prof = on != 0;
+    c->dc.prof = on ? 1 : 0;
+    return cuda_check(c, cudaGetLastError(), "profile enable");
+}
+
+apr_status apr_profile_read(apr_ctx* c, apr_profile* out, int reset)
+{
+    if (!c || !out) return APR_ERR_ARG;
+    prof_drain(c);
+    memset(out, 0, sizeof(*out));
+    for (int g = 0; g < APR_NPROF; ++g) {
+        out->ms[g] = c->prof_ms[g];
+        out->calls[g] = c->prof_calls[g];
+    }
+    out->launches = c->launches;
+    if (c->bound) {
+        unsigned long long cnt[APR_NPROF];
+        apr_status s = cuda_check(c, cudaMemcpyAsync(cnt, c->W.counters, sizeof(cnt),
+                                                     cudaMemcpyDeviceToHost, c->stream), "profile");
+        if (s == APR_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "profile");
+        if (s != APR_OK) return s;
+        for (int g = 0; g < APR_NPROF; ++g) out->pairs[g] = (double)cnt[g];
+        if (reset) cudaMemsetAsync(c->W.counters, 0, 8 * 16, c->stream);
+    }
+    if (reset)
+        for (int g = 0; g < APR_NPROF; ++g) {
+            c->prof_ms[g] = 0.0;
+            c->prof_calls[g] = 0;
+        }
     return APR_OK;
 }
 

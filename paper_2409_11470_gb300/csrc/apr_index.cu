@@ -72,26 +72,26 @@ __global__ void k_scan_total(const unsigned int* in, const unsigned int* out, lo
     *total = n > 0 ? out[n - 1] + in[n - 1] : 0u;
 }
 
-static void scan_rec(cudaStream_t st, const unsigned int* in, unsigned int* out, long long n,
+static void scan_rec(apr_ctx* c, const unsigned int* in, unsigned int* out, long long n,
                      unsigned int* tmp)
 {
     const long long nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
     if (nb <= 1) {
-        k_scan_block<<<1, 256, 0, st>>>(in, out, nullptr, n);
+        APR_LAUNCH(c, k_scan_block, 1, 256, in, out, nullptr, n);
         return;
     }
     unsigned int* sums = tmp;
     unsigned int* offs = tmp + nb;
-    k_scan_block<<<(unsigned)nb, 256, 0, st>>>(in, out, sums, n);
-    scan_rec(st, sums, offs, nb, tmp + 2 * nb);
-    k_scan_add<<<nblocks(n, 256), 256, 0, st>>>(out, offs, n);
+    APR_LAUNCH(c, k_scan_block, (unsigned)nb, 256, in, out, sums, n);
+    scan_rec(c, sums, offs, nb, tmp + 2 * nb);
+    APR_LAUNCH(c, k_scan_add, nblocks(n, 256), 256, out, offs, n);
 }
 
 apr_status scan_u32(apr_ctx* c, const unsigned int* in, unsigned int* out, long long n,
                     unsigned int* total_dev)
 {
-    if (n > 0) scan_rec(c->stream, in, out, n, c->W.scan_tmp);
-    if (total_dev) k_scan_total<<<1, 1, 0, c->stream>>>(in, out, n, total_dev);
+    if (n > 0) scan_rec(c, in, out, n, c->W.scan_tmp);
+    if (total_dev) APR_LAUNCH(c, k_scan_total, 1, 1, in, out, n, total_dev);
     return cuda_check(c, cudaGetLastError(), "scan");
 }
 
@@ -142,7 +142,7 @@ __global__ void k_quantise(DevCfg dc, const double* __restrict__ x, const double
 
 apr_status quantise(apr_ctx* c)
 {
-    k_quantise<<<nblocks(c->n, 256), 256, 0, c->stream>>>(c->dc, c->p.x, c->p.y, c->p.z,
+    APR_LAUNCH(c, k_quantise, nblocks(c->n, 256), 256, c->dc, c->p.x, c->p.y, c->p.z,
                                                           c->p.level, c->n, c->W.xi, nullptr,
                                                           nullptr);
     return cuda_check(c, cudaGetLastError(), "quantise");
@@ -216,9 +216,9 @@ static apr_status radix_sort(apr_ctx* c, long long n)
     const int ntiles = nblocks(n, RADIX_TILE);
     int cur = 0;
     for (int shift = 0; shift < 64; shift += 8) {
-        k_radix_hist<<<ntiles, 256, 0, c->stream>>>(W.key[cur], n, shift, W.hist, ntiles);
+        APR_LAUNCH(c, k_radix_hist, ntiles, 256, W.key[cur], n, shift, W.hist, ntiles);
         scan_u32(c, W.hist, W.hist + (size_t)256 * ntiles, (long long)256 * ntiles, nullptr);
-        k_radix_scatter<<<ntiles, 256, 0, c->stream>>>(W.key[cur], W.val[cur], W.key[cur ^ 1],
+        APR_LAUNCH(c, k_radix_scatter, ntiles, 256, W.key[cur], W.val[cur], W.key[cur ^ 1],
                                                        W.val[cur ^ 1], n, shift,
                                                        W.hist + (size_t)256 * ntiles, ntiles);
         cur ^= 1;
@@ -370,7 +370,7 @@ static apr_status tree_up(apr_ctx* c)
     int n = (int)c->n;
     if (n < 2) return APR_OK;
     cudaMemsetAsync(W.visit, 0, sizeof(int) * (size_t)(n - 1), c->stream);
-    k_tree_up<<<nblocks(n, 256), 256, 0, c->stream>>>(n, W.pk, W.sh, W.left, W.right,
+    APR_LAUNCH(c, k_tree_up, nblocks(n, 256), 256, n, W.pk, W.sh, W.left, W.right,
                                                       W.parent_int, W.parent_leaf, W.visit, W.nlo,
                                                       W.nhi, W.nhmax, W.status);
     return cuda_check(c, cudaGetLastError(), "tree up");
@@ -381,29 +381,37 @@ apr_status index_sort(apr_ctx* c)
     Workspace& W = c->W;
     long long n = c->n;
     if (n <= 0) return APR_OK;
-    k_quantise<<<nblocks(n, 256), 256, 0, c->stream>>>(c->dc, c->p.x, c->p.y, c->p.z, c->p.level,
+    int ps = prof_begin(c, APR_PROF_SORT);
+    APR_LAUNCH(c, k_quantise, nblocks(n, 256), 256, c->dc, c->p.x, c->p.y, c->p.z, c->p.level,
                                                        n, W.xi, W.key[0], W.val[0]);
     apr_status s = radix_sort(c, n);
     if (s != APR_OK) return s;
     const bool f64 = c->cfg.precision == APR_PREC_FP64;
-    k_gather_index<<<nblocks(n, 256), 256, 0, c->stream>>>(n, W.perm, W.xi, c->p.h, c->p.x, c->p.y,
+    APR_LAUNCH(c, k_gather_index, nblocks(n, 256), 256, n, W.perm, W.xi, c->p.h, c->p.x, c->p.y,
                                                            c->p.z, W.pk, W.sh, f64 ? W.sx : nullptr,
                                                            W.sy, W.sz);
+    prof_end(c, ps);
+    ps = prof_begin(c, APR_PROF_TREE);
     if (n >= 2)
-        k_tree_internal<<<nblocks(n - 1, 256), 256, 0, c->stream>>>(W.skey, (int)n, W.left, W.right,
+        APR_LAUNCH(c, k_tree_internal, nblocks(n - 1, 256), 256, W.skey, (int)n, W.left, W.right,
                                                                      W.parent_int, W.parent_leaf);
     s = cuda_check(c, cudaGetLastError(), "index sort");
     if (s != APR_OK) return s;
-    return tree_up(c);
+    s = tree_up(c);
+    prof_end(c, ps);
+    return s;
 }
 
 apr_status index_refresh_h(apr_ctx* c)
 {
     if (c->n <= 0) return APR_OK;
-    k_gather_h<<<nblocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->W.perm, c->p.h, c->W.sh);
+    int ps = prof_begin(c, APR_PROF_TREE);
+    APR_LAUNCH(c, k_gather_h, nblocks(c->n, 256), 256, c->n, c->W.perm, c->p.h, c->W.sh);
     apr_status s = cuda_check(c, cudaGetLastError(), "refresh h");
     if (s != APR_OK) return s;
-    return tree_up(c);
+    s = tree_up(c);
+    prof_end(c, ps);
+    return s;
 }
 
 // ------------------------------------------------------------------ cells
@@ -479,7 +487,8 @@ __global__ void k_candidates(DevCfg dc, int mode, double reach, int ncell, int n
                              const int* __restrict__ right, const int4* __restrict__ pk,
                              const double* __restrict__ sh, const int4* __restrict__ nlo,
                              const int4* __restrict__ nhi, const double* __restrict__ nhmax,
-                             int2* __restrict__ cand, int* __restrict__ ncand, int* status)
+                             int2* __restrict__ cand, int* __restrict__ ncand, int* status,
+                             int graceful)
 {
     int cid = blockIdx.x * blockDim.x + threadIdx.x;
     if (cid >= ncell) return;
@@ -507,8 +516,8 @@ __global__ void k_candidates(DevCfg dc, int mode, double reach, int ncell, int n
             overflow = true;
         }
     }
-    ncand[cid] = min(k, MAX_CAND);
-    if (overflow) atomicOr(&status[ST_CAND_OVERFLOW], 1);
+    ncand[cid] = overflow ? -1 : k;
+    if (overflow && !graceful) atomicOr(&status[ST_CAND_OVERFLOW], 1);
 }
 
 __global__ void k_thresholds(DevCfg dc, long long n, double reach, const double* __restrict__ sh,
@@ -527,7 +536,7 @@ __global__ void __launch_bounds__(128) k_lists(DevCfg dc, int mode, int ncell, i
                                                const int4* __restrict__ pk,
                                                const unsigned long long* __restrict__ thr,
                                                unsigned int* __restrict__ nbr, int* __restrict__ ncnt,
-                                               int* status)
+                                               int* status, int graceful)
 {
     const int lane = threadIdx.x & 31;
     const int cid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -543,6 +552,11 @@ __global__ void __launch_bounds__(128) k_lists(DevCfg dc, int mode, int ncell, i
     const int K = dc.max_neigh;
     int m = 0;
     const int nc = ncand[cid];
+    if (nc < 0) {  // candidate list overflowed: every list of this cell is incomplete
+        if (own) ncnt[a] = -1;
+        if (!graceful && lane == 0) atomicOr(&status[ST_NEIGH_OVERFLOW], 1);
+        return;
+    }
     for (int j = 0; j < nc; ++j) {
         int2 cb = cand[(long long)cid * MAX_CAND + j];
         if (cb.x < 0 || cb.y < 0 || cb.y > CELL_MAX || cb.x + cb.y > n) continue;
@@ -573,12 +587,12 @@ __global__ void __launch_bounds__(128) k_lists(DevCfg dc, int mode, int ncell, i
         }
     }
     if (own) {
-        ncnt[a] = min(m, K);
-        if (m > K) atomicOr(&status[ST_NEIGH_OVERFLOW], 1);
+        ncnt[a] = m > K ? -1 : m;
+        if (m > K && !graceful) atomicOr(&status[ST_NEIGH_OVERFLOW], 1);
     }
 }
 
-apr_status index_lists(apr_ctx* c, int mode, double reach)
+apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful)
 {
     Workspace& W = c->W;
     int n = (int)c->n;
@@ -587,28 +601,30 @@ apr_status index_lists(apr_ctx* c, int mode, double reach)
         return APR_OK;
     }
     cudaStream_t st = c->stream;
+    int ps = prof_begin(c, APR_PROF_LISTS);
     cudaMemsetAsync(W.cflag, 0, sizeof(unsigned) * (size_t)n, st);
     if (n <= CELL_MAX)
-        k_cells_root<<<1, 1, 0, st>>>(n, W.cflag, W.cmark);
+        APR_LAUNCH(c, k_cells_root, 1, 1, n, W.cflag, W.cmark);
     else
-        k_cells_mark<<<nblocks(n - 1, 256), 256, 0, st>>>(n, W.left, W.right, W.nlo, W.nhi, W.cflag,
+        APR_LAUNCH(c, k_cells_mark, nblocks(n - 1, 256), 256, n, W.left, W.right, W.nlo, W.nhi, W.cflag,
                                                            W.cmark);
     scan_u32(c, W.cflag, W.cscan, n, (unsigned*)&W.status[ST_COUNT_A]);
-    k_cells_compact<<<nblocks(n, 256), 256, 0, st>>>(n, W.cflag, W.cscan, W.cmark, W.nlo,
+    APR_LAUNCH(c, k_cells_compact, nblocks(n, 256), 256, n, W.cflag, W.cscan, W.cmark, W.nlo,
                                                      W.cell_first, W.cell_cnt, W.cell_node);
     cudaMemcpyAsync(c->hbuf, &W.status[ST_COUNT_A], sizeof(int), cudaMemcpyDeviceToHost, st);
     apr_status s = cuda_check(c, cudaStreamSynchronize(st), "cells");
     if (s != APR_OK) return s;
     int ncell = ((int*)c->hbuf)[0];
     c->ncell = ncell;
-    k_candidates<<<nblocks(ncell, 128), 128, 0, st>>>(c->dc, mode, mode == 0 ? reach : 1.0, ncell, n,
+    APR_LAUNCH(c, k_candidates, nblocks(ncell, 128), 128, c->dc, mode, mode == 0 ? reach : 1.0, ncell, n,
                                                        W.cell_node, W.left, W.right, W.pk, W.sh,
                                                        W.nlo, W.nhi, W.nhmax, W.cand,
-                                                       W.ncand, W.status);
-    k_thresholds<<<nblocks(n, 256), 256, 0, st>>>(c->dc, n, mode == 0 ? reach : 1.0, W.sh, W.sthr);
-    k_lists<<<nblocks((long long)ncell * 32, 128), 128, 0, st>>>(
+                                                       W.ncand, W.status, graceful ? 1 : 0);
+    APR_LAUNCH(c, k_thresholds, nblocks(n, 256), 256, c->dc, n, mode == 0 ? reach : 1.0, W.sh, W.sthr);
+    APR_LAUNCH(c, k_lists, nblocks((long long)ncell * 32, 128), 128, 
         c->dc, mode, ncell, n, c->cap, W.cell_first, W.cell_cnt, W.cand, W.ncand, W.pk, W.sthr,
-        W.nbr, W.ncnt, W.status);
+        W.nbr, W.ncnt, W.status, graceful ? 1 : 0);
+    prof_end(c, ps);
     return cuda_check(c, cudaGetLastError(), "lists");
 }
 

@@ -19,7 +19,7 @@ constexpr int MAX_CAND = 128;                // candidate cells per cell
 constexpr int RADIX_TILE = 2048;             // items per radix-sort block (256 x 8)
 constexpr int SCAN_BLOCK = 1024;             // items per scan block (256 x 4)
 constexpr int RED_BLOCKS = 1216;             // 8 x 152 SMs: fixed-shape f64 reductions
-constexpr int DEFAULT_MAX_NEIGH = 256;
+constexpr int DEFAULT_MAX_NEIGH = 512;
 constexpr float DENSITY_REACH = 1.125f;      // density lists cover r < 2 * 1.125 * h
 
 // status words written by kernels (device, read back by the host)
@@ -32,8 +32,18 @@ enum {
     ST_COUNT_B = 5,
     ST_MAXSEG = 6,           // merge tree: largest open segment
     ST_TREE_BAD = 7,         // radix tree walk left its bounds (must never happen)
+    ST_SHRINK = 8,           // density: lists overflowed, h shrunk for a retry
     ST_NSTATUS = 16
 };
+
+constexpr int PROF_POOL = 256;              // event pairs recorded before a drain
+
+// launch a kernel on the context's stream and count it
+#define APR_LAUNCH(c, kern, grid, block, ...)                                  \
+    do {                                                                       \
+        ++(c)->launches;                                                       \
+        kern<<<(grid), (block), 0, (c)->stream>>>(__VA_ARGS__);                \
+    } while (0)
 
 // configuration as the kernels see it (passed by value)
 struct DevCfg {
@@ -54,6 +64,7 @@ struct DevCfg {
     double nr_tol;
     int nr_maxit;
     int max_neigh;
+    int prof;                  // count pair evaluations into Workspace::counters
 };
 
 struct DevRegion {
@@ -117,8 +128,9 @@ struct Workspace {
     // neighbour lists, transposed: nbr[k * cap + sorted slot]
     unsigned int* nbr;
     int* ncnt;
-    // status words
+    // status words and profile counters
     int* status;
+    unsigned long long* counters;
     // split / merge / compaction scratch
     unsigned char* tgt;
     unsigned int* uflag;
@@ -164,6 +176,15 @@ struct apr_ctx {
     bool bound;
     bool have_force;
     int ncell;
+    int last_shrink;
+    // profiling
+    long long launches;
+    bool prof;
+    cudaEvent_t ev[2 * apr::PROF_POOL];
+    int ev_group[apr::PROF_POOL];
+    int ev_used;
+    double prof_ms[APR_NPROF];
+    long long prof_calls[APR_NPROF];
 };
 
 namespace apr {
@@ -210,6 +231,8 @@ __device__ __forceinline__ double level_mass_d(int level)
 apr_status fail(apr_ctx* c, apr_status s, const std::string& msg);
 apr_status cuda_check(apr_ctx* c, cudaError_t e, const char* what);
 DevRegions dev_regions(const apr_ctx* c);
+int prof_begin(apr_ctx* c, int group);        // -1 when profiling is off
+void prof_end(apr_ctx* c, int slot);
 DevSinks dev_sinks(const apr_ctx* c);
 
 // index build (apr_index.cu)
@@ -218,7 +241,9 @@ apr_status scan_u32(apr_ctx* c, const unsigned int* in, unsigned int* out, long 
 apr_status quantise(apr_ctx* c);
 apr_status index_sort(apr_ctx* c);           // quantise, Morton sort, gather, tree, node data
 apr_status index_refresh_h(apr_ctx* c);      // re-gather h and node hmax after a density pass
-apr_status index_lists(apr_ctx* c, int mode, double reach);  // cells, candidates, lists
+// mode 0: gather lists (r < 2 reach h_a), mode 1: symmetric lists (r < 2 max(h_a, h_b)).
+// graceful: an overflowing list is marked (count -1) instead of flagged as an error.
+apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful = false);
 
 // SPH passes (apr_sph.cu)
 apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv);

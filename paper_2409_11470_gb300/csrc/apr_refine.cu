@@ -473,9 +473,9 @@ static apr_status pair_tree(apr_ctx* c, int level, int* m_out, long long* spare,
     Workspace& W = c->W;
     cudaStream_t st = c->stream;
     const long long n = c->n;
-    k_merge_flag<<<nblocks(n, 256), 256, 0, st>>>(n, level, c->p.level, c->p.flags, W.uflag);
+    APR_LAUNCH(c, k_merge_flag, nblocks(n, 256), 256, n, level, c->p.level, c->p.flags, W.uflag);
     scan_u32(c, W.uflag, W.uscan, n, (unsigned*)&W.status[ST_COUNT_A]);
-    k_merge_collect<<<nblocks(n, 256), 256, 0, st>>>(n, W.uflag, W.uscan, W.mset[0]);
+    APR_LAUNCH(c, k_merge_collect, nblocks(n, 256), 256, n, W.uflag, W.uscan, W.mset[0]);
     cudaMemcpyAsync(c->hbuf, &W.status[ST_COUNT_A], sizeof(int), cudaMemcpyDeviceToHost, st);
     apr_status s = cuda_check(c, cudaStreamSynchronize(st), "merge candidates");
     if (s != APR_OK) return s;
@@ -500,26 +500,26 @@ static apr_status pair_tree(apr_ctx* c, int level, int* m_out, long long* spare,
     unsigned int* ak[2] = {W.acc_k, W.acc_k + c->cap};
     unsigned int* ak2[2] = {W.acc_k2, W.acc_k2 + c->cap};
     unsigned long long* akey[2] = {W.acc_key, W.acc_key + 3 * c->cap};
-    k_seg_init<<<nblocks(m, 256), 256, 0, st>>>(m, W.seg_lo[0], W.seg_hi[0], alo[0], ahi[0], asum[0],
+    APR_LAUNCH(c, k_seg_init, nblocks(m, 256), 256, m, W.seg_lo[0], W.seg_hi[0], alo[0], ahi[0], asum[0],
                                                ak[0], ak2[0], akey[0], key2[0]);
     int cur = 0;
     const int nb = nblocks(m, 256);
     for (int round = 0; round < 4 * m + 64; ++round) {
-        k_tree_bbox<<<nb, 256, 0, st>>>(m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], W.xi,
+        APR_LAUNCH(c, k_tree_bbox, nb, 256, m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], W.xi,
                                         alo[cur], ahi[cur]);
-        k_tree_sum<<<nb, 256, 0, st>>>(m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], W.xi, alo[cur],
+        APR_LAUNCH(c, k_tree_sum, nb, 256, m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], W.xi, alo[cur],
                                        ahi[cur], asum[cur]);
-        k_tree_count<<<nb, 256, 0, st>>>(m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], W.xi,
+        APR_LAUNCH(c, k_tree_count, nb, 256, m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], W.xi,
                                          alo[cur], ahi[cur], asum[cur], ak[cur], ak2[cur]);
-        k_tree_key<<<nb, 256, 0, st>>>(m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], W.xi, alo[cur],
+        APR_LAUNCH(c, k_tree_key, nb, 256, m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], W.xi, alo[cur],
                                        ahi[cur], asum[cur], ak[cur], ak2[cur], akey[cur], key2[cur]);
-        k_tree_flag<<<nb, 256, 0, st>>>(m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], W.xi,
+        APR_LAUNCH(c, k_tree_flag, nb, 256, m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], W.xi,
                                         alo[cur], ahi[cur], asum[cur], ak[cur], ak2[cur], akey[cur],
                                         key2[cur], W.lflag);
         scan_u32(c, W.lflag, W.uscan, m, nullptr);
         cudaMemsetAsync(&W.status[ST_MAXSEG], 0, sizeof(int), st);
         const int nx = cur ^ 1;
-        k_tree_scatter<<<nb, 256, 0, st>>>(m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], alo[cur],
+        APR_LAUNCH(c, k_tree_scatter, nb, 256, m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], alo[cur],
                                            ahi[cur], asum[cur], ak[cur], ak2[cur], W.lflag, W.uscan,
                                            W.mset[nx], W.seg_lo[nx], W.seg_hi[nx], alo[nx], ahi[nx],
                                            asum[nx], ak[nx], ak2[nx], akey[nx], key2[nx],
@@ -590,7 +590,7 @@ apr_status merge_pairs_debug(apr_ctx* c, int level, long long* pairs, long long 
     if (m / 2 > cap) return fail(c, APR_ERR_ARG, "merge_pairs: cap too small");
     if (m == 0) return APR_OK;
     long long* dev = (long long*)c->W.tmp8;
-    k_pairs_out<<<nblocks(m, 256), 256, 0, c->stream>>>(m / 2, c->W.mset[cur], dev);
+    APR_LAUNCH(c, k_pairs_out, nblocks(m, 256), 256, m / 2, c->W.mset[cur], dev);
     s = cuda_check(c, cudaMemcpyAsync(pairs, dev, sizeof(long long) * m, cudaMemcpyDeviceToHost,
                                       c->stream), "pairs out");
     if (s != APR_OK) return s;
@@ -619,7 +619,7 @@ template <typename T>
 static void compact_one(apr_ctx* c, T* field, long long n, long long nlive)
 {
     T* tmp = (T*)c->W.tmp8;
-    k_compact_field<T><<<nblocks(n, 256), 256, 0, c->stream>>>(n, c->p.flags, c->W.uscan, field, tmp);
+    APR_LAUNCH(c, k_compact_field<T>, nblocks(n, 256), 256, n, c->p.flags, c->W.uscan, field, tmp);
     cudaMemcpyAsync(field, tmp, sizeof(T) * (size_t)nlive, cudaMemcpyDeviceToDevice, c->stream);
 }
 
@@ -627,7 +627,7 @@ apr_status compact(apr_ctx* c, long long* removed)
 {
     const long long n = c->n;
     Workspace& W = c->W;
-    k_live_flag<<<nblocks(n, 256), 256, 0, c->stream>>>(n, c->p.flags, W.uflag);
+    APR_LAUNCH(c, k_live_flag, nblocks(n, 256), 256, n, c->p.flags, W.uflag);
     scan_u32(c, W.uflag, W.uscan, n, (unsigned*)&W.status[ST_COUNT_B]);
     cudaMemcpyAsync(c->hbuf, &W.status[ST_COUNT_B], sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     apr_status s = cuda_check(c, cudaStreamSynchronize(c->stream), "compaction count");
@@ -656,22 +656,32 @@ __global__ void k_clear_changed(long long n, unsigned char* flags)
 
 apr_status clear_changed(apr_ctx* c)
 {
-    if (c->n > 0) k_clear_changed<<<nblocks(c->n, 256), 256, 0, c->stream>>>(c->n, c->p.flags);
+    if (c->n > 0) APR_LAUNCH(c, k_clear_changed, nblocks(c->n, 256), 256, c->n, c->p.flags);
     return cuda_check(c, cudaGetLastError(), "clear changed");
 }
 
+static apr_status split_merge_body(apr_ctx* c, apr_counts* cnt);
+
 apr_status split_merge_pass(apr_ctx* c, apr_counts* cnt)
+{
+    const int ps = prof_begin(c, APR_PROF_REFINE);
+    apr_status s = split_merge_body(c, cnt);
+    prof_end(c, ps);
+    return s;
+}
+
+static apr_status split_merge_body(apr_ctx* c, apr_counts* cnt)
 {
     Workspace& W = c->W;
     cudaStream_t st = c->stream;
     const DevRegions rg = dev_regions(c);
     memset(cnt, 0, sizeof(*cnt));
     apr_status s;
-    if (c->n > 0) k_clear_changed<<<nblocks(c->n, 256), 256, 0, st>>>(c->n, c->p.flags);
+    if (c->n > 0) APR_LAUNCH(c, k_clear_changed, nblocks(c->n, 256), 256, c->n, c->p.flags);
     for (int l = 0; l < c->cfg.lmax; ++l) {
         const long long n = c->n;
         if (n == 0) break;
-        k_split_flag<<<nblocks(n, 256), 256, 0, st>>>(c->dc, rg, n, l, c->p.x, c->p.y, c->p.z,
+        APR_LAUNCH(c, k_split_flag, nblocks(n, 256), 256, c->dc, rg, n, l, c->p.x, c->p.y, c->p.z,
                                                       c->p.level, c->p.flags, W.uflag);
         scan_u32(c, W.uflag, W.uscan, n, (unsigned*)&W.status[ST_COUNT_A]);
         cudaMemcpyAsync(c->hbuf, &W.status[ST_COUNT_A], sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -681,7 +691,7 @@ apr_status split_merge_pass(apr_ctx* c, apr_counts* cnt)
         if (n + ns > c->cap)
             return fail(c, APR_ERR_CAPACITY, "split would exceed the bound capacity");
         if (ns > 0) {
-            k_split_apply<<<nblocks(n, 256), 256, 0, st>>>(c->dc, rg, n, l, c->step, c->next_id,
+            APR_LAUNCH(c, k_split_apply, nblocks(n, 256), 256, c->dc, rg, n, l, c->step, c->next_id,
                                                            W.uflag, W.uscan, c->p);
             c->n = n + ns;
             c->next_id += ns;
@@ -702,7 +712,7 @@ apr_status split_merge_pass(apr_ctx* c, apr_counts* cnt)
         cnt->n_spare[l] = spare >= 0 ? 1 : 0;
         if (m < 2) continue;
         cudaMemsetAsync(&W.status[ST_COUNT_B], 0, sizeof(int), st);
-        k_merge_apply<<<nblocks(m / 2, 256), 256, 0, st>>>(c->dc, rg, m / 2, l, W.mset[cur], c->p,
+        APR_LAUNCH(c, k_merge_apply, nblocks(m / 2, 256), 256, c->dc, rg, m / 2, l, W.mset[cur], c->p,
                                                          &W.status[ST_COUNT_B]);
         cudaMemcpyAsync(c->hbuf, &W.status[ST_COUNT_B], sizeof(int), cudaMemcpyDeviceToHost, st);
         s = cuda_check(c, cudaStreamSynchronize(st), "merge");
@@ -758,7 +768,7 @@ __global__ void k_reduce_final(int nblk, int nv, const double* __restrict__ part
 
 static apr_status reduce_readback(apr_ctx* c, int nv, int op_min, double* host)
 {
-    k_reduce_final<<<1, 32, 0, c->stream>>>(RED_BLOCKS, nv, c->W.red, c->W.redout, op_min);
+    APR_LAUNCH(c, k_reduce_final, 1, 32, RED_BLOCKS, nv, c->W.red, c->W.redout, op_min);
     cudaMemcpyAsync(c->hbuf, c->W.redout, sizeof(double) * nv, cudaMemcpyDeviceToHost, c->stream);
     apr_status s = cuda_check(c, cudaStreamSynchronize(c->stream), "reduce");
     if (s != APR_OK) return s;
@@ -790,7 +800,7 @@ __global__ void __launch_bounds__(256) k_stats(DevCfg dc, long long n, apr_parti
 
 apr_status compute_stats(apr_ctx* c, apr_stats* st)
 {
-    k_stats<<<RED_BLOCKS, 256, 0, c->stream>>>(c->dc, c->n, c->p, c->W.red);
+    APR_LAUNCH(c, k_stats, RED_BLOCKS, 256, c->dc, c->n, c->p, c->W.red);
     double r[9];
     apr_status s = reduce_readback(c, 9, 0, r);
     if (s != APR_OK) return s;
@@ -839,7 +849,7 @@ __global__ void __launch_bounds__(256) k_timestep(DevCfg dc, long long n, apr_pa
 
 apr_status compute_timestep(apr_ctx* c, double* dt)
 {
-    k_timestep<<<RED_BLOCKS, 256, 0, c->stream>>>(c->dc, c->n, c->p, c->W.red);
+    APR_LAUNCH(c, k_timestep, RED_BLOCKS, 256, c->dc, c->n, c->p, c->W.red);
     return reduce_readback(c, 1, 1, dt);
 }
 
@@ -877,7 +887,7 @@ __global__ void __launch_bounds__(256) k_sink_gravity(DevCfg dc, DevSinks sk, lo
 apr_status sink_gravity(apr_ctx* c)
 {
     if (c->nsink == 0) return APR_OK;
-    k_sink_gravity<<<RED_BLOCKS, 256, 0, c->stream>>>(c->dc, dev_sinks(c), c->n, c->p, c->W.red);
+    APR_LAUNCH(c, k_sink_gravity, RED_BLOCKS, 256, c->dc, dev_sinks(c), c->n, c->p, c->W.red);
     double r[3 * APR_MAXSINK];
     apr_status s = reduce_readback(c, 3 * c->nsink, 0, r);
     if (s != APR_OK) return s;
@@ -938,7 +948,7 @@ apr_status accrete(apr_ctx* c, long long* naccreted)
     if (c->nsink == 0 || c->n == 0) return APR_OK;
     if (c->nsink > 4) return fail(c, APR_ERR_ARG, "accretion supports at most 4 sinks");
     cudaMemsetAsync(&c->W.status[ST_COUNT_B], 0, sizeof(int), c->stream);
-    k_accrete<<<RED_BLOCKS, 256, 0, c->stream>>>(c->dc, dev_sinks(c), c->n, c->p, c->W.red,
+    APR_LAUNCH(c, k_accrete, RED_BLOCKS, 256, c->dc, dev_sinks(c), c->n, c->p, c->W.red,
                                                  &c->W.status[ST_COUNT_B]);
     double r[28];
     apr_status s = reduce_readback(c, 7 * c->nsink, 0, r);
@@ -985,7 +995,7 @@ __global__ void k_drift(DevCfg dc, long long n, double dt, apr_particles p)
 
 apr_status kick(apr_ctx* c, double hdt)
 {
-    if (c->n > 0) k_kick<<<nblocks(c->n, 256), 256, 0, c->stream>>>(c->dc, c->n, hdt, c->p);
+    if (c->n > 0) APR_LAUNCH(c, k_kick, nblocks(c->n, 256), 256, c->dc, c->n, hdt, c->p);
     for (int j = 0; j < c->nsink; ++j)
         for (int d = 0; d < 3; ++d) c->sinks[j].v[d] += hdt * c->sinks[j].a[d];
     return cuda_check(c, cudaGetLastError(), "kick");
@@ -993,7 +1003,7 @@ apr_status kick(apr_ctx* c, double hdt)
 
 apr_status drift(apr_ctx* c, double dt)
 {
-    if (c->n > 0) k_drift<<<nblocks(c->n, 256), 256, 0, c->stream>>>(c->dc, c->n, dt, c->p);
+    if (c->n > 0) APR_LAUNCH(c, k_drift, nblocks(c->n, 256), 256, c->dc, c->n, dt, c->p);
     for (int j = 0; j < c->nsink; ++j)
         for (int d = 0; d < 3; ++d) c->sinks[j].x[d] += dt * c->sinks[j].v[d];
     return cuda_check(c, cudaGetLastError(), "drift");

@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(128)
               const double* __restrict__ y, const double* __restrict__ u,
               double* __restrict__ h_out, double* __restrict__ rho_out,
               double* __restrict__ omega_out, double* __restrict__ dnn_out,
-              double* __restrict__ pres_out, double* __restrict__ cs_out, int* status)
+              double* __restrict__ pres_out, double* __restrict__ cs_out, int* status,
+              unsigned long long* counters)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -119,10 +120,19 @@ __global__ void __launch_bounds__(128)
     const R mua = Num<R>::mass(pa.w);
     const R target = R(3.14159265358979323846) * mua * R(dc.hfact * dc.hfact * dc.hfact);
     const int m = ncnt[a];
+    if (m < 0) {
+        // the list at this h overflowed (e.g. an initial h far too large at a
+        // density jump): shrink h and let the host rebuild the lists
+        h_out[perm[a]] = 0.8 * hlist;
+        atomicAdd(&status[ST_UNCOVERED], 1);
+        atomicAdd(&status[ST_SHRINK], 1);
+        return;
+    }
     R h = (R)hlist;
     R lo = R(0), hi = R(0);  // bracket of the root; hi == 0: none yet
     R D = R(0);              // sum mu_b (3 f + q f') at the last evaluated h
     bool conv = false, uncovered = false;
+    unsigned long long npair = 0;
     for (int it = 0; it < dc.nr_maxit; ++it) {
         const R hinv = R(1) / h;
         const R r2max = R(4) * h * h;
@@ -140,6 +150,7 @@ __global__ void __launch_bounds__(128)
             const R mub = Num<R>::mass(pb.w);
             S.add(mub * f);
             T.add(mub * q * df);
+            ++npair;
         }
         const R g = (S.s + mua) - target;           // pi h^3 (rho_sum - rho_h) / m0
         const R dg = -(T.s) * hinv;                   // dg/dh >= 0
@@ -149,21 +160,27 @@ __global__ void __launch_bounds__(128)
         R hn;
         if (dg > R(0)) hn = h - g / dg;
         else hn = h * R(1.25992105);
-        if (!(hn > lo) || (hi > R(0) && !(hn < hi)))
+        // a Newton step that leaves the bracket is replaced by bisection (or growth)
+        if (hn < lo || (hi > R(0) && hn > hi) || !(hn == hn))
             hn = hi > R(0) ? R(0.5) * (lo + hi) : h * R(1.25992105);
         if (hn > R(2) * h) hn = R(2) * h;
         if (hn < R(0.5) * h) hn = R(0.5) * h;
         const bool done = fabs((double)(hn - h)) <= dc.nr_tol * (double)h;
-        h = hn;
-        if ((double)h > reach * hlist) {
+        if ((double)hn > reach * hlist) {
+            // the root lies beyond this list's reach: stop at the reach; the host
+            // rebuilds the lists there and the iteration continues (growth is
+            // bounded per attempt, so lists stay short)
+            h = (R)(reach * hlist);
             uncovered = true;
             break;
         }
+        h = hn;
         if (done) {
             conv = true;
             break;
         }
     }
+    if (dc.prof) atomicAdd(&counters[APR_PROF_DENSITY], npair);
     const unsigned i = perm[a];
     const double hd = (double)h;
     h_out[i] = hd;
@@ -209,24 +226,29 @@ apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv)
     const long long n = c->n;
     cudaStream_t st = c->stream;
     cudaMemsetAsync(&W.status[ST_UNCOVERED], 0, 2 * sizeof(int), st);
+    cudaMemsetAsync(&W.status[ST_SHRINK], 0, sizeof(int), st);
+    int ps = prof_begin(c, APR_PROF_DENSITY);
     if (n > 0) {
         const double reach = DENSITY_REACH;
         if (c->cfg.precision == APR_PREC_FP64)
-            k_density<double><<<nblocks(n, 128), 128, 0, st>>>(
+            APR_LAUNCH(c, k_density<double>, nblocks(n, 128), 128, 
                 c->dc, n, c->cap, reach, W.pk, W.sh, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
                 c->p.x, c->p.y, c->p.u, c->p.h, c->p.rho, c->p.omega, c->p.dnn, c->p.pres, c->p.cs,
-                W.status);
+                W.status, W.counters);
         else
-            k_density<float><<<nblocks(n, 128), 128, 0, st>>>(
+            APR_LAUNCH(c, k_density<float>, nblocks(n, 128), 128, 
                 c->dc, n, c->cap, reach, W.pk, W.sh, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
                 c->p.x, c->p.y, c->p.u, c->p.h, c->p.rho, c->p.omega, c->p.dnn, c->p.pres, c->p.cs,
-                W.status);
+                W.status, W.counters);
     }
-    cudaMemcpyAsync(c->hbuf, &W.status[ST_UNCOVERED], 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    prof_end(c, ps);
+    cudaMemcpyAsync(c->hbuf, &W.status[ST_UNCOVERED], (ST_SHRINK - ST_UNCOVERED + 1) * sizeof(int),
+                    cudaMemcpyDeviceToHost, st);
     apr_status s = cuda_check(c, cudaStreamSynchronize(st), "density");
     if (s != APR_OK) return s;
     *uncovered = ((int*)c->hbuf)[0];
     *noconv = ((int*)c->hbuf)[1];
+    c->last_shrink = ((int*)c->hbuf)[ST_SHRINK - ST_UNCOVERED];
     return APR_OK;
 }
 
@@ -283,11 +305,11 @@ apr_status gather_force_data(apr_ctx* c)
     const long long n = c->n;
     if (n <= 0) return APR_OK;
     if (c->cfg.precision == APR_PREC_FP64)
-        k_gather_force_f64<<<nblocks(n, 256), 256, 0, c->stream>>>(
+        APR_LAUNCH(c, k_gather_force_f64, nblocks(n, 256), 256, 
             n, W.perm, W.pk, c->p.h, c->p.rho, c->p.omega, c->p.pres, c->p.cs, c->p.vx, c->p.vy,
             c->p.vz, c->p.u, W.dA, W.dV, W.dB);
     else
-        k_gather_force_f32<<<nblocks(n, 256), 256, 0, c->stream>>>(
+        APR_LAUNCH(c, k_gather_force_f32, nblocks(n, 256), 256, 
             n, W.perm, W.pk, c->p.h, c->p.rho, c->p.omega, c->p.pres, c->p.cs, c->p.vx, c->p.vy,
             c->p.vz, c->p.u, W.fA, W.fV, W.fB);
     return cuda_check(c, cudaGetLastError(), "gather force data");
@@ -322,7 +344,8 @@ __global__ void __launch_bounds__(128)
             const double* __restrict__ sx, const double* __restrict__ sy,
             const double* __restrict__ sz, const unsigned int* __restrict__ perm,
             double* __restrict__ ax_out, double* __restrict__ ay_out, double* __restrict__ az_out,
-            double* __restrict__ dudt_out, double* __restrict__ vsig_out)
+            double* __restrict__ dudt_out, double* __restrict__ vsig_out,
+            unsigned long long* counters)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -337,6 +360,7 @@ __global__ void __launch_bounds__(128)
     const bool cond = adiabatic && dc.alpha_u > 0.0;
     Acc<R> fx, fy, fz, du;
     R vsig = cs_a;
+    unsigned long long npair = 0;
     const int m = ncnt[a];
     for (int k = 0; k < m; ++k) {
         const int b = (int)nbr[(long long)k * cap + a];
@@ -350,6 +374,7 @@ __global__ void __launch_bounds__(128)
         const R hinv_b = Ab4.x;
         const R qa = r * hinv_a, qb = r * hinv_b;
         if (!(qa < R(2) || qb < R(2))) continue;
+        ++npair;
         R fa, dfa, fb, dfb;
         m4<R>(qa, fa, dfa);
         m4<R>(qb, fb, dfb);
@@ -380,6 +405,7 @@ __global__ void __launch_bounds__(128)
         const R vs = cs_a + beta * (vr < R(0) ? -vr : R(0));
         vsig = vs > vsig ? vs : vsig;
     }
+    if (dc.prof) atomicAdd(&counters[APR_PROF_FORCE], npair);
     const double scale = dc.m0 / 3.14159265358979323846;
     const unsigned i = perm[a];
     ax_out[i] = scale * ((double)fx.s - (double)fx.c);
@@ -394,14 +420,16 @@ apr_status force_pass(apr_ctx* c)
     Workspace& W = c->W;
     const long long n = c->n;
     if (n <= 0) return APR_OK;
+    const int ps = prof_begin(c, APR_PROF_FORCE);
     if (c->cfg.precision == APR_PREC_FP64)
-        k_force<double><<<nblocks(n, 128), 128, 0, c->stream>>>(
+        APR_LAUNCH(c, k_force<double>, nblocks(n, 128), 128, 
             c->dc, n, c->cap, W.pk, W.dA, W.dV, W.dB, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
-            c->p.ax, c->p.ay, c->p.az, c->p.dudt, c->p.vsig);
+            c->p.ax, c->p.ay, c->p.az, c->p.dudt, c->p.vsig, W.counters);
     else
-        k_force<float><<<nblocks(n, 128), 128, 0, c->stream>>>(
+        APR_LAUNCH(c, k_force<float>, nblocks(n, 128), 128, 
             c->dc, n, c->cap, W.pk, W.fA, W.fV, W.fB, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
-            c->p.ax, c->p.ay, c->p.az, c->p.dudt, c->p.vsig);
+            c->p.ax, c->p.ay, c->p.az, c->p.dudt, c->p.vsig, W.counters);
+    prof_end(c, ps);
     return cuda_check(c, cudaGetLastError(), "force");
 }
 

@@ -28,7 +28,7 @@ def _variable_h(w, seed=2):
 def test_neighbour_lists_bit_exact(make, mode):
     w = make()
     o = oracle.Oracle(w)
-    g = sim(w)
+    g = sim(w, max_neigh=1024)
     off_o, idx_o = o.neighbours(mode)
     off_g, idx_g = g.neighbour_lists(mode)
     assert np.array_equal(off_o, off_g)
@@ -62,7 +62,7 @@ def _density_both(w, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-@pytest.mark.parametrize("make", [apr_synth.c1_lattice, lambda: apr_synth.sod(10, slab=()),
+@pytest.mark.parametrize("make", [apr_synth.c1_lattice, lambda: apr_synth.sod(16, slab=()),
                                   lambda: apr_synth.disc_planet(30000)])
 def test_density_matches_oracle(make, precision):
     w = make()
@@ -81,7 +81,7 @@ def test_density_matches_oracle(make, precision):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("make", [lambda: with_velocities(apr_synth.c1_lattice(), 0.3),
-                                  lambda: with_velocities(apr_synth.sod(10, slab=()), 0.2),
+                                  lambda: with_velocities(apr_synth.sod(16, slab=()), 0.2),
                                   lambda: apr_synth.disc_planet(30000)])
 def test_force_matches_oracle(make, precision):
     w = make()
@@ -119,3 +119,16 @@ def test_neighbour_capacity_overflow_reported():
     with pytest.raises(AprError) as e:
         g.density()
     assert e.value.status == 4
+    with pytest.raises(AprError) as e:
+        g.neighbour_lists(1, cap=10 ** 6)
+    assert e.value.status == 4
+
+
+def test_density_recovers_from_a_far_too_large_initial_h():
+    w = apr_synth.c1_lattice()
+    w["p"]["h"] = w["p"]["h"] * 3.0  # lists at this h overflow: h must shrink and retry
+    o = oracle.Oracle(w)
+    o.density()
+    g = sim(w, max_neigh=256)
+    g.density()
+    assert rel(g.get("rho"), o["rho"]).max() < 1e-5

@@ -40,7 +40,7 @@ def _same(o, g):
 def test_split_pass_bit_exact():
     w = with_velocities(apr_synth.c1_lattice(), 0.5)
     o, g = _both(w, 3 * 4096)
-    co = o.split_merge(0)
+    co = o.split_merge()
     cg = g.split_merge()
     assert list(cg.n_split) == list(co.n_split) and co.n_split[0] > 200
     _same(o, g)
@@ -49,8 +49,8 @@ def test_split_pass_bit_exact():
 def test_two_level_split_then_merge_bit_exact():
     w = with_velocities(apr_synth.lattice_box(14, 0.1, sphere_R=(0.4, 0.3), seed=9), 0.2)
     o, g = _both(w, 6 * 14 ** 3)
-    for step in range(3):
-        co = o.split_merge(step)
+    for _ in range(3):
+        co = o.split_merge()
         cg = g.split_merge()
         assert list(cg.n_split) == list(co.n_split)
         assert list(cg.n_merge) == list(co.n_merge)
