@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nL", type=int, default=28, help="shock-tube resolution (28 = full size)")
+    ap.add_argument("--ncu-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu "
+                         "--profile-from-start off)")
     return ap.parse_args()
 
 
@@ -170,9 +173,13 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(bus)
+    if args.ncu_range:
+        torch.cuda.cudart().cudaProfilerStart()
     t_wall = time.perf_counter()
     ms, psteps = timed_steps(sim, torch, args.steps, flush)
     torch.cuda.synchronize()
+    if args.ncu_range:
+        torch.cuda.cudart().cudaProfilerStop()
     t_wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
     prof = sim.profile()
