@@ -18,7 +18,7 @@ def test_workspace_size_grows_with_capacity_and_lists():
     a = B.workspace_size(cfg, 1000)
     b = B.workspace_size(cfg, 2000)
     assert 0 < a < b and a % 256 == 0
-    cfg2 = B.make_config(apr_synth.c1_lattice()["cfg"], max_neigh=512)
+    cfg2 = B.make_config(apr_synth.c1_lattice()["cfg"], max_neigh=1024)
     assert B.workspace_size(cfg2, 1000) > a
     cfg64 = B.make_config(apr_synth.c1_lattice()["cfg"], precision="fp64")
     assert B.workspace_size(cfg64, 1000) > a
