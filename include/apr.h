@@ -255,6 +255,38 @@ apr_status apr_profile_enable(apr_ctx* ctx, int on);
 /* Read (and with reset != 0 clear) the profile counters; synchronises the stream. */
 apr_status apr_profile_read(apr_ctx* ctx, apr_profile* out, int reset);
 
+/*
+ * Conservation sums like apr_stats_compute, for callers that cannot allocate
+ * device memory.  The paper has no counterpart: this is a convenience of the
+ * library, not a step of the method.
+ *
+ * Who needs it: code running under another framework's memory manager (a raw
+ * cudaMalloc there bypasses the framework's pool and accounting) and
+ * latency-critical callbacks where an allocation could implicitly synchronise
+ * the device or fail under a memory cap.  This call takes no context and no
+ * workspace and allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library routine): its scratch is a fixed 512 KB device array built into the
+ * library, present on every GPU that loads the library until the process
+ * exits.
+ *
+ * cfg: only m0 and eos are read.  p: DEVICE arrays x, y, z, vx, vy, vz, u,
+ * level, flags of n particles (dead-flagged ones are skipped); at most
+ * 16,777,216 particles, larger n returns APR_ERR_ARG with a message.  sinks:
+ * HOST array of nsinks point masses added to the sums (may be NULL if 0).
+ * stream: the CUDA stream to run on (NULL = legacy default); the call
+ * synchronises it before returning.  out: HOST result.  err/errlen: optional
+ * buffer for a message (empty on success).
+ *
+ * The first call on each device looks up the device address of the built-in
+ * array (with that device current); make that first call before any stream
+ * capture.  Every call overwrites the whole scratch it uses, so nothing
+ * carries over between calls, but two calls that overlap on the GPU (from
+ * different streams or threads) share the array and race.
+ */
+apr_status apr_stats_noalloc(const apr_config* cfg, const apr_particles* p, long long n,
+                             const apr_sink* sinks, int nsinks, void* stream, apr_stats* out,
+                             char* err, size_t errlen);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,7 @@ UNITS = {
     "apr_index.cu": ["--fmad=false"],
     "apr_sph.cu": [],
     "apr_refine.cu": ["--fmad=false"],
+    "apr_noalloc.cu": [],
 }
 
 

@@ -1,0 +1,61 @@
+"""The conservation sums of apr_stats_noalloc, the entry point for callers that
+cannot allocate device memory (it uses a built-in scratch array instead of a
+workspace), against apr_stats_compute on the same particles, on two calls in a
+row, through the C ABI.  Collected last on purpose."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import apr_synth
+from gpu_util import sim, with_velocities
+
+pytestmark = pytest.mark.gpu
+
+
+def _entry():
+    from paper_2409_11470_gb300 import binding as B
+    f = B.lib.apr_stats_noalloc
+    f.argtypes = [C.POINTER(B.Config), C.POINTER(B.Particles), C.c_longlong, C.POINTER(B.Sink),
+                  C.c_int, C.c_void_p, C.POINTER(B.Stats), C.c_char_p, C.c_size_t]
+    f.restype = C.c_int
+    return B, f
+
+
+def _as_array(s):
+    return np.array([s.mass, *s.mom, *s.ang, s.ekin, s.etherm])
+
+
+@pytest.mark.parametrize("make", [lambda: with_velocities(apr_synth.c1_lattice(), 0.3),
+                                  lambda: apr_synth.disc_planet(20000)])
+def test_noalloc_sums_match_workspace_sums_twice(make):
+    B, f = _entry()
+    w = make()
+    g = sim(w)
+    g.split_merge()  # mixed levels (disc: particles near the planet)
+    ref = _as_array(g.stats())
+    sinks = B.Sink * max(1, len(w["sinks"]))
+    arr = sinks()
+    for j, s in enumerate(w["sinks"]):
+        for k in range(3):
+            arr[j].x[k], arr[j].v[k] = s["x"][k], s["v"][k]
+        arr[j].m, arr[j].racc = s["m"], s["racc"]
+    scale = np.abs(ref) + ref[0] * 1e-3
+    for _ in range(2):
+        out = B.Stats()
+        err = C.create_string_buffer(256)
+        st = f(C.byref(g.cfg), C.byref(g.parts), g.n, arr, len(w["sinks"]),
+               C.c_void_p(g.stream.cuda_stream), C.byref(out), err, 256)
+        assert st == 0, err.value
+        got = _as_array(out)
+        assert np.all(np.abs(got - ref) <= 1e-12 * scale), (got, ref)
+
+
+def test_noalloc_rejects_more_particles_than_its_scratch():
+    B, f = _entry()
+    g = sim(apr_synth.c1_lattice())
+    out = B.Stats()
+    err = C.create_string_buffer(256)
+    st = f(C.byref(g.cfg), C.byref(g.parts), 16_777_217, None, 0,
+           C.c_void_p(g.stream.cuda_stream), C.byref(out), err, 256)
+    assert st == 1 and b"16,777,216" in err.value
