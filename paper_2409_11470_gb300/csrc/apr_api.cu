@@ -132,6 +132,7 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.nlo = (int4*)take(16 * C);
     w.nhi = (int4*)take(16 * C);
     w.nhmax = (double*)take(8 * C);
+    w.nthr = (unsigned long long*)take(8 * C);
     w.cflag = (unsigned int*)take(4 * C);
     w.cscan = (unsigned int*)take(4 * C);
     w.cell_first = (int*)take(4 * C);
@@ -263,7 +264,9 @@ static apr_status run_density(apr_ctx* c, long long* noconv_out)
     long long unc = 0, noconv = 0, shrinks = 0;
     for (int attempt = 0; attempt < 64; ++attempt) {
         cudaMemsetAsync(c->W.status, 0, 2 * sizeof(int), c->stream);
-        s = index_lists(c, 0, DENSITY_REACH, true);
+        // symmetric lists at the reach: after the last attempt (no h beyond its reach)
+        // they also hold every force pair, r < 2 max(h_a, h_b)
+        s = index_lists(c, 1, DENSITY_REACH, true);
         if (s != APR_OK) return s;
         s = check_overflow(c);
         if (s != APR_OK) return s;
@@ -283,13 +286,18 @@ static apr_status run_density(apr_ctx* c, long long* noconv_out)
     return APR_OK;
 }
 
-static apr_status run_force(apr_ctx* c)
+// reuse_density_lists: the lists of a density pass that has just converged on the
+// same positions (every h within the lists' reach) contain every force pair
+static apr_status run_force(apr_ctx* c, bool reuse_density_lists)
 {
-    apr_status s = index_refresh_h(c);
-    if (s != APR_OK) return s;
-    cudaMemsetAsync(c->W.status, 0, 2 * sizeof(int), c->stream);
-    s = index_lists(c, 1, 1.0);
-    if (s != APR_OK) return s;
+    apr_status s;
+    if (!reuse_density_lists) {
+        s = index_sort(c);
+        if (s != APR_OK) return s;
+        cudaMemsetAsync(c->W.status, 0, 2 * sizeof(int), c->stream);
+        s = index_lists(c, 1, 1.0);
+        if (s != APR_OK) return s;
+    }
     int ps = prof_begin(c, APR_PROF_OTHER);
     s = gather_force_data(c);
     prof_end(c, ps);
@@ -343,6 +351,7 @@ apr_status apr_create(apr_ctx** out, const apr_config* cfg, void* stream)
     c->nreg = c->nsink = 0;
     c->ncell = 0;
     c->last_shrink = 0;
+    c->tree_smem_set = false;
     c->launches = 0;
     c->prof = false;
     c->ev_used = 0;
@@ -455,7 +464,7 @@ apr_status apr_sph_force(apr_ctx* c)
 {
     if (!c) return APR_ERR_ARG;
     if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
-    return run_force(c);
+    return run_force(c, false);
 }
 
 apr_status apr_split_merge(apr_ctx* c, long long* n_out, apr_counts* counts)
@@ -492,7 +501,7 @@ apr_status apr_init(apr_ctx* c, int* passes)
     if (s != APR_OK) return s;
     s = run_density(c, nullptr);
     if (s != APR_OK) return s;
-    s = run_force(c);
+    s = run_force(c, true);
     if (passes) *passes = np;
     return s;
 }
@@ -538,7 +547,7 @@ apr_status apr_step(apr_ctx* c, double dt, double* dt_used, apr_stats* stats,
     cnt.n_accreted = na;
     s = run_density(c, nullptr);
     if (s != APR_OK) return s;
-    s = run_force(c);
+    s = run_force(c, true);
     if (s != APR_OK) return s;
     ps = prof_begin(c, APR_PROF_OTHER);
     s = kick(c, hdt);

@@ -210,6 +210,28 @@ __global__ void k_radix_scatter(const unsigned long long* __restrict__ kin,
     }
 }
 
+__global__ void k_bin_starts(const unsigned int* __restrict__ hoff, int ntiles, int nbins,
+                             int* __restrict__ out)
+{
+    int d = threadIdx.x;
+    if (d < nbins) out[d] = (int)hoff[(long long)d * ntiles];
+}
+
+apr_status radix_pass8(apr_ctx* c, const unsigned long long* kin, const unsigned int* vin,
+                       unsigned long long* kout, unsigned int* vout, long long n, int shift,
+                       int* bin_starts, int nbins)
+{
+    Workspace& W = c->W;
+    const int ntiles = nblocks(n, RADIX_TILE);
+    APR_LAUNCH(c, k_radix_hist, ntiles, 256, kin, n, shift, W.hist, ntiles);
+    scan_u32(c, W.hist, W.hist + (size_t)256 * ntiles, (long long)256 * ntiles, nullptr);
+    APR_LAUNCH(c, k_radix_scatter, ntiles, 256, kin, vin, kout, vout, n, shift,
+               W.hist + (size_t)256 * ntiles, ntiles);
+    if (bin_starts)
+        APR_LAUNCH(c, k_bin_starts, 1, 32, W.hist + (size_t)256 * ntiles, ntiles, nbins, bin_starts);
+    return cuda_check(c, cudaGetLastError(), "radix pass");
+}
+
 static apr_status radix_sort(apr_ctx* c, long long n)
 {
     Workspace& W = c->W;
@@ -481,19 +503,67 @@ __device__ __forceinline__ unsigned long long box_dist2(const DevCfg& dc, const 
     return d2;
 }
 
-// candidate cells: traverse the tree from the root, keep cells within reach
-__global__ void k_candidates(DevCfg dc, int mode, double reach, int ncell, int n,
+// node thresholds thr(reach * max h of the subtree); thr is monotone in h, so the
+// symmetric test max(thr_a, thr_b) needs no float64 work during the traversal
+__global__ void k_node_thr(DevCfg dc, int n, double reach, const double* __restrict__ nhmax,
+                           unsigned long long* __restrict__ nthr)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n - 1) nthr[i] = neighbour_threshold(reach * nhmax[i], dc.delta);
+}
+
+struct NodeBox {
+    int lo[3], hi[3], count, first;
+    unsigned long long thr;
+};
+
+// read-only view of a node for the traversal (the tree is complete by now)
+__device__ __forceinline__ NodeBox node_box(int c, const int4* __restrict__ pk,
+                                            const unsigned long long* __restrict__ sthr,
+                                            const int4* __restrict__ nlo,
+                                            const int4* __restrict__ nhi,
+                                            const unsigned long long* __restrict__ nthr)
+{
+    NodeBox r;
+    if (c < 0) {
+        int s = ~c;
+        int4 p = __ldg(&pk[s]);
+        r.lo[0] = r.hi[0] = p.x;
+        r.lo[1] = r.hi[1] = p.y;
+        r.lo[2] = r.hi[2] = p.z;
+        r.count = 1;
+        r.first = s;
+        r.thr = __ldg(&sthr[s]);
+    } else {
+        int4 a = __ldg(&nlo[c]), b = __ldg(&nhi[c]);
+        r.lo[0] = a.x;
+        r.lo[1] = a.y;
+        r.lo[2] = a.z;
+        r.count = a.w;
+        r.hi[0] = b.x;
+        r.hi[1] = b.y;
+        r.hi[2] = b.z;
+        r.first = b.w;
+        r.thr = __ldg(&nthr[c]);
+    }
+    return r;
+}
+
+// candidate cells: traverse the tree from the root, keep cells within reach.
+// mode 0: the cell's own reach (gather); otherwise max of both reaches (symmetric).
+__global__ void k_candidates(DevCfg dc, int mode, int ncell, int n,
                              const int* __restrict__ cell_node, const int* __restrict__ left,
                              const int* __restrict__ right, const int4* __restrict__ pk,
-                             const double* __restrict__ sh, const int4* __restrict__ nlo,
-                             const int4* __restrict__ nhi, const double* __restrict__ nhmax,
+                             const unsigned long long* __restrict__ sthr,
+                             const int4* __restrict__ nlo, const int4* __restrict__ nhi,
+                             const unsigned long long* __restrict__ nthr,
                              int2* __restrict__ cand, int* __restrict__ ncand, int* status,
                              int graceful)
 {
     int cid = blockIdx.x * blockDim.x + threadIdx.x;
     if (cid >= ncell) return;
-    NodeData me = node_data(cell_node[cid], pk, sh, nlo, nhi, nhmax);
-    const unsigned long long thr_self = neighbour_threshold(reach * me.hmax, dc.delta);
+    NodeBox me = node_box(cell_node[cid], pk, sthr, nlo, nhi, nthr);
+    const unsigned long long thr_self = me.thr;
     int stack[128];
     int sp = 0;
     stack[sp++] = n >= 2 ? 0 : ~0;
@@ -501,17 +571,16 @@ __global__ void k_candidates(DevCfg dc, int mode, double reach, int ncell, int n
     bool overflow = false;
     while (sp > 0) {
         int node = stack[--sp];
-        NodeData o = node_data(node, pk, sh, nlo, nhi, nhmax);
-        unsigned long long thr =
-            mode == 0 ? thr_self : neighbour_threshold(reach * fmax(me.hmax, o.hmax), dc.delta);
+        NodeBox o = node_box(node, pk, sthr, nlo, nhi, nthr);
+        unsigned long long thr = (mode == 0 || o.thr < thr_self) ? thr_self : o.thr;
         if (box_dist2(dc, me.lo, me.hi, o.lo, o.hi) >= thr) continue;
         if (o.count <= CELL_MAX) {
             if (k < MAX_CAND) cand[(long long)cid * MAX_CAND + k] = make_int2(o.first, o.count);
             else overflow = true;
             ++k;
         } else if (sp + 2 <= 128) {
-            stack[sp++] = right[node];
-            stack[sp++] = left[node];
+            stack[sp++] = __ldg(&right[node]);
+            stack[sp++] = __ldg(&left[node]);
         } else {
             overflow = true;
         }
@@ -579,7 +648,7 @@ __global__ void __launch_bounds__(128) k_lists(DevCfg dc, int mode, int ncell, i
             unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
                                     (unsigned long long)((long long)dy * dy) +
                                     (unsigned long long)((long long)dz * dz);
-            unsigned long long th = (mode == 1 && t > ta) ? t : ta;
+            unsigned long long th = (mode != 0 && t > ta) ? t : ta;
             if (r2 < th) {
                 if (m < K) nbr[(long long)m * cap + a] = (unsigned)b;
                 ++m;
@@ -616,11 +685,11 @@ apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful)
     if (s != APR_OK) return s;
     int ncell = ((int*)c->hbuf)[0];
     c->ncell = ncell;
-    APR_LAUNCH(c, k_candidates, nblocks(ncell, 128), 128, c->dc, mode, mode == 0 ? reach : 1.0, ncell, n,
-                                                       W.cell_node, W.left, W.right, W.pk, W.sh,
-                                                       W.nlo, W.nhi, W.nhmax, W.cand,
-                                                       W.ncand, W.status, graceful ? 1 : 0);
-    APR_LAUNCH(c, k_thresholds, nblocks(n, 256), 256, c->dc, n, mode == 0 ? reach : 1.0, W.sh, W.sthr);
+    APR_LAUNCH(c, k_thresholds, nblocks(n, 256), 256, c->dc, n, reach, W.sh, W.sthr);
+    if (n >= 2) APR_LAUNCH(c, k_node_thr, nblocks(n - 1, 256), 256, c->dc, n, reach, W.nhmax, W.nthr);
+    APR_LAUNCH(c, k_candidates, nblocks(ncell, 128), 128, c->dc, mode, ncell, n, W.cell_node, W.left,
+               W.right, W.pk, W.sthr, W.nlo, W.nhi, W.nthr, W.cand, W.ncand, W.status,
+               graceful ? 1 : 0);
     APR_LAUNCH(c, k_lists, nblocks((long long)ncell * 32, 128), 128, 
         c->dc, mode, ncell, n, c->cap, W.cell_first, W.cell_cnt, W.cand, W.ncand, W.pk, W.sthr,
         W.nbr, W.ncnt, W.status, graceful ? 1 : 0);

@@ -33,6 +33,8 @@ enum {
     ST_MAXSEG = 6,           // merge tree: largest open segment
     ST_TREE_BAD = 7,         // radix tree walk left its bounds (must never happen)
     ST_SHRINK = 8,           // density: lists overflowed, h shrunk for a retry
+    ST_BINS = 16,            // merge: first slot of each level's candidates (10 words)
+    ST_MERGES = 32,          // merge: merges per level (8 words)
     ST_NSTATUS = 16
 };
 
@@ -43,6 +45,13 @@ constexpr int PROF_POOL = 256;              // event pairs recorded before a dra
     do {                                                                       \
         ++(c)->launches;                                                       \
         kern<<<(grid), (block), 0, (c)->stream>>>(__VA_ARGS__);                \
+    } while (0)
+
+// the same with dynamic shared memory
+#define APR_LAUNCH_SMEM(c, kern, grid, block, smem, ...)                       \
+    do {                                                                       \
+        ++(c)->launches;                                                       \
+        kern<<<(grid), (block), (smem), (c)->stream>>>(__VA_ARGS__);           \
     } while (0)
 
 // configuration as the kernels see it (passed by value)
@@ -116,6 +125,7 @@ struct Workspace {
     int4* nlo;                // node bbox min (x,y,z) + count
     int4* nhi;                // node bbox max (x,y,z) + first sorted slot
     double* nhmax;            // node max h
+    unsigned long long* nthr; // node neighbour threshold at the current reach
     // cells
     unsigned int* cflag;
     unsigned int* cscan;
@@ -177,6 +187,7 @@ struct apr_ctx {
     bool have_force;
     int ncell;
     int last_shrink;
+    bool tree_smem_set;       // dynamic shared memory opt-in of the pairing-tree kernel
     // profiling
     long long launches;
     bool prof;
@@ -239,9 +250,13 @@ DevSinks dev_sinks(const apr_ctx* c);
 apr_status scan_u32(apr_ctx* c, const unsigned int* in, unsigned int* out, long long n,
                     unsigned int* total_dev);
 apr_status quantise(apr_ctx* c);
+// one stable 8-bit radix pass; bin_starts[d] (d < nbins) = first output slot of digit d
+apr_status radix_pass8(apr_ctx* c, const unsigned long long* kin, const unsigned int* vin,
+                       unsigned long long* kout, unsigned int* vout, long long n, int shift,
+                       int* bin_starts, int nbins);
 apr_status index_sort(apr_ctx* c);           // quantise, Morton sort, gather, tree, node data
 apr_status index_refresh_h(apr_ctx* c);      // re-gather h and node hmax after a density pass
-// mode 0: gather lists (r < 2 reach h_a), mode 1: symmetric lists (r < 2 max(h_a, h_b)).
+// mode 0: gather lists (r < 2 reach h_a); mode 1: symmetric lists (r < 2 reach max(h_a, h_b)).
 // graceful: an overflowing list is marked (count -1) instead of flagged as an error.
 apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful = false);
 

@@ -14,6 +14,8 @@
 // float64 operation rounds exactly as written (the geometry is bit-exact).
 #include <cfloat>
 #include <climits>
+#include <cstring>
+#include <vector>
 
 #include "apr_internal.cuh"
 
@@ -188,41 +190,67 @@ __global__ void k_split_apply(DevCfg dc, DevRegions rg, long long n, int level,
 }
 
 // ------------------------------------------------------------ merge tree
+//
+// The candidates of every level are paired at once (their trees are
+// independent): one stable radix pass groups them by level in ascending
+// index order; global level-synchronous rounds cut every segment larger than
+// TREE_LOCAL; then one CTA per chunk finishes its segments in shared memory.
 
-__global__ void k_merge_flag(long long n, int level, const unsigned char* __restrict__ lev,
-                             const unsigned char* __restrict__ flags, unsigned int* __restrict__ out)
+constexpr int TREE_LOCAL = 512;      // largest segment left to the shared-memory phase
+constexpr int TREE_LOC_CAP = 1024;   // positions one CTA can hold (< 2 * TREE_LOCAL)
+constexpr int TREE_LOC_THREADS = 256;
+
+struct LevelOffsets {
+    int off[APR_MAXLEV + 2];  // candidates of level l occupy [off[l], off[l+1])
+    int lmax;
+};
+
+__global__ void k_merge_keys(long long n, const unsigned char* __restrict__ lev,
+                             const unsigned char* __restrict__ flags,
+                             unsigned long long* __restrict__ key, unsigned int* __restrict__ val)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    out[i] = (lev[i] == level &&
-              !(flags[i] & (APR_FLAG_CHANGED | APR_FLAG_FIXED | APR_FLAG_DEAD))) ? 1u : 0u;
+    const int l = lev[i];
+    const bool cand = l >= 1 && !(flags[i] & (APR_FLAG_CHANGED | APR_FLAG_FIXED | APR_FLAG_DEAD));
+    key[i] = cand ? (unsigned long long)l : 255ULL;
+    val[i] = (unsigned)i;
 }
 
-__global__ void k_merge_collect(long long n, const unsigned int* __restrict__ flag,
-                                const unsigned int* __restrict__ pos, unsigned int* __restrict__ set)
+__device__ __forceinline__ void acc_reset(int s, int4* acc_lo, int4* acc_hi,
+                                          unsigned long long* acc_sum, unsigned int* acc_k,
+                                          unsigned int* acc_k2, unsigned long long* acc_key,
+                                          unsigned long long* acc_key2)
 {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && flag[i]) set[pos[i]] = (unsigned)i;
+    acc_lo[s] = make_int4(INT_MAX, INT_MAX, INT_MAX, 0);
+    acc_hi[s] = make_int4(INT_MIN, INT_MIN, INT_MIN, 0);
+    acc_sum[s] = 0;
+    acc_k[s] = 0;
+    acc_k2[s] = 0;
+    acc_key[s] = 0;
+    acc_key2[s] = ~0ULL;
 }
 
-__global__ void k_seg_init(int m, int* __restrict__ lo, int* __restrict__ hi, int4* acc_lo,
-                           int4* acc_hi, unsigned long long* acc_sum, unsigned int* acc_k,
-                           unsigned int* acc_k2, unsigned long long* acc_key,
-                           unsigned long long* acc_key2)
+// one segment per level (even count); an odd level's last candidate is the spare
+__global__ void k_seg_setup(int M, LevelOffsets lo_off, int* __restrict__ lo, int* __restrict__ hi,
+                            int4* acc_lo, int4* acc_hi, unsigned long long* acc_sum,
+                            unsigned int* acc_k, unsigned int* acc_k2, unsigned long long* acc_key,
+                            unsigned long long* acc_key2)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= m) return;
-    lo[p] = 0;
-    hi[p] = m;
-    if (p == 0) {
-        acc_lo[0] = make_int4(INT_MAX, INT_MAX, INT_MAX, 0);
-        acc_hi[0] = make_int4(INT_MIN, INT_MIN, INT_MIN, 0);
-        acc_sum[0] = 0;
-        acc_k[0] = 0;
-        acc_k2[0] = 0;
-        acc_key[0] = 0;
-        acc_key2[0] = ~0ULL;
+    if (p >= M) return;
+    int l = 1;
+    while (l < lo_off.lmax && p >= lo_off.off[l + 1]) ++l;
+    const int a = lo_off.off[l], m = lo_off.off[l + 1] - a, be = a + (m & ~1);
+    if (p < be) {
+        lo[p] = a;
+        hi[p] = be;
+    } else {
+        lo[p] = p;
+        hi[p] = p + 1;
     }
+    if (p == a && be - a > TREE_LOCAL)
+        acc_reset(a, acc_lo, acc_hi, acc_sum, acc_k, acc_k2, acc_key, acc_key2);
 }
 
 // lanes of one warp that work on the same segment reduce before one atomic
@@ -237,9 +265,58 @@ __device__ __forceinline__ bool seg_leader(unsigned peers)
     return (int)(threadIdx.x & 31) == __ffs(peers) - 1;
 }
 
-__global__ void k_tree_bbox(int m, const unsigned int* __restrict__ set, const int* __restrict__ lo,
-                            const int* __restrict__ hi, const int4* __restrict__ xi, int4* acc_lo,
-                            int4* acc_hi)
+__device__ __forceinline__ int axis_of(int ex, int ey, int ez)
+{
+    int ax = 0, e = ex;
+    if (ey > e) {
+        ax = 1;
+        e = ey;
+    }
+    if (ez > e) ax = 2;
+    return ax;
+}
+
+__device__ __forceinline__ int seg_axis(const int4& a, const int4& b)
+{
+    return axis_of(b.x - a.x, b.y - a.y, b.z - a.z);
+}
+
+__device__ __forceinline__ int comp(const int4& q, int ax) { return ax == 0 ? q.x : (ax == 1 ? q.y : q.z); }
+
+// the cut of one segment from its count below the centre of mass (Sec. 2.3 reading):
+// k = #{x < com}; if 0, #{x <= com}; all coincident: 2 floor(n/4) by index; odd: k+-1
+struct Cut {
+    bool use_le, coincident;
+    int k, kfinal;
+};
+
+__device__ __forceinline__ Cut make_cut(int size, int k_lt, int k_le)
+{
+    Cut c;
+    c.k = k_lt;
+    c.use_le = false;
+    if (c.k == 0) {
+        c.k = k_le;
+        c.use_le = true;
+    }
+    c.coincident = c.k == size;
+    if (c.coincident) {
+        c.kfinal = 2 * (size / 4);
+    } else if (c.k % 2) {
+        int a = c.k - 1, b = c.k + 1;
+        int da = abs(2 * a - size), db = abs(2 * b - size);
+        c.kfinal = (da <= db) ? a : b;
+    } else {
+        c.kfinal = c.k;
+    }
+    return c;
+}
+
+// ---- global rounds: segments larger than `thresh`
+
+__global__ void k_tree_bbox(int m, int thresh, const unsigned int* __restrict__ set,
+                            const int* __restrict__ lo, const int* __restrict__ hi,
+                            const int4* __restrict__ xi, int4* acc_lo, int4* acc_hi)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     bool act = false;
@@ -247,7 +324,7 @@ __global__ void k_tree_bbox(int m, const unsigned int* __restrict__ set, const i
     int4 q = make_int4(0, 0, 0, 0);
     if (p < m) {
         seg = lo[p];
-        act = hi[p] - seg > 2;
+        act = hi[p] - seg > thresh;
         if (act) q = xi[set[p]];
     }
     unsigned peers = seg_peers(act, seg);
@@ -266,24 +343,10 @@ __global__ void k_tree_bbox(int m, const unsigned int* __restrict__ set, const i
     }
 }
 
-__device__ __forceinline__ int seg_axis(const int4& a, const int4& b)
-{
-    int ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
-    int ax = 0, e = ex;
-    if (ey > e) {
-        ax = 1;
-        e = ey;
-    }
-    if (ez > e) ax = 2;
-    return ax;
-}
-
-__device__ __forceinline__ int comp(const int4& q, int ax) { return ax == 0 ? q.x : (ax == 1 ? q.y : q.z); }
-
-__global__ void k_tree_sum(int m, const unsigned int* __restrict__ set, const int* __restrict__ lo,
-                           const int* __restrict__ hi, const int4* __restrict__ xi,
-                           const int4* __restrict__ acc_lo, const int4* __restrict__ acc_hi,
-                           unsigned long long* acc_sum)
+__global__ void k_tree_sum(int m, int thresh, const unsigned int* __restrict__ set,
+                           const int* __restrict__ lo, const int* __restrict__ hi,
+                           const int4* __restrict__ xi, const int4* __restrict__ acc_lo,
+                           const int4* __restrict__ acc_hi, unsigned long long* acc_sum)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     bool act = false;
@@ -291,7 +354,7 @@ __global__ void k_tree_sum(int m, const unsigned int* __restrict__ set, const in
     unsigned v = 0;
     if (p < m) {
         seg = lo[p];
-        act = hi[p] - seg > 2;
+        act = hi[p] - seg > thresh;
         if (act) v = (unsigned)comp(xi[set[p]], seg_axis(acc_lo[seg], acc_hi[seg]));
     }
     unsigned peers = seg_peers(act, seg);
@@ -302,9 +365,10 @@ __global__ void k_tree_sum(int m, const unsigned int* __restrict__ set, const in
         atomicAdd(&acc_sum[seg], ((unsigned long long)s_hi << 15) + (unsigned long long)s_lo);
 }
 
-__global__ void k_tree_count(int m, const unsigned int* __restrict__ set, const int* __restrict__ lo,
-                             const int* __restrict__ hi, const int4* __restrict__ xi,
-                             const int4* __restrict__ acc_lo, const int4* __restrict__ acc_hi,
+__global__ void k_tree_count(int m, int thresh, const unsigned int* __restrict__ set,
+                             const int* __restrict__ lo, const int* __restrict__ hi,
+                             const int4* __restrict__ xi, const int4* __restrict__ acc_lo,
+                             const int4* __restrict__ acc_hi,
                              const unsigned long long* __restrict__ acc_sum, unsigned int* acc_k,
                              unsigned int* acc_k2)
 {
@@ -315,7 +379,7 @@ __global__ void k_tree_count(int m, const unsigned int* __restrict__ set, const 
     if (p < m) {
         seg = lo[p];
         int size = hi[p] - seg;
-        act = size > 2;
+        act = size > thresh;
         if (act) {
             long long com = (long long)(acc_sum[seg] / (unsigned long long)size);
             long long v = comp(xi[set[p]], seg_axis(acc_lo[seg], acc_hi[seg]));
@@ -332,45 +396,10 @@ __global__ void k_tree_count(int m, const unsigned int* __restrict__ set, const 
     }
 }
 
-// the cut of one segment: predicate (< or <=), count, and the final left count
-struct Cut {
-    bool use_le, coincident;
-    int k, kfinal;
-    long long com;
-    int ax;
-};
-
-__device__ __forceinline__ Cut seg_cut(int seg, int size, const int4* acc_lo, const int4* acc_hi,
-                                       const unsigned long long* acc_sum, const unsigned int* acc_k,
-                                       const unsigned int* acc_k2)
-{
-    Cut c;
-    c.ax = seg_axis(acc_lo[seg], acc_hi[seg]);
-    c.com = (long long)(acc_sum[seg] / (unsigned long long)size);
-    c.k = (int)acc_k[seg];
-    c.use_le = false;
-    if (c.k == 0) {
-        c.k = (int)acc_k2[seg];
-        c.use_le = true;
-    }
-    c.coincident = c.k == size;
-    if (c.coincident) {
-        c.kfinal = 2 * (size / 4);
-    } else if (c.k % 2) {
-        int a = c.k - 1, b = c.k + 1;
-        int da = abs(2 * a - size), db = abs(2 * b - size);
-        c.kfinal = (da <= db) ? a : b;
-    } else {
-        c.kfinal = c.k;
-    }
-    return c;
-}
-
-// for an odd cut: the largest (coordinate, index) on the low side moves up, or
-// the smallest on the high side moves down
-__global__ void k_tree_key(int m, const unsigned int* __restrict__ set, const int* __restrict__ lo,
-                           const int* __restrict__ hi, const int4* __restrict__ xi,
-                           const int4* __restrict__ acc_lo, const int4* __restrict__ acc_hi,
+__global__ void k_tree_key(int m, int thresh, const unsigned int* __restrict__ set,
+                           const int* __restrict__ lo, const int* __restrict__ hi,
+                           const int4* __restrict__ xi, const int4* __restrict__ acc_lo,
+                           const int4* __restrict__ acc_hi,
                            const unsigned long long* __restrict__ acc_sum,
                            const unsigned int* __restrict__ acc_k,
                            const unsigned int* __restrict__ acc_k2, unsigned long long* acc_key,
@@ -379,20 +408,23 @@ __global__ void k_tree_key(int m, const unsigned int* __restrict__ set, const in
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= m) return;
     int seg = lo[p], size = hi[p] - seg;
-    if (size <= 2) return;
-    Cut c = seg_cut(seg, size, acc_lo, acc_hi, acc_sum, acc_k, acc_k2);
+    if (size <= thresh) return;
+    Cut c = make_cut(size, (int)acc_k[seg], (int)acc_k2[seg]);
     if (c.coincident || c.kfinal == c.k) return;
+    const int ax = seg_axis(acc_lo[seg], acc_hi[seg]);
+    const long long com = (long long)(acc_sum[seg] / (unsigned long long)size);
     unsigned idx = set[p];
-    long long v = comp(xi[idx], c.ax);
-    bool low = c.use_le ? v <= c.com : v < c.com;
+    long long v = comp(xi[idx], ax);
+    bool low = c.use_le ? v <= com : v < com;
     unsigned long long key = ((unsigned long long)v << 32) | idx;
     if (c.kfinal < c.k && low) atomicMax(&acc_key[seg], key);
     if (c.kfinal > c.k && !low) atomicMin(&acc_key2[seg], key);
 }
 
-__global__ void k_tree_flag(int m, const unsigned int* __restrict__ set, const int* __restrict__ lo,
-                            const int* __restrict__ hi, const int4* __restrict__ xi,
-                            const int4* __restrict__ acc_lo, const int4* __restrict__ acc_hi,
+__global__ void k_tree_flag(int m, int thresh, const unsigned int* __restrict__ set,
+                            const int* __restrict__ lo, const int* __restrict__ hi,
+                            const int4* __restrict__ xi, const int4* __restrict__ acc_lo,
+                            const int4* __restrict__ acc_hi,
                             const unsigned long long* __restrict__ acc_sum,
                             const unsigned int* __restrict__ acc_k,
                             const unsigned int* __restrict__ acc_k2,
@@ -403,18 +435,20 @@ __global__ void k_tree_flag(int m, const unsigned int* __restrict__ set, const i
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= m) return;
     int seg = lo[p], size = hi[p] - seg;
-    if (size <= 2) {
+    if (size <= thresh) {
         lflag[p] = 0;
         return;
     }
-    Cut c = seg_cut(seg, size, acc_lo, acc_hi, acc_sum, acc_k, acc_k2);
+    Cut c = make_cut(size, (int)acc_k[seg], (int)acc_k2[seg]);
     unsigned idx = set[p];
     bool left;
     if (c.coincident) {
         left = (p - seg) < c.kfinal;  // segments stay in ascending index order
     } else {
-        long long v = comp(xi[idx], c.ax);
-        left = c.use_le ? v <= c.com : v < c.com;
+        const int ax = seg_axis(acc_lo[seg], acc_hi[seg]);
+        const long long com = (long long)(acc_sum[seg] / (unsigned long long)size);
+        long long v = comp(xi[idx], ax);
+        left = c.use_le ? v <= com : v < com;
         unsigned long long key = ((unsigned long long)v << 32) | idx;
         if (c.kfinal < c.k && key == acc_key[seg]) left = false;
         if (c.kfinal > c.k && key == acc_key2[seg]) left = true;
@@ -422,10 +456,8 @@ __global__ void k_tree_flag(int m, const unsigned int* __restrict__ set, const i
     lflag[p] = left ? 1u : 0u;
 }
 
-__global__ void k_tree_scatter(int m, const unsigned int* __restrict__ set,
+__global__ void k_tree_scatter(int m, int thresh, const unsigned int* __restrict__ set,
                                const int* __restrict__ lo, const int* __restrict__ hi,
-                               const int4* __restrict__ acc_lo, const int4* __restrict__ acc_hi,
-                               const unsigned long long* __restrict__ acc_sum,
                                const unsigned int* __restrict__ acc_k,
                                const unsigned int* __restrict__ acc_k2,
                                const unsigned int* __restrict__ lflag,
@@ -440,9 +472,9 @@ __global__ void k_tree_scatter(int m, const unsigned int* __restrict__ set,
     if (p >= m) return;
     int seg = lo[p], end = hi[p], size = end - seg;
     int np = p, nlo = seg, nhi = end;
-    if (size > 2) {
-        Cut c = seg_cut(seg, size, acc_lo, acc_hi, acc_sum, acc_k, acc_k2);
-        int before = (int)(lscan[p] - lscan[seg]);  // left items before p in this segment
+    if (size > thresh) {
+        Cut c = make_cut(size, (int)acc_k[seg], (int)acc_k2[seg]);
+        int before = (int)(lscan[p] - lscan[seg]);  // low items before p in this segment
         if (lflag[p]) {
             np = seg + before;
             nhi = seg + c.kfinal;
@@ -450,102 +482,272 @@ __global__ void k_tree_scatter(int m, const unsigned int* __restrict__ set,
             np = seg + c.kfinal + ((p - seg) - before);
             nlo = seg + c.kfinal;
         }
-        atomicMax(maxseg, nhi - nlo);
+        if (nhi - nlo > thresh) atomicMax(maxseg, nhi - nlo);
     }
     set2[np] = set[p];
     lo2[np] = nlo;
     hi2[np] = nhi;
-    if (np == nlo && nhi - nlo > 2) {
-        acc_lo_n[np] = make_int4(INT_MAX, INT_MAX, INT_MAX, 0);
-        acc_hi_n[np] = make_int4(INT_MIN, INT_MIN, INT_MIN, 0);
-        acc_sum_n[np] = 0;
-        acc_k_n[np] = 0;
-        acc_k2_n[np] = 0;
-        acc_key_n[np] = 0;
-        acc_key2_n[np] = ~0ULL;
-    }
+    if (np == nlo && nhi - nlo > thresh)
+        acc_reset(np, acc_lo_n, acc_hi_n, acc_sum_n, acc_k_n, acc_k2_n, acc_key_n, acc_key2_n);
 }
 
-// pairs the merge candidates of one level; returns the count m (even) and the
-// spare index; on return W.mset[*cur] holds the pairs at (2j, 2j+1)
-static apr_status pair_tree(apr_ctx* c, int level, int* m_out, long long* spare, int* cur_out)
+// ---- shared-memory phase: every segment of size <= TREE_LOCAL, one CTA per chunk
+
+struct LocalSmem {
+    int X[TREE_LOC_CAP], Y[TREE_LOC_CAP], Z[TREE_LOC_CAP];
+    unsigned I[TREE_LOC_CAP];
+    short P[2][TREE_LOC_CAP];              // permutation of local slots
+    short Lo[2][TREE_LOC_CAP], Hi[2][TREE_LOC_CAP];
+    unsigned Fl[TREE_LOC_CAP];             // low flags
+    unsigned F[TREE_LOC_CAP];              // their exclusive prefix over the block's slots
+    int amin[3][TREE_LOC_CAP], amax[3][TREE_LOC_CAP];
+    unsigned long long asum[TREE_LOC_CAP];
+    unsigned ak[TREE_LOC_CAP], ak2[TREE_LOC_CAP];
+    unsigned long long akey[TREE_LOC_CAP], akey2[TREE_LOC_CAP];
+    unsigned wsum[TREE_LOC_THREADS / 32];
+    int range_lo, range_hi, any;
+};
+
+__device__ __forceinline__ int lcomp(const LocalSmem& S, int q, int ax)
 {
-    Workspace& W = c->W;
-    cudaStream_t st = c->stream;
-    const long long n = c->n;
-    APR_LAUNCH(c, k_merge_flag, nblocks(n, 256), 256, n, level, c->p.level, c->p.flags, W.uflag);
-    scan_u32(c, W.uflag, W.uscan, n, (unsigned*)&W.status[ST_COUNT_A]);
-    APR_LAUNCH(c, k_merge_collect, nblocks(n, 256), 256, n, W.uflag, W.uscan, W.mset[0]);
-    cudaMemcpyAsync(c->hbuf, &W.status[ST_COUNT_A], sizeof(int), cudaMemcpyDeviceToHost, st);
-    apr_status s = cuda_check(c, cudaStreamSynchronize(st), "merge candidates");
-    if (s != APR_OK) return s;
-    int m = ((int*)c->hbuf)[0];
-    *spare = -1;
-    if (m % 2) {
-        cudaMemcpyAsync(c->hbuf, W.mset[0] + (m - 1), sizeof(unsigned), cudaMemcpyDeviceToHost,
-                        st);
-        s = cuda_check(c, cudaStreamSynchronize(st), "spare");
-        if (s != APR_OK) return s;
-        *spare = ((unsigned*)c->hbuf)[0];
-        --m;
+    return ax == 0 ? S.X[q] : (ax == 1 ? S.Y[q] : S.Z[q]);
+}
+
+__device__ __forceinline__ int laxis(const LocalSmem& S, int seg)
+{
+    return axis_of(S.amax[0][seg] - S.amin[0][seg], S.amax[1][seg] - S.amin[1][seg],
+                   S.amax[2][seg] - S.amin[2][seg]);
+}
+
+__global__ void __launch_bounds__(TREE_LOC_THREADS)
+    k_tree_local(int M, const int4* __restrict__ xi, unsigned int* __restrict__ set,
+                 int* __restrict__ glo, int* __restrict__ ghi)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LocalSmem& S = *reinterpret_cast<LocalSmem*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int c0 = blockIdx.x * TREE_LOCAL, c1 = min(M, c0 + TREE_LOCAL);
+    if (tid == 0) {
+        S.range_lo = INT_MAX;
+        S.range_hi = INT_MIN;
     }
-    *m_out = m;
-    *cur_out = 0;
-    if (m <= 2) return APR_OK;
-    // accumulators live in two banks indexed by segment start
-    unsigned long long* key2[2] = {W.acc_key + c->cap, W.acc_key + 2 * c->cap};
-    int4* alo[2] = {W.acc_lo, W.acc_lo + c->cap};
-    int4* ahi[2] = {W.acc_hi, W.acc_hi + c->cap};
-    unsigned long long* asum[2] = {W.acc_sum, W.acc_sum + c->cap};
-    unsigned int* ak[2] = {W.acc_k, W.acc_k + c->cap};
-    unsigned int* ak2[2] = {W.acc_k2, W.acc_k2 + c->cap};
-    unsigned long long* akey[2] = {W.acc_key, W.acc_key + 3 * c->cap};
-    APR_LAUNCH(c, k_seg_init, nblocks(m, 256), 256, m, W.seg_lo[0], W.seg_hi[0], alo[0], ahi[0], asum[0],
-                                               ak[0], ak2[0], akey[0], key2[0]);
+    __syncthreads();
+    // segments starting in [c0, c1) belong to this block
+    for (int p = c0 + tid; p < c1; p += TREE_LOC_THREADS)
+        if (glo[p] == p) {
+            atomicMin(&S.range_lo, p);
+            atomicMax(&S.range_hi, ghi[p]);
+        }
+    __syncthreads();
+    const int base = S.range_lo, s = S.range_hi - S.range_lo;
+    if (base == INT_MAX || s <= 0 || s > TREE_LOC_CAP) return;  // s <= 2*TREE_LOCAL - 1 by construction
+    for (int q = tid; q < s; q += TREE_LOC_THREADS) {
+        unsigned e = set[base + q];
+        int4 v = xi[e];
+        S.X[q] = v.x;
+        S.Y[q] = v.y;
+        S.Z[q] = v.z;
+        S.I[q] = e;
+        S.P[0][q] = (short)q;
+        S.Lo[0][q] = (short)(glo[base + q] - base);
+        S.Hi[0][q] = (short)(ghi[base + q] - base);
+    }
+    __syncthreads();
+    const int lane = tid & 31, wid = tid >> 5;
     int cur = 0;
-    const int nb = nblocks(m, 256);
-    for (int round = 0; round < 4 * m + 64; ++round) {
-        APR_LAUNCH(c, k_tree_bbox, nb, 256, m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], W.xi,
-                                        alo[cur], ahi[cur]);
-        APR_LAUNCH(c, k_tree_sum, nb, 256, m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], W.xi, alo[cur],
-                                       ahi[cur], asum[cur]);
-        APR_LAUNCH(c, k_tree_count, nb, 256, m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], W.xi,
-                                         alo[cur], ahi[cur], asum[cur], ak[cur], ak2[cur]);
-        APR_LAUNCH(c, k_tree_key, nb, 256, m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], W.xi, alo[cur],
-                                       ahi[cur], asum[cur], ak[cur], ak2[cur], akey[cur], key2[cur]);
-        APR_LAUNCH(c, k_tree_flag, nb, 256, m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], W.xi,
-                                        alo[cur], ahi[cur], asum[cur], ak[cur], ak2[cur], akey[cur],
-                                        key2[cur], W.lflag);
-        scan_u32(c, W.lflag, W.uscan, m, nullptr);
-        cudaMemsetAsync(&W.status[ST_MAXSEG], 0, sizeof(int), st);
+    for (int level = 0; level < 4 * TREE_LOC_CAP; ++level) {
+        // open segments (size > 2) reset their accumulators
+        for (int p = tid; p < s; p += TREE_LOC_THREADS) {
+            int l = S.Lo[cur][p], h = S.Hi[cur][p];
+            if (l == p && h - l > 2) {
+                for (int k = 0; k < 3; ++k) {
+                    S.amin[k][p] = INT_MAX;
+                    S.amax[k][p] = INT_MIN;
+                }
+                S.asum[p] = 0;
+                S.ak[p] = 0;
+                S.ak2[p] = 0;
+                S.akey[p] = 0;
+                S.akey2[p] = ~0ULL;
+            }
+        }
+        if (tid == 0) S.any = 0;
+        __syncthreads();
+        // bounding boxes
+        for (int p0 = 0; p0 < s; p0 += TREE_LOC_THREADS) {
+            int p = p0 + tid;
+            bool act = false;
+            int seg = 0, q = 0;
+            if (p < s) {
+                seg = S.Lo[cur][p];
+                act = S.Hi[cur][p] - seg > 2;
+                q = S.P[cur][p];
+            }
+            unsigned peers = seg_peers(act, seg);
+            if (act) {
+                int mn[3] = {__reduce_min_sync(peers, S.X[q]), __reduce_min_sync(peers, S.Y[q]),
+                             __reduce_min_sync(peers, S.Z[q])};
+                int mx[3] = {__reduce_max_sync(peers, S.X[q]), __reduce_max_sync(peers, S.Y[q]),
+                             __reduce_max_sync(peers, S.Z[q])};
+                if (seg_leader(peers))
+                    for (int k = 0; k < 3; ++k) {
+                        atomicMin(&S.amin[k][seg], mn[k]);
+                        atomicMax(&S.amax[k][seg], mx[k]);
+                    }
+            }
+        }
+        __syncthreads();
+        // coordinate sums along each segment's widest axis
+        for (int p0 = 0; p0 < s; p0 += TREE_LOC_THREADS) {
+            int p = p0 + tid;
+            bool act = false;
+            int seg = 0;
+            unsigned v = 0;
+            if (p < s) {
+                seg = S.Lo[cur][p];
+                act = S.Hi[cur][p] - seg > 2;
+                if (act) v = (unsigned)lcomp(S, S.P[cur][p], laxis(S, seg));
+            }
+            unsigned peers = seg_peers(act, seg);
+            if (act) {
+                unsigned sh = __reduce_add_sync(peers, v >> 15), sl = __reduce_add_sync(peers, v & 0x7fffu);
+                if (seg_leader(peers))
+                    atomicAdd(&S.asum[seg], ((unsigned long long)sh << 15) + (unsigned long long)sl);
+            }
+        }
+        __syncthreads();
+        // counts below the centre of mass
+        for (int p0 = 0; p0 < s; p0 += TREE_LOC_THREADS) {
+            int p = p0 + tid;
+            bool act = false;
+            int seg = 0;
+            unsigned lt = 0, le = 0;
+            if (p < s) {
+                seg = S.Lo[cur][p];
+                int size = S.Hi[cur][p] - seg;
+                act = size > 2;
+                if (act) {
+                    long long com = (long long)(S.asum[seg] / (unsigned long long)size);
+                    long long v = lcomp(S, S.P[cur][p], laxis(S, seg));
+                    lt = v < com;
+                    le = v <= com;
+                }
+            }
+            unsigned peers = seg_peers(act, seg);
+            if (act) {
+                unsigned clt = __reduce_add_sync(peers, lt), cle = __reduce_add_sync(peers, le);
+                if (seg_leader(peers)) {
+                    atomicAdd(&S.ak[seg], clt);
+                    atomicAdd(&S.ak2[seg], cle);
+                }
+            }
+        }
+        __syncthreads();
+        // odd cuts: the particle that crosses
+        for (int p = tid; p < s; p += TREE_LOC_THREADS) {
+            int seg = S.Lo[cur][p], size = S.Hi[cur][p] - seg;
+            if (size <= 2) continue;
+            Cut c = make_cut(size, (int)S.ak[seg], (int)S.ak2[seg]);
+            if (c.coincident || c.kfinal == c.k) continue;
+            int q = S.P[cur][p];
+            long long com = (long long)(S.asum[seg] / (unsigned long long)size);
+            long long v = lcomp(S, q, laxis(S, seg));
+            bool low = c.use_le ? v <= com : v < com;
+            unsigned long long key = ((unsigned long long)v << 32) | S.I[q];
+            if (c.kfinal < c.k && low) atomicMax(&S.akey[seg], key);
+            if (c.kfinal > c.k && !low) atomicMin(&S.akey2[seg], key);
+        }
+        __syncthreads();
+        // low flags
+        for (int p = tid; p < s; p += TREE_LOC_THREADS) {
+            int seg = S.Lo[cur][p], size = S.Hi[cur][p] - seg;
+            unsigned f = 0;
+            if (size > 2) {
+                Cut c = make_cut(size, (int)S.ak[seg], (int)S.ak2[seg]);
+                if (c.coincident) {
+                    f = (p - seg) < c.kfinal;  // segments stay in ascending index order
+                } else {
+                    int q = S.P[cur][p];
+                    long long com = (long long)(S.asum[seg] / (unsigned long long)size);
+                    long long v = lcomp(S, q, laxis(S, seg));
+                    bool left = c.use_le ? v <= com : v < com;
+                    unsigned long long key = ((unsigned long long)v << 32) | S.I[q];
+                    if (c.kfinal < c.k && key == S.akey[seg]) left = false;
+                    if (c.kfinal > c.k && key == S.akey2[seg]) left = true;
+                    f = left;
+                }
+            }
+            S.Fl[p] = f;
+        }
+        __syncthreads();
+        // exclusive prefix of the flags over the block's slots (a contiguous run per thread)
+        {
+            const int per = (s + TREE_LOC_THREADS - 1) / TREE_LOC_THREADS;
+            const int b0 = min(s, tid * per), b1 = min(s, b0 + per);
+            unsigned run = 0;
+            for (int p = b0; p < b1; ++p) run += S.Fl[p];
+            unsigned incl = run;
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane == 31) S.wsum[wid] = incl;
+            __syncthreads();
+            unsigned ex = incl - run;
+            for (int w = 0; w < wid; ++w) ex += S.wsum[w];
+            for (int p = b0; p < b1; ++p) {
+                S.F[p] = ex;
+                ex += S.Fl[p];
+            }
+        }
+        __syncthreads();
+        // stable partition of every open segment into the other buffer
         const int nx = cur ^ 1;
-        APR_LAUNCH(c, k_tree_scatter, nb, 256, m, W.mset[cur], W.seg_lo[cur], W.seg_hi[cur], alo[cur],
-                                           ahi[cur], asum[cur], ak[cur], ak2[cur], W.lflag, W.uscan,
-                                           W.mset[nx], W.seg_lo[nx], W.seg_hi[nx], alo[nx], ahi[nx],
-                                           asum[nx], ak[nx], ak2[nx], akey[nx], key2[nx],
-                                           &W.status[ST_MAXSEG]);
+        for (int p = tid; p < s; p += TREE_LOC_THREADS) {
+            int seg = S.Lo[cur][p], end = S.Hi[cur][p], size = end - seg;
+            int np = p, nlo = seg, nhi = end;
+            if (size > 2) {
+                Cut c = make_cut(size, (int)S.ak[seg], (int)S.ak2[seg]);
+                int before = (int)(S.F[p] - S.F[seg]);  // low slots in [seg, p)
+                if (S.Fl[p]) {
+                    np = seg + before;
+                    nhi = seg + c.kfinal;
+                } else {
+                    np = seg + c.kfinal + ((p - seg) - before);
+                    nlo = seg + c.kfinal;
+                }
+                if (nhi - nlo > 2) S.any = 1;
+            }
+            S.P[nx][np] = S.P[cur][p];
+            S.Lo[nx][np] = (short)nlo;
+            S.Hi[nx][np] = (short)nhi;
+        }
+        __syncthreads();
         cur = nx;
-        cudaMemcpyAsync(c->hbuf, &W.status[ST_MAXSEG], sizeof(int), cudaMemcpyDeviceToHost, st);
-        s = cuda_check(c, cudaStreamSynchronize(st), "pairing tree");
-        if (s != APR_OK) return s;
-        if (((int*)c->hbuf)[0] <= 2) break;
+        if (!S.any) break;
+        __syncthreads();
     }
-    *cur_out = cur;
-    return APR_OK;
+    for (int p = tid; p < s; p += TREE_LOC_THREADS) {
+        set[base + p] = S.I[S.P[cur][p]];
+        glo[base + p] = base + S.Lo[cur][p];
+        ghi[base + p] = base + S.Hi[cur][p];
+    }
 }
 
-__global__ void k_merge_apply(DevCfg dc, DevRegions rg, int npairs, int level,
-                              const unsigned int* __restrict__ set, apr_particles p,
-                              int* __restrict__ count)
+// the merge decision of every leaf pair of every level (Sec. 2.3, Eq. 3)
+__global__ void k_merge_apply(DevCfg dc, DevRegions rg, int M, const unsigned int* __restrict__ set,
+                              const int* __restrict__ glo, const int* __restrict__ ghi,
+                              apr_particles p, int* __restrict__ count_per_level)
 {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= npairs) return;
-    unsigned a = set[2 * j], b = set[2 * j + 1];
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= M || glo[q] != q || ghi[q] - q != 2) return;
+    unsigned a = set[q], b = set[q + 1];
     if (b < a) {
         unsigned t = a;
         a = b;
         b = t;
     }
+    const int level = p.level[a];
     double pa[3] = {p.x[a], p.y[a], p.z[a]}, pb[3] = {p.x[b], p.y[b], p.z[b]};
     double com[3];
     for (int k = 0; k < 3; ++k) {
@@ -568,33 +770,146 @@ __global__ void k_merge_apply(DevCfg dc, DevRegions rg, int npairs, int level,
     p.level[a] = (unsigned char)(level - 1);
     p.flags[a] = p.flags[a] | APR_FLAG_CHANGED;
     p.flags[b] = p.flags[b] | APR_FLAG_DEAD;
-    atomicAdd(count, 1);
+    atomicAdd(&count_per_level[level], 1);
 }
 
-__global__ void k_pairs_out(int npairs, const unsigned int* __restrict__ set,
-                            long long* __restrict__ out)
+// the pairing trees of all levels.  On return (*set)[0..M) holds the candidates
+// grouped by level (ascending), each level's leaves at consecutive slots, and
+// (*lo, *hi) the leaf bounds of every slot; off[l] is the first slot of level l
+// (off[lmax+1] = M).
+static apr_status pair_trees(apr_ctx* c, int* off, unsigned int** set_out, int** lo_out,
+                             int** hi_out)
+{
+    Workspace& W = c->W;
+    cudaStream_t st = c->stream;
+    const long long n = c->n;
+    const int lmax = c->cfg.lmax;
+    APR_LAUNCH(c, k_merge_keys, nblocks(n, 256), 256, n, c->p.level, c->p.flags, W.key[0], W.val[0]);
+    apr_status s = radix_pass8(c, W.key[0], W.val[0], W.key[1], W.mset[0], n, 0, &W.status[ST_BINS],
+                               lmax + 2);
+    if (s != APR_OK) return s;
+    cudaMemcpyAsync(c->hbuf, &W.status[ST_BINS], sizeof(int) * (lmax + 2), cudaMemcpyDeviceToHost, st);
+    s = cuda_check(c, cudaStreamSynchronize(st), "merge candidates");
+    if (s != APR_OK) return s;
+    const int* bins = (const int*)c->hbuf;
+    // bins[l] = first sorted slot of level l; candidates are levels 1..lmax
+    LevelOffsets lo_off;
+    memset(&lo_off, 0, sizeof(lo_off));
+    lo_off.lmax = lmax;
+    const int first = lmax >= 1 ? bins[1] : 0;
+    for (int l = 1; l <= lmax + 1; ++l) {
+        off[l] = (l <= lmax + 1 ? bins[l] : bins[lmax + 1]) - first;
+        lo_off.off[l] = off[l];
+    }
+    off[0] = 0;
+    const int M = off[lmax + 1];
+    *set_out = W.mset[1];
+    *lo_out = W.seg_lo[0];
+    *hi_out = W.seg_hi[0];
+    if (M <= 0) return APR_OK;
+    if (first > 0)  // level-0 particles sorted first: move the candidates to slot 0
+        cudaMemcpyAsync(W.mset[1], W.mset[0] + first, sizeof(unsigned) * M, cudaMemcpyDeviceToDevice,
+                        st);
+    else
+        cudaMemcpyAsync(W.mset[1], W.mset[0], sizeof(unsigned) * M, cudaMemcpyDeviceToDevice, st);
+    unsigned long long* key2[2] = {W.acc_key + c->cap, W.acc_key + 2 * c->cap};
+    int4* alo[2] = {W.acc_lo, W.acc_lo + c->cap};
+    int4* ahi[2] = {W.acc_hi, W.acc_hi + c->cap};
+    unsigned long long* asum[2] = {W.acc_sum, W.acc_sum + c->cap};
+    unsigned int* ak[2] = {W.acc_k, W.acc_k + c->cap};
+    unsigned int* ak2[2] = {W.acc_k2, W.acc_k2 + c->cap};
+    unsigned long long* akey[2] = {W.acc_key, W.acc_key + 3 * c->cap};
+    // buffers: set[] alternates between mset[1] and mset[0]
+    unsigned int* sets[2] = {W.mset[1], W.mset[0]};
+    APR_LAUNCH(c, k_seg_setup, nblocks(M, 256), 256, M, lo_off, W.seg_lo[0], W.seg_hi[0], alo[0],
+               ahi[0], asum[0], ak[0], ak2[0], akey[0], key2[0]);
+    int maxm = 0;
+    for (int l = 1; l <= lmax; ++l) maxm = max(maxm, off[l + 1] - off[l]);
+    int cur = 0;
+    const int nb = nblocks(M, 256);
+    int rounds_left = 0;
+    if (maxm > TREE_LOCAL) {
+        int est = 1;
+        while ((TREE_LOCAL << est) < maxm) ++est;
+        rounds_left = est + 1;
+    }
+    for (int total = 0; rounds_left > 0 && total < 64 + 4 * 32; ) {
+        for (int r = 0; r < rounds_left; ++r, ++total) {
+            APR_LAUNCH(c, k_tree_bbox, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur],
+                       W.seg_hi[cur], W.xi, alo[cur], ahi[cur]);
+            APR_LAUNCH(c, k_tree_sum, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur], W.seg_hi[cur],
+                       W.xi, alo[cur], ahi[cur], asum[cur]);
+            APR_LAUNCH(c, k_tree_count, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur],
+                       W.seg_hi[cur], W.xi, alo[cur], ahi[cur], asum[cur], ak[cur], ak2[cur]);
+            APR_LAUNCH(c, k_tree_key, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur], W.seg_hi[cur],
+                       W.xi, alo[cur], ahi[cur], asum[cur], ak[cur], ak2[cur], akey[cur], key2[cur]);
+            APR_LAUNCH(c, k_tree_flag, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur],
+                       W.seg_hi[cur], W.xi, alo[cur], ahi[cur], asum[cur], ak[cur], ak2[cur],
+                       akey[cur], key2[cur], W.lflag);
+            scan_u32(c, W.lflag, W.uscan, M, nullptr);
+            cudaMemsetAsync(&W.status[ST_MAXSEG], 0, sizeof(int), st);
+            const int nx = cur ^ 1;
+            APR_LAUNCH(c, k_tree_scatter, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur],
+                       W.seg_hi[cur], ak[cur], ak2[cur], W.lflag, W.uscan, sets[nx], W.seg_lo[nx],
+                       W.seg_hi[nx], alo[nx], ahi[nx], asum[nx], ak[nx], ak2[nx], akey[nx], key2[nx],
+                       &W.status[ST_MAXSEG]);
+            cur = nx;
+        }
+        cudaMemcpyAsync(c->hbuf, &W.status[ST_MAXSEG], sizeof(int), cudaMemcpyDeviceToHost, st);
+        s = cuda_check(c, cudaStreamSynchronize(st), "pairing tree");
+        if (s != APR_OK) return s;
+        rounds_left = ((int*)c->hbuf)[0] > TREE_LOCAL ? 2 : 0;
+    }
+    if (rounds_left > 0) return fail(c, APR_ERR_STATE, "pairing tree did not reach its leaves");
+    if (!c->tree_smem_set) {
+        s = cuda_check(c, cudaFuncSetAttribute(k_tree_local,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sizeof(LocalSmem)), "tree smem");
+        if (s != APR_OK) return s;
+        c->tree_smem_set = true;
+    }
+    APR_LAUNCH_SMEM(c, k_tree_local, nblocks(M, TREE_LOCAL), TREE_LOC_THREADS, sizeof(LocalSmem), M,
+                    W.xi, sets[cur], W.seg_lo[cur], W.seg_hi[cur]);
+    *set_out = sets[cur];
+    *lo_out = W.seg_lo[cur];
+    *hi_out = W.seg_hi[cur];
+    return cuda_check(c, cudaGetLastError(), "pairing tree");
+}
+
+__global__ void k_pairs_out(int m, const unsigned int* __restrict__ set, long long* __restrict__ out)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < 2 * npairs) out[j] = set[j];
+    if (j < m) out[j] = set[j];
 }
 
 apr_status merge_pairs_debug(apr_ctx* c, int level, long long* pairs, long long cap,
                              long long* npairs, long long* spare)
 {
+    *npairs = 0;
+    *spare = -1;
+    if (level > c->cfg.lmax || c->n == 0) return APR_OK;
     apr_status s = quantise(c);
     if (s != APR_OK) return s;
-    int m, cur;
-    s = pair_tree(c, level, &m, spare, &cur);
+    int off[APR_MAXLEV + 2];
+    unsigned int* set;
+    int *lo, *hi;
+    s = pair_trees(c, off, &set, &lo, &hi);
     if (s != APR_OK) return s;
-    *npairs = m / 2;
-    if (m / 2 > cap) return fail(c, APR_ERR_ARG, "merge_pairs: cap too small");
+    const int a = off[level], m = off[level + 1] - a, me = m & ~1;
+    *npairs = me / 2;
+    if (me / 2 > cap) return fail(c, APR_ERR_ARG, "merge_pairs: cap too small");
     if (m == 0) return APR_OK;
     long long* dev = (long long*)c->W.tmp8;
-    APR_LAUNCH(c, k_pairs_out, nblocks(m, 256), 256, m / 2, c->W.mset[cur], dev);
-    s = cuda_check(c, cudaMemcpyAsync(pairs, dev, sizeof(long long) * m, cudaMemcpyDeviceToHost,
+    APR_LAUNCH(c, k_pairs_out, nblocks(m, 256), 256, m, set + a, dev);
+    std::vector<long long> buf(m);
+    s = cuda_check(c, cudaMemcpyAsync(buf.data(), dev, sizeof(long long) * m, cudaMemcpyDeviceToHost,
                                       c->stream), "pairs out");
     if (s != APR_OK) return s;
-    return cuda_check(c, cudaStreamSynchronize(c->stream), "pairs out");
+    s = cuda_check(c, cudaStreamSynchronize(c->stream), "pairs out");
+    if (s != APR_OK) return s;
+    for (int j = 0; j < me; ++j) pairs[j] = buf[j];
+    if (m % 2) *spare = buf[m - 1];
+    return APR_OK;
 }
 
 // ------------------------------------------------------------ compaction
@@ -698,29 +1013,27 @@ static apr_status split_merge_body(apr_ctx* c, apr_counts* cnt)
         }
         cnt->n_split[l] = ns;
     }
-    bool any_merge = false;
     if (c->cfg.lmax >= 1 && c->n > 0) {
         s = quantise(c);
         if (s != APR_OK) return s;
-    }
-    for (int l = c->cfg.lmax; l >= 1; --l) {
-        if (c->n == 0) break;
-        int m, cur;
-        long long spare;
-        s = pair_tree(c, l, &m, &spare, &cur);
+        int off[APR_MAXLEV + 2];
+        unsigned int* set;
+        int *lo, *hi;
+        s = pair_trees(c, off, &set, &lo, &hi);
         if (s != APR_OK) return s;
-        cnt->n_spare[l] = spare >= 0 ? 1 : 0;
-        if (m < 2) continue;
-        cudaMemsetAsync(&W.status[ST_COUNT_B], 0, sizeof(int), st);
-        APR_LAUNCH(c, k_merge_apply, nblocks(m / 2, 256), 256, c->dc, rg, m / 2, l, W.mset[cur], c->p,
-                                                         &W.status[ST_COUNT_B]);
-        cudaMemcpyAsync(c->hbuf, &W.status[ST_COUNT_B], sizeof(int), cudaMemcpyDeviceToHost, st);
-        s = cuda_check(c, cudaStreamSynchronize(st), "merge");
-        if (s != APR_OK) return s;
-        cnt->n_merge[l] = ((int*)c->hbuf)[0];
-        if (cnt->n_merge[l]) any_merge = true;
+        const int M = off[c->cfg.lmax + 1];
+        for (int l = 1; l <= c->cfg.lmax; ++l) cnt->n_spare[l] = (off[l + 1] - off[l]) & 1;
+        if (M >= 2) {
+            cudaMemsetAsync(&W.status[ST_MERGES], 0, sizeof(int) * APR_MAXLEV, st);
+            APR_LAUNCH(c, k_merge_apply, nblocks(M, 256), 256, c->dc, rg, M, set, lo, hi, c->p,
+                       &W.status[ST_MERGES]);
+            cudaMemcpyAsync(c->hbuf, &W.status[ST_MERGES], sizeof(int) * APR_MAXLEV,
+                            cudaMemcpyDeviceToHost, st);
+            s = cuda_check(c, cudaStreamSynchronize(st), "merge");
+            if (s != APR_OK) return s;
+            for (int l = 1; l <= c->cfg.lmax; ++l) cnt->n_merge[l] = ((int*)c->hbuf)[l];
+        }
     }
-    (void)any_merge;
     long long removed = 0;
     if (c->n > 0) {
         s = compact(c, &removed);
@@ -753,22 +1066,34 @@ __device__ void block_reduce_store(double (&v)[NV], double* partials)
     }
 }
 
-__global__ void k_reduce_final(int nblk, int nv, const double* __restrict__ partials,
-                               double* __restrict__ out, int op_min)
+// fixed-shape reduction of the block partials (one block): deterministic
+__global__ void __launch_bounds__(256) k_reduce_final(int nblk, int nv,
+                                                      const double* __restrict__ partials,
+                                                      double* __restrict__ out, int op_min)
 {
-    int k = threadIdx.x;
-    if (k >= nv) return;
-    double x = op_min ? INFINITY : 0.0;
-    for (int b = 0; b < nblk; ++b) {
-        double y = partials[b * 32 + k];
-        x = op_min ? fmin(x, y) : x + y;
+    __shared__ double sm[256];
+    for (int k = 0; k < nv; ++k) {
+        double x = op_min ? INFINITY : 0.0;
+        for (int b = threadIdx.x; b < nblk; b += 256) {
+            double y = partials[b * 32 + k];
+            x = op_min ? fmin(x, y) : x + y;
+        }
+        sm[threadIdx.x] = x;
+        __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if (threadIdx.x < s)
+                sm[threadIdx.x] = op_min ? fmin(sm[threadIdx.x], sm[threadIdx.x + s])
+                                         : sm[threadIdx.x] + sm[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[k] = sm[0];
+        __syncthreads();
     }
-    out[k] = x;
 }
 
 static apr_status reduce_readback(apr_ctx* c, int nv, int op_min, double* host)
 {
-    APR_LAUNCH(c, k_reduce_final, 1, 32, RED_BLOCKS, nv, c->W.red, c->W.redout, op_min);
+    APR_LAUNCH(c, k_reduce_final, 1, 256, RED_BLOCKS, nv, c->W.red, c->W.redout, op_min);
     cudaMemcpyAsync(c->hbuf, c->W.redout, sizeof(double) * nv, cudaMemcpyDeviceToHost, c->stream);
     apr_status s = cuda_check(c, cudaStreamSynchronize(c->stream), "reduce");
     if (s != APR_OK) return s;
