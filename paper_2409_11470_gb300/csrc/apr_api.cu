@@ -111,6 +111,7 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.scan_tmp = (unsigned int*)take(4 * (scan_n / 256 + 8192));
     w.pk = (int4*)take(16 * C);
     w.sthr = (unsigned long long*)take(8 * C);
+    w.sreach = (unsigned int*)take(4 * C);
     w.sh = (double*)take(8 * C);
     if (f64) {
         w.sx = (double*)take(8 * C);
@@ -141,7 +142,8 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.cmark = (int*)take(4 * C);
     w.cand = (int2*)take(8 * (size_t)MAX_CAND * C);
     w.ncand = (int*)take(4 * C);
-    w.nbr = (unsigned int*)take(4 * K * C);
+    // the list memory doubles as compaction scratch (20 x 8 bytes per particle)
+    w.nbr = (unsigned int*)take((4 * K > 160 ? 4 * K : 160) * C);
     w.ncnt = (int*)take(4 * C);
     w.status = (int*)take(4 * 64);
     w.counters = (unsigned long long*)take(8 * 16);
@@ -157,10 +159,10 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.seg_hi[1] = (int*)take(4 * C);
     w.acc_lo = (int4*)take(16 * C * 2);
     w.acc_hi = (int4*)take(16 * C * 2);
-    w.acc_sum = (unsigned long long*)take(8 * C * 2);
+    w.acc_sum = (unsigned long long*)take(8 * C * 6);
     w.acc_k = (unsigned int*)take(4 * C * 2);
     w.acc_k2 = (unsigned int*)take(4 * C * 2);
-    w.acc_key = (unsigned long long*)take(8 * C * 4);
+    w.acc_key = (unsigned long long*)take(8 * C * 8);
     w.lflag = (unsigned int*)take(4 * C);
     w.red = (double*)take(8 * 32 * (size_t)RED_BLOCKS);
     w.redout = (double*)take(8 * 32);
@@ -268,8 +270,6 @@ static apr_status run_density(apr_ctx* c, long long* noconv_out)
         // they also hold every force pair, r < 2 max(h_a, h_b)
         s = index_lists(c, 1, DENSITY_REACH, true);
         if (s != APR_OK) return s;
-        s = check_overflow(c);
-        if (s != APR_OK) return s;
         s = density_pass(c, &unc, &noconv);
         if (s != APR_OK) return s;
         shrinks += c->last_shrink;
@@ -351,6 +351,8 @@ apr_status apr_create(apr_ctx** out, const apr_config* cfg, void* stream)
     c->nreg = c->nsink = 0;
     c->ncell = 0;
     c->last_shrink = 0;
+    c->dt_valid = false;
+    c->dt_next = 0.0;
     c->tree_smem_set = false;
     c->launches = 0;
     c->prof = false;
@@ -413,6 +415,7 @@ apr_status apr_bind(apr_ctx* c, const apr_particles* p, long long n, long long c
     if (s != APR_OK) return s;
     c->bound = true;
     c->have_force = false;
+    c->dt_valid = false;
     return APR_OK;
 }
 
@@ -457,6 +460,7 @@ apr_status apr_sph_density(apr_ctx* c, long long* n_unconverged)
 {
     if (!c) return APR_ERR_ARG;
     if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    c->dt_valid = false;
     return run_density(c, n_unconverged);
 }
 
@@ -464,6 +468,7 @@ apr_status apr_sph_force(apr_ctx* c)
 {
     if (!c) return APR_ERR_ARG;
     if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    c->dt_valid = false;
     return run_force(c, false);
 }
 
@@ -473,6 +478,7 @@ apr_status apr_split_merge(apr_ctx* c, long long* n_out, apr_counts* counts)
     if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
     apr_counts cnt;
     track_regions(c);
+    c->dt_valid = false;
     apr_status s = split_merge_pass(c, &cnt);
     if (n_out) *n_out = c->n;
     if (counts) *counts = cnt;
@@ -503,6 +509,10 @@ apr_status apr_init(apr_ctx* c, int* passes)
     if (s != APR_OK) return s;
     s = run_force(c, true);
     if (passes) *passes = np;
+    if (s != APR_OK) return s;
+    apr_stats st_local;
+    s = compute_stats_dt(c, &st_local, &c->dt_next);
+    c->dt_valid = s == APR_OK;
     return s;
 }
 
@@ -510,6 +520,10 @@ apr_status apr_timestep(apr_ctx* c, double* dt)
 {
     if (!c || !dt) return APR_ERR_ARG;
     if (!c->bound || !c->have_force) return fail(c, APR_ERR_STATE, "no force pass yet");
+    if (c->dt_valid) {
+        *dt = c->dt_next;
+        return APR_OK;
+    }
     return compute_timestep(c, dt);
 }
 
@@ -527,8 +541,12 @@ apr_status apr_step(apr_ctx* c, double dt, double* dt_used, apr_stats* stats,
     if (!c->bound || !c->have_force) return fail(c, APR_ERR_STATE, "apr_init or a force pass first");
     apr_status s;
     if (!(dt > 0.0)) {
-        s = compute_timestep(c, &dt);
-        if (s != APR_OK) return s;
+        if (c->dt_valid) {
+            dt = c->dt_next;
+        } else {
+            s = compute_timestep(c, &dt);
+            if (s != APR_OK) return s;
+        }
     }
     const double hdt = 0.5 * dt;
     int ps = prof_begin(c, APR_PROF_OTHER);
@@ -555,11 +573,12 @@ apr_status apr_step(apr_ctx* c, double dt, double* dt_used, apr_stats* stats,
     if (s != APR_OK) return s;
     if (dt_used) *dt_used = dt;
     if (counts) *counts = cnt;
-    if (stats) {
-        s = compute_stats(c, stats);
-        if (s != APR_OK) return s;
-    }
-    return cuda_check(c, cudaStreamSynchronize(c->stream), "step");
+    // conservation sums and the next step's limit in one reduction
+    apr_stats st_local;
+    s = compute_stats_dt(c, stats ? stats : &st_local, &c->dt_next);
+    if (s != APR_OK) return s;
+    c->dt_valid = true;
+    return APR_OK;
 }
 
 apr_status apr_neighbour_lists(apr_ctx* c, int mode, long long* offsets, int* idx, long long cap,

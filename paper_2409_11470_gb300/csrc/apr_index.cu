@@ -133,7 +133,7 @@ __global__ void k_quantise(DevCfg dc, const double* __restrict__ x, const double
     long long qx = quant1(dc, 0, x[i]), qy = quant1(dc, 1, y[i]), qz = quant1(dc, 2, z[i]);
     xi[i] = make_int4((int)qx, (int)qy, (int)qz, (int)level[i]);
     if (key) {
-        const int sh = COORD_BITS - 21;
+        const int sh = COORD_BITS - KEY_BITS;
         key[i] = (spread21((unsigned)(qx >> sh)) << 2) | (spread21((unsigned)(qy >> sh)) << 1) |
                  spread21((unsigned)(qz >> sh));
         val[i] = (unsigned)i;
@@ -237,7 +237,7 @@ static apr_status radix_sort(apr_ctx* c, long long n)
     Workspace& W = c->W;
     const int ntiles = nblocks(n, RADIX_TILE);
     int cur = 0;
-    for (int shift = 0; shift < 64; shift += 8) {
+    for (int shift = 0; shift < 3 * KEY_BITS; shift += 8) {
         APR_LAUNCH(c, k_radix_hist, ntiles, 256, W.key[cur], n, shift, W.hist, ntiles);
         scan_u32(c, W.hist, W.hist + (size_t)256 * ntiles, (long long)256 * ntiles, nullptr);
         APR_LAUNCH(c, k_radix_scatter, ntiles, 256, W.key[cur], W.val[cur], W.key[cur ^ 1],
@@ -551,7 +551,7 @@ __device__ __forceinline__ NodeBox node_box(int c, const int4* __restrict__ pk,
 
 // candidate cells: traverse the tree from the root, keep cells within reach.
 // mode 0: the cell's own reach (gather); otherwise max of both reaches (symmetric).
-__global__ void k_candidates(DevCfg dc, int mode, int ncell, int n,
+__global__ void k_candidates(DevCfg dc, int mode, const int* __restrict__ ncell_dev, int n,
                              const int* __restrict__ cell_node, const int* __restrict__ left,
                              const int* __restrict__ right, const int4* __restrict__ pk,
                              const unsigned long long* __restrict__ sthr,
@@ -560,8 +560,9 @@ __global__ void k_candidates(DevCfg dc, int mode, int ncell, int n,
                              int2* __restrict__ cand, int* __restrict__ ncand, int* status,
                              int graceful)
 {
-    int cid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cid >= ncell) return;
+    const int ncell = *ncell_dev;
+    for (int cid = blockIdx.x * blockDim.x + threadIdx.x; cid < ncell;
+         cid += gridDim.x * blockDim.x) {
     NodeBox me = node_box(cell_node[cid], pk, sthr, nlo, nhi, nthr);
     const unsigned long long thr_self = me.thr;
     int stack[128];
@@ -587,68 +588,92 @@ __global__ void k_candidates(DevCfg dc, int mode, int ncell, int n,
     }
     ncand[cid] = overflow ? -1 : k;
     if (overflow && !graceful) atomicOr(&status[ST_CAND_OVERFLOW], 1);
+    }
 }
 
+// per particle: the squared-distance threshold and the smallest integer R with
+// R^2 >= thr (every neighbour has |dx|, |dy|, |dz| < R on the lattice)
 __global__ void k_thresholds(DevCfg dc, long long n, double reach, const double* __restrict__ sh,
-                             unsigned long long* __restrict__ thr)
+                             unsigned long long* __restrict__ thr, unsigned int* __restrict__ rint)
 {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < n) thr[s] = neighbour_threshold(reach * sh[s], dc.delta);
+    if (s >= n) return;
+    const unsigned long long t = neighbour_threshold(reach * sh[s], dc.delta);
+    thr[s] = t;
+    unsigned long long r = (unsigned long long)ceil(sqrt((double)t));
+    while (r > 0 && (r - 1) * (r - 1) >= t) --r;
+    while (r * r < t) ++r;
+    rint[s] = r > 0xffffffffULL ? 0xffffffffu : (unsigned)r;
 }
 
-// exact lists: warp per cell; candidate particles broadcast lane to lane
-__global__ void __launch_bounds__(128) k_lists(DevCfg dc, int mode, int ncell, int n, long long cap,
-                                               const int* __restrict__ cell_first,
-                                               const int* __restrict__ cell_cnt,
-                                               const int2* __restrict__ cand,
-                                               const int* __restrict__ ncand,
-                                               const int4* __restrict__ pk,
-                                               const unsigned long long* __restrict__ thr,
-                                               unsigned int* __restrict__ nbr, int* __restrict__ ncnt,
-                                               int* status, int graceful)
+// exact lists: warp per cell; each candidate cell is staged in shared memory
+// and read back as broadcasts.  A candidate is rejected early by the exact
+// per-axis test |d| >= R (R^2 >= thr); the rest take the exact 64-bit r^2 < thr.
+template <int PX, int PY, int PZ, int SYM>
+__global__ void __launch_bounds__(128)
+    k_lists(DevCfg dc, const int* __restrict__ ncell_dev, int n, long long cap,
+            const int* __restrict__ cell_first,
+            const int* __restrict__ cell_cnt, const int2* __restrict__ cand,
+            const int* __restrict__ ncand, const int4* __restrict__ pk,
+            const unsigned long long* __restrict__ thr, const unsigned int* __restrict__ rint,
+            unsigned int* __restrict__ nbr, int* __restrict__ ncnt, int* status, int graceful)
 {
-    const int lane = threadIdx.x & 31;
-    const int cid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (cid >= ncell) return;
+    __shared__ int4 cpk[4][CELL_MAX];
+    __shared__ unsigned long long cth[4][CELL_MAX];
+    __shared__ unsigned int crr[4][CELL_MAX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int ncell = *ncell_dev;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int cid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; cid < ncell; cid += nwarps) {
     const int first = cell_first[cid], cnt = cell_cnt[cid];
-    if (first < 0 || cnt < 1 || cnt > CELL_MAX || first + cnt > n) return;
+    if (first < 0 || cnt < 1 || cnt > CELL_MAX || first + cnt > n) continue;
     const bool own = lane < cnt;
     const int a = first + (own ? lane : 0);
     const int4 pa = pk[a];
     const unsigned long long ta = thr[a];
+    const unsigned int Ra = own ? rint[a] : 0u;  // 0: every test fails for idle lanes
     const int Lx = (int)dc.Lint[0], Ly = (int)dc.Lint[1], Lz = (int)dc.Lint[2];
-    const int px = dc.periodic[0], py = dc.periodic[1], pz = dc.periodic[2];
+    const int Hx = Lx >> 1, Hy = Ly >> 1, Hz = Lz >> 1;
     const int K = dc.max_neigh;
     int m = 0;
     const int nc = ncand[cid];
     if (nc < 0) {  // candidate list overflowed: every list of this cell is incomplete
         if (own) ncnt[a] = -1;
         if (!graceful && lane == 0) atomicOr(&status[ST_NEIGH_OVERFLOW], 1);
-        return;
+        continue;
     }
     for (int j = 0; j < nc; ++j) {
-        int2 cb = cand[(long long)cid * MAX_CAND + j];
+        const int2 cb = cand[(long long)cid * MAX_CAND + j];
         if (cb.x < 0 || cb.y < 0 || cb.y > CELL_MAX || cb.x + cb.y > n) continue;
-        int4 pb = make_int4(0, 0, 0, 0);
-        unsigned long long tb = 0;
+        __syncwarp();
         if (lane < cb.y) {
-            pb = pk[cb.x + lane];
-            tb = thr[cb.x + lane];
+            cpk[w][lane] = pk[cb.x + lane];
+            cth[w][lane] = thr[cb.x + lane];
+            crr[w][lane] = rint[cb.x + lane];
         }
+        __syncwarp();
         for (int l = 0; l < cb.y; ++l) {
-            int bx = __shfl_sync(0xffffffffu, pb.x, l);
-            int by = __shfl_sync(0xffffffffu, pb.y, l);
-            int bz = __shfl_sync(0xffffffffu, pb.z, l);
-            unsigned long long t = __shfl_sync(0xffffffffu, tb, l);
-            int b = cb.x + l;
-            if (!own || b == a) continue;
-            int dx = min_image32(pa.x - bx, px, Lx);
-            int dy = min_image32(pa.y - by, py, Ly);
-            int dz = min_image32(pa.z - bz, pz, Lz);
-            unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
-                                    (unsigned long long)((long long)dy * dy) +
-                                    (unsigned long long)((long long)dz * dz);
-            unsigned long long th = (mode != 0 && t > ta) ? t : ta;
+            const int4 q = cpk[w][l];
+            int dx = pa.x - q.x, dy = pa.y - q.y, dz = pa.z - q.z;
+            if (PX) dx = dx > Hx ? dx - Lx : (dx < -Hx ? dx + Lx : dx);
+            if (PY) dy = dy > Hy ? dy - Ly : (dy < -Hy ? dy + Ly : dy);
+            if (PZ) dz = dz > Hz ? dz - Lz : (dz < -Hz ? dz + Lz : dz);
+            unsigned int R = Ra;
+            if (SYM) {
+                const unsigned int Rb = crr[w][l];
+                R = (own && Rb > R) ? Rb : R;
+            }
+            if ((unsigned)abs(dx) >= R || (unsigned)abs(dy) >= R || (unsigned)abs(dz) >= R) continue;
+            const int b = cb.x + l;
+            if (b == a) continue;
+            const unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
+                                          (unsigned long long)((long long)dy * dy) +
+                                          (unsigned long long)((long long)dz * dz);
+            unsigned long long th = ta;
+            if (SYM) {
+                const unsigned long long t = cth[w][l];
+                th = t > th ? t : th;
+            }
             if (r2 < th) {
                 if (m < K) nbr[(long long)m * cap + a] = (unsigned)b;
                 ++m;
@@ -659,6 +684,34 @@ __global__ void __launch_bounds__(128) k_lists(DevCfg dc, int mode, int ncell, i
         ncnt[a] = m > K ? -1 : m;
         if (m > K && !graceful) atomicOr(&status[ST_NEIGH_OVERFLOW], 1);
     }
+    __syncwarp();
+    }
+}
+
+template <int SYM>
+static void launch_lists(apr_ctx* c, const int* ncell_dev, int n, bool graceful)
+{
+    Workspace& W = c->W;
+    const int mask = (c->dc.periodic[0] ? 1 : 0) | (c->dc.periodic[1] ? 2 : 0) |
+                     (c->dc.periodic[2] ? 4 : 0);
+    const int grid = min(nblocks((long long)n * 32, 128), 152 * 16);
+#define APR_LISTS_CASE(M, X, Y, Z)                                                                   \
+    case M:                                                                                          \
+        APR_LAUNCH(c, (k_lists<X, Y, Z, SYM>), grid, 128, c->dc, ncell_dev, n, c->cap, W.cell_first, \
+                   W.cell_cnt, W.cand, W.ncand, W.pk, W.sthr, W.sreach, W.nbr, W.ncnt, W.status,     \
+                   graceful ? 1 : 0);                                                                \
+        break;
+    switch (mask) {
+        APR_LISTS_CASE(0, 0, 0, 0)
+        APR_LISTS_CASE(1, 1, 0, 0)
+        APR_LISTS_CASE(2, 0, 1, 0)
+        APR_LISTS_CASE(3, 1, 1, 0)
+        APR_LISTS_CASE(4, 0, 0, 1)
+        APR_LISTS_CASE(5, 1, 0, 1)
+        APR_LISTS_CASE(6, 0, 1, 1)
+        APR_LISTS_CASE(7, 1, 1, 1)
+    }
+#undef APR_LISTS_CASE
 }
 
 apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful)
@@ -677,22 +730,19 @@ apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful)
     else
         APR_LAUNCH(c, k_cells_mark, nblocks(n - 1, 256), 256, n, W.left, W.right, W.nlo, W.nhi, W.cflag,
                                                            W.cmark);
-    scan_u32(c, W.cflag, W.cscan, n, (unsigned*)&W.status[ST_COUNT_A]);
+    int* ncell_dev = &W.status[ST_NCELL];
+    scan_u32(c, W.cflag, W.cscan, n, (unsigned*)ncell_dev);
     APR_LAUNCH(c, k_cells_compact, nblocks(n, 256), 256, n, W.cflag, W.cscan, W.cmark, W.nlo,
-                                                     W.cell_first, W.cell_cnt, W.cell_node);
-    cudaMemcpyAsync(c->hbuf, &W.status[ST_COUNT_A], sizeof(int), cudaMemcpyDeviceToHost, st);
-    apr_status s = cuda_check(c, cudaStreamSynchronize(st), "cells");
-    if (s != APR_OK) return s;
-    int ncell = ((int*)c->hbuf)[0];
-    c->ncell = ncell;
-    APR_LAUNCH(c, k_thresholds, nblocks(n, 256), 256, c->dc, n, reach, W.sh, W.sthr);
+               W.cell_first, W.cell_cnt, W.cell_node);
+    APR_LAUNCH(c, k_thresholds, nblocks(n, 256), 256, c->dc, n, reach, W.sh, W.sthr, W.sreach);
     if (n >= 2) APR_LAUNCH(c, k_node_thr, nblocks(n - 1, 256), 256, c->dc, n, reach, W.nhmax, W.nthr);
-    APR_LAUNCH(c, k_candidates, nblocks(ncell, 128), 128, c->dc, mode, ncell, n, W.cell_node, W.left,
-               W.right, W.pk, W.sthr, W.nlo, W.nhi, W.nthr, W.cand, W.ncand, W.status,
-               graceful ? 1 : 0);
-    APR_LAUNCH(c, k_lists, nblocks((long long)ncell * 32, 128), 128, 
-        c->dc, mode, ncell, n, c->cap, W.cell_first, W.cell_cnt, W.cand, W.ncand, W.pk, W.sthr,
-        W.nbr, W.ncnt, W.status, graceful ? 1 : 0);
+    APR_LAUNCH(c, k_candidates, min(nblocks(n, 32), 152 * 16), 32, c->dc, mode, ncell_dev, n,
+               W.cell_node, W.left, W.right, W.pk, W.sthr, W.nlo, W.nhi, W.nthr, W.cand, W.ncand,
+               W.status, graceful ? 1 : 0);
+    if (mode == 0)
+        launch_lists<0>(c, ncell_dev, n, graceful);
+    else
+        launch_lists<1>(c, ncell_dev, n, graceful);
     prof_end(c, ps);
     return cuda_check(c, cudaGetLastError(), "lists");
 }

@@ -15,6 +15,7 @@ namespace apr {
 constexpr int COORD_BITS = 30;               // lattice coordinates are in [0, 2^30)
 constexpr long long COORD_MAX = (1LL << COORD_BITS) - 1;
 constexpr int CELL_MAX = 32;                 // particles per cell (one warp)
+constexpr int KEY_BITS = 16;                 // Morton key bits per axis (48-bit keys, 6 passes)
 constexpr int MAX_CAND = 128;                // candidate cells per cell
 constexpr int RADIX_TILE = 2048;             // items per radix-sort block (256 x 8)
 constexpr int SCAN_BLOCK = 1024;             // items per scan block (256 x 4)
@@ -33,6 +34,7 @@ enum {
     ST_MAXSEG = 6,           // merge tree: largest open segment
     ST_TREE_BAD = 7,         // radix tree walk left its bounds (must never happen)
     ST_SHRINK = 8,           // density: lists overflowed, h shrunk for a retry
+    ST_NCELL = 9,            // number of cells of the current index
     ST_BINS = 16,            // merge: first slot of each level's candidates (10 words)
     ST_MERGES = 32,          // merge: merges per level (8 words)
     ST_NSTATUS = 16
@@ -106,6 +108,7 @@ struct Workspace {
     unsigned long long* skey; // sorted keys (aliases key[0] or key[1])
     int4* pk;                 // sorted lattice coordinates + level
     unsigned long long* sthr; // sorted neighbour thresholds of the current list
+    unsigned int* sreach;     // smallest integer R with R^2 >= sthr
     double* sh;               // sorted h (float64)
     float4* fA;               // FP32 force data: hinv, P/(Omega rho^2), cs, rho
     float4* fV;               // FP32 velocities + u
@@ -188,6 +191,8 @@ struct apr_ctx {
     int ncell;
     int last_shrink;
     bool tree_smem_set;       // dynamic shared memory opt-in of the pairing-tree kernel
+    bool dt_valid;            // dt_next belongs to the current forces
+    double dt_next;
     // profiling
     long long launches;
     bool prof;
@@ -276,6 +281,7 @@ apr_status kick(apr_ctx* c, double hdt);
 apr_status drift(apr_ctx* c, double dt);
 apr_status compute_stats(apr_ctx* c, apr_stats* st);
 apr_status compute_timestep(apr_ctx* c, double* dt);
+apr_status compute_stats_dt(apr_ctx* c, apr_stats* st, double* dt);
 apr_status compact(apr_ctx* c, long long* removed);
 
 inline int nblocks(long long n, int bs) { return (int)((n + bs - 1) / bs); }

@@ -128,27 +128,41 @@ __device__ __forceinline__ double wrap1(const DevCfg& dc, int k, double x)
     return x;
 }
 
-__global__ void k_split_flag(DevCfg dc, DevRegions rg, long long n, int level,
-                             const double* __restrict__ x, const double* __restrict__ y,
-                             const double* __restrict__ z, const unsigned char* __restrict__ lev,
-                             const unsigned char* __restrict__ flags, unsigned int* __restrict__ out)
+// split parents of every level: key = level for a parent, 255 otherwise.  A stable
+// sort by this key ranks the parents by (level, index), which is the order in
+// which level-by-level passes (lowest level first) append the new children.
+__global__ void k_split_keys(DevCfg dc, DevRegions rg, long long n, const double* __restrict__ x,
+                             const double* __restrict__ y, const double* __restrict__ z,
+                             const unsigned char* __restrict__ lev,
+                             const unsigned char* __restrict__ flags,
+                             unsigned long long* __restrict__ key, unsigned int* __restrict__ val)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    unsigned f = 0;
-    if (lev[i] == level && !(flags[i] & (APR_FLAG_CHANGED | APR_FLAG_FIXED | APR_FLAG_DEAD)))
-        f = target_level(dc, rg, x[i], y[i], z[i], nullptr) > level ? 1u : 0u;
-    out[i] = f;
+    const int l = lev[i];
+    bool split = false;
+    if (l < dc.lmax && !(flags[i] & (APR_FLAG_CHANGED | APR_FLAG_FIXED | APR_FLAG_DEAD)))
+        split = target_level(dc, rg, x[i], y[i], z[i], nullptr) > l;
+    key[i] = split ? (unsigned long long)l : 255ULL;
+    val[i] = (unsigned)i;
 }
 
-__global__ void k_split_apply(DevCfg dc, DevRegions rg, long long n, int level,
-                              unsigned long long step, long long next_id,
-                              const unsigned int* __restrict__ flag,
-                              const unsigned int* __restrict__ rank, apr_particles p)
+__global__ void k_split_rank(int total, const unsigned int* __restrict__ sorted,
+                             unsigned int* __restrict__ rank)
 {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || !flag[i]) return;
-    const long long j = n + rank[i];
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < total) rank[sorted[r]] = (unsigned)r;
+}
+
+__global__ void k_split_apply(DevCfg dc, DevRegions rg, int total, long long n,
+                              unsigned long long step, long long next_id,
+                              const unsigned int* __restrict__ sorted, apr_particles p)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= total) return;
+    const unsigned i = sorted[r];
+    const long long j = n + r;
+    const int level = p.level[i];
     const double px = p.x[i], py = p.y[i], pz = p.z[i];
     int which;
     target_level(dc, rg, px, py, pz, &which);
@@ -186,7 +200,7 @@ __global__ void k_split_apply(DevCfg dc, DevRegions rg, long long n, int level,
     p.level[j] = (unsigned char)(level + 1);
     p.flags[i] = p.flags[i] | APR_FLAG_CHANGED;
     p.flags[j] = p.flags[i];
-    p.id[j] = (unsigned long long)(next_id + (long long)rank[i]);
+    p.id[j] = (unsigned long long)(next_id + (long long)r);
 }
 
 // ------------------------------------------------------------ merge tree
@@ -217,42 +231,8 @@ __global__ void k_merge_keys(long long n, const unsigned char* __restrict__ lev,
     val[i] = (unsigned)i;
 }
 
-__device__ __forceinline__ void acc_reset(int s, int4* acc_lo, int4* acc_hi,
-                                          unsigned long long* acc_sum, unsigned int* acc_k,
-                                          unsigned int* acc_k2, unsigned long long* acc_key,
-                                          unsigned long long* acc_key2)
-{
-    acc_lo[s] = make_int4(INT_MAX, INT_MAX, INT_MAX, 0);
-    acc_hi[s] = make_int4(INT_MIN, INT_MIN, INT_MIN, 0);
-    acc_sum[s] = 0;
-    acc_k[s] = 0;
-    acc_k2[s] = 0;
-    acc_key[s] = 0;
-    acc_key2[s] = ~0ULL;
-}
 
 // one segment per level (even count); an odd level's last candidate is the spare
-__global__ void k_seg_setup(int M, LevelOffsets lo_off, int* __restrict__ lo, int* __restrict__ hi,
-                            int4* acc_lo, int4* acc_hi, unsigned long long* acc_sum,
-                            unsigned int* acc_k, unsigned int* acc_k2, unsigned long long* acc_key,
-                            unsigned long long* acc_key2)
-{
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= M) return;
-    int l = 1;
-    while (l < lo_off.lmax && p >= lo_off.off[l + 1]) ++l;
-    const int a = lo_off.off[l], m = lo_off.off[l + 1] - a, be = a + (m & ~1);
-    if (p < be) {
-        lo[p] = a;
-        hi[p] = be;
-    } else {
-        lo[p] = p;
-        hi[p] = p + 1;
-    }
-    if (p == a && be - a > TREE_LOCAL)
-        acc_reset(a, acc_lo, acc_hi, acc_sum, acc_k, acc_k2, acc_key, acc_key2);
-}
-
 // lanes of one warp that work on the same segment reduce before one atomic
 __device__ __forceinline__ unsigned seg_peers(bool active, int seg)
 {
@@ -313,10 +293,61 @@ __device__ __forceinline__ Cut make_cut(int size, int k_lt, int k_le)
 }
 
 // ---- global rounds: segments larger than `thresh`
+//
+// Per segment (indexed by its first slot): bounding box, coordinate sums on all
+// three axes, counts below the centre of mass for < and <=, and the four keys an
+// odd cut could move (largest (x, index) below / smallest above, for both tests).
 
-__global__ void k_tree_bbox(int m, int thresh, const unsigned int* __restrict__ set,
-                            const int* __restrict__ lo, const int* __restrict__ hi,
-                            const int4* __restrict__ xi, int4* acc_lo, int4* acc_hi)
+struct SegAcc {
+    int4* lo;                    // bbox min (x, y, z)
+    int4* hi;                    // bbox max
+    unsigned long long* sum;     // 3 per segment: sum[3 * s + axis]
+    unsigned int* k;             // count x < com
+    unsigned int* k2;            // count x <= com
+    unsigned long long* key;     // 4 per segment: max low(<), min high(>=), max low(<=), min high(>)
+};
+
+__device__ __forceinline__ void acc_reset_all(const SegAcc& A, int s)
+{
+    A.lo[s] = make_int4(INT_MAX, INT_MAX, INT_MAX, 0);
+    A.hi[s] = make_int4(INT_MIN, INT_MIN, INT_MIN, 0);
+    A.sum[3 * s] = A.sum[3 * s + 1] = A.sum[3 * s + 2] = 0;
+    A.k[s] = 0;
+    A.k2[s] = 0;
+    A.key[4 * s + 0] = 0;
+    A.key[4 * s + 1] = ~0ULL;
+    A.key[4 * s + 2] = 0;
+    A.key[4 * s + 3] = ~0ULL;
+}
+
+__device__ __forceinline__ void warp_sum_u64(unsigned peers, unsigned v, bool leader,
+                                             unsigned long long* dst)
+{
+    unsigned sh = __reduce_add_sync(peers, v >> 15), sl = __reduce_add_sync(peers, v & 0x7fffu);
+    if (leader) atomicAdd(dst, ((unsigned long long)sh << 15) + (unsigned long long)sl);
+}
+
+__global__ void k_seg_setup(int M, LevelOffsets lo_off, int* __restrict__ lo, int* __restrict__ hi,
+                            SegAcc A)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M) return;
+    int l = 1;
+    while (l < lo_off.lmax && p >= lo_off.off[l + 1]) ++l;
+    const int a = lo_off.off[l], m = lo_off.off[l + 1] - a, be = a + (m & ~1);
+    if (p < be) {
+        lo[p] = a;
+        hi[p] = be;
+    } else {
+        lo[p] = p;
+        hi[p] = p + 1;
+    }
+    if (p == a && be - a > TREE_LOCAL) acc_reset_all(A, a);
+}
+
+__global__ void k_tree_bbox_sum(int m, int thresh, const unsigned int* __restrict__ set,
+                                const int* __restrict__ lo, const int* __restrict__ hi,
+                                const int4* __restrict__ xi, SegAcc A)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     bool act = false;
@@ -329,108 +360,90 @@ __global__ void k_tree_bbox(int m, int thresh, const unsigned int* __restrict__ 
     }
     unsigned peers = seg_peers(act, seg);
     if (!act) return;
+    const bool lead = seg_leader(peers);
     int mnx = __reduce_min_sync(peers, q.x), mny = __reduce_min_sync(peers, q.y),
         mnz = __reduce_min_sync(peers, q.z);
     int mxx = __reduce_max_sync(peers, q.x), mxy = __reduce_max_sync(peers, q.y),
         mxz = __reduce_max_sync(peers, q.z);
-    if (seg_leader(peers)) {
-        atomicMin(&acc_lo[seg].x, mnx);
-        atomicMin(&acc_lo[seg].y, mny);
-        atomicMin(&acc_lo[seg].z, mnz);
-        atomicMax(&acc_hi[seg].x, mxx);
-        atomicMax(&acc_hi[seg].y, mxy);
-        atomicMax(&acc_hi[seg].z, mxz);
+    if (lead) {
+        atomicMin(&A.lo[seg].x, mnx);
+        atomicMin(&A.lo[seg].y, mny);
+        atomicMin(&A.lo[seg].z, mnz);
+        atomicMax(&A.hi[seg].x, mxx);
+        atomicMax(&A.hi[seg].y, mxy);
+        atomicMax(&A.hi[seg].z, mxz);
     }
+    warp_sum_u64(peers, (unsigned)q.x, lead, &A.sum[3 * seg + 0]);
+    warp_sum_u64(peers, (unsigned)q.y, lead, &A.sum[3 * seg + 1]);
+    warp_sum_u64(peers, (unsigned)q.z, lead, &A.sum[3 * seg + 2]);
 }
 
-__global__ void k_tree_sum(int m, int thresh, const unsigned int* __restrict__ set,
-                           const int* __restrict__ lo, const int* __restrict__ hi,
-                           const int4* __restrict__ xi, const int4* __restrict__ acc_lo,
-                           const int4* __restrict__ acc_hi, unsigned long long* acc_sum)
+// largest (v, idx) over the lanes in `peers` that have pred; 0 if none
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned peers, bool pred, int v,
+                                                           unsigned idx)
+{
+    int vm = __reduce_max_sync(peers, pred ? v : -1);
+    unsigned im = __reduce_max_sync(peers, (pred && v == vm) ? idx : 0u);
+    return vm < 0 ? 0ULL : (((unsigned long long)vm << 32) | im);
+}
+
+// smallest (v, idx) over the lanes in `peers` that have pred; ~0 if none
+__device__ __forceinline__ unsigned long long warp_min_key(unsigned peers, bool pred, int v,
+                                                           unsigned idx)
+{
+    int vm = __reduce_min_sync(peers, pred ? v : INT_MAX);
+    unsigned im = __reduce_min_sync(peers, (pred && v == vm) ? idx : 0xffffffffu);
+    return vm == INT_MAX ? ~0ULL : (((unsigned long long)vm << 32) | im);
+}
+
+__device__ __forceinline__ long long seg_com(const SegAcc& A, int seg, int size, int ax)
+{
+    return (long long)(A.sum[3 * seg + ax] / (unsigned long long)size);
+}
+
+__global__ void k_tree_count_key(int m, int thresh, const unsigned int* __restrict__ set,
+                                 const int* __restrict__ lo, const int* __restrict__ hi,
+                                 const int4* __restrict__ xi, SegAcc A)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     bool act = false;
-    int seg = 0;
-    unsigned v = 0;
-    if (p < m) {
-        seg = lo[p];
-        act = hi[p] - seg > thresh;
-        if (act) v = (unsigned)comp(xi[set[p]], seg_axis(acc_lo[seg], acc_hi[seg]));
-    }
-    unsigned peers = seg_peers(act, seg);
-    if (!act) return;
-    unsigned s_hi = __reduce_add_sync(peers, v >> 15);
-    unsigned s_lo = __reduce_add_sync(peers, v & 0x7fffu);
-    if (seg_leader(peers))
-        atomicAdd(&acc_sum[seg], ((unsigned long long)s_hi << 15) + (unsigned long long)s_lo);
-}
-
-__global__ void k_tree_count(int m, int thresh, const unsigned int* __restrict__ set,
-                             const int* __restrict__ lo, const int* __restrict__ hi,
-                             const int4* __restrict__ xi, const int4* __restrict__ acc_lo,
-                             const int4* __restrict__ acc_hi,
-                             const unsigned long long* __restrict__ acc_sum, unsigned int* acc_k,
-                             unsigned int* acc_k2)
-{
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    bool act = false;
-    int seg = 0;
-    unsigned lt = 0, le = 0;
+    int seg = 0, v = 0;
+    unsigned idx = 0;
+    bool lt = false, le = false;
     if (p < m) {
         seg = lo[p];
         int size = hi[p] - seg;
         act = size > thresh;
         if (act) {
-            long long com = (long long)(acc_sum[seg] / (unsigned long long)size);
-            long long v = comp(xi[set[p]], seg_axis(acc_lo[seg], acc_hi[seg]));
+            const int ax = seg_axis(A.lo[seg], A.hi[seg]);
+            const long long com = seg_com(A, seg, size, ax);
+            idx = set[p];
+            v = comp(xi[idx], ax);
             lt = v < com;
             le = v <= com;
         }
     }
     unsigned peers = seg_peers(act, seg);
     if (!act) return;
-    unsigned clt = __reduce_add_sync(peers, lt), cle = __reduce_add_sync(peers, le);
-    if (seg_leader(peers)) {
-        atomicAdd(&acc_k[seg], clt);
-        atomicAdd(&acc_k2[seg], cle);
+    const bool lead = seg_leader(peers);
+    unsigned clt = __reduce_add_sync(peers, lt ? 1u : 0u), cle = __reduce_add_sync(peers, le ? 1u : 0u);
+    unsigned long long k0 = warp_max_key(peers, lt, v, idx);
+    unsigned long long k1 = warp_min_key(peers, !lt, v, idx);
+    unsigned long long k2 = warp_max_key(peers, le, v, idx);
+    unsigned long long k3 = warp_min_key(peers, !le, v, idx);
+    if (lead) {
+        atomicAdd(&A.k[seg], clt);
+        atomicAdd(&A.k2[seg], cle);
+        if (k0) atomicMax(&A.key[4 * seg + 0], k0);
+        if (k1 != ~0ULL) atomicMin(&A.key[4 * seg + 1], k1);
+        if (k2) atomicMax(&A.key[4 * seg + 2], k2);
+        if (k3 != ~0ULL) atomicMin(&A.key[4 * seg + 3], k3);
     }
-}
-
-__global__ void k_tree_key(int m, int thresh, const unsigned int* __restrict__ set,
-                           const int* __restrict__ lo, const int* __restrict__ hi,
-                           const int4* __restrict__ xi, const int4* __restrict__ acc_lo,
-                           const int4* __restrict__ acc_hi,
-                           const unsigned long long* __restrict__ acc_sum,
-                           const unsigned int* __restrict__ acc_k,
-                           const unsigned int* __restrict__ acc_k2, unsigned long long* acc_key,
-                           unsigned long long* acc_key2)
-{
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= m) return;
-    int seg = lo[p], size = hi[p] - seg;
-    if (size <= thresh) return;
-    Cut c = make_cut(size, (int)acc_k[seg], (int)acc_k2[seg]);
-    if (c.coincident || c.kfinal == c.k) return;
-    const int ax = seg_axis(acc_lo[seg], acc_hi[seg]);
-    const long long com = (long long)(acc_sum[seg] / (unsigned long long)size);
-    unsigned idx = set[p];
-    long long v = comp(xi[idx], ax);
-    bool low = c.use_le ? v <= com : v < com;
-    unsigned long long key = ((unsigned long long)v << 32) | idx;
-    if (c.kfinal < c.k && low) atomicMax(&acc_key[seg], key);
-    if (c.kfinal > c.k && !low) atomicMin(&acc_key2[seg], key);
 }
 
 __global__ void k_tree_flag(int m, int thresh, const unsigned int* __restrict__ set,
                             const int* __restrict__ lo, const int* __restrict__ hi,
-                            const int4* __restrict__ xi, const int4* __restrict__ acc_lo,
-                            const int4* __restrict__ acc_hi,
-                            const unsigned long long* __restrict__ acc_sum,
-                            const unsigned int* __restrict__ acc_k,
-                            const unsigned int* __restrict__ acc_k2,
-                            const unsigned long long* __restrict__ acc_key,
-                            const unsigned long long* __restrict__ acc_key2,
-                            unsigned int* __restrict__ lflag)
+                            const int4* __restrict__ xi, SegAcc A, unsigned int* __restrict__ lflag)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= m) return;
@@ -439,41 +452,36 @@ __global__ void k_tree_flag(int m, int thresh, const unsigned int* __restrict__ 
         lflag[p] = 0;
         return;
     }
-    Cut c = make_cut(size, (int)acc_k[seg], (int)acc_k2[seg]);
+    Cut c = make_cut(size, (int)A.k[seg], (int)A.k2[seg]);
     unsigned idx = set[p];
     bool left;
     if (c.coincident) {
         left = (p - seg) < c.kfinal;  // segments stay in ascending index order
     } else {
-        const int ax = seg_axis(acc_lo[seg], acc_hi[seg]);
-        const long long com = (long long)(acc_sum[seg] / (unsigned long long)size);
+        const int ax = seg_axis(A.lo[seg], A.hi[seg]);
+        const long long com = seg_com(A, seg, size, ax);
         long long v = comp(xi[idx], ax);
         left = c.use_le ? v <= com : v < com;
         unsigned long long key = ((unsigned long long)v << 32) | idx;
-        if (c.kfinal < c.k && key == acc_key[seg]) left = false;
-        if (c.kfinal > c.k && key == acc_key2[seg]) left = true;
+        const int kk = c.use_le ? 2 : 0;
+        if (c.kfinal < c.k && key == A.key[4 * seg + kk]) left = false;
+        if (c.kfinal > c.k && key == A.key[4 * seg + kk + 1]) left = true;
     }
     lflag[p] = left ? 1u : 0u;
 }
 
 __global__ void k_tree_scatter(int m, int thresh, const unsigned int* __restrict__ set,
-                               const int* __restrict__ lo, const int* __restrict__ hi,
-                               const unsigned int* __restrict__ acc_k,
-                               const unsigned int* __restrict__ acc_k2,
+                               const int* __restrict__ lo, const int* __restrict__ hi, SegAcc A,
                                const unsigned int* __restrict__ lflag,
                                const unsigned int* __restrict__ lscan, unsigned int* __restrict__ set2,
-                               int* __restrict__ lo2, int* __restrict__ hi2, int4* acc_lo_n,
-                               int4* acc_hi_n, unsigned long long* acc_sum_n,
-                               unsigned int* acc_k_n, unsigned int* acc_k2_n,
-                               unsigned long long* acc_key_n, unsigned long long* acc_key2_n,
-                               int* maxseg)
+                               int* __restrict__ lo2, int* __restrict__ hi2, SegAcc An, int* maxseg)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= m) return;
     int seg = lo[p], end = hi[p], size = end - seg;
     int np = p, nlo = seg, nhi = end;
     if (size > thresh) {
-        Cut c = make_cut(size, (int)acc_k[seg], (int)acc_k2[seg]);
+        Cut c = make_cut(size, (int)A.k[seg], (int)A.k2[seg]);
         int before = (int)(lscan[p] - lscan[seg]);  // low items before p in this segment
         if (lflag[p]) {
             np = seg + before;
@@ -487,8 +495,7 @@ __global__ void k_tree_scatter(int m, int thresh, const unsigned int* __restrict
     set2[np] = set[p];
     lo2[np] = nlo;
     hi2[np] = nhi;
-    if (np == nlo && nhi - nlo > thresh)
-        acc_reset(np, acc_lo_n, acc_hi_n, acc_sum_n, acc_k_n, acc_k2_n, acc_key_n, acc_key2_n);
+    if (np == nlo && nhi - nlo > thresh) acc_reset_all(An, np);
 }
 
 // ---- shared-memory phase: every segment of size <= TREE_LOCAL, one CTA per chunk
@@ -812,17 +819,19 @@ static apr_status pair_trees(apr_ctx* c, int* off, unsigned int** set_out, int**
                         st);
     else
         cudaMemcpyAsync(W.mset[1], W.mset[0], sizeof(unsigned) * M, cudaMemcpyDeviceToDevice, st);
-    unsigned long long* key2[2] = {W.acc_key + c->cap, W.acc_key + 2 * c->cap};
-    int4* alo[2] = {W.acc_lo, W.acc_lo + c->cap};
-    int4* ahi[2] = {W.acc_hi, W.acc_hi + c->cap};
-    unsigned long long* asum[2] = {W.acc_sum, W.acc_sum + c->cap};
-    unsigned int* ak[2] = {W.acc_k, W.acc_k + c->cap};
-    unsigned int* ak2[2] = {W.acc_k2, W.acc_k2 + c->cap};
-    unsigned long long* akey[2] = {W.acc_key, W.acc_key + 3 * c->cap};
+    const long long C = c->cap;
+    SegAcc acc[2];
+    for (int k = 0; k < 2; ++k) {
+        acc[k].lo = W.acc_lo + k * C;
+        acc[k].hi = W.acc_hi + k * C;
+        acc[k].sum = W.acc_sum + 3 * k * C;
+        acc[k].k = W.acc_k + k * C;
+        acc[k].k2 = W.acc_k2 + k * C;
+        acc[k].key = W.acc_key + 4 * k * C;
+    }
     // buffers: set[] alternates between mset[1] and mset[0]
     unsigned int* sets[2] = {W.mset[1], W.mset[0]};
-    APR_LAUNCH(c, k_seg_setup, nblocks(M, 256), 256, M, lo_off, W.seg_lo[0], W.seg_hi[0], alo[0],
-               ahi[0], asum[0], ak[0], ak2[0], akey[0], key2[0]);
+    APR_LAUNCH(c, k_seg_setup, nblocks(M, 256), 256, M, lo_off, W.seg_lo[0], W.seg_hi[0], acc[0]);
     int maxm = 0;
     for (int l = 1; l <= lmax; ++l) maxm = max(maxm, off[l + 1] - off[l]);
     int cur = 0;
@@ -835,24 +844,18 @@ static apr_status pair_trees(apr_ctx* c, int* off, unsigned int** set_out, int**
     }
     for (int total = 0; rounds_left > 0 && total < 64 + 4 * 32; ) {
         for (int r = 0; r < rounds_left; ++r, ++total) {
-            APR_LAUNCH(c, k_tree_bbox, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur],
-                       W.seg_hi[cur], W.xi, alo[cur], ahi[cur]);
-            APR_LAUNCH(c, k_tree_sum, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur], W.seg_hi[cur],
-                       W.xi, alo[cur], ahi[cur], asum[cur]);
-            APR_LAUNCH(c, k_tree_count, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur],
-                       W.seg_hi[cur], W.xi, alo[cur], ahi[cur], asum[cur], ak[cur], ak2[cur]);
-            APR_LAUNCH(c, k_tree_key, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur], W.seg_hi[cur],
-                       W.xi, alo[cur], ahi[cur], asum[cur], ak[cur], ak2[cur], akey[cur], key2[cur]);
+            APR_LAUNCH(c, k_tree_bbox_sum, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur],
+                       W.seg_hi[cur], W.xi, acc[cur]);
+            APR_LAUNCH(c, k_tree_count_key, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur],
+                       W.seg_hi[cur], W.xi, acc[cur]);
             APR_LAUNCH(c, k_tree_flag, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur],
-                       W.seg_hi[cur], W.xi, alo[cur], ahi[cur], asum[cur], ak[cur], ak2[cur],
-                       akey[cur], key2[cur], W.lflag);
+                       W.seg_hi[cur], W.xi, acc[cur], W.lflag);
             scan_u32(c, W.lflag, W.uscan, M, nullptr);
             cudaMemsetAsync(&W.status[ST_MAXSEG], 0, sizeof(int), st);
             const int nx = cur ^ 1;
             APR_LAUNCH(c, k_tree_scatter, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur],
-                       W.seg_hi[cur], ak[cur], ak2[cur], W.lflag, W.uscan, sets[nx], W.seg_lo[nx],
-                       W.seg_hi[nx], alo[nx], ahi[nx], asum[nx], ak[nx], ak2[nx], akey[nx], key2[nx],
-                       &W.status[ST_MAXSEG]);
+                       W.seg_hi[cur], acc[cur], W.lflag, W.uscan, sets[nx], W.seg_lo[nx],
+                       W.seg_hi[nx], acc[nx], &W.status[ST_MAXSEG]);
             cur = nx;
         }
         cudaMemcpyAsync(c->hbuf, &W.status[ST_MAXSEG], sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -914,13 +917,23 @@ apr_status merge_pairs_debug(apr_ctx* c, int level, long long* pairs, long long 
 
 // ------------------------------------------------------------ compaction
 
-template <typename T>
-__global__ void k_compact_field(long long n, const unsigned char* __restrict__ flags,
-                                const unsigned int* __restrict__ pos, const T* __restrict__ in,
-                                T* __restrict__ out)
+struct FieldPtrs {
+    double* d[18];
+    unsigned long long* id;
+    unsigned char* level;
+    unsigned char* flags;
+};
+
+static FieldPtrs field_ptrs(const apr_particles& p)
 {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && !(flags[i] & APR_FLAG_DEAD)) out[pos[i]] = in[i];
+    FieldPtrs f;
+    double* d[18] = {p.x,  p.y,  p.z,  p.vx,   p.vy,   p.vz,  p.u,    p.h,    p.rho,
+                     p.omega, p.ax, p.ay, p.az, p.dudt, p.vsig, p.dnn, p.pres, p.cs};
+    for (int k = 0; k < 18; ++k) f.d[k] = d[k];
+    f.id = p.id;
+    f.level = p.level;
+    f.flags = p.flags;
+    return f;
 }
 
 __global__ void k_live_flag(long long n, const unsigned char* __restrict__ flags,
@@ -930,14 +943,36 @@ __global__ void k_live_flag(long long n, const unsigned char* __restrict__ flags
     if (i < n) out[i] = (flags[i] & APR_FLAG_DEAD) ? 0u : 1u;
 }
 
-template <typename T>
-static void compact_one(apr_ctx* c, T* field, long long n, long long nlive)
+// live particles to their compacted slots in scratch laid out field by field
+__global__ void k_compact_out(long long n, long long cap, FieldPtrs f,
+                              const unsigned int* __restrict__ pos, double* __restrict__ tmp)
 {
-    T* tmp = (T*)c->W.tmp8;
-    APR_LAUNCH(c, k_compact_field<T>, nblocks(n, 256), 256, n, c->p.flags, c->W.uscan, field, tmp);
-    cudaMemcpyAsync(field, tmp, sizeof(T) * (size_t)nlive, cudaMemcpyDeviceToDevice, c->stream);
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned char fl = f.flags[i];
+    if (fl & APR_FLAG_DEAD) return;
+    const long long j = pos[i];
+    for (int k = 0; k < 18; ++k) tmp[k * cap + j] = f.d[k][i];
+    ((unsigned long long*)(tmp + 18 * cap))[j] = f.id[i];
+    unsigned char* b = (unsigned char*)(tmp + 19 * cap);
+    b[j] = f.level[i];
+    b[cap + j] = fl;
 }
 
+__global__ void k_compact_back(long long nlive, long long cap, FieldPtrs f,
+                               const double* __restrict__ tmp)
+{
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nlive) return;
+    for (int k = 0; k < 18; ++k) f.d[k][j] = tmp[k * cap + j];
+    f.id[j] = ((const unsigned long long*)(tmp + 18 * cap))[j];
+    const unsigned char* b = (const unsigned char*)(tmp + 19 * cap);
+    f.level[j] = b[j];
+    f.flags[j] = b[cap + j];
+}
+
+// stable removal of dead particles.  The neighbour-list memory serves as scratch
+// (the lists are rebuilt after any change of the particle set).
 apr_status compact(apr_ctx* c, long long* removed)
 {
     const long long n = c->n;
@@ -950,13 +985,10 @@ apr_status compact(apr_ctx* c, long long* removed)
     long long nlive = (unsigned)((int*)c->hbuf)[0];
     *removed = n - nlive;
     if (nlive == n) return APR_OK;
-    apr_particles& p = c->p;
-    double* d[] = {p.x, p.y, p.z, p.vx, p.vy, p.vz, p.u, p.h, p.rho, p.omega,
-                   p.ax, p.ay, p.az, p.dudt, p.vsig, p.dnn, p.pres, p.cs};
-    for (double* f : d) compact_one<double>(c, f, n, nlive);
-    compact_one<unsigned long long>(c, p.id, n, nlive);
-    compact_one<unsigned char>(c, p.level, n, nlive);
-    compact_one<unsigned char>(c, p.flags, n, nlive);  // last: the others read the flags
+    const FieldPtrs f = field_ptrs(c->p);
+    double* tmp = (double*)W.nbr;  // 20 x cap x 8 bytes <= max_neigh x cap x 4 bytes
+    APR_LAUNCH(c, k_compact_out, nblocks(n, 256), 256, n, c->cap, f, W.uscan, tmp);
+    APR_LAUNCH(c, k_compact_back, nblocks(nlive, 256), 256, nlive, c->cap, f, tmp);
     c->n = nlive;
     return cuda_check(c, cudaGetLastError(), "compaction");
 }
@@ -993,25 +1025,28 @@ static apr_status split_merge_body(apr_ctx* c, apr_counts* cnt)
     memset(cnt, 0, sizeof(*cnt));
     apr_status s;
     if (c->n > 0) APR_LAUNCH(c, k_clear_changed, nblocks(c->n, 256), 256, c->n, c->p.flags);
-    for (int l = 0; l < c->cfg.lmax; ++l) {
+    if (c->cfg.lmax >= 1 && c->n > 0) {
         const long long n = c->n;
-        if (n == 0) break;
-        APR_LAUNCH(c, k_split_flag, nblocks(n, 256), 256, c->dc, rg, n, l, c->p.x, c->p.y, c->p.z,
-                                                      c->p.level, c->p.flags, W.uflag);
-        scan_u32(c, W.uflag, W.uscan, n, (unsigned*)&W.status[ST_COUNT_A]);
-        cudaMemcpyAsync(c->hbuf, &W.status[ST_COUNT_A], sizeof(int), cudaMemcpyDeviceToHost, st);
+        APR_LAUNCH(c, k_split_keys, nblocks(n, 256), 256, c->dc, rg, n, c->p.x, c->p.y, c->p.z,
+                   c->p.level, c->p.flags, W.key[0], W.val[0]);
+        s = radix_pass8(c, W.key[0], W.val[0], W.key[1], W.val[1], n, 0, &W.status[ST_BINS],
+                        c->cfg.lmax + 1);
+        if (s != APR_OK) return s;
+        cudaMemcpyAsync(c->hbuf, &W.status[ST_BINS], sizeof(int) * (c->cfg.lmax + 1),
+                        cudaMemcpyDeviceToHost, st);
         s = cuda_check(c, cudaStreamSynchronize(st), "split count");
         if (s != APR_OK) return s;
-        long long ns = (unsigned)((int*)c->hbuf)[0];
-        if (n + ns > c->cap)
+        const int* bins = (const int*)c->hbuf;  // parents of level l: [bins[l], bins[l+1])
+        const int total = bins[c->cfg.lmax];
+        for (int l = 0; l < c->cfg.lmax; ++l) cnt->n_split[l] = bins[l + 1] - bins[l];
+        if (n + total > c->cap)
             return fail(c, APR_ERR_CAPACITY, "split would exceed the bound capacity");
-        if (ns > 0) {
-            APR_LAUNCH(c, k_split_apply, nblocks(n, 256), 256, c->dc, rg, n, l, c->step, c->next_id,
-                                                           W.uflag, W.uscan, c->p);
-            c->n = n + ns;
-            c->next_id += ns;
+        if (total > 0) {
+            APR_LAUNCH(c, k_split_apply, nblocks(total, 256), 256, c->dc, rg, total, n, c->step,
+                       c->next_id, W.val[1], c->p);
+            c->n = n + total;
+            c->next_id += total;
         }
-        cnt->n_split[l] = ns;
     }
     if (c->cfg.lmax >= 1 && c->n > 0) {
         s = quantise(c);
@@ -1069,10 +1104,12 @@ __device__ void block_reduce_store(double (&v)[NV], double* partials)
 // fixed-shape reduction of the block partials (one block): deterministic
 __global__ void __launch_bounds__(256) k_reduce_final(int nblk, int nv,
                                                       const double* __restrict__ partials,
-                                                      double* __restrict__ out, int op_min)
+                                                      double* __restrict__ out,
+                                                      unsigned int min_mask)
 {
     __shared__ double sm[256];
     for (int k = 0; k < nv; ++k) {
+        const bool op_min = (min_mask >> k) & 1u;
         double x = op_min ? INFINITY : 0.0;
         for (int b = threadIdx.x; b < nblk; b += 256) {
             double y = partials[b * 32 + k];
@@ -1091,9 +1128,9 @@ __global__ void __launch_bounds__(256) k_reduce_final(int nblk, int nv,
     }
 }
 
-static apr_status reduce_readback(apr_ctx* c, int nv, int op_min, double* host)
+static apr_status reduce_readback(apr_ctx* c, int nv, unsigned int min_mask, double* host)
 {
-    APR_LAUNCH(c, k_reduce_final, 1, 256, RED_BLOCKS, nv, c->W.red, c->W.redout, op_min);
+    APR_LAUNCH(c, k_reduce_final, 1, 256, RED_BLOCKS, nv, c->W.red, c->W.redout, min_mask);
     cudaMemcpyAsync(c->hbuf, c->W.redout, sizeof(double) * nv, cudaMemcpyDeviceToHost, c->stream);
     apr_status s = cuda_check(c, cudaStreamSynchronize(c->stream), "reduce");
     if (s != APR_OK) return s;
@@ -1123,11 +1160,88 @@ __global__ void __launch_bounds__(256) k_stats(DevCfg dc, long long n, apr_parti
     block_reduce_store<9>(v, partials);
 }
 
+// conservation sums (9) and the time-step limit (slot 9, a minimum) in one pass
+__global__ void __launch_bounds__(256) k_stats_dt(DevCfg dc, long long n, apr_particles p,
+                                                  double* partials)
+{
+    double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double dt = INFINITY;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned char fl = p.flags[i];
+        if (fl & APR_FLAG_DEAD) continue;
+        double m = dc.m0 * level_mass_d(p.level[i]);
+        double vx = p.vx[i], vy = p.vy[i], vz = p.vz[i];
+        v[0] += m;
+        v[1] += m * vx;
+        v[2] += m * vy;
+        v[3] += m * vz;
+        v[4] += m * (p.y[i] * vz - p.z[i] * vy);
+        v[5] += m * (p.z[i] * vx - p.x[i] * vz);
+        v[6] += m * (p.x[i] * vy - p.y[i] * vx);
+        v[7] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+        if (dc.eos == APR_EOS_ADIABATIC) v[8] += m * p.u[i];
+        if (fl & APR_FLAG_FIXED) continue;
+        double h = p.h[i];
+        if (p.vsig[i] > 0.0) dt = fmin(dt, dc.ccour * h / p.vsig[i]);
+        double a = sqrt(p.ax[i] * p.ax[i] + p.ay[i] * p.ay[i] + p.az[i] * p.az[i]);
+        if (a > 0.0) dt = fmin(dt, dc.cforce * sqrt(h / a));
+    }
+    __shared__ double sm[10][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < 9; ++k) {
+        double x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sm[k][wid] = x;
+    }
+    for (int o = 16; o > 0; o >>= 1) dt = fmin(dt, __shfl_down_sync(0xffffffffu, dt, o));
+    if (lane == 0) sm[9][wid] = dt;
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        double x = sm[threadIdx.x][0];
+        for (int w = 1; w < 8; ++w)
+            x = threadIdx.x == 9 ? fmin(x, sm[threadIdx.x][w]) : x + sm[threadIdx.x][w];
+        partials[blockIdx.x * 32 + threadIdx.x] = x;
+    }
+}
+
+static void stats_from(const apr_ctx* c, const double* r, apr_stats* st)
+{
+    st->mass = r[0];
+    for (int k = 0; k < 3; ++k) {
+        st->mom[k] = r[1 + k];
+        st->ang[k] = r[4 + k];
+    }
+    st->ekin = r[7];
+    st->etherm = r[8];
+    for (int j = 0; j < c->nsink; ++j) {
+        const apr_sink& k = c->sinks[j];
+        double m = k.m;
+        st->mass += m;
+        for (int d = 0; d < 3; ++d) st->mom[d] += m * k.v[d];
+        st->ang[0] += m * (k.x[1] * k.v[2] - k.x[2] * k.v[1]);
+        st->ang[1] += m * (k.x[2] * k.v[0] - k.x[0] * k.v[2]);
+        st->ang[2] += m * (k.x[0] * k.v[1] - k.x[1] * k.v[0]);
+        st->ekin += 0.5 * m * (k.v[0] * k.v[0] + k.v[1] * k.v[1] + k.v[2] * k.v[2]);
+    }
+}
+
+apr_status compute_stats_dt(apr_ctx* c, apr_stats* st, double* dt)
+{
+    APR_LAUNCH(c, k_stats_dt, RED_BLOCKS, 256, c->dc, c->n, c->p, c->W.red);
+    double r[10];
+    apr_status s = reduce_readback(c, 10, 1u << 9, r);
+    if (s != APR_OK) return s;
+    stats_from(c, r, st);
+    *dt = r[9];
+    return APR_OK;
+}
+
 apr_status compute_stats(apr_ctx* c, apr_stats* st)
 {
     APR_LAUNCH(c, k_stats, RED_BLOCKS, 256, c->dc, c->n, c->p, c->W.red);
     double r[9];
-    apr_status s = reduce_readback(c, 9, 0, r);
+    apr_status s = reduce_readback(c, 9, 0u, r);
     if (s != APR_OK) return s;
     st->mass = r[0];
     for (int k = 0; k < 3; ++k) {
@@ -1175,7 +1289,7 @@ __global__ void __launch_bounds__(256) k_timestep(DevCfg dc, long long n, apr_pa
 apr_status compute_timestep(apr_ctx* c, double* dt)
 {
     APR_LAUNCH(c, k_timestep, RED_BLOCKS, 256, c->dc, c->n, c->p, c->W.red);
-    return reduce_readback(c, 1, 1, dt);
+    return reduce_readback(c, 1, 1u, dt);
 }
 
 // ------------------------------------------------------- point masses
@@ -1214,7 +1328,7 @@ apr_status sink_gravity(apr_ctx* c)
     if (c->nsink == 0) return APR_OK;
     APR_LAUNCH(c, k_sink_gravity, RED_BLOCKS, 256, c->dc, dev_sinks(c), c->n, c->p, c->W.red);
     double r[3 * APR_MAXSINK];
-    apr_status s = reduce_readback(c, 3 * c->nsink, 0, r);
+    apr_status s = reduce_readback(c, 3 * c->nsink, 0u, r);
     if (s != APR_OK) return s;
     for (int j = 0; j < c->nsink; ++j) {
         apr_sink& k = c->sinks[j];
@@ -1276,7 +1390,7 @@ apr_status accrete(apr_ctx* c, long long* naccreted)
     APR_LAUNCH(c, k_accrete, RED_BLOCKS, 256, c->dc, dev_sinks(c), c->n, c->p, c->W.red,
                                                  &c->W.status[ST_COUNT_B]);
     double r[28];
-    apr_status s = reduce_readback(c, 7 * c->nsink, 0, r);
+    apr_status s = reduce_readback(c, 7 * c->nsink, 0u, r);
     if (s != APR_OK) return s;
     cudaMemcpyAsync(c->hbuf, &c->W.status[ST_COUNT_B], sizeof(int), cudaMemcpyDeviceToHost,
                     c->stream);

@@ -99,26 +99,72 @@ struct Rel<double> {
 
 // ----------------------------------------------------------------- density
 
+// exact lattice separation (minimum image) and its square
+__device__ __forceinline__ unsigned long long lattice_r2(const DevCfg& dc, const int4& pa,
+                                                         const int4& pb, int d[3])
+{
+    d[0] = min_image32(pa.x - pb.x, dc.periodic[0], (int)dc.Lint[0]);
+    d[1] = min_image32(pa.y - pb.y, dc.periodic[1], (int)dc.Lint[1]);
+    d[2] = min_image32(pa.z - pb.z, dc.periodic[2], (int)dc.Lint[2]);
+    return (unsigned long long)((long long)d[0] * d[0]) + (unsigned long long)((long long)d[1] * d[1]) +
+           (unsigned long long)((long long)d[2] * d[2]);
+}
+
+// one density term mu_b f(q), mu_b q f'(q) for a pair inside 2h
+template <typename R>
+__device__ __forceinline__ void density_term(R r2, R hinv, R r2max, int levb, Acc<R>& S,
+                                             Acc<R>& T, unsigned long long& npair)
+{
+    if (r2 >= r2max) return;
+    const R q = Num<R>::sqrt_(r2) * hinv;
+    R f, df;
+    m4<R>(q, f, df);
+    const R mub = Num<R>::mass(levb);
+    S.add(mub * f);
+    T.add(mub * q * df);
+    ++npair;
+}
+
+template <typename R>
+__device__ __forceinline__ R rel_r2(const DevCfg& dc, const int d[3], const double* sx,
+                                    const double* sy, const double* sz, int a, int b);
+template <>
+__device__ __forceinline__ float rel_r2<float>(const DevCfg& dc, const int d[3], const double*,
+                                               const double*, const double*, int, int)
+{
+    const float x = (float)d[0] * dc.deltaf, y = (float)d[1] * dc.deltaf, z = (float)d[2] * dc.deltaf;
+    return x * x + y * y + z * z;
+}
+template <>
+__device__ __forceinline__ double rel_r2<double>(const DevCfg& dc, const int*, const double* sx,
+                                                 const double* sy, const double* sz, int a, int b)
+{
+    double d[3];
+    Rel<double>::get(dc, int4(), int4(), sx, sy, sz, a, b, d);
+    return d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+}
+
+// Newton-Raphson on g(h) with a bracket over this particle's (symmetric,
+// reach-scaled) list; the first pass also finds the nearest lattice neighbour.
+// Four list entries are loaded ahead so that several gathers are in flight.
 template <typename R>
 __global__ void __launch_bounds__(128)
     k_density(DevCfg dc, long long n, long long cap, double reach, const int4* __restrict__ pk,
-              const double* __restrict__ sh, const unsigned int* __restrict__ nbr,
-              const int* __restrict__ ncnt, const double* __restrict__ sx,
-              const double* __restrict__ sy, const double* __restrict__ sz,
-              const unsigned int* __restrict__ perm, const double* __restrict__ x,
-              const double* __restrict__ y, const double* __restrict__ u,
-              double* __restrict__ h_out, double* __restrict__ rho_out,
-              double* __restrict__ omega_out, double* __restrict__ dnn_out,
-              double* __restrict__ pres_out, double* __restrict__ cs_out, int* status,
-              unsigned long long* counters)
+              const double* __restrict__ sh, const unsigned long long* __restrict__ sthr,
+              const unsigned int* __restrict__ nbr, const int* __restrict__ ncnt,
+              const double* __restrict__ sx, const double* __restrict__ sy,
+              const double* __restrict__ sz, const unsigned int* __restrict__ perm,
+              const double* __restrict__ x, const double* __restrict__ y,
+              const double* __restrict__ u, double* __restrict__ h_out,
+              double* __restrict__ rho_out, double* __restrict__ omega_out,
+              double* __restrict__ dnn_out, double* __restrict__ pres_out,
+              double* __restrict__ cs_out, int* status, unsigned long long* counters)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int a = (int)s;
     const int4 pa = pk[a];
     const double hlist = sh[a];
-    const R mua = Num<R>::mass(pa.w);
-    const R target = R(3.14159265358979323846) * mua * R(dc.hfact * dc.hfact * dc.hfact);
     const int m = ncnt[a];
     if (m < 0) {
         // the list at this h overflowed (e.g. an initial h far too large at a
@@ -128,29 +174,45 @@ __global__ void __launch_bounds__(128)
         atomicAdd(&status[ST_SHRINK], 1);
         return;
     }
+    const R mua = Num<R>::mass(pa.w);
+    const R target = R(3.14159265358979323846) * mua * R(dc.hfact * dc.hfact * dc.hfact);
+    const unsigned int* col = nbr + a;  // this particle's list: col[k * cap]
     R h = (R)hlist;
     R lo = R(0), hi = R(0);  // bracket of the root; hi == 0: none yet
     R D = R(0);              // sum mu_b (3 f + q f') at the last evaluated h
     bool conv = false, uncovered = false;
-    unsigned long long npair = 0;
+    unsigned long long npair = 0, best = ~0ULL;
     for (int it = 0; it < dc.nr_maxit; ++it) {
         const R hinv = R(1) / h;
         const R r2max = R(4) * h * h;
         Acc<R> S, T;
-        for (int k = 0; k < m; ++k) {
-            const int b = (int)nbr[(long long)k * cap + a];
+        const bool first_pass = it == 0;
+        int k = 0;
+        for (; k + 4 <= m; k += 4) {
+            const int b0 = (int)col[(long long)k * cap], b1 = (int)col[(long long)(k + 1) * cap];
+            const int b2 = (int)col[(long long)(k + 2) * cap], b3 = (int)col[(long long)(k + 3) * cap];
+            const int4 p0 = pk[b0], p1 = pk[b1], p2 = pk[b2], p3 = pk[b3];
+            int d0[3], d1[3], d2[3], d3[3];
+            const unsigned long long q0 = lattice_r2(dc, pa, p0, d0), q1 = lattice_r2(dc, pa, p1, d1);
+            const unsigned long long q2 = lattice_r2(dc, pa, p2, d2), q3 = lattice_r2(dc, pa, p3, d3);
+            if (first_pass) {
+                best = q0 < best ? q0 : best;
+                best = q1 < best ? q1 : best;
+                best = q2 < best ? q2 : best;
+                best = q3 < best ? q3 : best;
+            }
+            density_term<R>(rel_r2<R>(dc, d0, sx, sy, sz, a, b0), hinv, r2max, p0.w, S, T, npair);
+            density_term<R>(rel_r2<R>(dc, d1, sx, sy, sz, a, b1), hinv, r2max, p1.w, S, T, npair);
+            density_term<R>(rel_r2<R>(dc, d2, sx, sy, sz, a, b2), hinv, r2max, p2.w, S, T, npair);
+            density_term<R>(rel_r2<R>(dc, d3, sx, sy, sz, a, b3), hinv, r2max, p3.w, S, T, npair);
+        }
+        for (; k < m; ++k) {
+            const int b = (int)col[(long long)k * cap];
             const int4 pb = pk[b];
-            R d[3];
-            Rel<R>::get(dc, pa, pb, sx, sy, sz, a, b, d);
-            const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            if (r2 >= r2max) continue;
-            const R q = Num<R>::sqrt_(r2) * hinv;
-            R f, df;
-            m4<R>(q, f, df);
-            const R mub = Num<R>::mass(pb.w);
-            S.add(mub * f);
-            T.add(mub * q * df);
-            ++npair;
+            int d[3];
+            const unsigned long long q = lattice_r2(dc, pa, pb, d);
+            if (first_pass) best = q < best ? q : best;
+            density_term<R>(rel_r2<R>(dc, d, sx, sy, sz, a, b), hinv, r2max, pb.w, S, T, npair);
         }
         const R g = (S.s + mua) - target;           // pi h^3 (rho_sum - rho_h) / m0
         const R dg = -(T.s) * hinv;                   // dg/dh >= 0
@@ -189,20 +251,10 @@ __global__ void __launch_bounds__(128)
         return;
     }
     if (!conv) atomicAdd(&status[ST_NOCONV], 1);
-    // nearest neighbour on the lattice among the neighbours at the final h
+    // nearest lattice neighbour within 2h: the list holds every particle within
+    // the reach, so the overall nearest counts iff it lies inside 2h
     const unsigned long long thr = neighbour_threshold(hd, dc.delta);
-    unsigned long long best = ~0ULL;
-    for (int k = 0; k < m; ++k) {
-        const int b = (int)nbr[(long long)k * cap + a];
-        const int4 pb = pk[b];
-        long long dx = min_image((long long)pa.x - pb.x, dc.periodic[0], dc.Lint[0]);
-        long long dy = min_image((long long)pa.y - pb.y, dc.periodic[1], dc.Lint[1]);
-        long long dz = min_image((long long)pa.z - pb.z, dc.periodic[2], dc.Lint[2]);
-        unsigned long long r2 = (unsigned long long)(dx * dx) + (unsigned long long)(dy * dy) +
-                                (unsigned long long)(dz * dz);
-        if (r2 < thr && r2 < best) best = r2;
-    }
-    dnn_out[i] = best == ~0ULL ? (double)INFINITY : sqrt((double)best) * dc.delta;
+    dnn_out[i] = best < thr ? sqrt((double)best) * dc.delta : (double)INFINITY;
     const double hr = dc.hfact / hd;
     const double rho = dc.m0 * (double)level_mass_d(pa.w) * hr * hr * hr;
     rho_out[i] = rho;
@@ -232,23 +284,27 @@ apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv)
         const double reach = DENSITY_REACH;
         if (c->cfg.precision == APR_PREC_FP64)
             APR_LAUNCH(c, k_density<double>, nblocks(n, 128), 128, 
-                c->dc, n, c->cap, reach, W.pk, W.sh, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
+                c->dc, n, c->cap, reach, W.pk, W.sh, W.sthr, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
                 c->p.x, c->p.y, c->p.u, c->p.h, c->p.rho, c->p.omega, c->p.dnn, c->p.pres, c->p.cs,
                 W.status, W.counters);
         else
             APR_LAUNCH(c, k_density<float>, nblocks(n, 128), 128, 
-                c->dc, n, c->cap, reach, W.pk, W.sh, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
+                c->dc, n, c->cap, reach, W.pk, W.sh, W.sthr, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
                 c->p.x, c->p.y, c->p.u, c->p.h, c->p.rho, c->p.omega, c->p.dnn, c->p.pres, c->p.cs,
                 W.status, W.counters);
     }
     prof_end(c, ps);
-    cudaMemcpyAsync(c->hbuf, &W.status[ST_UNCOVERED], (ST_SHRINK - ST_UNCOVERED + 1) * sizeof(int),
-                    cudaMemcpyDeviceToHost, st);
+    // one read-back for the index status words and the density counters
+    cudaMemcpyAsync(c->hbuf, W.status, (ST_SHRINK + 1) * sizeof(int), cudaMemcpyDeviceToHost, st);
     apr_status s = cuda_check(c, cudaStreamSynchronize(st), "density");
     if (s != APR_OK) return s;
-    *uncovered = ((int*)c->hbuf)[0];
-    *noconv = ((int*)c->hbuf)[1];
-    c->last_shrink = ((int*)c->hbuf)[ST_SHRINK - ST_UNCOVERED];
+    const int* hs = (const int*)c->hbuf;
+    if (hs[ST_TREE_BAD]) return fail(c, APR_ERR_STATE, "internal error: malformed radix tree");
+    if (hs[ST_NEIGH_OVERFLOW] || hs[ST_CAND_OVERFLOW])
+        return fail(c, APR_ERR_NEIGH_OVERFLOW, "a neighbour list overflowed");
+    *uncovered = hs[ST_UNCOVERED];
+    *noconv = hs[ST_NOCONV];
+    c->last_shrink = hs[ST_SHRINK];
     return APR_OK;
 }
 
@@ -336,14 +392,68 @@ __device__ __forceinline__ F4<double> ld4<double>(const void* base, long long s)
     return {a.x, a.y, b.x, b.y};
 }
 
+// per-particle state the force sums need
+template <typename R>
+struct ForceSelf {
+    R hinv, h4, pro, cs, rho, P, ior, vx, vy, vz, u;
+};
+
+// one pair of the force / energy sums (pairs outside both supports add nothing)
+template <typename R>
+__device__ __forceinline__ void force_pair(const DevCfg& dc, const ForceSelf<R>& A, const R d[3],
+                                           const F4<R>& Ab, const F4<R>& Vb, const F4<R>& Bb,
+                                           bool adiabatic, bool cond, Acc<R>& fx, Acc<R>& fy,
+                                           Acc<R>& fz, Acc<R>& du, R& vsig,
+                                           unsigned long long& npair)
+{
+    const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const R rinv = Num<R>::rsqrt_(r2);
+    const R r = r2 * rinv;
+    const R hinv_b = Ab.x;
+    const R qa = r * A.hinv, qb = r * hinv_b;
+    if (!(qa < R(2) || qb < R(2))) return;
+    ++npair;
+    R fa, dfa, fb, dfb;
+    m4<R>(qa, fa, dfa);
+    m4<R>(qb, fb, dfb);
+    const R alpha = (R)dc.alpha_av, beta = (R)dc.beta_av;
+    const R Fa = dfa * A.h4;
+    const R Fb = dfb * (hinv_b * hinv_b * hinv_b * hinv_b);
+    const R vr = ((A.vx - Vb.x) * d[0] + (A.vy - Vb.y) * d[1] + (A.vz - Vb.z) * d[2]) * rinv;
+    R ta = A.pro, tb = Ab.y;
+    if (vr < R(0)) {
+        const R vsa = alpha * A.cs - beta * vr;
+        const R vsb = alpha * Ab.z - beta * vr;
+        ta -= R(0.5) * vsa * vr * A.ior;
+        tb -= R(0.5) * vsb * vr * Bb.y;
+    }
+    const R mub = Bb.w;
+    const R fac = mub * (ta * Fa + tb * Fb) * rinv;
+    fx.add(-fac * d[0]);
+    fy.add(-fac * d[1]);
+    fz.add(-fac * d[2]);
+    if (adiabatic) {
+        R e = mub * ta * vr * Fa;
+        if (cond) {
+            const R dP = A.P - Bb.x;
+            const R vsu = Num<R>::sqrt_(fabs(dP) / (R(0.5) * (A.rho + Ab.w)));
+            e += mub * (R)dc.alpha_u * vsu * (A.u - Vb.w) * R(0.5) * (Fa * A.ior + Fb * Bb.y);
+        }
+        du.add(e);
+    }
+    const R vs = A.cs + beta * (vr < R(0) ? -vr : R(0));
+    vsig = vs > vsig ? vs : vsig;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(128)
     k_force(DevCfg dc, long long n, long long cap, const int4* __restrict__ pk,
-            const void* __restrict__ Ab, const void* __restrict__ Vb, const void* __restrict__ Bb,
-            const unsigned int* __restrict__ nbr, const int* __restrict__ ncnt,
-            const double* __restrict__ sx, const double* __restrict__ sy,
-            const double* __restrict__ sz, const unsigned int* __restrict__ perm,
-            double* __restrict__ ax_out, double* __restrict__ ay_out, double* __restrict__ az_out,
+            const void* __restrict__ Abuf, const void* __restrict__ Vbuf,
+            const void* __restrict__ Bbuf, const unsigned int* __restrict__ nbr,
+            const int* __restrict__ ncnt, const double* __restrict__ sx,
+            const double* __restrict__ sy, const double* __restrict__ sz,
+            const unsigned int* __restrict__ perm, double* __restrict__ ax_out,
+            double* __restrict__ ay_out, double* __restrict__ az_out,
             double* __restrict__ dudt_out, double* __restrict__ vsig_out,
             unsigned long long* counters)
 {
@@ -351,59 +461,45 @@ __global__ void __launch_bounds__(128)
     if (s >= n) return;
     const int a = (int)s;
     const int4 pa = pk[a];
-    const F4<R> A = ld4<R>(Ab, a), V = ld4<R>(Vb, a), B = ld4<R>(Bb, a);
-    const R hinv_a = A.x, pro_a = A.y, cs_a = A.z, rho_a = A.w;
-    const R P_a = B.x, ior_a = B.y;
-    const R h4a = hinv_a * hinv_a * hinv_a * hinv_a;
-    const R alpha = (R)dc.alpha_av, beta = (R)dc.beta_av, alpha_u = (R)dc.alpha_u;
+    const F4<R> Aa = ld4<R>(Abuf, a), Va = ld4<R>(Vbuf, a), Ba = ld4<R>(Bbuf, a);
+    ForceSelf<R> A;
+    A.hinv = Aa.x;
+    A.h4 = Aa.x * Aa.x * Aa.x * Aa.x;
+    A.pro = Aa.y;
+    A.cs = Aa.z;
+    A.rho = Aa.w;
+    A.P = Ba.x;
+    A.ior = Ba.y;
+    A.vx = Va.x;
+    A.vy = Va.y;
+    A.vz = Va.z;
+    A.u = Va.w;
     const bool adiabatic = dc.eos == APR_EOS_ADIABATIC;
     const bool cond = adiabatic && dc.alpha_u > 0.0;
     Acc<R> fx, fy, fz, du;
-    R vsig = cs_a;
+    R vsig = A.cs;
     unsigned long long npair = 0;
     const int m = ncnt[a];
-    for (int k = 0; k < m; ++k) {
-        const int b = (int)nbr[(long long)k * cap + a];
+    const unsigned int* col = nbr + a;
+    int k = 0;
+    for (; k + 2 <= m; k += 2) {
+        const int b0 = (int)col[(long long)k * cap], b1 = (int)col[(long long)(k + 1) * cap];
+        const int4 p0 = pk[b0], p1 = pk[b1];
+        const F4<R> A0 = ld4<R>(Abuf, b0), V0 = ld4<R>(Vbuf, b0), B0 = ld4<R>(Bbuf, b0);
+        const F4<R> A1 = ld4<R>(Abuf, b1), V1 = ld4<R>(Vbuf, b1), B1 = ld4<R>(Bbuf, b1);
+        R d0[3], d1[3];
+        Rel<R>::get(dc, pa, p0, sx, sy, sz, a, b0, d0);
+        Rel<R>::get(dc, pa, p1, sx, sy, sz, a, b1, d1);
+        force_pair<R>(dc, A, d0, A0, V0, B0, adiabatic, cond, fx, fy, fz, du, vsig, npair);
+        force_pair<R>(dc, A, d1, A1, V1, B1, adiabatic, cond, fx, fy, fz, du, vsig, npair);
+    }
+    for (; k < m; ++k) {
+        const int b = (int)col[(long long)k * cap];
         const int4 pb = pk[b];
+        const F4<R> Ab = ld4<R>(Abuf, b), Vb = ld4<R>(Vbuf, b), Bb = ld4<R>(Bbuf, b);
         R d[3];
         Rel<R>::get(dc, pa, pb, sx, sy, sz, a, b, d);
-        const F4<R> Ab4 = ld4<R>(Ab, b), Vb4 = ld4<R>(Vb, b), Bb4 = ld4<R>(Bb, b);
-        const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        const R rinv = Num<R>::rsqrt_(r2);
-        const R r = r2 * rinv;
-        const R hinv_b = Ab4.x;
-        const R qa = r * hinv_a, qb = r * hinv_b;
-        if (!(qa < R(2) || qb < R(2))) continue;
-        ++npair;
-        R fa, dfa, fb, dfb;
-        m4<R>(qa, fa, dfa);
-        m4<R>(qb, fb, dfb);
-        const R Fa = dfa * h4a;
-        const R Fb = dfb * (hinv_b * hinv_b * hinv_b * hinv_b);
-        const R vr = ((V.x - Vb4.x) * d[0] + (V.y - Vb4.y) * d[1] + (V.z - Vb4.z) * d[2]) * rinv;
-        R ta = pro_a, tb = Ab4.y;
-        if (vr < R(0)) {
-            const R vsa = alpha * cs_a - beta * vr;
-            const R vsb = alpha * Ab4.z - beta * vr;
-            ta -= R(0.5) * vsa * vr * ior_a;
-            tb -= R(0.5) * vsb * vr * Bb4.y;
-        }
-        const R mub = Bb4.w;
-        const R fac = mub * (ta * Fa + tb * Fb) * rinv;
-        fx.add(-fac * d[0]);
-        fy.add(-fac * d[1]);
-        fz.add(-fac * d[2]);
-        if (adiabatic) {
-            R e = mub * ta * vr * Fa;
-            if (cond) {
-                const R dP = P_a - Bb4.x;
-                const R vsu = Num<R>::sqrt_(fabs(dP) / (R(0.5) * (rho_a + Ab4.w)));
-                e += mub * alpha_u * vsu * (V.w - Vb4.w) * R(0.5) * (Fa * ior_a + Fb * Bb4.y);
-            }
-            du.add(e);
-        }
-        const R vs = cs_a + beta * (vr < R(0) ? -vr : R(0));
-        vsig = vs > vsig ? vs : vsig;
+        force_pair<R>(dc, A, d, Ab, Vb, Bb, adiabatic, cond, fx, fy, fz, du, vsig, npair);
     }
     if (dc.prof) atomicAdd(&counters[APR_PROF_FORCE], npair);
     const double scale = dc.m0 / 3.14159265358979323846;
