@@ -20,8 +20,11 @@ namespace apr {
 
 // ------------------------------------------------------------------- scan
 
+// block-local exclusive scan of SCAN_BLOCK items; bsum[block] = the block's total;
+// with a single block, *total receives the total
 __global__ void k_scan_block(const unsigned int* __restrict__ in, unsigned int* __restrict__ out,
-                             unsigned int* __restrict__ bsum, long long n)
+                             unsigned int* __restrict__ bsum, long long n,
+                             unsigned int* __restrict__ total)
 {
     __shared__ unsigned int wsum[8];
     const long long base = (long long)blockIdx.x * SCAN_BLOCK + 4 * threadIdx.x;
@@ -56,7 +59,32 @@ __global__ void k_scan_block(const unsigned int* __restrict__ in, unsigned int* 
         if (base + k < n) out[base + k] = run;
         run += v[k];
     }
-    if (threadIdx.x == 255 && bsum) bsum[blockIdx.x] = wsum[7];
+    if (threadIdx.x == 255) {
+        if (bsum) bsum[blockIdx.x] = wsum[7];
+        if (total && gridDim.x == 1) *total = wsum[7];
+    }
+}
+
+// adds the sum of the preceding block totals (computed here, no second pass);
+// the last block writes the grand total
+__global__ void k_scan_fix(unsigned int* __restrict__ out, const unsigned int* __restrict__ bsum,
+                           long long n, unsigned int* __restrict__ total)
+{
+    __shared__ unsigned int red[256];
+    unsigned int s = 0;
+    for (int j = threadIdx.x; j < (int)blockIdx.x; j += 256) s += bsum[j];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const unsigned int off = red[0];
+    const long long base = (long long)blockIdx.x * SCAN_BLOCK + 4 * threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (base + k < n) out[base + k] += off;
+    if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total = off + bsum[blockIdx.x];
 }
 
 __global__ void k_scan_add(unsigned int* __restrict__ out, const unsigned int* __restrict__ boff,
@@ -72,26 +100,33 @@ __global__ void k_scan_total(const unsigned int* in, const unsigned int* out, lo
     *total = n > 0 ? out[n - 1] + in[n - 1] : 0u;
 }
 
+constexpr long long SCAN_FIX_MAX_BLOCKS = 4096;
+
 static void scan_rec(apr_ctx* c, const unsigned int* in, unsigned int* out, long long n,
-                     unsigned int* tmp)
+                     unsigned int* tmp, unsigned int* total)
 {
     const long long nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
     if (nb <= 1) {
-        APR_LAUNCH(c, k_scan_block, 1, 256, in, out, nullptr, n);
+        APR_LAUNCH(c, k_scan_block, 1, 256, in, out, nullptr, n, total);
         return;
     }
     unsigned int* sums = tmp;
+    APR_LAUNCH(c, k_scan_block, (unsigned)nb, 256, in, out, sums, n, nullptr);
+    if (nb <= SCAN_FIX_MAX_BLOCKS) {
+        APR_LAUNCH(c, k_scan_fix, (unsigned)nb, 256, out, sums, n, total);
+        return;
+    }
     unsigned int* offs = tmp + nb;
-    APR_LAUNCH(c, k_scan_block, (unsigned)nb, 256, in, out, sums, n);
-    scan_rec(c, sums, offs, nb, tmp + 2 * nb);
+    scan_rec(c, sums, offs, nb, tmp + 2 * nb, nullptr);
     APR_LAUNCH(c, k_scan_add, nblocks(n, 256), 256, out, offs, n);
+    if (total) APR_LAUNCH(c, k_scan_total, 1, 1, in, out, n, total);
 }
 
 apr_status scan_u32(apr_ctx* c, const unsigned int* in, unsigned int* out, long long n,
                     unsigned int* total_dev)
 {
-    if (n > 0) scan_rec(c, in, out, n, c->W.scan_tmp);
-    if (total_dev) APR_LAUNCH(c, k_scan_total, 1, 1, in, out, n, total_dev);
+    if (n > 0) scan_rec(c, in, out, n, c->W.scan_tmp, total_dev);
+    else if (total_dev) cudaMemsetAsync(total_dev, 0, sizeof(unsigned int), c->stream);
     return cuda_check(c, cudaGetLastError(), "scan");
 }
 
@@ -549,45 +584,75 @@ __device__ __forceinline__ NodeBox node_box(int c, const int4* __restrict__ pk,
     return r;
 }
 
-// candidate cells: traverse the tree from the root, keep cells within reach.
-// mode 0: the cell's own reach (gather); otherwise max of both reaches (symmetric).
-__global__ void k_candidates(DevCfg dc, int mode, const int* __restrict__ ncell_dev, int n,
-                             const int* __restrict__ cell_node, const int* __restrict__ left,
-                             const int* __restrict__ right, const int4* __restrict__ pk,
-                             const unsigned long long* __restrict__ sthr,
-                             const int4* __restrict__ nlo, const int4* __restrict__ nhi,
-                             const unsigned long long* __restrict__ nthr,
-                             int2* __restrict__ cand, int* __restrict__ ncand, int* status,
-                             int graceful)
+// candidate cells: one warp per cell walks the tree from the root, popping up to
+// 32 nodes at a time from a shared-memory stack and testing them in parallel;
+// cells within reach are emitted in a fixed (lane) order, internal nodes within
+// reach push their children.  mode 0: the cell's own reach (gather); otherwise
+// the larger of the two reaches (symmetric).
+constexpr int CAND_STACK = 1024;
+
+__global__ void __launch_bounds__(128)
+    k_candidates(DevCfg dc, int mode, const int* __restrict__ ncell_dev, int n,
+                 const int* __restrict__ cell_node, const int* __restrict__ left,
+                 const int* __restrict__ right, const int4* __restrict__ pk,
+                 const unsigned long long* __restrict__ sthr, const int4* __restrict__ nlo,
+                 const int4* __restrict__ nhi, const unsigned long long* __restrict__ nthr,
+                 int2* __restrict__ cand, int* __restrict__ ncand, int* status, int graceful)
 {
+    __shared__ int stk[4][CAND_STACK];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const int ncell = *ncell_dev;
-    for (int cid = blockIdx.x * blockDim.x + threadIdx.x; cid < ncell;
-         cid += gridDim.x * blockDim.x) {
-    NodeBox me = node_box(cell_node[cid], pk, sthr, nlo, nhi, nthr);
-    const unsigned long long thr_self = me.thr;
-    int stack[128];
-    int sp = 0;
-    stack[sp++] = n >= 2 ? 0 : ~0;
-    int k = 0;
-    bool overflow = false;
-    while (sp > 0) {
-        int node = stack[--sp];
-        NodeBox o = node_box(node, pk, sthr, nlo, nhi, nthr);
-        unsigned long long thr = (mode == 0 || o.thr < thr_self) ? thr_self : o.thr;
-        if (box_dist2(dc, me.lo, me.hi, o.lo, o.hi) >= thr) continue;
-        if (o.count <= CELL_MAX) {
-            if (k < MAX_CAND) cand[(long long)cid * MAX_CAND + k] = make_int2(o.first, o.count);
-            else overflow = true;
-            ++k;
-        } else if (sp + 2 <= 128) {
-            stack[sp++] = __ldg(&right[node]);
-            stack[sp++] = __ldg(&left[node]);
-        } else {
-            overflow = true;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int cid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; cid < ncell; cid += nwarps) {
+        const NodeBox me = node_box(cell_node[cid], pk, sthr, nlo, nhi, nthr);
+        const unsigned long long thr_self = me.thr;
+        __syncwarp();
+        if (lane == 0) stk[w][0] = n >= 2 ? 0 : ~0;
+        __syncwarp();
+        int sp = 1, k = 0;
+        bool overflow = false;
+        while (sp > 0) {
+            const int take = sp < 32 ? sp : 32;
+            const bool have = lane < take;
+            const int node = have ? stk[w][sp - 1 - lane] : 0;
+            sp -= take;
+            bool pass = false, cell = false;
+            int first = 0, count = 0;
+            if (have) {
+                const NodeBox o = node_box(node, pk, sthr, nlo, nhi, nthr);
+                const unsigned long long thr = (mode == 0 || o.thr < thr_self) ? thr_self : o.thr;
+                pass = box_dist2(dc, me.lo, me.hi, o.lo, o.hi) < thr;
+                cell = o.count <= CELL_MAX;
+                first = o.first;
+                count = o.count;
+            }
+            const unsigned cm = __ballot_sync(0xffffffffu, pass && cell);
+            if (pass && cell) {
+                const int pos = k + __popc(cm & lt);
+                if (pos < MAX_CAND) cand[(long long)cid * MAX_CAND + pos] = make_int2(first, count);
+            }
+            k += __popc(cm);
+            const unsigned im = __ballot_sync(0xffffffffu, pass && !cell);
+            const int nint = __popc(im);
+            __syncwarp();  // every lane has read its node before the stack is overwritten
+            if (sp + 2 * nint > CAND_STACK) {
+                overflow = true;
+                break;
+            }
+            if (pass && !cell) {
+                const int pos = sp + 2 * __popc(im & lt);
+                stk[w][pos] = __ldg(&right[node]);
+                stk[w][pos + 1] = __ldg(&left[node]);
+            }
+            sp += 2 * nint;
+            __syncwarp();
         }
-    }
-    ncand[cid] = overflow ? -1 : k;
-    if (overflow && !graceful) atomicOr(&status[ST_CAND_OVERFLOW], 1);
+        overflow = overflow || k > MAX_CAND;
+        if (lane == 0) {
+            ncand[cid] = overflow ? -1 : k;
+            if (overflow && !graceful) atomicOr(&status[ST_CAND_OVERFLOW], 1);
+        }
     }
 }
 
@@ -736,7 +801,8 @@ apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful)
                W.cell_first, W.cell_cnt, W.cell_node);
     APR_LAUNCH(c, k_thresholds, nblocks(n, 256), 256, c->dc, n, reach, W.sh, W.sthr, W.sreach);
     if (n >= 2) APR_LAUNCH(c, k_node_thr, nblocks(n - 1, 256), 256, c->dc, n, reach, W.nhmax, W.nthr);
-    APR_LAUNCH(c, k_candidates, min(nblocks(n, 32), 152 * 16), 32, c->dc, mode, ncell_dev, n,
+    APR_LAUNCH(c, k_candidates, min(nblocks((long long)n * 32, 128), 152 * 16), 128, c->dc, mode,
+               ncell_dev, n,
                W.cell_node, W.left, W.right, W.pk, W.sthr, W.nlo, W.nhi, W.nthr, W.cand, W.ncand,
                W.status, graceful ? 1 : 0);
     if (mode == 0)

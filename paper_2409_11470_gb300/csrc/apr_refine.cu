@@ -12,6 +12,7 @@
 // with segmented reductions, then a stable partition.
 // This file is compiled without fused multiply-add contraction so that every
 // float64 operation rounds exactly as written (the geometry is bit-exact).
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <cstring>
@@ -1128,6 +1129,17 @@ __global__ void __launch_bounds__(256) k_reduce_final(int nblk, int nv,
     }
 }
 
+static apr_status reduce_readback_n(apr_ctx* c, int nblk, int nv, unsigned int min_mask,
+                                   double* host)
+{
+    APR_LAUNCH(c, k_reduce_final, 1, 256, nblk, nv, c->W.red, c->W.redout, min_mask);
+    cudaMemcpyAsync(c->hbuf, c->W.redout, sizeof(double) * nv, cudaMemcpyDeviceToHost, c->stream);
+    apr_status s = cuda_check(c, cudaStreamSynchronize(c->stream), "reduce");
+    if (s != APR_OK) return s;
+    memcpy(host, c->hbuf, sizeof(double) * nv);
+    return APR_OK;
+}
+
 static apr_status reduce_readback(apr_ctx* c, int nv, unsigned int min_mask, double* host)
 {
     APR_LAUNCH(c, k_reduce_final, 1, 256, RED_BLOCKS, nv, c->W.red, c->W.redout, min_mask);
@@ -1228,9 +1240,10 @@ static void stats_from(const apr_ctx* c, const double* r, apr_stats* st)
 
 apr_status compute_stats_dt(apr_ctx* c, apr_stats* st, double* dt)
 {
-    APR_LAUNCH(c, k_stats_dt, RED_BLOCKS, 256, c->dc, c->n, c->p, c->W.red);
+    const int nblk = (int)std::min<long long>(RED_BLOCKS, std::max<long long>(1, (c->n + 2047) / 2048));
+    APR_LAUNCH(c, k_stats_dt, nblk, 256, c->dc, c->n, c->p, c->W.red);
     double r[10];
-    apr_status s = reduce_readback(c, 10, 1u << 9, r);
+    apr_status s = reduce_readback_n(c, nblk, 10, 1u << 9, r);
     if (s != APR_OK) return s;
     stats_from(c, r, st);
     *dt = r[9];
