@@ -214,6 +214,9 @@ static apr_status check_cfg(const apr_config* cfg, DevCfg* dc, std::string* why)
     }
     dc->delta = cfg->delta;
     dc->deltaf = (float)cfg->delta;
+    dc->alpha_avf = (float)cfg->alpha_av;
+    dc->beta_avf = (float)cfg->beta_av;
+    dc->alpha_uf = (float)cfg->alpha_u;
     dc->hfact = cfg->hfact;
     dc->gamma = cfg->gamma;
     dc->eos = cfg->eos;

@@ -671,9 +671,76 @@ __global__ void k_thresholds(DevCfg dc, long long n, double reach, const double*
     rint[s] = r > 0xffffffffULL ? 0xffffffffu : (unsigned)r;
 }
 
-// exact lists: warp per cell; each candidate cell is staged in shared memory
-// and read back as broadcasts.  A candidate is rejected early by the exact
-// per-axis test |d| >= R (R^2 >= thr); the rest take the exact 64-bit r^2 < thr.
+// exact lists: warp per cell.  The particles of each candidate cell are culled
+// against the cell's bounding box first (exact: a particle whose squared gap to
+// the box is >= the larger threshold reaches no particle inside it), moved to
+// their periodic image nearest the box centre, and packed into a per-warp batch
+// in shared memory; a full batch is read back as broadcasts.  A pair is
+// rejected early by the exact per-axis test |d| >= R (R^2 >= thr); the rest
+// take the exact 64-bit r^2 < thr.  The image shift is exact while
+// w + 2R + 1 <= L on every periodic axis (w: box width): a pair whose true
+// minimum image differs from the shifted one is then at least
+// L/2 - ceil(w/2) >= R apart on that axis, so both readings reject it.
+// Batches holding a particle that breaks this take the per-pair minimum image.
+constexpr int LIST_BUF = 64;
+
+__device__ __forceinline__ int wrap_near(int d, int L)
+{
+    return 2 * d > L ? d - L : (2 * d < -L ? d + L : d);
+}
+
+// gap from coordinate v to [lo, hi], minimum over the periodic images when P
+template <int P>
+__device__ __forceinline__ long long axis_gap(int v, int lo, int hi, int L)
+{
+    long long g = max(0LL, max((long long)lo - v, (long long)v - hi));
+    if (P) {
+        long long g1 = max(0LL, max((long long)lo - (v + (long long)L), (long long)v + L - hi));
+        long long g2 = max(0LL, max((long long)lo - (v - (long long)L), (long long)v - L - hi));
+        g = min(g, min(g1, g2));
+    }
+    return g;
+}
+
+template <int PX, int PY, int PZ, int SYM, bool WRAP>
+__device__ __forceinline__ void list_batch(int nb, const int4* __restrict__ cq,
+                                           const unsigned long long* __restrict__ ct,
+                                           const unsigned int* __restrict__ cr, const int4& pa,
+                                           int a, bool own, unsigned long long ta, unsigned int Ra,
+                                           int Lx, int Ly, int Lz, int K, long long cap,
+                                           unsigned int* __restrict__ nbr, int& m)
+{
+    for (int l = 0; l < nb; ++l) {
+        const int4 q = cq[l];
+        int dx = pa.x - q.x, dy = pa.y - q.y, dz = pa.z - q.z;
+        if (WRAP) {
+            if (PX) dx = wrap_near(dx, Lx);
+            if (PY) dy = wrap_near(dy, Ly);
+            if (PZ) dz = wrap_near(dz, Lz);
+        }
+        unsigned int R = Ra;
+        if (SYM) {
+            const unsigned int Rb = cr[l];
+            R = (own && Rb > R) ? Rb : R;
+        }
+        if ((unsigned)abs(dx) >= R || (unsigned)abs(dy) >= R || (unsigned)abs(dz) >= R) continue;
+        const int b = q.w;
+        if (b == a) continue;
+        const unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
+                                      (unsigned long long)((long long)dy * dy) +
+                                      (unsigned long long)((long long)dz * dz);
+        unsigned long long th = ta;
+        if (SYM) {
+            const unsigned long long t = ct[l];
+            th = t > th ? t : th;
+        }
+        if (r2 < th) {
+            if (m < K) nbr[(long long)m * cap + a] = (unsigned)b;
+            ++m;
+        }
+    }
+}
+
 template <int PX, int PY, int PZ, int SYM>
 __global__ void __launch_bounds__(128)
     k_lists(DevCfg dc, const int* __restrict__ ncell_dev, int n, long long cap,
@@ -683,23 +750,24 @@ __global__ void __launch_bounds__(128)
             const unsigned long long* __restrict__ thr, const unsigned int* __restrict__ rint,
             unsigned int* __restrict__ nbr, int* __restrict__ ncnt, int* status, int graceful)
 {
-    __shared__ int4 cpk[4][CELL_MAX];
-    __shared__ unsigned long long cth[4][CELL_MAX];
-    __shared__ unsigned int crr[4][CELL_MAX];
+    __shared__ int4 cq[4][LIST_BUF];
+    __shared__ unsigned long long ct[4][LIST_BUF];
+    __shared__ unsigned int cr[4][LIST_BUF];
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const int ncell = *ncell_dev;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int Lx = (int)dc.Lint[0], Ly = (int)dc.Lint[1], Lz = (int)dc.Lint[2];
+    const int K = dc.max_neigh;
     for (int cid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; cid < ncell; cid += nwarps) {
     const int first = cell_first[cid], cnt = cell_cnt[cid];
     if (first < 0 || cnt < 1 || cnt > CELL_MAX || first + cnt > n) continue;
     const bool own = lane < cnt;
     const int a = first + (own ? lane : 0);
     const int4 pa = pk[a];
-    const unsigned long long ta = thr[a];
+    const unsigned long long ta = own ? thr[a] : 0ULL;
     const unsigned int Ra = own ? rint[a] : 0u;  // 0: every test fails for idle lanes
-    const int Lx = (int)dc.Lint[0], Ly = (int)dc.Lint[1], Lz = (int)dc.Lint[2];
-    const int Hx = Lx >> 1, Hy = Ly >> 1, Hz = Lz >> 1;
-    const int K = dc.max_neigh;
     int m = 0;
     const int nc = ncand[cid];
     if (nc < 0) {  // candidate list overflowed: every list of this cell is incomplete
@@ -707,43 +775,86 @@ __global__ void __launch_bounds__(128)
         if (!graceful && lane == 0) atomicOr(&status[ST_NEIGH_OVERFLOW], 1);
         continue;
     }
+    // the cell's box, largest threshold and largest R
+    const int lox = __reduce_min_sync(FULL, own ? pa.x : INT_MAX);
+    const int loy = __reduce_min_sync(FULL, own ? pa.y : INT_MAX);
+    const int loz = __reduce_min_sync(FULL, own ? pa.z : INT_MAX);
+    const int hix = __reduce_max_sync(FULL, own ? pa.x : INT_MIN);
+    const int hiy = __reduce_max_sync(FULL, own ? pa.y : INT_MIN);
+    const int hiz = __reduce_max_sync(FULL, own ? pa.z : INT_MIN);
+    const unsigned th_hi = __reduce_max_sync(FULL, (unsigned)(ta >> 32));
+    const unsigned th_lo = __reduce_max_sync(FULL, (unsigned)(ta >> 32) == th_hi ? (unsigned)ta : 0u);
+    const unsigned long long tcell = ((unsigned long long)th_hi << 32) | th_lo;
+    const unsigned int rcell = __reduce_max_sync(FULL, Ra);
+    const int cx = lox + ((hix - lox) >> 1), cy = loy + ((hiy - loy) >> 1), cz = loz + ((hiz - loz) >> 1);
+    int nb = 0;
+    bool wrapb = false;
     for (int j = 0; j < nc; ++j) {
         const int2 cb = cand[(long long)cid * MAX_CAND + j];
         if (cb.x < 0 || cb.y < 0 || cb.y > CELL_MAX || cb.x + cb.y > n) continue;
-        __syncwarp();
+        bool keep = false, nw = false;
+        int4 q = make_int4(0, 0, 0, 0);
+        unsigned long long tq = 0;
+        unsigned int rq = 0;
         if (lane < cb.y) {
-            cpk[w][lane] = pk[cb.x + lane];
-            cth[w][lane] = thr[cb.x + lane];
-            crr[w][lane] = rint[cb.x + lane];
+            const int b = cb.x + lane;
+            q = pk[b];
+            q.w = b;
+            tq = thr[b];
+            rq = rint[b];
+            const unsigned long long T = (SYM && tq > tcell) ? tq : tcell;
+            const long long gx = axis_gap<PX>(q.x, lox, hix, Lx);
+            const long long gy = axis_gap<PY>(q.y, loy, hiy, Ly);
+            const long long gz = axis_gap<PZ>(q.z, loz, hiz, Lz);
+            keep = (unsigned long long)(gx * gx) + (unsigned long long)(gy * gy) +
+                       (unsigned long long)(gz * gz) < T;
+            if (keep) {
+                const long long R2 = 2LL * (long long)((SYM && rq > rcell) ? rq : rcell);
+                if (PX) {
+                    q.x = cx + wrap_near(q.x - cx, Lx);
+                    nw = nw || (long long)(hix - lox) + R2 + 1 > Lx;
+                }
+                if (PY) {
+                    q.y = cy + wrap_near(q.y - cy, Ly);
+                    nw = nw || (long long)(hiy - loy) + R2 + 1 > Ly;
+                }
+                if (PZ) {
+                    q.z = cz + wrap_near(q.z - cz, Lz);
+                    nw = nw || (long long)(hiz - loz) + R2 + 1 > Lz;
+                }
+            }
         }
+        const unsigned km = __ballot_sync(FULL, keep);
+        wrapb = wrapb || __any_sync(FULL, nw);
+        if (keep) {
+            const int pos = nb + __popc(km & lt);
+            cq[w][pos] = q;
+            if (SYM) {
+                ct[w][pos] = tq;
+                cr[w][pos] = rq;
+            }
+        }
+        nb += __popc(km);
         __syncwarp();
-        for (int l = 0; l < cb.y; ++l) {
-            const int4 q = cpk[w][l];
-            int dx = pa.x - q.x, dy = pa.y - q.y, dz = pa.z - q.z;
-            if (PX) dx = dx > Hx ? dx - Lx : (dx < -Hx ? dx + Lx : dx);
-            if (PY) dy = dy > Hy ? dy - Ly : (dy < -Hy ? dy + Ly : dy);
-            if (PZ) dz = dz > Hz ? dz - Lz : (dz < -Hz ? dz + Lz : dz);
-            unsigned int R = Ra;
-            if (SYM) {
-                const unsigned int Rb = crr[w][l];
-                R = (own && Rb > R) ? Rb : R;
-            }
-            if ((unsigned)abs(dx) >= R || (unsigned)abs(dy) >= R || (unsigned)abs(dz) >= R) continue;
-            const int b = cb.x + l;
-            if (b == a) continue;
-            const unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
-                                          (unsigned long long)((long long)dy * dy) +
-                                          (unsigned long long)((long long)dz * dz);
-            unsigned long long th = ta;
-            if (SYM) {
-                const unsigned long long t = cth[w][l];
-                th = t > th ? t : th;
-            }
-            if (r2 < th) {
-                if (m < K) nbr[(long long)m * cap + a] = (unsigned)b;
-                ++m;
-            }
+        if (nb >= 32) {
+            if (wrapb)
+                list_batch<PX, PY, PZ, SYM, true>(nb, cq[w], ct[w], cr[w], pa, a, own, ta, Ra, Lx, Ly,
+                                                  Lz, K, cap, nbr, m);
+            else
+                list_batch<PX, PY, PZ, SYM, false>(nb, cq[w], ct[w], cr[w], pa, a, own, ta, Ra, Lx, Ly,
+                                                   Lz, K, cap, nbr, m);
+            nb = 0;
+            wrapb = false;
+            __syncwarp();
         }
+    }
+    if (nb > 0) {
+        if (wrapb)
+            list_batch<PX, PY, PZ, SYM, true>(nb, cq[w], ct[w], cr[w], pa, a, own, ta, Ra, Lx, Ly, Lz,
+                                              K, cap, nbr, m);
+        else
+            list_batch<PX, PY, PZ, SYM, false>(nb, cq[w], ct[w], cr[w], pa, a, own, ta, Ra, Lx, Ly, Lz,
+                                               K, cap, nbr, m);
     }
     if (own) {
         ncnt[a] = m > K ? -1 : m;

@@ -67,6 +67,7 @@ struct DevCfg {
     int eos;
     double cs0, qcs;
     double alpha_av, beta_av, alpha_u;
+    float alpha_avf, beta_avf, alpha_uf;  // the same in float for the FP32 pair loops
     double rsep_fac, dnn_cap;
     double m0;
     int lmax;

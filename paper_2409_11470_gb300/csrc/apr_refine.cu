@@ -651,19 +651,39 @@ __global__ void __launch_bounds__(TREE_LOC_THREADS)
             }
         }
         __syncthreads();
-        // odd cuts: the particle that crosses
-        for (int p = tid; p < s; p += TREE_LOC_THREADS) {
-            int seg = S.Lo[cur][p], size = S.Hi[cur][p] - seg;
-            if (size <= 2) continue;
-            Cut c = make_cut(size, (int)S.ak[seg], (int)S.ak2[seg]);
-            if (c.coincident || c.kfinal == c.k) continue;
-            int q = S.P[cur][p];
-            long long com = (long long)(S.asum[seg] / (unsigned long long)size);
-            long long v = lcomp(S, q, laxis(S, seg));
-            bool low = c.use_le ? v <= com : v < com;
-            unsigned long long key = ((unsigned long long)v << 32) | S.I[q];
-            if (c.kfinal < c.k && low) atomicMax(&S.akey[seg], key);
-            if (c.kfinal > c.k && !low) atomicMin(&S.akey2[seg], key);
+        // odd cuts: the particle that crosses (reduced per warp, one atomic per segment run)
+        for (int p0 = 0; p0 < s; p0 += TREE_LOC_THREADS) {
+            int p = p0 + tid;
+            bool act = false, down = false;
+            int seg = 0, v = 0;
+            unsigned idx = 0;
+            if (p < s) {
+                seg = S.Lo[cur][p];
+                int size = S.Hi[cur][p] - seg;
+                if (size > 2) {
+                    Cut c = make_cut(size, (int)S.ak[seg], (int)S.ak2[seg]);
+                    if (!c.coincident && c.kfinal != c.k) {
+                        int q = S.P[cur][p];
+                        long long com = (long long)(S.asum[seg] / (unsigned long long)size);
+                        v = lcomp(S, q, laxis(S, seg));
+                        bool low = c.use_le ? v <= com : v < com;
+                        down = c.kfinal < c.k;
+                        act = down ? low : !low;
+                        idx = S.I[q];
+                    }
+                }
+            }
+            // the cut direction is a property of the segment, so peers share it
+            unsigned peers = seg_peers(act, seg);
+            if (act) {
+                if (down) {
+                    unsigned long long k0 = warp_max_key(peers, true, v, idx);
+                    if (seg_leader(peers)) atomicMax(&S.akey[seg], k0);
+                } else {
+                    unsigned long long k1 = warp_min_key(peers, true, v, idx);
+                    if (seg_leader(peers)) atomicMin(&S.akey2[seg], k1);
+                }
+            }
         }
         __syncthreads();
         // low flags

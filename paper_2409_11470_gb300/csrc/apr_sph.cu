@@ -416,7 +416,17 @@ __device__ __forceinline__ void force_pair(const DevCfg& dc, const ForceSelf<R>&
     R fa, dfa, fb, dfb;
     m4<R>(qa, fa, dfa);
     m4<R>(qb, fb, dfb);
-    const R alpha = (R)dc.alpha_av, beta = (R)dc.beta_av;
+    // float copies of the coefficients: no double-to-float conversion per pair
+    R alpha, beta, alpha_u;
+    if constexpr (sizeof(R) == 4) {
+        alpha = dc.alpha_avf;
+        beta = dc.beta_avf;
+        alpha_u = dc.alpha_uf;
+    } else {
+        alpha = dc.alpha_av;
+        beta = dc.beta_av;
+        alpha_u = dc.alpha_u;
+    }
     const R Fa = dfa * A.h4;
     const R Fb = dfb * (hinv_b * hinv_b * hinv_b * hinv_b);
     const R vr = ((A.vx - Vb.x) * d[0] + (A.vy - Vb.y) * d[1] + (A.vz - Vb.z) * d[2]) * rinv;
@@ -437,7 +447,7 @@ __device__ __forceinline__ void force_pair(const DevCfg& dc, const ForceSelf<R>&
         if (cond) {
             const R dP = A.P - Bb.x;
             const R vsu = Num<R>::sqrt_(fabs(dP) / (R(0.5) * (A.rho + Ab.w)));
-            e += mub * (R)dc.alpha_u * vsu * (A.u - Vb.w) * R(0.5) * (Fa * A.ior + Fb * Bb.y);
+            e += mub * alpha_u * vsu * (A.u - Vb.w) * R(0.5) * (Fa * A.ior + Fb * Bb.y);
         }
         du.add(e);
     }

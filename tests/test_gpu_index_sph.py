@@ -36,17 +36,22 @@ def test_neighbour_lists_bit_exact(make, mode):
         assert np.array_equal(ro, rg)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("n", [0, 1, 5, 31, 32, 33, 100])
-def test_neighbour_lists_small_and_ragged(n):
+def test_neighbour_lists_small_and_ragged(n, mode):
+    # a periodic box only a few smoothing lengths wide: pairs near half the box
+    # take the per-pair minimum image
     w = apr_synth.lattice_box(6, 0.3, seed=n + 1)
     w["p"] = {k: v[:n] for k, v in w["p"].items()}
+    if mode == 1 and n > 1:
+        w = _variable_h(w, seed=n)
     g = sim(w, capacity=max(n, 1) * 2)
-    off_g, idx_g = g.neighbour_lists(0)
+    off_g, idx_g = g.neighbour_lists(mode)
     if n == 0:
         assert len(off_g) == 1 and len(idx_g) == 0
         return
     o = oracle.Oracle(w)
-    off_o, idx_o = o.neighbours(0)
+    off_o, idx_o = o.neighbours(mode)
     assert np.array_equal(off_o, off_g)
     for ro, rg in zip(rows(off_o, idx_o), rows(off_g, idx_g)):
         assert np.array_equal(ro, rg)
