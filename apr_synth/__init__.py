@@ -232,6 +232,42 @@ def c5_adjoint_lattice(n_side=126):
                        name=f"c5_lattice{n_side ** 3}")
 
 
+def adjoint_problem(w, radius=None, centre=(0.5, 0.5, 0.5), seed=SEED_BASE + 4, rsep=0.2,
+                    subset=2048):
+    """Inputs of one split's density-error loss on the particle set ``w``.
+
+    Splits: every particle closer than ``radius`` (default: the first region's outer
+    radius) to ``centre`` on the periodic unit box, in ascending index.  Offsets:
+    a uniform random direction times ``rsep * h_p * U(0.5, 1.5)``.  Child smoothing
+    lengths: ``h_p * U(0.75, 0.85)`` each.  ``want``: the ``subset`` splits nearest the
+    centre (ties by index), the set on which gradients are compared at full size.
+    Returns dict(parent, d (k x 3), hc (2k), want (k, bool)).
+    """
+    p = w["p"]
+    if radius is None:
+        radius = w["regions"][0]["R"][0]
+    rng = np.random.default_rng(seed)
+    sep = []
+    for k, key in enumerate(("x", "y", "z")):
+        dd = p[key] - centre[k]
+        if w["cfg"]["periodic"][k]:
+            L = w["cfg"]["box_hi"][k] - w["cfg"]["box_lo"][k]
+            dd = dd - L * np.round(dd / L)
+        sep.append(dd)
+    r2 = sep[0] ** 2 + sep[1] ** 2 + sep[2] ** 2
+    parent = np.nonzero(r2 < radius * radius)[0].astype(np.int64)
+    k = len(parent)
+    v = rng.normal(size=(k, 3))
+    v /= np.maximum(np.linalg.norm(v, axis=1, keepdims=True), 1e-300)
+    hp = p["h"][parent]
+    d = v * (rsep * hp * rng.uniform(0.5, 1.5, k))[:, None]
+    hc = np.repeat(hp, 2) * rng.uniform(0.75, 0.85, 2 * k)
+    order = np.lexsort((parent, r2[parent]))
+    want = np.zeros(k, bool)
+    want[order[:subset]] = True
+    return dict(parent=parent, d=np.ascontiguousarray(d), hc=np.ascontiguousarray(hc), want=want)
+
+
 def copy_workload(w, capacity=None):
     """Deep copy with particle arrays grown to ``capacity`` (new slots zeroed)."""
     import copy

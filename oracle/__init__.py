@@ -163,6 +163,9 @@ def lib():
             L.orc_step.restype = C.c_int
             L.orc_step.argtypes = [P(Cfg), P(State), P(Region), C.c_int, P(Sink), C.c_int,
                                    C.c_double, C.c_ulonglong, P(Counts), P(Stats)]
+            L.orc_split_loss_grad.restype = C.c_int
+            L.orc_split_loss_grad.argtypes = [P(Cfg), P(State), C.c_longlong, P(C.c_longlong), _DP,
+                                              _DP, _UP, _DP, _DP, _DP]
             _lib = L
     return _lib
 
@@ -370,6 +373,30 @@ class Oracle:
         if rc < 0:
             raise RuntimeError("oracle init: capacity exhausted")
         return rc
+
+    def split_loss_grad(self, parent, d, hc, want=None):
+        """Density error J of splitting ``parent[k]`` into children at x_p +- d[k] with
+        smoothing lengths hc[2k], hc[2k+1], against the current particles as the
+        reference set; returns (J, dJ/dd (k x 3), dJ/dhc (2k)).  ``want`` (bool per split)
+        restricts the gradient to those splits (the rest are 0)."""
+        par = np.ascontiguousarray(parent, np.int64)
+        k = len(par)
+        dd = np.ascontiguousarray(np.reshape(d, (k, 3)), np.float64)
+        hh = np.ascontiguousarray(hc, np.float64)
+        if hh.shape != (2 * k,):
+            raise ValueError("hc needs two smoothing lengths per split")
+        wnt = None if want is None else np.ascontiguousarray(want, np.uint8)
+        J = C.c_double(0.0)
+        gd = np.zeros((k, 3))
+        gh = np.zeros(2 * k)
+        rc = self.L.orc_split_loss_grad(
+            C.byref(self.cfg), C.byref(self.st), k, par.ctypes.data_as(C.POINTER(C.c_longlong)),
+            dd.ctypes.data_as(_DP), hh.ctypes.data_as(_DP),
+            None if wnt is None else wnt.ctypes.data_as(_UP), C.byref(J), gd.ctypes.data_as(_DP),
+            gh.ctypes.data_as(_DP))
+        if rc != 0:
+            raise ValueError("split_loss_grad: parent out of range, dead or repeated")
+        return J.value, gd, gh
 
     def step(self, dt):
         cnt, stt = Counts(), Stats()

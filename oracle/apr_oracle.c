@@ -31,6 +31,12 @@
  *          conductivity (the paper cites them, Sec. 3 and Sec. 4) -- a proposed
  *          reading, pinned by conservation laws, a lattice, a linear pressure
  *          gradient and the Sod shock tube closed form.
+ *   density error of one split pass and its gradient with respect to the
+ *          children's offsets and smoothing lengths (h held fixed): not in the
+ *          paper, which motivates it (Sec. 2.2 r_sep choice, Sec. 2.5 relaxing
+ *          to the original density); pinned by a hand-worked isolated split,
+ *          exact reproduction when children sit on their parent, periodic
+ *          translation invariance and central finite differences.
  *
  * Decisions (neighbour membership, nearest-neighbour distance, the pairing
  * tree's cuts) are taken on a quantised integer lattice x_int = floor((x-lo)/D)
@@ -1330,5 +1336,199 @@ int orc_step(const orc_cfg* c, orc_state* s, orc_region* rg, int nr, orc_sink* k
     for (int j = 0; j < nk; ++j)
         for (int d = 0; d < 3; ++d) k[j].v[d] += hdt * k[j].a[d];
     orc_stats_compute(c, s, k, nk, st);
+    return 0;
+}
+
+/* ------------------------------------------- density error of a split, adjoint */
+
+/*
+ * The density error that one split pass creates, and its gradient with respect
+ * to the children's offsets and smoothing lengths.  The paper has no such
+ * function: Sec. 2.2 picks r_sep and Sec. 2.5 relaxes children so that the new
+ * distribution reproduces the density of the original one; this is a
+ * differentiable statement of that error.
+ *
+ * Reference set: the live particles of s, at their own h.  Split k replaces
+ * parent[k] by two children at x_p + d_k (child 2k) and x_p - d_k (child 2k+1),
+ * one level finer (Eq. 1 mass), with smoothing lengths hc[2k], hc[2k+1].  The
+ * new set is the reference set without the parents, plus the children.
+ *
+ *   rho_new(a)  = sum_{b in new set} m_b W(|x_a - x_b|, h_a)    (self included)
+ *   rho_ref(x)  = sum_{b in reference set} m_b W(|x - x_b|, h_b)
+ *   J           = sum_{children a} (rho_new(a) - rho_ref(x_a))^2
+ *
+ * With W' = dW/dr = f'(q) / (pi h^4), u_ab = (x_a - x_b)/|x_a - x_b| and
+ * e_a = rho_new(a) - rho_ref(x_a):
+ *   dJ/dx_a = 2 e_a [ sum_{b new, b != a} m_b W'(r_ab, h_a) u_ab
+ *                     - sum_{b ref} m_b W'(r_ab, h_b) u_ab ]
+ *             + sum_{children c != a} 2 e_c m_a W'(r_ac, h_c) u_ac
+ *   dJ/dh_a = 2 e_a sum_{b new} m_b dW/dh(r_ab, h_a),
+ *             dW/dh = -(3 f(q) + q f'(q)) / (pi h^4)
+ *   dJ/dd_k = dJ/dx_(child 2k) - dJ/dx_(child 2k+1)
+ *
+ * Gradients are computed for the splits with want[k] != 0 (all if want is
+ * NULL; the rest are set to 0); J always covers every child.  Returns 0, or -1
+ * if a parent index is out of range, dead or repeated.
+ */
+#define ORC_ROLE_NEW 1u
+#define ORC_ROLE_REF 2u
+#define ORC_ROLE_CHILD 4u
+
+static void free_state_arrays(orc_state* t)
+{
+    free(t->x);
+    free(t->y);
+    free(t->z);
+    free(t->h);
+    free(t->level);
+    free(t->flags);
+}
+
+int orc_split_loss_grad(const orc_cfg* c, const orc_state* s, long long npar,
+                        const long long* parent, const double* d, const double* hc,
+                        const unsigned char* want, double* J, double* grad_d, double* grad_hc)
+{
+    const long long n = s->n, nt = n + 2 * npar;
+    orc_state T;
+    memset(&T, 0, sizeof(T));
+    T.n = nt;
+    T.cap = nt;
+    size_t sz = (size_t)(nt > 0 ? nt : 1);
+    T.x = (double*)malloc(sizeof(double) * sz);
+    T.y = (double*)malloc(sizeof(double) * sz);
+    T.z = (double*)malloc(sizeof(double) * sz);
+    T.h = (double*)malloc(sizeof(double) * sz);
+    T.level = (unsigned char*)malloc(sz);
+    T.flags = (unsigned char*)malloc(sz);
+    unsigned char* role = (unsigned char*)malloc(sz);
+    for (long long i = 0; i < n; ++i) {
+        T.x[i] = s->x[i];
+        T.y[i] = s->y[i];
+        T.z[i] = s->z[i];
+        T.h[i] = s->h[i];
+        T.level[i] = s->level[i];
+        T.flags[i] = is_live(s, i) ? 0 : ORC_FLAG_DEAD;
+        role[i] = is_live(s, i) ? (ORC_ROLE_NEW | ORC_ROLE_REF) : 0;
+    }
+    for (long long k = 0; k < npar; ++k) {
+        long long p = parent[k];
+        if (p < 0 || p >= n || role[p] != (ORC_ROLE_NEW | ORC_ROLE_REF)) {
+            free_state_arrays(&T);
+            free(role);
+            return -1;
+        }
+        role[p] = ORC_ROLE_REF; /* the parent leaves the new set */
+        double xp[3] = {s->x[p], s->y[p], s->z[p]};
+        for (int side = 0; side < 2; ++side) {
+            long long j = n + 2 * k + side;
+            double sg = side == 0 ? 1.0 : -1.0, q[3];
+            for (int m = 0; m < 3; ++m) q[m] = wrap1(c, m, xp[m] + sg * d[3 * k + m]);
+            T.x[j] = q[0];
+            T.y[j] = q[1];
+            T.z[j] = q[2];
+            T.h[j] = hc[2 * k + side];
+            T.level[j] = (unsigned char)(s->level[p] + 1);
+            T.flags[j] = 0;
+            role[j] = ORC_ROLE_NEW | ORC_ROLE_CHILD;
+        }
+    }
+    double hmax = 0.0;
+    for (long long i = 0; i < nt; ++i)
+        if (role[i] && T.h[i] > hmax) hmax = T.h[i];
+    cellgrid grid, *g = NULL;
+    if (c->enumerate && nt > 0) {
+        grid_build(c, &T, 2.0 * hmax, &grid);
+        g = &grid;
+    }
+    double* e = (double*)calloc(sz, sizeof(double));
+    set_threads(c);
+    /* forward: the density error of every child */
+#pragma omp parallel
+    {
+        blist L = {0};
+#pragma omp for schedule(dynamic, 64)
+        for (long long a = n; a < nt; ++a) {
+            gather_within(c, &T, g, a, 2.0 * hmax, &L);
+            const double ha = T.h[a];
+            double rho_new = 0.0, rho_ref = 0.0;
+            for (long long t = 0; t < L.n; ++t) {
+                long long b = L.idx[t];
+                double r = sqrt(L.r2[t]), mb = mass_of(c, T.level[b]), f, df;
+                if (role[b] & ORC_ROLE_NEW) {
+                    m4(r / ha, &f, &df);
+                    rho_new += mb * f / (M_PI * ha * ha * ha);
+                }
+                if (role[b] & ORC_ROLE_REF) {
+                    double hb = T.h[b];
+                    m4(r / hb, &f, &df);
+                    rho_ref += mb * f / (M_PI * hb * hb * hb);
+                }
+            }
+            e[a] = rho_new - rho_ref;
+        }
+        free(L.idx);
+        free(L.r2);
+    }
+    double sum = 0.0;
+    for (long long a = n; a < nt; ++a) sum += e[a] * e[a];
+    *J = sum;
+    /* reverse: gradients of the wanted splits */
+#pragma omp parallel
+    {
+        blist L = {0};
+#pragma omp for schedule(dynamic, 16)
+        for (long long k = 0; k < npar; ++k) {
+            if (want && !want[k]) {
+                for (int m = 0; m < 3; ++m) grad_d[3 * k + m] = 0.0;
+                grad_hc[2 * k] = grad_hc[2 * k + 1] = 0.0;
+                continue;
+            }
+            double gx[2][3];
+            for (int side = 0; side < 2; ++side) {
+                long long a = n + 2 * k + side;
+                gather_within(c, &T, g, a, 2.0 * hmax, &L);
+                const double ha = T.h[a], ma = mass_of(c, T.level[a]);
+                double own[3] = {0.0, 0.0, 0.0}, rev[3] = {0.0, 0.0, 0.0}, dh = 0.0;
+                for (long long t = 0; t < L.n; ++t) {
+                    long long b = L.idx[t];
+                    double r = sqrt(L.r2[t]), mb = mass_of(c, T.level[b]), f, df;
+                    double sep[3] = {0.0, 0.0, 0.0};
+                    if (b != a && r > 0.0) { /* coincident pairs: f'(0) = 0, no direction */
+                        sep64(c, &T, a, b, sep);
+                        for (int m = 0; m < 3; ++m) sep[m] /= r; /* u_ab */
+                    }
+                    if (role[b] & ORC_ROLE_NEW) {
+                        double q = r / ha;
+                        m4(q, &f, &df);
+                        dh += mb * (-(3.0 * f + q * df) / (M_PI * ha * ha * ha * ha));
+                        if (b != a)
+                            for (int m = 0; m < 3; ++m)
+                                own[m] += mb * (df / (M_PI * ha * ha * ha * ha)) * sep[m];
+                    }
+                    if (role[b] & ORC_ROLE_REF) {
+                        double hb = T.h[b];
+                        m4(r / hb, &f, &df);
+                        for (int m = 0; m < 3; ++m)
+                            own[m] -= mb * (df / (M_PI * hb * hb * hb * hb)) * sep[m];
+                    }
+                    if ((role[b] & ORC_ROLE_CHILD) && b != a) {
+                        double hb = T.h[b];
+                        m4(r / hb, &f, &df);
+                        for (int m = 0; m < 3; ++m)
+                            rev[m] += 2.0 * e[b] * ma * (df / (M_PI * hb * hb * hb * hb)) * sep[m];
+                    }
+                }
+                for (int m = 0; m < 3; ++m) gx[side][m] = 2.0 * e[a] * own[m] + rev[m];
+                grad_hc[2 * k + side] = 2.0 * e[a] * dh;
+            }
+            for (int m = 0; m < 3; ++m) grad_d[3 * k + m] = gx[0][m] - gx[1][m];
+        }
+        free(L.idx);
+        free(L.r2);
+    }
+    if (g) grid_free(g);
+    free(e);
+    free(role);
+    free_state_arrays(&T);
     return 0;
 }
