@@ -245,6 +245,44 @@ apr_status apr_merge_pairs(apr_ctx* ctx, int level, long long* pairs, long long 
                            long long* npairs, long long* spare);
 
 /*
+ * Density error of one split pass and its gradient (adjoint).  The paper's
+ * method has no such call: it chooses the child separation (Sec. 2.2, Eq. 2)
+ * and relaxes new children (Sec. 2.5) so that the split set reproduces the
+ * density of the original set; this call measures that error and its gradient
+ * with respect to the children's offsets and smoothing lengths, so that child
+ * placement can be optimised.
+ *
+ * Reference set: the n bound particles as they are, each at its own h (dead
+ * ones take no part).  Split k replaces parent[k] by two children at
+ * x_p + d[k] and x_p - d[k], one level finer (mass by Eq. 1), with smoothing
+ * lengths hc[2k] and hc[2k+1].  The new set is the reference set without the
+ * parents, plus the children.
+ *   J = sum over children a of (rho_new(a) - rho_ref(x_a))^2
+ *   rho_new(a) = sum over the new set of m_b W(|x_a - x_b|, h_a)   (h fixed, self included)
+ *   rho_ref(x) = sum over the reference set of m_b W(|x - x_b|, h_b)
+ * M4 kernel, minimum image on periodic axes.
+ *
+ * parent: DEVICE, npar int64 indices into [0, n), each live and used once.
+ * d: DEVICE, npar x 3 float64, row-major.  hc: DEVICE, 2*npar float64, > 0.
+ * loss: HOST, receives J.  grad_d: DEVICE npar x 3 float64 (dJ/dd), grad_hc:
+ * DEVICE 2*npar float64 (dJ/dhc).  All buffers are the caller's.  Pair sums
+ * run in float on relative lattice coordinates with compensated accumulation
+ * (double with APR_PREC_FP64); J is reduced in float64 in a fixed order.
+ *
+ * Needs n + 2*npar <= capacity, else APR_ERR_CAPACITY and nothing is written.
+ * The spare bound slots [n, n + 2*npar) are scratch: on return they hold the
+ * children (x, y, z, h, level), each child's density error in rho and its
+ * position and h gradients in ax, ay, az and dudt.  Particles [0, n) and the
+ * count n are unchanged; the next density or force call rebuilds the index.
+ * APR_ERR_ARG for a bad split (parent out of range, dead or repeated, an
+ * offset not finite, hc not finite and positive); APR_ERR_NEIGH_OVERFLOW if a
+ * list exceeds max_neigh.  Synchronises the stream.
+ */
+apr_status apr_density_loss_grad(apr_ctx* ctx, long long npar, const long long* parent,
+                                 const double* d, const double* hc, double* loss, double* grad_d,
+                                 double* grad_hc);
+
+/*
  * Profiling (not part of the method): on != 0 starts timing kernel groups with
  * CUDA events on the bound stream and counting pair evaluations, and clears
  * the counters; on == 0 stops.  The event pool is created here, not in the

@@ -106,6 +106,7 @@ def _load():
         "apr_merge_pairs": [vp, i32, P(ll), ll, P(ll), P(ll)],
         "apr_profile_enable": [vp, i32],
         "apr_profile_read": [vp, P(Profile), i32],
+        "apr_density_loss_grad": [vp, ll, vp, vp, vp, P(C.c_double), vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -330,6 +331,26 @@ class Simulation:
         out["launches"] = pr.launches
         return out
 
+    def density_loss_grad(self, parent, d, hc):
+        """Density error J of splitting ``parent[k]`` into children at x_p +- d[k] with
+        smoothing lengths hc[2k], hc[2k+1] (the current particles are the reference
+        set), and its gradients: returns (J, dJ/dd (k x 3), dJ/dhc (2k)) with the
+        gradients as float64 tensors on the device."""
+        torch = self.torch
+        dev = self.device
+        par = torch.as_tensor(parent, dtype=torch.int64, device=dev).contiguous()
+        k = par.numel()
+        dd = torch.as_tensor(d, dtype=torch.float64, device=dev).reshape(k, 3).contiguous()
+        hh = torch.as_tensor(hc, dtype=torch.float64, device=dev).reshape(2 * k).contiguous()
+        gd = torch.empty((k, 3), dtype=torch.float64, device=dev)
+        gh = torch.empty(2 * k, dtype=torch.float64, device=dev)
+        J = C.c_double(0.0)
+        self._check(lib.apr_density_loss_grad(self.ctx, k, C.c_void_p(par.data_ptr()),
+                                              C.c_void_p(dd.data_ptr()), C.c_void_p(hh.data_ptr()),
+                                              C.byref(J), C.c_void_p(gd.data_ptr()),
+                                              C.c_void_p(gh.data_ptr())), "density_loss_grad")
+        return J.value, gd, gh
+
     def merge_pairs(self, level):
         n = self.n
         cap = max(1, n // 2)
@@ -339,3 +360,38 @@ class Simulation:
                                         pairs.ctypes.data_as(C.POINTER(C.c_longlong)), cap,
                                         C.byref(npairs), C.byref(spare)), "merge_pairs")
         return pairs[: 2 * npairs.value].reshape(-1, 2), spare.value
+
+
+def _loss_function():
+    import torch
+
+    class SplitDensityLoss(torch.autograd.Function):
+        """J(d, hc) of one split pass as an autograd op.  The forward call runs the
+        library's density-error forward and reverse sweeps (apr_density_loss_grad)
+        and keeps both gradients; backward only scales them by the incoming
+        gradient of J."""
+
+        @staticmethod
+        def forward(ctx, d, hc, sim, parent):
+            J, gd, gh = sim.density_loss_grad(parent, d.detach(), hc.detach())
+            ctx.save_for_backward(gd, gh)
+            return torch.tensor(J, dtype=torch.float64, device=d.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            gd, gh = ctx.saved_tensors
+            return gJ * gd, gJ * gh, None, None
+
+    return SplitDensityLoss
+
+
+_LOSS_FN = None
+
+
+def split_density_loss(sim, parent, d, hc):
+    """Differentiable J for ``torch.autograd``: gradients flow to ``d`` (k x 3) and
+    ``hc`` (2k), both float64 tensors on the simulation's device."""
+    global _LOSS_FN
+    if _LOSS_FN is None:
+        _LOSS_FN = _loss_function()
+    return _LOSS_FN.apply(d, hc, sim, parent)

@@ -24,6 +24,7 @@ UNITS = {
     "apr_sph.cu": [],
     "apr_refine.cu": ["--fmad=false"],
     "apr_noalloc.cu": [],
+    "apr_adjoint.cu": [],
 }
 
 

@@ -622,6 +622,41 @@ apr_status apr_neighbour_lists(apr_ctx* c, int mode, long long* offsets, int* id
     return APR_OK;
 }
 
+apr_status apr_density_loss_grad(apr_ctx* c, long long npar, const long long* parent,
+                                 const double* d, const double* hc, double* loss, double* grad_d,
+                                 double* grad_hc)
+{
+    if (!c || !loss || npar < 0) return APR_ERR_ARG;
+    if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    *loss = 0.0;
+    if (npar > 0 && (!parent || !d || !hc || !grad_d || !grad_hc))
+        return fail(c, APR_ERR_ARG, "density loss: null pointer");
+    const long long n = c->n;
+    if (npar > (c->cap - n) / 2)
+        return fail(c, APR_ERR_CAPACITY, "density loss needs n + 2 npar <= capacity");
+    if (npar == 0) return APR_OK;
+    bool bad = false;
+    apr_status s = adjoint_children(c, npar, parent, d, hc, &bad);
+    if (s != APR_OK) return s;
+    if (bad)
+        return fail(c, APR_ERR_ARG,
+                    "density loss: a parent is out of range, dead or repeated, or an offset or "
+                    "smoothing length is not finite and positive");
+    // the index over the combined set; the bound count is restored on every path
+    c->n = n + 2 * npar;
+    s = index_sort(c);
+    if (s == APR_OK) {
+        cudaMemsetAsync(c->W.status, 0, 2 * sizeof(int), c->stream);
+        s = index_lists(c, 1, 1.0);
+    }
+    if (s == APR_OK) s = check_overflow(c);
+    if (s == APR_OK) s = adjoint_sums(c, n, npar, loss, grad_d, grad_hc);
+    c->n = n;
+    c->have_force = false;
+    c->dt_valid = false;
+    return s;
+}
+
 apr_status apr_profile_enable(apr_ctx* c, int on)
 {
     if (!c) return APR_ERR_ARG;

@@ -35,6 +35,7 @@ enum {
     ST_TREE_BAD = 7,         // radix tree walk left its bounds (must never happen)
     ST_SHRINK = 8,           // density: lists overflowed, h shrunk for a retry
     ST_NCELL = 9,            // number of cells of the current index
+    ST_ADJ_BAD = 10,         // density loss: a bad split in the input
     ST_BINS = 16,            // merge: first slot of each level's candidates (10 words)
     ST_MERGES = 32,          // merge: merges per level (8 words)
     ST_NSTATUS = 16
@@ -283,6 +284,11 @@ apr_status drift(apr_ctx* c, double dt);
 apr_status compute_stats(apr_ctx* c, apr_stats* st);
 apr_status compute_timestep(apr_ctx* c, double* dt);
 apr_status compute_stats_dt(apr_ctx* c, apr_stats* st, double* dt);
+// density error of a split and its adjoint (apr_adjoint.cu)
+apr_status adjoint_children(apr_ctx* c, long long npar, const long long* parent, const double* d,
+                            const double* hc, bool* bad);
+apr_status adjoint_sums(apr_ctx* c, long long n, long long npar, double* loss, double* grad_d,
+                        double* grad_hc);
 apr_status compact(apr_ctx* c, long long* removed);
 
 inline int nblocks(long long n, int bs) { return (int)((n + bs - 1) / bs); }
