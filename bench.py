@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the side measurements (disc, flyby, split adjoint)")
+    ap.add_argument("--extra-steps", type=int, default=10)
     ap.add_argument("--nL", type=int, default=28, help="shock-tube resolution (28 = full size)")
     ap.add_argument("--ncu-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu "
@@ -73,22 +76,81 @@ def workload(nL):
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
+    """SM clock and clock-event reasons sampled while the timed region runs.
+
+    Reads NVML (libnvidia-ml, read-only queries) from a thread every 2 ms; falls
+    back to ``nvidia-smi -lms 200`` if NVML cannot be loaded.  Nothing is set."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, bus_id=None):
+    def __init__(self, uuid=None):
+        self.sm, self.mx, self.bits = [], [], 0
+        self.source = None
+        self._stop = False
+        try:
+            self._nvml_start(uuid)
+            self.source = "nvml"
+        except Exception:
+            self._smi_start()
+            self.source = "nvidia-smi"
+
+    def _nvml_start(self, uuid):
+        import ctypes
+        import threading
+        L = ctypes.CDLL("libnvidia-ml.so.1")
+        if L.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit")
+        h = ctypes.c_void_p()
+        if uuid:
+            rc = L.nvmlDeviceGetHandleByUUID(str(uuid).encode(), ctypes.byref(h))
+        else:
+            cnt = ctypes.c_uint(0)
+            L.nvmlDeviceGetCount_v2(ctypes.byref(cnt))
+            if cnt.value != 1:
+                raise OSError("several GPUs and no UUID")
+            rc = L.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(h))
+        if rc != 0:
+            raise OSError("nvml handle")
+        reasons = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            L.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint(0)
+        L.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+        self.mx.append(float(mx.value))
+
+        def run():
+            clk, bits = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+            while not self._stop:
+                if L.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0:
+                    self.sm.append(float(clk.value))
+                if reasons(h, ctypes.byref(bits)) == 0:
+                    self.bits |= bits.value
+                time.sleep(0.002)
+
+        self.thread = threading.Thread(target=run, daemon=True)
+        self.thread.start()
+        time.sleep(0.01)  # first samples before the timed region starts
+
+    def _smi_start(self):
         self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                "-lms", "200"]
-        if bus_id:
-            cmd += ["-i", bus_id]
         try:
             self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
 
     def stop(self):
+        if self.source == "nvml":
+            self._stop = True
+            self.thread.join(timeout=2)
+            reasons = sorted(v for b, v in self.REASONS.items() if self.bits & b)
+            return {"sm_mhz": statistics.median(self.sm) if self.sm else None,
+                    "sm_max_mhz": max(self.mx) if self.mx else None, "reasons": reasons,
+                    "samples": len(self.sm), "source": "nvml, every 2 ms"}
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -106,7 +168,7 @@ class ClockSampler:
                           if r[5 + k].strip().lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi -lms 200"}
 
 
 # ----------------------------------------------------------- our arm
@@ -166,13 +228,14 @@ def run_ours(args):
     for _ in range(args.warmup):
         sim.step(0.0)
     props = torch.cuda.get_device_properties(local)
-    bus = getattr(props, "pci_bus_id", None)
+    uuid = getattr(props, "uuid", None)
+    uuid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else uuid
     sim.profile_enable(True)
     launches0 = sim.profile()["launches"]  # kernels launched before the timed region
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    sampler = ClockSampler(bus)
+    sampler = ClockSampler(uuid)
     if args.ncu_range:
         torch.cuda.cudart().cudaProfilerStart()
     t_wall = time.perf_counter()
@@ -275,12 +338,103 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = oracle_baseline(w, cap, args.cpu_seconds)
 
+    if rank == 0 and not args.no_extra:
+        sim.close()
+        out["other_workloads"] = side_measurements(args, torch, flush)
+
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-    sim.close()
+    sim.close()  # idempotent
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------- side measurements
+
+def _workload_rate(w, precision, steps, warmup, torch, flush, cap_factor, max_neigh=0):
+    from paper_2409_11470_gb300.binding import Simulation
+    n0 = len(w["p"]["x"])
+    sim = Simulation(w, capacity=int(cap_factor * n0) + 1024, precision=precision,
+                     max_neigh=max_neigh)
+    sim.init()
+    n_init = sim.n
+    m_sinks0 = sum(k["m"] for k in sim.sinks())
+    for _ in range(warmup):
+        sim.step(0.0)
+    sim.profile_enable(True)
+    ms, psteps = timed_steps(sim, torch, steps, flush)
+    prof = sim.profile()
+    sim.profile_enable(False)
+    res = {"value": psteps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+           "n_after_init": n_init, "n_last": sim.n,
+           "sink_mass_gain": sum(k["m"] for k in sim.sinks()) - m_sinks0,
+           "breakdown_ms_per_step": {g: round(prof[g]["ms"] / steps, 3) for g in
+                                     ("sort", "tree", "lists", "density", "force", "refine",
+                                      "other")},
+           "density_calls_per_step": prof["density"]["calls"] / steps}
+    sim.close()
+    return res
+
+
+def side_measurements(args, torch, flush):
+    """The disc workloads and the split adjoint, each on its own: particle-steps/s
+    of whole steps (FP32-mixed and FP64) and loss+gradient evaluations/s."""
+    import apr_synth
+    out = {}
+    k = max(1, args.extra_steps)
+    # the discs' Gaussian vertical tails put up to ~1240 particles inside 2.25 h of a
+    # tail particle (measured on the oracle's converged state): lists of 2048
+    for name, make, cap_factor, fp64 in (
+            ("disc_planet_1e6_3level_sphere", apr_synth.disc_planet, 1.6, True),
+            ("flyby_disc_8e6_2level_sphere", apr_synth.flyby, 1.2, True)):
+        try:
+            w = make()
+            r = {"n_initial": len(w["p"]["x"]), "max_neigh": 2048,
+                 "fp32": _workload_rate(w, "fp32", k, 2, torch, flush, cap_factor, 2048)}
+            if fp64:
+                r["fp64"] = _workload_rate(w, "fp64", max(2, k // 3), 1, torch, flush, cap_factor,
+                                           2048)
+                r["fp32_over_fp64"] = r["fp32"]["value"] / r["fp64"]["value"]
+            out[name] = r
+        except Exception as e:  # a side measurement never takes the headline down
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+    try:
+        out["split_adjoint_c5_2000376p"] = adjoint_rate(torch, k)
+    except Exception as e:
+        out["split_adjoint_c5_2000376p"] = {"error": f"{type(e).__name__}: {e}"}
+    return out
+
+
+def adjoint_rate(torch, k):
+    """apr_density_loss_grad on the 126^3 jittered lattice, first split pass of the
+    R = 0.35 zone: evaluations (J and the full gradient) per second."""
+    import apr_synth
+    from paper_2409_11470_gb300.binding import Simulation
+    w = apr_synth.c5_adjoint_lattice()
+    prob = apr_synth.adjoint_problem(w)
+    n, npar = len(w["p"]["x"]), len(prob["parent"])
+    sim = Simulation(w, capacity=n + 2 * npar, precision="fp32")
+    dev = sim.device
+    par = torch.as_tensor(prob["parent"], device=dev)
+    d = torch.as_tensor(prob["d"], device=dev)
+    hc = torch.as_tensor(prob["hc"], device=dev)
+    for _ in range(2):
+        J0 = sim.density_loss_grad(par, d, hc)[0]
+    st = sim.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(k):
+        sim.density_loss_grad(par, d, hc)
+    e1.record(st)
+    st.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    sim.close()
+    return {"evals_per_s": 1e3 / ms, "ms_per_eval": ms, "particles": n, "splits": npar,
+            "children": 2 * npar, "children_per_s": 2 * npar * 1e3 / ms, "J": J0,
+            "precision": "fp32 pair sums, fp64 reduction",
+            "note": "one evaluation = children placed, index over the combined set, forward "
+                    "and reverse sweeps, chain rule to the offsets, J read back"}
 
 
 # ------------------------------------------------------------ the oracle

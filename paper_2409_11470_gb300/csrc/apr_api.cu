@@ -142,6 +142,7 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.cmark = (int*)take(4 * C);
     w.cand = (int2*)take(8 * (size_t)MAX_CAND * C);
     w.ncand = (int*)take(4 * C);
+    w.point_q = (int*)take(4 * C);
     // the list memory doubles as compaction scratch (20 x 8 bytes per particle)
     w.nbr = (unsigned int*)take((4 * K > 160 ? 4 * K : 160) * C);
     w.ncnt = (int*)take(4 * C);

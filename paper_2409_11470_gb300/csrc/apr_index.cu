@@ -649,19 +649,19 @@ __global__ void __launch_bounds__(128)
             __syncwarp();
         }
         overflow = overflow || k > MAX_CAND;
-        if (lane == 0) {
-            ncand[cid] = overflow ? -1 : k;
-            if (overflow && !graceful) atomicOr(&status[ST_CAND_OVERFLOW], 1);
-        }
+        // an overflowed cell is not an error: its particles take the per-particle search
+        if (lane == 0) ncand[cid] = overflow ? -1 : k;
     }
 }
 
 // per particle: the squared-distance threshold and the smallest integer R with
 // R^2 >= thr (every neighbour has |dx|, |dy|, |dz| < R on the lattice)
 __global__ void k_thresholds(DevCfg dc, long long n, double reach, const double* __restrict__ sh,
-                             unsigned long long* __restrict__ thr, unsigned int* __restrict__ rint)
+                             unsigned long long* __restrict__ thr, unsigned int* __restrict__ rint,
+                             int* status)
 {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s == 0) status[ST_POINT_N] = 0;  // the per-particle queue of this list build
     if (s >= n) return;
     const unsigned long long t = neighbour_threshold(reach * sh[s], dc.delta);
     thr[s] = t;
@@ -748,7 +748,8 @@ __global__ void __launch_bounds__(128)
             const int* __restrict__ cell_cnt, const int2* __restrict__ cand,
             const int* __restrict__ ncand, const int4* __restrict__ pk,
             const unsigned long long* __restrict__ thr, const unsigned int* __restrict__ rint,
-            unsigned int* __restrict__ nbr, int* __restrict__ ncnt, int* status, int graceful)
+            unsigned int* __restrict__ nbr, int* __restrict__ ncnt, int* __restrict__ point_q,
+            int* status, int graceful)
 {
     __shared__ int4 cq[4][LIST_BUF];
     __shared__ unsigned long long ct[4][LIST_BUF];
@@ -770,9 +771,11 @@ __global__ void __launch_bounds__(128)
     const unsigned int Ra = own ? rint[a] : 0u;  // 0: every test fails for idle lanes
     int m = 0;
     const int nc = ncand[cid];
-    if (nc < 0) {  // candidate list overflowed: every list of this cell is incomplete
-        if (own) ncnt[a] = -1;
-        if (!graceful && lane == 0) atomicOr(&status[ST_NEIGH_OVERFLOW], 1);
+    if (nc < 0) {  // candidate list overflowed: this cell's particles search one by one
+        if (own) {
+            const int q = atomicAdd(&status[ST_POINT_N], 1);
+            if (q < n) point_q[q] = a;
+        }
         continue;
     }
     // the cell's box, largest threshold and largest R
@@ -864,6 +867,109 @@ __global__ void __launch_bounds__(128)
     }
 }
 
+// the particles of cells whose candidate-cell list overflowed (a large cell in a
+// sparse region with a large smoothing length): one warp per particle walks the
+// radix tree with the particle's own point-to-box test and tests the particles
+// of every cell within reach exactly, a cell at a time in lane order
+template <int PX, int PY, int PZ, int SYM>
+__global__ void __launch_bounds__(128)
+    k_lists_point(DevCfg dc, const int* __restrict__ qlen, const int* __restrict__ point_q, int n,
+                  long long cap, const int* __restrict__ left, const int* __restrict__ right,
+                  const int4* __restrict__ pk, const unsigned long long* __restrict__ sthr,
+                  const int4* __restrict__ nlo, const int4* __restrict__ nhi,
+                  const unsigned long long* __restrict__ nthr, unsigned int* __restrict__ nbr,
+                  int* __restrict__ ncnt, int* status, int graceful)
+{
+    __shared__ int stk[4][CAND_STACK];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int nq = min(*qlen, n);
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int Lx = (int)dc.Lint[0], Ly = (int)dc.Lint[1], Lz = (int)dc.Lint[2];
+    const int K = dc.max_neigh;
+    for (int qi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; qi < nq; qi += nwarps) {
+        const int a = point_q[qi];
+        if (a < 0 || a >= n) continue;
+        const int4 pa = pk[a];
+        const unsigned long long ta = sthr[a];
+        __syncwarp();
+        if (lane == 0) stk[w][0] = n >= 2 ? 0 : ~0;
+        __syncwarp();
+        int sp = 1, m = 0;
+        bool overflow = false;
+        while (sp > 0) {
+            const int take = sp < 32 ? sp : 32;
+            const bool have = lane < take;
+            const int node = have ? stk[w][sp - 1 - lane] : 0;
+            sp -= take;
+            bool pass = false, cell = false;
+            int first = 0, count = 0;
+            if (have) {
+                const NodeBox o = node_box(node, pk, sthr, nlo, nhi, nthr);
+                const unsigned long long T = (SYM && o.thr > ta) ? o.thr : ta;
+                const long long gx = axis_gap<PX>(pa.x, o.lo[0], o.hi[0], Lx);
+                const long long gy = axis_gap<PY>(pa.y, o.lo[1], o.hi[1], Ly);
+                const long long gz = axis_gap<PZ>(pa.z, o.lo[2], o.hi[2], Lz);
+                pass = (unsigned long long)(gx * gx) + (unsigned long long)(gy * gy) +
+                           (unsigned long long)(gz * gz) < T;
+                cell = o.count <= CELL_MAX;
+                first = o.first;
+                count = o.count;
+            }
+            unsigned cm = __ballot_sync(FULL, pass && cell);
+            while (cm) {
+                const int src = __ffs(cm) - 1;
+                cm &= cm - 1;
+                const int f = __shfl_sync(FULL, first, src), cnt = __shfl_sync(FULL, count, src);
+                const int b = f + lane;
+                bool hit = false;
+                if (lane < cnt && b >= 0 && b < n && b != a) {
+                    const int4 q = pk[b];
+                    int dx = pa.x - q.x, dy = pa.y - q.y, dz = pa.z - q.z;
+                    if (PX) dx = wrap_near(dx, Lx);
+                    if (PY) dy = wrap_near(dy, Ly);
+                    if (PZ) dz = wrap_near(dz, Lz);
+                    const unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
+                                                  (unsigned long long)((long long)dy * dy) +
+                                                  (unsigned long long)((long long)dz * dz);
+                    unsigned long long th = ta;
+                    if (SYM) {
+                        const unsigned long long tb = sthr[b];
+                        th = tb > th ? tb : th;
+                    }
+                    hit = r2 < th;
+                }
+                const unsigned hm = __ballot_sync(FULL, hit);
+                if (hit) {
+                    const int pos = m + __popc(hm & lt);
+                    if (pos < K) nbr[(long long)pos * cap + a] = (unsigned)b;
+                }
+                m += __popc(hm);
+            }
+            const unsigned im = __ballot_sync(FULL, pass && !cell);
+            const int nint = __popc(im);
+            __syncwarp();  // every lane has read its node before the stack is overwritten
+            if (sp + 2 * nint > CAND_STACK) {
+                overflow = true;
+                break;
+            }
+            if (pass && !cell) {
+                const int pos = sp + 2 * __popc(im & lt);
+                stk[w][pos] = __ldg(&right[node]);
+                stk[w][pos + 1] = __ldg(&left[node]);
+            }
+            sp += 2 * nint;
+            __syncwarp();
+        }
+        if (lane == 0) {
+            const bool over = overflow || m > K;
+            ncnt[a] = over ? -1 : m;
+            if (over && !graceful) atomicOr(&status[ST_NEIGH_OVERFLOW], 1);
+        }
+    }
+}
+
 template <int SYM>
 static void launch_lists(apr_ctx* c, const int* ncell_dev, int n, bool graceful)
 {
@@ -874,8 +980,11 @@ static void launch_lists(apr_ctx* c, const int* ncell_dev, int n, bool graceful)
 #define APR_LISTS_CASE(M, X, Y, Z)                                                                   \
     case M:                                                                                          \
         APR_LAUNCH(c, (k_lists<X, Y, Z, SYM>), grid, 128, c->dc, ncell_dev, n, c->cap, W.cell_first, \
-                   W.cell_cnt, W.cand, W.ncand, W.pk, W.sthr, W.sreach, W.nbr, W.ncnt, W.status,     \
-                   graceful ? 1 : 0);                                                                \
+                   W.cell_cnt, W.cand, W.ncand, W.pk, W.sthr, W.sreach, W.nbr, W.ncnt, W.point_q,    \
+                   W.status, graceful ? 1 : 0);                                                      \
+        APR_LAUNCH(c, (k_lists_point<X, Y, Z, SYM>), 152 * 4, 128, c->dc, &W.status[ST_POINT_N],     \
+                   W.point_q, n, c->cap, W.left, W.right, W.pk, W.sthr, W.nlo, W.nhi, W.nthr, W.nbr, \
+                   W.ncnt, W.status, graceful ? 1 : 0);                                              \
         break;
     switch (mask) {
         APR_LISTS_CASE(0, 0, 0, 0)
@@ -910,7 +1019,8 @@ apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful)
     scan_u32(c, W.cflag, W.cscan, n, (unsigned*)ncell_dev);
     APR_LAUNCH(c, k_cells_compact, nblocks(n, 256), 256, n, W.cflag, W.cscan, W.cmark, W.nlo,
                W.cell_first, W.cell_cnt, W.cell_node);
-    APR_LAUNCH(c, k_thresholds, nblocks(n, 256), 256, c->dc, n, reach, W.sh, W.sthr, W.sreach);
+    APR_LAUNCH(c, k_thresholds, nblocks(n, 256), 256, c->dc, n, reach, W.sh, W.sthr, W.sreach,
+               W.status);
     if (n >= 2) APR_LAUNCH(c, k_node_thr, nblocks(n - 1, 256), 256, c->dc, n, reach, W.nhmax, W.nthr);
     APR_LAUNCH(c, k_candidates, min(nblocks((long long)n * 32, 128), 152 * 16), 128, c->dc, mode,
                ncell_dev, n,

@@ -36,6 +36,7 @@ enum {
     ST_SHRINK = 8,           // density: lists overflowed, h shrunk for a retry
     ST_NCELL = 9,            // number of cells of the current index
     ST_ADJ_BAD = 10,         // density loss: a bad split in the input
+    ST_POINT_N = 11,         // lists: particles queued for the per-particle search
     ST_BINS = 16,            // merge: first slot of each level's candidates (10 words)
     ST_MERGES = 32,          // merge: merges per level (8 words)
     ST_NSTATUS = 16
@@ -140,6 +141,7 @@ struct Workspace {
     int* cmark;               // node of the cell starting at a sorted slot
     int2* cand;               // MAX_CAND (first slot, count) per cell
     int* ncand;
+    int* point_q;             // particles of cells whose candidate list overflowed
     // neighbour lists, transposed: nbr[k * cap + sorted slot]
     unsigned int* nbr;
     int* ncnt;

@@ -21,10 +21,19 @@ def _variable_h(w, seed=2):
     return w
 
 
+def _few_wide(w, h=0.2, count=3, seed=3):
+    """A few particles whose 2h spans most of the box: their cells overflow the
+    candidate-cell list and take the per-particle tree search."""
+    rng = np.random.default_rng(seed)
+    w["p"]["h"][rng.choice(len(w["p"]["h"]), count, replace=False)] = h
+    return w
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("make", [apr_synth.c1_lattice,
                                   lambda: apr_synth.lattice_box(11, 0.2, seed=5),
-                                  lambda: _variable_h(apr_synth.sod(8, slab=()))])
+                                  lambda: _variable_h(apr_synth.sod(8, slab=())),
+                                  lambda: _few_wide(apr_synth.lattice_box(14, 0.2, seed=8))])
 def test_neighbour_lists_bit_exact(make, mode):
     w = make()
     o = oracle.Oracle(w)
