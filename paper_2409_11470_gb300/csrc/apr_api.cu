@@ -165,6 +165,7 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.acc_k2 = (unsigned int*)take(4 * C * 2);
     w.acc_key = (unsigned long long*)take(8 * C * 8);
     w.lflag = (unsigned int*)take(4 * C);
+    w.coop = (unsigned int*)take(4 * (2 * COOP_MAX_BLOCKS + 16));
     w.red = (double*)take(8 * 32 * (size_t)RED_BLOCKS);
     w.redout = (double*)take(8 * 32);
     w.bytes = align256(off);
@@ -350,6 +351,7 @@ apr_status apr_create(apr_ctx** out, const apr_config* cfg, void* stream)
     c->stream = (cudaStream_t)stream;
     c->bound = false;
     c->have_force = false;
+    c->coop_blocks = 0;
     c->n = c->cap = c->next_id = 0;
     c->step = 0;
     c->nreg = c->nsink = 0;

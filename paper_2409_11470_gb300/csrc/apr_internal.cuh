@@ -37,11 +37,13 @@ enum {
     ST_NCELL = 9,            // number of cells of the current index
     ST_ADJ_BAD = 10,         // density loss: a bad split in the input
     ST_POINT_N = 11,         // lists: particles queued for the per-particle search
+    ST_TREE_ERR = 12,        // pairing tree: 1 barrier timeout, 2 leaves not reached
     ST_BINS = 16,            // merge: first slot of each level's candidates (10 words)
     ST_MERGES = 32,          // merge: merges per level (8 words)
     ST_NSTATUS = 16
 };
 
+constexpr int COOP_MAX_BLOCKS = 2048;  // blocks of the cooperative pairing-tree kernel
 constexpr int PROF_POOL = 256;              // event pairs recorded before a drain
 
 // launch a kernel on the context's stream and count it
@@ -163,6 +165,7 @@ struct Workspace {
     unsigned int* acc_k2;
     unsigned long long* acc_key;
     unsigned int* lflag;
+    unsigned int* coop;       // pairing-tree rounds: block totals, offsets, barrier, counters
     // reductions
     double* red;              // RED_BLOCKS x 32 partial sums
     double* redout;           // 32 final sums
@@ -192,6 +195,7 @@ struct apr_ctx {
     std::string err;
     bool bound;
     bool have_force;
+    int coop_blocks;          // co-resident blocks of the pairing-tree kernel (0: unknown)
     int ncell;
     int last_shrink;
     bool tree_smem_set;       // dynamic shared memory opt-in of the pairing-tree kernel

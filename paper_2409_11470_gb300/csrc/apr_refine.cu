@@ -208,12 +208,12 @@ __global__ void k_split_apply(DevCfg dc, DevRegions rg, int total, long long n,
 //
 // The candidates of every level are paired at once (their trees are
 // independent): one stable radix pass groups them by level in ascending
-// index order; global level-synchronous rounds cut every segment larger than
-// TREE_LOCAL; then one CTA per chunk finishes its segments in shared memory.
+// index order; a cooperative kernel cuts every segment larger than TREE_WARP
+// round by round; then one warp per segment finishes it in registers.
 
-constexpr int TREE_LOCAL = 512;      // largest segment left to the shared-memory phase
-constexpr int TREE_LOC_CAP = 1024;   // positions one CTA can hold (< 2 * TREE_LOCAL)
-constexpr int TREE_LOC_THREADS = 256;
+constexpr int TREE_WARP = 32;          // segments of at most this size finish in one warp
+constexpr int COOP_THREADS = 1024;
+constexpr unsigned BARRIER_SPIN_LIMIT = 1u << 22;  // polls of ~32 ns + latency: well above 0.1 s
 
 struct LevelOffsets {
     int off[APR_MAXLEV + 2];  // candidates of level l occupy [off[l], off[l+1])
@@ -343,40 +343,7 @@ __global__ void k_seg_setup(int M, LevelOffsets lo_off, int* __restrict__ lo, in
         lo[p] = p;
         hi[p] = p + 1;
     }
-    if (p == a && be - a > TREE_LOCAL) acc_reset_all(A, a);
-}
-
-__global__ void k_tree_bbox_sum(int m, int thresh, const unsigned int* __restrict__ set,
-                                const int* __restrict__ lo, const int* __restrict__ hi,
-                                const int4* __restrict__ xi, SegAcc A)
-{
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    bool act = false;
-    int seg = 0;
-    int4 q = make_int4(0, 0, 0, 0);
-    if (p < m) {
-        seg = lo[p];
-        act = hi[p] - seg > thresh;
-        if (act) q = xi[set[p]];
-    }
-    unsigned peers = seg_peers(act, seg);
-    if (!act) return;
-    const bool lead = seg_leader(peers);
-    int mnx = __reduce_min_sync(peers, q.x), mny = __reduce_min_sync(peers, q.y),
-        mnz = __reduce_min_sync(peers, q.z);
-    int mxx = __reduce_max_sync(peers, q.x), mxy = __reduce_max_sync(peers, q.y),
-        mxz = __reduce_max_sync(peers, q.z);
-    if (lead) {
-        atomicMin(&A.lo[seg].x, mnx);
-        atomicMin(&A.lo[seg].y, mny);
-        atomicMin(&A.lo[seg].z, mnz);
-        atomicMax(&A.hi[seg].x, mxx);
-        atomicMax(&A.hi[seg].y, mxy);
-        atomicMax(&A.hi[seg].z, mxz);
-    }
-    warp_sum_u64(peers, (unsigned)q.x, lead, &A.sum[3 * seg + 0]);
-    warp_sum_u64(peers, (unsigned)q.y, lead, &A.sum[3 * seg + 1]);
-    warp_sum_u64(peers, (unsigned)q.z, lead, &A.sum[3 * seg + 2]);
+    if (p == a && be - a > TREE_WARP) acc_reset_all(A, a);
 }
 
 // largest (v, idx) over the lanes in `peers` that have pred; 0 if none
@@ -402,11 +369,101 @@ __device__ __forceinline__ long long seg_com(const SegAcc& A, int seg, int size,
     return (long long)(A.sum[3 * seg + ax] / (unsigned long long)size);
 }
 
-__global__ void k_tree_count_key(int m, int thresh, const unsigned int* __restrict__ set,
-                                 const int* __restrict__ lo, const int* __restrict__ hi,
-                                 const int4* __restrict__ xi, SegAcc A)
+
+// ---- global rounds: one cooperative persistent kernel
+//
+// Every round cuts all segments larger than TREE_WARP at once, in three phases
+// separated by grid barriers: (B) counts below the centre of mass and the keys
+// an odd cut could move; (C) low flags and their prefix within each block's
+// chunk, and the reset of the children's accumulators; (D) the chunk offsets
+// (scanned again in every block), the stable partition into the other
+// buffers, and the children's bounding boxes and coordinate sums for the next
+// round.  The loop ends on the device when no segment is larger than
+// TREE_WARP.  The grid is no larger than the number of co-resident blocks
+// (cooperative launch), so every barrier is reached by all blocks; each wait
+// is still bounded and records a timeout.
+
+struct Coop {
+    unsigned* btot;     // per block: low flags in its chunk
+    unsigned* bar;      // [0] arrivals, [1] generation
+    int* maxseg;        // [3], rotating: largest open segment after a round
+    int* rounds;        // rounds taken
+    int* err;           // 1: a barrier wait timed out; 2: the leaves were not reached
+};
+
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned* p)
 {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// all blocks of the (co-resident) grid: the block's writes before, everyone's after
+__device__ __forceinline__ void grid_barrier(const Coop& co)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned* gen = co.bar + 1;
+        const unsigned g = ld_relaxed_gpu(gen);
+        if (atom_add_acq_rel_gpu(co.bar, 1u) == gridDim.x - 1) {
+            atomicExch(co.bar, 0u);
+            red_add_release_gpu(gen, 1u);
+        } else {
+            // poll without acquire semantics, then acquire once
+            unsigned it = 0;
+            while (ld_relaxed_gpu(gen) == g) {
+                if (++it > BARRIER_SPIN_LIMIT) {
+                    atomicOr(co.err, 1);
+                    break;
+                }
+            }
+        }
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    }
+    __syncthreads();
+}
+
+// one particle's bounding box and coordinate sums into its segment (warp-aggregated)
+__device__ __forceinline__ void accumulate_box_sum(bool act, int seg, const int4& q, const SegAcc& A)
+{
+    unsigned peers = seg_peers(act, seg);
+    if (!act) return;
+    const bool lead = seg_leader(peers);
+    int mnx = __reduce_min_sync(peers, q.x), mny = __reduce_min_sync(peers, q.y),
+        mnz = __reduce_min_sync(peers, q.z);
+    int mxx = __reduce_max_sync(peers, q.x), mxy = __reduce_max_sync(peers, q.y),
+        mxz = __reduce_max_sync(peers, q.z);
+    if (lead) {
+        atomicMin(&A.lo[seg].x, mnx);
+        atomicMin(&A.lo[seg].y, mny);
+        atomicMin(&A.lo[seg].z, mnz);
+        atomicMax(&A.hi[seg].x, mxx);
+        atomicMax(&A.hi[seg].y, mxy);
+        atomicMax(&A.hi[seg].z, mxz);
+    }
+    warp_sum_u64(peers, (unsigned)q.x, lead, &A.sum[3 * seg + 0]);
+    warp_sum_u64(peers, (unsigned)q.y, lead, &A.sum[3 * seg + 1]);
+    warp_sum_u64(peers, (unsigned)q.z, lead, &A.sum[3 * seg + 2]);
+}
+
+__device__ __forceinline__ void round_count_key(int p, int m, int thresh,
+                                                const unsigned int* __restrict__ set,
+                                                const int* __restrict__ lo,
+                                                const int* __restrict__ hi,
+                                                const int4* __restrict__ xi, const SegAcc& A)
+{
     bool act = false;
     int seg = 0, v = 0;
     unsigned idx = 0;
@@ -442,323 +499,568 @@ __global__ void k_tree_count_key(int m, int thresh, const unsigned int* __restri
     }
 }
 
-__global__ void k_tree_flag(int m, int thresh, const unsigned int* __restrict__ set,
-                            const int* __restrict__ lo, const int* __restrict__ hi,
-                            const int4* __restrict__ xi, SegAcc A, unsigned int* __restrict__ lflag)
+__device__ __forceinline__ unsigned round_flag(int p, int thresh, const unsigned int* __restrict__ set,
+                                               const int* __restrict__ lo, const int* __restrict__ hi,
+                                               const int4* __restrict__ xi, const SegAcc& A)
 {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= m) return;
     int seg = lo[p], size = hi[p] - seg;
-    if (size <= thresh) {
-        lflag[p] = 0;
-        return;
-    }
+    if (size <= thresh) return 0u;
     Cut c = make_cut(size, (int)A.k[seg], (int)A.k2[seg]);
+    if (c.coincident) return (p - seg) < c.kfinal ? 1u : 0u;  // segments keep ascending index order
     unsigned idx = set[p];
-    bool left;
-    if (c.coincident) {
-        left = (p - seg) < c.kfinal;  // segments stay in ascending index order
-    } else {
-        const int ax = seg_axis(A.lo[seg], A.hi[seg]);
-        const long long com = seg_com(A, seg, size, ax);
-        long long v = comp(xi[idx], ax);
-        left = c.use_le ? v <= com : v < com;
-        unsigned long long key = ((unsigned long long)v << 32) | idx;
-        const int kk = c.use_le ? 2 : 0;
-        if (c.kfinal < c.k && key == A.key[4 * seg + kk]) left = false;
-        if (c.kfinal > c.k && key == A.key[4 * seg + kk + 1]) left = true;
-    }
-    lflag[p] = left ? 1u : 0u;
+    const int ax = seg_axis(A.lo[seg], A.hi[seg]);
+    const long long com = seg_com(A, seg, size, ax);
+    long long v = comp(xi[idx], ax);
+    bool left = c.use_le ? v <= com : v < com;
+    unsigned long long key = ((unsigned long long)v << 32) | idx;
+    const int kk = c.use_le ? 2 : 0;
+    if (c.kfinal < c.k && key == A.key[4 * seg + kk]) left = false;
+    if (c.kfinal > c.k && key == A.key[4 * seg + kk + 1]) left = true;
+    return left ? 1u : 0u;
 }
 
-__global__ void k_tree_scatter(int m, int thresh, const unsigned int* __restrict__ set,
-                               const int* __restrict__ lo, const int* __restrict__ hi, SegAcc A,
-                               const unsigned int* __restrict__ lflag,
-                               const unsigned int* __restrict__ lscan, unsigned int* __restrict__ set2,
-                               int* __restrict__ lo2, int* __restrict__ hi2, SegAcc An, int* maxseg)
+// exclusive block scan of one value per thread; returns the block total in *total
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned* total)
 {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= m) return;
-    int seg = lo[p], end = hi[p], size = end - seg;
-    int np = p, nlo = seg, nhi = end;
-    if (size > thresh) {
-        Cut c = make_cut(size, (int)A.k[seg], (int)A.k2[seg]);
-        int before = (int)(lscan[p] - lscan[seg]);  // low items before p in this segment
-        if (lflag[p]) {
-            np = seg + before;
-            nhi = seg + c.kfinal;
-        } else {
-            np = seg + c.kfinal + ((p - seg) - before);
-            nlo = seg + c.kfinal;
-        }
-        if (nhi - nlo > thresh) atomicMax(maxseg, nhi - nlo);
+    __shared__ unsigned wsum[COOP_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
     }
-    set2[np] = set[p];
-    lo2[np] = nlo;
-    hi2[np] = nhi;
-    if (np == nlo && nhi - nlo > thresh) acc_reset_all(An, np);
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    unsigned before = 0, all = 0;
+    for (int w = 0; w < COOP_THREADS / 32; ++w) {
+        if (w < wid) before += wsum[w];
+        all += wsum[w];
+    }
+    __syncthreads();
+    *total = all;
+    return before + incl - v;
 }
 
-// ---- shared-memory phase: every segment of size <= TREE_LOCAL, one CTA per chunk
+__global__ void __launch_bounds__(COOP_THREADS)
+    k_tree_rounds(int M, int thresh, int max_rounds, const int4* __restrict__ xi,
+                  unsigned int* set0, unsigned int* set1, int* lo0, int* lo1, int* hi0, int* hi1,
+                  SegAcc A0, SegAcc A1, unsigned int* lflag, unsigned int* lscan, Coop co)
+{
+    __shared__ unsigned s_off[COOP_MAX_BLOCKS];
+    __shared__ int s_stop;
+    const int G = gridDim.x;
+    const int gtid = blockIdx.x * COOP_THREADS + threadIdx.x, gstride = G * COOP_THREADS;
+    const int chunk = (M + G - 1) / G;
+    // round 0's boxes and sums (accumulators reset by the setup kernel)
+    for (int p0 = 0; p0 < M; p0 += gstride) {
+        const int p = p0 + gtid;
+        bool act = false;
+        int seg = 0;
+        int4 q = make_int4(0, 0, 0, 0);
+        if (p < M) {
+            seg = lo0[p];
+            act = hi0[p] - seg > thresh;
+            if (act) q = xi[set0[p]];
+        }
+        accumulate_box_sum(act, seg, q, A0);
+    }
+    grid_barrier(co);
+    int cur = 0, r = 0;
+    while (r < max_rounds) {
+        // this round's buffers (selected, not indexed, so that they stay in registers)
+        unsigned int* const sc = cur ? set1 : set0;
+        unsigned int* const sn = cur ? set0 : set1;
+        const int* const lc = cur ? lo1 : lo0;
+        int* const ln = cur ? lo0 : lo1;
+        const int* const hc = cur ? hi1 : hi0;
+        int* const hn = cur ? hi0 : hi1;
+        const SegAcc Ac = cur ? A1 : A0;
+        const SegAcc An = cur ? A0 : A1;
+        if (gtid == 0) co.maxseg[(r + 1) % 3] = 0;
+        // (B) counts below the centre of mass and the odd-cut keys
+        for (int p0 = 0; p0 < M; p0 += gstride) round_count_key(p0 + gtid, M, thresh, sc, lc, hc, xi, Ac);
+        grid_barrier(co);
+        // (C) low flags and their prefix within this block's chunk; the children's
+        // accumulators are reset by the thread at the start of the parent segment
+        {
+            const int c0 = blockIdx.x * chunk, c1 = min(M, c0 + chunk);
+            unsigned run = 0;
+            for (int base = c0; base < c1; base += COOP_THREADS) {
+                const int p = base + threadIdx.x;
+                unsigned f = 0u;
+                if (p < c1) {
+                    f = round_flag(p, thresh, sc, lc, hc, xi, Ac);
+                    const int seg = lc[p], size = hc[p] - seg;
+                    if (p == seg && size > thresh) {
+                        const Cut c = make_cut(size, (int)Ac.k[seg], (int)Ac.k2[seg]);
+                        if (c.kfinal > thresh) acc_reset_all(An, seg);
+                        if (size - c.kfinal > thresh) acc_reset_all(An, seg + c.kfinal);
+                    }
+                }
+                unsigned tot;
+                const unsigned ex = block_exclusive_scan(f, &tot);
+                if (p < c1) {
+                    lflag[p] = f;
+                    lscan[p] = run + ex;
+                }
+                run += tot;
+            }
+            if (threadIdx.x == 0) co.btot[blockIdx.x] = run;
+        }
+        grid_barrier(co);
+        // (D) chunk offsets (every block scans them), stable partition, and the
+        // children's boxes and sums for the next round
+        {
+            unsigned run = 0;
+            for (int base = 0; base < G; base += COOP_THREADS) {
+                const int j = base + threadIdx.x;
+                const unsigned v = j < G ? __ldcg(&co.btot[j]) : 0u;
+                unsigned tot;
+                const unsigned ex = block_exclusive_scan(v, &tot);
+                if (j < G) s_off[j] = run + ex;
+                run += tot;
+            }
+            __syncthreads();
+        }
+        for (int p0 = 0; p0 < M; p0 += gstride) {
+            const int p = p0 + gtid;
+            bool act = false;
+            int np = 0, nlo = 0, nhi = 0;
+            int4 q = make_int4(0, 0, 0, 0);
+            if (p < M) {
+                const int seg = lc[p], end = hc[p], size = end - seg;
+                np = p;
+                nlo = seg;
+                nhi = end;
+                const unsigned e = sc[p];
+                if (size > thresh) {
+                    const Cut c = make_cut(size, (int)Ac.k[seg], (int)Ac.k2[seg]);
+                    const unsigned gp = s_off[p / chunk] + lscan[p];
+                    const unsigned gs = s_off[seg / chunk] + lscan[seg];
+                    const int before = (int)(gp - gs);  // low items before p in this segment
+                    if (lflag[p]) {
+                        np = seg + before;
+                        nhi = seg + c.kfinal;
+                    } else {
+                        np = seg + c.kfinal + ((p - seg) - before);
+                        nlo = seg + c.kfinal;
+                    }
+                    act = nhi - nlo > thresh;
+                    if (act) {
+                        atomicMax(&co.maxseg[r % 3], nhi - nlo);
+                        q = xi[e];
+                    }
+                }
+                sn[np] = e;
+                ln[np] = nlo;
+                hn[np] = nhi;
+            }
+            accumulate_box_sum(act, nlo, q, An);
+        }
+        grid_barrier(co);
+        cur ^= 1;
+        // one decision per block (thread 0 reads, everyone follows), so that no
+        // thread leaves the loop while the rest of its block waits at a barrier
+        if (threadIdx.x == 0)
+            s_stop = (*((volatile int*)&co.maxseg[r % 3]) <= thresh || *((volatile int*)co.err)) ? 1 : 0;
+        __syncthreads();
+        const int stop = s_stop;
+        ++r;
+        if (stop) break;
+    }
+    if (cur == 1)  // leave the result in buffer 0 (the end of the kernel orders this)
+        for (int p = gtid; p < M; p += gstride) {
+            set0[p] = set1[p];
+            lo0[p] = lo1[p];
+            hi0[p] = hi1[p];
+        }
+    if (gtid == 0) {
+        *co.rounds = r;
+        if (*((volatile int*)&co.maxseg[(r + 2) % 3]) > thresh) atomicOr(co.err, 2);
+    }
+}
 
-struct LocalSmem {
-    int X[TREE_LOC_CAP], Y[TREE_LOC_CAP], Z[TREE_LOC_CAP];
-    unsigned I[TREE_LOC_CAP];
-    short P[2][TREE_LOC_CAP];              // permutation of local slots
-    short Lo[2][TREE_LOC_CAP], Hi[2][TREE_LOC_CAP];
-    unsigned Fl[TREE_LOC_CAP];             // low flags
-    unsigned F[TREE_LOC_CAP];              // their exclusive prefix over the block's slots
-    int amin[3][TREE_LOC_CAP], amax[3][TREE_LOC_CAP];
-    unsigned long long asum[TREE_LOC_CAP];
-    unsigned ak[TREE_LOC_CAP], ak2[TREE_LOC_CAP];
-    unsigned long long akey[TREE_LOC_CAP], akey2[TREE_LOC_CAP];
-    unsigned wsum[TREE_LOC_THREADS / 32];
+// ---- segments of at most TREE_BLOCK: one block per window of TREE_BLOCK slots
+//
+// The block takes every segment that starts in its window (at most
+// 2 TREE_BLOCK - 1 slots) into shared memory and cuts, level by level with
+// block barriers, every segment larger than TREE_WARP.  Open segments are
+// larger than TREE_WARP, so their starts are more than TREE_WARP slots apart
+// and start / TREE_WARP indexes their accumulators without collisions.
+
+constexpr int TREE_BLOCK = 1024;
+constexpr int BLK_CAP = 2 * TREE_BLOCK;         // slots one block can hold
+constexpr int BLK_ACC = BLK_CAP / TREE_WARP;    // accumulator entries
+
+struct BlockSmem {
+    int4 Q[2][BLK_CAP];         // (x, y, z, particle index), two buffers
+    short Lo[2][BLK_CAP], Hi[2][BLK_CAP];
+    unsigned F[BLK_CAP];        // low flags
+    unsigned S[BLK_CAP];        // their exclusive prefix over the block's slots
+    // per open segment, 32-bit only (shared-memory atomics stay native)
+    int mn[BLK_ACC][3], mx[BLK_ACC][3];
+    unsigned sh[BLK_ACC][3], sl[BLK_ACC][3];  // coordinate sums: high 15-bit parts and low parts
+    unsigned k[BLK_ACC], k2[BLK_ACC];
+    int vk[BLK_ACC][4];         // largest x below (<), smallest above, largest below (<=), smallest above
+    unsigned ik[BLK_ACC][4];    // the index that breaks the tie among those x
+    unsigned wsum[TREE_BLOCK / 32];
     int range_lo, range_hi, any;
 };
 
-__device__ __forceinline__ int lcomp(const LocalSmem& S, int q, int ax)
+__device__ __forceinline__ int blk_axis(const BlockSmem& S, int e)
 {
-    return ax == 0 ? S.X[q] : (ax == 1 ? S.Y[q] : S.Z[q]);
+    return axis_of(S.mx[e][0] - S.mn[e][0], S.mx[e][1] - S.mn[e][1], S.mx[e][2] - S.mn[e][2]);
 }
 
-__device__ __forceinline__ int laxis(const LocalSmem& S, int seg)
+__device__ __forceinline__ long long blk_com(const BlockSmem& S, int e, int ax, int size)
 {
-    return axis_of(S.amax[0][seg] - S.amin[0][seg], S.amax[1][seg] - S.amin[1][seg],
-                   S.amax[2][seg] - S.amin[2][seg]);
+    const unsigned long long sum = ((unsigned long long)S.sh[e][ax] << 15) + S.sl[e][ax];
+    return (long long)(sum / (unsigned long long)size);
 }
 
-__global__ void __launch_bounds__(TREE_LOC_THREADS)
-    k_tree_local(int M, const int4* __restrict__ xi, unsigned int* __restrict__ set,
-                 int* __restrict__ glo, int* __restrict__ ghi)
+__global__ void __launch_bounds__(TREE_BLOCK)
+    k_tree_block(int M, unsigned int* __restrict__ set, int* __restrict__ glo, int* __restrict__ ghi,
+                 const int4* __restrict__ xi, int* err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    LocalSmem& S = *reinterpret_cast<LocalSmem*>(smem_raw);
-    const int tid = threadIdx.x;
-    const int c0 = blockIdx.x * TREE_LOCAL, c1 = min(M, c0 + TREE_LOCAL);
+    BlockSmem& S = *reinterpret_cast<BlockSmem*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int w0 = blockIdx.x * TREE_BLOCK, w1 = min(M, w0 + TREE_BLOCK);
     if (tid == 0) {
         S.range_lo = INT_MAX;
         S.range_hi = INT_MIN;
     }
     __syncthreads();
-    // segments starting in [c0, c1) belong to this block
-    for (int p = c0 + tid; p < c1; p += TREE_LOC_THREADS)
-        if (glo[p] == p) {
+    {
+        const int p = w0 + tid;
+        if (p < w1 && glo[p] == p) {
             atomicMin(&S.range_lo, p);
             atomicMax(&S.range_hi, ghi[p]);
         }
+    }
     __syncthreads();
-    const int base = S.range_lo, s = S.range_hi - S.range_lo;
-    if (base == INT_MAX || s <= 0 || s > TREE_LOC_CAP) return;  // s <= 2*TREE_LOCAL - 1 by construction
-    for (int q = tid; q < s; q += TREE_LOC_THREADS) {
-        unsigned e = set[base + q];
-        int4 v = xi[e];
-        S.X[q] = v.x;
-        S.Y[q] = v.y;
-        S.Z[q] = v.z;
-        S.I[q] = e;
-        S.P[0][q] = (short)q;
+    const int base = S.range_lo, n = S.range_hi - S.range_lo;
+    if (base == INT_MAX || n <= 0) return;
+    if (n > BLK_CAP) {  // a segment larger than TREE_BLOCK reached this kernel
+        if (tid == 0) atomicOr(err, 2);
+        return;
+    }
+    for (int q = tid; q < n; q += TREE_BLOCK) {
+        const unsigned e = set[base + q];
+        const int4 v = xi[e];
+        S.Q[0][q] = make_int4(v.x, v.y, v.z, (int)e);
         S.Lo[0][q] = (short)(glo[base + q] - base);
         S.Hi[0][q] = (short)(ghi[base + q] - base);
     }
-    __syncthreads();
-    const int lane = tid & 31, wid = tid >> 5;
     int cur = 0;
-    for (int level = 0; level < 4 * TREE_LOC_CAP; ++level) {
-        // open segments (size > 2) reset their accumulators
-        for (int p = tid; p < s; p += TREE_LOC_THREADS) {
-            int l = S.Lo[cur][p], h = S.Hi[cur][p];
-            if (l == p && h - l > 2) {
-                for (int k = 0; k < 3; ++k) {
-                    S.amin[k][p] = INT_MAX;
-                    S.amax[k][p] = INT_MIN;
-                }
-                S.asum[p] = 0;
-                S.ak[p] = 0;
-                S.ak2[p] = 0;
-                S.akey[p] = 0;
-                S.akey2[p] = ~0ULL;
+    for (int level = 0; level < 4 * BLK_CAP; ++level) {
+        // accumulators of this level
+        for (int e = tid; e < BLK_ACC; e += TREE_BLOCK) {
+            for (int a = 0; a < 3; ++a) {
+                S.mn[e][a] = INT_MAX;
+                S.mx[e][a] = INT_MIN;
+                S.sh[e][a] = S.sl[e][a] = 0u;
             }
+            S.k[e] = S.k2[e] = 0u;
+            S.vk[e][0] = S.vk[e][2] = -1;
+            S.vk[e][1] = S.vk[e][3] = INT_MAX;
+            S.ik[e][0] = S.ik[e][2] = 0u;
+            S.ik[e][1] = S.ik[e][3] = 0xffffffffu;
         }
         if (tid == 0) S.any = 0;
         __syncthreads();
-        // bounding boxes
-        for (int p0 = 0; p0 < s; p0 += TREE_LOC_THREADS) {
-            int p = p0 + tid;
-            bool act = false;
-            int seg = 0, q = 0;
-            if (p < s) {
-                seg = S.Lo[cur][p];
-                act = S.Hi[cur][p] - seg > 2;
-                q = S.P[cur][p];
-            }
-            unsigned peers = seg_peers(act, seg);
-            if (act) {
-                int mn[3] = {__reduce_min_sync(peers, S.X[q]), __reduce_min_sync(peers, S.Y[q]),
-                             __reduce_min_sync(peers, S.Z[q])};
-                int mx[3] = {__reduce_max_sync(peers, S.X[q]), __reduce_max_sync(peers, S.Y[q]),
-                             __reduce_max_sync(peers, S.Z[q])};
-                if (seg_leader(peers))
-                    for (int k = 0; k < 3; ++k) {
-                        atomicMin(&S.amin[k][seg], mn[k]);
-                        atomicMax(&S.amax[k][seg], mx[k]);
-                    }
-            }
-        }
-        __syncthreads();
-        // coordinate sums along each segment's widest axis
-        for (int p0 = 0; p0 < s; p0 += TREE_LOC_THREADS) {
-            int p = p0 + tid;
+        // bounding boxes and coordinate sums
+        for (int q0 = 0; q0 < BLK_CAP; q0 += TREE_BLOCK) {
+            const int q = q0 + tid;
             bool act = false;
             int seg = 0;
-            unsigned v = 0;
-            if (p < s) {
-                seg = S.Lo[cur][p];
-                act = S.Hi[cur][p] - seg > 2;
-                if (act) v = (unsigned)lcomp(S, S.P[cur][p], laxis(S, seg));
+            int4 v = make_int4(0, 0, 0, 0);
+            if (q < n) {
+                seg = S.Lo[cur][q];
+                act = S.Hi[cur][q] - seg > TREE_WARP;
+                v = S.Q[cur][q];
             }
-            unsigned peers = seg_peers(act, seg);
+            const unsigned peers = seg_peers(act, seg);
             if (act) {
-                unsigned sh = __reduce_add_sync(peers, v >> 15), sl = __reduce_add_sync(peers, v & 0x7fffu);
-                if (seg_leader(peers))
-                    atomicAdd(&S.asum[seg], ((unsigned long long)sh << 15) + (unsigned long long)sl);
-            }
-        }
-        __syncthreads();
-        // counts below the centre of mass
-        for (int p0 = 0; p0 < s; p0 += TREE_LOC_THREADS) {
-            int p = p0 + tid;
-            bool act = false;
-            int seg = 0;
-            unsigned lt = 0, le = 0;
-            if (p < s) {
-                seg = S.Lo[cur][p];
-                int size = S.Hi[cur][p] - seg;
-                act = size > 2;
-                if (act) {
-                    long long com = (long long)(S.asum[seg] / (unsigned long long)size);
-                    long long v = lcomp(S, S.P[cur][p], laxis(S, seg));
-                    lt = v < com;
-                    le = v <= com;
-                }
-            }
-            unsigned peers = seg_peers(act, seg);
-            if (act) {
-                unsigned clt = __reduce_add_sync(peers, lt), cle = __reduce_add_sync(peers, le);
+                const int e = seg / TREE_WARP;
+                const int mnx = __reduce_min_sync(peers, v.x), mny = __reduce_min_sync(peers, v.y),
+                          mnz = __reduce_min_sync(peers, v.z);
+                const int mxx = __reduce_max_sync(peers, v.x), mxy = __reduce_max_sync(peers, v.y),
+                          mxz = __reduce_max_sync(peers, v.z);
+                const unsigned hx = __reduce_add_sync(peers, (unsigned)v.x >> 15),
+                               lx = __reduce_add_sync(peers, (unsigned)v.x & 0x7fffu);
+                const unsigned hy = __reduce_add_sync(peers, (unsigned)v.y >> 15),
+                               ly = __reduce_add_sync(peers, (unsigned)v.y & 0x7fffu);
+                const unsigned hz = __reduce_add_sync(peers, (unsigned)v.z >> 15),
+                               lz = __reduce_add_sync(peers, (unsigned)v.z & 0x7fffu);
                 if (seg_leader(peers)) {
-                    atomicAdd(&S.ak[seg], clt);
-                    atomicAdd(&S.ak2[seg], cle);
+                    atomicMin(&S.mn[e][0], mnx);
+                    atomicMin(&S.mn[e][1], mny);
+                    atomicMin(&S.mn[e][2], mnz);
+                    atomicMax(&S.mx[e][0], mxx);
+                    atomicMax(&S.mx[e][1], mxy);
+                    atomicMax(&S.mx[e][2], mxz);
+                    atomicAdd(&S.sh[e][0], hx);
+                    atomicAdd(&S.sl[e][0], lx);
+                    atomicAdd(&S.sh[e][1], hy);
+                    atomicAdd(&S.sl[e][1], ly);
+                    atomicAdd(&S.sh[e][2], hz);
+                    atomicAdd(&S.sl[e][2], lz);
                 }
             }
         }
         __syncthreads();
-        // odd cuts: the particle that crosses (reduced per warp, one atomic per segment run)
-        for (int p0 = 0; p0 < s; p0 += TREE_LOC_THREADS) {
-            int p = p0 + tid;
-            bool act = false, down = false;
+        // counts below the centre of mass and the extreme coordinates on either side
+        for (int q0 = 0; q0 < BLK_CAP; q0 += TREE_BLOCK) {
+            const int q = q0 + tid;
+            bool act = false, blt = false, ble = false;
             int seg = 0, v = 0;
+            if (q < n) {
+                seg = S.Lo[cur][q];
+                const int size = S.Hi[cur][q] - seg;
+                act = size > TREE_WARP;
+                if (act) {
+                    const int e = seg / TREE_WARP;
+                    const int ax = blk_axis(S, e);
+                    const long long com = blk_com(S, e, ax, size);
+                    v = comp(S.Q[cur][q], ax);
+                    blt = v < com;
+                    ble = v <= com;
+                }
+            }
+            const unsigned peers = seg_peers(act, seg);
+            if (act) {
+                const int e = seg / TREE_WARP;
+                const unsigned clt = __reduce_add_sync(peers, blt ? 1u : 0u);
+                const unsigned cle = __reduce_add_sync(peers, ble ? 1u : 0u);
+                const int v0 = __reduce_max_sync(peers, blt ? v : -1);
+                const int v1 = __reduce_min_sync(peers, !blt ? v : INT_MAX);
+                const int v2 = __reduce_max_sync(peers, ble ? v : -1);
+                const int v3 = __reduce_min_sync(peers, !ble ? v : INT_MAX);
+                if (seg_leader(peers)) {
+                    atomicAdd(&S.k[e], clt);
+                    atomicAdd(&S.k2[e], cle);
+                    atomicMax(&S.vk[e][0], v0);
+                    atomicMin(&S.vk[e][1], v1);
+                    atomicMax(&S.vk[e][2], v2);
+                    atomicMin(&S.vk[e][3], v3);
+                }
+            }
+        }
+        __syncthreads();
+        // where the cut moves by one particle: the index among the extreme coordinates
+        for (int q0 = 0; q0 < BLK_CAP; q0 += TREE_BLOCK) {
+            const int q = q0 + tid;
+            bool act = false, pick = false;
+            int seg = 0, slot = 0;
             unsigned idx = 0;
-            if (p < s) {
-                seg = S.Lo[cur][p];
-                int size = S.Hi[cur][p] - seg;
-                if (size > 2) {
-                    Cut c = make_cut(size, (int)S.ak[seg], (int)S.ak2[seg]);
+            if (q < n) {
+                seg = S.Lo[cur][q];
+                const int size = S.Hi[cur][q] - seg;
+                if (size > TREE_WARP) {
+                    const int e = seg / TREE_WARP;
+                    const Cut c = make_cut(size, (int)S.k[e], (int)S.k2[e]);
                     if (!c.coincident && c.kfinal != c.k) {
-                        int q = S.P[cur][p];
-                        long long com = (long long)(S.asum[seg] / (unsigned long long)size);
-                        v = lcomp(S, q, laxis(S, seg));
-                        bool low = c.use_le ? v <= com : v < com;
-                        down = c.kfinal < c.k;
-                        act = down ? low : !low;
-                        idx = S.I[q];
+                        act = true;
+                        const int ax = blk_axis(S, e);
+                        const long long com = blk_com(S, e, ax, size);
+                        const int4 t = S.Q[cur][q];
+                        const int v = comp(t, ax);
+                        const bool pl = c.use_le ? v <= com : v < com;
+                        slot = (c.use_le ? 2 : 0) + (c.kfinal < c.k ? 0 : 1);
+                        pick = (c.kfinal < c.k ? pl : !pl) && v == S.vk[e][slot];
+                        idx = (unsigned)t.w;
                     }
                 }
             }
-            // the cut direction is a property of the segment, so peers share it
-            unsigned peers = seg_peers(act, seg);
+            // the slot is a property of the segment, so peers share it
+            const unsigned peers = seg_peers(act, seg);
             if (act) {
-                if (down) {
-                    unsigned long long k0 = warp_max_key(peers, true, v, idx);
-                    if (seg_leader(peers)) atomicMax(&S.akey[seg], k0);
+                const int e = seg / TREE_WARP;
+                // lanes without a pick give the identity, so an empty group changes nothing
+                if ((slot & 1) == 0) {
+                    const unsigned im = __reduce_max_sync(peers, pick ? idx : 0u);
+                    if (seg_leader(peers)) atomicMax(&S.ik[e][slot], im);
                 } else {
-                    unsigned long long k1 = warp_min_key(peers, true, v, idx);
-                    if (seg_leader(peers)) atomicMin(&S.akey2[seg], k1);
+                    const unsigned im = __reduce_min_sync(peers, pick ? idx : 0xffffffffu);
+                    if (seg_leader(peers)) atomicMin(&S.ik[e][slot], im);
                 }
             }
         }
         __syncthreads();
         // low flags
-        for (int p = tid; p < s; p += TREE_LOC_THREADS) {
-            int seg = S.Lo[cur][p], size = S.Hi[cur][p] - seg;
+        for (int q = tid; q < BLK_CAP; q += TREE_BLOCK) {
             unsigned f = 0;
-            if (size > 2) {
-                Cut c = make_cut(size, (int)S.ak[seg], (int)S.ak2[seg]);
-                if (c.coincident) {
-                    f = (p - seg) < c.kfinal;  // segments stay in ascending index order
-                } else {
-                    int q = S.P[cur][p];
-                    long long com = (long long)(S.asum[seg] / (unsigned long long)size);
-                    long long v = lcomp(S, q, laxis(S, seg));
-                    bool left = c.use_le ? v <= com : v < com;
-                    unsigned long long key = ((unsigned long long)v << 32) | S.I[q];
-                    if (c.kfinal < c.k && key == S.akey[seg]) left = false;
-                    if (c.kfinal > c.k && key == S.akey2[seg]) left = true;
-                    f = left;
+            if (q < n) {
+                const int seg = S.Lo[cur][q], size = S.Hi[cur][q] - seg;
+                if (size > TREE_WARP) {
+                    const int e = seg / TREE_WARP;
+                    const Cut c = make_cut(size, (int)S.k[e], (int)S.k2[e]);
+                    if (c.coincident) {
+                        f = (q - seg) < c.kfinal;  // segments keep ascending index order
+                    } else {
+                        const int ax = blk_axis(S, e);
+                        const long long com = blk_com(S, e, ax, size);
+                        const int4 t = S.Q[cur][q];
+                        const int v = comp(t, ax);
+                        bool left = c.use_le ? v <= com : v < com;
+                        const int kk = c.use_le ? 2 : 0;
+                        if (c.kfinal < c.k && v == S.vk[e][kk] && (unsigned)t.w == S.ik[e][kk])
+                            left = false;
+                        if (c.kfinal > c.k && v == S.vk[e][kk + 1] && (unsigned)t.w == S.ik[e][kk + 1])
+                            left = true;
+                        f = left;
+                    }
                 }
             }
-            S.Fl[p] = f;
+            S.F[q] = f;
         }
         __syncthreads();
-        // exclusive prefix of the flags over the block's slots (a contiguous run per thread)
+        // exclusive prefix of the flags: two consecutive slots per thread
         {
-            const int per = (s + TREE_LOC_THREADS - 1) / TREE_LOC_THREADS;
-            const int b0 = min(s, tid * per), b1 = min(s, b0 + per);
-            unsigned run = 0;
-            for (int p = b0; p < b1; ++p) run += S.Fl[p];
+            const unsigned a0 = S.F[2 * tid], a1 = S.F[2 * tid + 1];
+            const unsigned run = a0 + a1;
             unsigned incl = run;
             for (int o = 1; o < 32; o <<= 1) {
-                unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+                const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += t;
             }
             if (lane == 31) S.wsum[wid] = incl;
             __syncthreads();
             unsigned ex = incl - run;
             for (int w = 0; w < wid; ++w) ex += S.wsum[w];
-            for (int p = b0; p < b1; ++p) {
-                S.F[p] = ex;
-                ex += S.Fl[p];
-            }
+            S.S[2 * tid] = ex;
+            S.S[2 * tid + 1] = ex + a0;
         }
         __syncthreads();
         // stable partition of every open segment into the other buffer
         const int nx = cur ^ 1;
-        for (int p = tid; p < s; p += TREE_LOC_THREADS) {
-            int seg = S.Lo[cur][p], end = S.Hi[cur][p], size = end - seg;
-            int np = p, nlo = seg, nhi = end;
-            if (size > 2) {
-                Cut c = make_cut(size, (int)S.ak[seg], (int)S.ak2[seg]);
-                int before = (int)(S.F[p] - S.F[seg]);  // low slots in [seg, p)
-                if (S.Fl[p]) {
+        for (int q = tid; q < n; q += TREE_BLOCK) {
+            const int seg = S.Lo[cur][q], end = S.Hi[cur][q], size = end - seg;
+            int np = q, nlo = seg, nhi = end;
+            if (size > TREE_WARP) {
+                const int e = seg / TREE_WARP;
+                const Cut c = make_cut(size, (int)S.k[e], (int)S.k2[e]);
+                const int before = (int)(S.S[q] - S.S[seg]);  // low slots in [seg, q)
+                if (S.F[q]) {
                     np = seg + before;
                     nhi = seg + c.kfinal;
                 } else {
-                    np = seg + c.kfinal + ((p - seg) - before);
+                    np = seg + c.kfinal + ((q - seg) - before);
                     nlo = seg + c.kfinal;
                 }
-                if (nhi - nlo > 2) S.any = 1;
+                if (nhi - nlo > TREE_WARP) S.any = 1;
             }
-            S.P[nx][np] = S.P[cur][p];
-            S.Lo[nx][np] = (short)nlo;
-            S.Hi[nx][np] = (short)nhi;
+            if (np >= 0 && np < n) {  // always true for a consistent cut
+                S.Q[nx][np] = S.Q[cur][q];
+                S.Lo[nx][np] = (short)nlo;
+                S.Hi[nx][np] = (short)nhi;
+            }
         }
         __syncthreads();
         cur = nx;
         if (!S.any) break;
         __syncthreads();
     }
-    for (int p = tid; p < s; p += TREE_LOC_THREADS) {
-        set[base + p] = S.I[S.P[cur][p]];
-        glo[base + p] = base + S.Lo[cur][p];
-        ghi[base + p] = base + S.Hi[cur][p];
+    for (int q = tid; q < n; q += TREE_BLOCK) {
+        set[base + q] = (unsigned)S.Q[cur][q].w;
+        glo[base + q] = base + S.Lo[cur][q];
+        ghi[base + q] = base + S.Hi[cur][q];
+    }
+}
+
+// ---- segments of at most TREE_WARP: one warp each, one particle per lane
+//
+// The same cut as the rounds above, with the segment in registers: warp
+// reductions over the lanes of each open sub-segment, the stable partition by
+// ballot ranks, and an exchange through shared memory.
+
+__global__ void __launch_bounds__(128)
+    k_tree_warp(int M, const int4* __restrict__ xi, unsigned int* __restrict__ set,
+                int* __restrict__ glo, int* __restrict__ ghi)
+{
+    __shared__ int4 xbuf[4][32];
+    __shared__ int2 bbuf[4][32];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int nwin = (M + 31) / 32;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int win = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; win < nwin; win += nwarps) {
+        const int p = win * 32 + lane;
+        const bool start = p < M && glo[p] == p && ghi[p] - p > 2;
+        unsigned sm = __ballot_sync(FULL, start);
+        while (sm) {
+            const int src = __ffs(sm) - 1;
+            sm &= sm - 1;
+            const int base = win * 32 + src;
+            const int s = min(ghi[base] - base, TREE_WARP);
+            const bool own = lane < s;
+            unsigned idx = own ? set[base + lane] : 0u;
+            int4 q = own ? xi[idx] : make_int4(0, 0, 0, 0);
+            int slo = 0, shi = s;
+            for (int round = 0; round < TREE_WARP; ++round) {
+                const int size = shi - slo;
+                const bool act = own && size > 2;
+                if (!__any_sync(FULL, act)) break;
+                const unsigned peers = seg_peers(act, slo);
+                int np = lane, nlo = slo, nhi = shi;
+                if (act) {
+                    const int mn0 = __reduce_min_sync(peers, q.x), mx0 = __reduce_max_sync(peers, q.x);
+                    const int mn1 = __reduce_min_sync(peers, q.y), mx1 = __reduce_max_sync(peers, q.y);
+                    const int mn2 = __reduce_min_sync(peers, q.z), mx2 = __reduce_max_sync(peers, q.z);
+                    const int ax = axis_of(mx0 - mn0, mx1 - mn1, mx2 - mn2);
+                    const int v = comp(q, ax);
+                    const unsigned sh = __reduce_add_sync(peers, (unsigned)v >> 15);
+                    const unsigned sl = __reduce_add_sync(peers, (unsigned)v & 0x7fffu);
+                    const unsigned long long sum = ((unsigned long long)sh << 15) + sl;
+                    const long long com = (long long)(sum / (unsigned long long)size);
+                    const bool blt = v < com, ble = v <= com;
+                    const int klt = (int)__reduce_add_sync(peers, blt ? 1u : 0u);
+                    const int kle = (int)__reduce_add_sync(peers, ble ? 1u : 0u);
+                    const Cut c = make_cut(size, klt, kle);
+                    bool low;
+                    if (c.coincident) {
+                        low = (lane - slo) < c.kfinal;  // lanes hold ascending index order
+                    } else {
+                        const bool pl = c.use_le ? ble : blt;
+                        low = pl;
+                        const unsigned long long key = ((unsigned long long)v << 32) | idx;
+                        if (c.kfinal < c.k && key == warp_max_key(peers, pl, v, idx)) low = false;
+                        if (c.kfinal > c.k && key == warp_min_key(peers, !pl, v, idx)) low = true;
+                    }
+                    const unsigned lm = __ballot_sync(peers, low) & peers;
+                    if (low) {
+                        np = slo + __popc(lm & lt);
+                        nhi = slo + c.kfinal;
+                    } else {
+                        np = slo + c.kfinal + __popc(~lm & peers & lt);
+                        nlo = slo + c.kfinal;
+                    }
+                }
+                __syncwarp();
+                if (own && np >= 0 && np < TREE_WARP) {  // always true for a consistent cut
+                    xbuf[w][np] = make_int4(q.x, q.y, q.z, (int)idx);
+                    bbuf[w][np] = make_int2(nlo, nhi);
+                }
+                __syncwarp();
+                if (own) {
+                    const int4 t = xbuf[w][lane];
+                    q = make_int4(t.x, t.y, t.z, 0);
+                    idx = (unsigned)t.w;
+                    const int2 b = bbuf[w][lane];
+                    slo = b.x;
+                    shi = b.y;
+                }
+                __syncwarp();
+            }
+            if (own) {
+                set[base + lane] = idx;
+                glo[base + lane] = base + slo;
+                ghi[base + lane] = base + shi;
+            }
+            __syncwarp();
+        }
     }
 }
 
@@ -855,48 +1157,57 @@ static apr_status pair_trees(apr_ctx* c, int* off, unsigned int** set_out, int**
     APR_LAUNCH(c, k_seg_setup, nblocks(M, 256), 256, M, lo_off, W.seg_lo[0], W.seg_hi[0], acc[0]);
     int maxm = 0;
     for (int l = 1; l <= lmax; ++l) maxm = max(maxm, off[l + 1] - off[l]);
-    int cur = 0;
-    const int nb = nblocks(M, 256);
-    int rounds_left = 0;
-    if (maxm > TREE_LOCAL) {
-        int est = 1;
-        while ((TREE_LOCAL << est) < maxm) ++est;
-        rounds_left = est + 1;
-    }
-    for (int total = 0; rounds_left > 0 && total < 64 + 4 * 32; ) {
-        for (int r = 0; r < rounds_left; ++r, ++total) {
-            APR_LAUNCH(c, k_tree_bbox_sum, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur],
-                       W.seg_hi[cur], W.xi, acc[cur]);
-            APR_LAUNCH(c, k_tree_count_key, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur],
-                       W.seg_hi[cur], W.xi, acc[cur]);
-            APR_LAUNCH(c, k_tree_flag, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur],
-                       W.seg_hi[cur], W.xi, acc[cur], W.lflag);
-            scan_u32(c, W.lflag, W.uscan, M, nullptr);
-            cudaMemsetAsync(&W.status[ST_MAXSEG], 0, sizeof(int), st);
-            const int nx = cur ^ 1;
-            APR_LAUNCH(c, k_tree_scatter, nb, 256, M, TREE_LOCAL, sets[cur], W.seg_lo[cur],
-                       W.seg_hi[cur], acc[cur], W.lflag, W.uscan, sets[nx], W.seg_lo[nx],
-                       W.seg_hi[nx], acc[nx], &W.status[ST_MAXSEG]);
-            cur = nx;
+    if (maxm > TREE_BLOCK) {
+        if (c->coop_blocks <= 0) {
+            int per_sm = 0, nsm = 0;
+            s = cuda_check(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree_rounds,
+                                                                            COOP_THREADS, 0),
+                           "pairing tree occupancy");
+            if (s != APR_OK) return s;
+            s = cuda_check(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device),
+                           "SM count");
+            if (s != APR_OK) return s;
+            c->coop_blocks = min(per_sm * nsm, COOP_MAX_BLOCKS);
+            if (c->coop_blocks <= 0) return fail(c, APR_ERR_CUDA, "pairing tree: no resident block");
         }
-        cudaMemcpyAsync(c->hbuf, &W.status[ST_MAXSEG], sizeof(int), cudaMemcpyDeviceToHost, st);
-        s = cuda_check(c, cudaStreamSynchronize(st), "pairing tree");
+        const int grid = max(1, min(c->coop_blocks, (M + COOP_THREADS - 1) / COOP_THREADS));
+        Coop co;
+        co.btot = W.coop;
+        co.bar = W.coop + 2 * COOP_MAX_BLOCKS;
+        co.maxseg = (int*)(co.bar + 2);
+        co.rounds = co.maxseg + 3;
+        co.err = &W.status[ST_TREE_ERR];
+        cudaMemsetAsync(co.bar, 0, sizeof(unsigned) * 8, st);
+        cudaMemsetAsync(co.err, 0, sizeof(int), st);
+        int M_ = M, thresh = TREE_BLOCK, max_rounds = 64 + 4 * 32;
+        void* args[] = {&M_, &thresh, &max_rounds, (void*)&W.xi, (void*)&sets[0], (void*)&sets[1],
+                        (void*)&W.seg_lo[0], (void*)&W.seg_lo[1], (void*)&W.seg_hi[0],
+                        (void*)&W.seg_hi[1], (void*)&acc[0], (void*)&acc[1], (void*)&W.lflag,
+                        (void*)&W.uscan, (void*)&co};
+        ++c->launches;
+        s = cuda_check(c, cudaLaunchCooperativeKernel((const void*)k_tree_rounds, dim3(grid),
+                                                      dim3(COOP_THREADS), args, 0, st),
+                       "pairing tree rounds");
         if (s != APR_OK) return s;
-        rounds_left = ((int*)c->hbuf)[0] > TREE_LOCAL ? 2 : 0;
     }
-    if (rounds_left > 0) return fail(c, APR_ERR_STATE, "pairing tree did not reach its leaves");
-    if (!c->tree_smem_set) {
-        s = cuda_check(c, cudaFuncSetAttribute(k_tree_local,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)sizeof(LocalSmem)), "tree smem");
-        if (s != APR_OK) return s;
-        c->tree_smem_set = true;
+    // the rounds leave their result in buffer 0
+    if (maxm > TREE_WARP) {
+        if (!c->tree_smem_set) {
+            s = cuda_check(c, cudaFuncSetAttribute(k_tree_block,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)sizeof(BlockSmem)), "tree smem");
+            if (s != APR_OK) return s;
+            c->tree_smem_set = true;
+        }
+        APR_LAUNCH_SMEM(c, k_tree_block, (M + TREE_BLOCK - 1) / TREE_BLOCK, TREE_BLOCK,
+                        sizeof(BlockSmem), M, sets[0], W.seg_lo[0], W.seg_hi[0], W.xi,
+                        &W.status[ST_TREE_ERR]);
     }
-    APR_LAUNCH_SMEM(c, k_tree_local, nblocks(M, TREE_LOCAL), TREE_LOC_THREADS, sizeof(LocalSmem), M,
-                    W.xi, sets[cur], W.seg_lo[cur], W.seg_hi[cur]);
-    *set_out = sets[cur];
-    *lo_out = W.seg_lo[cur];
-    *hi_out = W.seg_hi[cur];
+    APR_LAUNCH(c, k_tree_warp, min(nblocks((long long)((M + 31) / 32) * 32, 128), 152 * 16), 128, M,
+               W.xi, sets[0], W.seg_lo[0], W.seg_hi[0]);
+    *set_out = sets[0];
+    *lo_out = W.seg_lo[0];
+    *hi_out = W.seg_hi[0];
     return cuda_check(c, cudaGetLastError(), "pairing tree");
 }
 
@@ -926,11 +1237,14 @@ apr_status merge_pairs_debug(apr_ctx* c, int level, long long* pairs, long long 
     long long* dev = (long long*)c->W.tmp8;
     APR_LAUNCH(c, k_pairs_out, nblocks(m, 256), 256, m, set + a, dev);
     std::vector<long long> buf(m);
+    int terr = 0;
     s = cuda_check(c, cudaMemcpyAsync(buf.data(), dev, sizeof(long long) * m, cudaMemcpyDeviceToHost,
                                       c->stream), "pairs out");
     if (s != APR_OK) return s;
+    cudaMemcpyAsync(&terr, &c->W.status[ST_TREE_ERR], sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     s = cuda_check(c, cudaStreamSynchronize(c->stream), "pairs out");
     if (s != APR_OK) return s;
+    if (terr) return fail(c, APR_ERR_STATE, "pairing tree: a grid barrier timed out");
     for (int j = 0; j < me; ++j) pairs[j] = buf[j];
     if (m % 2) *spare = buf[m - 1];
     return APR_OK;
@@ -1085,8 +1399,13 @@ static apr_status split_merge_body(apr_ctx* c, apr_counts* cnt)
                        &W.status[ST_MERGES]);
             cudaMemcpyAsync(c->hbuf, &W.status[ST_MERGES], sizeof(int) * APR_MAXLEV,
                             cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync((int*)c->hbuf + APR_MAXLEV, &W.status[ST_TREE_ERR], sizeof(int),
+                            cudaMemcpyDeviceToHost, st);
             s = cuda_check(c, cudaStreamSynchronize(st), "merge");
             if (s != APR_OK) return s;
+            if (((int*)c->hbuf)[APR_MAXLEV])
+                return fail(c, APR_ERR_STATE, "pairing tree: a grid barrier timed out or the "
+                                              "leaves were not reached");
             for (int l = 1; l <= c->cfg.lmax; ++l) cnt->n_merge[l] = ((int*)c->hbuf)[l];
         }
     }
