@@ -362,6 +362,7 @@ def _workload_rate(w, precision, steps, warmup, torch, flush, cap_factor, max_ne
     m_sinks0 = sum(k["m"] for k in sim.sinks())
     for _ in range(warmup):
         sim.step(0.0)
+    sim.profile(reset=True)
     sim.profile_enable(True)
     ms, psteps = timed_steps(sim, torch, steps, flush)
     prof = sim.profile()
@@ -372,7 +373,9 @@ def _workload_rate(w, precision, steps, warmup, torch, flush, cap_factor, max_ne
            "breakdown_ms_per_step": {g: round(prof[g]["ms"] / steps, 3) for g in
                                      ("sort", "tree", "lists", "density", "force", "refine",
                                       "other")},
-           "density_calls_per_step": prof["density"]["calls"] / steps}
+           "density_attempts_per_step": prof["density_attempts"] / steps,
+           "retried_particles_per_step": prof["uncovered"] / steps,
+           "shrunk_particles_per_step": prof["shrunk"] / steps}
     sim.close()
     return res
 

@@ -148,12 +148,19 @@ enum {
  * the density kernel (pairs inside 2h, summed over Newton-Raphson iterations)
  * and by the force kernel (pairs inside max(2h_a, 2h_b)).  launches: every
  * kernel the library launched since the context was created (always counted).
+ * density_attempts: list builds + Newton-Raphson passes of the density solve;
+ * uncovered: particles, summed over attempts, that needed another attempt
+ * (h beyond the lists' reach, or a list that overflowed); shrunk: those of
+ * them whose list overflowed (h reduced).
  */
 typedef struct {
     double ms[APR_NPROF];
     long long calls[APR_NPROF];
     double pairs[APR_NPROF];
     long long launches;
+    long long density_attempts;
+    long long uncovered;
+    long long shrunk;
 } apr_profile;
 
 typedef struct apr_ctx apr_ctx;

@@ -69,7 +69,9 @@ PROF_GROUPS = ("sort", "tree", "lists", "density", "force", "refine", "other")
 
 class Profile(C.Structure):
     _fields_ = [("ms", C.c_double * NPROF), ("calls", C.c_longlong * NPROF),
-                ("pairs", C.c_double * NPROF), ("launches", C.c_longlong)]
+                ("pairs", C.c_double * NPROF), ("launches", C.c_longlong),
+                ("density_attempts", C.c_longlong), ("uncovered", C.c_longlong),
+                ("shrunk", C.c_longlong)]
 
 
 class AprError(RuntimeError):
@@ -329,6 +331,9 @@ class Simulation:
         out = {g: dict(ms=pr.ms[k], calls=pr.calls[k], pairs=pr.pairs[k])
                for k, g in enumerate(PROF_GROUPS)}
         out["launches"] = pr.launches
+        out["density_attempts"] = pr.density_attempts
+        out["uncovered"] = pr.uncovered
+        out["shrunk"] = pr.shrunk
         return out
 
     def density_loss_grad(self, parent, d, hc):

@@ -143,6 +143,8 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.cand = (int2*)take(8 * (size_t)MAX_CAND * C);
     w.ncand = (int*)take(4 * C);
     w.point_q = (int*)take(4 * C);
+    w.retry_q[0] = (int*)take(4 * C);
+    w.retry_q[1] = (int*)take(4 * C);
     // the list memory doubles as compaction scratch (20 x 8 bytes per particle)
     w.nbr = (unsigned int*)take((4 * K > 160 ? 4 * K : 160) * C);
     w.ncnt = (int*)take(4 * C);
@@ -269,19 +271,36 @@ static apr_status run_density(apr_ctx* c, long long* noconv_out)
     apr_status s = index_sort(c);
     if (s != APR_OK) return s;
     long long unc = 0, noconv = 0, shrinks = 0;
+    int attempts = 0, q = 0;
     for (int attempt = 0; attempt < 64; ++attempt) {
         cudaMemsetAsync(c->W.status, 0, 2 * sizeof(int), c->stream);
-        // symmetric lists at the reach: after the last attempt (no h beyond its reach)
-        // they also hold every force pair, r < 2 max(h_a, h_b)
-        s = index_lists(c, 1, DENSITY_REACH, true);
+        if (attempt == 0) {
+            // symmetric lists at the reach: if every h converges within it, they
+            // also hold every force pair, r < 2 max(h_a, h_b)
+            s = index_lists(c, 1, DENSITY_REACH, true);
+            if (s != APR_OK) return s;
+            s = density_pass(c, &unc, &noconv, nullptr, 0, q);
+        } else {
+            // only the particles queued by the last pass: their lists by a
+            // per-particle tree walk at their new h, then their Newton-Raphson
+            s = index_refresh_h(c);
+            if (s != APR_OK) return s;
+            s = index_lists_queue(c, c->W.retry_q[q], &c->W.status[ST_RETRY_N + q], DENSITY_REACH);
+            if (s != APR_OK) return s;
+            const long long nq = unc;
+            s = density_pass(c, &unc, &noconv, c->W.retry_q[q], nq, q ^ 1);
+            q ^= 1;
+        }
         if (s != APR_OK) return s;
-        s = density_pass(c, &unc, &noconv);
-        if (s != APR_OK) return s;
+        ++attempts;
         shrinks += c->last_shrink;
+        c->prof_attempts += 1;
+        c->prof_unc += unc;
+        c->prof_shrink += c->last_shrink;
         if (unc == 0) break;
-        s = index_refresh_h(c);
-        if (s != APR_OK) return s;
     }
+    // after a retry, particles that kept their lists may miss a neighbour whose h grew
+    c->lists_fresh = attempts == 1;
     if (noconv_out) *noconv_out = noconv + unc;
     if (unc && shrinks)
         return fail(c, APR_ERR_NEIGH_OVERFLOW,
@@ -296,12 +315,18 @@ static apr_status run_density(apr_ctx* c, long long* noconv_out)
 static apr_status run_force(apr_ctx* c, bool reuse_density_lists)
 {
     apr_status s;
-    if (!reuse_density_lists) {
-        s = index_sort(c);
+    if (!reuse_density_lists || !c->lists_fresh) {
+        if (reuse_density_lists) {
+            // same positions as the density pass: the sort stands, only h moved
+            s = index_refresh_h(c);
+        } else {
+            s = index_sort(c);
+        }
         if (s != APR_OK) return s;
         cudaMemsetAsync(c->W.status, 0, 2 * sizeof(int), c->stream);
         s = index_lists(c, 1, 1.0);
         if (s != APR_OK) return s;
+        c->lists_fresh = true;
     }
     int ps = prof_begin(c, APR_PROF_OTHER);
     s = gather_force_data(c);
@@ -352,6 +377,8 @@ apr_status apr_create(apr_ctx** out, const apr_config* cfg, void* stream)
     c->bound = false;
     c->have_force = false;
     c->coop_blocks = 0;
+    c->lists_fresh = false;
+    c->prof_attempts = c->prof_unc = c->prof_shrink = 0;
     c->n = c->cap = c->next_id = 0;
     c->step = 0;
     c->nreg = c->nsink = 0;
@@ -657,6 +684,7 @@ apr_status apr_density_loss_grad(apr_ctx* c, long long npar, const long long* pa
     c->n = n;
     c->have_force = false;
     c->dt_valid = false;
+    c->lists_fresh = false;
     return s;
 }
 
@@ -691,6 +719,9 @@ apr_status apr_profile_read(apr_ctx* c, apr_profile* out, int reset)
         out->calls[g] = c->prof_calls[g];
     }
     out->launches = c->launches;
+    out->density_attempts = c->prof_attempts;
+    out->uncovered = c->prof_unc;
+    out->shrunk = c->prof_shrink;
     if (c->bound) {
         unsigned long long cnt[APR_NPROF];
         apr_status s = cuda_check(c, cudaMemcpyAsync(cnt, c->W.counters, sizeof(cnt),
@@ -700,11 +731,13 @@ apr_status apr_profile_read(apr_ctx* c, apr_profile* out, int reset)
         for (int g = 0; g < APR_NPROF; ++g) out->pairs[g] = (double)cnt[g];
         if (reset) cudaMemsetAsync(c->W.counters, 0, 8 * 16, c->stream);
     }
-    if (reset)
+    if (reset) {
         for (int g = 0; g < APR_NPROF; ++g) {
             c->prof_ms[g] = 0.0;
             c->prof_calls[g] = 0;
         }
+        c->prof_attempts = c->prof_unc = c->prof_shrink = 0;
+    }
     return APR_OK;
 }
 

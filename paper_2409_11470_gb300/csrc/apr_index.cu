@@ -999,6 +999,39 @@ static void launch_lists(apr_ctx* c, const int* ncell_dev, int n, bool graceful)
 #undef APR_LISTS_CASE
 }
 
+// symmetric lists (graceful: an overflow marks the list, the density pass shrinks h)
+// of the queued particles only; the cells and candidate lists are not touched
+apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, double reach)
+{
+    Workspace& W = c->W;
+    const int n = (int)c->n;
+    if (n <= 0) return APR_OK;
+    int ps = prof_begin(c, APR_PROF_LISTS);
+    APR_LAUNCH(c, k_thresholds, nblocks(n, 256), 256, c->dc, n, reach, W.sh, W.sthr, W.sreach,
+               W.status);
+    if (n >= 2) APR_LAUNCH(c, k_node_thr, nblocks(n - 1, 256), 256, c->dc, n, reach, W.nhmax, W.nthr);
+    const int mask = (c->dc.periodic[0] ? 1 : 0) | (c->dc.periodic[1] ? 2 : 0) |
+                     (c->dc.periodic[2] ? 4 : 0);
+#define APR_QUEUE_CASE(M, X, Y, Z)                                                                   \
+    case M:                                                                                          \
+        APR_LAUNCH(c, (k_lists_point<X, Y, Z, 1>), 152 * 4, 128, c->dc, qlen_dev, queue, n, c->cap,   \
+                   W.left, W.right, W.pk, W.sthr, W.nlo, W.nhi, W.nthr, W.nbr, W.ncnt, W.status, 1);  \
+        break;
+    switch (mask) {
+        APR_QUEUE_CASE(0, 0, 0, 0)
+        APR_QUEUE_CASE(1, 1, 0, 0)
+        APR_QUEUE_CASE(2, 0, 1, 0)
+        APR_QUEUE_CASE(3, 1, 1, 0)
+        APR_QUEUE_CASE(4, 0, 0, 1)
+        APR_QUEUE_CASE(5, 1, 0, 1)
+        APR_QUEUE_CASE(6, 0, 1, 1)
+        APR_QUEUE_CASE(7, 1, 1, 1)
+    }
+#undef APR_QUEUE_CASE
+    prof_end(c, ps);
+    return cuda_check(c, cudaGetLastError(), "queue lists");
+}
+
 apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful)
 {
     Workspace& W = c->W;

@@ -38,6 +38,7 @@ enum {
     ST_ADJ_BAD = 10,         // density loss: a bad split in the input
     ST_POINT_N = 11,         // lists: particles queued for the per-particle search
     ST_TREE_ERR = 12,        // pairing tree: 1 barrier timeout, 2 leaves not reached
+    ST_RETRY_N = 13,         // density: lengths of the two retry queues (2 words)
     ST_BINS = 16,            // merge: first slot of each level's candidates (10 words)
     ST_MERGES = 32,          // merge: merges per level (8 words)
     ST_NSTATUS = 16
@@ -144,6 +145,7 @@ struct Workspace {
     int2* cand;               // MAX_CAND (first slot, count) per cell
     int* ncand;
     int* point_q;             // particles of cells whose candidate list overflowed
+    int* retry_q[2];          // density: particles that need another attempt
     // neighbour lists, transposed: nbr[k * cap + sorted slot]
     unsigned int* nbr;
     int* ncnt;
@@ -196,6 +198,8 @@ struct apr_ctx {
     bool bound;
     bool have_force;
     int coop_blocks;          // co-resident blocks of the pairing-tree kernel (0: unknown)
+    long long prof_attempts, prof_unc, prof_shrink;  // density-solve counters
+    bool lists_fresh;         // the current lists hold every pair at the current h
     int ncell;
     int last_shrink;
     bool tree_smem_set;       // dynamic shared memory opt-in of the pairing-tree kernel
@@ -272,9 +276,12 @@ apr_status index_refresh_h(apr_ctx* c);      // re-gather h and node hmax after 
 // mode 0: gather lists (r < 2 reach h_a); mode 1: symmetric lists (r < 2 reach max(h_a, h_b)).
 // graceful: an overflowing list is marked (count -1) instead of flagged as an error.
 apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful = false);
+// symmetric lists of the queued particles only, by a per-particle tree walk
+apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, double reach);
 
 // SPH passes (apr_sph.cu)
-apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv);
+apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv,
+                        const int* active = nullptr, long long nactive = 0, int out_q = 0);
 apr_status force_pass(apr_ctx* c);
 apr_status gather_force_data(apr_ctx* c);
 

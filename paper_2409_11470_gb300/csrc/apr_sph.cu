@@ -80,11 +80,15 @@ __global__ void __launch_bounds__(128)
               const double* __restrict__ u, double* __restrict__ h_out,
               double* __restrict__ rho_out, double* __restrict__ omega_out,
               double* __restrict__ dnn_out, double* __restrict__ pres_out,
-              double* __restrict__ cs_out, int* status, unsigned long long* counters)
+              double* __restrict__ cs_out, int* status, unsigned long long* counters,
+              const int* __restrict__ active, long long nactive, int* __restrict__ retry_q,
+              int* __restrict__ retry_n)
 {
+    // all particles, or (active != nullptr) only the queued ones of a retry
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const int a = (int)s;
+    if (s >= (active ? nactive : n)) return;
+    const int a = active ? active[s] : (int)s;
+    if (a < 0 || a >= n) return;
     const int4 pa = pk[a];
     const double hlist = sh[a];
     const int m = ncnt[a];
@@ -94,6 +98,7 @@ __global__ void __launch_bounds__(128)
         h_out[perm[a]] = 0.8 * hlist;
         atomicAdd(&status[ST_UNCOVERED], 1);
         atomicAdd(&status[ST_SHRINK], 1);
+        retry_q[atomicAdd(retry_n, 1)] = a;
         return;
     }
     const R mua = Num<R>::mass(pa.w);
@@ -170,6 +175,7 @@ __global__ void __launch_bounds__(128)
     h_out[i] = hd;
     if (uncovered) {
         atomicAdd(&status[ST_UNCOVERED], 1);
+        retry_q[atomicAdd(retry_n, 1)] = a;
         return;
     }
     if (!conv) atomicAdd(&status[ST_NOCONV], 1);
@@ -194,26 +200,31 @@ __global__ void __launch_bounds__(128)
     cs_out[i] = cs;
 }
 
-apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv)
+// one Newton-Raphson pass over all particles (active == nullptr) or over the
+// nactive queued ones; particles that need another attempt go to retry_q[out_q]
+apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv, const int* active,
+                        long long nactive, int out_q)
 {
     Workspace& W = c->W;
     const long long n = c->n;
     cudaStream_t st = c->stream;
     cudaMemsetAsync(&W.status[ST_UNCOVERED], 0, 2 * sizeof(int), st);
     cudaMemsetAsync(&W.status[ST_SHRINK], 0, sizeof(int), st);
+    cudaMemsetAsync(&W.status[ST_RETRY_N + out_q], 0, sizeof(int), st);
     int ps = prof_begin(c, APR_PROF_DENSITY);
-    if (n > 0) {
+    const long long work = active ? nactive : n;
+    if (work > 0) {
         const double reach = DENSITY_REACH;
         if (c->cfg.precision == APR_PREC_FP64)
-            APR_LAUNCH(c, k_density<double>, nblocks(n, 128), 128, 
+            APR_LAUNCH(c, k_density<double>, nblocks(work, 128), 128,
                 c->dc, n, c->cap, reach, W.pk, W.sh, W.sthr, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
                 c->p.x, c->p.y, c->p.u, c->p.h, c->p.rho, c->p.omega, c->p.dnn, c->p.pres, c->p.cs,
-                W.status, W.counters);
+                W.status, W.counters, active, nactive, W.retry_q[out_q], &W.status[ST_RETRY_N + out_q]);
         else
-            APR_LAUNCH(c, k_density<float>, nblocks(n, 128), 128, 
+            APR_LAUNCH(c, k_density<float>, nblocks(work, 128), 128,
                 c->dc, n, c->cap, reach, W.pk, W.sh, W.sthr, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
                 c->p.x, c->p.y, c->p.u, c->p.h, c->p.rho, c->p.omega, c->p.dnn, c->p.pres, c->p.cs,
-                W.status, W.counters);
+                W.status, W.counters, active, nactive, W.retry_q[out_q], &W.status[ST_RETRY_N + out_q]);
     }
     prof_end(c, ps);
     // one read-back for the index status words and the density counters
