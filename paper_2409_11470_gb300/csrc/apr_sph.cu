@@ -69,8 +69,15 @@ __device__ __forceinline__ double rel_r2<double>(const DevCfg& dc, const int*, c
 // Newton-Raphson on g(h) with a bracket over this particle's (symmetric,
 // reach-scaled) list; the first pass also finds the nearest lattice neighbour.
 // Four list entries are loaded ahead so that several gathers are in flight.
+// resident blocks per SM asked of the compiler: the float kernels are bound by
+// gather latency, so more warps in flight pay; the double kernels keep their registers
 template <typename R>
-__global__ void __launch_bounds__(128)
+constexpr int density_min_blocks() { return sizeof(R) == 4 ? 10 : 1; }
+template <typename R>
+constexpr int force_min_blocks() { return sizeof(R) == 4 ? 8 : 1; }
+
+template <typename R>
+__global__ void __launch_bounds__(128, density_min_blocks<R>())
     k_density(DevCfg dc, long long n, long long cap, double reach, const int4* __restrict__ pk,
               const double* __restrict__ sh, const unsigned long long* __restrict__ sthr,
               const unsigned int* __restrict__ nbr, const int* __restrict__ ncnt,
@@ -389,7 +396,7 @@ __device__ __forceinline__ void force_pair(const DevCfg& dc, const ForceSelf<R>&
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, force_min_blocks<R>())
     k_force(DevCfg dc, long long n, long long cap, const int4* __restrict__ pk,
             const void* __restrict__ Abuf, const void* __restrict__ Vbuf,
             const void* __restrict__ Bbuf, const unsigned int* __restrict__ nbr,
