@@ -39,6 +39,9 @@ SHAPE_SLAB = 1
 EOS_ADIABATIC = 0
 EOS_LOCALLY_ISOTHERMAL = 1
 
+KERNEL_M4 = 0
+KERNEL_WENDLAND_C2 = 1
+
 
 def _cfg(**kw):
     base = dict(
@@ -49,6 +52,7 @@ def _cfg(**kw):
         rsep_fac=0.2, dnn_cap=0.35,
         m0=1.0, lmax=1, seed=SEED_BASE,
         ccour=0.3, cforce=0.25, G=1.0,
+        kernel=KERNEL_M4, level_default=0,
     )
     base.update(kw)
     return base
@@ -73,7 +77,7 @@ def _particles(x, y, z, vx, vy, vz, u, h, flags=None, level=None):
 
 
 def lattice_box(n_side=16, jitter=0.05, seed=SEED_BASE, sphere_R=(0.25,), gamma=5.0 / 3.0,
-                u0=1.0, rho0=1.0, hfact=1.2, name=None):
+                u0=1.0, rho0=1.0, hfact=1.2, name=None, kernel=KERNEL_M4):
     """Cubic lattice of ``n_side**3`` particles in the periodic unit box.
 
     Positions are cell centres ``(i + 1/2)/n_side`` moved by ``U(-jitter, jitter)``
@@ -93,7 +97,8 @@ def lattice_box(n_side=16, jitter=0.05, seed=SEED_BASE, sphere_R=(0.25,), gamma=
     zeros = np.zeros(n)
     p = _particles(pos[:, 0], pos[:, 1], pos[:, 2], zeros, zeros, zeros,
                    np.full(n, u0), np.full(n, hfact * s))
-    cfg = _cfg(gamma=gamma, hfact=hfact, m0=rho0 * s ** 3, lmax=max(1, len(sphere_R)), seed=seed)
+    cfg = _cfg(gamma=gamma, hfact=hfact, m0=rho0 * s ** 3, lmax=max(1, len(sphere_R)), seed=seed,
+               kernel=kernel)
     regions = [dict(shape=SHAPE_SPHERE, axis=0, track_sink=-1, centre=[0.5, 0.5, 0.5],
                     R=list(sphere_R))] if sphere_R else []
     return dict(name=name or f"lattice{n_side}", cfg=cfg, regions=regions, sinks=[], p=p,
@@ -224,6 +229,25 @@ def flyby(n=8_000_000, seed=SEED_BASE + 3, name=None):
              dict(x=pos, v=vel, m=1.0, racc=1.0)]
     regions = [dict(shape=SHAPE_SPHERE, axis=0, track_sink=1, centre=list(pos), R=[7.5, 5.0])]
     return dict(name=name or f"c4_flyby{n}", cfg=cfg, regions=regions, sinks=sinks, p=p)
+
+
+def wendland_lattice(n_side=16, jitter=0.05, seed=SEED_BASE + 5, sphere_R=(0.25,)):
+    """The C1 lattice with the Wendland C2 kernel at h_fact = 1.3 (the kernel and
+    h_fact of the paper's applications, Sec. 3)."""
+    return lattice_box(n_side, jitter, seed, sphere_R=sphere_R, hfact=1.3,
+                       kernel=KERNEL_WENDLAND_C2, name=f"wendland_lattice{n_side}")
+
+
+def deref_lattice(n_side=16, jitter=0.05, seed=SEED_BASE + 6, level=1, sphere_R=(0.25,)):
+    """Derefinement: a jittered lattice whose particles all start at ``level`` (mass
+    m0 / 2^level with m0 = 2^level rho0 spacing^3), ``level_default = level``, and a
+    zone at the box centre asking for one level less inside each radius."""
+    w = lattice_box(n_side, jitter, seed, sphere_R=sphere_R, name=f"deref_lattice{n_side}")
+    w["cfg"]["m0"] = w["cfg"]["m0"] * 2.0 ** level
+    w["cfg"]["lmax"] = level
+    w["cfg"]["level_default"] = level
+    w["p"]["level"][:] = level
+    return w
 
 
 def c5_adjoint_lattice(n_side=126):

@@ -53,6 +53,7 @@ enum { APR_FLAG_CHANGED = 1, APR_FLAG_FIXED = 2, APR_FLAG_DEAD = 4 };
 enum { APR_SHAPE_SPHERE = 0, APR_SHAPE_SLAB = 1 };
 enum { APR_EOS_ADIABATIC = 0, APR_EOS_LOCALLY_ISOTHERMAL = 1 };
 enum { APR_PREC_FP32_MIXED = 0, APR_PREC_FP64 = 1 };
+enum { APR_KERNEL_M4 = 0, APR_KERNEL_WENDLAND_C2 = 1 };
 
 /*
  * Run configuration.  box_lo/box_hi: domain; periodic axes wrap.  delta: the
@@ -67,6 +68,12 @@ enum { APR_PREC_FP32_MIXED = 0, APR_PREC_FP64 = 1 };
  * coordinates, compensated; state, integration and global sums in double) or
  * APR_PREC_FP64.  nr_tol, nr_maxit: h-rho Newton-Raphson stopping rule.
  * max_neigh: capacity of one particle's neighbour list (0 = default 512).
+ * kernel: APR_KERNEL_M4 (cubic spline, h_fact 1.2) or APR_KERNEL_WENDLAND_C2
+ * (the applications' kernel of Sec. 3, h_fact 1.3); both have support 2h.
+ * level_default: 0 refines (a point inside k nested boundaries of a zone asks
+ * for level k, the maximum over zones); L >= 1 derefines (every point asks for
+ * level L, a point inside k boundaries for L - k, the minimum over zones), the
+ * mode Sec. 2.1 and Sec. 4 describe for zones of lower resolution.
  */
 typedef struct {
     double box_lo[3], box_hi[3];
@@ -85,6 +92,8 @@ typedef struct {
     double nr_tol;
     int nr_maxit;
     int max_neigh;
+    int kernel;
+    int level_default;
 } apr_config;
 
 /*

@@ -66,7 +66,7 @@ class Cfg(C.Structure):
                 ("rsep_fac", C.c_double), ("dnn_cap", C.c_double), ("m0", C.c_double),
                 ("lmax", C.c_int), ("seed", C.c_ulonglong), ("ccour", C.c_double),
                 ("cforce", C.c_double), ("G", C.c_double), ("nthreads", C.c_int),
-                ("enumerate", C.c_int)]
+                ("enumerate", C.c_int), ("kernel", C.c_int), ("level_default", C.c_int)]
 
 
 class Region(C.Structure):
@@ -129,6 +129,8 @@ def lib():
             L.orc_force.argtypes = [P(Cfg), P(State), P(C.c_longlong), C.c_longlong]
             L.orc_sink_gravity.argtypes = [P(Cfg), P(State), P(Sink), C.c_int]
             L.orc_kernel_m4.argtypes = [C.c_double, _DP]
+            L.orc_kernel.argtypes = [C.c_int, C.c_double, _DP]
+            L.orc_kernel.restype = None
             L.orc_target_levels.argtypes = [P(Cfg), P(Region), C.c_int, C.c_longlong, _DP, _DP,
                                             _DP, _UP]
             L.orc_track_regions.argtypes = [P(Region), C.c_int, P(Sink), C.c_int]
@@ -184,6 +186,8 @@ def make_cfg(cfg, nthreads=0, enumerate=1):
     c.seed = int(cfg["seed"])
     c.nthreads = int(nthreads)
     c.enumerate = int(enumerate)
+    c.kernel = int(cfg.get("kernel", 0))
+    c.level_default = int(cfg.get("level_default", 0))
     return c
 
 
@@ -412,6 +416,13 @@ class Oracle:
 def kernel_m4(q):
     out = np.zeros(2)
     lib().orc_kernel_m4(float(q), out.ctypes.data_as(_DP))
+    return out
+
+
+def kernel_shape(kernel, q):
+    """f(q), f'(q) of kernel 0 (M4) or 1 (Wendland C2)."""
+    out = np.zeros(2)
+    lib().orc_kernel(int(kernel), float(q), out.ctypes.data_as(_DP))
     return out
 
 

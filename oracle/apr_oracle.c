@@ -87,6 +87,8 @@ typedef struct {
     double ccour, cforce, G;
     int nthreads;
     int enumerate; /* 0 brute force, 1 uniform cell list (same sets, sorted) */
+    int kernel;        /* 0 M4 cubic spline, 1 Wendland C2 (both support 2h) */
+    int level_default; /* 0: zones refine; L >= 1: zones derefine from level L */
 } orc_cfg;
 
 typedef struct {
@@ -238,6 +240,39 @@ static void m4(double q, double* f, double* df)
 }
 
 void orc_kernel_m4(double q, double* out2) { m4(q, &out2[0], &out2[1]); }
+
+/* Wendland C2 with support 2h: f(q) = (1 - q/2)^4 (2q + 1); W = 21 f / (16 pi h^3) */
+static void wendland_c2(double q, double* f, double* df)
+{
+    if (q < 2.0) {
+        double t = 1.0 - 0.5 * q;
+        *f = t * t * t * t * (2.0 * q + 1.0);
+        *df = -5.0 * q * t * t * t;
+    } else {
+        *f = 0.0;
+        *df = 0.0;
+    }
+}
+
+/* the configured kernel shape f(q), f'(q) */
+static void kern(const orc_cfg* c, double q, double* f, double* df)
+{
+    if (c->kernel == 1)
+        wendland_c2(q, f, df);
+    else
+        m4(q, f, df);
+}
+
+/* W = f(q) / (kinv h^3): the inverse of the kernel's normalisation constant */
+static double kinv(const orc_cfg* c) { return c->kernel == 1 ? 16.0 * M_PI / 21.0 : M_PI; }
+
+void orc_kernel(int kernel, double q, double* out2)
+{
+    if (kernel == 1)
+        wendland_c2(q, &out2[0], &out2[1]);
+    else
+        m4(q, &out2[0], &out2[1]);
+}
 
 /* ------------------------------------------------ candidate enumeration */
 
@@ -465,12 +500,12 @@ static double g_of_h(const orc_cfg* c, const double* r, const double* mb, long l
     double sum = 0.0, d = 0.0;
     for (long long t = 0; t < n; ++t) {
         double q = r[t] / h, f, df;
-        m4(q, &f, &df);
+        kern(c, q, &f, &df);
         sum += mb[t] * f;
         d += mb[t] * df * (-q / h);
     }
     if (dg) *dg = d;
-    return sum - M_PI * ma * c->hfact * c->hfact * c->hfact;
+    return sum - kinv(c) * ma * c->hfact * c->hfact * c->hfact;
 }
 
 static void eos(const orc_cfg* c, const orc_state* s, long long a, double rho, double* P,
@@ -539,8 +574,8 @@ static int density_one(const orc_cfg* c, orc_state* s, const cellgrid* g, const 
     double dwdh = 0.0;
     for (long long t = 0; t < n; ++t) {
         double q = r[t] / h, f, df;
-        m4(q, &f, &df);
-        dwdh += mb[t] * (-(3.0 * f + q * df) / (M_PI * h * h * h * h));
+        kern(c, q, &f, &df);
+        dwdh += mb[t] * (-(3.0 * f + q * df) / (kinv(c) * h * h * h * h));
     }
     s->h[a] = h;
     s->rho[a] = rho;
@@ -610,10 +645,10 @@ void orc_rho_sum(const orc_cfg* c, const orc_state* s, long long a, double h, do
     double rho = 0.0, dwdh = 0.0;
     for (long long t = 0; t < L.n; ++t) {
         double q = sqrt(L.r2[t]) / h, f, df;
-        m4(q, &f, &df);
+        kern(c, q, &f, &df);
         double mb = mass_of(c, s->level[L.idx[t]]);
-        rho += mb * f / (M_PI * h * h * h);
-        dwdh += mb * (-(3.0 * f + q * df) / (M_PI * h * h * h * h));
+        rho += mb * f / (kinv(c) * h * h * h);
+        dwdh += mb * (-(3.0 * f + q * df) / (kinv(c) * h * h * h * h));
     }
     out2[0] = rho;
     out2[1] = dwdh;
@@ -640,10 +675,10 @@ static void force_sum(const orc_cfg* c, orc_state* s, long long a, const long lo
         if (!(qa < 2.0 || qb < 2.0)) continue;
         double rx = d[0] / r, ry = d[1] / r, rz = d[2] / r;
         double fa, dfa, fb, dfb;
-        m4(qa, &fa, &dfa);
-        m4(qb, &fb, &dfb);
-        double Fa = dfa / (M_PI * ha * ha * ha * ha);
-        double Fb = dfb / (M_PI * hb * hb * hb * hb);
+        kern(c, qa, &fa, &dfa);
+        kern(c, qb, &fb, &dfb);
+        double Fa = dfa / (kinv(c) * ha * ha * ha * ha);
+        double Fb = dfb / (kinv(c) * hb * hb * hb * hb);
         double vx = s->vx[a] - s->vx[b], vy = s->vy[a] - s->vy[b], vz = s->vz[a] - s->vz[b];
         double vr = vx * rx + vy * ry + vz * rz;
         double mb = mass_of(c, s->level[b]);
@@ -832,7 +867,14 @@ static int region_level(const orc_region* r, const double p[3])
     return lev;
 }
 
-/* target level: maximum over regions, default 0, capped at lmax; *which = deciding region */
+/*
+ * Target level (Sec. 2.1).  Refinement (level_default 0): the deepest zone's
+ * level, default 0, capped at lmax.  Derefinement (level_default L >= 1, the
+ * lower-resolution zones of Sec. 2.1 and Sec. 4): L minus the deepest zone's
+ * depth, floored at 0.  *which = the deciding zone (the deepest, lowest index
+ * on a tie; in derefinement a point outside every zone is decided by zone 0),
+ * -1 if there is none.
+ */
 static int target_level(const orc_cfg* c, const orc_region* rg, int nr, const double p[3],
                         int* which)
 {
@@ -844,9 +886,16 @@ static int target_level(const orc_cfg* c, const orc_region* rg, int nr, const do
             w = j;
         }
     }
-    if (best > c->lmax) best = c->lmax;
+    int t;
+    if (c->level_default > 0) {
+        t = c->level_default - best;
+        if (t < 0) t = 0;
+        if (w < 0 && nr > 0) w = 0;
+    } else {
+        t = best > c->lmax ? c->lmax : best;
+    }
     if (which) *which = w;
-    return best;
+    return t;
 }
 
 void orc_target_levels(const orc_cfg* c, const orc_region* rg, int nr, long long n,
@@ -979,7 +1028,19 @@ long long orc_split_pass(const orc_cfg* c, orc_state* s, const orc_region* rg, i
         if (target_level(c, rg, nr, p, &which) <= l) continue;
         double t = orc_split_uniform(c->seed, s->id[i], step);
         double w[3];
-        orc_split_direction(&rg[which], p, t, w);
+        if (which >= 0) {
+            orc_split_direction(&rg[which], p, t, w);
+        } else {
+            /* no zone decides (derefinement without zones): a sphere centred on
+               the parent, whose direction falls back to the x axis */
+            orc_region self;
+            memset(&self, 0, sizeof(self));
+            self.shape = 0;
+            self.centre[0] = p[0];
+            self.centre[1] = p[1];
+            self.centre[2] = p[2];
+            orc_split_direction(&self, p, t, w);
+        }
         double rsep = c->rsep_fac * s->h[i];
         double cap = c->dnn_cap * s->dnn[i];
         if (cap < rsep) rsep = cap;
@@ -1455,13 +1516,13 @@ int orc_split_loss_grad(const orc_cfg* c, const orc_state* s, long long npar,
                 long long b = L.idx[t];
                 double r = sqrt(L.r2[t]), mb = mass_of(c, T.level[b]), f, df;
                 if (role[b] & ORC_ROLE_NEW) {
-                    m4(r / ha, &f, &df);
-                    rho_new += mb * f / (M_PI * ha * ha * ha);
+                    kern(c, r / ha, &f, &df);
+                    rho_new += mb * f / (kinv(c) * ha * ha * ha);
                 }
                 if (role[b] & ORC_ROLE_REF) {
                     double hb = T.h[b];
-                    m4(r / hb, &f, &df);
-                    rho_ref += mb * f / (M_PI * hb * hb * hb);
+                    kern(c, r / hb, &f, &df);
+                    rho_ref += mb * f / (kinv(c) * hb * hb * hb);
                 }
             }
             e[a] = rho_new - rho_ref;
@@ -1499,23 +1560,23 @@ int orc_split_loss_grad(const orc_cfg* c, const orc_state* s, long long npar,
                     }
                     if (role[b] & ORC_ROLE_NEW) {
                         double q = r / ha;
-                        m4(q, &f, &df);
-                        dh += mb * (-(3.0 * f + q * df) / (M_PI * ha * ha * ha * ha));
+                        kern(c, q, &f, &df);
+                        dh += mb * (-(3.0 * f + q * df) / (kinv(c) * ha * ha * ha * ha));
                         if (b != a)
                             for (int m = 0; m < 3; ++m)
-                                own[m] += mb * (df / (M_PI * ha * ha * ha * ha)) * sep[m];
+                                own[m] += mb * (df / (kinv(c) * ha * ha * ha * ha)) * sep[m];
                     }
                     if (role[b] & ORC_ROLE_REF) {
                         double hb = T.h[b];
-                        m4(r / hb, &f, &df);
+                        kern(c, r / hb, &f, &df);
                         for (int m = 0; m < 3; ++m)
-                            own[m] -= mb * (df / (M_PI * hb * hb * hb * hb)) * sep[m];
+                            own[m] -= mb * (df / (kinv(c) * hb * hb * hb * hb)) * sep[m];
                     }
                     if ((role[b] & ORC_ROLE_CHILD) && b != a) {
                         double hb = T.h[b];
-                        m4(r / hb, &f, &df);
+                        kern(c, r / hb, &f, &df);
                         for (int m = 0; m < 3; ++m)
-                            rev[m] += 2.0 * e[b] * ma * (df / (M_PI * hb * hb * hb * hb)) * sep[m];
+                            rev[m] += 2.0 * e[b] * ma * (df / (kinv(c) * hb * hb * hb * hb)) * sep[m];
                     }
                 }
                 for (int m = 0; m < 3; ++m) gx[side][m] = 2.0 * e[a] * own[m] + rev[m];

@@ -34,7 +34,8 @@ class Config(C.Structure):
                 ("rsep_fac", C.c_double), ("dnn_cap", C.c_double), ("m0", C.c_double),
                 ("lmax", C.c_int), ("seed", C.c_ulonglong), ("ccour", C.c_double),
                 ("cforce", C.c_double), ("G", C.c_double), ("precision", C.c_int),
-                ("nr_tol", C.c_double), ("nr_maxit", C.c_int), ("max_neigh", C.c_int)]
+                ("nr_tol", C.c_double), ("nr_maxit", C.c_int), ("max_neigh", C.c_int),
+                ("kernel", C.c_int), ("level_default", C.c_int)]
 
 
 class Region(C.Structure):
@@ -145,6 +146,8 @@ def make_config(cfg, precision="fp32", nr_tol=0.0, nr_maxit=0, max_neigh=0):
     c.nr_tol = float(nr_tol)
     c.nr_maxit = int(nr_maxit)
     c.max_neigh = int(max_neigh)
+    c.kernel = int(cfg.get("kernel", 0))
+    c.level_default = int(cfg.get("level_default", 0))
     return c
 
 

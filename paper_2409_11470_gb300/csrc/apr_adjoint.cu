@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(ADJ_THREADS)
                   double* __restrict__ rho_out, double* __restrict__ partials)
 {
     double jsum = 0.0;
-    const double scale = dc.m0 / 3.14159265358979323846;
+    const double scale = dc.m0 / dc.knorm_inv;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < nt;
          s += (long long)gridDim.x * blockDim.x) {
         const AdjSlot<R> xa = X[s];
@@ -155,11 +155,11 @@ __global__ void __launch_bounds__(ADJ_THREADS)
             const R r = Num<R>::sqrt_(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
             R f, df;
             if (xb.role & ROLE_NEW) {
-                m4<R>(r * xa.hinv, f, df);
+                kern<R>(dc.kernel, r * xa.hinv, f, df);
                 Sn.add(xb.mu * f);
             }
             if (xb.role & ROLE_REF) {
-                m4<R>(r * xb.hinv, f, df);
+                kern<R>(dc.kernel, r * xb.hinv, f, df);
                 Sr.add(xb.mu * f * (xb.hinv * xb.hinv * xb.hinv));
             }
         }
@@ -224,22 +224,22 @@ __global__ void __launch_bounds__(ADJ_THREADS)
         R f, df;
         if (xb.role & ROLE_NEW) {
             const R q = r * xa.hinv;
-            m4<R>(q, f, df);
+            kern<R>(dc.kernel, q, f, df);
             dh.add(-xb.mu * (R(3) * f + q * df));
             on.add(xb.mu * df * rinv, d);
         }
         if (xb.role & ROLE_REF) {
-            m4<R>(r * xb.hinv, f, df);
+            kern<R>(dc.kernel, r * xb.hinv, f, df);
             const R h4 = (xb.hinv * xb.hinv) * (xb.hinv * xb.hinv);
             rf.add(xb.mu * df * h4 * rinv, d);
         }
         if (xb.role & ROLE_CHILD) {
-            m4<R>(r * xb.hinv, f, df);
+            kern<R>(dc.kernel, r * xb.hinv, f, df);
             const R h4 = (xb.hinv * xb.hinv) * (xb.hinv * xb.hinv);
             rv.add(E[b] * df * h4 * rinv, d);
         }
     }
-    const double scale = dc.m0 / 3.14159265358979323846;
+    const double scale = dc.m0 / dc.knorm_inv;
     const double ha = (double)xa.hinv, ha4 = (ha * ha) * (ha * ha);
     const double e2 = 2.0 * (double)ea, mua = (double)xa.mu;
     double g[3];

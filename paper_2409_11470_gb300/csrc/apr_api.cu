@@ -193,7 +193,19 @@ static apr_status check_cfg(const apr_config* cfg, DevCfg* dc, std::string* why)
         *why = "unknown precision";
         return APR_ERR_ARG;
     }
+    if (cfg->kernel != APR_KERNEL_M4 && cfg->kernel != APR_KERNEL_WENDLAND_C2) {
+        *why = "unknown kernel";
+        return APR_ERR_ARG;
+    }
+    if (cfg->level_default < 0 || cfg->level_default > cfg->lmax) {
+        *why = "level_default must lie in [0, lmax]";
+        return APR_ERR_ARG;
+    }
     memset(dc, 0, sizeof(*dc));
+    dc->kernel = cfg->kernel;
+    // W = f(q) / (knorm_inv h^3): M4 1/pi; Wendland C2 21/(16 pi) (unit integral over its support)
+    dc->knorm_inv = cfg->kernel == APR_KERNEL_WENDLAND_C2 ? 16.0 * M_PI / 21.0 : M_PI;
+    dc->level_default = cfg->level_default;
     for (int k = 0; k < 3; ++k) {
         double L = cfg->box_hi[k] - cfg->box_lo[k];
         if (!(L > 0.0)) {

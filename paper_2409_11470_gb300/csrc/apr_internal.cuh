@@ -82,6 +82,9 @@ struct DevCfg {
     int nr_maxit;
     int max_neigh;
     int prof;                  // count pair evaluations into Workspace::counters
+    int kernel;                // APR_KERNEL_M4 or APR_KERNEL_WENDLAND_C2
+    double knorm_inv;          // W = f(q) / (knorm_inv h^3): pi (M4), 16 pi / 21 (Wendland C2)
+    int level_default;         // 0: zones refine; L >= 1: zones derefine from level L
 };
 
 struct DevRegion {

@@ -39,6 +39,31 @@ __device__ __forceinline__ void m4(R q, R& f, R& df)
     }
 }
 
+// Wendland C2 (support 2h): f(q) = (1 - q/2)^4 (2q + 1), f'(q) = -5 q (1 - q/2)^3
+template <typename R>
+__device__ __forceinline__ void wendland_c2(R q, R& f, R& df)
+{
+    if (q < R(2)) {
+        const R t = R(1) - R(0.5) * q;
+        const R t3 = t * t * t;
+        f = t3 * t * (R(2) * q + R(1));
+        df = R(-5) * q * t3;
+    } else {
+        f = R(0);
+        df = R(0);
+    }
+}
+
+// the configured kernel (the branch is uniform across the grid)
+template <typename R>
+__device__ __forceinline__ void kern(int kernel, R q, R& f, R& df)
+{
+    if (kernel == APR_KERNEL_WENDLAND_C2)
+        wendland_c2<R>(q, f, df);
+    else
+        m4<R>(q, f, df);
+}
+
 // compensated (Kahan) accumulator
 template <typename R>
 struct Acc {

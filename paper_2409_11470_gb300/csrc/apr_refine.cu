@@ -45,6 +45,10 @@ __device__ int region_level(const DevRegion& r, double px, double py, double pz)
     return lev;
 }
 
+// target level (Sec. 2.1): refinement (level_default 0) takes the deepest zone,
+// capped at lmax; derefinement (level_default L) lowers L by the deepest zone's
+// depth, floored at 0.  *which: the deciding zone (the deepest; in derefinement
+// a point outside every zone is decided by zone 0), -1 if there is none.
 __device__ int target_level(const DevCfg& dc, const DevRegions& rg, double px, double py,
                             double pz, int* which)
 {
@@ -56,9 +60,16 @@ __device__ int target_level(const DevCfg& dc, const DevRegions& rg, double px, d
             w = j;
         }
     }
-    if (best > dc.lmax) best = dc.lmax;
+    int t;
+    if (dc.level_default > 0) {
+        t = dc.level_default - best;
+        if (t < 0) t = 0;
+        if (w < 0 && rg.n > 0) w = 0;
+    } else {
+        t = best > dc.lmax ? dc.lmax : best;
+    }
     if (which) *which = w;
-    return best;
+    return t;
 }
 
 // ------------------------------------------------------------------ split
@@ -169,7 +180,20 @@ __global__ void k_split_apply(DevCfg dc, DevRegions rg, int total, long long n,
     target_level(dc, rg, px, py, pz, &which);
     const double t = split_uniform(dc.seed, p.id[i], step);
     double w[3];
-    split_direction(rg.r[which], px, py, pz, t, w);
+    if (which >= 0) {
+        split_direction(rg.r[which], px, py, pz, t, w);
+    } else {
+        // no zone decides (derefinement without zones): a sphere centred on the
+        // parent, whose direction falls back to the x axis
+        DevRegion self;
+        self.shape = APR_SHAPE_SPHERE;
+        self.axis = 0;
+        self.nlev = 0;
+        self.centre[0] = px;
+        self.centre[1] = py;
+        self.centre[2] = pz;
+        split_direction(self, px, py, pz, t, w);
+    }
     double rsep = dc.rsep_fac * p.h[i];
     double cap = dc.dnn_cap * p.dnn[i];
     if (cap < rsep) rsep = cap;

@@ -34,13 +34,13 @@ __device__ __forceinline__ unsigned long long lattice_r2(const DevCfg& dc, const
 
 // one density term mu_b f(q), mu_b q f'(q) for a pair inside 2h
 template <typename R>
-__device__ __forceinline__ void density_term(R r2, R hinv, R r2max, int levb, Acc<R>& S,
-                                             Acc<R>& T, unsigned long long& npair)
+__device__ __forceinline__ void density_term(int kernel, R r2, R hinv, R r2max, int levb,
+                                             Acc<R>& S, Acc<R>& T, unsigned long long& npair)
 {
     if (r2 >= r2max) return;
     const R q = Num<R>::sqrt_(r2) * hinv;
     R f, df;
-    m4<R>(q, f, df);
+    kern<R>(kernel, q, f, df);
     const R mub = Num<R>::mass(levb);
     S.add(mub * f);
     T.add(mub * q * df);
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(128, density_min_blocks<R>())
         return;
     }
     const R mua = Num<R>::mass(pa.w);
-    const R target = R(3.14159265358979323846) * mua * R(dc.hfact * dc.hfact * dc.hfact);
+    const R target = R(dc.knorm_inv) * mua * R(dc.hfact * dc.hfact * dc.hfact);
     const unsigned int* col = nbr + a;  // this particle's list: col[k * cap]
     R h = (R)hlist;
     R lo = R(0), hi = R(0);  // bracket of the root; hi == 0: none yet
@@ -135,10 +135,10 @@ __global__ void __launch_bounds__(128, density_min_blocks<R>())
                 best = q2 < best ? q2 : best;
                 best = q3 < best ? q3 : best;
             }
-            density_term<R>(rel_r2<R>(dc, d0, sx, sy, sz, a, b0), hinv, r2max, p0.w, S, T, npair);
-            density_term<R>(rel_r2<R>(dc, d1, sx, sy, sz, a, b1), hinv, r2max, p1.w, S, T, npair);
-            density_term<R>(rel_r2<R>(dc, d2, sx, sy, sz, a, b2), hinv, r2max, p2.w, S, T, npair);
-            density_term<R>(rel_r2<R>(dc, d3, sx, sy, sz, a, b3), hinv, r2max, p3.w, S, T, npair);
+            density_term<R>(dc.kernel, rel_r2<R>(dc, d0, sx, sy, sz, a, b0), hinv, r2max, p0.w, S, T, npair);
+            density_term<R>(dc.kernel, rel_r2<R>(dc, d1, sx, sy, sz, a, b1), hinv, r2max, p1.w, S, T, npair);
+            density_term<R>(dc.kernel, rel_r2<R>(dc, d2, sx, sy, sz, a, b2), hinv, r2max, p2.w, S, T, npair);
+            density_term<R>(dc.kernel, rel_r2<R>(dc, d3, sx, sy, sz, a, b3), hinv, r2max, p3.w, S, T, npair);
         }
         for (; k < m; ++k) {
             const int b = (int)col[(long long)k * cap];
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(128, density_min_blocks<R>())
             int d[3];
             const unsigned long long q = lattice_r2(dc, pa, pb, d);
             if (first_pass) best = q < best ? q : best;
-            density_term<R>(rel_r2<R>(dc, d, sx, sy, sz, a, b), hinv, r2max, pb.w, S, T, npair);
+            density_term<R>(dc.kernel, rel_r2<R>(dc, d, sx, sy, sz, a, b), hinv, r2max, pb.w, S, T, npair);
         }
         const R g = (S.s + mua) - target;           // pi h^3 (rho_sum - rho_h) / m0
         const R dg = -(T.s) * hinv;                   // dg/dh >= 0
@@ -354,8 +354,8 @@ __device__ __forceinline__ void force_pair(const DevCfg& dc, const ForceSelf<R>&
     if (!(qa < R(2) || qb < R(2))) return;
     ++npair;
     R fa, dfa, fb, dfb;
-    m4<R>(qa, fa, dfa);
-    m4<R>(qb, fb, dfb);
+    kern<R>(dc.kernel, qa, fa, dfa);
+    kern<R>(dc.kernel, qb, fb, dfb);
     // float copies of the coefficients: no double-to-float conversion per pair
     R alpha, beta, alpha_u;
     if constexpr (sizeof(R) == 4) {
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(128, force_min_blocks<R>())
         force_pair<R>(dc, A, d, Ab, Vb, Bb, adiabatic, cond, fx, fy, fz, du, vsig, npair);
     }
     if (dc.prof) atomicAdd(&counters[APR_PROF_FORCE], npair);
-    const double scale = dc.m0 / 3.14159265358979323846;
+    const double scale = dc.m0 / dc.knorm_inv;
     const unsigned i = perm[a];
     ax_out[i] = scale * ((double)fx.s - (double)fx.c);
     ay_out[i] = scale * ((double)fy.s - (double)fy.c);

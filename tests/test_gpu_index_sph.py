@@ -77,7 +77,8 @@ def _density_both(w, precision):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("make", [apr_synth.c1_lattice, lambda: apr_synth.sod(16, slab=()),
-                                  lambda: apr_synth.disc_planet(30000)])
+                                  lambda: apr_synth.disc_planet(30000),
+                                  lambda: apr_synth.wendland_lattice(16, jitter=0.2)])
 def test_density_matches_oracle(make, precision):
     w = make()
     o, g = _density_both(w, precision)
@@ -96,7 +97,8 @@ def test_density_matches_oracle(make, precision):
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("make", [lambda: with_velocities(apr_synth.c1_lattice(), 0.3),
                                   lambda: with_velocities(apr_synth.sod(16, slab=()), 0.2),
-                                  lambda: apr_synth.disc_planet(30000)])
+                                  lambda: apr_synth.disc_planet(30000),
+                                  lambda: with_velocities(apr_synth.wendland_lattice(14, 0.2), 0.3)])
 def test_force_matches_oracle(make, precision):
     w = make()
     w["cfg"]["alpha_u"] = max(w["cfg"]["alpha_u"], 0.0)

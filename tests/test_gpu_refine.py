@@ -132,3 +132,33 @@ def test_empty_and_single_particle_passes():
         g = sim(w, capacity=64)
         g.split_merge()
         assert g.n == n
+
+
+def test_derefinement_bit_exact():
+    """Zones of lower resolution (level_default 1): the initial merges inside the
+    zone, then splits as the zone moves away, identical to the oracle."""
+    w = with_velocities(apr_synth.deref_lattice(12), 0.1)
+    o, g = _both(w, 3 * 12 ** 3)
+    merges = 0
+    for _ in range(2):
+        co = o.split_merge()
+        cg = g.split_merge()
+        assert list(cg.n_split) == list(co.n_split)
+        assert list(cg.n_merge) == list(co.n_merge)
+        _same(o, g)
+        merges += co.n_merge[1]
+    assert merges > 20
+    regs = [dict(shape=0, axis=0, track_sink=-1, centre=[0.8, 0.5, 0.5], R=[0.25])]
+    o.regions = oracle.make_regions(regs)
+    o.nreg = 1
+    g.set_regions(regs)
+    splits = 0
+    for _ in range(2):
+        co = o.split_merge()
+        cg = g.split_merge()
+        assert list(cg.n_split) == list(co.n_split)
+        assert list(cg.n_merge) == list(co.n_merge)
+        _same(o, g)
+        splits += co.n_split[0]
+    assert splits > 0
+

@@ -1,0 +1,146 @@
+"""Pins of the oracle for the rows beyond the default path (not GPU).
+
+Wendland C2 kernel (the kernel of the paper's applications, Sec. 3, with
+h_fact = 1.3): normalisation by quadrature, the derivative by finite
+differences, the constant seen by an isolated particle, the lattice density,
+the neighbour number of a kernel of radius 2h, Omega against a finite
+difference and momentum conservation.  Derefinement (zones of lower
+resolution, Sec. 2.1 and Sec. 4): a hand table of target levels, and a
+derefining initialisation that merges inside the zone while conserving mass
+and momentum and splits again when the zone moves away.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import apr_synth
+import oracle
+
+WC2 = 1
+
+
+def test_wendland_c2_normalised_to_unity():
+    # W = 21 f(q) / (16 pi h^3): the integral over the sphere of radius 2h is
+    # (21/4) int_0^2 q^2 f(q) dq
+    val, _ = integrate.quad(lambda q: 21.0 / 4.0 * q * q * oracle.kernel_shape(WC2, q)[0], 0.0, 2.0)
+    assert abs(val - 1.0) < 1e-12
+
+
+def test_wendland_c2_derivative_and_support():
+    e = 1e-6
+    for q in np.linspace(0.05, 1.95, 39):
+        fd = (oracle.kernel_shape(WC2, q + e)[0] - oracle.kernel_shape(WC2, q - e)[0]) / (2 * e)
+        assert abs(fd - oracle.kernel_shape(WC2, q)[1]) < 1e-8
+    assert tuple(oracle.kernel_shape(WC2, 2.0)) == (0.0, 0.0)
+    assert oracle.kernel_shape(WC2, 0.0)[0] == 1.0
+    lo = oracle.kernel_shape(WC2, 2.0 - 1e-9)
+    assert abs(lo[0]) < 1e-30 and abs(lo[1]) < 1e-20  # C2: value and slope vanish at 2h
+
+
+def test_wendland_constant_of_an_isolated_particle():
+    w = apr_synth.wendland_lattice(2, jitter=0.0, sphere_R=())
+    w["p"] = {k: v[:1] for k, v in w["p"].items()}
+    o = oracle.Oracle(w)
+    h = 0.3
+    rho, _ = o.rho_sum(0, h)  # self only: m f(0) 21 / (16 pi h^3)
+    assert rho == pytest.approx(w["cfg"]["m0"] * 21.0 / (16.0 * math.pi * h ** 3), rel=1e-14)
+
+
+def test_wendland_lattice_density_and_neighbour_number():
+    w = apr_synth.wendland_lattice(16, jitter=0.0, sphere_R=())
+    o = oracle.Oracle(w)
+    assert o.density() == 0
+    rho = o["rho"]
+    assert rho.max() / rho.min() - 1.0 < 1e-12
+    assert abs(rho.mean() / w["rho0"] - 1.0) < 2e-2  # the kernel's density bias
+    # a lattice jittered by 0.3 spacings smears the shells (at 2h = 2.59 spacings a
+    # perfect lattice holds exactly 81 points); the mean count, self included, then
+    # follows the closed form for a kernel of radius 2h, 73.6
+    wj = apr_synth.wendland_lattice(16, jitter=0.3, sphere_R=())
+    oj = oracle.Oracle(wj)
+    oj.density()
+    off, _ = oj.neighbours(0)
+    nn = 4.0 * math.pi / 3.0 * (2.0 * 1.3) ** 3
+    assert abs(np.diff(off).mean() + 1.0 - nn) < 2.0
+
+
+def test_wendland_omega_matches_finite_difference():
+    o = oracle.Oracle(apr_synth.wendland_lattice())
+    o.density()
+    for a in range(0, o.n, 511):
+        h = o["h"][a]
+        e = 1e-6 * h
+        drho_dh = (o.rho_sum(a, h + e)[0] - o.rho_sum(a, h - e)[0]) / (2 * e)
+        omega_fd = 1.0 + h / (3.0 * o["rho"][a]) * drho_dh
+        assert abs(omega_fd - o["omega"][a]) < 1e-7
+
+
+def test_wendland_forces_conserve_momentum():
+    w = apr_synth.wendland_lattice(10, jitter=0.2)
+    rng = np.random.default_rng(4)
+    for f in ("vx", "vy", "vz"):
+        w["p"][f] = rng.normal(0.0, 0.2, len(w["p"]["x"]))
+    o = oracle.Oracle(w)
+    o.density_force()
+    m = o.mass()
+    scale = np.sum(m * np.sqrt(o["ax"] ** 2 + o["ay"] ** 2 + o["az"] ** 2))
+    for f in ("ax", "ay", "az"):
+        assert abs(np.sum(m * o[f])) < 1e-12 * scale
+
+
+# ------------------------------------------------------------ derefinement
+
+def _deref_world(level, radii, centres):
+    w = apr_synth.lattice_box(2, jitter=0.0, sphere_R=())
+    w["cfg"]["lmax"] = level
+    w["cfg"]["level_default"] = level
+    w["regions"] = [dict(shape=0, axis=0, track_sink=-1, centre=list(c), R=list(radii))
+                    for c in centres]
+    return oracle.Oracle(w)
+
+
+def test_derefinement_target_levels_hand_table():
+    # default level 2; inside 0.3 one level less, inside 0.1 two levels less
+    o = _deref_world(2, [0.3, 0.1], [(0.0, 0.0, 0.0)])
+    got = o.target_levels([0.05, 0.2, 0.5, 0.3, 0.1], [0.0] * 5, [0.0] * 5)
+    assert list(got) == [0, 1, 2, 2, 1]  # boundaries are strict
+    # several zones: the deepest wins (the lowest level)
+    o2 = _deref_world(2, [0.3, 0.1], [(0.0, 0.0, 0.0), (0.25, 0.0, 0.0)])
+    # 0.27: 0.02 from the second centre; 0.5: 0.25 from it; 0.7: outside both
+    assert list(o2.target_levels([0.27, 0.5, 0.7], [0.0] * 3, [0.0] * 3)) == [0, 1, 2]
+
+
+def test_derefinement_init_merges_inside_and_conserves():
+    w = apr_synth.deref_lattice(12)
+    rng = np.random.default_rng(5)
+    for f in ("vx", "vy", "vz"):
+        w["p"][f] = rng.normal(0.0, 0.1, len(w["p"]["x"]))
+    o = oracle.Oracle(w, capacity=2 * len(w["p"]["x"]))
+    units0 = int(np.sum(2 ** (1 - o["level"].astype(np.int64))))  # mass in units of m0 / 2
+    s0 = o.stats()
+    o.init()
+    s1 = o.stats()
+    lev = o["level"]
+    assert (lev == 0).sum() > 20 and (lev == 1).sum() > 0
+    assert int(np.sum(2 ** (1 - lev.astype(np.int64)))) == units0  # exact, in mass units
+    assert s1.mass == pytest.approx(s0.mass, rel=1e-14)
+    for k in range(3):
+        assert abs(s1.mom[k] - s0.mom[k]) < 1e-15
+    # every merged particle sits where the zone asks for level 0, and nothing
+    # else is left below its target
+    tgt = o.target_levels()
+    assert np.all(tgt[lev == 0] == 0)
+    assert np.all(lev >= tgt - 0)  # no particle needs refining
+
+
+def test_derefinement_splits_when_the_zone_moves_away():
+    w = apr_synth.deref_lattice(12)
+    o = oracle.Oracle(w, capacity=2 * len(w["p"]["x"]))
+    o.init()
+    n0, coarse = o.n, int((o["level"] == 0).sum())
+    o.regions[0].centre[0] = 5.0  # the zone leaves the box
+    cnt = o.split_merge()
+    assert cnt.n_split[0] == coarse and o.n == n0 + coarse
+    assert np.all(o["level"] == 1)
