@@ -35,6 +35,7 @@ FLAG_DEAD = 4      # removed (merged away or accreted) until the next compaction
 
 SHAPE_SPHERE = 0
 SHAPE_SLAB = 1
+SHAPE_CYLINDER = 2
 
 EOS_ADIABATIC = 0
 EOS_LOCALLY_ISOTHERMAL = 1
@@ -248,6 +249,78 @@ def deref_lattice(n_side=16, jitter=0.05, seed=SEED_BASE + 6, level=1, sphere_R=
     w["cfg"]["level_default"] = level
     w["p"]["level"][:] = level
     return w
+
+
+def sound_wave_box(n_across=64, A=0.02, seed=SEED_BASE + 7, gamma=5.0 / 3.0, cs0=1.0,
+                   vx0=0.001, noise=1e-4, R=0.1, hfact=1.2, kernel=KERNEL_M4):
+    """The periodic sound-wave box of the paper's appendix tests.
+
+    A close-packed (ABAB) lattice with ``n_across`` particles along x in a box
+    [0, 1) x [0, Ly) x [0, Lz) (Ly, Lz: whole numbers of rows and layers, rounded
+    to whole lattice units), 64 x 74 x 12 = 56,832 particles at the default size.
+    x is stretched so that the density is rho0 + A sin(2 pi x) (rho0 = 1, equal
+    masses); u = u0 + A (P0/rho0) sin(2 pi x) with P0 = rho0 cs0^2 / gamma, adiabatic;
+    v = (vx0, 0, 0); x and y moved by U(-noise, noise) box lengths.  The zone is a
+    cylinder along z of radius R through (0.5, 0.5) with one level; the paper first
+    activates it at t = 0.5 (``regions_at`` below; ``regions`` starts empty).
+    """
+    rng = np.random.default_rng(seed)
+    a = 1.0 / n_across
+    dy, dz = a * math.sqrt(3.0) / 2.0, a * math.sqrt(2.0 / 3.0)
+    ny = 2 * max(1, int(round(1.0 / dy / 2.0)))
+    nz = 2 * max(1, int(round(0.15 / dz / 2.0)))
+    delta = 2.0 ** -29
+    Ly = round(ny * dy / delta) * delta
+    Lz = round(nz * dz / delta) * delta
+    i, j, k = np.meshgrid(np.arange(n_across), np.arange(ny), np.arange(nz), indexing="ij")
+    i, j, k = i.ravel(), j.ravel(), k.ravel()
+    x0 = (i + 0.5 * (j % 2) + 0.5 * (k % 2)) * a
+    y = (j + (k % 2) / 3.0) * (Ly / ny)
+    z = k * (Lz / nz)
+    x0 = np.mod(x0, 1.0)
+    # mass coordinate -> position: x + A/(2 pi rho0) (1 - cos 2 pi x) = x0
+    x = x0.copy()
+    for _ in range(50):
+        g = x + A / (2.0 * math.pi) * (1.0 - np.cos(2.0 * math.pi * x)) - x0
+        x -= g / (1.0 + A * np.sin(2.0 * math.pi * x))
+    x = np.mod(x + rng.uniform(-noise, noise, x.size), 1.0)
+    y = np.mod(y + rng.uniform(-noise, noise, y.size) * 1.0, Ly)
+    n = x.size
+    rho = 1.0 + A * np.sin(2.0 * math.pi * x)
+    m = Ly * Lz / n
+    P0 = cs0 * cs0 / gamma
+    u0 = P0 / (gamma - 1.0)
+    u = u0 + A * P0 * np.sin(2.0 * math.pi * x)
+    h = hfact * (m / rho) ** (1.0 / 3.0)
+    zeros = np.zeros(n)
+    p = _particles(x, y, z, np.full(n, vx0), zeros, zeros, u, h)
+    cfg = _cfg(box_hi=[1.0, Ly, Lz], periodic=[1, 1, 1], delta=delta, gamma=gamma, hfact=hfact,
+               m0=m, lmax=1, seed=seed, alpha_av=0.1, beta_av=0.2, kernel=kernel)
+    zone = dict(shape=SHAPE_CYLINDER, axis=2, track_sink=-1, centre=[0.5, 0.5, 0.5 * Lz], R=[R])
+    return dict(name=f"sound_wave_box{n}", cfg=cfg, regions=[], regions_at=(0.5, [zone]),
+                sinks=[], p=p, rho0=1.0, A=A, Ly=Ly, Lz=Lz)
+
+
+def wave_profile(x, y, rho, Ly, nbins=64, band=(0.4, 0.6)):
+    """Mean density in x bins over the band band[0] < y/Ly < band[1] (the paper's
+    cross section of the sound-wave box); returns (bin centres, means)."""
+    sel = (y > band[0] * Ly) & (y < band[1] * Ly)
+    idx = np.minimum((x[sel] * nbins).astype(np.int64), nbins - 1)
+    cnt = np.bincount(idx, minlength=nbins)
+    tot = np.bincount(idx, weights=rho[sel], minlength=nbins)
+    return (np.arange(nbins) + 0.5) / nbins, tot / np.maximum(cnt, 1)
+
+
+def zone_fuzz(x, y, level, h, centre=(0.5, 0.5), R=0.1):
+    """How far the mixed-level transition reaches past a circular zone boundary:
+    the largest distance of a level-1 particle outside R or a level-0 particle
+    inside R, in units of the level-0 smoothing length (mean over level 0)."""
+    r = np.hypot(x - centre[0], y - centre[1])
+    out = (level >= 1) & (r >= R)
+    inn = (level == 0) & (r < R)
+    d = np.concatenate([r[out] - R, R - r[inn]])
+    h0 = float(np.mean(h[level == 0])) if np.any(level == 0) else float(np.mean(h))
+    return float(d.max() / h0) if d.size else 0.0
 
 
 def c5_adjoint_lattice(n_side=126):

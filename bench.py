@@ -403,10 +403,65 @@ def side_measurements(args, torch, flush):
         except Exception as e:  # a side measurement never takes the headline down
             out[name] = {"error": f"{type(e).__name__}: {e}"}
     try:
+        out["sound_wave_box_56832p_cylinder_zone"] = sound_wave_measurement(torch)
+    except Exception as e:
+        out["sound_wave_box_56832p_cylinder_zone"] = {"error": f"{type(e).__name__}: {e}"}
+    try:
         out["split_adjoint_c5_2000376p"] = adjoint_rate(torch, k)
     except Exception as e:
         out["split_adjoint_c5_2000376p"] = {"error": f"{type(e).__name__}: {e}"}
     return out
+
+
+def sound_wave_measurement(torch, t_end=2.0):
+    """The appendix sound-wave box (56,832 particles, circular zone switched on at
+    t = 0.5) run to t = 2 with and without the zone: whole-step particle-steps/s of
+    the zoned run, the density blip at the boundary (largest difference of the
+    binned cross-section densities, in units of the initial mean density) and how
+    far the mixed-level transition reaches past the boundary (in level-0 h)."""
+    import numpy as np
+
+    import apr_synth
+    from paper_2409_11470_gb300.binding import Simulation
+    w = apr_synth.sound_wave_box()
+    n0 = len(w["p"]["x"])
+    t_on, regs = w["regions_at"]
+
+    def run(zone):
+        g = Simulation(w, capacity=2 * n0, precision="fp32")
+        g.init()
+        rho0 = float(np.mean(g.get("rho")))
+        st = g.stream
+        t, on, steps, psteps, ms = 0.0, False, 0, 0, 0.0
+        while t < t_end - 1e-12:
+            if zone and not on and t >= t_on - 1e-12:
+                g.set_regions(regs)
+                on = True
+            dt = min(g.timestep(), t_end - t, (t_on - t) if (zone and not on) else 1e9)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            g.step(dt)
+            e1.record(st)
+            st.synchronize()
+            ms += e0.elapsed_time(e1)
+            steps += 1
+            psteps += g.n
+            t += dt
+        return g, rho0, ms, steps, psteps
+
+    ref, rho_ic, _, _, _ = run(False)
+    apr, _, ms, steps, psteps = run(True)
+    _, pr = apr_synth.wave_profile(ref.get("x"), ref.get("y"), ref.get("rho"), w["Ly"])
+    _, pa = apr_synth.wave_profile(apr.get("x"), apr.get("y"), apr.get("rho"), w["Ly"])
+    blip = float(np.max(np.abs(pa - pr)) / rho_ic)
+    fuzz = apr_synth.zone_fuzz(apr.get("x"), apr.get("y"), apr.get("level"), apr.get("h"))
+    res = {"value": psteps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+           "n_initial": n0, "n_last": apr.n, "t_end": t_end, "blip_over_rho0": blip,
+           "transition_over_h": fuzz,
+           "paper": "blip below 5% of the initial density; transition about 10% of h"}
+    ref.close()
+    apr.close()
+    return res
 
 
 def adjoint_rate(torch, k):

@@ -50,7 +50,7 @@ typedef enum {
 
 /* particle flag bits */
 enum { APR_FLAG_CHANGED = 1, APR_FLAG_FIXED = 2, APR_FLAG_DEAD = 4 };
-enum { APR_SHAPE_SPHERE = 0, APR_SHAPE_SLAB = 1 };
+enum { APR_SHAPE_SPHERE = 0, APR_SHAPE_SLAB = 1, APR_SHAPE_CYLINDER = 2 };
 enum { APR_EOS_ADIABATIC = 0, APR_EOS_LOCALLY_ISOTHERMAL = 1 };
 enum { APR_PREC_FP32_MIXED = 0, APR_PREC_FP64 = 1 };
 enum { APR_KERNEL_M4 = 0, APR_KERNEL_WENDLAND_C2 = 1 };
@@ -99,7 +99,9 @@ typedef struct {
 /*
  * A refinement zone (Sec. 2.1, Table 1): nested boundaries R[0] > R[1] > ...,
  * a point strictly inside R[k] asks for level k + 1.  shape sphere:
- * |x - centre| < R; slab: |x[axis] - centre[axis]| < R.  track_sink >= 0 makes
+ * |x - centre| < R; slab: |x[axis] - centre[axis]| < R; cylinder along axis:
+ * the distance from the line through centre along axis < R (the circular zone
+ * of a thin box, appendix sound-wave test).  track_sink >= 0 makes
  * the centre follow that sink every step (co-moving zone, Sec. 2.1).
  */
 typedef struct {

@@ -92,7 +92,7 @@ typedef struct {
 } orc_cfg;
 
 typedef struct {
-    int shape; /* 0 sphere, 1 slab */
+    int shape; /* 0 sphere, 1 slab, 2 cylinder along axis */
     int axis;
     int track_sink; /* -1 fixed */
     int nlev;
@@ -858,6 +858,11 @@ static int region_level(const orc_region* r, const double p[3])
             double dx = p[0] - r->centre[0], dy = p[1] - r->centre[1], dz = p[2] - r->centre[2];
             double d2 = dx * dx + dy * dy + dz * dz;
             inside = d2 < r->R[k] * r->R[k];
+        } else if (r->shape == 2) { /* cylinder: distance from the axis line */
+            double d[3] = {p[0] - r->centre[0], p[1] - r->centre[1], p[2] - r->centre[2]};
+            int a1 = r->axis == 0 ? 1 : 0, a2 = r->axis == 2 ? 1 : 2;
+            double d2 = d[a1] * d[a1] + d[a2] * d[a2];
+            inside = d2 < r->R[k] * r->R[k];
         } else {
             double d = p[r->axis] - r->centre[r->axis];
             inside = fabs(d) < r->R[k];
@@ -968,6 +973,20 @@ void orc_split_direction(const orc_region* r, const double p[3], double t, doubl
             v[0] = 1.0;
             v[1] = 0.0;
             v[2] = 0.0;
+        }
+    } else if (r->shape == 2) { /* cylinder: radial from the axis line */
+        v[0] = p[0] - r->centre[0];
+        v[1] = p[1] - r->centre[1];
+        v[2] = p[2] - r->centre[2];
+        v[r->axis] = 0.0;
+        double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (vn > 0.0) {
+            v[0] = v[0] / vn;
+            v[1] = v[1] / vn;
+            v[2] = v[2] / vn;
+        } else {
+            v[0] = v[1] = v[2] = 0.0;
+            v[r->axis == 0 ? 1 : 0] = 1.0;
         }
     } else {
         v[0] = v[1] = v[2] = 0.0;

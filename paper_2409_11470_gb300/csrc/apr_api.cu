@@ -469,7 +469,8 @@ apr_status apr_set_regions(apr_ctx* c, const apr_region* r, int nregions)
     if (!c || nregions < 0 || nregions > APR_MAXREG || (nregions > 0 && !r)) return APR_ERR_ARG;
     for (int j = 0; j < nregions; ++j) {
         if (r[j].nlev < 0 || r[j].nlev > APR_MAXLEV || r[j].axis < 0 || r[j].axis > 2 ||
-            (r[j].shape != APR_SHAPE_SPHERE && r[j].shape != APR_SHAPE_SLAB))
+            (r[j].shape != APR_SHAPE_SPHERE && r[j].shape != APR_SHAPE_SLAB &&
+             r[j].shape != APR_SHAPE_CYLINDER))
             return fail(c, APR_ERR_ARG, "bad region");
         c->regions[j] = r[j];
     }

@@ -36,6 +36,12 @@ __device__ int region_level(const DevRegion& r, double px, double py, double pz)
             double dx = px - r.centre[0], dy = py - r.centre[1], dz = pz - r.centre[2];
             double d2 = dx * dx + dy * dy + dz * dz;
             inside = d2 < r.R[k] * r.R[k];
+        } else if (r.shape == APR_SHAPE_CYLINDER) {
+            // distance from the axis line: the two other components, in axis order
+            double d[3] = {px - r.centre[0], py - r.centre[1], pz - r.centre[2]};
+            const int a1 = r.axis == 0 ? 1 : 0, a2 = r.axis == 2 ? 1 : 2;
+            double d2 = d[a1] * d[a1] + d[a2] * d[a2];
+            inside = d2 < r.R[k] * r.R[k];
         } else {
             double p = r.axis == 0 ? px : (r.axis == 1 ? py : pz);
             inside = fabs(p - r.centre[r.axis]) < r.R[k];
@@ -107,6 +113,21 @@ __device__ void split_direction(const DevRegion& r, double px, double py, double
             v[0] = 1.0;
             v[1] = 0.0;
             v[2] = 0.0;
+        }
+    } else if (r.shape == APR_SHAPE_CYLINDER) {
+        // the radial direction from the axis line (the axis component removed)
+        v[0] = px - r.centre[0];
+        v[1] = py - r.centre[1];
+        v[2] = pz - r.centre[2];
+        v[r.axis] = 0.0;
+        double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (vn > 0.0) {
+            v[0] = v[0] / vn;
+            v[1] = v[1] / vn;
+            v[2] = v[2] / vn;
+        } else {
+            v[0] = v[1] = v[2] = 0.0;
+            v[r.axis == 0 ? 1 : 0] = 1.0;
         }
     } else {
         v[0] = v[1] = v[2] = 0.0;

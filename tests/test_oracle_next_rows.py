@@ -144,3 +144,51 @@ def test_derefinement_splits_when_the_zone_moves_away():
     cnt = o.split_merge()
     assert cnt.n_split[0] == coarse and o.n == n0 + coarse
     assert np.all(o["level"] == 1)
+
+
+# ------------------------------------------------- cylinder zone, sound wave
+
+def test_cylinder_zone_levels_hand_table():
+    w = apr_synth.lattice_box(2, jitter=0.0, sphere_R=())
+    w["cfg"]["lmax"] = 2
+    w["regions"] = [dict(shape=apr_synth.SHAPE_CYLINDER, axis=2, track_sink=-1,
+                         centre=[0.5, 0.5, 0.0], R=[0.3, 0.1])]
+    o = oracle.Oracle(w)
+    # distance from the z axis line through (0.5, 0.5): z does not matter
+    xs = [0.55, 0.55, 0.7, 0.5, 0.9, 0.8]
+    ys = [0.5, 0.5, 0.5, 0.8, 0.5, 0.5]
+    zs = [0.0, 0.9, 0.3, 0.5, 0.1, 0.0]
+    assert list(o.target_levels(xs, ys, zs)) == [2, 2, 1, 0, 0, 0]  # 0.3 is on the boundary
+
+
+def test_cylinder_split_direction_is_tangential():
+    reg = dict(shape=apr_synth.SHAPE_CYLINDER, axis=2, track_sink=-1, centre=[0.5, 0.5, 0.0],
+               R=[0.1])
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        p = rng.uniform(0.0, 1.0, 3)
+        t = rng.uniform(-1.0, 1.0)
+        wv = oracle.split_direction(reg, p, t)
+        radial = np.array([p[0] - 0.5, p[1] - 0.5, 0.0])
+        radial /= np.linalg.norm(radial)
+        assert abs(np.dot(wv, radial)) < 1e-14 and abs(np.linalg.norm(wv) - 1.0) < 1e-14
+
+
+def test_sound_wave_box_inputs():
+    w = apr_synth.sound_wave_box()
+    p = w["p"]
+    assert len(p["x"]) == 56832  # the paper's count at 64 particles across
+    # equal masses filling the box at mean density 1
+    assert w["cfg"]["m0"] * len(p["x"]) == pytest.approx(w["Ly"] * w["Lz"], rel=1e-14)
+    # the stretch rho = dx0/dx = 1 + A sin(2 pi x): undoing it puts every particle
+    # back on a lattice column (multiples of half a spacing) up to the 1e-4 noise
+    A = w["A"]
+    x = p["x"]
+    x0 = x + A / (2 * math.pi) * (1.0 - np.cos(2 * math.pi * x))
+    col = x0 / (0.5 / 64)
+    assert np.abs(col - np.round(col)).max() * (0.5 / 64) < 1.1e-4
+    # u follows the density perturbation with amplitude A P0 / rho0
+    P0 = 1.0 / w["cfg"]["gamma"]
+    assert np.allclose(p["u"] - P0 / (w["cfg"]["gamma"] - 1.0), A * P0 * np.sin(2 * math.pi * p["x"]),
+                       atol=1e-12)
+
