@@ -32,6 +32,7 @@ SEED_BASE = 20240917
 FLAG_CHANGED = 1   # split or merged during the current split/merge pass
 FLAG_FIXED = 2     # boundary particle: never moved, split or merged
 FLAG_DEAD = 4      # removed (merged away or accreted) until the next compaction
+FLAG_NEW = 8       # introduced by a split or merge, not yet relaxed
 
 SHAPE_SPHERE = 0
 SHAPE_SLAB = 1

@@ -48,8 +48,10 @@ typedef enum {
     APR_ERR_WORKSPACE = 7       /* workspace too small for the bound capacity */
 } apr_status;
 
-/* particle flag bits */
-enum { APR_FLAG_CHANGED = 1, APR_FLAG_FIXED = 2, APR_FLAG_DEAD = 4 };
+/* particle flag bits: CHANGED by the current split/merge pass; FIXED never moves,
+   splits or merges; DEAD removed at the next compaction; NEW introduced by a split
+   or merge and not yet relaxed (apr_relax clears it) */
+enum { APR_FLAG_CHANGED = 1, APR_FLAG_FIXED = 2, APR_FLAG_DEAD = 4, APR_FLAG_NEW = 8 };
 enum { APR_SHAPE_SPHERE = 0, APR_SHAPE_SLAB = 1, APR_SHAPE_CYLINDER = 2 };
 enum { APR_EOS_ADIABATIC = 0, APR_EOS_LOCALLY_ISOTHERMAL = 1 };
 enum { APR_PREC_FP32_MIXED = 0, APR_PREC_FP64 = 1 };

@@ -44,7 +44,7 @@ _lock = threading.Lock()
 _lib = None
 
 MAXLEV = 8
-FLAG_CHANGED, FLAG_FIXED, FLAG_DEAD = 1, 2, 4
+FLAG_CHANGED, FLAG_FIXED, FLAG_DEAD, FLAG_NEW = 1, 2, 4, 8
 
 
 def build(force=False):
@@ -165,6 +165,10 @@ def lib():
             L.orc_step.restype = C.c_int
             L.orc_step.argtypes = [P(Cfg), P(State), P(Region), C.c_int, P(Sink), C.c_int,
                                    C.c_double, C.c_ulonglong, P(Counts), P(Stats)]
+            L.orc_interp_ref.argtypes = [P(Cfg), P(State), C.c_longlong, _DP, _DP]
+            L.orc_relax.restype = C.c_int
+            L.orc_relax.argtypes = [P(Cfg), P(State), P(State), P(Sink), C.c_int, C.c_int, C.c_double,
+                                    _DP]
             L.orc_split_loss_grad.restype = C.c_int
             L.orc_split_loss_grad.argtypes = [P(Cfg), P(State), C.c_longlong, P(C.c_longlong), _DP,
                                               _DP, _UP, _DP, _DP, _DP]
@@ -377,6 +381,37 @@ class Oracle:
         if rc < 0:
             raise RuntimeError("oracle init: capacity exhausted")
         return rc
+
+    def copy(self):
+        """An independent oracle holding a copy of the current particles (e.g. the
+        reference set before a split)."""
+        import copy as _copy
+        w = _copy.deepcopy({k: v for k, v in self.w.items() if k != "p"})
+        w["p"] = {f: self.a[f][: self.n].copy() for f in ("x", "y", "z", "vx", "vy", "vz", "u", "h",
+                                                            "level", "flags", "id")}
+        o = Oracle(w, capacity=self.st.cap)
+        for f in DOUBLE_FIELDS:
+            o.a[f][: self.n] = self.a[f][: self.n]
+        o.st.next_id = self.st.next_id
+        return o
+
+    def interp_ref(self, pts):
+        """This oracle's accelerations interpolated (SPH, each particle at its own h)
+        to the points pts (k x 3)."""
+        pts = np.ascontiguousarray(pts, np.float64).reshape(-1, 3)
+        out = np.zeros_like(pts)
+        self.L.orc_interp_ref(C.byref(self.cfg), C.byref(self.st), len(pts), pts.ctypes.data_as(_DP),
+                              out.ctypes.data_as(_DP))
+        return out
+
+    def relax(self, ref, max_iter=50, tol=0.005):
+        """Relaxing (Sec. 2.4) of the particles flagged NEW towards the reference
+        oracle ``ref`` (its positions, h, density and accelerations); returns
+        (shuffles done, last / first shuffle energy)."""
+        ratio = C.c_double(0.0)
+        it = self.L.orc_relax(C.byref(self.cfg), C.byref(self.st), C.byref(ref.st), self.sinks,
+                              self.nsink, int(max_iter), float(tol), C.byref(ratio))
+        return it, ratio.value
 
     def split_loss_grad(self, parent, d, hc, want=None):
         """Density error J of splitting ``parent[k]`` into children at x_p +- d[k] with

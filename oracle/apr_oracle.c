@@ -60,6 +60,7 @@
 #define ORC_FLAG_CHANGED 1u
 #define ORC_FLAG_FIXED 2u
 #define ORC_FLAG_DEAD 4u
+#define ORC_FLAG_NEW 8u /* introduced by a split or merge, until relaxed (Sec. 2.4) */
 
 #define ORC_MAXLEV 8
 #ifndef M_PI
@@ -1074,8 +1075,8 @@ long long orc_split_pass(const orc_cfg* c, orc_state* s, const orc_region* rg, i
         double hn = s->h[i] * ORC_SPLIT_HFAC;
         s->h[i] = s->h[j] = hn;
         s->level[i] = s->level[j] = (unsigned char)(l + 1);
-        s->flags[i] |= ORC_FLAG_CHANGED;
-        s->flags[j] |= ORC_FLAG_CHANGED;
+        s->flags[i] |= ORC_FLAG_CHANGED | ORC_FLAG_NEW;
+        s->flags[j] |= ORC_FLAG_CHANGED | ORC_FLAG_NEW;
         s->id[j] = (unsigned long long)(s->next_id + k);
         ++k;
     }
@@ -1211,7 +1212,7 @@ long long orc_merge_pass(const orc_cfg* c, orc_state* s, const orc_region* rg, i
             s->u[a] = 0.5 * (s->u[a] + s->u[b]);
             s->h[a] = s->h[a] * ORC_MERGE_HFAC;
             s->level[a] = (unsigned char)(l - 1);
-            s->flags[a] |= ORC_FLAG_CHANGED;
+            s->flags[a] |= ORC_FLAG_CHANGED | ORC_FLAG_NEW;
             s->flags[b] |= ORC_FLAG_DEAD;
             ++nm;
         }
@@ -1611,4 +1612,188 @@ int orc_split_loss_grad(const orc_cfg* c, const orc_state* s, long long npar,
     free(role);
     free_state_arrays(&T);
     return 0;
+}
+
+/* ------------------------------------------------------------- relaxing */
+
+/* live particles b of s with |p - x_b| < 2 h_b (each at its own h), sorted by index */
+static void gather_point_scatter(const orc_cfg* c, const orc_state* s, const cellgrid* g,
+                                 const double p[3], double hmax, blist* out)
+{
+    out->n = 0;
+    const double R = 2.0 * hmax;
+    long long lo[3], hi[3], cnt[3];
+    for (int k = 0; k < 3; ++k) {
+        if (!g) break;
+        long long ck = cell_coord(c, g, k, p[k]);
+        long long m = (long long)ceil(R / g->cw[k]);
+        if (c->periodic[k] && 2 * m + 1 >= g->nc[k]) {
+            lo[k] = 0;
+            hi[k] = g->nc[k] - 1;
+        } else if (c->periodic[k]) {
+            lo[k] = ck - m;
+            hi[k] = ck + m;
+        } else {
+            lo[k] = ck - m < 0 ? 0 : ck - m;
+            hi[k] = ck + m >= g->nc[k] ? g->nc[k] - 1 : ck + m;
+        }
+        cnt[k] = g->nc[k];
+    }
+    long long nb = 0;
+    long long* cand = NULL;
+    if (!g) {
+        cand = (long long*)malloc(sizeof(long long) * (size_t)(s->n ? s->n : 1));
+        for (long long b = 0; b < s->n; ++b) cand[nb++] = b;
+    } else {
+        long long capc = 64;
+        cand = (long long*)malloc(sizeof(long long) * (size_t)capc);
+        for (long long i = lo[0]; i <= hi[0]; ++i)
+            for (long long j = lo[1]; j <= hi[1]; ++j)
+                for (long long k = lo[2]; k <= hi[2]; ++k) {
+                    long long ii = (i % cnt[0] + cnt[0]) % cnt[0];
+                    long long jj = (j % cnt[1] + cnt[1]) % cnt[1];
+                    long long kk = (k % cnt[2] + cnt[2]) % cnt[2];
+                    long long cell = (ii * cnt[1] + jj) * cnt[2] + kk;
+                    for (long long t = g->head[cell]; t < g->head[cell + 1]; ++t) {
+                        if (nb == capc) {
+                            capc *= 2;
+                            cand = (long long*)realloc(cand, sizeof(long long) * (size_t)capc);
+                        }
+                        cand[nb++] = g->items[t];
+                    }
+                }
+        qsort(cand, (size_t)nb, sizeof(long long), cmp_ll);
+    }
+    for (long long t = 0; t < nb; ++t) {
+        long long b = cand[t];
+        if (!is_live(s, b)) continue;
+        double d[3] = {p[0] - s->x[b], p[1] - s->y[b], p[2] - s->z[b]};
+        for (int k = 0; k < 3; ++k)
+            if (c->periodic[k]) {
+                double L = box_len(c, k);
+                if (d[k] > 0.5 * L) d[k] -= L;
+                else if (d[k] < -0.5 * L) d[k] += L;
+            }
+        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (r2 < 4.0 * s->h[b] * s->h[b]) bl_push(out, b, r2);
+    }
+    free(cand);
+}
+
+/* sum over the reference set of (m_b / rho_b) a_b W(|p - x_b|, h_b) at point p */
+static void interp_ref(const orc_cfg* c, const orc_state* ref, const cellgrid* g, double hmax,
+                       const double p[3], blist* L, double out[3])
+{
+    gather_point_scatter(c, ref, g, p, hmax, L);
+    out[0] = out[1] = out[2] = 0.0;
+    for (long long t = 0; t < L->n; ++t) {
+        long long b = L->idx[t];
+        double hb = ref->h[b], f, df;
+        kern(c, sqrt(L->r2[t]) / hb, &f, &df);
+        double wgt = mass_of(c, ref->level[b]) / ref->rho[b] * f / (kinv(c) * hb * hb * hb);
+        out[0] += wgt * ref->ax[b];
+        out[1] += wgt * ref->ay[b];
+        out[2] += wgt * ref->az[b];
+    }
+}
+
+/* the reference accelerations interpolated to npts points (xyz interleaved) */
+void orc_interp_ref(const orc_cfg* c, const orc_state* ref, long long npts, const double* pts,
+                    double* out)
+{
+    double hmax = 0.0;
+    for (long long b = 0; b < ref->n; ++b)
+        if (is_live(ref, b) && ref->h[b] > hmax) hmax = ref->h[b];
+    blist L = {0};
+    for (long long i = 0; i < npts; ++i) interp_ref(c, ref, NULL, hmax, &pts[3 * i], &L, &out[3 * i]);
+    free(L.idx);
+    free(L.r2);
+}
+
+/*
+ * Relaxing (Sec. 2.4).  The particles of s flagged NEW (introduced by splits
+ * and merges) are shuffled towards the reference set ref (the particles before
+ * the split/merge, with their density and accelerations):
+ *   a_new: the accelerations of s at the current positions (density, forces,
+ *          point masses);
+ *   a_ref: the reference accelerations interpolated to the same position,
+ *          sum over ref of (m_b / rho_b) a_b W(|x - x_b|, h_b);
+ *   dx = 0.5 dt^2 (a_new - a_ref), dt = 0.3 h / c_s of the moved particle, |dx|
+ *   capped at h; the shuffle's "kinetic energy" is sum |dx| / dt^2.
+ * Shuffles repeat until that energy is at most tol times the first shuffle's, or
+ * max_iter shuffles are done; then density and forces are recomputed and the NEW
+ * flags cleared.  Returns the shuffles done; *ke_ratio = last energy / first.
+ */
+int orc_relax(const orc_cfg* c, orc_state* s, const orc_state* ref, orc_sink* k, int nk,
+              int max_iter, double tol, double* ke_ratio)
+{
+    double hmax = 0.0;
+    for (long long b = 0; b < ref->n; ++b)
+        if (is_live(ref, b) && ref->h[b] > hmax) hmax = ref->h[b];
+    cellgrid grid, *g = NULL;
+    if (c->enumerate && ref->n > 0) {
+        grid_build(c, ref, 2.0 * hmax, &grid);
+        g = &grid;
+    }
+    double ke0 = 0.0, ke = 0.0;
+    int it = 0;
+    *ke_ratio = 0.0;
+    const long long n = s->n;
+    double* dx = (double*)calloc((size_t)(3 * (n ? n : 1)), sizeof(double));
+    double* kt = (double*)calloc((size_t)(n ? n : 1), sizeof(double));
+    for (it = 0; it < max_iter; ++it) {
+        orc_density_force(c, s, k, nk);
+        set_threads(c);
+#pragma omp parallel
+        {
+            blist L = {0};
+#pragma omp for schedule(dynamic, 64)
+            for (long long a = 0; a < n; ++a) {
+                kt[a] = 0.0;
+                dx[3 * a] = dx[3 * a + 1] = dx[3 * a + 2] = 0.0;
+                if (!is_live(s, a) || !(s->flags[a] & ORC_FLAG_NEW)) continue;
+                double p[3] = {s->x[a], s->y[a], s->z[a]};
+                double aref[3];
+                interp_ref(c, ref, g, hmax, p, &L, aref);
+                double dt = 0.3 * s->h[a] / s->cs[a];
+                double d[3] = {0.5 * dt * dt * (s->ax[a] - aref[0]), 0.5 * dt * dt * (s->ay[a] - aref[1]),
+                               0.5 * dt * dt * (s->az[a] - aref[2])};
+                double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                if (len > s->h[a]) {
+                    double sc = s->h[a] / len;
+                    d[0] *= sc;
+                    d[1] *= sc;
+                    d[2] *= sc;
+                    len = s->h[a];
+                }
+                dx[3 * a] = d[0];
+                dx[3 * a + 1] = d[1];
+                dx[3 * a + 2] = d[2];
+                kt[a] = len / (dt * dt);
+            }
+            free(L.idx);
+            free(L.r2);
+        }
+        ke = 0.0;
+        for (long long a = 0; a < n; ++a) {
+            ke += kt[a];
+            if (kt[a] > 0.0 || dx[3 * a] != 0.0 || dx[3 * a + 1] != 0.0 || dx[3 * a + 2] != 0.0) {
+                s->x[a] = wrap1(c, 0, s->x[a] + dx[3 * a]);
+                s->y[a] = wrap1(c, 1, s->y[a] + dx[3 * a + 1]);
+                s->z[a] = wrap1(c, 2, s->z[a] + dx[3 * a + 2]);
+            }
+        }
+        if (it == 0) ke0 = ke;
+        if (ke0 <= 0.0 || ke <= tol * ke0) {
+            ++it;
+            break;
+        }
+    }
+    *ke_ratio = ke0 > 0.0 ? ke / ke0 : 0.0;
+    orc_density_force(c, s, k, nk);
+    for (long long a = 0; a < n; ++a) s->flags[a] &= (unsigned char)~ORC_FLAG_NEW;
+    if (g) grid_free(g);
+    free(dx);
+    free(kt);
+    return it;
 }

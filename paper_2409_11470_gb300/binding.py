@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libapr.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "apr.h")
 
 MAXLEV, MAXREG, MAXSINK = 8, 8, 8
-FLAG_CHANGED, FLAG_FIXED, FLAG_DEAD = 1, 2, 4
+FLAG_CHANGED, FLAG_FIXED, FLAG_DEAD, FLAG_NEW = 1, 2, 4, 8
 PREC = {"fp32": 0, "fp64": 1}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CAPACITY", 3: "ERR_NR_NOCONV", 4: "ERR_NEIGH_OVERFLOW",
           5: "ERR_CUDA", 6: "ERR_STATE", 7: "ERR_WORKSPACE"}

@@ -244,7 +244,7 @@ __global__ void k_split_apply(DevCfg dc, DevRegions rg, int total, long long n,
     p.h[j] = hn;
     p.level[i] = (unsigned char)(level + 1);
     p.level[j] = (unsigned char)(level + 1);
-    p.flags[i] = p.flags[i] | APR_FLAG_CHANGED;
+    p.flags[i] = p.flags[i] | APR_FLAG_CHANGED | APR_FLAG_NEW;
     p.flags[j] = p.flags[i];
     p.id[j] = (unsigned long long)(next_id + (long long)r);
 }
@@ -1143,7 +1143,7 @@ __global__ void k_merge_apply(DevCfg dc, DevRegions rg, int M, const unsigned in
     p.u[a] = 0.5 * (p.u[a] + p.u[b]);
     p.h[a] = p.h[a] * MERGE_HFAC;
     p.level[a] = (unsigned char)(level - 1);
-    p.flags[a] = p.flags[a] | APR_FLAG_CHANGED;
+    p.flags[a] = p.flags[a] | APR_FLAG_CHANGED | APR_FLAG_NEW;
     p.flags[b] = p.flags[b] | APR_FLAG_DEAD;
     atomicAdd(&count_per_level[level], 1);
 }

@@ -192,3 +192,86 @@ def test_sound_wave_box_inputs():
     assert np.allclose(p["u"] - P0 / (w["cfg"]["gamma"] - 1.0), A * P0 * np.sin(2 * math.pi * p["x"]),
                        atol=1e-12)
 
+
+
+# ------------------------------------------------------------- relaxing
+
+def _split_c1():
+    base = oracle.Oracle(apr_synth.c1_lattice(), capacity=3 * 4096)
+    base.density_force()
+    ref = base.copy()
+    o = ref.copy()
+    o.init()
+    return ref, o
+
+
+def test_reference_interpolation_reproduces_constant_and_linear_fields():
+    # rho0 = 2.5, so that a weight m_b instead of m_b / rho_b would be off by 2.5
+    ref = oracle.Oracle(apr_synth.lattice_box(16, 0.05, seed=6, rho0=2.5, sphere_R=()))
+    ref.density()
+    n = ref.n
+    ref.a["ax"][:n] = 1.0
+    ref.a["ay"][:n] = ref["x"] - 0.5
+    ref.a["az"][:n] = 0.0
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(0.2, 0.8, (200, 3))
+    got = ref.interp_ref(pts)
+    assert np.abs(got[:, 0] - 1.0).max() < 0.06  # SPH partition of unity on a jittered lattice
+    assert np.abs(got[:, 1] - (pts[:, 0] - 0.5)).max() < 0.015
+    assert np.abs(got[:, 2]).max() == 0.0
+
+
+def test_one_shuffle_follows_the_paper_step():
+    ref, o = _split_c1()
+    new = np.nonzero(o["flags"] & oracle.FLAG_NEW)[0]
+    assert len(new) > 400
+    a_new = np.stack([o["ax"], o["ay"], o["az"]], 1)[new]  # init ends with density and forces
+    pos0 = np.stack([o["x"], o["y"], o["z"]], 1)
+    a_ref = ref.interp_ref(pos0[new])
+    dt = 0.3 * o["h"][new] / o["cs"][new]
+    d = 0.5 * (dt ** 2)[:, None] * (a_new - a_ref)
+    ln = np.linalg.norm(d, axis=1)
+    cap = ln > o["h"][new]
+    d[cap] *= (o["h"][new][cap] / ln[cap])[:, None]
+    it, _ = o.relax(ref, 1, 0.0)
+    assert it == 1
+    moved = np.stack([o["x"], o["y"], o["z"]], 1) - pos0
+    moved -= np.round(moved)  # periodic unit box
+    assert np.abs(moved[new] - d).max() < 1e-15
+    others = np.setdiff1d(np.arange(o.n), new)
+    assert not moved[others].any()
+    assert not np.any(o["flags"] & oracle.FLAG_NEW)
+
+
+def test_relaxing_energy_decays_and_improves_the_density():
+    ref, o = _split_c1()
+    lev1 = np.nonzero(o["level"] == 1)[0]
+    field = ref.copy()
+    field.a["ax"][: field.n] = field["rho"]  # interpolating rho_b gives sum m_b W = rho_ref
+
+    def rho_err(st):
+        pts = np.stack([st["x"][lev1], st["y"][lev1], st["z"][lev1]], 1)
+        return np.abs(st["rho"][lev1] / field.interp_ref(pts)[:, 0] - 1.0).mean()
+
+    e0 = rho_err(o)
+    s0 = o.stats()
+    ratios = []
+    for k in (2, 5, 10):
+        t = ref.copy()
+        t.init()
+        it, r = t.relax(ref, k, 0.0)
+        assert it == k
+        ratios.append(r)
+        if k == 5:
+            assert rho_err(t) < 0.85 * e0
+            s1 = t.stats()
+            assert s1.mass == s0.mass
+            for m in range(3):
+                assert abs(s1.mom[m] - s0.mom[m]) < 1e-15  # only positions move
+    assert 1.0 > ratios[0] > ratios[1] > ratios[2]
+    assert ratios[2] < 0.6  # about 0.91 per shuffle at this resolution
+    # the stopping rule: a tolerance reached before max_iter ends the shuffles early
+    t = ref.copy()
+    t.init()
+    it, r = t.relax(ref, 50, 0.8)
+    assert it < 50 and r <= 0.8
