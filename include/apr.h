@@ -265,6 +265,30 @@ apr_status apr_merge_pairs(apr_ctx* ctx, int level, long long* pairs, long long 
                            long long* npairs, long long* spare);
 
 /*
+ * Relaxing (Sec. 2.4): shuffle the particles flagged APR_FLAG_NEW (introduced
+ * by the split/merge passes since the last relax) towards a reference set, the
+ * particles as they were before those passes.  Each shuffle computes density
+ * and forces of the current particles (a_new), interpolates the reference
+ * accelerations to every NEW particle, a_ref = sum over the reference set of
+ * (m_b / rho_b) a_b W(|x - x_b|, h_b) (each reference particle at its own h),
+ * and moves it by dx = 0.5 dt^2 (a_new - a_ref) with dt = 0.3 h / c_s, |dx|
+ * capped at h.  The shuffle's energy is the sum of |dx| / dt^2; shuffles stop
+ * when it is at most tol times the first one's, or after max_iter (the paper:
+ * 0.005 and 50).  Then density and forces are recomputed and the NEW flags
+ * cleared.
+ *
+ * ref: DEVICE arrays x, y, z, h, rho, ax, ay, az, level, flags of nref
+ * particles (dead ones take no part; other fields are not read), caller-owned.
+ * iters (may be NULL): shuffles done; ke_ratio (may be NULL): last energy /
+ * first.  Needs n + nref <= capacity (APR_ERR_CAPACITY otherwise): the
+ * reference set is staged in the spare bound slots [n, n + nref), which are
+ * scratch.  Errors of the density solve or the lists are returned as by
+ * apr_sph_density.  Synchronises the stream.
+ */
+apr_status apr_relax(apr_ctx* ctx, const apr_particles* ref, long long nref, int max_iter,
+                     double tol, int* iters, double* ke_ratio);
+
+/*
  * Density error of one split pass and its gradient (adjoint).  The paper's
  * method has no such call: it chooses the child separation (Sec. 2.2, Eq. 2)
  * and relaxes new children (Sec. 2.5) so that the split set reproduces the

@@ -110,6 +110,7 @@ def _load():
         "apr_profile_enable": [vp, i32],
         "apr_profile_read": [vp, P(Profile), i32],
         "apr_density_loss_grad": [vp, ll, vp, vp, vp, P(C.c_double), vp, vp],
+        "apr_relax": [vp, P(Particles), ll, i32, C.c_double, P(i32), P(C.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -358,6 +359,26 @@ class Simulation:
                                               C.byref(J), C.c_void_p(gd.data_ptr()),
                                               C.c_void_p(gh.data_ptr())), "density_loss_grad")
         return J.value, gd, gh
+
+    REF_FIELDS = ("x", "y", "z", "h", "rho", "ax", "ay", "az", "level", "flags")
+
+    def snapshot(self):
+        """Device copies of the current particles' positions, h, density,
+        accelerations, levels and flags: the reference set for ``relax``."""
+        n = self.n
+        self.stream.synchronize()
+        return {f: self.t[f][:n].clone() for f in self.REF_FIELDS}
+
+    def relax(self, ref, max_iter=50, tol=0.005):
+        """Relaxing (Sec. 2.4) of the particles flagged NEW towards the reference
+        set ``ref`` (a ``snapshot`` taken before the split/merge); returns
+        (shuffles done, last / first shuffle energy)."""
+        nref = int(ref["x"].numel())
+        parts = Particles(**{f: C.c_void_p(ref[f].data_ptr()) for f in self.REF_FIELDS})
+        it, ratio = C.c_int(0), C.c_double(0.0)
+        self._check(lib.apr_relax(self.ctx, C.byref(parts), nref, int(max_iter), float(tol),
+                                  C.byref(it), C.byref(ratio)), "relax")
+        return it.value, ratio.value
 
     def merge_pairs(self, level):
         n = self.n

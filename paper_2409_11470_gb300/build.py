@@ -25,6 +25,7 @@ UNITS = {
     "apr_refine.cu": ["--fmad=false"],
     "apr_noalloc.cu": [],
     "apr_adjoint.cu": [],
+    "apr_relax.cu": [],
 }
 
 

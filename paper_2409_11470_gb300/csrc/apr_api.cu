@@ -665,6 +665,55 @@ apr_status apr_neighbour_lists(apr_ctx* c, int mode, long long* offsets, int* id
     return APR_OK;
 }
 
+// the index over the bound particles with symmetric lists at 2 max(h_a, h_b)
+static apr_status relax_index(apr_ctx* c)
+{
+    apr_status s = index_sort(c);
+    if (s != APR_OK) return s;
+    cudaMemsetAsync(c->W.status, 0, 2 * sizeof(int), c->stream);
+    s = index_lists(c, 1, 1.0);
+    if (s != APR_OK) return s;
+    return check_overflow(c);
+}
+
+apr_status apr_relax(apr_ctx* c, const apr_particles* ref, long long nref, int max_iter, double tol,
+                     int* iters, double* ke_ratio)
+{
+    if (!c || !ref || nref < 0 || max_iter < 0 || !(tol >= 0.0)) return APR_ERR_ARG;
+    if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    if (iters) *iters = 0;
+    if (ke_ratio) *ke_ratio = 0.0;
+    if (nref > 0 && (!ref->x || !ref->y || !ref->z || !ref->h || !ref->rho || !ref->ax || !ref->ay ||
+                     !ref->az || !ref->level || !ref->flags))
+        return fail(c, APR_ERR_ARG, "relax: null reference array");
+    if (nref > c->cap - c->n) return fail(c, APR_ERR_CAPACITY, "relax needs n + nref <= capacity");
+    apr_status s = relax_stage(c, ref, nref);
+    if (s != APR_OK) return s;
+    double ke0 = 0.0, ke = 0.0;
+    int it = 0;
+    for (it = 0; it < max_iter; ++it) {
+        // a_new at the current positions, then a_ref there, then the shift
+        s = run_density(c, nullptr);
+        if (s == APR_OK) s = run_force(c, true);
+        if (s == APR_OK) s = relax_interp(c, nref, relax_index);
+        if (s == APR_OK) s = relax_shift(c, &ke);
+        if (s != APR_OK) return s;
+        if (it == 0) ke0 = ke;
+        if (ke0 <= 0.0 || ke <= tol * ke0) {
+            ++it;
+            break;
+        }
+    }
+    s = run_density(c, nullptr);
+    if (s == APR_OK) s = run_force(c, true);
+    if (s == APR_OK) s = clear_new(c);
+    c->dt_valid = false;
+    if (s != APR_OK) return s;
+    if (iters) *iters = it;
+    if (ke_ratio) *ke_ratio = ke0 > 0.0 ? ke / ke0 : 0.0;
+    return APR_OK;
+}
+
 apr_status apr_density_loss_grad(apr_ctx* c, long long npar, const long long* parent,
                                  const double* d, const double* hc, double* loss, double* grad_d,
                                  double* grad_hc)

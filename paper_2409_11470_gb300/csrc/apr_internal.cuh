@@ -300,6 +300,12 @@ apr_status drift(apr_ctx* c, double dt);
 apr_status compute_stats(apr_ctx* c, apr_stats* st);
 apr_status compute_timestep(apr_ctx* c, double* dt);
 apr_status compute_stats_dt(apr_ctx* c, apr_stats* st, double* dt);
+// relaxing (apr_relax.cu)
+apr_status relax_stage(apr_ctx* c, const apr_particles* ref, long long nref);
+apr_status relax_interp(apr_ctx* c, long long nref, apr_status (*index)(apr_ctx*));
+apr_status relax_shift(apr_ctx* c, double* ke);
+apr_status clear_new(apr_ctx* c);
+
 // density error of a split and its adjoint (apr_adjoint.cu)
 apr_status adjoint_children(apr_ctx* c, long long npar, const long long* parent, const double* d,
                             const double* hc, bool* bad);
