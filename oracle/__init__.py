@@ -88,7 +88,7 @@ class State(C.Structure):
     _fields_ = [("n", C.c_longlong), ("cap", C.c_longlong), ("next_id", C.c_longlong)] + \
         [(f, _DP) for f in ("x", "y", "z", "vx", "vy", "vz", "u", "h", "rho", "omega", "ax",
                              "ay", "az", "dudt", "vsig", "dnn", "pres", "cs")] + \
-        [("level", _UP), ("flags", _UP), ("id", _ULP)]
+        [("level", _UP), ("flags", _UP), ("id", _ULP), ("bin", _UP)]
 
 
 class Counts(C.Structure):
@@ -166,6 +166,10 @@ def lib():
             L.orc_step.argtypes = [P(Cfg), P(State), P(Region), C.c_int, P(Sink), C.c_int,
                                    C.c_double, C.c_ulonglong, P(Counts), P(Stats)]
             L.orc_interp_ref.argtypes = [P(Cfg), P(State), C.c_longlong, _DP, _DP]
+            L.orc_step_bins.restype = C.c_int
+            L.orc_step_bins.argtypes = [P(Cfg), P(State), P(Region), C.c_int, C.c_int, C.c_double,
+                                        C.c_int, C.c_int, P(C.c_ulonglong), P(Counts),
+                                        P(C.c_longlong), P(C.c_longlong)]
             L.orc_relax.restype = C.c_int
             L.orc_relax.argtypes = [P(Cfg), P(State), P(State), P(Sink), C.c_int, C.c_int, C.c_double,
                                     _DP]
@@ -236,6 +240,7 @@ class Oracle:
         self.a["level"] = np.zeros(cap, np.uint8)
         self.a["flags"] = np.zeros(cap, np.uint8)
         self.a["id"] = np.zeros(cap, np.uint64)
+        self.a["bin"] = np.zeros(cap, np.uint8)
         for f, v in w["p"].items():
             self.a[f][:n] = v
         self.a["dnn"][:n] = np.inf
@@ -248,6 +253,7 @@ class Oracle:
         self.st.level = self.a["level"].ctypes.data_as(_UP)
         self.st.flags = self.a["flags"].ctypes.data_as(_UP)
         self.st.id = self.a["id"].ctypes.data_as(_ULP)
+        self.st.bin = self.a["bin"].ctypes.data_as(_UP)
         self.regions = make_regions(w["regions"])
         self.nreg = len(w["regions"])
         self.sinks = make_sinks(w["sinks"])
@@ -436,6 +442,22 @@ class Oracle:
         if rc != 0:
             raise ValueError("split_loss_grad: parent out of range, dead or repeated")
         return J.value, gd, gh
+
+    def step_bins(self, dt_max, B, init_bins=False):
+        """One step of length dt_max with individual time steps in bins 0..B
+        (Sec. 2.5); returns (counts, force updates, saturated updates)."""
+        cnt = Counts()
+        st = C.c_ulonglong(self.step_counter)
+        upd, sat = C.c_longlong(0), C.c_longlong(0)
+        rc = self.L.orc_step_bins(C.byref(self.cfg), C.byref(self.st), self.regions, self.nreg,
+                                  self.nsink, float(dt_max), int(B), 1 if init_bins else 0,
+                                  C.byref(st), C.byref(cnt), C.byref(upd), C.byref(sat))
+        self.step_counter = st.value
+        if rc == -2:
+            raise ValueError("step_bins: point masses are not supported with time-step bins")
+        if rc != 0:
+            raise RuntimeError("oracle step_bins: capacity exhausted")
+        return cnt, upd.value, sat.value
 
     def step(self, dt):
         cnt, stt = Counts(), Stats()

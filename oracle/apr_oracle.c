@@ -61,6 +61,7 @@
 #define ORC_FLAG_FIXED 2u
 #define ORC_FLAG_DEAD 4u
 #define ORC_FLAG_NEW 8u /* introduced by a split or merge, until relaxed (Sec. 2.4) */
+#define ORC_FLAG_INACTIVE 16u /* individual time steps: not at the end of its step */
 
 #define ORC_MAXLEV 8
 #ifndef M_PI
@@ -112,6 +113,7 @@ typedef struct {
     double *rho, *omega, *ax, *ay, *az, *dudt, *vsig, *dnn, *pres, *cs;
     unsigned char *level, *flags;
     unsigned long long *id;
+    unsigned char* bin; /* time-step bin (individual time steps); may be NULL otherwise */
 } orc_state;
 
 typedef struct {
@@ -1018,6 +1020,7 @@ static void copy_particle(orc_state* s, long long dst, long long src)
     CP(x); CP(y); CP(z); CP(vx); CP(vy); CP(vz); CP(u); CP(h);
     CP(rho); CP(omega); CP(ax); CP(ay); CP(az); CP(dudt); CP(vsig); CP(dnn); CP(pres); CP(cs);
     CP(level); CP(flags); CP(id);
+    if (s->bin) CP(bin);
 #undef CP
 }
 
@@ -1033,7 +1036,7 @@ long long orc_split_pass(const orc_cfg* c, orc_state* s, const orc_region* rg, i
 {
     long long n = s->n, ns = 0;
     for (long long i = 0; i < n; ++i) {
-        if (s->level[i] != l || (s->flags[i] & (ORC_FLAG_CHANGED | ORC_FLAG_FIXED | ORC_FLAG_DEAD)))
+        if (s->level[i] != l || (s->flags[i] & (ORC_FLAG_CHANGED | ORC_FLAG_FIXED | ORC_FLAG_DEAD | ORC_FLAG_INACTIVE)))
             continue;
         double p[3] = {s->x[i], s->y[i], s->z[i]};
         if (target_level(c, rg, nr, p, NULL) > l) ++ns;
@@ -1041,7 +1044,7 @@ long long orc_split_pass(const orc_cfg* c, orc_state* s, const orc_region* rg, i
     if (n + ns > s->cap) return -1;
     long long k = 0;
     for (long long i = 0; i < n; ++i) {
-        if (s->level[i] != l || (s->flags[i] & (ORC_FLAG_CHANGED | ORC_FLAG_FIXED | ORC_FLAG_DEAD)))
+        if (s->level[i] != l || (s->flags[i] & (ORC_FLAG_CHANGED | ORC_FLAG_FIXED | ORC_FLAG_DEAD | ORC_FLAG_INACTIVE)))
             continue;
         double p[3] = {s->x[i], s->y[i], s->z[i]};
         int which;
@@ -1173,7 +1176,7 @@ long long orc_merge_pass(const orc_cfg* c, orc_state* s, const orc_region* rg, i
     long long* set = (long long*)malloc(sizeof(long long) * (size_t)(n ? n : 1));
     for (long long i = 0; i < n; ++i)
         if (s->level[i] == l &&
-            !(s->flags[i] & (ORC_FLAG_CHANGED | ORC_FLAG_FIXED | ORC_FLAG_DEAD)))
+            !(s->flags[i] & (ORC_FLAG_CHANGED | ORC_FLAG_FIXED | ORC_FLAG_DEAD | ORC_FLAG_INACTIVE)))
             set[m++] = i;
     if (m % 2) {
         *spare = set[m - 1];
@@ -1796,4 +1799,134 @@ int orc_relax(const orc_cfg* c, orc_state* s, const orc_state* ref, orc_sink* k,
     free(dx);
     free(kt);
     return it;
+}
+
+/* ------------------------------------------------- individual time steps */
+
+/* the time-step limit of particle i: min(ccour h / v_sig, cforce sqrt(h / |a|)) */
+static double particle_dt(const orc_cfg* c, const orc_state* s, long long i)
+{
+    double dt = INFINITY;
+    if (s->vsig[i] > 0.0) {
+        double t = c->ccour * s->h[i] / s->vsig[i];
+        if (t < dt) dt = t;
+    }
+    double a = sqrt(s->ax[i] * s->ax[i] + s->ay[i] * s->ay[i] + s->az[i] * s->az[i]);
+    if (a > 0.0) {
+        double t = c->cforce * sqrt(s->h[i] / a);
+        if (t < dt) dt = t;
+    }
+    return dt;
+}
+
+/* the smallest bin b <= B with dt_max / 2^b <= dt (B if none) */
+static int wanted_bin(double dt, double dt_max, int B)
+{
+    int b = 0;
+    double d = dt_max;
+    while (b < B && d > dt) {
+        d *= 0.5;
+        ++b;
+    }
+    return b;
+}
+
+static void kick_one(const orc_cfg* c, orc_state* s, long long i, double hdt)
+{
+    s->vx[i] += hdt * s->ax[i];
+    s->vy[i] += hdt * s->ay[i];
+    s->vz[i] += hdt * s->az[i];
+    if (c->eos == 0) s->u[i] += hdt * s->dudt[i];
+}
+
+/*
+ * One step of length dt_max with individual time steps (Sec. 2.5): particle i
+ * in bin b_i (0 <= b_i <= B) takes steps of dt_max / 2^b_i on the grid of the
+ * 2^B substeps of dt_min = dt_max / 2^B.  Per substep k:
+ *   half kick of the particles whose step starts at k (old accelerations);
+ *   drift of every particle by dt_min;
+ *   for the particles whose step ends at k + 1 (the active ones), in the order
+ *   of the global step: split/merge restricted to them (Sec. 2.5: APR over
+ *   active particles only; children keep the parent's bin for this kick),
+ *   density and forces of the active particles (the others keep their last
+ *   values), their second half kick, and their new bins: a split or merged
+ *   particle goes to bin B (Sec. 2.5), the others to the bin of their time-step
+ *   limit, moving to a longer step only where its grid meets the current time.
+ * init_bins != 0 first assigns every particle's bin from its limit.  With B = 0
+ * this is the global step.  No point masses.  Returns 0, -1 if capacity ran
+ * out, -2 if point masses are present.  *updates: particle force updates done;
+ * *saturated: updates whose limit was below dt_min (kept in bin B).
+ */
+int orc_step_bins(const orc_cfg* c, orc_state* s, orc_region* rg, int nr, int nk, double dt_max,
+                  int B, int init_bins, unsigned long long* step, orc_counts* cnt,
+                  long long* updates, long long* saturated)
+{
+    if (nk > 0) return -2;
+    const long long nsub = 1LL << B;
+    const double dtmin = dt_max / (double)nsub;
+    memset(cnt, 0, sizeof(*cnt));
+    *updates = 0;
+    *saturated = 0;
+    if (init_bins)
+        for (long long i = 0; i < s->n; ++i) s->bin[i] = (unsigned char)wanted_bin(particle_dt(c, s, i), dt_max, B);
+    long long* act = (long long*)malloc(sizeof(long long) * (size_t)(s->cap ? s->cap : 1));
+    for (long long k = 0; k < nsub; ++k) {
+        for (long long i = 0; i < s->n; ++i) {
+            if (s->flags[i] & (ORC_FLAG_FIXED | ORC_FLAG_DEAD)) continue;
+            long long period = nsub >> s->bin[i];
+            if (k % period == 0) kick_one(c, s, i, 0.5 * dt_max / (double)(1LL << s->bin[i]));
+        }
+        for (long long i = 0; i < s->n; ++i) {
+            if (s->flags[i] & (ORC_FLAG_FIXED | ORC_FLAG_DEAD)) continue;
+            s->x[i] = wrap1(c, 0, s->x[i] + dtmin * s->vx[i]);
+            s->y[i] = wrap1(c, 1, s->y[i] + dtmin * s->vy[i]);
+            s->z[i] = wrap1(c, 2, s->z[i] + dtmin * s->vz[i]);
+        }
+        /* APR over the particles whose step ends now */
+        for (long long i = 0; i < s->n; ++i)
+            if ((k + 1) % (nsub >> s->bin[i]) != 0) s->flags[i] |= ORC_FLAG_INACTIVE;
+        orc_counts cs;
+        int rc = orc_split_merge(c, s, rg, nr, *step, &cs);
+        (*step)++;
+        for (long long i = 0; i < s->n; ++i) s->flags[i] &= (unsigned char)~ORC_FLAG_INACTIVE;
+        if (rc != 0) {
+            free(act);
+            return -1;
+        }
+        for (int l = 0; l < ORC_MAXLEV; ++l) {
+            cnt->n_split[l] += cs.n_split[l];
+            cnt->n_merge[l] += cs.n_merge[l];
+            cnt->n_spare[l] = cs.n_spare[l];
+        }
+        cnt->n_dead += cs.n_dead;
+        long long na = 0;
+        for (long long i = 0; i < s->n; ++i)
+            if (!(s->flags[i] & ORC_FLAG_DEAD) && (k + 1) % (nsub >> s->bin[i]) == 0) act[na++] = i;
+        orc_density(c, s, act, na);
+        orc_force(c, s, act, na);
+        for (long long t = 0; t < na; ++t) {
+            long long i = act[t];
+            if (s->flags[i] & ORC_FLAG_FIXED) continue;
+            kick_one(c, s, i, 0.5 * dt_max / (double)(1LL << s->bin[i]));
+        }
+        *updates += na;
+        /* new bins, on the grid point k + 1 */
+        int aligned = B; /* the longest step whose grid contains k + 1 */
+        while (aligned > 0 && (k + 1) % (nsub >> (aligned - 1)) == 0) --aligned;
+        for (long long t = 0; t < na; ++t) {
+            long long i = act[t];
+            double dti = particle_dt(c, s, i);
+            int b;
+            if (s->flags[i] & ORC_FLAG_CHANGED) {
+                b = B;
+            } else {
+                b = wanted_bin(dti, dt_max, B);
+                if (b < aligned) b = aligned;
+            }
+            if (dti < dtmin) ++(*saturated);
+            s->bin[i] = (unsigned char)b;
+        }
+    }
+    free(act);
+    return 0;
 }

@@ -275,3 +275,75 @@ def test_relaxing_energy_decays_and_improves_the_density():
     t.init()
     it, r = t.relax(ref, 50, 0.8)
     assert it < 50 and r <= 0.8
+
+
+# ------------------------------------------------- individual time steps
+
+def _sod_pair(nL=8):
+    w = apr_synth.sod(nL)
+    cap = 4 * len(w["p"]["x"])
+    a = oracle.Oracle(w, capacity=cap)
+    a.init()
+    b = oracle.Oracle(w, capacity=cap)
+    b.init()
+    return a, b
+
+
+def test_one_bin_is_the_global_step():
+    a, b = _sod_pair()
+    dt = 0.5 * a.timestep()
+    for _ in range(2):
+        ca, _ = a.step(dt)
+        cb, upd, _ = b.step_bins(dt, 0, init_bins=True)
+        assert upd == b.n
+        assert list(ca.n_split) == list(cb.n_split) and list(ca.n_merge) == list(cb.n_merge)
+    for f in ("x", "vx", "u", "rho", "h", "level", "id", "flags"):
+        assert np.array_equal(a[f], b[f]), f
+
+
+def test_bins_follow_global_stepping_at_the_finest_step():
+    a, b = _sod_pair()
+    dtmin = 0.5 * a.timestep()
+    B = 2
+    cb, upd, sat = b.step_bins(4 * dtmin, B, init_bins=True)
+    for _ in range(4):
+        a.step(dtmin)
+    assert a.n == b.n and sat == 0
+    # fewer force updates than stepping everything at dt_min
+    assert upd < 4 * b.n
+    so, sb = np.argsort(a["id"]), np.argsort(b["id"])
+    h = a["h"][so]
+    for f in ("x", "y", "z"):
+        d = np.abs(a[f][so] - b[f][sb])
+        assert d.max() < 0.05 * h.min(), f
+    assert np.abs(a["rho"][so] / b["rho"][sb] - 1.0).max() < 0.02
+    s0, s1 = a.stats(), b.stats()
+    assert s1.mass == pytest.approx(s0.mass, rel=1e-14)
+
+
+def test_bins_at_the_end_of_a_step_follow_each_limit():
+    _, b = _sod_pair()
+    dt_max = 8 * b.timestep()
+    B = 4
+    b.step_bins(dt_max, B, init_bins=True)
+    cfg = b.w["cfg"]
+    h, vs = b["h"], b["vsig"]
+    acc = np.sqrt(b["ax"] ** 2 + b["ay"] ** 2 + b["az"] ** 2)
+    lim = np.minimum(np.where(vs > 0, cfg["ccour"] * h / np.where(vs > 0, vs, 1), np.inf),
+                     np.where(acc > 0, cfg["cforce"] * np.sqrt(h / np.where(acc > 0, acc, 1)), np.inf))
+    # the longest step dt_max / 2^b that does not exceed the limit (bin B at most)
+    want = np.zeros(b.n, np.int64)
+    for k in range(1, B + 1):
+        want += (dt_max / 2.0 ** (k - 1) > lim).astype(np.int64)
+    changed = (b["flags"] & oracle.FLAG_CHANGED) != 0
+    live = (b["flags"] & oracle.FLAG_DEAD) == 0
+    assert np.array_equal(b["bin"][live & ~changed], want[live & ~changed])
+    assert np.all(b["bin"][live & changed] == B)
+    assert len(np.unique(b["bin"][live])) >= 2
+
+
+def test_bins_refuse_point_masses():
+    o = oracle.Oracle(apr_synth.disc_planet(2000), capacity=8000)
+    o.init()
+    with pytest.raises(ValueError):
+        o.step_bins(0.01, 2, init_bins=True)
