@@ -403,6 +403,10 @@ def side_measurements(args, torch, flush):
         except Exception as e:  # a side measurement never takes the headline down
             out[name] = {"error": f"{type(e).__name__}: {e}"}
     try:
+        out["sod_time_step_bins"] = bins_measurement(torch)
+    except Exception as e:
+        out["sod_time_step_bins"] = {"error": f"{type(e).__name__}: {e}"}
+    try:
         out["sound_wave_box_56832p_cylinder_zone"] = sound_wave_measurement(torch)
     except Exception as e:
         out["sound_wave_box_56832p_cylinder_zone"] = {"error": f"{type(e).__name__}: {e}"}
@@ -411,6 +415,49 @@ def side_measurements(args, torch, flush):
     except Exception as e:
         out["split_adjoint_c5_2000376p"] = {"error": f"{type(e).__name__}: {e}"}
     return out
+
+
+def bins_measurement(torch, big_steps=4):
+    """The full shock tube advanced over the same simulated time with one global
+    step (the smallest limit) and with individual time steps in bins (Sec. 2.5):
+    device time per unit of simulated time and force updates per particle and
+    unit time."""
+    import apr_synth
+    from paper_2409_11470_gb300.binding import Simulation
+    w = apr_synth.c2_sod()
+    n0 = len(w["p"]["x"])
+    res = {}
+    base = Simulation(w, capacity=3 * n0, precision="fp32")
+    base.init()
+    dt_glob = base.timestep()
+    base.close()
+    for B in (0, 2, 3):
+        g = Simulation(w, capacity=3 * n0, precision="fp32")
+        g.init()
+        dt_max = dt_glob * (1 << B)
+        st = g.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        upd, sat, first = 0, 0, True
+        for _ in range(big_steps):
+            _, u, sa, _ = g.step_bins(dt_max, B, init_bins=first)
+            first = False
+            upd += u
+            sat += sa
+        e1.record(st)
+        st.synchronize()
+        ms = e0.elapsed_time(e1)
+        t_sim = big_steps * dt_max
+        res[f"B{B}"] = {"dt_max": dt_max, "ms_per_unit_time": ms / t_sim,
+                        "updates_per_particle_per_unit_time": upd / g.n / t_sim,
+                        "saturated_updates": sat, "n_last": g.n}
+        g.close()
+    b0 = res["B0"]["ms_per_unit_time"]
+    for B in (2, 3):
+        res[f"B{B}"]["speedup_vs_global_step"] = b0 / res[f"B{B}"]["ms_per_unit_time"]
+    res["note"] = ("B0 is the global step at the smallest limit; every substep re-sorts all "
+                   "particles, so the force updates saved are only part of the step")
+    return res
 
 
 def sound_wave_measurement(torch, t_end=2.0):

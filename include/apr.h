@@ -51,7 +51,8 @@ typedef enum {
 /* particle flag bits: CHANGED by the current split/merge pass; FIXED never moves,
    splits or merges; DEAD removed at the next compaction; NEW introduced by a split
    or merge and not yet relaxed (apr_relax clears it) */
-enum { APR_FLAG_CHANGED = 1, APR_FLAG_FIXED = 2, APR_FLAG_DEAD = 4, APR_FLAG_NEW = 8 };
+enum { APR_FLAG_CHANGED = 1, APR_FLAG_FIXED = 2, APR_FLAG_DEAD = 4, APR_FLAG_NEW = 8,
+       APR_FLAG_INACTIVE = 16 /* set only inside apr_step_bins: not at the end of its step */ };
 enum { APR_SHAPE_SPHERE = 0, APR_SHAPE_SLAB = 1, APR_SHAPE_CYLINDER = 2 };
 enum { APR_EOS_ADIABATIC = 0, APR_EOS_LOCALLY_ISOTHERMAL = 1 };
 enum { APR_PREC_FP32_MIXED = 0, APR_PREC_FP64 = 1 };
@@ -130,6 +131,7 @@ typedef struct {
     double *rho, *omega, *ax, *ay, *az, *dudt, *vsig, *dnn, *pres, *cs;
     unsigned char *level, *flags;
     unsigned long long *id;
+    unsigned char* bin; /* time-step bin (apr_step_bins); may be NULL otherwise */
 } apr_particles;
 
 typedef struct {
@@ -263,6 +265,30 @@ apr_status apr_neighbour_lists(apr_ctx* ctx, int mode, long long* offsets, int* 
  */
 apr_status apr_merge_pairs(apr_ctx* ctx, int level, long long* pairs, long long cap,
                            long long* npairs, long long* spare);
+
+/*
+ * One step of length dt_max with individual time steps (Sec. 2.5).  Particle i
+ * sits in bin b_i (0..max_bin) and steps dt_max / 2^b_i on the grid of the
+ * 2^max_bin substeps of dt_min = dt_max / 2^max_bin.  Per substep: half kick of
+ * the particles whose step starts (old accelerations), drift of every
+ * particle, then for the particles whose step ends (the active ones), in the
+ * order of apr_step: split/merge restricted to them (APR over active particles
+ * only), their density and forces (the others keep their last values), their
+ * second half kick, and their new bin: split or merged particles go to
+ * max_bin; the others to the longest step dt_max / 2^b not above their limit
+ * min(ccour h / v_sig, cforce sqrt(h / |a|)), moving to a longer step only
+ * where its grid meets the current time.  init_bins != 0 first bins every
+ * particle by its limit.  With max_bin = 0 this is apr_step(dt_max).
+ *
+ * Needs the bound bin array and forces from a previous pass (apr_init or a
+ * step); point masses are not supported (APR_ERR_STATE).  counts: summed over
+ * the substeps; updates: particle force updates done; saturated: updates whose
+ * limit was below dt_min (kept in max_bin); stats: conservation sums at the
+ * end.  Any of them may be NULL.
+ */
+apr_status apr_step_bins(apr_ctx* ctx, double dt_max, int max_bin, int init_bins,
+                         apr_counts* counts, long long* updates, long long* saturated,
+                         apr_stats* stats);
 
 /*
  * Relaxing (Sec. 2.4): shuffle the particles flagged APR_FLAG_NEW (introduced

@@ -50,7 +50,7 @@ class Sink(C.Structure):
 
 class Particles(C.Structure):
     _fields_ = [(f, C.c_void_p) for f in F64_FIELDS] + \
-        [("level", C.c_void_p), ("flags", C.c_void_p), ("id", C.c_void_p)]
+        [("level", C.c_void_p), ("flags", C.c_void_p), ("id", C.c_void_p), ("bin", C.c_void_p)]
 
 
 class Counts(C.Structure):
@@ -111,6 +111,7 @@ def _load():
         "apr_profile_read": [vp, P(Profile), i32],
         "apr_density_loss_grad": [vp, ll, vp, vp, vp, P(C.c_double), vp, vp],
         "apr_relax": [vp, P(Particles), ll, i32, C.c_double, P(i32), P(C.c_double)],
+        "apr_step_bins": [vp, C.c_double, i32, i32, P(Counts), P(ll), P(ll), P(Stats)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -205,6 +206,7 @@ class Simulation:
         self.t["level"] = torch.zeros(cap, dtype=torch.uint8, device=self.device)
         self.t["flags"] = torch.zeros(cap, dtype=torch.uint8, device=self.device)
         self.t["id"] = torch.zeros(cap, dtype=torch.int64, device=self.device)
+        self.t["bin"] = torch.zeros(cap, dtype=torch.uint8, device=self.device)
         for f, v in w["p"].items():
             src = torch.from_numpy(np.ascontiguousarray(v).view(np.int64) if f == "id" else
                                    np.ascontiguousarray(v))
@@ -297,6 +299,16 @@ class Simulation:
         self._check(lib.apr_step(self.ctx, float(dt), C.byref(used), C.byref(st), C.byref(cnt)),
                     "step")
         return used.value, st, cnt
+
+    def step_bins(self, dt_max, max_bin, init_bins=False):
+        """One step of dt_max with individual time steps in bins 0..max_bin
+        (Sec. 2.5); returns (counts, force updates, saturated updates, stats)."""
+        cnt, st = Counts(), Stats()
+        upd, sat = C.c_longlong(0), C.c_longlong(0)
+        self._check(lib.apr_step_bins(self.ctx, float(dt_max), int(max_bin), 1 if init_bins else 0,
+                                      C.byref(cnt), C.byref(upd), C.byref(sat), C.byref(st)),
+                    "step_bins")
+        return cnt, upd.value, sat.value, st
 
     def timestep(self):
         dt = C.c_double()

@@ -1,8 +1,9 @@
 """Build the CUDA library ``libapr.so`` for sm_103a, in-tree, with nvcc.
 
-Four translation units compile in parallel; the refinement and index units
-are compiled with ``--fmad=false`` so their float64 geometry (split placement,
-merge centre of mass, lattice quantisation) rounds exactly as written.
+The translation units compile in parallel; the refinement, index and
+time-step-bin units are compiled with ``--fmad=false`` so their float64
+geometry and integration (split placement, merge centre of mass, lattice
+quantisation, kicks, bin decisions) round exactly as written.
 """
 from __future__ import annotations
 
@@ -26,6 +27,7 @@ UNITS = {
     "apr_noalloc.cu": [],
     "apr_adjoint.cu": [],
     "apr_relax.cu": [],
+    "apr_bins.cu": ["--fmad=false"],
 }
 
 

@@ -145,6 +145,7 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.point_q = (int*)take(4 * C);
     w.retry_q[0] = (int*)take(4 * C);
     w.retry_q[1] = (int*)take(4 * C);
+    w.active_q = (int*)take(4 * C);
     // the list memory doubles as compaction scratch (20 x 8 bytes per particle)
     w.nbr = (unsigned int*)take((4 * K > 160 ? 4 * K : 160) * C);
     w.ncnt = (int*)take(4 * C);
@@ -662,6 +663,134 @@ apr_status apr_neighbour_lists(apr_ctx* c, int mode, long long* offsets, int* id
         long long a = perm[sl], o = offsets[a];
         for (int k = 0; k < cnt[sl]; ++k) idx[o + k] = (int)perm[nb[(size_t)k * n + sl]];
     }
+    return APR_OK;
+}
+
+// density of the nq particles of the active queue (sorted slots), with retries
+// over the ones that outgrow their lists; their lists come from the cell pass
+// when they are many, from per-particle tree walks when they are few
+static apr_status run_density_active(apr_ctx* c, long long nq, bool all)
+{
+    Workspace& W = c->W;
+    long long unc = 0, noconv = 0, shrinks = 0;
+    int attempts = 0, q = 0;
+    apr_status s = APR_OK;
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        cudaMemsetAsync(W.status, 0, 2 * sizeof(int), c->stream);
+        if (attempt == 0) {
+            s = all ? index_lists(c, 1, DENSITY_REACH, true)
+                    : index_lists_queue(c, W.active_q, &W.status[ST_ACTIVE_N], DENSITY_REACH, true);
+            if (s == APR_OK) s = density_pass(c, &unc, &noconv, W.active_q, nq, q);
+        } else {
+            s = index_refresh_h(c);
+            if (s == APR_OK)
+                s = index_lists_queue(c, W.retry_q[q], &W.status[ST_RETRY_N + q], DENSITY_REACH);
+            const long long nr = unc;
+            if (s == APR_OK) s = density_pass(c, &unc, &noconv, W.retry_q[q], nr, q ^ 1);
+            q ^= 1;
+        }
+        if (s != APR_OK) return s;
+        ++attempts;
+        shrinks += c->last_shrink;
+        c->prof_attempts += 1;
+        c->prof_unc += unc;
+        c->prof_shrink += c->last_shrink;
+        if (unc == 0) break;
+    }
+    c->lists_fresh = attempts == 1;
+    if (unc && shrinks)
+        return fail(c, APR_ERR_NEIGH_OVERFLOW,
+                    "neighbour lists cannot hold the particles within reach: raise max_neigh");
+    if (unc) return fail(c, APR_ERR_NR_NOCONV, "smoothing lengths kept outgrowing their lists");
+    if (noconv) return fail(c, APR_ERR_NR_NOCONV, "h-rho iteration did not converge everywhere");
+    return APR_OK;
+}
+
+// forces of the particles of the active queue
+static apr_status run_force_active(apr_ctx* c, long long nq, bool all)
+{
+    Workspace& W = c->W;
+    apr_status s;
+    if (!c->lists_fresh) {
+        s = index_refresh_h(c);
+        if (s != APR_OK) return s;
+        cudaMemsetAsync(W.status, 0, 2 * sizeof(int), c->stream);
+        s = all ? index_lists(c, 1, 1.0)
+                : index_lists_queue(c, W.active_q, &W.status[ST_ACTIVE_N], 1.0, false);
+        if (s != APR_OK) return s;
+        c->lists_fresh = true;
+    }
+    int ps = prof_begin(c, APR_PROF_OTHER);
+    s = gather_force_data(c);
+    prof_end(c, ps);
+    if (s != APR_OK) return s;
+    s = force_pass(c, W.active_q, nq);
+    if (s != APR_OK) return s;
+    return check_overflow(c);
+}
+
+apr_status apr_step_bins(apr_ctx* c, double dt_max, int B, int init_bins, apr_counts* counts,
+                         long long* updates, long long* saturated, apr_stats* stats)
+{
+    if (!c) return APR_ERR_ARG;
+    if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    if (!c->p.bin) return fail(c, APR_ERR_STATE, "step_bins: no bin array bound");
+    if (c->nsink > 0)
+        return fail(c, APR_ERR_STATE, "step_bins: point masses are not supported with time-step bins");
+    if (!(dt_max > 0.0) || B < 0 || B > 20) return fail(c, APR_ERR_ARG, "step_bins: bad dt_max or max_bin");
+    if (!c->have_force) return fail(c, APR_ERR_STATE, "apr_init or a force pass first");
+    Workspace& W = c->W;
+    apr_counts total;
+    memset(&total, 0, sizeof(total));
+    long long upd = 0;
+    cudaMemsetAsync(&W.status[ST_SATURATED], 0, sizeof(int), c->stream);
+    apr_status s = APR_OK;
+    if (init_bins) s = bins_init(c, dt_max, B);
+    const long long nsub = 1LL << B;
+    const double dtmin = dt_max / (double)nsub;
+    for (long long k = 0; k < nsub && s == APR_OK; ++k) {
+        s = bins_kick(c, dt_max, B, k, 0);
+        if (s == APR_OK) s = drift(c, dtmin);
+        if (s != APR_OK) break;
+        // split/merge over the particles whose step ends now (Sec. 2.5)
+        apr_counts cs;
+        s = bins_mark_inactive(c, k, B, true);
+        if (s == APR_OK) s = split_merge_pass(c, &cs);
+        apr_status s2 = bins_mark_inactive(c, k, B, false);
+        if (s == APR_OK) s = s2;
+        if (s != APR_OK) break;
+        for (int l = 0; l < APR_MAXLEV; ++l) {
+            total.n_split[l] += cs.n_split[l];
+            total.n_merge[l] += cs.n_merge[l];
+            total.n_spare[l] = cs.n_spare[l];
+        }
+        total.n_dead += cs.n_dead;
+        long long nq = 0;
+        s = index_sort(c);
+        if (s == APR_OK) s = bins_active_queue(c, k, B, &nq);
+        const bool all = nq > c->n / 4;
+        if (s == APR_OK && nq > 0) s = run_density_active(c, nq, all);
+        if (s == APR_OK && nq > 0) s = run_force_active(c, nq, all);
+        if (s == APR_OK) s = bins_kick(c, dt_max, B, k, 1);
+        if (s == APR_OK) s = bins_rebin(c, dt_max, B, k, nq);
+        upd += nq;
+    }
+    c->dt_valid = false;
+    c->lists_fresh = false;
+    if (s != APR_OK) return s;
+    int sat = 0;
+    cudaMemcpyAsync(c->hbuf, &W.status[ST_SATURATED], sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    s = cuda_check(c, cudaStreamSynchronize(c->stream), "step_bins");
+    if (s != APR_OK) return s;
+    sat = ((int*)c->hbuf)[0];
+    if (stats) {
+        s = compute_stats(c, stats);
+        if (s != APR_OK) return s;
+    }
+    if (counts) *counts = total;
+    if (updates) *updates = upd;
+    if (saturated) *saturated = sat;
+    c->have_force = true;
     return APR_OK;
 }
 

@@ -1001,7 +1001,8 @@ static void launch_lists(apr_ctx* c, const int* ncell_dev, int n, bool graceful)
 
 // symmetric lists (graceful: an overflow marks the list, the density pass shrinks h)
 // of the queued particles only; the cells and candidate lists are not touched
-apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, double reach)
+apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, double reach,
+                             bool graceful)
 {
     Workspace& W = c->W;
     const int n = (int)c->n;
@@ -1015,7 +1016,8 @@ apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, 
 #define APR_QUEUE_CASE(M, X, Y, Z)                                                                   \
     case M:                                                                                          \
         APR_LAUNCH(c, (k_lists_point<X, Y, Z, 1>), 152 * 4, 128, c->dc, qlen_dev, queue, n, c->cap,   \
-                   W.left, W.right, W.pk, W.sthr, W.nlo, W.nhi, W.nthr, W.nbr, W.ncnt, W.status, 1);  \
+                   W.left, W.right, W.pk, W.sthr, W.nlo, W.nhi, W.nthr, W.nbr, W.ncnt, W.status,      \
+                   graceful ? 1 : 0);                                                                \
         break;
     switch (mask) {
         APR_QUEUE_CASE(0, 0, 0, 0)

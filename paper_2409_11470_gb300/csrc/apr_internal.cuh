@@ -39,6 +39,8 @@ enum {
     ST_POINT_N = 11,         // lists: particles queued for the per-particle search
     ST_TREE_ERR = 12,        // pairing tree: 1 barrier timeout, 2 leaves not reached
     ST_RETRY_N = 13,         // density: lengths of the two retry queues (2 words)
+    ST_ACTIVE_N = 15,        // time-step bins: length of the active queue
+    ST_SATURATED = 40,       // time-step bins: updates whose limit was below dt_min
     ST_BINS = 16,            // merge: first slot of each level's candidates (10 words)
     ST_MERGES = 32,          // merge: merges per level (8 words)
     ST_NSTATUS = 16
@@ -149,6 +151,7 @@ struct Workspace {
     int* ncand;
     int* point_q;             // particles of cells whose candidate list overflowed
     int* retry_q[2];          // density: particles that need another attempt
+    int* active_q;            // time-step bins: sorted slots of the active particles
     // neighbour lists, transposed: nbr[k * cap + sorted slot]
     unsigned int* nbr;
     int* ncnt;
@@ -280,12 +283,13 @@ apr_status index_refresh_h(apr_ctx* c);      // re-gather h and node hmax after 
 // graceful: an overflowing list is marked (count -1) instead of flagged as an error.
 apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful = false);
 // symmetric lists of the queued particles only, by a per-particle tree walk
-apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, double reach);
+apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, double reach,
+                             bool graceful = true);
 
 // SPH passes (apr_sph.cu)
 apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv,
                         const int* active = nullptr, long long nactive = 0, int out_q = 0);
-apr_status force_pass(apr_ctx* c);
+apr_status force_pass(apr_ctx* c, const int* active = nullptr, long long nactive = 0);
 apr_status gather_force_data(apr_ctx* c);
 
 // refinement, sinks, integration (apr_refine.cu)
@@ -300,6 +304,13 @@ apr_status drift(apr_ctx* c, double dt);
 apr_status compute_stats(apr_ctx* c, apr_stats* st);
 apr_status compute_timestep(apr_ctx* c, double* dt);
 apr_status compute_stats_dt(apr_ctx* c, apr_stats* st, double* dt);
+// individual time steps (apr_bins.cu)
+apr_status bins_init(apr_ctx* c, double dt_max, int B);
+apr_status bins_kick(apr_ctx* c, double dt_max, int B, long long k, int end_of_step);
+apr_status bins_mark_inactive(apr_ctx* c, long long k, int B, bool on);
+apr_status bins_active_queue(apr_ctx* c, long long k, int B, long long* nact);
+apr_status bins_rebin(apr_ctx* c, double dt_max, int B, long long k, long long nq);
+
 // relaxing (apr_relax.cu)
 apr_status relax_stage(apr_ctx* c, const apr_particles* ref, long long nref);
 apr_status relax_interp(apr_ctx* c, long long nref, apr_status (*index)(apr_ctx*));

@@ -174,7 +174,7 @@ __global__ void k_split_keys(DevCfg dc, DevRegions rg, long long n, const double
     if (i >= n) return;
     const int l = lev[i];
     bool split = false;
-    if (l < dc.lmax && !(flags[i] & (APR_FLAG_CHANGED | APR_FLAG_FIXED | APR_FLAG_DEAD)))
+    if (l < dc.lmax && !(flags[i] & (APR_FLAG_CHANGED | APR_FLAG_FIXED | APR_FLAG_DEAD | APR_FLAG_INACTIVE)))
         split = target_level(dc, rg, x[i], y[i], z[i], nullptr) > l;
     key[i] = split ? (unsigned long long)l : 255ULL;
     val[i] = (unsigned)i;
@@ -232,6 +232,7 @@ __global__ void k_split_apply(DevCfg dc, DevRegions rg, int total, long long n,
     p.vsig[j] = p.vsig[i];
     p.dnn[j] = p.dnn[i];
     p.pres[j] = p.pres[i];
+    if (p.bin) p.bin[j] = p.bin[i];
     p.cs[j] = p.cs[i];
     p.x[i] = wrap1(dc, 0, px + rsep * w[0]);
     p.y[i] = wrap1(dc, 1, py + rsep * w[1]);
@@ -272,7 +273,7 @@ __global__ void k_merge_keys(long long n, const unsigned char* __restrict__ lev,
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int l = lev[i];
-    const bool cand = l >= 1 && !(flags[i] & (APR_FLAG_CHANGED | APR_FLAG_FIXED | APR_FLAG_DEAD));
+    const bool cand = l >= 1 && !(flags[i] & (APR_FLAG_CHANGED | APR_FLAG_FIXED | APR_FLAG_DEAD | APR_FLAG_INACTIVE));
     key[i] = cand ? (unsigned long long)l : 255ULL;
     val[i] = (unsigned)i;
 }
@@ -1302,6 +1303,7 @@ struct FieldPtrs {
     unsigned long long* id;
     unsigned char* level;
     unsigned char* flags;
+    unsigned char* bin;  // may be null
 };
 
 static FieldPtrs field_ptrs(const apr_particles& p)
@@ -1313,6 +1315,7 @@ static FieldPtrs field_ptrs(const apr_particles& p)
     f.id = p.id;
     f.level = p.level;
     f.flags = p.flags;
+    f.bin = p.bin;
     return f;
 }
 
@@ -1337,6 +1340,7 @@ __global__ void k_compact_out(long long n, long long cap, FieldPtrs f,
     unsigned char* b = (unsigned char*)(tmp + 19 * cap);
     b[j] = f.level[i];
     b[cap + j] = fl;
+    if (f.bin) b[2 * cap + j] = f.bin[i];
 }
 
 __global__ void k_compact_back(long long nlive, long long cap, FieldPtrs f,
@@ -1349,6 +1353,7 @@ __global__ void k_compact_back(long long nlive, long long cap, FieldPtrs f,
     const unsigned char* b = (const unsigned char*)(tmp + 19 * cap);
     f.level[j] = b[j];
     f.flags[j] = b[cap + j];
+    if (f.bin) f.bin[j] = b[2 * cap + j];
 }
 
 // stable removal of dead particles.  The neighbour-list memory serves as scratch

@@ -405,11 +405,13 @@ __global__ void __launch_bounds__(128, force_min_blocks<R>())
             const unsigned int* __restrict__ perm, double* __restrict__ ax_out,
             double* __restrict__ ay_out, double* __restrict__ az_out,
             double* __restrict__ dudt_out, double* __restrict__ vsig_out,
-            unsigned long long* counters)
+            unsigned long long* counters, const int* __restrict__ active, long long nactive)
 {
+    // all particles, or (active != nullptr) the nactive listed sorted slots
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const int a = (int)s;
+    if (s >= (active ? nactive : n)) return;
+    const int a = active ? active[s] : (int)s;
+    if (a < 0 || a >= n) return;
     const int4 pa = pk[a];
     const F4<R> Aa = ld4<R>(Abuf, a), Va = ld4<R>(Vbuf, a), Ba = ld4<R>(Bbuf, a);
     ForceSelf<R> A;
@@ -461,20 +463,21 @@ __global__ void __launch_bounds__(128, force_min_blocks<R>())
     vsig_out[i] = (double)vsig;
 }
 
-apr_status force_pass(apr_ctx* c)
+apr_status force_pass(apr_ctx* c, const int* active, long long nactive)
 {
     Workspace& W = c->W;
     const long long n = c->n;
-    if (n <= 0) return APR_OK;
+    const long long work = active ? nactive : n;
+    if (n <= 0 || work <= 0) return APR_OK;
     const int ps = prof_begin(c, APR_PROF_FORCE);
     if (c->cfg.precision == APR_PREC_FP64)
-        APR_LAUNCH(c, k_force<double>, nblocks(n, 128), 128, 
+        APR_LAUNCH(c, k_force<double>, nblocks(work, 128), 128,
             c->dc, n, c->cap, W.pk, W.dA, W.dV, W.dB, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
-            c->p.ax, c->p.ay, c->p.az, c->p.dudt, c->p.vsig, W.counters);
+            c->p.ax, c->p.ay, c->p.az, c->p.dudt, c->p.vsig, W.counters, active, nactive);
     else
-        APR_LAUNCH(c, k_force<float>, nblocks(n, 128), 128, 
+        APR_LAUNCH(c, k_force<float>, nblocks(work, 128), 128,
             c->dc, n, c->cap, W.pk, W.fA, W.fV, W.fB, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
-            c->p.ax, c->p.ay, c->p.az, c->p.dudt, c->p.vsig, W.counters);
+            c->p.ax, c->p.ay, c->p.az, c->p.dudt, c->p.vsig, W.counters, active, nactive);
     prof_end(c, ps);
     return cuda_check(c, cudaGetLastError(), "force");
 }
