@@ -167,9 +167,9 @@ def lib():
                                    C.c_double, C.c_ulonglong, P(Counts), P(Stats)]
             L.orc_interp_ref.argtypes = [P(Cfg), P(State), C.c_longlong, _DP, _DP]
             L.orc_step_bins.restype = C.c_int
-            L.orc_step_bins.argtypes = [P(Cfg), P(State), P(Region), C.c_int, C.c_int, C.c_double,
-                                        C.c_int, C.c_int, P(C.c_ulonglong), P(Counts),
-                                        P(C.c_longlong), P(C.c_longlong)]
+            L.orc_step_bins.argtypes = [P(Cfg), P(State), P(Region), C.c_int, P(Sink), C.c_int,
+                                        C.c_double, C.c_int, C.c_int, P(C.c_ulonglong),
+                                        P(Counts), P(C.c_longlong), P(C.c_longlong)]
             L.orc_relax.restype = C.c_int
             L.orc_relax.argtypes = [P(Cfg), P(State), P(State), P(Sink), C.c_int, C.c_int, C.c_double,
                                     _DP]
@@ -450,11 +450,10 @@ class Oracle:
         st = C.c_ulonglong(self.step_counter)
         upd, sat = C.c_longlong(0), C.c_longlong(0)
         rc = self.L.orc_step_bins(C.byref(self.cfg), C.byref(self.st), self.regions, self.nreg,
-                                  self.nsink, float(dt_max), int(B), 1 if init_bins else 0,
-                                  C.byref(st), C.byref(cnt), C.byref(upd), C.byref(sat))
+                                  self.sinks, self.nsink, float(dt_max), int(B),
+                                  1 if init_bins else 0, C.byref(st), C.byref(cnt), C.byref(upd),
+                                  C.byref(sat))
         self.step_counter = st.value
-        if rc == -2:
-            raise ValueError("step_bins: point masses are not supported with time-step bins")
         if rc != 0:
             raise RuntimeError("oracle step_bins: capacity exhausted")
         return cnt, upd.value, sat.value

@@ -816,20 +816,26 @@ void orc_force(const orc_cfg* c, orc_state* s, const long long* sample, long lon
 }
 
 /* point-mass gravity: sinks on gas (added to a), gas and sinks on sinks */
-void orc_sink_gravity(const orc_cfg* c, orc_state* s, orc_sink* k, int nk)
+/* gets == NULL: every live gas particle takes the point masses' pull; else only
+ * those with gets[i] != 0.  The point masses feel every live gas particle. */
+static void sink_gravity_some(const orc_cfg* c, orc_state* s, orc_sink* k, int nk,
+                              const unsigned char* gets)
 {
     for (int j = 0; j < nk; ++j) k[j].a[0] = k[j].a[1] = k[j].a[2] = 0.0;
     for (long long i = 0; i < s->n; ++i) {
         if (!is_live(s, i)) continue;
         double mi = mass_of(c, s->level[i]);
+        const int pulled = gets == NULL || gets[i];
         for (int j = 0; j < nk; ++j) {
             double dx = s->x[i] - k[j].x[0], dy = s->y[i] - k[j].x[1], dz = s->z[i] - k[j].x[2];
             double r2 = dx * dx + dy * dy + dz * dz;
             double r = sqrt(r2);
             double f = c->G / (r2 * r);
-            s->ax[i] -= f * k[j].m * dx;
-            s->ay[i] -= f * k[j].m * dy;
-            s->az[i] -= f * k[j].m * dz;
+            if (pulled) {
+                s->ax[i] -= f * k[j].m * dx;
+                s->ay[i] -= f * k[j].m * dy;
+                s->az[i] -= f * k[j].m * dz;
+            }
             k[j].a[0] += f * mi * dx;
             k[j].a[1] += f * mi * dy;
             k[j].a[2] += f * mi * dz;
@@ -847,6 +853,11 @@ void orc_sink_gravity(const orc_cfg* c, orc_state* s, orc_sink* k, int nk)
             k[j].a[1] -= f * dy;
             k[j].a[2] -= f * dz;
         }
+}
+
+void orc_sink_gravity(const orc_cfg* c, orc_state* s, orc_sink* k, int nk)
+{
+    sink_gravity_some(c, s, k, nk, NULL);
 }
 
 /* ----------------------------------------------------- refinement levels */
@@ -1852,16 +1863,20 @@ static void kick_one(const orc_cfg* c, orc_state* s, long long i, double hdt)
  *   values), their second half kick, and their new bins: a split or merged
  *   particle goes to bin B (Sec. 2.5), the others to the bin of their time-step
  *   limit, moving to a longer step only where its grid meets the current time.
+ * Point masses take every substep (bin B): half kick, drift, accretion of the
+ * live gas inside their radii and zones moved onto them after the drift, and
+ * after the active particles' forces their pull on the active gas and their
+ * accelerations from every live gas particle at its current position, then the
+ * closing half kick.
  * init_bins != 0 first assigns every particle's bin from its limit.  With B = 0
- * this is the global step.  No point masses.  Returns 0, -1 if capacity ran
- * out, -2 if point masses are present.  *updates: particle force updates done;
- * *saturated: updates whose limit was below dt_min (kept in bin B).
+ * this is the global step.  Returns 0, or -1 if capacity ran out.  *updates:
+ * particle force updates done; *saturated: updates whose limit was below
+ * dt_min (kept in bin B).
  */
-int orc_step_bins(const orc_cfg* c, orc_state* s, orc_region* rg, int nr, int nk, double dt_max,
-                  int B, int init_bins, unsigned long long* step, orc_counts* cnt,
+int orc_step_bins(const orc_cfg* c, orc_state* s, orc_region* rg, int nr, orc_sink* kk, int nk,
+                  double dt_max, int B, int init_bins, unsigned long long* step, orc_counts* cnt,
                   long long* updates, long long* saturated)
 {
-    if (nk > 0) return -2;
     const long long nsub = 1LL << B;
     const double dtmin = dt_max / (double)nsub;
     memset(cnt, 0, sizeof(*cnt));
@@ -1870,18 +1885,25 @@ int orc_step_bins(const orc_cfg* c, orc_state* s, orc_region* rg, int nr, int nk
     if (init_bins)
         for (long long i = 0; i < s->n; ++i) s->bin[i] = (unsigned char)wanted_bin(particle_dt(c, s, i), dt_max, B);
     long long* act = (long long*)malloc(sizeof(long long) * (size_t)(s->cap ? s->cap : 1));
+    unsigned char* pulled = (unsigned char*)malloc((size_t)(s->cap ? s->cap : 1));
     for (long long k = 0; k < nsub; ++k) {
         for (long long i = 0; i < s->n; ++i) {
             if (s->flags[i] & (ORC_FLAG_FIXED | ORC_FLAG_DEAD)) continue;
             long long period = nsub >> s->bin[i];
             if (k % period == 0) kick_one(c, s, i, 0.5 * dt_max / (double)(1LL << s->bin[i]));
         }
+        for (int j = 0; j < nk; ++j)
+            for (int d = 0; d < 3; ++d) kk[j].v[d] += 0.5 * dtmin * kk[j].a[d];
         for (long long i = 0; i < s->n; ++i) {
             if (s->flags[i] & (ORC_FLAG_FIXED | ORC_FLAG_DEAD)) continue;
             s->x[i] = wrap1(c, 0, s->x[i] + dtmin * s->vx[i]);
             s->y[i] = wrap1(c, 1, s->y[i] + dtmin * s->vy[i]);
             s->z[i] = wrap1(c, 2, s->z[i] + dtmin * s->vz[i]);
         }
+        for (int j = 0; j < nk; ++j)
+            for (int d = 0; d < 3; ++d) kk[j].x[d] += dtmin * kk[j].v[d];
+        if (nk > 0) cnt->n_accreted += orc_accrete(c, s, kk, nk);
+        orc_track_regions(rg, nr, kk, nk);
         /* APR over the particles whose step ends now */
         for (long long i = 0; i < s->n; ++i)
             if ((k + 1) % (nsub >> s->bin[i]) != 0) s->flags[i] |= ORC_FLAG_INACTIVE;
@@ -1891,6 +1913,7 @@ int orc_step_bins(const orc_cfg* c, orc_state* s, orc_region* rg, int nr, int nk
         for (long long i = 0; i < s->n; ++i) s->flags[i] &= (unsigned char)~ORC_FLAG_INACTIVE;
         if (rc != 0) {
             free(act);
+            free(pulled);
             return -1;
         }
         for (int l = 0; l < ORC_MAXLEV; ++l) {
@@ -1904,11 +1927,18 @@ int orc_step_bins(const orc_cfg* c, orc_state* s, orc_region* rg, int nr, int nk
             if (!(s->flags[i] & ORC_FLAG_DEAD) && (k + 1) % (nsub >> s->bin[i]) == 0) act[na++] = i;
         orc_density(c, s, act, na);
         orc_force(c, s, act, na);
+        if (nk > 0) {
+            memset(pulled, 0, (size_t)s->n);
+            for (long long t = 0; t < na; ++t) pulled[act[t]] = 1;
+            sink_gravity_some(c, s, kk, nk, pulled);
+        }
         for (long long t = 0; t < na; ++t) {
             long long i = act[t];
             if (s->flags[i] & ORC_FLAG_FIXED) continue;
             kick_one(c, s, i, 0.5 * dt_max / (double)(1LL << s->bin[i]));
         }
+        for (int j = 0; j < nk; ++j)
+            for (int d = 0; d < 3; ++d) kk[j].v[d] += 0.5 * dtmin * kk[j].a[d];
         *updates += na;
         /* new bins, on the grid point k + 1 */
         int aligned = B; /* the longest step whose grid contains k + 1 */
@@ -1928,5 +1958,6 @@ int orc_step_bins(const orc_cfg* c, orc_state* s, orc_region* rg, int nr, int nk
         }
     }
     free(act);
+    free(pulled);
     return 0;
 }

@@ -342,8 +342,81 @@ def test_bins_at_the_end_of_a_step_follow_each_limit():
     assert len(np.unique(b["bin"][live])) >= 2
 
 
-def test_bins_refuse_point_masses():
-    o = oracle.Oracle(apr_synth.disc_planet(2000), capacity=8000)
-    o.init()
-    with pytest.raises(ValueError):
-        o.step_bins(0.01, 2, init_bins=True)
+def _disc_pair(n=2000, racc_star=None, zone=True):
+    w = apr_synth.disc_planet(n)
+    if racc_star is not None:
+        w["sinks"][0]["racc"] = racc_star
+    if not zone:
+        w["regions"] = []
+    a = oracle.Oracle(w, capacity=4 * n)
+    a.init()
+    b = oracle.Oracle(w, capacity=4 * n)
+    b.init()
+    return a, b
+
+
+def test_one_bin_is_the_global_step_with_point_masses():
+    # the inner edge of the disc (R = 1) falls inside a star radius of 1.02
+    a, b = _disc_pair(racc_star=1.02)
+    dt = 0.5 * a.timestep()
+    acc = 0
+    for _ in range(3):
+        ca, _ = a.step(dt)
+        cb, upd, _ = b.step_bins(dt, 0, init_bins=True)
+        assert ca.n_accreted == cb.n_accreted
+        acc += cb.n_accreted
+        assert list(ca.n_split) == list(cb.n_split) and list(ca.n_merge) == list(cb.n_merge)
+    assert acc > 0
+    for f in ("x", "vx", "rho", "h", "ax", "level", "id", "flags"):
+        assert np.array_equal(a[f], b[f]), f
+    assert a.sinks_state() == b.sinks_state()
+
+
+@pytest.mark.parametrize("zone", [False, True])
+def test_bins_with_point_masses_follow_fine_global_stepping(zone):
+    a, b = _disc_pair(zone=zone)
+    n0 = a.n
+    dtmin = 0.5 * a.timestep()
+    B = 3
+    _, upd, sat = b.step_bins(8 * dtmin, B, init_bins=True)
+    for _ in range(8):
+        a.step(dtmin)
+    assert sat == 0
+    # the Keplerian limits span several bins: far fewer updates than 8 per particle
+    assert len(np.unique(b["bin"])) >= 3 and upd < 4 * b.n
+    so, sb = np.argsort(a["id"]), np.argsort(b["id"])
+    if zone:
+        # splits inside the zone happen at other substeps (other ids and angles):
+        # compare the particles that were at level 0 before and after in both runs
+        ia, ib = a["id"][so], b["id"][sb]
+        keep_a = (ia < n0) & (a["level"][so] == 0)
+        keep_b = (ib < n0) & (b["level"][sb] == 0)
+        common = np.intersect1d(ia[keep_a], ib[keep_b])
+        assert len(common) > 0.8 * n0
+        so = so[np.searchsorted(ia, common)]
+        sb = sb[np.searchsorted(ib, common)]
+    assert np.array_equal(a["id"][so], b["id"][sb])
+    h = a["h"][so]
+    for f in ("x", "y", "z"):
+        d = np.abs(a[f][so] - b[f][sb])
+        assert np.all(d < 0.02 * h), f
+    # the point masses take every substep: their orbits follow the fine global steps
+    for ka, kb in zip(a.sinks_state(), b.sinks_state()):
+        assert np.allclose(ka["x"], kb["x"], rtol=0, atol=1e-7)
+        assert np.allclose(ka["v"], kb["v"], rtol=0, atol=1e-6)
+
+
+def test_bins_accretion_conserves_mass():
+    _, b = _disc_pair(racc_star=1.02)
+    s0 = b.stats()
+    m0 = s0.mass
+    total = 0
+    for first in (True, False):
+        cnt, _, _ = b.step_bins(8 * b.timestep(), 3, init_bins=first)
+        total += cnt.n_accreted
+    s1 = b.stats()
+    assert total > 0
+    # gas mass leaves only into the point masses (both sums count them)
+    assert s1.mass == pytest.approx(m0, rel=1e-14)
+    ks = b.sinks_state()
+    assert ks[0]["m"] > 1.0
