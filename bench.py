@@ -402,10 +402,13 @@ def side_measurements(args, torch, flush):
             out[name] = r
         except Exception as e:  # a side measurement never takes the headline down
             out[name] = {"error": f"{type(e).__name__}: {e}"}
-    try:
-        out["sod_time_step_bins"] = bins_measurement(torch)
-    except Exception as e:
-        out["sod_time_step_bins"] = {"error": f"{type(e).__name__}: {e}"}
+    for name, make, Bs, big, capf, mn in (
+            ("sod_time_step_bins", apr_synth.c2_sod, (2, 3), 4, 3.0, 0),
+            ("disc_planet_1e6_time_step_bins", apr_synth.disc_planet, (3, 5), 2, 1.6, 2048)):
+        try:
+            out[name] = bins_measurement(torch, make(), Bs, big, capf, mn)
+        except Exception as e:
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
     try:
         out["sound_wave_box_56832p_cylinder_zone"] = sound_wave_measurement(torch)
     except Exception as e:
@@ -417,46 +420,53 @@ def side_measurements(args, torch, flush):
     return out
 
 
-def bins_measurement(torch, big_steps=4):
-    """The full shock tube advanced over the same simulated time with one global
-    step (the smallest limit) and with individual time steps in bins (Sec. 2.5):
-    device time per unit of simulated time and force updates per particle and
-    unit time."""
-    import apr_synth
+def bins_measurement(torch, w, Bs, big_steps, cap_factor=3.0, max_neigh=0):
+    """A workload advanced with one global step (B = 0, the smallest limit taken
+    afresh every step) and with individual time steps in bins (Sec. 2.5; dt_max =
+    2^B times the smallest limit, taken afresh every step of dt_max), all runs
+    over the same simulated time: device time per unit of simulated time, force
+    updates per particle and unit time, and the device time by group."""
     from paper_2409_11470_gb300.binding import Simulation
-    w = apr_synth.c2_sod()
     n0 = len(w["p"]["x"])
-    res = {}
-    base = Simulation(w, capacity=3 * n0, precision="fp32")
-    base.init()
-    dt_glob = base.timestep()
-    base.close()
-    for B in (0, 2, 3):
-        g = Simulation(w, capacity=3 * n0, precision="fp32")
+    res = {"n_initial": n0}
+    t_end = None
+    for B in (0,) + tuple(b for b in Bs if b > 0):
+        g = Simulation(w, capacity=int(cap_factor * n0) + 1024, precision="fp32",
+                       max_neigh=max_neigh)
         g.init()
-        dt_max = dt_glob * (1 << B)
+        if t_end is None:
+            t_end = big_steps * g.timestep() * (1 << max(Bs))
+        g.profile(reset=True)
+        g.profile_enable(True)
         st = g.stream
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        upd, sat, first = 0, 0, True
-        for _ in range(big_steps):
-            _, u, sa, _ = g.step_bins(dt_max, B, init_bins=first)
+        t, upd, sat, steps, first, acc = 0.0, 0, 0, 0, True, 0
+        while t < t_end:
+            dt_max = g.timestep() * (1 << B)
+            c, u, sa, _ = g.step_bins(dt_max, B, init_bins=first)
             first = False
+            t += dt_max
             upd += u
             sat += sa
+            acc += c.n_accreted
+            steps += 1
         e1.record(st)
         st.synchronize()
         ms = e0.elapsed_time(e1)
-        t_sim = big_steps * dt_max
-        res[f"B{B}"] = {"dt_max": dt_max, "ms_per_unit_time": ms / t_sim,
-                        "updates_per_particle_per_unit_time": upd / g.n / t_sim,
-                        "saturated_updates": sat, "n_last": g.n}
+        prof = g.profile()
+        g.profile_enable(False)
+        res[f"B{B}"] = {"steps_of_dt_max": steps, "t_sim": t, "ms_per_unit_time": ms / t,
+                        "updates_per_particle_per_unit_time": upd / g.n / t,
+                        "saturated_updates": sat, "accreted": acc, "n_last": g.n,
+                        "breakdown_ms_per_unit_time": {
+                            k: round(prof[k]["ms"] / t, 2) for k in
+                            ("sort", "tree", "lists", "density", "force", "refine", "other")}}
         g.close()
     b0 = res["B0"]["ms_per_unit_time"]
-    for B in (2, 3):
-        res[f"B{B}"]["speedup_vs_global_step"] = b0 / res[f"B{B}"]["ms_per_unit_time"]
-    res["note"] = ("B0 is the global step at the smallest limit; every substep re-sorts all "
-                   "particles, so the force updates saved are only part of the step")
+    for B in Bs:
+        if B > 0:
+            res[f"B{B}"]["speedup_vs_global_step"] = b0 / res[f"B{B}"]["ms_per_unit_time"]
     return res
 
 

@@ -277,14 +277,18 @@ apr_status apr_merge_pairs(apr_ctx* ctx, int level, long long* pairs, long long 
  * second half kick, and their new bin: split or merged particles go to
  * max_bin; the others to the longest step dt_max / 2^b not above their limit
  * min(ccour h / v_sig, cforce sqrt(h / |a|)), moving to a longer step only
- * where its grid meets the current time.  init_bins != 0 first bins every
- * particle by its limit.  With max_bin = 0 this is apr_step(dt_max).
+ * where its grid meets the current time.  Point masses take every substep:
+ * half kick, drift, accretion and zones moved onto them after the drift; after
+ * the active particles' forces, their pull on the active particles only and
+ * their own accelerations from every live particle; then the closing half
+ * kick.  init_bins != 0 first bins every particle by its limit.  With
+ * max_bin = 0 this is apr_step(dt_max).
  *
  * Needs the bound bin array and forces from a previous pass (apr_init or a
- * step); point masses are not supported (APR_ERR_STATE).  counts: summed over
- * the substeps; updates: particle force updates done; saturated: updates whose
- * limit was below dt_min (kept in max_bin); stats: conservation sums at the
- * end.  Any of them may be NULL.
+ * step).  counts: summed over the substeps (n_accreted included); updates:
+ * particle force updates done; saturated: updates whose limit was below dt_min
+ * (kept in max_bin); stats: conservation sums at the end.  Any of them may be
+ * NULL.
  */
 apr_status apr_step_bins(apr_ctx* ctx, double dt_max, int max_bin, int init_bins,
                          apr_counts* counts, long long* updates, long long* saturated,

@@ -357,6 +357,12 @@ static apr_status run_force(apr_ctx* c, bool reuse_density_lists)
     return APR_OK;
 }
 
+static void kick_sinks(apr_ctx* c, double hdt)
+{
+    for (int j = 0; j < c->nsink; ++j)
+        for (int d = 0; d < 3; ++d) c->sinks[j].v[d] += hdt * c->sinks[j].a[d];
+}
+
 static void track_regions(apr_ctx* c)
 {
     for (int j = 0; j < c->nreg; ++j) {
@@ -735,8 +741,6 @@ apr_status apr_step_bins(apr_ctx* c, double dt_max, int B, int init_bins, apr_co
     if (!c) return APR_ERR_ARG;
     if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
     if (!c->p.bin) return fail(c, APR_ERR_STATE, "step_bins: no bin array bound");
-    if (c->nsink > 0)
-        return fail(c, APR_ERR_STATE, "step_bins: point masses are not supported with time-step bins");
     if (!(dt_max > 0.0) || B < 0 || B > 20) return fail(c, APR_ERR_ARG, "step_bins: bad dt_max or max_bin");
     if (!c->have_force) return fail(c, APR_ERR_STATE, "apr_init or a force pass first");
     Workspace& W = c->W;
@@ -748,10 +752,19 @@ apr_status apr_step_bins(apr_ctx* c, double dt_max, int B, int init_bins, apr_co
     if (init_bins) s = bins_init(c, dt_max, B);
     const long long nsub = 1LL << B;
     const double dtmin = dt_max / (double)nsub;
+    long long nacc = 0;
     for (long long k = 0; k < nsub && s == APR_OK; ++k) {
+        // point masses take every substep (bin B)
+        int ps = prof_begin(c, APR_PROF_OTHER);
         s = bins_kick(c, dt_max, B, k, 0);
+        kick_sinks(c, 0.5 * dtmin);
         if (s == APR_OK) s = drift(c, dtmin);
+        long long na = 0;
+        if (s == APR_OK) s = accrete(c, &na);
+        prof_end(c, ps);
         if (s != APR_OK) break;
+        nacc += na;
+        track_regions(c);
         // split/merge over the particles whose step ends now (Sec. 2.5)
         apr_counts cs;
         s = bins_mark_inactive(c, k, B, true);
@@ -767,12 +780,18 @@ apr_status apr_step_bins(apr_ctx* c, double dt_max, int B, int init_bins, apr_co
         total.n_dead += cs.n_dead;
         long long nq = 0;
         s = index_sort(c);
+        ps = prof_begin(c, APR_PROF_OTHER);
         if (s == APR_OK) s = bins_active_queue(c, k, B, &nq);
+        prof_end(c, ps);
         const bool all = nq > c->n / 4;
         if (s == APR_OK && nq > 0) s = run_density_active(c, nq, all);
         if (s == APR_OK && nq > 0) s = run_force_active(c, nq, all);
+        ps = prof_begin(c, APR_PROF_OTHER);
+        if (s == APR_OK) s = sink_gravity(c, B, k + 1);
         if (s == APR_OK) s = bins_kick(c, dt_max, B, k, 1);
+        kick_sinks(c, 0.5 * dtmin);
         if (s == APR_OK) s = bins_rebin(c, dt_max, B, k, nq);
+        prof_end(c, ps);
         upd += nq;
     }
     c->dt_valid = false;
@@ -787,6 +806,7 @@ apr_status apr_step_bins(apr_ctx* c, double dt_max, int B, int init_bins, apr_co
         s = compute_stats(c, stats);
         if (s != APR_OK) return s;
     }
+    total.n_accreted = nacc;
     if (counts) *counts = total;
     if (updates) *updates = upd;
     if (saturated) *saturated = sat;

@@ -297,7 +297,9 @@ apr_status split_merge_pass(apr_ctx* c, apr_counts* cnt);
 apr_status clear_changed(apr_ctx* c);
 apr_status merge_pairs_debug(apr_ctx* c, int level, long long* pairs, long long cap,
                              long long* npairs, long long* spare);
-apr_status sink_gravity(apr_ctx* c);
+// point-mass gravity; B >= 0: only the particles whose time-step bin ends at
+// substep boundary `sub` take the pull (the point masses feel every particle)
+apr_status sink_gravity(apr_ctx* c, int B = -1, long long sub = 0);
 apr_status accrete(apr_ctx* c, long long* naccreted);
 apr_status kick(apr_ctx* c, double hdt);
 apr_status drift(apr_ctx* c, double dt);

@@ -1696,8 +1696,11 @@ apr_status compute_timestep(apr_ctx* c, double* dt)
 
 // ------------------------------------------------------- point masses
 
+// every live particle pulls the point masses; with B >= 0 (time-step bins) only
+// the particles whose step ends at substep boundary `sub` take their pull
 __global__ void __launch_bounds__(256) k_sink_gravity(DevCfg dc, DevSinks sk, long long n,
-                                                      apr_particles p, double* partials)
+                                                      apr_particles p, int B, long long sub,
+                                                      double* partials)
 {
     double v[3 * APR_MAXSINK];
     for (int k = 0; k < 3 * APR_MAXSINK; ++k) v[k] = 0.0;
@@ -1705,6 +1708,7 @@ __global__ void __launch_bounds__(256) k_sink_gravity(DevCfg dc, DevSinks sk, lo
          i += (long long)gridDim.x * blockDim.x) {
         if (p.flags[i] & APR_FLAG_DEAD) continue;
         const double mi = dc.m0 * level_mass_d(p.level[i]);
+        const bool pulled = B < 0 || sub % ((1LL << B) >> p.bin[i]) == 0;
         double ax = 0.0, ay = 0.0, az = 0.0;
         for (int j = 0; j < sk.n; ++j) {
             double dx = p.x[i] - sk.x[j][0], dy = p.y[i] - sk.x[j][1], dz = p.z[i] - sk.x[j][2];
@@ -1718,17 +1722,20 @@ __global__ void __launch_bounds__(256) k_sink_gravity(DevCfg dc, DevSinks sk, lo
             v[3 * j + 1] += f * mi * dy;
             v[3 * j + 2] += f * mi * dz;
         }
-        p.ax[i] += ax;
-        p.ay[i] += ay;
-        p.az[i] += az;
+        if (pulled) {
+            p.ax[i] += ax;
+            p.ay[i] += ay;
+            p.az[i] += az;
+        }
     }
     block_reduce_store<3 * APR_MAXSINK>(v, partials);
 }
 
-apr_status sink_gravity(apr_ctx* c)
+apr_status sink_gravity(apr_ctx* c, int B, long long sub)
 {
     if (c->nsink == 0) return APR_OK;
-    APR_LAUNCH(c, k_sink_gravity, RED_BLOCKS, 256, c->dc, dev_sinks(c), c->n, c->p, c->W.red);
+    APR_LAUNCH(c, k_sink_gravity, RED_BLOCKS, 256, c->dc, dev_sinks(c), c->n, c->p, B, sub,
+               c->W.red);
     double r[3 * APR_MAXSINK];
     apr_status s = reduce_readback(c, 3 * c->nsink, 0u, r);
     if (s != APR_OK) return s;

@@ -1,7 +1,7 @@
 """Individual time steps in bins (Sec. 2.5) on the GPU: one bin is the global
-step bit for bit; with several bins the bins, the split/merge counts and the
-number of force updates equal the oracle's (FP64), and the fields agree
-within 1e-9; point masses are refused."""
+step bit for bit, with and without point masses; with several bins the bins,
+the split/merge/accretion counts and the number of force updates equal the
+oracle's (FP64), and the fields agree within 1e-8 relative."""
 import numpy as np
 import pytest
 
@@ -59,8 +59,7 @@ def test_bins_match_oracle(B):
         assert np.max(np.abs(a - b) / (np.abs(a) + floor)) < 1e-8, f
 
 
-def test_bins_fp32_close_to_fp64_and_refuse_point_masses():
-    import paper_2409_11470_gb300.binding as Bnd
+def test_bins_fp32_close_to_fp64():
     w = apr_synth.sod(8)
     cap = 4 * len(w["p"]["x"])
     g64 = sim(w, "fp64", capacity=cap)
@@ -74,8 +73,74 @@ def test_bins_fp32_close_to_fp64_and_refuse_point_masses():
     if g32.n == g64.n and u32 == u64:
         a, b = g64.get("x"), g32.get("x")
         assert np.abs(a - b).max() < 1e-4 * g64.get("h").min()
-    d = sim(apr_synth.disc_planet(2000), "fp32", capacity=8000)
-    d.init()
-    with pytest.raises(Bnd.AprError) as e:
-        d.step_bins(0.01, 2, init_bins=True)
-    assert e.value.status == 6
+
+
+def _disc(n=2000, racc_star=1.02, zone=True):
+    # the inner edge of the disc (R = 1) falls inside a star radius of 1.02
+    w = apr_synth.disc_planet(n)
+    w["sinks"][0]["racc"] = racc_star
+    if not zone:
+        w["regions"] = []
+    return w, 4 * n
+
+
+def test_one_bin_is_the_global_step_with_point_masses_on_the_gpu():
+    w, cap = _disc()
+    a = sim(w, "fp64", capacity=cap)
+    b = sim(w, "fp64", capacity=cap)
+    a.init()
+    b.init()
+    dt = 0.5 * a.timestep()
+    acc = 0
+    for _ in range(3):
+        _, _, ca = a.step(dt)
+        cb, upd, _, _ = b.step_bins(dt, 0, init_bins=True)
+        assert upd == b.n and ca.n_accreted == cb.n_accreted
+        assert list(ca.n_split) == list(cb.n_split) and list(ca.n_merge) == list(cb.n_merge)
+        acc += cb.n_accreted
+    assert acc > 0
+    for f in ("x", "vx", "rho", "h", "ax", "level", "id"):
+        assert np.array_equal(a.get(f), b.get(f)), f
+    assert a.sinks() == b.sinks()
+
+
+@pytest.mark.parametrize("zone", [False, True])
+def test_bins_with_point_masses_match_oracle(zone):
+    w, cap = _disc(zone=zone)
+    o = oracle.Oracle(w, capacity=cap)
+    g = sim(w, "fp64", capacity=cap)
+    o.init()
+    g.init()
+    B = 3
+    dt_max = 1.37 * 2 ** (B - 1) * o.timestep()
+    acc = 0
+    for first in (True, False):
+        co, uo, so = o.step_bins(dt_max, B, init_bins=first)
+        cg, ug, sg, _ = g.step_bins(dt_max, B, init_bins=first)
+        assert (ug, sg) == (uo, so)
+        assert list(cg.n_split) == list(co.n_split) and list(cg.n_merge) == list(co.n_merge)
+        assert cg.n_accreted == co.n_accreted
+        acc += cg.n_accreted
+        assert g.n == o.n
+        bo, bg = _by_id(o, g, "bin")
+        assert np.array_equal(bo, bg)
+    assert acc > 0 and len(np.unique(g.get("bin"))) >= 3
+    for f, floor in (("x", 0.01), ("vx", 0.05), ("rho", 0.0), ("ax", 0.01)):
+        a, b = _by_id(o, g, f)
+        assert np.max(np.abs(a - b) / (np.abs(a) + floor)) < 1e-8, f
+    for ko, kg in zip(o.sinks_state(), g.sinks()):
+        assert np.allclose(ko["x"], kg["x"], rtol=0, atol=1e-10)
+        assert np.allclose(ko["v"], kg["v"], rtol=0, atol=1e-10)
+        assert ko["m"] == pytest.approx(kg["m"], rel=1e-14)
+
+
+def test_bins_with_point_masses_conserve_mass_fp32():
+    w, cap = _disc()
+    g = sim(w, "fp32", capacity=cap)
+    g.init()
+    m0 = g.stats().mass
+    acc = 0
+    for first in (True, False):
+        c, _, _, st = g.step_bins(8 * g.timestep(), 3, init_bins=first)
+        acc += c.n_accreted
+    assert acc > 0 and st.mass == pytest.approx(m0, rel=1e-14)
