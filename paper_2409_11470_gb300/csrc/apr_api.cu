@@ -146,6 +146,8 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.retry_q[0] = (int*)take(4 * C);
     w.retry_q[1] = (int*)take(4 * C);
     w.active_q = (int*)take(4 * C);
+    w.relist_q = (int*)take(4 * C);
+    w.qmark = (unsigned int*)take(4 * C);
     // the list memory doubles as compaction scratch (20 x 8 bytes per particle)
     w.nbr = (unsigned int*)take((4 * K > 160 ? 4 * K : 160) * C);
     w.ncnt = (int*)take(4 * C);
@@ -294,11 +296,14 @@ static apr_status run_density(apr_ctx* c, long long* noconv_out)
             if (s != APR_OK) return s;
             s = density_pass(c, &unc, &noconv, nullptr, 0, q);
         } else {
-            // only the particles queued by the last pass: their lists by a
+            // only the particles queued by the last pass: their gather lists by a
             // per-particle tree walk at their new h, then their Newton-Raphson
-            s = index_refresh_h(c);
+            // (the symmetric lists the force needs are rebuilt after the last attempt)
+            s = relist_mark(c, c->W.retry_q[q], &c->W.status[ST_RETRY_N + q], attempt == 1);
+            if (s == APR_OK) s = index_refresh_sh(c);
             if (s != APR_OK) return s;
-            s = index_lists_queue(c, c->W.retry_q[q], &c->W.status[ST_RETRY_N + q], DENSITY_REACH);
+            s = index_lists_queue(c, c->W.retry_q[q], &c->W.status[ST_RETRY_N + q], DENSITY_REACH,
+                                  true, false);
             if (s != APR_OK) return s;
             const long long nq = unc;
             s = density_pass(c, &unc, &noconv, c->W.retry_q[q], nq, q ^ 1);
@@ -312,8 +317,14 @@ static apr_status run_density(apr_ctx* c, long long* noconv_out)
         c->prof_shrink += c->last_shrink;
         if (unc == 0) break;
     }
-    // after a retry, particles that kept their lists may miss a neighbour whose h grew
+    // after retries, the lists around the retried particles are rebuilt at the
+    // final h; with them every list holds its force pairs
     c->lists_fresh = attempts == 1;
+    if (attempts > 1 && unc == 0) {
+        s = relist_finish(c);
+        if (s != APR_OK) return s;
+        c->lists_fresh = true;
+    }
     if (noconv_out) *noconv_out = noconv + unc;
     if (unc && shrinks)
         return fail(c, APR_ERR_NEIGH_OVERFLOW,
@@ -688,9 +699,11 @@ static apr_status run_density_active(apr_ctx* c, long long nq, bool all)
                     : index_lists_queue(c, W.active_q, &W.status[ST_ACTIVE_N], DENSITY_REACH, true);
             if (s == APR_OK) s = density_pass(c, &unc, &noconv, W.active_q, nq, q);
         } else {
-            s = index_refresh_h(c);
+            s = relist_mark(c, W.retry_q[q], &W.status[ST_RETRY_N + q], attempt == 1);
+            if (s == APR_OK) s = index_refresh_sh(c);
             if (s == APR_OK)
-                s = index_lists_queue(c, W.retry_q[q], &W.status[ST_RETRY_N + q], DENSITY_REACH);
+                s = index_lists_queue(c, W.retry_q[q], &W.status[ST_RETRY_N + q], DENSITY_REACH,
+                                      true, false);
             const long long nr = unc;
             if (s == APR_OK) s = density_pass(c, &unc, &noconv, W.retry_q[q], nr, q ^ 1);
             q ^= 1;
@@ -704,6 +717,12 @@ static apr_status run_density_active(apr_ctx* c, long long nq, bool all)
         if (unc == 0) break;
     }
     c->lists_fresh = attempts == 1;
+    if (attempts > 1 && unc == 0) {
+        // as in run_density; lists rebuilt for inactive partners go unused
+        s = relist_finish(c);
+        if (s != APR_OK) return s;
+        c->lists_fresh = true;
+    }
     if (unc && shrinks)
         return fail(c, APR_ERR_NEIGH_OVERFLOW,
                     "neighbour lists cannot hold the particles within reach: raise max_neigh");

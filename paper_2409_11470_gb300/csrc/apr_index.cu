@@ -459,6 +459,15 @@ apr_status index_sort(apr_ctx* c)
     return s;
 }
 
+apr_status index_refresh_sh(apr_ctx* c)
+{
+    if (c->n <= 0) return APR_OK;
+    int ps = prof_begin(c, APR_PROF_TREE);
+    APR_LAUNCH(c, k_gather_h, nblocks(c->n, 256), 256, c->n, c->W.perm, c->p.h, c->W.sh);
+    prof_end(c, ps);
+    return cuda_check(c, cudaGetLastError(), "refresh sh");
+}
+
 apr_status index_refresh_h(apr_ctx* c)
 {
     if (c->n <= 0) return APR_OK;
@@ -999,23 +1008,20 @@ static void launch_lists(apr_ctx* c, const int* ncell_dev, int n, bool graceful)
 #undef APR_LISTS_CASE
 }
 
-// symmetric lists (graceful: an overflow marks the list, the density pass shrinks h)
-// of the queued particles only; the cells and candidate lists are not touched
-apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, double reach,
-                             bool graceful)
+// lists (graceful: an overflow marks the list, the density pass shrinks h) of the
+// queued particles only; the cells and candidate lists are not touched.  sym:
+// symmetric lists (r < 2 reach max(h_a, h_b), node h maxima must be current);
+// else gather lists (r < 2 reach h_a), which read no neighbour's h
+template <int SYM>
+static void launch_queue_lists(apr_ctx* c, const int* queue, const int* qlen_dev, int n,
+                               bool graceful)
 {
     Workspace& W = c->W;
-    const int n = (int)c->n;
-    if (n <= 0) return APR_OK;
-    int ps = prof_begin(c, APR_PROF_LISTS);
-    APR_LAUNCH(c, k_thresholds, nblocks(n, 256), 256, c->dc, n, reach, W.sh, W.sthr, W.sreach,
-               W.status);
-    if (n >= 2) APR_LAUNCH(c, k_node_thr, nblocks(n - 1, 256), 256, c->dc, n, reach, W.nhmax, W.nthr);
     const int mask = (c->dc.periodic[0] ? 1 : 0) | (c->dc.periodic[1] ? 2 : 0) |
                      (c->dc.periodic[2] ? 4 : 0);
 #define APR_QUEUE_CASE(M, X, Y, Z)                                                                   \
     case M:                                                                                          \
-        APR_LAUNCH(c, (k_lists_point<X, Y, Z, 1>), 152 * 4, 128, c->dc, qlen_dev, queue, n, c->cap,   \
+        APR_LAUNCH(c, (k_lists_point<X, Y, Z, SYM>), 152 * 4, 128, c->dc, qlen_dev, queue, n, c->cap, \
                    W.left, W.right, W.pk, W.sthr, W.nlo, W.nhi, W.nthr, W.nbr, W.ncnt, W.status,      \
                    graceful ? 1 : 0);                                                                \
         break;
@@ -1030,8 +1036,99 @@ apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, 
         APR_QUEUE_CASE(7, 1, 1, 1)
     }
 #undef APR_QUEUE_CASE
+}
+
+apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, double reach,
+                             bool graceful, bool sym)
+{
+    Workspace& W = c->W;
+    const int n = (int)c->n;
+    if (n <= 0) return APR_OK;
+    int ps = prof_begin(c, APR_PROF_LISTS);
+    APR_LAUNCH(c, k_thresholds, nblocks(n, 256), 256, c->dc, n, reach, W.sh, W.sthr, W.sreach,
+               W.status);
+    if (sym) {
+        if (n >= 2)
+            APR_LAUNCH(c, k_node_thr, nblocks(n - 1, 256), 256, c->dc, n, reach, W.nhmax, W.nthr);
+        launch_queue_lists<1>(c, queue, qlen_dev, n, graceful);
+    } else {
+        launch_queue_lists<0>(c, queue, qlen_dev, n, graceful);
+    }
     prof_end(c, ps);
     return cuda_check(c, cudaGetLastError(), "queue lists");
+}
+
+// ------------------------------------------------- lists after density retries
+//
+// A density pass keeps the symmetric lists of its first attempt for the force
+// when every h converged within their reach.  A particle b that needed retries
+// may end with h_b beyond that reach, so a partner y that converged at once can
+// lack b in its first list although r_yb < 2 h_b.  Such a y lies in b's last
+// list (built at b's last reach and y's final h): rebuilding, at the final h,
+// the lists of every retried particle and of every particle in their last lists
+// restores every force pair; all other lists already hold theirs.
+
+// mark the slots of a retry queue as retried (2) and queue each once
+__global__ void k_relist_mark_queue(const int* __restrict__ queue, const int* __restrict__ qlen,
+                                    int n, unsigned int* __restrict__ mark,
+                                    int* __restrict__ relist_q, int* __restrict__ relist_n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= min(*qlen, n)) return;
+    const int a = queue[i];
+    if (a < 0 || a >= n) return;
+    if (atomicExch(&mark[a], 2u) != 2u) relist_q[atomicAdd(relist_n, 1)] = a;
+}
+
+// warp per retried slot: every unmarked slot in its last list is marked (1) and queued
+__global__ void k_relist_mark_reach(int n, long long cap, int K, const int* __restrict__ nretried,
+                                    const unsigned int* __restrict__ nbr,
+                                    const int* __restrict__ ncnt, unsigned int* __restrict__ mark,
+                                    int* __restrict__ relist_q, int* __restrict__ relist_n)
+{
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int nr = min(*nretried, n);
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nr; w += nw) {
+        const int b = relist_q[w];
+        const int m = min(ncnt[b], K);
+        for (int k = lane; k < m; k += 32) {
+            const int y = (int)nbr[(long long)k * cap + b];
+            if (y >= 0 && y < n && atomicCAS(&mark[y], 0u, 1u) == 0u)
+                relist_q[atomicAdd(relist_n, 1)] = y;
+        }
+    }
+}
+
+apr_status relist_mark(apr_ctx* c, const int* queue, const int* qlen_dev, bool first)
+{
+    Workspace& W = c->W;
+    const int n = (int)c->n;
+    if (first) {
+        cudaMemsetAsync(W.qmark, 0, sizeof(unsigned) * (size_t)n, c->stream);
+        cudaMemsetAsync(&W.status[ST_RELIST_N], 0, sizeof(int), c->stream);
+    }
+    if (n > 0)
+        APR_LAUNCH(c, k_relist_mark_queue, nblocks(n, 256), 256, queue, qlen_dev, n, W.qmark,
+                   W.relist_q, &W.status[ST_RELIST_N]);
+    return cuda_check(c, cudaGetLastError(), "relist mark");
+}
+
+apr_status relist_finish(apr_ctx* c)
+{
+    Workspace& W = c->W;
+    const int n = (int)c->n;
+    if (n <= 0) return APR_OK;
+    int ps = prof_begin(c, APR_PROF_LISTS);
+    cudaMemcpyAsync(&W.status[ST_RETRIED_N], &W.status[ST_RELIST_N], sizeof(int),
+                    cudaMemcpyDeviceToDevice, c->stream);
+    APR_LAUNCH(c, k_relist_mark_reach, 152 * 8, 256, n, c->cap, c->dc.max_neigh,
+               &W.status[ST_RETRIED_N], W.nbr,
+               W.ncnt, W.qmark, W.relist_q, &W.status[ST_RELIST_N]);
+    prof_end(c, ps);
+    apr_status s = index_refresh_h(c);
+    if (s != APR_OK) return s;
+    return index_lists_queue(c, W.relist_q, &W.status[ST_RELIST_N], 1.0, false);
 }
 
 apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful)

@@ -41,6 +41,8 @@ enum {
     ST_RETRY_N = 13,         // density: lengths of the two retry queues (2 words)
     ST_ACTIVE_N = 15,        // time-step bins: length of the active queue
     ST_SATURATED = 40,       // time-step bins: updates whose limit was below dt_min
+    ST_RELIST_N = 41,        // density retries: particles whose lists are rebuilt after
+    ST_RETRIED_N = 42,       //   them, and how many of those were retried themselves
     ST_BINS = 16,            // merge: first slot of each level's candidates (10 words)
     ST_MERGES = 32,          // merge: merges per level (8 words)
     ST_NSTATUS = 16
@@ -152,6 +154,8 @@ struct Workspace {
     int* point_q;             // particles of cells whose candidate list overflowed
     int* retry_q[2];          // density: particles that need another attempt
     int* active_q;            // time-step bins: sorted slots of the active particles
+    int* relist_q;            // density retries: retried slots, then their list partners
+    unsigned int* qmark;      // per slot: 2 retried, 1 in a retried particle's list
     // neighbour lists, transposed: nbr[k * cap + sorted slot]
     unsigned int* nbr;
     int* ncnt;
@@ -279,12 +283,20 @@ apr_status radix_pass8(apr_ctx* c, const unsigned long long* kin, const unsigned
                        int* bin_starts, int nbins);
 apr_status index_sort(apr_ctx* c);           // quantise, Morton sort, gather, tree, node data
 apr_status index_refresh_h(apr_ctx* c);      // re-gather h and node hmax after a density pass
+// lists after density retries: relist_mark records a retry queue before its
+// attempt (the first call clears the marks); relist_finish rebuilds, at the final
+// h, the lists of every retried particle and of every particle in a retried
+// particle's last list, so that all lists hold every force pair
+apr_status relist_mark(apr_ctx* c, const int* queue, const int* qlen_dev, bool first);
+apr_status relist_finish(apr_ctx* c);
 // mode 0: gather lists (r < 2 reach h_a); mode 1: symmetric lists (r < 2 reach max(h_a, h_b)).
 // graceful: an overflowing list is marked (count -1) instead of flagged as an error.
 apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful = false);
-// symmetric lists of the queued particles only, by a per-particle tree walk
+// lists of the queued particles only, by a per-particle tree walk: symmetric
+// (sym) or gather lists
 apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, double reach,
-                             bool graceful = true);
+                             bool graceful = true, bool sym = true);
+apr_status index_refresh_sh(apr_ctx* c);     // re-gather h only (no node h maxima)
 
 // SPH passes (apr_sph.cu)
 apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv,

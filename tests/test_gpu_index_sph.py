@@ -118,6 +118,43 @@ def test_force_matches_oracle(make, precision):
     assert rel(g.get("vsig"), o["vsig"]).max() < 4 * t["rho"]
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("frac", [0.02, 0.3])
+def test_step_force_after_density_retries_matches_oracle(precision, frac):
+    """A subset is put at half its smoothing length before a step: those particles
+    take several density attempts (h grows at most 1.125x per attempt), after which
+    the step rebuilds only the lists of the retried particles and of their partners
+    before its force pass, which needs every pair within 2 max(h_a, h_b)."""
+    import torch
+    w = with_velocities(apr_synth.lattice_box(14, 0.2, seed=11, sphere_R=()), 0.3)
+    n = len(w["p"]["x"])
+    o = oracle.Oracle(w, capacity=2 * n)
+    g = sim(w, precision, capacity=2 * n)
+    o.init()
+    g.init()
+    assert g.n == o.n == n
+    pick = np.random.default_rng(4).random(n) < frac
+    o.a["h"][:n][pick] *= 0.5
+    h = g.get("h")
+    h[pick] *= 0.5
+    g.t["h"][:n] = torch.as_tensor(h, device=g.t["h"].device)
+    torch.cuda.synchronize()
+    dt = 0.1 * o.timestep()
+    o.step(dt)
+    g.profile(reset=True)
+    g.step(dt)
+    assert g.profile()["density_attempts"] >= 5
+    t = TOL[precision]
+    assert rel(g.get("h"), o["h"]).max() < t["rho"]
+    scale = o["pres"] / (o["rho"] * o["h"])
+    for f in ("ax", "ay", "az"):
+        err = np.abs(g.get(f) - o[f]) / (np.abs(o[f]) + scale)
+        assert err.max() < t["a"], (f, err.max())
+    escale = scale * np.sqrt(o["vx"] ** 2 + o["vy"] ** 2 + o["vz"] ** 2 + o["cs"] ** 2)
+    err = np.abs(g.get("dudt") - o["dudt"]) / (np.abs(o["dudt"]) + escale)
+    assert err.max() < t["a"]
+
+
 def test_fp32_total_momentum_conserved_on_gpu():
     w = with_velocities(apr_synth.c1_lattice(), 0.3)
     g = sim(w)
