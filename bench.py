@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--ncu-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off)")
+    ap.add_argument("--profile-workload", choices=["disc_planet"], default=None,
+                    help="profiling only: initialise this workload, take --warmup steps, "
+                         "then --steps steps inside cudaProfilerStart/Stop")
     return ap.parse_args()
 
 
@@ -651,9 +654,33 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_profile_workload(args):
+    """A side workload's steps bracketed for ``ncu --profile-from-start off``."""
+    import torch
+
+    import apr_synth
+    from paper_2409_11470_gb300.binding import Simulation
+    w = apr_synth.disc_planet()
+    n0 = len(w["p"]["x"])
+    sim = Simulation(w, capacity=int(1.6 * n0) + 1024, precision="fp32", max_neigh=2048)
+    sim.init()
+    for _ in range(args.warmup):
+        sim.step(0.0)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    for _ in range(args.steps):
+        sim.step(0.0)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    print(json.dumps({"profile_workload": w["name"], "steps": args.steps, "n": sim.n}), flush=True)
+    sim.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_workload:
+        run_profile_workload(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

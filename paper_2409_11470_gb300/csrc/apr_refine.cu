@@ -1562,11 +1562,64 @@ __global__ void __launch_bounds__(256) k_stats(DevCfg dc, long long n, apr_parti
 }
 
 // conservation sums (9) and the time-step limit (slot 9, a minimum) in one pass
+// smallest time-step limit min(ccour h / v_sig, cforce sqrt(h / |a|)) without a
+// division or square root per particle (FP64 is a slow pipe on this part): each
+// criterion keeps its best (numerator, denominator) pair, compared by cross
+// products (h / |a| compares as h^2 / a^2); the winner's quotient is formed once
+// per block with the same expressions as per particle
+struct DtMin {
+    double cn = 0.0, cd = 0.0;  // courant: h, v_sig (cd == 0: none yet)
+    double fn = 0.0, fd = 0.0;  // force: h^2, a^2 (fd == 0: none yet)
+    double fh = 0.0;            // the force winner's h
+    __device__ void add(double h, double vsig, double a2)
+    {
+        if (vsig > 0.0 && (cd == 0.0 || h * cd < cn * vsig)) {
+            cn = h;
+            cd = vsig;
+        }
+        const double h2 = h * h;
+        if (a2 > 0.0 && (fd == 0.0 || h2 * fd < fn * a2)) {
+            fn = h2;
+            fd = a2;
+            fh = h;
+        }
+    }
+    __device__ void merge(const DtMin& o)
+    {
+        if (o.cd > 0.0 && (cd == 0.0 || o.cn * cd < cn * o.cd)) {
+            cn = o.cn;
+            cd = o.cd;
+        }
+        if (o.fd > 0.0 && (fd == 0.0 || o.fn * fd < fn * o.fd)) {
+            fn = o.fn;
+            fd = o.fd;
+            fh = o.fh;
+        }
+    }
+    __device__ void shfl_down(int o)
+    {
+        DtMin t;
+        t.cn = __shfl_down_sync(0xffffffffu, cn, o);
+        t.cd = __shfl_down_sync(0xffffffffu, cd, o);
+        t.fn = __shfl_down_sync(0xffffffffu, fn, o);
+        t.fd = __shfl_down_sync(0xffffffffu, fd, o);
+        t.fh = __shfl_down_sync(0xffffffffu, fh, o);
+        merge(t);
+    }
+    __device__ double value(const DevCfg& dc) const
+    {
+        double dt = INFINITY;
+        if (cd > 0.0) dt = fmin(dt, dc.ccour * cn / cd);
+        if (fd > 0.0) dt = fmin(dt, dc.cforce * sqrt(fh / sqrt(fd)));
+        return dt;
+    }
+};
+
 __global__ void __launch_bounds__(256) k_stats_dt(DevCfg dc, long long n, apr_particles p,
                                                   double* partials)
 {
     double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    double dt = INFINITY;
+    DtMin best;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const unsigned char fl = p.flags[i];
@@ -1583,20 +1636,25 @@ __global__ void __launch_bounds__(256) k_stats_dt(DevCfg dc, long long n, apr_pa
         v[7] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
         if (dc.eos == APR_EOS_ADIABATIC) v[8] += m * p.u[i];
         if (fl & APR_FLAG_FIXED) continue;
-        double h = p.h[i];
-        if (p.vsig[i] > 0.0) dt = fmin(dt, dc.ccour * h / p.vsig[i]);
-        double a = sqrt(p.ax[i] * p.ax[i] + p.ay[i] * p.ay[i] + p.az[i] * p.az[i]);
-        if (a > 0.0) dt = fmin(dt, dc.cforce * sqrt(h / a));
+        best.add(p.h[i], p.vsig[i], p.ax[i] * p.ax[i] + p.ay[i] * p.ay[i] + p.az[i] * p.az[i]);
     }
     __shared__ double sm[10][8];
+    __shared__ DtMin sd[8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int k = 0; k < 9; ++k) {
         double x = v[k];
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
         if (lane == 0) sm[k][wid] = x;
     }
-    for (int o = 16; o > 0; o >>= 1) dt = fmin(dt, __shfl_down_sync(0xffffffffu, dt, o));
-    if (lane == 0) sm[9][wid] = dt;
+    for (int o = 16; o > 0; o >>= 1) best.shfl_down(o);
+    if (lane == 0) sd[wid] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        DtMin b = sd[0];
+        for (int w = 1; w < 8; ++w) b.merge(sd[w]);
+        sm[9][0] = b.value(dc);
+        for (int w = 1; w < 8; ++w) sm[9][w] = INFINITY;
+    }
     __syncthreads();
     if (threadIdx.x < 10) {
         double x = sm[threadIdx.x][0];
@@ -1629,7 +1687,9 @@ static void stats_from(const apr_ctx* c, const double* r, apr_stats* st)
 
 apr_status compute_stats_dt(apr_ctx* c, apr_stats* st, double* dt)
 {
-    const int nblk = (int)std::min<long long>(RED_BLOCKS, std::max<long long>(1, (c->n + 2047) / 2048));
+    // one particle per thread up to RED_BLOCKS x 256 particles: the FP64 work per
+    // particle is short, so parallel slack matters more than the partials count
+    const int nblk = (int)std::min<long long>(RED_BLOCKS, std::max<long long>(1, (c->n + 255) / 256));
     APR_LAUNCH(c, k_stats_dt, nblk, 256, c->dc, c->n, c->p, c->W.red);
     double r[10];
     apr_status s = reduce_readback_n(c, nblk, 10, 1u << 9, r);
@@ -1668,23 +1728,20 @@ apr_status compute_stats(apr_ctx* c, apr_stats* st)
 __global__ void __launch_bounds__(256) k_timestep(DevCfg dc, long long n, apr_particles p,
                                                   double* partials)
 {
-    double dt = INFINITY;
+    DtMin best;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         if (p.flags[i] & (APR_FLAG_DEAD | APR_FLAG_FIXED)) continue;
-        double h = p.h[i];
-        if (p.vsig[i] > 0.0) dt = fmin(dt, dc.ccour * h / p.vsig[i]);
-        double a = sqrt(p.ax[i] * p.ax[i] + p.ay[i] * p.ay[i] + p.az[i] * p.az[i]);
-        if (a > 0.0) dt = fmin(dt, dc.cforce * sqrt(h / a));
+        best.add(p.h[i], p.vsig[i], p.ax[i] * p.ax[i] + p.ay[i] * p.ay[i] + p.az[i] * p.az[i]);
     }
-    __shared__ double sm[8];
-    for (int o = 16; o > 0; o >>= 1) dt = fmin(dt, __shfl_down_sync(0xffffffffu, dt, o));
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = dt;
+    __shared__ DtMin sd[8];
+    for (int o = 16; o > 0; o >>= 1) best.shfl_down(o);
+    if ((threadIdx.x & 31) == 0) sd[threadIdx.x >> 5] = best;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double x = sm[0];
-        for (int w = 1; w < 8; ++w) x = fmin(x, sm[w]);
-        partials[blockIdx.x * 32] = x;
+        DtMin b = sd[0];
+        for (int w = 1; w < 8; ++w) b.merge(sd[w]);
+        partials[blockIdx.x * 32] = b.value(dc);
     }
 }
 
