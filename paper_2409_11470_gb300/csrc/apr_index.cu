@@ -711,6 +711,30 @@ __device__ __forceinline__ long long axis_gap(int v, int lo, int hi, int L)
     return g;
 }
 
+// the exact test of one staged candidate l against this lane's particle a
+template <int PX, int PY, int PZ, int SYM, bool WRAP>
+__device__ __forceinline__ bool exact_pair(const int4& q, unsigned long long tq, unsigned int rq,
+                                           const int4& pa, int a, bool own, unsigned long long ta,
+                                           unsigned int Ra, int Lx, int Ly, int Lz)
+{
+    int dx = pa.x - q.x, dy = pa.y - q.y, dz = pa.z - q.z;
+    if (WRAP) {
+        if (PX) dx = wrap_near(dx, Lx);
+        if (PY) dy = wrap_near(dy, Ly);
+        if (PZ) dz = wrap_near(dz, Lz);
+    }
+    unsigned int R = Ra;
+    if (SYM) R = (own && rq > R) ? rq : R;
+    if ((unsigned)abs(dx) >= R || (unsigned)abs(dy) >= R || (unsigned)abs(dz) >= R) return false;
+    if (q.w == a) return false;
+    const unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
+                                  (unsigned long long)((long long)dy * dy) +
+                                  (unsigned long long)((long long)dz * dz);
+    unsigned long long th = ta;
+    if (SYM) th = tq > th ? tq : th;
+    return r2 < th;
+}
+
 template <int PX, int PY, int PZ, int SYM, bool WRAP>
 __device__ __forceinline__ void list_batch(int nb, const int4* __restrict__ cq,
                                            const unsigned long long* __restrict__ ct,
@@ -721,33 +745,82 @@ __device__ __forceinline__ void list_batch(int nb, const int4* __restrict__ cq,
 {
     for (int l = 0; l < nb; ++l) {
         const int4 q = cq[l];
-        int dx = pa.x - q.x, dy = pa.y - q.y, dz = pa.z - q.z;
-        if (WRAP) {
-            if (PX) dx = wrap_near(dx, Lx);
-            if (PY) dy = wrap_near(dy, Ly);
-            if (PZ) dz = wrap_near(dz, Lz);
-        }
-        unsigned int R = Ra;
-        if (SYM) {
-            const unsigned int Rb = cr[l];
-            R = (own && Rb > R) ? Rb : R;
-        }
-        if ((unsigned)abs(dx) >= R || (unsigned)abs(dy) >= R || (unsigned)abs(dz) >= R) continue;
-        const int b = q.w;
-        if (b == a) continue;
-        const unsigned long long r2 = (unsigned long long)((long long)dx * dx) +
-                                      (unsigned long long)((long long)dy * dy) +
-                                      (unsigned long long)((long long)dz * dz);
-        unsigned long long th = ta;
-        if (SYM) {
-            const unsigned long long t = ct[l];
-            th = t > th ? t : th;
-        }
-        if (r2 < th) {
-            if (m < K) nbr[(long long)m * cap + a] = (unsigned)b;
+        if (exact_pair<PX, PY, PZ, SYM, WRAP>(q, SYM ? ct[l] : 0ULL, SYM ? cr[l] : 0u, pa, a, own, ta,
+                                             Ra, Lx, Ly, Lz)) {
+            if (m < K) nbr[(long long)m * cap + a] = (unsigned)q.w;
             ++m;
         }
     }
+}
+
+// The same decisions through a float filter: the candidate and the lane's
+// particle as float coordinates relative to the cell centre (tf: the float
+// threshold), r^2 in float; the exact test runs only inside the band
+// |r2f - th| <= FILTER_EPS th.  With V the largest relative coordinate of the
+// batch and the cell, u = 2^-24, |r2f - r^2| <= 6.93 u V r + 5 u r^2, which at
+// r^2 ~ th is at most 1.1e-4 th while V <= FILTER_SPAN sqrt(th); the caller
+// checks that bound (th >= the smallest own threshold) before it takes this path.
+constexpr float FILTER_EPS = 1.0f / 1024.0f;
+constexpr long long FILTER_SPAN = 256;
+
+template <int PX, int PY, int PZ, int SYM>
+__device__ __forceinline__ void list_batch_fast(int nb, const int4* __restrict__ cq,
+                                                const float4* __restrict__ cf,
+                                                const unsigned long long* __restrict__ ct,
+                                                const unsigned int* __restrict__ cr,
+                                                const int4& pa, float pfx, float pfy, float pfz,
+                                                float tfa, int a, bool own, unsigned long long ta,
+                                                unsigned int Ra, int Lx, int Ly, int Lz, int K,
+                                                long long cap, unsigned int* __restrict__ nbr,
+                                                int& m)
+{
+    const float lo_k = 1.0f - FILTER_EPS, hi_k = 1.0f + FILTER_EPS;
+    for (int l = 0; l < nb; ++l) {
+        const float4 f = cf[l];
+        const float dx = pfx - f.x, dy = pfy - f.y, dz = pfz - f.z;
+        const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        float thf = tfa;  // -1 on idle lanes: nothing passes
+        if (SYM && own) thf = fmaxf(thf, f.w);
+        bool hit;
+        if (r2f < thf * lo_k) {
+            hit = cq[l].w != a;
+        } else if (r2f <= thf * hi_k) {
+            hit = exact_pair<PX, PY, PZ, SYM, false>(cq[l], SYM ? ct[l] : 0ULL, SYM ? cr[l] : 0u, pa,
+                                                     a, own, ta, Ra, Lx, Ly, Lz);
+        } else {
+            continue;
+        }
+        if (hit) {
+            if (m < K) nbr[(long long)m * cap + a] = (unsigned)cq[l].w;
+            ++m;
+        }
+    }
+}
+
+// one staged batch: the float filter when the batch's relative coordinates stay
+// within FILTER_SPAN times the smallest own R (R - 1 <= sqrt(threshold)), else,
+// and for batches that need the per-pair minimum image, the exact tests
+template <int PX, int PY, int PZ, int SYM>
+__device__ __forceinline__ void flush_batch(int nb, bool wrapb, long long vlane, long long vown,
+                                            unsigned int rmin, const int4* cq, const float4* cf,
+                                            const unsigned long long* ct, const unsigned int* cr,
+                                            const int4& pa, float pfx, float pfy, float pfz,
+                                            float tfa, int a, bool own, unsigned long long ta,
+                                            unsigned int Ra, int Lx, int Ly, int Lz, int K,
+                                            long long cap, unsigned int* nbr, int& m)
+{
+    const long long v = max(vown, (long long)__reduce_max_sync(0xffffffffu, (unsigned)vlane));
+    const bool fast = !wrapb && rmin >= 2u && rmin != 0xffffffffu &&
+                      v <= FILTER_SPAN * (long long)(rmin - 1u);
+    if (wrapb)
+        list_batch<PX, PY, PZ, SYM, true>(nb, cq, ct, cr, pa, a, own, ta, Ra, Lx, Ly, Lz, K, cap, nbr,
+                                          m);
+    else if (fast)
+        list_batch_fast<PX, PY, PZ, SYM>(nb, cq, cf, ct, cr, pa, pfx, pfy, pfz, tfa, a, own, ta, Ra, Lx,
+                                         Ly, Lz, K, cap, nbr, m);
+    else
+        list_batch<PX, PY, PZ, SYM, false>(nb, cq, ct, cr, pa, a, own, ta, Ra, Lx, Ly, Lz, K, cap, nbr,
+                                           m);
 }
 
 template <int PX, int PY, int PZ, int SYM>
@@ -761,6 +834,7 @@ __global__ void __launch_bounds__(128)
             int* status, int graceful)
 {
     __shared__ int4 cq[4][LIST_BUF];
+    __shared__ float4 cf[4][LIST_BUF];
     __shared__ unsigned long long ct[4][LIST_BUF];
     __shared__ unsigned int cr[4][LIST_BUF];
     const unsigned FULL = 0xffffffffu;
@@ -799,6 +873,14 @@ __global__ void __launch_bounds__(128)
     const unsigned long long tcell = ((unsigned long long)th_hi << 32) | th_lo;
     const unsigned int rcell = __reduce_max_sync(FULL, Ra);
     const int cx = lox + ((hix - lox) >> 1), cy = loy + ((hiy - loy) >> 1), cz = loz + ((hiz - loz) >> 1);
+    // the float filter: this lane's coordinates relative to the centre, the float
+    // threshold (-1: idle lane), the smallest own R and the largest relative
+    // coordinate so far (own particles: at most half the box, rounded up)
+    const float pfx = (float)(pa.x - cx), pfy = (float)(pa.y - cy), pfz = (float)(pa.z - cz);
+    const float tfa = own ? (float)ta : -1.0f;
+    const unsigned int rmin = __reduce_min_sync(FULL, own ? Ra : 0xffffffffu);
+    const long long vown = max(max(hix - lox, hiy - loy), hiz - loz) / 2 + 1;
+    long long vlane = 0;  // largest |coordinate - centre| this lane staged into the batch
     int nb = 0;
     bool wrapb = false;
     for (int j = 0; j < nc; ++j) {
@@ -840,7 +922,10 @@ __global__ void __launch_bounds__(128)
         wrapb = wrapb || __any_sync(FULL, nw);
         if (keep) {
             const int pos = nb + __popc(km & lt);
+            const int rx = q.x - cx, ry = q.y - cy, rz = q.z - cz;
             cq[w][pos] = q;
+            cf[w][pos] = make_float4((float)rx, (float)ry, (float)rz, (float)tq);
+            vlane = max(vlane, (long long)max(max(abs(rx), abs(ry)), abs(rz)));
             if (SYM) {
                 ct[w][pos] = tq;
                 cr[w][pos] = rq;
@@ -849,25 +934,18 @@ __global__ void __launch_bounds__(128)
         nb += __popc(km);
         __syncwarp();
         if (nb >= 32) {
-            if (wrapb)
-                list_batch<PX, PY, PZ, SYM, true>(nb, cq[w], ct[w], cr[w], pa, a, own, ta, Ra, Lx, Ly,
-                                                  Lz, K, cap, nbr, m);
-            else
-                list_batch<PX, PY, PZ, SYM, false>(nb, cq[w], ct[w], cr[w], pa, a, own, ta, Ra, Lx, Ly,
-                                                   Lz, K, cap, nbr, m);
+            flush_batch<PX, PY, PZ, SYM>(nb, wrapb, vlane, vown, rmin, cq[w], cf[w], ct[w], cr[w], pa,
+                                         pfx, pfy, pfz, tfa, a, own, ta, Ra, Lx, Ly, Lz, K, cap, nbr,
+                                         m);
             nb = 0;
             wrapb = false;
+            vlane = 0;
             __syncwarp();
         }
     }
-    if (nb > 0) {
-        if (wrapb)
-            list_batch<PX, PY, PZ, SYM, true>(nb, cq[w], ct[w], cr[w], pa, a, own, ta, Ra, Lx, Ly, Lz,
-                                              K, cap, nbr, m);
-        else
-            list_batch<PX, PY, PZ, SYM, false>(nb, cq[w], ct[w], cr[w], pa, a, own, ta, Ra, Lx, Ly, Lz,
-                                               K, cap, nbr, m);
-    }
+    if (nb > 0)
+        flush_batch<PX, PY, PZ, SYM>(nb, wrapb, vlane, vown, rmin, cq[w], cf[w], ct[w], cr[w], pa, pfx,
+                                     pfy, pfz, tfa, a, own, ta, Ra, Lx, Ly, Lz, K, cap, nbr, m);
     if (own) {
         ncnt[a] = m > K ? -1 : m;
         if (m > K && !graceful) atomicOr(&status[ST_NEIGH_OVERFLOW], 1);
