@@ -196,17 +196,24 @@ def timed_steps(sim, torch, k, flush):
 
 
 def traffic_record(kernel):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
-    if not os.path.exists(path):
+    """DRAM bytes per launch from a committed ncu summary (profiles/<kernel>_traffic_*.md,
+    lines "key: value"), if it was taken on the current kernel source (else None)."""
+    import glob
+    paths = sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_traffic_*.md")))
+    if not paths:
         return None
-    with open(path) as f:
-        rec = json.load(f)
+    rec = {}
+    with open(paths[0]) as f:
+        for line in f:
+            k, sep, v = line.partition(":")
+            if sep and k.strip() in ("dram_bytes_per_launch", "n", "source_sha256_16"):
+                rec[k.strip()] = v.strip()
     src = os.path.join(ROOT, "paper_2409_11470_gb300", "csrc", "apr_sph.cu")
     with open(src, "rb") as f:
         digest = hashlib.sha256(f.read()).hexdigest()[:16]
-    return rec if rec.get("source_sha256_16") == digest else None
+    if rec.get("source_sha256_16") != digest or "dram_bytes_per_launch" not in rec or "n" not in rec:
+        return None
+    return {"dram_bytes_per_launch": float(rec["dram_bytes_per_launch"]), "n": float(rec["n"])}
 
 
 def run_ours(args):

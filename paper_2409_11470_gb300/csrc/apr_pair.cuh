@@ -3,6 +3,8 @@
 // particles (float on relative lattice coordinates, or double).
 #pragma once
 
+#include <cfloat>
+
 #include "apr_internal.cuh"
 
 namespace apr {
@@ -13,45 +15,42 @@ template <>
 struct Num<float> {
     __device__ static float sqrt_(float x) { return sqrtf(x); }
     __device__ static float rsqrt_(float x) { return rsqrtf(x); }
+    // sqrt of a pair's r^2 for a kernel argument: r^2 / sqrt(r^2) (0 stays 0)
+    __device__ static float root_(float x) { return x * rsqrtf(fmaxf(x, FLT_MIN)); }
+    __device__ static float max_(float a, float b) { return fmaxf(a, b); }
     __device__ static float mass(int level) { return level_mass_f(level); }
 };
 template <>
 struct Num<double> {
     __device__ static double sqrt_(double x) { return sqrt(x); }
     __device__ static double rsqrt_(double x) { return 1.0 / sqrt(x); }
+    __device__ static double root_(double x) { return sqrt(x); }
+    __device__ static double max_(double a, double b) { return fmax(a, b); }
     __device__ static double mass(int level) { return level_mass_d(level); }
 };
 
-// M4 cubic spline: f(q) and f'(q), zero for q >= 2
+// M4 cubic spline: f(q) and f'(q), zero for q >= 2.  Without branches: with
+// t = max(2 - q, 0) and s = max(1 - q, 0), f = t^3 / 4 - s^3 and
+// f' = 3 s^2 - 3 t^2 / 4 (for q < 1 this expands to 1 - 3q^2/2 + 3q^3/4 and
+// -3q + 9q^2/4; for 1 <= q < 2 s vanishes)
 template <typename R>
 __device__ __forceinline__ void m4(R q, R& f, R& df)
 {
-    if (q < R(1)) {
-        f = R(1) - R(1.5) * q * q + R(0.75) * q * q * q;
-        df = R(-3) * q + R(2.25) * q * q;
-    } else if (q < R(2)) {
-        R t = R(2) - q;
-        f = R(0.25) * t * t * t;
-        df = R(-0.75) * t * t;
-    } else {
-        f = R(0);
-        df = R(0);
-    }
+    const R t = Num<R>::max_(R(2) - q, R(0)), s = Num<R>::max_(R(1) - q, R(0));
+    const R t2 = t * t, s2 = s * s;
+    f = R(0.25) * t2 * t - s2 * s;
+    df = R(3) * s2 - R(0.75) * t2;
 }
 
-// Wendland C2 (support 2h): f(q) = (1 - q/2)^4 (2q + 1), f'(q) = -5 q (1 - q/2)^3
+// Wendland C2 (support 2h): f(q) = (1 - q/2)^4 (2q + 1), f'(q) = -5 q (1 - q/2)^3,
+// with t = max(1 - q/2, 0) so that both vanish for q >= 2
 template <typename R>
 __device__ __forceinline__ void wendland_c2(R q, R& f, R& df)
 {
-    if (q < R(2)) {
-        const R t = R(1) - R(0.5) * q;
-        const R t3 = t * t * t;
-        f = t3 * t * (R(2) * q + R(1));
-        df = R(-5) * q * t3;
-    } else {
-        f = R(0);
-        df = R(0);
-    }
+    const R t = Num<R>::max_(R(1) - R(0.5) * q, R(0));
+    const R t3 = t * t * t;
+    f = t3 * t * (R(2) * q + R(1));
+    df = R(-5) * q * t3;
 }
 
 // the configured kernel (the branch is uniform across the grid)
@@ -59,6 +58,16 @@ template <typename R>
 __device__ __forceinline__ void kern(int kernel, R q, R& f, R& df)
 {
     if (kernel == APR_KERNEL_WENDLAND_C2)
+        wendland_c2<R>(q, f, df);
+    else
+        m4<R>(q, f, df);
+}
+
+// the kernel fixed at compile time (KT: APR_KERNEL_M4 or APR_KERNEL_WENDLAND_C2)
+template <int KT, typename R>
+__device__ __forceinline__ void kern_t(R q, R& f, R& df)
+{
+    if constexpr (KT == APR_KERNEL_WENDLAND_C2)
         wendland_c2<R>(q, f, df);
     else
         m4<R>(q, f, df);

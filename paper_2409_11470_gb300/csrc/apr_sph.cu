@@ -33,14 +33,14 @@ __device__ __forceinline__ unsigned long long lattice_r2(const DevCfg& dc, const
 }
 
 // one density term mu_b f(q), mu_b q f'(q) for a pair inside 2h
-template <typename R>
-__device__ __forceinline__ void density_term(int kernel, R r2, R hinv, R r2max, int levb,
-                                             Acc<R>& S, Acc<R>& T, unsigned long long& npair)
+template <int KT, typename R>
+__device__ __forceinline__ void density_term(R r2, R hinv, R r2max, int levb, Acc<R>& S,
+                                             Acc<R>& T, unsigned int& npair)
 {
     if (r2 >= r2max) return;
-    const R q = Num<R>::sqrt_(r2) * hinv;
+    const R q = Num<R>::root_(r2) * hinv;
     R f, df;
-    kern<R>(kernel, q, f, df);
+    kern_t<KT, R>(q, f, df);
     const R mub = Num<R>::mass(levb);
     S.add(mub * f);
     T.add(mub * q * df);
@@ -76,7 +76,7 @@ constexpr int density_min_blocks() { return sizeof(R) == 4 ? 10 : 1; }
 template <typename R>
 constexpr int force_min_blocks() { return sizeof(R) == 4 ? 8 : 1; }
 
-template <typename R>
+template <typename R, int KT>
 __global__ void __launch_bounds__(128, density_min_blocks<R>())
     k_density(DevCfg dc, long long n, long long cap, double reach, const int4* __restrict__ pk,
               const double* __restrict__ sh, const unsigned long long* __restrict__ sthr,
@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(128, density_min_blocks<R>())
     R lo = R(0), hi = R(0);  // bracket of the root; hi == 0: none yet
     R D = R(0);              // sum mu_b (3 f + q f') at the last evaluated h
     bool conv = false, uncovered = false;
-    unsigned long long npair = 0, best = ~0ULL;
+    unsigned int npair = 0;
+    unsigned long long best = ~0ULL;
     for (int it = 0; it < dc.nr_maxit; ++it) {
         const R hinv = R(1) / h;
         const R r2max = R(4) * h * h;
@@ -135,10 +136,10 @@ __global__ void __launch_bounds__(128, density_min_blocks<R>())
                 best = q2 < best ? q2 : best;
                 best = q3 < best ? q3 : best;
             }
-            density_term<R>(dc.kernel, rel_r2<R>(dc, d0, sx, sy, sz, a, b0), hinv, r2max, p0.w, S, T, npair);
-            density_term<R>(dc.kernel, rel_r2<R>(dc, d1, sx, sy, sz, a, b1), hinv, r2max, p1.w, S, T, npair);
-            density_term<R>(dc.kernel, rel_r2<R>(dc, d2, sx, sy, sz, a, b2), hinv, r2max, p2.w, S, T, npair);
-            density_term<R>(dc.kernel, rel_r2<R>(dc, d3, sx, sy, sz, a, b3), hinv, r2max, p3.w, S, T, npair);
+            density_term<KT, R>(rel_r2<R>(dc, d0, sx, sy, sz, a, b0), hinv, r2max, p0.w, S, T, npair);
+            density_term<KT, R>(rel_r2<R>(dc, d1, sx, sy, sz, a, b1), hinv, r2max, p1.w, S, T, npair);
+            density_term<KT, R>(rel_r2<R>(dc, d2, sx, sy, sz, a, b2), hinv, r2max, p2.w, S, T, npair);
+            density_term<KT, R>(rel_r2<R>(dc, d3, sx, sy, sz, a, b3), hinv, r2max, p3.w, S, T, npair);
         }
         for (; k < m; ++k) {
             const int b = (int)col[(long long)k * cap];
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(128, density_min_blocks<R>())
             int d[3];
             const unsigned long long q = lattice_r2(dc, pa, pb, d);
             if (first_pass) best = q < best ? q : best;
-            density_term<R>(dc.kernel, rel_r2<R>(dc, d, sx, sy, sz, a, b), hinv, r2max, pb.w, S, T, npair);
+            density_term<KT, R>(rel_r2<R>(dc, d, sx, sy, sz, a, b), hinv, r2max, pb.w, S, T, npair);
         }
         const R g = (S.s + mua) - target;           // pi h^3 (rho_sum - rho_h) / m0
         const R dg = -(T.s) * hinv;                   // dg/dh >= 0
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(128, density_min_blocks<R>())
             break;
         }
     }
-    if (dc.prof) atomicAdd(&counters[APR_PROF_DENSITY], npair);
+    if (dc.prof) atomicAdd(&counters[APR_PROF_DENSITY], (unsigned long long)npair);
     const unsigned i = perm[a];
     const double hd = (double)h;
     h_out[i] = hd;
@@ -222,16 +223,20 @@ apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv, con
     const long long work = active ? nactive : n;
     if (work > 0) {
         const double reach = DENSITY_REACH;
-        if (c->cfg.precision == APR_PREC_FP64)
-            APR_LAUNCH(c, k_density<double>, nblocks(work, 128), 128,
-                c->dc, n, c->cap, reach, W.pk, W.sh, W.sthr, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
-                c->p.x, c->p.y, c->p.u, c->p.h, c->p.rho, c->p.omega, c->p.dnn, c->p.pres, c->p.cs,
-                W.status, W.counters, active, nactive, W.retry_q[out_q], &W.status[ST_RETRY_N + out_q]);
-        else
-            APR_LAUNCH(c, k_density<float>, nblocks(work, 128), 128,
-                c->dc, n, c->cap, reach, W.pk, W.sh, W.sthr, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
-                c->p.x, c->p.y, c->p.u, c->p.h, c->p.rho, c->p.omega, c->p.dnn, c->p.pres, c->p.cs,
-                W.status, W.counters, active, nactive, W.retry_q[out_q], &W.status[ST_RETRY_N + out_q]);
+        const bool c2 = c->cfg.kernel == APR_KERNEL_WENDLAND_C2;
+#define APR_DENSITY(R, KT)                                                                           \
+    APR_LAUNCH(c, (k_density<R, KT>), nblocks(work, 128), 128, c->dc, n, c->cap, reach, W.pk, W.sh,  \
+               W.sthr, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm, c->p.x, c->p.y, c->p.u, c->p.h,    \
+               c->p.rho, c->p.omega, c->p.dnn, c->p.pres, c->p.cs, W.status, W.counters, active,   \
+               nactive, W.retry_q[out_q], &W.status[ST_RETRY_N + out_q])
+        if (c->cfg.precision == APR_PREC_FP64) {
+            if (c2) APR_DENSITY(double, APR_KERNEL_WENDLAND_C2);
+            else APR_DENSITY(double, APR_KERNEL_M4);
+        } else {
+            if (c2) APR_DENSITY(float, APR_KERNEL_WENDLAND_C2);
+            else APR_DENSITY(float, APR_KERNEL_M4);
+        }
+#undef APR_DENSITY
     }
     prof_end(c, ps);
     // one read-back for the index status words and the density counters
@@ -339,12 +344,11 @@ struct ForceSelf {
 };
 
 // one pair of the force / energy sums (pairs outside both supports add nothing)
-template <typename R>
+template <int KT, typename R>
 __device__ __forceinline__ void force_pair(const DevCfg& dc, const ForceSelf<R>& A, const R d[3],
                                            const F4<R>& Ab, const F4<R>& Vb, const F4<R>& Bb,
                                            bool adiabatic, bool cond, Acc<R>& fx, Acc<R>& fy,
-                                           Acc<R>& fz, Acc<R>& du, R& vsig,
-                                           unsigned long long& npair)
+                                           Acc<R>& fz, Acc<R>& du, R& vsig, unsigned int& npair)
 {
     const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     const R rinv = Num<R>::rsqrt_(r2);
@@ -354,8 +358,8 @@ __device__ __forceinline__ void force_pair(const DevCfg& dc, const ForceSelf<R>&
     if (!(qa < R(2) || qb < R(2))) return;
     ++npair;
     R fa, dfa, fb, dfb;
-    kern<R>(dc.kernel, qa, fa, dfa);
-    kern<R>(dc.kernel, qb, fb, dfb);
+    kern_t<KT, R>(qa, fa, dfa);
+    kern_t<KT, R>(qb, fb, dfb);
     // float copies of the coefficients: no double-to-float conversion per pair
     R alpha, beta, alpha_u;
     if constexpr (sizeof(R) == 4) {
@@ -395,7 +399,7 @@ __device__ __forceinline__ void force_pair(const DevCfg& dc, const ForceSelf<R>&
     vsig = vs > vsig ? vs : vsig;
 }
 
-template <typename R>
+template <typename R, int KT>
 __global__ void __launch_bounds__(128, force_min_blocks<R>())
     k_force(DevCfg dc, long long n, long long cap, const int4* __restrict__ pk,
             const void* __restrict__ Abuf, const void* __restrict__ Vbuf,
@@ -430,7 +434,7 @@ __global__ void __launch_bounds__(128, force_min_blocks<R>())
     const bool cond = adiabatic && dc.alpha_u > 0.0;
     Acc<R> fx, fy, fz, du;
     R vsig = A.cs;
-    unsigned long long npair = 0;
+    unsigned int npair = 0;
     const int m = ncnt[a];
     const unsigned int* col = nbr + a;
     int k = 0;
@@ -442,8 +446,8 @@ __global__ void __launch_bounds__(128, force_min_blocks<R>())
         R d0[3], d1[3];
         Rel<R>::get(dc, pa, p0, sx, sy, sz, a, b0, d0);
         Rel<R>::get(dc, pa, p1, sx, sy, sz, a, b1, d1);
-        force_pair<R>(dc, A, d0, A0, V0, B0, adiabatic, cond, fx, fy, fz, du, vsig, npair);
-        force_pair<R>(dc, A, d1, A1, V1, B1, adiabatic, cond, fx, fy, fz, du, vsig, npair);
+        force_pair<KT, R>(dc, A, d0, A0, V0, B0, adiabatic, cond, fx, fy, fz, du, vsig, npair);
+        force_pair<KT, R>(dc, A, d1, A1, V1, B1, adiabatic, cond, fx, fy, fz, du, vsig, npair);
     }
     for (; k < m; ++k) {
         const int b = (int)col[(long long)k * cap];
@@ -451,9 +455,9 @@ __global__ void __launch_bounds__(128, force_min_blocks<R>())
         const F4<R> Ab = ld4<R>(Abuf, b), Vb = ld4<R>(Vbuf, b), Bb = ld4<R>(Bbuf, b);
         R d[3];
         Rel<R>::get(dc, pa, pb, sx, sy, sz, a, b, d);
-        force_pair<R>(dc, A, d, Ab, Vb, Bb, adiabatic, cond, fx, fy, fz, du, vsig, npair);
+        force_pair<KT, R>(dc, A, d, Ab, Vb, Bb, adiabatic, cond, fx, fy, fz, du, vsig, npair);
     }
-    if (dc.prof) atomicAdd(&counters[APR_PROF_FORCE], npair);
+    if (dc.prof) atomicAdd(&counters[APR_PROF_FORCE], (unsigned long long)npair);
     const double scale = dc.m0 / dc.knorm_inv;
     const unsigned i = perm[a];
     ax_out[i] = scale * ((double)fx.s - (double)fx.c);
@@ -470,14 +474,19 @@ apr_status force_pass(apr_ctx* c, const int* active, long long nactive)
     const long long work = active ? nactive : n;
     if (n <= 0 || work <= 0) return APR_OK;
     const int ps = prof_begin(c, APR_PROF_FORCE);
-    if (c->cfg.precision == APR_PREC_FP64)
-        APR_LAUNCH(c, k_force<double>, nblocks(work, 128), 128,
-            c->dc, n, c->cap, W.pk, W.dA, W.dV, W.dB, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
-            c->p.ax, c->p.ay, c->p.az, c->p.dudt, c->p.vsig, W.counters, active, nactive);
-    else
-        APR_LAUNCH(c, k_force<float>, nblocks(work, 128), 128,
-            c->dc, n, c->cap, W.pk, W.fA, W.fV, W.fB, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm,
-            c->p.ax, c->p.ay, c->p.az, c->p.dudt, c->p.vsig, W.counters, active, nactive);
+    const bool c2 = c->cfg.kernel == APR_KERNEL_WENDLAND_C2;
+#define APR_FORCE(R, KT, A, V, B)                                                                    \
+    APR_LAUNCH(c, (k_force<R, KT>), nblocks(work, 128), 128, c->dc, n, c->cap, W.pk, A, V, B, W.nbr, \
+               W.ncnt, W.sx, W.sy, W.sz, W.perm, c->p.ax, c->p.ay, c->p.az, c->p.dudt, c->p.vsig,   \
+               W.counters, active, nactive)
+    if (c->cfg.precision == APR_PREC_FP64) {
+        if (c2) APR_FORCE(double, APR_KERNEL_WENDLAND_C2, W.dA, W.dV, W.dB);
+        else APR_FORCE(double, APR_KERNEL_M4, W.dA, W.dV, W.dB);
+    } else {
+        if (c2) APR_FORCE(float, APR_KERNEL_WENDLAND_C2, W.fA, W.fV, W.fB);
+        else APR_FORCE(float, APR_KERNEL_M4, W.fA, W.fV, W.fB);
+    }
+#undef APR_FORCE
     prof_end(c, ps);
     return cuda_check(c, cudaGetLastError(), "force");
 }
