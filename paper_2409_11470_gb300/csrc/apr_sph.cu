@@ -72,7 +72,7 @@ __device__ __forceinline__ double rel_r2<double>(const DevCfg& dc, const int*, c
 // resident blocks per SM asked of the compiler: the float kernels are bound by
 // gather latency, so more warps in flight pay; the double kernels keep their registers
 template <typename R>
-constexpr int density_min_blocks() { return sizeof(R) == 4 ? 10 : 1; }
+constexpr int density_min_blocks() { return sizeof(R) == 4 ? 8 : 1; }
 template <typename R>
 constexpr int force_min_blocks() { return sizeof(R) == 4 ? 8 : 1; }
 
