@@ -324,6 +324,7 @@ static apr_status run_density(apr_ctx* c, long long* noconv_out)
         s = relist_finish(c);
         if (s != APR_OK) return s;
         c->lists_fresh = true;
+        c->lists_unchecked = true;
     }
     if (noconv_out) *noconv_out = noconv + unc;
     if (unc && shrinks)
@@ -340,6 +341,7 @@ static apr_status run_force(apr_ctx* c, bool reuse_density_lists)
 {
     apr_status s;
     if (!reuse_density_lists || !c->lists_fresh) {
+        c->lists_unchecked = true;
         if (reuse_density_lists) {
             // same positions as the density pass: the sort stands, only h moved
             s = index_refresh_h(c);
@@ -358,8 +360,12 @@ static apr_status run_force(apr_ctx* c, bool reuse_density_lists)
     if (s != APR_OK) return s;
     s = force_pass(c);
     if (s != APR_OK) return s;
-    s = check_overflow(c);
-    if (s != APR_OK) return s;
+    // lists the density pass built and checked need no second read of the status
+    if (c->lists_unchecked) {
+        s = check_overflow(c);
+        if (s != APR_OK) return s;
+        c->lists_unchecked = false;
+    }
     ps = prof_begin(c, APR_PROF_OTHER);
     s = sink_gravity(c);
     prof_end(c, ps);
@@ -722,6 +728,7 @@ static apr_status run_density_active(apr_ctx* c, long long nq, bool all)
         s = relist_finish(c);
         if (s != APR_OK) return s;
         c->lists_fresh = true;
+        c->lists_unchecked = true;
     }
     if (unc && shrinks)
         return fail(c, APR_ERR_NEIGH_OVERFLOW,
@@ -744,13 +751,15 @@ static apr_status run_force_active(apr_ctx* c, long long nq, bool all)
                 : index_lists_queue(c, W.active_q, &W.status[ST_ACTIVE_N], 1.0, false);
         if (s != APR_OK) return s;
         c->lists_fresh = true;
+        c->lists_unchecked = true;
     }
     int ps = prof_begin(c, APR_PROF_OTHER);
     s = gather_force_data(c);
     prof_end(c, ps);
     if (s != APR_OK) return s;
     s = force_pass(c, W.active_q, nq);
-    if (s != APR_OK) return s;
+    if (s != APR_OK || !c->lists_unchecked) return s;
+    c->lists_unchecked = false;
     return check_overflow(c);
 }
 

@@ -210,6 +210,7 @@ struct apr_ctx {
     int coop_blocks;          // co-resident blocks of the pairing-tree kernel (0: unknown)
     long long prof_attempts, prof_unc, prof_shrink;  // density-solve counters
     bool lists_fresh;         // the current lists hold every pair at the current h
+    bool lists_unchecked;     // lists were built after the last read of the status words
     int ncell;
     int last_shrink;
     bool tree_smem_set;       // dynamic shared memory opt-in of the pairing-tree kernel

@@ -1402,6 +1402,10 @@ apr_status split_merge_pass(apr_ctx* c, apr_counts* cnt)
     return s;
 }
 
+// host words for the merge counts and the pairing-tree status, apart from the
+// words the compaction count uses
+static int* merge_hbuf(apr_ctx* c) { return (int*)c->hbuf + 512; }
+
 static apr_status split_merge_body(apr_ctx* c, apr_counts* cnt)
 {
     Workspace& W = c->W;
@@ -1409,6 +1413,7 @@ static apr_status split_merge_body(apr_ctx* c, apr_counts* cnt)
     const DevRegions rg = dev_regions(c);
     memset(cnt, 0, sizeof(*cnt));
     apr_status s;
+    bool merged = false;
     if (c->n > 0) APR_LAUNCH(c, k_clear_changed, nblocks(c->n, 256), 256, c->n, c->p.flags);
     if (c->cfg.lmax >= 1 && c->n > 0) {
         const long long n = c->n;
@@ -1447,22 +1452,24 @@ static apr_status split_merge_body(apr_ctx* c, apr_counts* cnt)
             cudaMemsetAsync(&W.status[ST_MERGES], 0, sizeof(int) * APR_MAXLEV, st);
             APR_LAUNCH(c, k_merge_apply, nblocks(M, 256), 256, c->dc, rg, M, set, lo, hi, c->p,
                        &W.status[ST_MERGES]);
-            cudaMemcpyAsync(c->hbuf, &W.status[ST_MERGES], sizeof(int) * APR_MAXLEV,
+            // read back with the compaction count below (one host synchronisation)
+            cudaMemcpyAsync(merge_hbuf(c), &W.status[ST_MERGES], sizeof(int) * APR_MAXLEV,
                             cudaMemcpyDeviceToHost, st);
-            cudaMemcpyAsync((int*)c->hbuf + APR_MAXLEV, &W.status[ST_TREE_ERR], sizeof(int),
+            cudaMemcpyAsync(merge_hbuf(c) + APR_MAXLEV, &W.status[ST_TREE_ERR], sizeof(int),
                             cudaMemcpyDeviceToHost, st);
-            s = cuda_check(c, cudaStreamSynchronize(st), "merge");
-            if (s != APR_OK) return s;
-            if (((int*)c->hbuf)[APR_MAXLEV])
-                return fail(c, APR_ERR_STATE, "pairing tree: a grid barrier timed out or the "
-                                              "leaves were not reached");
-            for (int l = 1; l <= c->cfg.lmax; ++l) cnt->n_merge[l] = ((int*)c->hbuf)[l];
+            merged = true;
         }
     }
     long long removed = 0;
     if (c->n > 0) {
         s = compact(c, &removed);
         if (s != APR_OK) return s;
+    }
+    if (merged) {
+        if (merge_hbuf(c)[APR_MAXLEV])
+            return fail(c, APR_ERR_STATE, "pairing tree: a grid barrier timed out or the "
+                                          "leaves were not reached");
+        for (int l = 1; l <= c->cfg.lmax; ++l) cnt->n_merge[l] = merge_hbuf(c)[l];
     }
     cnt->n_dead = removed;
     c->step += 1;
