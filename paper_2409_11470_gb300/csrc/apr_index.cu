@@ -712,6 +712,15 @@ __device__ __forceinline__ long long axis_gap(int v, int lo, int hi, int L)
 }
 
 // the exact test of one staged candidate l against this lane's particle a
+// gap from v to [lo, hi]; P: v is the periodic image nearest the box centre, and
+// the gap less one (never more than the smallest gap over the images)
+template <int P>
+__device__ __forceinline__ long long box_gap(int v, int lo, int hi)
+{
+    const int g = max(0, max(lo - v, v - hi));
+    return P ? (long long)max(0, g - 1) : (long long)g;
+}
+
 template <int PX, int PY, int PZ, int SYM, bool WRAP>
 __device__ __forceinline__ bool exact_pair(const int4& q, unsigned long long tq, unsigned int rq,
                                            const int4& pa, int a, bool own, unsigned long long ta,
@@ -897,25 +906,22 @@ __global__ void __launch_bounds__(128)
             tq = thr[b];
             rq = rint[b];
             const unsigned long long T = (SYM && tq > tcell) ? tq : tcell;
-            const long long gx = axis_gap<PX>(q.x, lox, hix, Lx);
-            const long long gy = axis_gap<PY>(q.y, loy, hiy, Ly);
-            const long long gz = axis_gap<PZ>(q.z, loz, hiz, Lz);
+            // periodic axes: the image nearest the box centre is at most one unit
+            // farther from the box than the nearest image (the centre rounds
+            // down), so its gap less one keeps the culling conservative
+            if (PX) q.x = cx + wrap_near(q.x - cx, Lx);
+            if (PY) q.y = cy + wrap_near(q.y - cy, Ly);
+            if (PZ) q.z = cz + wrap_near(q.z - cz, Lz);
+            const long long gx = box_gap<PX>(q.x, lox, hix);
+            const long long gy = box_gap<PY>(q.y, loy, hiy);
+            const long long gz = box_gap<PZ>(q.z, loz, hiz);
             keep = (unsigned long long)(gx * gx) + (unsigned long long)(gy * gy) +
                        (unsigned long long)(gz * gz) < T;
             if (keep) {
                 const long long R2 = 2LL * (long long)((SYM && rq > rcell) ? rq : rcell);
-                if (PX) {
-                    q.x = cx + wrap_near(q.x - cx, Lx);
-                    nw = nw || (long long)(hix - lox) + R2 + 1 > Lx;
-                }
-                if (PY) {
-                    q.y = cy + wrap_near(q.y - cy, Ly);
-                    nw = nw || (long long)(hiy - loy) + R2 + 1 > Ly;
-                }
-                if (PZ) {
-                    q.z = cz + wrap_near(q.z - cz, Lz);
-                    nw = nw || (long long)(hiz - loz) + R2 + 1 > Lz;
-                }
+                if (PX) nw = nw || (long long)(hix - lox) + R2 + 1 > Lx;
+                if (PY) nw = nw || (long long)(hiy - loy) + R2 + 1 > Ly;
+                if (PZ) nw = nw || (long long)(hiz - loz) + R2 + 1 > Lz;
             }
         }
         const unsigned km = __ballot_sync(FULL, keep);
