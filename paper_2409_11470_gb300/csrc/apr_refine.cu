@@ -1694,9 +1694,9 @@ static void stats_from(const apr_ctx* c, const double* r, apr_stats* st)
 
 apr_status compute_stats_dt(apr_ctx* c, apr_stats* st, double* dt)
 {
-    // one particle per thread up to RED_BLOCKS x 256 particles: the FP64 work per
-    // particle is short, so parallel slack matters more than the partials count
-    const int nblk = (int)std::min<long long>(RED_BLOCKS, std::max<long long>(1, (c->n + 255) / 256));
+    // about four particles per thread: enough to hide the loads, few enough blocks
+    // that the per-block FP64 reduction (ten shuffled sums) stays small
+    const int nblk = (int)std::min<long long>(RED_BLOCKS, std::max<long long>(1, (c->n + 1023) / 1024));
     APR_LAUNCH(c, k_stats_dt, nblk, 256, c->dc, c->n, c->p, c->W.red);
     double r[10];
     apr_status s = reduce_readback_n(c, nblk, 10, 1u << 9, r);
