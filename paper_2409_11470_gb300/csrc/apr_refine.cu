@@ -1536,14 +1536,11 @@ static apr_status reduce_readback_n(apr_ctx* c, int nblk, int nv, unsigned int m
     return APR_OK;
 }
 
-static apr_status reduce_readback(apr_ctx* c, int nv, unsigned int min_mask, double* host)
+// blocks of a fixed-shape reduction over n particles: about four particles per
+// thread, so that the per-block shuffled sums stay a small share of the work
+static int red_grid(long long n)
 {
-    APR_LAUNCH(c, k_reduce_final, 1, 256, RED_BLOCKS, nv, c->W.red, c->W.redout, min_mask);
-    cudaMemcpyAsync(c->hbuf, c->W.redout, sizeof(double) * nv, cudaMemcpyDeviceToHost, c->stream);
-    apr_status s = cuda_check(c, cudaStreamSynchronize(c->stream), "reduce");
-    if (s != APR_OK) return s;
-    memcpy(host, c->hbuf, sizeof(double) * nv);
-    return APR_OK;
+    return (int)std::min<long long>(RED_BLOCKS, std::max<long long>(1, (n + 1023) / 1024));
 }
 
 __global__ void __launch_bounds__(256) k_stats(DevCfg dc, long long n, apr_particles p,
@@ -1696,7 +1693,7 @@ apr_status compute_stats_dt(apr_ctx* c, apr_stats* st, double* dt)
 {
     // about four particles per thread: enough to hide the loads, few enough blocks
     // that the per-block FP64 reduction (ten shuffled sums) stays small
-    const int nblk = (int)std::min<long long>(RED_BLOCKS, std::max<long long>(1, (c->n + 1023) / 1024));
+    const int nblk = red_grid(c->n);
     APR_LAUNCH(c, k_stats_dt, nblk, 256, c->dc, c->n, c->p, c->W.red);
     double r[10];
     apr_status s = reduce_readback_n(c, nblk, 10, 1u << 9, r);
@@ -1708,9 +1705,10 @@ apr_status compute_stats_dt(apr_ctx* c, apr_stats* st, double* dt)
 
 apr_status compute_stats(apr_ctx* c, apr_stats* st)
 {
-    APR_LAUNCH(c, k_stats, RED_BLOCKS, 256, c->dc, c->n, c->p, c->W.red);
+    const int nblk = red_grid(c->n);
+    APR_LAUNCH(c, k_stats, nblk, 256, c->dc, c->n, c->p, c->W.red);
     double r[9];
-    apr_status s = reduce_readback(c, 9, 0u, r);
+    apr_status s = reduce_readback_n(c, nblk, 9, 0u, r);
     if (s != APR_OK) return s;
     st->mass = r[0];
     for (int k = 0; k < 3; ++k) {
@@ -1754,31 +1752,51 @@ __global__ void __launch_bounds__(256) k_timestep(DevCfg dc, long long n, apr_pa
 
 apr_status compute_timestep(apr_ctx* c, double* dt)
 {
-    APR_LAUNCH(c, k_timestep, RED_BLOCKS, 256, c->dc, c->n, c->p, c->W.red);
-    return reduce_readback(c, 1, 1u, dt);
+    const int nblk = red_grid(c->n);
+    APR_LAUNCH(c, k_timestep, nblk, 256, c->dc, c->n, c->p, c->W.red);
+    return reduce_readback_n(c, nblk, 1, 1u, dt);
 }
 
 // ------------------------------------------------------- point masses
 
+// 1 / sqrt(x) in FP64 without a division or a square root (FP64 runs on a narrow
+// pipe on this part): the FP32 estimate refined by two Newton steps for
+// f(y) = 1/y^2 - x, y <- y (3 - x y^2) / 2, each of which squares the relative
+// error (2^-22 -> 2^-44 -> below FP64 rounding); outside the FP32 normal range the
+// plain quotient
+__device__ __forceinline__ double rsqrt_newton(double x)
+{
+    if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    y = y * (1.5 - 0.5 * x * y * y);
+    return y;
+}
+
 // every live particle pulls the point masses; with B >= 0 (time-step bins) only
-// the particles whose step ends at substep boundary `sub` take their pull
+// the particles whose step ends at substep boundary `sub` take their pull.
+// NS bounds the number of point masses (the per-block sums are 3 NS wide).
+template <int NS>
 __global__ void __launch_bounds__(256) k_sink_gravity(DevCfg dc, DevSinks sk, long long n,
                                                       apr_particles p, int B, long long sub,
                                                       double* partials)
 {
-    double v[3 * APR_MAXSINK];
-    for (int k = 0; k < 3 * APR_MAXSINK; ++k) v[k] = 0.0;
+    double v[3 * NS];
+    for (int k = 0; k < 3 * NS; ++k) v[k] = 0.0;
+    const int ns = sk.n < NS ? sk.n : NS;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         if (p.flags[i] & APR_FLAG_DEAD) continue;
         const double mi = dc.m0 * level_mass_d(p.level[i]);
         const bool pulled = B < 0 || sub % ((1LL << B) >> p.bin[i]) == 0;
         double ax = 0.0, ay = 0.0, az = 0.0;
-        for (int j = 0; j < sk.n; ++j) {
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            if (j >= ns) break;
             double dx = p.x[i] - sk.x[j][0], dy = p.y[i] - sk.x[j][1], dz = p.z[i] - sk.x[j][2];
             double r2 = dx * dx + dy * dy + dz * dz;
-            double r = sqrt(r2);
-            double f = dc.G / (r2 * r);
+            const double y = rsqrt_newton(r2);
+            double f = dc.G * (y * y * y);
             ax -= f * sk.m[j] * dx;
             ay -= f * sk.m[j] * dy;
             az -= f * sk.m[j] * dz;
@@ -1792,16 +1810,20 @@ __global__ void __launch_bounds__(256) k_sink_gravity(DevCfg dc, DevSinks sk, lo
             p.az[i] += az;
         }
     }
-    block_reduce_store<3 * APR_MAXSINK>(v, partials);
+    block_reduce_store<3 * NS>(v, partials);
 }
 
 apr_status sink_gravity(apr_ctx* c, int B, long long sub)
 {
     if (c->nsink == 0) return APR_OK;
-    APR_LAUNCH(c, k_sink_gravity, RED_BLOCKS, 256, c->dc, dev_sinks(c), c->n, c->p, B, sub,
-               c->W.red);
+    const int nblk = red_grid(c->n);
+    if (c->nsink <= 2)
+        APR_LAUNCH(c, k_sink_gravity<2>, nblk, 256, c->dc, dev_sinks(c), c->n, c->p, B, sub, c->W.red);
+    else
+        APR_LAUNCH(c, k_sink_gravity<APR_MAXSINK>, nblk, 256, c->dc, dev_sinks(c), c->n, c->p, B, sub,
+                   c->W.red);
     double r[3 * APR_MAXSINK];
-    apr_status s = reduce_readback(c, 3 * c->nsink, 0u, r);
+    apr_status s = reduce_readback_n(c, nblk, 3 * c->nsink, 0u, r);
     if (s != APR_OK) return s;
     for (int j = 0; j < c->nsink; ++j) {
         apr_sink& k = c->sinks[j];
@@ -1850,7 +1872,12 @@ __global__ void __launch_bounds__(256) k_accrete(DevCfg dc, DevSinks sk, long lo
         }
     }
     if (cnt) atomicAdd(count, cnt);
-    // 7 per sink, at most 4 sinks per reduction slot set of 32
+    // 7 per sink, at most 4 sinks per reduction slot set of 32; a block that absorbed
+    // nothing stores zeros without the shuffled sums (the usual case)
+    if (!__syncthreads_or(cnt)) {
+        if (threadIdx.x < 28) partials[blockIdx.x * 32 + threadIdx.x] = 0.0;
+        return;
+    }
     block_reduce_store<28>(*reinterpret_cast<double(*)[28]>(v), partials);
 }
 
@@ -1860,16 +1887,20 @@ apr_status accrete(apr_ctx* c, long long* naccreted)
     if (c->nsink == 0 || c->n == 0) return APR_OK;
     if (c->nsink > 4) return fail(c, APR_ERR_ARG, "accretion supports at most 4 sinks");
     cudaMemsetAsync(&c->W.status[ST_COUNT_B], 0, sizeof(int), c->stream);
-    APR_LAUNCH(c, k_accrete, RED_BLOCKS, 256, c->dc, dev_sinks(c), c->n, c->p, c->W.red,
-                                                 &c->W.status[ST_COUNT_B]);
-    double r[28];
-    apr_status s = reduce_readback(c, 7 * c->nsink, 0u, r);
-    if (s != APR_OK) return s;
-    cudaMemcpyAsync(c->hbuf, &c->W.status[ST_COUNT_B], sizeof(int), cudaMemcpyDeviceToHost,
+    const int nblk = red_grid(c->n);
+    APR_LAUNCH(c, k_accrete, nblk, 256, c->dc, dev_sinks(c), c->n, c->p, c->W.red,
+               &c->W.status[ST_COUNT_B]);
+    // the sums and the count in one read-back
+    APR_LAUNCH(c, k_reduce_final, 1, 256, nblk, 7 * c->nsink, c->W.red, c->W.redout, 0u);
+    cudaMemcpyAsync(c->hbuf, c->W.redout, sizeof(double) * 7 * c->nsink, cudaMemcpyDeviceToHost,
                     c->stream);
-    s = cuda_check(c, cudaStreamSynchronize(c->stream), "accrete");
+    cudaMemcpyAsync((double*)c->hbuf + 28, &c->W.status[ST_COUNT_B], sizeof(int),
+                    cudaMemcpyDeviceToHost, c->stream);
+    apr_status s = cuda_check(c, cudaStreamSynchronize(c->stream), "accrete");
     if (s != APR_OK) return s;
-    *naccreted = ((int*)c->hbuf)[0];
+    double r[28];
+    memcpy(r, c->hbuf, sizeof(double) * 7 * c->nsink);
+    *naccreted = *(const int*)((const double*)c->hbuf + 28);
     for (int j = 0; j < c->nsink; ++j) {
         double M = r[7 * j];
         if (!(M > 0.0)) continue;
