@@ -148,6 +148,7 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.active_q = (int*)take(4 * C);
     w.relist_q = (int*)take(4 * C);
     w.qmark = (unsigned int*)take(4 * C);
+    w.sthr0 = (unsigned long long*)take(8 * C);
     // the list memory doubles as compaction scratch (20 x 8 bytes per particle)
     w.nbr = (unsigned int*)take((4 * K > 160 ? 4 * K : 160) * C);
     w.ncnt = (int*)take(4 * C);

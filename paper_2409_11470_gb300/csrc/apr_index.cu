@@ -1148,9 +1148,9 @@ apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, 
 // when every h converged within their reach.  A particle b that needed retries
 // may end with h_b beyond that reach, so a partner y that converged at once can
 // lack b in its first list although r_yb < 2 h_b.  Such a y lies in b's last
-// list (built at b's last reach and y's final h): rebuilding, at the final h,
-// the lists of every retried particle and of every particle in their last lists
-// restores every force pair; all other lists already hold theirs.
+// list (built at b's last reach): rebuilding, at the final h, the lists of every
+// retried particle and of every partner in their last lists that lacks a pair the
+// force needs restores every force pair; all other lists already hold theirs.
 
 // mark the slots of a retry queue as retried (2) and queue each once
 __global__ void k_relist_mark_queue(const int* __restrict__ queue, const int* __restrict__ qlen,
@@ -1164,21 +1164,42 @@ __global__ void k_relist_mark_queue(const int* __restrict__ queue, const int* __
     if (atomicExch(&mark[a], 2u) != 2u) relist_q[atomicAdd(relist_n, 1)] = a;
 }
 
-// warp per retried slot: every unmarked slot in its last list is marked (1) and queued
-__global__ void k_relist_mark_reach(int n, long long cap, int K, const int* __restrict__ nretried,
+// warp per retried slot b: a slot y in b's last list is marked (1) and queued when
+// the force needs the pair because of b's final h (lattice r^2 below the threshold
+// at h_b) and y's first list lacks b (r^2 at or above the larger of the two
+// first-build thresholds, which decided that list's membership)
+__global__ void k_relist_mark_reach(DevCfg dc, int n, long long cap, int K,
+                                    const int* __restrict__ nretried,
                                     const unsigned int* __restrict__ nbr,
-                                    const int* __restrict__ ncnt, unsigned int* __restrict__ mark,
-                                    int* __restrict__ relist_q, int* __restrict__ relist_n)
+                                    const int* __restrict__ ncnt, const int4* __restrict__ pk,
+                                    const unsigned int* __restrict__ perm,
+                                    const double* __restrict__ h,
+                                    const unsigned long long* __restrict__ sthr0,
+                                    unsigned int* __restrict__ mark, int* __restrict__ relist_q,
+                                    int* __restrict__ relist_n)
 {
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int nr = min(*nretried, n);
+    const int Lx = (int)dc.Lint[0], Ly = (int)dc.Lint[1], Lz = (int)dc.Lint[2];
     for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nr; w += nw) {
         const int b = relist_q[w];
         const int m = min(ncnt[b], K);
+        const int4 pb = pk[b];
+        const unsigned long long tf = neighbour_threshold(h[perm[b]], dc.delta);
+        const unsigned long long tb0 = sthr0[b];
         for (int k = lane; k < m; k += 32) {
             const int y = (int)nbr[(long long)k * cap + b];
-            if (y >= 0 && y < n && atomicCAS(&mark[y], 0u, 1u) == 0u)
+            if (y < 0 || y >= n) continue;
+            const int4 py = pk[y];
+            const long long dx = min_image32(pb.x - py.x, dc.periodic[0], Lx);
+            const long long dy = min_image32(pb.y - py.y, dc.periodic[1], Ly);
+            const long long dz = min_image32(pb.z - py.z, dc.periodic[2], Lz);
+            const unsigned long long r2 = (unsigned long long)(dx * dx) +
+                                          (unsigned long long)(dy * dy) +
+                                          (unsigned long long)(dz * dz);
+            const unsigned long long t0 = sthr0[y] > tb0 ? sthr0[y] : tb0;
+            if (r2 < tf && r2 >= t0 && atomicCAS(&mark[y], 0u, 1u) == 0u)
                 relist_q[atomicAdd(relist_n, 1)] = y;
         }
     }
@@ -1191,6 +1212,9 @@ apr_status relist_mark(apr_ctx* c, const int* queue, const int* qlen_dev, bool f
     if (first) {
         cudaMemsetAsync(W.qmark, 0, sizeof(unsigned) * (size_t)n, c->stream);
         cudaMemsetAsync(&W.status[ST_RELIST_N], 0, sizeof(int), c->stream);
+        // the first build's thresholds, before the retries recompute them
+        cudaMemcpyAsync(W.sthr0, W.sthr, sizeof(unsigned long long) * (size_t)n,
+                        cudaMemcpyDeviceToDevice, c->stream);
     }
     if (n > 0)
         APR_LAUNCH(c, k_relist_mark_queue, nblocks(n, 256), 256, queue, qlen_dev, n, W.qmark,
@@ -1206,9 +1230,9 @@ apr_status relist_finish(apr_ctx* c)
     int ps = prof_begin(c, APR_PROF_LISTS);
     cudaMemcpyAsync(&W.status[ST_RETRIED_N], &W.status[ST_RELIST_N], sizeof(int),
                     cudaMemcpyDeviceToDevice, c->stream);
-    APR_LAUNCH(c, k_relist_mark_reach, 152 * 8, 256, n, c->cap, c->dc.max_neigh,
-               &W.status[ST_RETRIED_N], W.nbr,
-               W.ncnt, W.qmark, W.relist_q, &W.status[ST_RELIST_N]);
+    APR_LAUNCH(c, k_relist_mark_reach, 152 * 8, 256, c->dc, n, c->cap, c->dc.max_neigh,
+               &W.status[ST_RETRIED_N], W.nbr, W.ncnt, W.pk, W.perm, c->p.h, W.sthr0, W.qmark,
+               W.relist_q, &W.status[ST_RELIST_N]);
     prof_end(c, ps);
     apr_status s = index_refresh_h(c);
     if (s != APR_OK) return s;

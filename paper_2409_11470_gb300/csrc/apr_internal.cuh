@@ -156,6 +156,7 @@ struct Workspace {
     int* active_q;            // time-step bins: sorted slots of the active particles
     int* relist_q;            // density retries: retried slots, then their list partners
     unsigned int* qmark;      // per slot: 2 retried, 1 in a retried particle's list
+    unsigned long long* sthr0; // density retries: the first list build's thresholds
     // neighbour lists, transposed: nbr[k * cap + sorted slot]
     unsigned int* nbr;
     int* ncnt;
