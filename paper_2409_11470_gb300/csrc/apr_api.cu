@@ -108,6 +108,8 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.val[0] = (unsigned int*)take(4 * C);
     w.val[1] = (unsigned int*)take(4 * C);
     w.hist = (unsigned int*)take(4 * 256 * ntiles * 2);
+    w.sort_hist = (unsigned int*)take(4 * 256 * 6);
+    w.sort_tile = (unsigned int*)take(4 * 256 * std::min<size_t>(ntiles, SORT_SWEEP_MAX_TILES) * 6);
     w.scan_tmp = (unsigned int*)take(4 * (scan_n / 256 + 8192));
     w.pk = (int4*)take(16 * C);
     w.sthr = (unsigned long long*)take(8 * C);
@@ -274,8 +276,13 @@ static apr_status read_status(apr_ctx* c, int first, int count, int* out)
 static apr_status check_overflow(apr_ctx* c)
 {
     int st[8];
+    // the Morton sort's status word rides along in the same read-back
+    cudaMemcpyAsync((int*)c->hbuf + 16, &c->W.status[ST_SORT_ERR], sizeof(int),
+                    cudaMemcpyDeviceToHost, c->stream);
     apr_status s = read_status(c, 0, 8, st);
     if (s != APR_OK) return s;
+    if (((int*)c->hbuf)[16])
+        return fail(c, APR_ERR_STATE, "Morton sort: a tile gave up waiting for its predecessors");
     if (st[ST_TREE_BAD]) return fail(c, APR_ERR_STATE, "internal error: malformed radix tree");
     if (st[0]) return fail(c, APR_ERR_NEIGH_OVERFLOW, "a neighbour list exceeded max_neigh");
     if (st[1]) return fail(c, APR_ERR_NEIGH_OVERFLOW, "a candidate-cell list overflowed");

@@ -267,18 +267,192 @@ apr_status radix_pass8(apr_ctx* c, const unsigned long long* kin, const unsigned
     return cuda_check(c, cudaGetLastError(), "radix pass");
 }
 
+// ---- Morton sort in one sweep per digit
+//
+// The six 8-bit digit histograms are counted in one read of the keys and scanned
+// once; each pass then needs a single launch: a tile takes a ticket (so that
+// every lower ticket belongs to a block that has already started), counts its
+// digits, publishes them, and adds up the counts of the tiles before it by
+// looking back over their published words (count with a flag: aggregate only, or
+// inclusive prefix), stopping at the first inclusive one.  Its items then go to
+// digit offset + tiles before + rank in the tile, the same stable order as a
+// histogram-scan-scatter pass.  Waits are bounded; a wait that gives up sets
+// ST_SORT_ERR, and no write leaves [0, n).
+
+static_assert(3 * KEY_BITS == 48, "the single-sweep sort takes six 8-bit digits");
+constexpr unsigned SORT_FLAG_A = 1u << 30;   // the tile's own counts
+constexpr unsigned SORT_FLAG_P = 2u << 30;   // counts of this tile and all before it
+constexpr unsigned SORT_COUNT = (1u << 30) - 1u;
+constexpr unsigned SORT_SPIN_LIMIT = 1u << 22;
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(256)
+    k_sort_hist6(const unsigned long long* __restrict__ keys, long long n,
+                 unsigned int* __restrict__ hist6)
+{
+    __shared__ unsigned int h[6][256];
+    for (int k = 0; k < 6; ++k) h[k][threadIdx.x] = 0;
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long key = keys[i];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) atomicAdd(&h[k][(unsigned)(key >> (8 * k)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int k = 0; k < 6; ++k) {
+        const unsigned v = h[k][threadIdx.x];
+        if (v) atomicAdd(&hist6[k * 256 + threadIdx.x], v);
+    }
+}
+
+// counts -> exclusive offsets, one pass per warp-group of the block
+__global__ void __launch_bounds__(256) k_sort_scan6(unsigned int* __restrict__ hist6)
+{
+    __shared__ unsigned wsum[8];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    for (int k = 0; k < 6; ++k) {
+        const unsigned v = hist6[k * 256 + t];
+        unsigned incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        unsigned ex = incl - v;
+        for (int w = 0; w < wid; ++w) ex += wsum[w];
+        hist6[k * 256 + t] = ex;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    k_sort_pass(const unsigned long long* __restrict__ kin, const unsigned int* __restrict__ vin,
+                unsigned long long* __restrict__ kout, unsigned int* __restrict__ vout, long long n,
+                int shift, const unsigned int* __restrict__ goff, unsigned int* tiles,
+                unsigned int* ticket, int* err)
+{
+    __shared__ unsigned s_tile;
+    __shared__ unsigned h[256], excl[256], run[256];
+    __shared__ unsigned wcnt[8][256];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    if (t == 0) s_tile = atomicAdd(ticket, 1u);
+    h[t] = 0;
+    run[t] = 0;
+    for (int w = 0; w < 8; ++w) wcnt[w][t] = 0;
+    __syncthreads();
+    const unsigned tile = s_tile;
+    const long long base = (long long)tile * RADIX_TILE;
+    constexpr int R = RADIX_TILE / 256;
+    unsigned long long k[R];
+    unsigned int v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const long long i = base + r * 256 + t;
+        k[r] = i < n ? kin[i] : 0ULL;
+        v[r] = i < n ? vin[i] : 0u;
+        if (i < n) atomicAdd(&h[(unsigned)(k[r] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    // publish, then the counts of every tile before this one
+    unsigned* mine = tiles + (size_t)tile * 256;
+    const unsigned own = h[t];
+    if (tile == 0) {
+        st_release_u32(&mine[t], SORT_FLAG_P | own);
+        excl[t] = 0;
+    } else {
+        st_release_u32(&mine[t], SORT_FLAG_A | own);
+        unsigned acc = 0;
+        for (long long j = (long long)tile - 1; j >= 0; --j) {
+            const unsigned* w = tiles + (size_t)j * 256 + t;
+            unsigned word = ld_acquire_u32(w);
+            unsigned spins = 0;
+            while ((word & ~SORT_COUNT) == 0u && ++spins < SORT_SPIN_LIMIT) word = ld_acquire_u32(w);
+            if ((word & ~SORT_COUNT) == 0u) {
+                atomicOr(err, 1);
+                break;
+            }
+            acc += word & SORT_COUNT;
+            if ((word & ~SORT_COUNT) == SORT_FLAG_P) break;
+        }
+        excl[t] = acc;
+        st_release_u32(&mine[t], SORT_FLAG_P | ((acc + own) & SORT_COUNT));
+    }
+    __syncthreads();
+    // stable ranks within the tile, round by round as the items were loaded
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const long long i = base + r * 256 + t;
+        const bool valid = i < n;
+        const unsigned d = valid ? (unsigned)(k[r] >> shift) & 255u : 256u + lane;  // invalid: unique
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned rank = __popc(peers & lt);
+        if (valid && (peers & lt) == 0) wcnt[wid][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            unsigned long long pos = (unsigned long long)goff[d] + excl[d] + run[d] + rank;
+            for (int w = 0; w < wid; ++w) pos += wcnt[w][d];
+            if (pos < (unsigned long long)n) {
+                kout[pos] = k[r];
+                vout[pos] = v[r];
+            } else {
+                atomicOr(err, 2);
+            }
+        }
+        __syncthreads();
+        unsigned tot = 0;
+        for (int w = 0; w < 8; ++w) {
+            tot += wcnt[w][t];
+            wcnt[w][t] = 0;
+        }
+        run[t] += tot;
+        __syncthreads();
+    }
+}
+
 static apr_status radix_sort(apr_ctx* c, long long n)
 {
     Workspace& W = c->W;
     const int ntiles = nblocks(n, RADIX_TILE);
     int cur = 0;
-    for (int shift = 0; shift < 3 * KEY_BITS; shift += 8) {
-        APR_LAUNCH(c, k_radix_hist, ntiles, 256, W.key[cur], n, shift, W.hist, ntiles);
-        scan_u32(c, W.hist, W.hist + (size_t)256 * ntiles, (long long)256 * ntiles, nullptr);
-        APR_LAUNCH(c, k_radix_scatter, ntiles, 256, W.key[cur], W.val[cur], W.key[cur ^ 1],
-                                                       W.val[cur ^ 1], n, shift,
-                                                       W.hist + (size_t)256 * ntiles, ntiles);
-        cur ^= 1;
+    // the look-back walks past every predecessor that has not yet published its
+    // prefix; with all tiles in flight at once that grows with the square of the
+    // tile count, so large sorts keep the histogram-scan-scatter passes (measured:
+    // 103 tiles 19% faster, 550 tiles 8% slower)
+    if (ntiles <= SORT_SWEEP_MAX_TILES) {
+        cudaMemsetAsync(W.sort_hist, 0, sizeof(unsigned) * 256 * 6, c->stream);
+        cudaMemsetAsync(W.sort_tile, 0, sizeof(unsigned) * 256 * (size_t)ntiles * 6, c->stream);
+        cudaMemsetAsync(&W.status[ST_SORT_TICKET], 0, sizeof(int) * 6, c->stream);
+        APR_LAUNCH(c, k_sort_hist6, min(ntiles, 152 * 4), 256, W.key[0], n, W.sort_hist);
+        APR_LAUNCH(c, k_sort_scan6, 1, 256, W.sort_hist);
+        for (int pass = 0; pass < 6; ++pass) {
+            APR_LAUNCH(c, k_sort_pass, ntiles, 256, W.key[cur], W.val[cur], W.key[cur ^ 1],
+                       W.val[cur ^ 1], n, 8 * pass, W.sort_hist + 256 * pass,
+                       W.sort_tile + (size_t)256 * ntiles * pass,
+                       (unsigned*)&W.status[ST_SORT_TICKET + pass], &W.status[ST_SORT_ERR]);
+            cur ^= 1;
+        }
+    } else {
+        for (int shift = 0; shift < 3 * KEY_BITS; shift += 8) {
+            APR_LAUNCH(c, k_radix_hist, ntiles, 256, W.key[cur], n, shift, W.hist, ntiles);
+            scan_u32(c, W.hist, W.hist + (size_t)256 * ntiles, (long long)256 * ntiles, nullptr);
+            APR_LAUNCH(c, k_radix_scatter, ntiles, 256, W.key[cur], W.val[cur], W.key[cur ^ 1],
+                       W.val[cur ^ 1], n, shift, W.hist + (size_t)256 * ntiles, ntiles);
+            cur ^= 1;
+        }
     }
     W.skey = W.key[cur];
     W.perm = W.val[cur];

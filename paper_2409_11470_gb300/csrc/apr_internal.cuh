@@ -18,6 +18,7 @@ constexpr int CELL_MAX = 32;                 // particles per cell (one warp)
 constexpr int KEY_BITS = 16;                 // Morton key bits per axis (48-bit keys, 6 passes)
 constexpr int MAX_CAND = 128;                // candidate cells per cell
 constexpr int RADIX_TILE = 2048;             // items per radix-sort block (256 x 8)
+constexpr int SORT_SWEEP_MAX_TILES = 256;     // Morton sort: single-sweep passes up to this many tiles
 constexpr int SCAN_BLOCK = 1024;             // items per scan block (256 x 4)
 constexpr int RED_BLOCKS = 1216;             // 8 x 152 SMs: fixed-shape f64 reductions
 constexpr int DEFAULT_MAX_NEIGH = 512;
@@ -43,6 +44,8 @@ enum {
     ST_SATURATED = 40,       // time-step bins: updates whose limit was below dt_min
     ST_RELIST_N = 41,        // density retries: particles whose lists are rebuilt after
     ST_RETRIED_N = 42,       //   them, and how many of those were retried themselves
+    ST_SORT_ERR = 43,        // Morton sort: a tile's look-back gave up waiting (bounded)
+    ST_SORT_TICKET = 44,     // Morton sort: tile tickets of the passes (6 words, 44..49)
     ST_BINS = 16,            // merge: first slot of each level's candidates (10 words)
     ST_MERGES = 32,          // merge: merges per level (8 words)
     ST_NSTATUS = 16
@@ -116,6 +119,8 @@ struct Workspace {
     unsigned long long* key[2];
     unsigned int* val[2];
     unsigned int* hist;
+    unsigned int* sort_hist;  // Morton sort: digit counts of every pass (6 x 256), then offsets
+    unsigned int* sort_tile;  // Morton sort: per pass and tile, 256 published digit counts
     unsigned int* scan_tmp;
     unsigned int* perm;       // sorted slot -> canonical index
     unsigned long long* skey; // sorted keys (aliases key[0] or key[1])

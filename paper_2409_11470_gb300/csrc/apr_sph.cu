@@ -241,9 +241,12 @@ apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv, con
     prof_end(c, ps);
     // one read-back for the index status words and the density counters
     cudaMemcpyAsync(c->hbuf, W.status, (ST_SHRINK + 1) * sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync((int*)c->hbuf + 16, &W.status[ST_SORT_ERR], sizeof(int), cudaMemcpyDeviceToHost,
+                    st);
     apr_status s = cuda_check(c, cudaStreamSynchronize(st), "density");
     if (s != APR_OK) return s;
     const int* hs = (const int*)c->hbuf;
+    if (hs[16]) return fail(c, APR_ERR_STATE, "Morton sort: a tile gave up waiting for its predecessors");
     if (hs[ST_TREE_BAD]) return fail(c, APR_ERR_STATE, "internal error: malformed radix tree");
     if (hs[ST_NEIGH_OVERFLOW] || hs[ST_CAND_OVERFLOW])
         return fail(c, APR_ERR_NEIGH_OVERFLOW, "a neighbour list overflowed");
