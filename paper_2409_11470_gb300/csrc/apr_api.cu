@@ -142,6 +142,10 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.cell_cnt = (int*)take(4 * C);
     w.cell_node = (int*)take(4 * C);
     w.cmark = (int*)take(4 * C);
+    w.acell_first = (int*)take(4 * C);
+    w.acell_cnt = (int*)take(4 * C);
+    w.acell_node = (int*)take(4 * C);
+    w.amark = (unsigned char*)take(C);
     w.cand = (int2*)take(8 * (size_t)MAX_CAND * C);
     w.ncand = (int*)take(4 * C);
     w.point_q = (int*)take(4 * C);
@@ -710,7 +714,8 @@ static apr_status run_density_active(apr_ctx* c, long long nq, bool all)
         cudaMemsetAsync(W.status, 0, 2 * sizeof(int), c->stream);
         if (attempt == 0) {
             s = all ? index_lists(c, 1, DENSITY_REACH, true)
-                    : index_lists_queue(c, W.active_q, &W.status[ST_ACTIVE_N], DENSITY_REACH, true);
+                    : index_lists_cells_of(c, W.active_q, &W.status[ST_ACTIVE_N], DENSITY_REACH,
+                                           true);
             if (s == APR_OK) s = density_pass(c, &unc, &noconv, W.active_q, nq, q);
         } else {
             s = relist_mark(c, W.retry_q[q], &W.status[ST_RETRY_N + q], attempt == 1);
@@ -756,7 +761,7 @@ static apr_status run_force_active(apr_ctx* c, long long nq, bool all)
         if (s != APR_OK) return s;
         cudaMemsetAsync(W.status, 0, 2 * sizeof(int), c->stream);
         s = all ? index_lists(c, 1, 1.0)
-                : index_lists_queue(c, W.active_q, &W.status[ST_ACTIVE_N], 1.0, false);
+                : index_lists_cells_of(c, W.active_q, &W.status[ST_ACTIVE_N], 1.0, false);
         if (s != APR_OK) return s;
         c->lists_fresh = true;
         c->lists_unchecked = true;

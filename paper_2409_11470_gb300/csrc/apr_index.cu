@@ -1238,7 +1238,8 @@ __global__ void __launch_bounds__(128)
 }
 
 template <int SYM>
-static void launch_lists(apr_ctx* c, const int* ncell_dev, int n, bool graceful)
+static void launch_lists(apr_ctx* c, const int* ncell_dev, int n, bool graceful,
+                         const int* cell_first, const int* cell_cnt)
 {
     Workspace& W = c->W;
     const int mask = (c->dc.periodic[0] ? 1 : 0) | (c->dc.periodic[1] ? 2 : 0) |
@@ -1246,8 +1247,8 @@ static void launch_lists(apr_ctx* c, const int* ncell_dev, int n, bool graceful)
     const int grid = min(nblocks((long long)n * 32, 128), 152 * 16);
 #define APR_LISTS_CASE(M, X, Y, Z)                                                                   \
     case M:                                                                                          \
-        APR_LAUNCH(c, (k_lists<X, Y, Z, SYM>), grid, 128, c->dc, ncell_dev, n, c->cap, W.cell_first, \
-                   W.cell_cnt, W.cand, W.ncand, W.pk, W.sthr, W.sreach, W.nbr, W.ncnt, W.point_q,    \
+        APR_LAUNCH(c, (k_lists<X, Y, Z, SYM>), grid, 128, c->dc, ncell_dev, n, c->cap, cell_first,   \
+                   cell_cnt, W.cand, W.ncand, W.pk, W.sthr, W.sreach, W.nbr, W.ncnt, W.point_q,      \
                    W.status, graceful ? 1 : 0);                                                      \
         APR_LAUNCH(c, (k_lists_point<X, Y, Z, SYM>), 152 * 4, 128, c->dc, &W.status[ST_POINT_N],     \
                    W.point_q, n, c->cap, W.left, W.right, W.pk, W.sthr, W.nlo, W.nhi, W.nthr, W.nbr, \
@@ -1441,11 +1442,85 @@ apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful)
                W.cell_node, W.left, W.right, W.pk, W.sthr, W.nlo, W.nhi, W.nthr, W.cand, W.ncand,
                W.status, graceful ? 1 : 0);
     if (mode == 0)
-        launch_lists<0>(c, ncell_dev, n, graceful);
+        launch_lists<0>(c, ncell_dev, n, graceful, W.cell_first, W.cell_cnt);
     else
-        launch_lists<1>(c, ncell_dev, n, graceful);
+        launch_lists<1>(c, ncell_dev, n, graceful, W.cell_first, W.cell_cnt);
     prof_end(c, ps);
     return cuda_check(c, cudaGetLastError(), "lists");
+}
+
+// ---- symmetric lists of the cells that hold a queued particle
+//
+// For a queue that is a small part of the particles (the active particles of a
+// time-step bin), clustered in space as bins follow the flow: the cells that
+// hold one of them take the warp-per-cell path, which costs a few particles'
+// worth of a per-particle tree walk.  Every particle of such a cell gets its
+// list; the queued ones are among them.
+
+__global__ void k_mark_queue_slots(const int* __restrict__ queue, const int* __restrict__ qlen,
+                                   int n, unsigned char* __restrict__ amark)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= min(*qlen, n)) return;
+    const int a = queue[i];
+    if (a >= 0 && a < n) amark[a] = 1;
+}
+
+// the cells with a marked slot, appended in any order (each cell's lists are
+// built on their own)
+__global__ void k_active_cells(const int* __restrict__ ncell_dev, int n,
+                               const int* __restrict__ cell_first, const int* __restrict__ cell_cnt,
+                               const int* __restrict__ cell_node,
+                               const unsigned char* __restrict__ amark, int* __restrict__ acell_first,
+                               int* __restrict__ acell_cnt, int* __restrict__ acell_node,
+                               int* __restrict__ nactive)
+{
+    const int cid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cid >= min(*ncell_dev, n)) return;
+    const int f = cell_first[cid], cnt = cell_cnt[cid];
+    if (f < 0 || cnt < 1 || f + cnt > n) return;
+    bool any = false;
+    for (int k = 0; k < cnt && !any; ++k) any = amark[f + k] != 0;
+    if (!any) return;
+    const int slot = atomicAdd(nactive, 1);
+    acell_first[slot] = f;
+    acell_cnt[slot] = cnt;
+    acell_node[slot] = cell_node[cid];
+}
+
+apr_status index_lists_cells_of(apr_ctx* c, const int* queue, const int* qlen_dev, double reach,
+                                bool graceful)
+{
+    Workspace& W = c->W;
+    int n = (int)c->n;
+    if (n <= 0) return APR_OK;
+    cudaStream_t st = c->stream;
+    int ps = prof_begin(c, APR_PROF_LISTS);
+    cudaMemsetAsync(W.cflag, 0, sizeof(unsigned) * (size_t)n, st);
+    if (n <= CELL_MAX)
+        APR_LAUNCH(c, k_cells_root, 1, 1, n, W.cflag, W.cmark);
+    else
+        APR_LAUNCH(c, k_cells_mark, nblocks(n - 1, 256), 256, n, W.left, W.right, W.nlo, W.nhi, W.cflag,
+                   W.cmark);
+    int* ncell_dev = &W.status[ST_NCELL];
+    scan_u32(c, W.cflag, W.cscan, n, (unsigned*)ncell_dev);
+    APR_LAUNCH(c, k_cells_compact, nblocks(n, 256), 256, n, W.cflag, W.cscan, W.cmark, W.nlo,
+               W.cell_first, W.cell_cnt, W.cell_node);
+    cudaMemsetAsync(W.amark, 0, (size_t)n, st);
+    cudaMemsetAsync(&W.status[ST_ACELL_N], 0, sizeof(int), st);
+    APR_LAUNCH(c, k_mark_queue_slots, nblocks(n, 256), 256, queue, qlen_dev, n, W.amark);
+    APR_LAUNCH(c, k_active_cells, nblocks(n, 256), 256, ncell_dev, n, W.cell_first, W.cell_cnt,
+               W.cell_node, W.amark, W.acell_first, W.acell_cnt, W.acell_node, &W.status[ST_ACELL_N]);
+    APR_LAUNCH(c, k_thresholds, nblocks(n, 256), 256, c->dc, n, reach, W.sh, W.sthr, W.sreach,
+               W.status);
+    if (n >= 2) APR_LAUNCH(c, k_node_thr, nblocks(n - 1, 256), 256, c->dc, n, reach, W.nhmax, W.nthr);
+    int* nac = &W.status[ST_ACELL_N];
+    APR_LAUNCH(c, k_candidates, min(nblocks((long long)n * 32, 128), 152 * 16), 128, c->dc, 1, nac, n,
+               W.acell_node, W.left, W.right, W.pk, W.sthr, W.nlo, W.nhi, W.nthr, W.cand, W.ncand,
+               W.status, graceful ? 1 : 0);
+    launch_lists<1>(c, nac, n, graceful, W.acell_first, W.acell_cnt);
+    prof_end(c, ps);
+    return cuda_check(c, cudaGetLastError(), "active-cell lists");
 }
 
 }  // namespace apr

@@ -46,6 +46,7 @@ enum {
     ST_RETRIED_N = 42,       //   them, and how many of those were retried themselves
     ST_SORT_ERR = 43,        // Morton sort: a tile's look-back gave up waiting (bounded)
     ST_SORT_TICKET = 44,     // Morton sort: tile tickets of the passes (6 words, 44..49)
+    ST_ACELL_N = 50,         // lists of the cells that hold a queued particle: cell count
     ST_BINS = 16,            // merge: first slot of each level's candidates (10 words)
     ST_MERGES = 32,          // merge: merges per level (8 words)
     ST_NSTATUS = 16
@@ -154,6 +155,10 @@ struct Workspace {
     int* cell_cnt;
     int* cell_node;
     int* cmark;               // node of the cell starting at a sorted slot
+    int* acell_first;         // the cells that hold a queued particle (any order)
+    int* acell_cnt;
+    int* acell_node;
+    unsigned char* amark;     // per sorted slot: queued
     int2* cand;               // MAX_CAND (first slot, count) per cell
     int* ncand;
     int* point_q;             // particles of cells whose candidate list overflowed
@@ -303,6 +308,9 @@ apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful = false
 // (sym) or gather lists
 apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, double reach,
                              bool graceful = true, bool sym = true);
+// symmetric lists of every particle in a cell that holds a queued particle
+apr_status index_lists_cells_of(apr_ctx* c, const int* queue, const int* qlen_dev, double reach,
+                                bool graceful);
 apr_status index_refresh_sh(apr_ctx* c);     // re-gather h only (no node h maxima)
 
 // SPH passes (apr_sph.cu)
