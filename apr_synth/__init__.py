@@ -115,7 +115,8 @@ def c1_lattice():
 def sod(nL=28, gamma=1.4, slab=(0.15, 0.10), seed=SEED_BASE + 1, jitter=0.05, name=None):
     """Three-dimensional Sod shock tube.
 
-    x in [-0.5, 0.5], y and z periodic with width 0.1.  Left state rho = 1, P = 1 on a
+    x in [-0.5, 0.5], y and z periodic with width 0.1 (to within 4e-10: a whole number
+    of lattice units 2^-29).  Left state rho = 1, P = 1 on a
     lattice of spacing 0.1/nL; right state rho = 0.125, P = 0.1 on spacing 0.2/nL (equal
     particle masses).  Each particle is moved by U(-jitter, jitter) local spacings per
     axis: a perfect cubic lattice cannot rearrange sideways under the one-dimensional
@@ -124,7 +125,11 @@ def sod(nL=28, gamma=1.4, slab=(0.15, 0.10), seed=SEED_BASE + 1, jitter=0.05, na
     x = +-0.5 are FIXED.  The refinement region is a slab |x| < slab[k] for level k + 1.
     """
     assert nL % 2 == 0
-    w = 0.1
+    # the width 0.1 rounded to a whole number of lattice units 2^-29 (within 4e-10):
+    # periodic lengths are whole numbers of units, and a power-of-two unit lets the
+    # GPU quantise by a multiplication
+    delta = 2.0 ** -29
+    w = round(0.1 / delta) * delta
     hfact = 1.2
     sL = w / nL
     sR = 2.0 * sL
@@ -155,7 +160,7 @@ def sod(nL=28, gamma=1.4, slab=(0.15, 0.10), seed=SEED_BASE + 1, jitter=0.05, na
     zeros = np.zeros(n)
     p = _particles(x, y, z, zeros, zeros, zeros, u, h, flags=flags)
     cfg = _cfg(box_lo=[-0.6, 0.0, 0.0], box_hi=[0.6, w, w], periodic=[0, 1, 1],
-               delta=w * 2.0 ** -26, gamma=gamma, hfact=hfact, m0=sL ** 3,
+               delta=delta, gamma=gamma, hfact=hfact, m0=sL ** 3,
                alpha_av=1.0, beta_av=2.0, alpha_u=1.0, lmax=len(slab), seed=seed)
     regions = [dict(shape=SHAPE_SLAB, axis=0, track_sink=-1, centre=[0.0, 0.05, 0.05],
                     R=list(slab))] if slab else []

@@ -60,9 +60,10 @@ def parse():
     ap.add_argument("--ncu-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off)")
-    ap.add_argument("--profile-workload", choices=["disc_planet"], default=None,
+    ap.add_argument("--profile-workload", choices=["disc_planet", "disc_planet_bins"], default=None,
                     help="profiling only: initialise this workload, take --warmup steps, "
-                         "then --steps steps inside cudaProfilerStart/Stop")
+                         "then --steps steps inside cudaProfilerStart/Stop (the _bins form: "
+                         "steps of 32 times the smallest limit in time-step bins 0..5)")
     return ap.parse_args()
 
 
@@ -671,12 +672,20 @@ def run_profile_workload(args):
     n0 = len(w["p"]["x"])
     sim = Simulation(w, capacity=int(1.6 * n0) + 1024, precision="fp32", max_neigh=2048)
     sim.init()
-    for _ in range(args.warmup):
-        sim.step(0.0)
+    bins = args.profile_workload.endswith("_bins")
+
+    def one(first):
+        if bins:
+            sim.step_bins(32 * sim.timestep(), 5, init_bins=first)
+        else:
+            sim.step(0.0)
+
+    for k in range(args.warmup):
+        one(k == 0)
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStart()
-    for _ in range(args.steps):
-        sim.step(0.0)
+    for k in range(args.steps):
+        one(args.warmup == 0 and k == 0)
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStop()
     print(json.dumps({"profile_workload": w["name"], "steps": args.steps, "n": sim.n}), flush=True)

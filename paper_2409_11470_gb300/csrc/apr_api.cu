@@ -240,6 +240,11 @@ static apr_status check_cfg(const apr_config* cfg, DevCfg* dc, std::string* why)
     }
     dc->delta = cfg->delta;
     dc->deltaf = (float)cfg->delta;
+    {
+        int ex = 0;
+        const double mant = std::frexp(cfg->delta, &ex);
+        dc->inv_delta = mant == 0.5 ? std::ldexp(1.0, 1 - ex) : 0.0;
+    }
     dc->alpha_avf = (float)cfg->alpha_av;
     dc->beta_avf = (float)cfg->beta_av;
     dc->alpha_uf = (float)cfg->alpha_u;

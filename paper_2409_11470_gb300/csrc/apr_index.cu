@@ -134,11 +134,16 @@ apr_status scan_u32(apr_ctx* c, const unsigned int* in, unsigned int* out, long 
 
 __device__ __forceinline__ long long quant1(const DevCfg& dc, int k, double x)
 {
-    long long q = (long long)floor((x - dc.lo[k]) / dc.delta);
+    // a power-of-two unit multiplies (exactly the quotient); the remainder only for
+    // the rare coordinate outside the periodic box
+    const double t = dc.inv_delta > 0.0 ? (x - dc.lo[k]) * dc.inv_delta : (x - dc.lo[k]) / dc.delta;
+    long long q = (long long)floor(t);
     if (dc.periodic[k]) {
         long long L = dc.Lint[k];
-        q %= L;
-        if (q < 0) q += L;
+        if (q < 0 || q >= L) {
+            q %= L;
+            if (q < 0) q += L;
+        }
     } else {
         if (q < 0) q = 0;
         if (q > COORD_MAX) q = COORD_MAX;
@@ -727,7 +732,7 @@ __global__ void k_node_thr(DevCfg dc, int n, double reach, const double* __restr
                            unsigned long long* __restrict__ nthr)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n - 1) nthr[i] = neighbour_threshold(reach * nhmax[i], dc.delta);
+    if (i < n - 1) nthr[i] = lattice_threshold(dc, reach * nhmax[i]);
 }
 
 struct NodeBox {
@@ -846,9 +851,10 @@ __global__ void k_thresholds(DevCfg dc, long long n, double reach, const double*
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s == 0) status[ST_POINT_N] = 0;  // the per-particle queue of this list build
     if (s >= n) return;
-    const unsigned long long t = neighbour_threshold(reach * sh[s], dc.delta);
+    const unsigned long long t = lattice_threshold(dc, reach * sh[s]);
     thr[s] = t;
-    unsigned long long r = (unsigned long long)ceil(sqrt((double)t));
+    // a float root as the start, made exact by the integer steps below
+    unsigned long long r = (unsigned long long)ceilf(sqrtf((float)t));
     while (r > 0 && (r - 1) * (r - 1) >= t) --r;
     while (r * r < t) ++r;
     rint[s] = r > 0xffffffffULL ? 0xffffffffu : (unsigned)r;
@@ -1361,7 +1367,7 @@ __global__ void k_relist_mark_reach(DevCfg dc, int n, long long cap, int K,
         const int b = relist_q[w];
         const int m = min(ncnt[b], K);
         const int4 pb = pk[b];
-        const unsigned long long tf = neighbour_threshold(h[perm[b]], dc.delta);
+        const unsigned long long tf = lattice_threshold(dc, h[perm[b]]);
         const unsigned long long tb0 = sthr0[b];
         for (int k = lane; k < m; k += 32) {
             const int y = (int)nbr[(long long)k * cap + b];

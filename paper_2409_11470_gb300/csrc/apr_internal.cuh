@@ -76,6 +76,7 @@ struct DevCfg {
     long long Lint[3];
     double delta;
     float deltaf;
+    double inv_delta;          // 1 / delta when delta is a power of two (exact), else 0
     double hfact, gamma;
     int eos;
     double cs0, qcs;
@@ -245,6 +246,16 @@ __host__ __device__ inline unsigned long long neighbour_threshold(double h, doub
 {
     // b is within the kernel radius 2h of a iff r2_lattice(a, b) < thr(h)
     double t = (2.0 * h) / delta;
+    double t2 = t * t;
+    if (!(t2 < 4.6e18)) return 4611686018427387904ULL;
+    return (unsigned long long)ceil(t2);
+}
+
+// the same threshold with dc's lattice unit: a multiplication where the unit is a
+// power of two (then x * (1/delta) equals x / delta exactly), else the division
+__device__ __forceinline__ unsigned long long lattice_threshold(const DevCfg& dc, double h)
+{
+    double t = dc.inv_delta > 0.0 ? (2.0 * h) * dc.inv_delta : (2.0 * h) / dc.delta;
     double t2 = t * t;
     if (!(t2 < 4.6e18)) return 4611686018427387904ULL;
     return (unsigned long long)ceil(t2);

@@ -1775,12 +1775,51 @@ __device__ __forceinline__ double rsqrt_newton(double x)
 
 // every live particle pulls the point masses; with B >= 0 (time-step bins) only
 // the particles whose step ends at substep boundary `sub` take their pull.
-// NS bounds the number of point masses (the per-block sums are 3 NS wide).
-template <int NS>
+// NS bounds the number of point masses (the per-block sums are 3 NS wide).  F32
+// (the FP32-mixed path): the separation is formed in FP64 and the pull evaluated
+// in FP32, like the pair sums; the point masses' sums stay FP64.
+template <int NS, bool F32>
 __global__ void __launch_bounds__(256) k_sink_gravity(DevCfg dc, DevSinks sk, long long n,
                                                       apr_particles p, int B, long long sub,
                                                       double* partials)
 {
+    if constexpr (F32) {
+        double v[3 * NS];
+        for (int k = 0; k < 3 * NS; ++k) v[k] = 0.0;
+        const int ns = sk.n < NS ? sk.n : NS;
+        const float G = (float)dc.G;
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            if (p.flags[i] & APR_FLAG_DEAD) continue;
+            const float mi = (float)(dc.m0 * level_mass_d(p.level[i]));
+            const bool pulled = B < 0 || sub % ((1LL << B) >> p.bin[i]) == 0;
+            float ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                if (j >= ns) break;
+                const float dx = (float)(p.x[i] - sk.x[j][0]), dy = (float)(p.y[i] - sk.x[j][1]),
+                            dz = (float)(p.z[i] - sk.x[j][2]);
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const float y = rsqrtf(r2);
+                const float f = G * (y * y * y);
+                const float fm = f * (float)sk.m[j];
+                ax -= fm * dx;
+                ay -= fm * dy;
+                az -= fm * dz;
+                const float fi = f * mi;
+                v[3 * j + 0] += (double)(fi * dx);
+                v[3 * j + 1] += (double)(fi * dy);
+                v[3 * j + 2] += (double)(fi * dz);
+            }
+            if (pulled) {
+                p.ax[i] += (double)ax;
+                p.ay[i] += (double)ay;
+                p.az[i] += (double)az;
+            }
+        }
+        block_reduce_store<3 * NS>(v, partials);
+        return;
+    }
     double v[3 * NS];
     for (int k = 0; k < 3 * NS; ++k) v[k] = 0.0;
     const int ns = sk.n < NS ? sk.n : NS;
@@ -1817,11 +1856,17 @@ apr_status sink_gravity(apr_ctx* c, int B, long long sub)
 {
     if (c->nsink == 0) return APR_OK;
     const int nblk = red_grid(c->n);
-    if (c->nsink <= 2)
-        APR_LAUNCH(c, k_sink_gravity<2>, nblk, 256, c->dc, dev_sinks(c), c->n, c->p, B, sub, c->W.red);
-    else
-        APR_LAUNCH(c, k_sink_gravity<APR_MAXSINK>, nblk, 256, c->dc, dev_sinks(c), c->n, c->p, B, sub,
-                   c->W.red);
+    const bool f32 = c->cfg.precision == APR_PREC_FP32_MIXED;
+#define APR_SINKS(NS, F)                                                                             \
+    APR_LAUNCH(c, (k_sink_gravity<NS, F>), nblk, 256, c->dc, dev_sinks(c), c->n, c->p, B, sub, c->W.red)
+    if (c->nsink <= 2) {
+        if (f32) APR_SINKS(2, true);
+        else APR_SINKS(2, false);
+    } else {
+        if (f32) APR_SINKS(APR_MAXSINK, true);
+        else APR_SINKS(APR_MAXSINK, false);
+    }
+#undef APR_SINKS
     double r[3 * APR_MAXSINK];
     apr_status s = reduce_readback_n(c, nblk, 3 * c->nsink, 0u, r);
     if (s != APR_OK) return s;

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(128, density_min_blocks<R>())
     if (!conv) atomicAdd(&status[ST_NOCONV], 1);
     // nearest lattice neighbour within 2h: the list holds every particle within
     // the reach, so the overall nearest counts iff it lies inside 2h
-    const unsigned long long thr = neighbour_threshold(hd, dc.delta);
+    const unsigned long long thr = lattice_threshold(dc, hd);
     dnn_out[i] = best < thr ? sqrt((double)best) * dc.delta : (double)INFINITY;
     const double hr = dc.hfact / hd;
     const double rho = dc.m0 * (double)level_mass_d(pa.w) * hr * hr * hr;
