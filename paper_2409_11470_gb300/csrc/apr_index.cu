@@ -568,6 +568,13 @@ __device__ __forceinline__ NodeData node_data(int c, const int4* pk, const doubl
     return r;
 }
 
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // bottom-up: the second child to arrive at a node merges both children
 __global__ void k_tree_up(int n, const int4* __restrict__ pk, const double* __restrict__ sh,
                           const int* __restrict__ left, const int* __restrict__ right,
@@ -583,9 +590,9 @@ __global__ void k_tree_up(int n, const int4* __restrict__ pk, const double* __re
             atomicOr(&status[ST_TREE_BAD], 1);
             return;
         }
-        __threadfence();
-        if (atomicAdd(&visit[node], 1) == 0) return;
-        __threadfence();
+        // release: this thread's child data (stored just before) is visible to the
+        // sibling's thread; acquire: the sibling's child data is visible here
+        if (atom_add_acq_rel_u32((unsigned*)&visit[node], 1u) == 0u) return;
         NodeData a = node_data(left[node], pk, sh, nlo, nhi, nhmax);
         NodeData b = node_data(right[node], pk, sh, nlo, nhi, nhmax);
         int4 lo = make_int4(min(a.lo[0], b.lo[0]), min(a.lo[1], b.lo[1]), min(a.lo[2], b.lo[2]),

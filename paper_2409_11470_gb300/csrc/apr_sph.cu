@@ -196,13 +196,26 @@ __global__ void __launch_bounds__(128, density_min_blocks<R>())
     rho_out[i] = rho;
     omega_out[i] = 1.0 - (double)D / (3.0 * (double)target);
     double P, cs;
-    if (dc.eos == APR_EOS_ADIABATIC) {
-        P = (dc.gamma - 1.0) * rho * u[i];
-        cs = sqrt(dc.gamma * P / rho);
+    if constexpr (sizeof(R) == 4) {
+        // FP32-mixed: the sound speed at the pair sums' precision (FP64 square
+        // roots, quotients and powers are slow on this part); c_s^2 = gamma (gamma - 1) u
+        if (dc.eos == APR_EOS_ADIABATIC) {
+            P = (dc.gamma - 1.0) * rho * u[i];
+            cs = (double)sqrtf((float)(dc.gamma * (dc.gamma - 1.0) * u[i]));
+        } else {
+            const float Rc = sqrtf((float)(x[i] * x[i] + y[i] * y[i]));
+            cs = (double)((float)dc.cs0 * powf(Rc, -(float)dc.qcs));
+            P = cs * cs * rho;
+        }
     } else {
-        double Rc = sqrt(x[i] * x[i] + y[i] * y[i]);
-        cs = dc.cs0 * pow(Rc, -dc.qcs);
-        P = cs * cs * rho;
+        if (dc.eos == APR_EOS_ADIABATIC) {
+            P = (dc.gamma - 1.0) * rho * u[i];
+            cs = sqrt(dc.gamma * P / rho);
+        } else {
+            double Rc = sqrt(x[i] * x[i] + y[i] * y[i]);
+            cs = dc.cs0 * pow(Rc, -dc.qcs);
+            P = cs * cs * rho;
+        }
     }
     pres_out[i] = P;
     cs_out[i] = cs;
