@@ -29,11 +29,25 @@ def _few_wide(w, h=0.2, count=3, seed=3):
     return w
 
 
+def _odd_unit(w, seed=6):
+    """The same box on a lattice unit that is not a power of two (3 x 2^-31 for the unit
+    box, whose length stays a whole number of units), so that quantisation and list
+    thresholds take the division; some particles sit one box length outside, so that
+    quantisation takes the periodic remainder."""
+    L = 1.0
+    w["cfg"]["delta"] = L / round(L / (3.0 * 2.0 ** -31))
+    rng = np.random.default_rng(seed)
+    pick = rng.random(len(w["p"]["x"])) < 0.05
+    w["p"]["x"] = np.where(pick, w["p"]["x"] + L, w["p"]["x"])
+    return w
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("make", [apr_synth.c1_lattice,
                                   lambda: apr_synth.lattice_box(11, 0.2, seed=5),
                                   lambda: _variable_h(apr_synth.sod(8, slab=())),
-                                  lambda: _few_wide(apr_synth.lattice_box(14, 0.2, seed=8))])
+                                  lambda: _few_wide(apr_synth.lattice_box(14, 0.2, seed=8)),
+                                  lambda: _odd_unit(apr_synth.lattice_box(12, 0.2, seed=9))])
 def test_neighbour_lists_bit_exact(make, mode):
     w = make()
     o = oracle.Oracle(w)
