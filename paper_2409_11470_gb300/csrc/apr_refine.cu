@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(COOP_THREADS)
     const int G = gridDim.x;
     const int gtid = blockIdx.x * COOP_THREADS + threadIdx.x, gstride = G * COOP_THREADS;
     const int chunk = (M + G - 1) / G;
-    // round 0's boxes and sums (accumulators reset by the setup kernel)
+    // the first cut's boxes and sums (accumulators reset by the setup kernel)
     for (int p0 = 0; p0 < M; p0 += gstride) {
         const int p = p0 + gtid;
         bool act = false;
