@@ -217,6 +217,18 @@ def traffic_record(kernel):
     return {"dram_bytes_per_launch": float(rec["dram_bytes_per_launch"]), "n": float(rec["n"])}
 
 
+def replica_totals(torch, ms, psteps, world, device):
+    """Whole-job totals of independent replicas: the slowest rank's time and the
+    particle-steps of all ranks (the only collective of a multi-GPU run)."""
+    ms_t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    ps_t = torch.tensor([float(psteps)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(ps_t, op=dist.ReduceOp.SUM)
+    return float(ms_t.item()), float(ps_t.item())
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -259,13 +271,7 @@ def run_ours(args):
     prof = sim.profile()
     sim.profile_enable(False)
     launches = prof["launches"] - launches0
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    ps_t = torch.tensor([float(psteps)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(ps_t, op=dist.ReduceOp.SUM)
-    ms_max, ps_all = float(ms_t.item()), float(ps_t.item())
+    ms_max, ps_all = replica_totals(torch, ms, psteps, world, "cuda")
     value = ps_all / (ms_max / 1e3)
 
     # roofline of the dominant kernel (live events on the library's stream)
