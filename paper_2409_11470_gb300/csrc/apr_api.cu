@@ -637,9 +637,7 @@ apr_status apr_step(apr_ctx* c, double dt, double* dt_used, apr_stats* stats,
     }
     const double hdt = 0.5 * dt;
     int ps = prof_begin(c, APR_PROF_OTHER);
-    s = kick(c, hdt);
-    if (s != APR_OK) return s;
-    s = drift(c, dt);
+    s = kick_drift(c, hdt, dt);
     if (s != APR_OK) return s;
     long long na = 0;
     s = accrete(c, &na);
@@ -654,15 +652,13 @@ apr_status apr_step(apr_ctx* c, double dt, double* dt_used, apr_stats* stats,
     if (s != APR_OK) return s;
     s = run_force(c, true);
     if (s != APR_OK) return s;
-    ps = prof_begin(c, APR_PROF_OTHER);
-    s = kick(c, hdt);
-    prof_end(c, ps);
-    if (s != APR_OK) return s;
     if (dt_used) *dt_used = dt;
     if (counts) *counts = cnt;
-    // conservation sums and the next step's limit in one reduction
+    // the closing half kick (point masses here, the gas in the same pass as the
+    // conservation sums and the next step's limit)
+    kick_sinks(c, hdt);
     apr_stats st_local;
-    s = compute_stats_dt(c, stats ? stats : &st_local, &c->dt_next);
+    s = compute_stats_dt(c, stats ? stats : &st_local, &c->dt_next, hdt);
     if (s != APR_OK) return s;
     c->dt_valid = true;
     return APR_OK;

@@ -341,9 +341,12 @@ apr_status sink_gravity(apr_ctx* c, int B = -1, long long sub = 0);
 apr_status accrete(apr_ctx* c, long long* naccreted);
 apr_status kick(apr_ctx* c, double hdt);
 apr_status drift(apr_ctx* c, double dt);
+apr_status kick_drift(apr_ctx* c, double hdt, double dt);  // opening half kick + drift
 apr_status compute_stats(apr_ctx* c, apr_stats* st);
 apr_status compute_timestep(apr_ctx* c, double* dt);
-apr_status compute_stats_dt(apr_ctx* c, apr_stats* st, double* dt);
+// conservation sums and the step limit; kick_hdt != 0 applies the step's closing
+// half kick to the gas first (the same pass)
+apr_status compute_stats_dt(apr_ctx* c, apr_stats* st, double* dt, double kick_hdt = 0.0);
 // individual time steps (apr_bins.cu)
 apr_status bins_init(apr_ctx* c, double dt_max, int B);
 apr_status bins_kick(apr_ctx* c, double dt_max, int B, long long k, int end_of_step);

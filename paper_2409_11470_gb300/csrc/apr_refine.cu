@@ -1619,8 +1619,9 @@ struct DtMin {
     }
 };
 
+// hdt != 0: first the closing half kick of the step (as k_kick), then the sums
 __global__ void __launch_bounds__(256) k_stats_dt(DevCfg dc, long long n, apr_particles p,
-                                                  double* partials)
+                                                  double hdt, double* partials)
 {
     double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     DtMin best;
@@ -1630,6 +1631,15 @@ __global__ void __launch_bounds__(256) k_stats_dt(DevCfg dc, long long n, apr_pa
         if (fl & APR_FLAG_DEAD) continue;
         double m = dc.m0 * level_mass_d(p.level[i]);
         double vx = p.vx[i], vy = p.vy[i], vz = p.vz[i];
+        if (hdt != 0.0 && !(fl & APR_FLAG_FIXED)) {
+            vx += hdt * p.ax[i];
+            vy += hdt * p.ay[i];
+            vz += hdt * p.az[i];
+            p.vx[i] = vx;
+            p.vy[i] = vy;
+            p.vz[i] = vz;
+            if (dc.eos == APR_EOS_ADIABATIC) p.u[i] += hdt * p.dudt[i];
+        }
         v[0] += m;
         v[1] += m * vx;
         v[2] += m * vy;
@@ -1689,12 +1699,12 @@ static void stats_from(const apr_ctx* c, const double* r, apr_stats* st)
     }
 }
 
-apr_status compute_stats_dt(apr_ctx* c, apr_stats* st, double* dt)
+apr_status compute_stats_dt(apr_ctx* c, apr_stats* st, double* dt, double kick_hdt)
 {
     // about four particles per thread: enough to hide the loads, few enough blocks
     // that the per-block FP64 reduction (ten shuffled sums) stays small
     const int nblk = red_grid(c->n);
-    APR_LAUNCH(c, k_stats_dt, nblk, 256, c->dc, c->n, c->p, c->W.red);
+    APR_LAUNCH(c, k_stats_dt, nblk, 256, c->dc, c->n, c->p, kick_hdt, c->W.red);
     double r[10];
     apr_status s = reduce_readback_n(c, nblk, 10, 1u << 9, r);
     if (s != APR_OK) return s;
@@ -1970,6 +1980,34 @@ __global__ void k_kick(DevCfg dc, long long n, double hdt, apr_particles p)
     p.vy[i] += hdt * p.ay[i];
     p.vz[i] += hdt * p.az[i];
     if (dc.eos == APR_EOS_ADIABATIC) p.u[i] += hdt * p.dudt[i];
+}
+
+// the opening half kick and the drift of one global step in one pass (as k_kick
+// then k_drift)
+__global__ void k_kick_drift(DevCfg dc, long long n, double hdt, double dt, apr_particles p)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || (p.flags[i] & (APR_FLAG_FIXED | APR_FLAG_DEAD))) return;
+    const double vx = p.vx[i] + hdt * p.ax[i], vy = p.vy[i] + hdt * p.ay[i],
+                 vz = p.vz[i] + hdt * p.az[i];
+    p.vx[i] = vx;
+    p.vy[i] = vy;
+    p.vz[i] = vz;
+    if (dc.eos == APR_EOS_ADIABATIC) p.u[i] += hdt * p.dudt[i];
+    p.x[i] = wrap1(dc, 0, p.x[i] + dt * vx);
+    p.y[i] = wrap1(dc, 1, p.y[i] + dt * vy);
+    p.z[i] = wrap1(dc, 2, p.z[i] + dt * vz);
+}
+
+apr_status kick_drift(apr_ctx* c, double hdt, double dt)
+{
+    if (c->n > 0) APR_LAUNCH(c, k_kick_drift, nblocks(c->n, 256), 256, c->dc, c->n, hdt, dt, c->p);
+    for (int j = 0; j < c->nsink; ++j)
+        for (int d = 0; d < 3; ++d) {
+            c->sinks[j].v[d] += hdt * c->sinks[j].a[d];
+            c->sinks[j].x[d] += dt * c->sinks[j].v[d];
+        }
+    return cuda_check(c, cudaGetLastError(), "kick and drift");
 }
 
 __global__ void k_drift(DevCfg dc, long long n, double dt, apr_particles p)
