@@ -47,6 +47,9 @@ enum {
     ST_SORT_ERR = 43,        // Morton sort: a tile's look-back gave up waiting (bounded)
     ST_SORT_TICKET = 44,     // Morton sort: tile tickets of the passes (6 words, 44..49)
     ST_ACELL_N = 50,         // lists of the cells that hold a queued particle: cell count
+    ST_SM_NSPLIT = 51,       // split/merge pass: split candidates,
+    ST_SM_FLAGS = 52,        //   1: a dead particle, 2: a merge candidate not safely inside its zone,
+    ST_SM_NCAND = 53,        //   merge candidates per level (APR_MAXLEV words, 53..60)
     ST_BINS = 16,            // merge: first slot of each level's candidates (10 words)
     ST_MERGES = 32,          // merge: merges per level (8 words)
     ST_NSTATUS = 16
@@ -223,6 +226,7 @@ struct apr_ctx {
     long long prof_attempts, prof_unc, prof_shrink;  // density-solve counters
     bool lists_fresh;         // the current lists hold every pair at the current h
     bool lists_unchecked;     // lists were built after the last read of the status words
+    bool quiet_pass;          // the last split/merge pass changed nothing
     int ncell;
     int last_shrink;
     bool tree_smem_set;       // dynamic shared memory opt-in of the pairing-tree kernel

@@ -164,20 +164,76 @@ __device__ __forceinline__ double wrap1(const DevCfg& dc, int k, double x)
 // split parents of every level: key = level for a parent, 255 otherwise.  A stable
 // sort by this key ranks the parents by (level, index), which is the order in
 // which level-by-level passes (lowest level first) append the new children.
+// the level a single zone asks for at p with every boundary shrunk by a relative
+// 1e-8: a point that reaches level l here lies inside the level-l boundary by more
+// than the rounding of any midpoint formed from it
+__device__ int region_level_inset(const DevRegion& r, double px, double py, double pz)
+{
+    constexpr double INSET = 1.0 - 1e-8;
+    int lev = 0;
+    for (int k = 0; k < r.nlev; ++k) {
+        const double R = r.R[k] * INSET;
+        bool inside;
+        if (r.shape == APR_SHAPE_SPHERE) {
+            double dx = px - r.centre[0], dy = py - r.centre[1], dz = pz - r.centre[2];
+            inside = dx * dx + dy * dy + dz * dz < R * R;
+        } else if (r.shape == APR_SHAPE_CYLINDER) {
+            double d[3] = {px - r.centre[0], py - r.centre[1], pz - r.centre[2]};
+            const int a1 = r.axis == 0 ? 1 : 0, a2 = r.axis == 2 ? 1 : 2;
+            inside = d[a1] * d[a1] + d[a2] * d[a2] < R * R;
+        } else {
+            double p = r.axis == 0 ? px : (r.axis == 1 ? py : pz);
+            inside = fabs(p - r.centre[r.axis]) < R;
+        }
+        if (inside) lev = k + 1;
+    }
+    return lev;
+}
+
+// split keys (level of a split candidate, 255 otherwise) and the pass's summary in
+// sm[]: split candidates, dead particles, and (check_merge: one convex zone, see
+// merge_shortcut_ok) merge candidates per level and whether one of them is not
+// safely inside its level's zone
 __global__ void k_split_keys(DevCfg dc, DevRegions rg, long long n, const double* __restrict__ x,
                              const double* __restrict__ y, const double* __restrict__ z,
                              const unsigned char* __restrict__ lev,
                              const unsigned char* __restrict__ flags,
-                             unsigned long long* __restrict__ key, unsigned int* __restrict__ val)
+                             unsigned long long* __restrict__ key, unsigned int* __restrict__ val,
+                             int check_merge, int* __restrict__ sm)
 {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int l = lev[i];
-    bool split = false;
-    if (l < dc.lmax && !(flags[i] & (APR_FLAG_CHANGED | APR_FLAG_FIXED | APR_FLAG_DEAD | APR_FLAG_INACTIVE)))
-        split = target_level(dc, rg, x[i], y[i], z[i], nullptr) > l;
-    key[i] = split ? (unsigned long long)l : 255ULL;
-    val[i] = (unsigned)i;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < n;
+    int l = 0;
+    bool split = false, dead = false, cand = false, loose = false;
+    if (live) {
+        l = lev[i];
+        const unsigned char f = flags[i];
+        dead = (f & APR_FLAG_DEAD) != 0;
+        const bool free_ = !(f & (APR_FLAG_CHANGED | APR_FLAG_FIXED | APR_FLAG_DEAD | APR_FLAG_INACTIVE));
+        if (l < dc.lmax && free_) split = target_level(dc, rg, x[i], y[i], z[i], nullptr) > l;
+        if (check_merge && l >= 1 && free_) {
+            cand = true;
+            int t = region_level_inset(rg.r[0], x[i], y[i], z[i]);
+            if (t > dc.lmax) t = dc.lmax;
+            loose = t < l;
+        }
+        key[i] = split ? (unsigned long long)l : 255ULL;
+        val[i] = (unsigned)i;
+    }
+    const unsigned FULL = 0xffffffffu;
+    const bool lead = (threadIdx.x & 31) == 0;
+    const unsigned ns = __popc(__ballot_sync(FULL, split));
+    const bool any_dead = __any_sync(FULL, dead), any_loose = __any_sync(FULL, loose);
+    if (lead) {
+        if (ns) atomicAdd(&sm[ST_SM_NSPLIT - ST_SM_NSPLIT], (int)ns);
+        if (any_dead || any_loose) atomicOr(&sm[ST_SM_FLAGS - ST_SM_NSPLIT], (any_dead ? 1 : 0) | (any_loose ? 2 : 0));
+    }
+    if (check_merge && __any_sync(FULL, cand)) {
+        for (int k = 1; k <= dc.lmax; ++k) {
+            const unsigned c = __popc(__ballot_sync(FULL, cand && l == k));
+            if (lead && c) atomicAdd(&sm[ST_SM_NCAND - ST_SM_NSPLIT + k], (int)c);
+        }
+    }
 }
 
 __global__ void k_split_rank(int total, const unsigned int* __restrict__ sorted,
@@ -1402,6 +1458,42 @@ apr_status split_merge_pass(apr_ctx* c, apr_counts* cnt)
     return s;
 }
 
+// The split/merge pass may skip its sorts, pairing trees and compaction when it
+// provably changes nothing (see split_merge_body).  That needs one zone of the
+// refinement kind (the set a level asks for is then the convex inside of one
+// boundary) and midpoints that are formed without a periodic wrap across the zone:
+// on every periodic axis the zone constrains, the zone lies inside the box and
+// two points inside it are closer than half the box; coordinates at most 1e6
+// times the innermost radius keep a midpoint's rounding far below the 1e-8 inset.
+static bool merge_shortcut_ok(const apr_ctx* c)
+{
+    if (c->nreg != 1 || c->cfg.level_default != 0 || c->cfg.lmax < 1) return false;
+    const apr_region& r = c->regions[0];
+    if (r.nlev < 1 || r.nlev > APR_MAXLEV) return false;
+    double Rout = 0.0, Rin = INFINITY;
+    for (int k = 0; k < r.nlev; ++k) {
+        Rout = std::max(Rout, r.R[k]);
+        Rin = std::min(Rin, r.R[k]);
+    }
+    if (!(Rin > 0.0)) return false;
+    bool axes[3] = {true, true, true};
+    if (r.shape == APR_SHAPE_SLAB) {
+        for (int k = 0; k < 3; ++k) axes[k] = k == r.axis;
+    } else if (r.shape == APR_SHAPE_CYLINDER) {
+        axes[r.axis] = false;
+    } else if (r.shape != APR_SHAPE_SPHERE) {
+        return false;
+    }
+    for (int k = 0; k < 3; ++k) {
+        const double lo = c->cfg.box_lo[k], hi = c->cfg.box_hi[k];
+        if (std::max(std::fabs(lo), std::fabs(hi)) > 1e6 * Rin) return false;
+        if (axes[k] && c->cfg.periodic[k] &&
+            (r.centre[k] - Rout < lo || r.centre[k] + Rout > hi || 4.0 * Rout >= hi - lo))
+            return false;
+    }
+    return true;
+}
+
 // host words for the merge counts and the pairing-tree status, apart from the
 // words the compaction count uses
 static int* merge_hbuf(apr_ctx* c) { return (int*)c->hbuf + 512; }
@@ -1417,18 +1509,46 @@ static apr_status split_merge_body(apr_ctx* c, apr_counts* cnt)
     if (c->n > 0) APR_LAUNCH(c, k_clear_changed, nblocks(c->n, 256), 256, c->n, c->p.flags);
     if (c->cfg.lmax >= 1 && c->n > 0) {
         const long long n = c->n;
+        // the summary costs a host synchronisation: read it while passes keep being
+        // quiet, else only every eighth pass (a busy zone rarely turns quiet)
+        const bool shortcut = merge_shortcut_ok(c) && (c->quiet_pass || c->step % 8 == 0);
+        int* sm = &W.status[ST_SM_NSPLIT];
+        cudaMemsetAsync(sm, 0, sizeof(int) * (2 + APR_MAXLEV), st);
         APR_LAUNCH(c, k_split_keys, nblocks(n, 256), 256, c->dc, rg, n, c->p.x, c->p.y, c->p.z,
-                   c->p.level, c->p.flags, W.key[0], W.val[0]);
-        s = radix_pass8(c, W.key[0], W.val[0], W.key[1], W.val[1], n, 0, &W.status[ST_BINS],
-                        c->cfg.lmax + 1);
-        if (s != APR_OK) return s;
-        cudaMemcpyAsync(c->hbuf, &W.status[ST_BINS], sizeof(int) * (c->cfg.lmax + 1),
-                        cudaMemcpyDeviceToHost, st);
-        s = cuda_check(c, cudaStreamSynchronize(st), "split count");
-        if (s != APR_OK) return s;
-        const int* bins = (const int*)c->hbuf;  // parents of level l: [bins[l], bins[l+1])
-        const int total = bins[c->cfg.lmax];
-        for (int l = 0; l < c->cfg.lmax; ++l) cnt->n_split[l] = bins[l + 1] - bins[l];
+                   c->p.level, c->p.flags, W.key[0], W.val[0], shortcut ? 1 : 0, sm);
+        int nsplit = -1;  // unknown until read
+        if (shortcut) {
+            // the pass's summary first: a pass with nothing to split, no dead particle
+            // and every merge candidate safely inside its (convex) zone changes nothing
+            // (a pair's centre of mass lies inside a convex zone with both particles),
+            // so the sort by level, the pairing trees and the compaction are skipped
+            cudaMemcpyAsync((int*)c->hbuf + 600, sm, sizeof(int) * (2 + APR_MAXLEV),
+                            cudaMemcpyDeviceToHost, st);
+            s = cuda_check(c, cudaStreamSynchronize(st), "split/merge summary");
+            if (s != APR_OK) return s;
+            const int* h = (const int*)c->hbuf + 600;
+            nsplit = h[0];
+            if (nsplit == 0 && h[1] == 0) {
+                for (int l = 1; l <= c->cfg.lmax; ++l) cnt->n_spare[l] = h[2 + l] & 1;
+                c->step += 1;
+                c->quiet_pass = true;
+                return APR_OK;
+            }
+        }
+        c->quiet_pass = false;
+        int total = 0;
+        if (nsplit != 0) {
+            s = radix_pass8(c, W.key[0], W.val[0], W.key[1], W.val[1], n, 0, &W.status[ST_BINS],
+                            c->cfg.lmax + 1);
+            if (s != APR_OK) return s;
+            cudaMemcpyAsync(c->hbuf, &W.status[ST_BINS], sizeof(int) * (c->cfg.lmax + 1),
+                            cudaMemcpyDeviceToHost, st);
+            s = cuda_check(c, cudaStreamSynchronize(st), "split count");
+            if (s != APR_OK) return s;
+            const int* bins = (const int*)c->hbuf;  // parents of level l: [bins[l], bins[l+1])
+            total = bins[c->cfg.lmax];
+            for (int l = 0; l < c->cfg.lmax; ++l) cnt->n_split[l] = bins[l + 1] - bins[l];
+        }
         if (n + total > c->cap)
             return fail(c, APR_ERR_CAPACITY, "split would exceed the bound capacity");
         if (total > 0) {

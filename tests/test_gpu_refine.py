@@ -73,6 +73,53 @@ def test_two_level_split_then_merge_bit_exact():
     assert o["level"].max() <= 2
 
 
+def _launches(g):
+    return g.profile()["launches"]
+
+
+def test_unchanging_pass_skips_its_trees_and_matches_oracle():
+    """One convex zone (a slab across a non-periodic axis): a pass in which nothing
+    can split or merge skips its sort, pairing trees and compaction (fewer launches)
+    and still reports the oracle's counts and spares; a candidate inside its zone by
+    less than the 1e-8 inset, or outside it, takes the full pass (the summary that
+    decides this is read while passes stay quiet, and every eighth pass)."""
+    w = with_velocities(apr_synth.lattice_box(12, 0.1, sphere_R=(), seed=4), 0.1)
+    w["cfg"]["periodic"] = [0, 1, 1]
+    w["cfg"]["lmax"] = 1
+    slab = lambda R: [dict(shape=apr_synth.SHAPE_SLAB, axis=0, track_sink=-1,
+                           centre=[0.5, 0.5, 0.5], R=[R])]
+    w["regions"] = slab(0.3)
+    n = len(w["p"]["x"])
+    o, g = _both(w, 4 * n)
+    g.profile_enable(True)
+
+    def both_pass():
+        l0 = _launches(g)
+        co, cg = o.split_merge(), g.split_merge()
+        for f in ("n_split", "n_merge", "n_spare"):
+            assert list(getattr(cg, f)) == list(getattr(co, f)), f
+        _same(o, g)
+        return co, _launches(g) - l0
+
+    co, _ = both_pass()
+    assert co.n_split[0] > 100
+    # nothing left to do; after a busy pass the summary is read every eighth pass
+    quiet = min(both_pass()[1] for _ in range(9))
+    # a level-1 particle just inside the boundary (by 5e-9 of R): the full pass
+    lv = o["level"]
+    d = np.abs(o["x"] - 0.5)
+    j = int(np.argmax(np.where(lv == 1, d, -1.0)))
+    R = float(d[j]) * (1.0 + 5e-9)
+    for regs in (slab(R), slab(0.25)):          # then a zone that leaves particles outside
+        o.w["regions"] = regs
+        o.regions = oracle.make_regions(regs)
+        o.nreg = len(regs)
+        g.set_regions(regs)
+        co, full = both_pass()
+        assert full > quiet
+    assert sum(co.n_merge) > 0
+
+
 def _levelled(points, level=1, h=0.01):
     w = apr_synth.lattice_box(2, 0.0, sphere_R=())
     n = len(points)
