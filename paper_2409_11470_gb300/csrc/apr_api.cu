@@ -107,6 +107,7 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.key[1] = (unsigned long long*)take(8 * C);
     w.val[0] = (unsigned int*)take(4 * C);
     w.val[1] = (unsigned int*)take(4 * C);
+    w.perm_keep = (unsigned int*)take(4 * C);
     w.hist = (unsigned int*)take(4 * 256 * ntiles * 2);
     w.sort_hist = (unsigned int*)take(4 * 256 * 6);
     w.sort_tile = (unsigned int*)take(4 * 256 * std::min<size_t>(ntiles, SORT_SWEEP_MAX_TILES) * 6);
@@ -500,6 +501,7 @@ apr_status apr_bind(apr_ctx* c, const apr_particles* p, long long n, long long c
         cuda_check(c, cudaMemsetAsync(c->W.status, 0, 4 * 64 + 8 * 16 + 256, c->stream), "bind");
     if (s != APR_OK) return s;
     c->bound = true;
+    c->order_valid = false;
     c->have_force = false;
     c->dt_valid = false;
     return APR_OK;

@@ -619,29 +619,53 @@ static apr_status tree_up(apr_ctx* c)
     return cuda_check(c, cudaGetLastError(), "tree up");
 }
 
+// The index: a Morton sort and the radix tree over it, or, while the particle set
+// and its canonical order are those of a recent sort, a refit: the same order and
+// tree topology with every node's box recomputed from the current positions.  The
+// lists are exact either way (the candidate search prunes by true bounding boxes
+// of each subtree's current members); the order only decides how tight the boxes
+// are, so a full sort comes at least every REFIT_MAX + 1 builds.
+constexpr int REFIT_MAX = 3;
+
 apr_status index_sort(apr_ctx* c)
 {
     Workspace& W = c->W;
     long long n = c->n;
     if (n <= 0) return APR_OK;
+    const bool refit = c->order_valid && c->order_n == n && c->order_age < REFIT_MAX;
     int ps = prof_begin(c, APR_PROF_SORT);
     APR_LAUNCH(c, k_quantise, nblocks(n, 256), 256, c->dc, c->p.x, c->p.y, c->p.z, c->p.level,
-                                                       n, W.xi, W.key[0], W.val[0]);
-    apr_status s = radix_sort(c, n);
-    if (s != APR_OK) return s;
+                                                       n, W.xi, refit ? nullptr : W.key[0],
+                                                       refit ? nullptr : W.val[0]);
+    apr_status s;
+    if (!refit) {
+        s = radix_sort(c, n);
+        if (s != APR_OK) return s;
+        // the order outlives the key buffers, which other passes reuse as scratch
+        cudaMemcpyAsync(W.perm_keep, W.perm, sizeof(unsigned) * (size_t)n, cudaMemcpyDeviceToDevice,
+                        c->stream);
+    }
+    W.perm = W.perm_keep;
     const bool f64 = c->cfg.precision == APR_PREC_FP64;
     APR_LAUNCH(c, k_gather_index, nblocks(n, 256), 256, n, W.perm, W.xi, c->p.h, c->p.x, c->p.y,
                                                            c->p.z, W.pk, W.sh, f64 ? W.sx : nullptr,
                                                            W.sy, W.sz);
     prof_end(c, ps);
     ps = prof_begin(c, APR_PROF_TREE);
-    if (n >= 2)
+    if (n >= 2 && !refit)
         APR_LAUNCH(c, k_tree_internal, nblocks(n - 1, 256), 256, W.skey, (int)n, W.left, W.right,
                                                                      W.parent_int, W.parent_leaf);
     s = cuda_check(c, cudaGetLastError(), "index sort");
     if (s != APR_OK) return s;
     s = tree_up(c);
     prof_end(c, ps);
+    if (refit) {
+        ++c->order_age;
+    } else {
+        c->order_valid = true;
+        c->order_n = n;
+        c->order_age = 0;
+    }
     return s;
 }
 

@@ -128,6 +128,7 @@ struct Workspace {
     unsigned int* sort_tile;  // Morton sort: per pass and tile, 256 published digit counts
     unsigned int* scan_tmp;
     unsigned int* perm;       // sorted slot -> canonical index
+    unsigned int* perm_keep;  // the last sort's order (perm points here after an index build)
     unsigned long long* skey; // sorted keys (aliases key[0] or key[1])
     int4* pk;                 // sorted lattice coordinates + level
     unsigned long long* sthr; // sorted neighbour thresholds of the current list
@@ -227,6 +228,9 @@ struct apr_ctx {
     bool lists_fresh;         // the current lists hold every pair at the current h
     bool lists_unchecked;     // lists were built after the last read of the status words
     bool quiet_pass;          // the last split/merge pass changed nothing
+    bool order_valid;         // the kept Morton order is a permutation of the current set
+    long long order_n;        //   of this many particles,
+    int order_age;            //   refitted this many times since its sort
     int ncell;
     int last_shrink;
     bool tree_smem_set;       // dynamic shared memory opt-in of the pairing-tree kernel

@@ -1431,6 +1431,7 @@ apr_status compact(apr_ctx* c, long long* removed)
     APR_LAUNCH(c, k_compact_out, nblocks(n, 256), 256, n, c->cap, f, W.uscan, tmp);
     APR_LAUNCH(c, k_compact_back, nblocks(nlive, 256), 256, nlive, c->cap, f, tmp);
     c->n = nlive;
+    c->order_valid = false;
     return cuda_check(c, cudaGetLastError(), "compaction");
 }
 
@@ -1556,6 +1557,7 @@ static apr_status split_merge_body(apr_ctx* c, apr_counts* cnt)
                        c->next_id, W.val[1], c->p);
             c->n = n + total;
             c->next_id += total;
+            c->order_valid = false;
         }
     }
     if (c->cfg.lmax >= 1 && c->n > 0) {
