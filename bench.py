@@ -319,12 +319,12 @@ def run_ours(args):
         s64.close()
 
     if rank == 0 and not args.no_e2e:
-        # the same steps through the public API with host buffers: pinned host state
-        # is copied in before and read back after every step
+        # the same steps through the C ABI with host buffers: every step uploads the
+        # pinned host state (apr_upload), steps, and downloads it (apr_download); the
+        # step length is the cached limit, read before the upload drops it
         fields = list(F64_FIELDS) + ["level", "flags", "id"]
-        host = {f: torch.empty_like(sim.t[f], device="cpu").pin_memory() for f in fields}
-        for f in fields:
-            host[f].copy_(sim.t[f])
+        host = {f: b for f, b in sim.host_buffers().items() if f in fields}
+        sim.download(host)
         st = sim.stream
         evs = []
         bi = bo = 0
@@ -334,15 +334,11 @@ def run_ours(args):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(st):
                 flush.zero_()
+            dt = sim.timestep()
             e0.record(st)
-            with torch.cuda.stream(st):
-                for f in fields:
-                    sim.t[f][:n].copy_(host[f][:n], non_blocking=True)
-            sim.step(0.0)
-            n2 = sim.n
-            with torch.cuda.stream(st):
-                for f in fields:
-                    host[f][:n2].copy_(sim.t[f][:n2], non_blocking=True)
+            sim.upload(host, n)
+            sim.step(dt)
+            n2 = sim.download(host)
             e1.record(st)
             st.synchronize()
             evs.append(e0.elapsed_time(e1))

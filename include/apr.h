@@ -196,6 +196,27 @@ apr_status apr_workspace_size(const apr_config* cfg, long long capacity, size_t*
 apr_status apr_bind(apr_ctx* ctx, const apr_particles* p, long long n, long long capacity,
                     long long next_id, void* workspace, size_t bytes);
 
+/*
+ * Host exchange of the bound particle state, for callers that keep it in host
+ * memory between steps (the paper has no counterpart: these move data only).  host:
+ * an apr_particles of HOST pointers (page-locked memory lets
+ * the copies run asynchronously); a NULL field is skipped.
+ *
+ * apr_upload copies n particles (0 <= n <= capacity) into the bound arrays on
+ * the context's stream and makes n the bound count.  The cached time-step
+ * limit and lists are dropped (call apr_timestep before uploading if the next
+ * step should use the limit of the last pass); the forces a step needs are
+ * whatever the uploaded ax..dudt hold.  APR_ERR_ARG for a bad n,
+ * APR_ERR_STATE if a given field has no bound array (bin).
+ *
+ * apr_download copies the current particles to host arrays of room for cap
+ * particles, waits for the copies, and stores the count in *n_out (may be
+ * NULL); APR_ERR_CAPACITY (nothing copied) if cap is too small.
+ */
+apr_status apr_upload(apr_ctx* ctx, const apr_particles* host, long long n);
+apr_status apr_download(apr_ctx* ctx, const apr_particles* host, long long cap,
+                        long long* n_out);
+
 /* Refinement zones and point masses (host arrays, copied). */
 apr_status apr_set_regions(apr_ctx* ctx, const apr_region* r, int nregions);
 apr_status apr_set_sinks(apr_ctx* ctx, const apr_sink* s, int nsinks);

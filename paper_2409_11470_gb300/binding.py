@@ -94,6 +94,8 @@ def _load():
         "apr_last_error": [vp],
         "apr_workspace_size": [P(Config), ll, P(C.c_size_t)],
         "apr_bind": [vp, P(Particles), ll, ll, ll, vp, C.c_size_t],
+        "apr_upload": [vp, P(Particles), ll],
+        "apr_download": [vp, P(Particles), ll, P(ll)],
         "apr_set_regions": [vp, P(Region), i32],
         "apr_set_sinks": [vp, P(Sink), i32],
         "apr_get_sinks": [vp, P(Sink), i32],
@@ -229,6 +231,28 @@ class Simulation:
                                  C.c_void_p(self.ws_ptr), self.ws_bytes), "bind")
         self.set_regions(w["regions"])
         self.set_sinks(w["sinks"])
+
+    # -- host exchange ----------------------------------------------------------
+    def host_buffers(self, pinned=True):
+        """Host tensors (page-locked by default) of the bound fields, capacity long,
+        for upload / download."""
+        return {f: self.torch.empty(self.cap, dtype=t.dtype, pin_memory=pinned)
+                for f, t in self.t.items()}
+
+    def upload(self, host, n):
+        """Copy n particles from the host tensors `host` (field -> CPU tensor; missing
+        fields are skipped) into the bound arrays (apr_upload)."""
+        parts = Particles(**{f: C.c_void_p(host[f].data_ptr()) for f in self.t if f in host})
+        self._check(lib.apr_upload(self.ctx, C.byref(parts), int(n)), "upload")
+
+    def download(self, host):
+        """Copy the current particles into the host tensors `host` (apr_download);
+        returns the particle count."""
+        cap = min(int(t.numel()) for t in host.values())
+        parts = Particles(**{f: C.c_void_p(host[f].data_ptr()) for f in self.t if f in host})
+        n = C.c_longlong(0)
+        self._check(lib.apr_download(self.ctx, C.byref(parts), cap, C.byref(n)), "download")
+        return n.value
 
     # -- plumbing ---------------------------------------------------------------
     def _check(self, st, what):

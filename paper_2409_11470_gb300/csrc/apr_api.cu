@@ -507,6 +507,73 @@ apr_status apr_bind(apr_ctx* c, const apr_particles* p, long long n, long long c
     return APR_OK;
 }
 
+// the fields of an apr_particles with their element sizes (bin last, optional)
+static int particle_fields(const apr_particles* p, void** ptr, size_t* size)
+{
+    double* const* d[] = {&p->x,   &p->y,     &p->z,  &p->vx, &p->vy, &p->vz,
+                          &p->u,   &p->h,     &p->rho, &p->omega, &p->ax, &p->ay,
+                          &p->az,  &p->dudt,  &p->vsig, &p->dnn, &p->pres, &p->cs};
+    int k = 0;
+    for (double* const* q : d) {
+        ptr[k] = *q;
+        size[k++] = sizeof(double);
+    }
+    ptr[k] = p->level;
+    size[k++] = 1;
+    ptr[k] = p->flags;
+    size[k++] = 1;
+    ptr[k] = p->id;
+    size[k++] = sizeof(unsigned long long);
+    ptr[k] = p->bin;
+    size[k++] = 1;
+    return k;
+}
+
+apr_status apr_upload(apr_ctx* c, const apr_particles* host, long long n)
+{
+    if (!c || !host) return APR_ERR_ARG;
+    if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    if (n < 0 || n > c->cap) return fail(c, APR_ERR_ARG, "upload needs 0 <= n <= capacity");
+    void *hp[24], *dp[24];
+    size_t sz[24];
+    const int k = particle_fields(host, hp, sz);
+    particle_fields(&c->p, dp, sz);
+    for (int j = 0; j < k; ++j) {
+        if (!hp[j] || n == 0) continue;
+        if (!dp[j]) return fail(c, APR_ERR_STATE, "upload: no bound array for a given field");
+        apr_status s = cuda_check(c, cudaMemcpyAsync(dp[j], hp[j], sz[j] * (size_t)n,
+                                                     cudaMemcpyHostToDevice, c->stream),
+                                  "upload");
+        if (s != APR_OK) return s;
+    }
+    if (n != c->n) c->order_valid = false;  // the kept order is a permutation of n particles
+    c->n = n;
+    c->dt_valid = false;
+    c->lists_fresh = false;
+    return APR_OK;
+}
+
+apr_status apr_download(apr_ctx* c, const apr_particles* host, long long cap, long long* n_out)
+{
+    if (!c || !host) return APR_ERR_ARG;
+    if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    const long long n = c->n;
+    if (n_out) *n_out = n;
+    if (n > cap) return fail(c, APR_ERR_CAPACITY, "download: the host arrays hold fewer than n");
+    void *hp[24], *dp[24];
+    size_t sz[24];
+    const int k = particle_fields(host, hp, sz);
+    particle_fields(&c->p, dp, sz);
+    for (int j = 0; j < k; ++j) {
+        if (!hp[j] || !dp[j] || n == 0) continue;
+        apr_status s = cuda_check(c, cudaMemcpyAsync(hp[j], dp[j], sz[j] * (size_t)n,
+                                                     cudaMemcpyDeviceToHost, c->stream),
+                                  "download");
+        if (s != APR_OK) return s;
+    }
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "download");
+}
+
 apr_status apr_set_regions(apr_ctx* c, const apr_region* r, int nregions)
 {
     if (!c || nregions < 0 || nregions > APR_MAXREG || (nregions > 0 && !r)) return APR_ERR_ARG;

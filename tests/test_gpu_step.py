@@ -102,3 +102,38 @@ def test_full_size_sod_sampled():
     scale = o["pres"][a_o] / (o["rho"][a_o] * o["h"][a_o])
     err = np.abs(g.get("ax")[a_g] - o["ax"][a_o]) / (np.abs(o["ax"][a_o]) + scale)
     assert err.max() < 2e-4
+
+
+def test_host_exchange_round_trip_and_step():
+    """apr_download / apr_upload: the state survives a round trip through host
+    buffers, and a step taken after an upload equals the device-resident one bit
+    for bit (with the same step length)."""
+    import paper_2409_11470_gb300.binding as B
+    w = apr_synth.sod(8)
+    cap = 4 * len(w["p"]["x"])
+    a = sim(w, "fp32", capacity=cap)
+    b = sim(w, "fp32", capacity=cap)
+    a.init()
+    b.init()
+    host = b.host_buffers()
+    n = b.download(host)
+    assert n == b.n
+    for f in ("x", "vx", "h", "rho", "ax", "level", "flags", "id"):
+        assert np.array_equal(host[f][:n].numpy().view(b.get(f).dtype), b.get(f)), f
+    for _ in range(2):
+        dt = a.timestep()
+        assert b.timestep() == dt
+        b.upload(host, b.n)
+        a.step(dt)
+        b.step(dt)
+        n = b.download(host)
+        assert n == a.n
+        for f in ("x", "vx", "u", "rho", "h", "ax", "id"):
+            assert np.array_equal(a.get(f), b.get(f)), f
+    small = {f: t[:3] for f, t in host.items()}
+    with pytest.raises(B.AprError) as e:
+        b.download(small)
+    assert e.value.status == 2
+    with pytest.raises(B.AprError) as e:
+        b.upload(host, cap + 1)
+    assert e.value.status == 1
