@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(ADJ_THREADS)
                   double* __restrict__ rho_out, double* __restrict__ partials)
 {
     double jsum = 0.0;
-    const double scale = dc.m0 / dc.knorm_inv;
+    const double scale = dc.m0_knorm;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < nt;
          s += (long long)gridDim.x * blockDim.x) {
         const AdjSlot<R> xa = X[s];
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(ADJ_THREADS)
             rv.add(E[b] * df * h4 * rinv, d);
         }
     }
-    const double scale = dc.m0 / dc.knorm_inv;
+    const double scale = dc.m0_knorm;
     const double ha = (double)xa.hinv, ha4 = (ha * ha) * (ha * ha);
     const double e2 = 2.0 * (double)ea, mua = (double)xa.mu;
     double g[3];

@@ -260,6 +260,7 @@ static apr_status check_cfg(const apr_config* cfg, DevCfg* dc, std::string* why)
     dc->rsep_fac = cfg->rsep_fac;
     dc->dnn_cap = cfg->dnn_cap;
     dc->m0 = cfg->m0;
+    dc->m0_knorm = cfg->m0 / dc->knorm_inv;
     dc->lmax = cfg->lmax;
     dc->seed = cfg->seed;
     dc->ccour = cfg->ccour;

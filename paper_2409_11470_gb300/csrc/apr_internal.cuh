@@ -96,6 +96,7 @@ struct DevCfg {
     int prof;                  // count pair evaluations into Workspace::counters
     int kernel;                // APR_KERNEL_M4 or APR_KERNEL_WENDLAND_C2
     double knorm_inv;          // W = f(q) / (knorm_inv h^3): pi (M4), 16 pi / 21 (Wendland C2)
+    double m0_knorm;           // m0 / knorm_inv, the factor of the pair sums
     int level_default;         // 0: zones refine; L >= 1: zones derefine from level L
 };
 

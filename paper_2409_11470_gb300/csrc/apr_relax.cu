@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(128)
         gy.add(wgt * (R)ay[j]);
         gz.add(wgt * (R)az[j]);
     }
-    const double scale = dc.m0 / dc.knorm_inv;
+    const double scale = dc.m0_knorm;
     aref[3 * (long long)i] = scale * ((double)gx.s - (double)gx.c);
     aref[3 * (long long)i + 1] = scale * ((double)gy.s - (double)gy.c);
     aref[3 * (long long)i + 2] = scale * ((double)gz.s - (double)gz.c);

@@ -48,6 +48,13 @@ __device__ __forceinline__ void density_term(R r2, R hinv, R r2max, int levb, Ac
 }
 
 template <typename R>
+__device__ __forceinline__ R round_down(double x);
+template <>
+__device__ __forceinline__ float round_down<float>(double x) { return __double2float_rd(x); }
+template <>
+__device__ __forceinline__ double round_down<double>(double x) { return x; }
+
+template <typename R>
 __device__ __forceinline__ R rel_r2(const DevCfg& dc, const int d[3], const double* sx,
                                     const double* sy, const double* sz, int a, int b);
 template <>
@@ -112,6 +119,10 @@ __global__ void __launch_bounds__(128, density_min_blocks<R>())
     const R target = R(dc.knorm_inv) * mua * R(dc.hfact * dc.hfact * dc.hfact);
     const unsigned int* col = nbr + a;  // this particle's list: col[k * cap]
     R h = (R)hlist;
+    // the list's reach (float: rounded down, so that h stays inside it) and the
+    // convergence tolerance at the iteration's precision
+    const R hreach = round_down<R>(reach * hlist);
+    const R tol = (R)dc.nr_tol;
     R lo = R(0), hi = R(0);  // bracket of the root; hi == 0: none yet
     R D = R(0);              // sum mu_b (3 f + q f') at the last evaluated h
     bool conv = false, uncovered = false;
@@ -123,9 +134,21 @@ __global__ void __launch_bounds__(128, density_min_blocks<R>())
         Acc<R> S, T;
         const bool first_pass = it == 0;
         int k = 0;
+        // the next four list entries are loaded one step ahead (clamped to the
+        // last entry), so that only the gathers of a step wait on memory
+        unsigned int n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+        if (m >= 4) {
+            n0 = col[0];
+            n1 = col[cap];
+            n2 = col[2 * cap];
+            n3 = col[3 * cap];
+        }
         for (; k + 4 <= m; k += 4) {
-            const int b0 = (int)col[(long long)k * cap], b1 = (int)col[(long long)(k + 1) * cap];
-            const int b2 = (int)col[(long long)(k + 2) * cap], b3 = (int)col[(long long)(k + 3) * cap];
+            const int b0 = (int)n0, b1 = (int)n1, b2 = (int)n2, b3 = (int)n3;
+            n0 = col[(long long)min(k + 4, m - 1) * cap];
+            n1 = col[(long long)min(k + 5, m - 1) * cap];
+            n2 = col[(long long)min(k + 6, m - 1) * cap];
+            n3 = col[(long long)min(k + 7, m - 1) * cap];
             const int4 p0 = pk[b0], p1 = pk[b1], p2 = pk[b2], p3 = pk[b3];
             int d0[3], d1[3], d2[3], d3[3];
             const unsigned long long q0 = lattice_r2(dc, pa, p0, d0), q1 = lattice_r2(dc, pa, p1, d1);
@@ -162,12 +185,12 @@ __global__ void __launch_bounds__(128, density_min_blocks<R>())
             hn = hi > R(0) ? R(0.5) * (lo + hi) : h * R(1.25992105);
         if (hn > R(2) * h) hn = R(2) * h;
         if (hn < R(0.5) * h) hn = R(0.5) * h;
-        const bool done = fabs((double)(hn - h)) <= dc.nr_tol * (double)h;
-        if ((double)hn > reach * hlist) {
+        const bool done = fabs(hn - h) <= tol * h;
+        if (hn > hreach) {
             // the root lies beyond this list's reach: stop at the reach; the host
             // rebuilds the lists there and the iteration continues (growth is
             // bounded per attempt, so lists stay short)
-            h = (R)(reach * hlist);
+            h = hreach;
             uncovered = true;
             break;
         }
@@ -454,8 +477,17 @@ __global__ void __launch_bounds__(128, force_min_blocks<R>())
     const int m = ncnt[a];
     const unsigned int* col = nbr + a;
     int k = 0;
+    // the next two list entries are loaded one step ahead (clamped to the last
+    // entry), so that only the gathers of a step wait on memory
+    unsigned int n0 = 0, n1 = 0;
+    if (m >= 2) {
+        n0 = col[0];
+        n1 = col[cap];
+    }
     for (; k + 2 <= m; k += 2) {
-        const int b0 = (int)col[(long long)k * cap], b1 = (int)col[(long long)(k + 1) * cap];
+        const int b0 = (int)n0, b1 = (int)n1;
+        n0 = col[(long long)min(k + 2, m - 1) * cap];
+        n1 = col[(long long)min(k + 3, m - 1) * cap];
         const int4 p0 = pk[b0], p1 = pk[b1];
         const F4<R> A0 = ld4<R>(Abuf, b0), V0 = ld4<R>(Vbuf, b0), B0 = ld4<R>(Bbuf, b0);
         const F4<R> A1 = ld4<R>(Abuf, b1), V1 = ld4<R>(Vbuf, b1), B1 = ld4<R>(Bbuf, b1);
@@ -474,7 +506,7 @@ __global__ void __launch_bounds__(128, force_min_blocks<R>())
         force_pair<KT, R>(dc, A, d, Ab, Vb, Bb, adiabatic, cond, fx, fy, fz, du, vsig, npair);
     }
     if (dc.prof) atomicAdd(&counters[APR_PROF_FORCE], (unsigned long long)npair);
-    const double scale = dc.m0 / dc.knorm_inv;
+    const double scale = dc.m0_knorm;
     const unsigned i = perm[a];
     ax_out[i] = scale * ((double)fx.s - (double)fx.c);
     ay_out[i] = scale * ((double)fy.s - (double)fy.c);
