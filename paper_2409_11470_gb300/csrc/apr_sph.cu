@@ -21,13 +21,17 @@ namespace apr {
 
 // ----------------------------------------------------------------- density
 
-// exact lattice separation (minimum image) and its square
-__device__ __forceinline__ unsigned long long lattice_r2(const DevCfg& dc, const int4& pa,
-                                                         const int4& pb, int d[3])
+// exact lattice separation (minimum image)
+__device__ __forceinline__ void lattice_d(const DevCfg& dc, const int4& pa, const int4& pb, int d[3])
 {
     d[0] = min_image32(pa.x - pb.x, dc.periodic[0], (int)dc.Lint[0]);
     d[1] = min_image32(pa.y - pb.y, dc.periodic[1], (int)dc.Lint[1]);
     d[2] = min_image32(pa.z - pb.z, dc.periodic[2], (int)dc.Lint[2]);
+}
+
+// its exact square
+__device__ __forceinline__ unsigned long long lattice_sq(const int d[3])
+{
     return (unsigned long long)((long long)d[0] * d[0]) + (unsigned long long)((long long)d[1] * d[1]) +
            (unsigned long long)((long long)d[2] * d[2]);
 }
@@ -151,9 +155,14 @@ __global__ void __launch_bounds__(128, density_min_blocks<R>())
             n3 = col[(long long)min(k + 7, m - 1) * cap];
             const int4 p0 = pk[b0], p1 = pk[b1], p2 = pk[b2], p3 = pk[b3];
             int d0[3], d1[3], d2[3], d3[3];
-            const unsigned long long q0 = lattice_r2(dc, pa, p0, d0), q1 = lattice_r2(dc, pa, p1, d1);
-            const unsigned long long q2 = lattice_r2(dc, pa, p2, d2), q3 = lattice_r2(dc, pa, p3, d3);
+            lattice_d(dc, pa, p0, d0);
+            lattice_d(dc, pa, p1, d1);
+            lattice_d(dc, pa, p2, d2);
+            lattice_d(dc, pa, p3, d3);
             if (first_pass) {
+                // the nearest lattice neighbour, on the first pass only
+                const unsigned long long q0 = lattice_sq(d0), q1 = lattice_sq(d1);
+                const unsigned long long q2 = lattice_sq(d2), q3 = lattice_sq(d3);
                 best = q0 < best ? q0 : best;
                 best = q1 < best ? q1 : best;
                 best = q2 < best ? q2 : best;
@@ -168,8 +177,11 @@ __global__ void __launch_bounds__(128, density_min_blocks<R>())
             const int b = (int)col[(long long)k * cap];
             const int4 pb = pk[b];
             int d[3];
-            const unsigned long long q = lattice_r2(dc, pa, pb, d);
-            if (first_pass) best = q < best ? q : best;
+            lattice_d(dc, pa, pb, d);
+            if (first_pass) {
+                const unsigned long long q = lattice_sq(d);
+                best = q < best ? q : best;
+            }
             density_term<KT, R>(rel_r2<R>(dc, d, sx, sy, sz, a, b), hinv, r2max, pb.w, S, T, npair);
         }
         const R g = (S.s + mua) - target;           // pi h^3 (rho_sum - rho_h) / m0
