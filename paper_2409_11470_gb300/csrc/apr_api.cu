@@ -2,6 +2,7 @@
 // checks, the caller-owned workspace layout, and the host-side order of the
 // passes of one step (Sec. 2.6: zones -> split ascending -> merge descending
 // -> density -> forces, inside a kick-drift-kick update).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -530,6 +531,77 @@ static int particle_fields(const apr_particles* p, void** ptr, size_t* size)
     return k;
 }
 
+// Host exchange.  Fields whose host arrays are page-locked (hence visible to the
+// device) move in one kernel that reads or writes host memory directly: a copy
+// call per field costs more than its bytes at these sizes.  Other host arrays go
+// through one cudaMemcpyAsync each.
+constexpr int COPY_FIELDS = 24;
+struct FieldCopy {
+    const unsigned char* src[COPY_FIELDS];
+    unsigned char* dst[COPY_FIELDS];
+    unsigned long long bytes[COPY_FIELDS];
+    int n;
+};
+
+__global__ void __launch_bounds__(256) k_copy_fields(FieldCopy f)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (int j = 0; j < f.n; ++j) {
+        const unsigned char* src = f.src[j];
+        unsigned char* dst = f.dst[j];
+        const long long nb = (long long)f.bytes[j];
+        const bool vec = ((reinterpret_cast<size_t>(src) | reinterpret_cast<size_t>(dst)) & 15) == 0;
+        const long long nv = vec ? nb / 16 : 0;  // 16-byte words, then single bytes
+        for (long long i = t; i < nv; i += stride)
+            reinterpret_cast<int4*>(dst)[i] = reinterpret_cast<const int4*>(src)[i];
+        for (long long i = 16 * nv + t; i < nb; i += stride) dst[i] = src[i];
+    }
+}
+
+// the device's address of host memory, or nullptr if it is not page-locked
+static void* host_device_ptr(const void* h)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// k fields of n particles between host (hp) and device (dp) arrays
+static apr_status copy_fields(apr_ctx* c, void* const* hp, void* const* dp, const size_t* sz, int k,
+                              long long n, bool to_device, const char* what)
+{
+    FieldCopy f;
+    f.n = 0;
+    long long total = 0;
+    for (int j = 0; j < k; ++j) {
+        if (!hp[j] || !dp[j] || n == 0) continue;
+        const size_t bytes = sz[j] * (size_t)n;
+        void* hd = host_device_ptr(hp[j]);
+        if (hd && f.n < COPY_FIELDS) {
+            f.src[f.n] = (const unsigned char*)(to_device ? hd : dp[j]);
+            f.dst[f.n] = (unsigned char*)(to_device ? dp[j] : hd);
+            f.bytes[f.n++] = bytes;
+            total += (long long)bytes;
+            continue;
+        }
+        apr_status s = cuda_check(
+            c,
+            cudaMemcpyAsync(to_device ? dp[j] : hp[j], to_device ? hp[j] : dp[j], bytes,
+                            to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, c->stream),
+            what);
+        if (s != APR_OK) return s;
+    }
+    if (f.n == 0) return APR_OK;
+    const long long words = total / 16 + 1;
+    const int grid = (int)std::min<long long>(152 * 8, (words + 255) / 256);
+    APR_LAUNCH(c, k_copy_fields, grid, 256, f);
+    return cuda_check(c, cudaGetLastError(), what);
+}
+
 apr_status apr_upload(apr_ctx* c, const apr_particles* host, long long n)
 {
     if (!c || !host) return APR_ERR_ARG;
@@ -539,14 +611,11 @@ apr_status apr_upload(apr_ctx* c, const apr_particles* host, long long n)
     size_t sz[24];
     const int k = particle_fields(host, hp, sz);
     particle_fields(&c->p, dp, sz);
-    for (int j = 0; j < k; ++j) {
-        if (!hp[j] || n == 0) continue;
-        if (!dp[j]) return fail(c, APR_ERR_STATE, "upload: no bound array for a given field");
-        apr_status s = cuda_check(c, cudaMemcpyAsync(dp[j], hp[j], sz[j] * (size_t)n,
-                                                     cudaMemcpyHostToDevice, c->stream),
-                                  "upload");
-        if (s != APR_OK) return s;
-    }
+    for (int j = 0; j < k; ++j)
+        if (hp[j] && n > 0 && !dp[j])
+            return fail(c, APR_ERR_STATE, "upload: no bound array for a given field");
+    apr_status s = copy_fields(c, hp, dp, sz, k, n, true, "upload");
+    if (s != APR_OK) return s;
     if (n != c->n) c->order_valid = false;  // the kept order is a permutation of n particles
     c->n = n;
     c->dt_valid = false;
@@ -565,13 +634,8 @@ apr_status apr_download(apr_ctx* c, const apr_particles* host, long long cap, lo
     size_t sz[24];
     const int k = particle_fields(host, hp, sz);
     particle_fields(&c->p, dp, sz);
-    for (int j = 0; j < k; ++j) {
-        if (!hp[j] || !dp[j] || n == 0) continue;
-        apr_status s = cuda_check(c, cudaMemcpyAsync(hp[j], dp[j], sz[j] * (size_t)n,
-                                                     cudaMemcpyDeviceToHost, c->stream),
-                                  "download");
-        if (s != APR_OK) return s;
-    }
+    apr_status s = copy_fields(c, hp, dp, sz, k, n, false, "download");
+    if (s != APR_OK) return s;
     return cuda_check(c, cudaStreamSynchronize(c->stream), "download");
 }
 

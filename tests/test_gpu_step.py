@@ -104,10 +104,12 @@ def test_full_size_sod_sampled():
     assert err.max() < 2e-4
 
 
-def test_host_exchange_round_trip_and_step():
+@pytest.mark.parametrize("pinned", ["pinned", "pageable", "mixed"])
+def test_host_exchange_round_trip_and_step(pinned):
     """apr_download / apr_upload: the state survives a round trip through host
     buffers, and a step taken after an upload equals the device-resident one bit
-    for bit (with the same step length)."""
+    for bit (with the same step length).  Page-locked host arrays move in one
+    kernel, pageable ones by copy calls, and a call may mix the two."""
     import paper_2409_11470_gb300.binding as B
     w = apr_synth.sod(8)
     cap = 4 * len(w["p"]["x"])
@@ -115,7 +117,11 @@ def test_host_exchange_round_trip_and_step():
     b = sim(w, "fp32", capacity=cap)
     a.init()
     b.init()
-    host = b.host_buffers()
+    host = b.host_buffers(pinned=pinned != "pageable")
+    if pinned == "mixed":
+        for f in ("x", "level", "id"):
+            host[f] = host[f].clone()  # pageable copies of a few fields
+            assert not host[f].is_pinned()
     n = b.download(host)
     assert n == b.n
     for f in ("x", "vx", "h", "rho", "ax", "level", "flags", "id"):
