@@ -1658,11 +1658,14 @@ static apr_status reduce_readback_n(apr_ctx* c, int nblk, int nv, unsigned int m
     return APR_OK;
 }
 
-// blocks of a fixed-shape reduction over n particles: about four particles per
-// thread, so that the per-block shuffled sums stay a small share of the work
+// blocks of a fixed-shape reduction over n particles: one to eight per SM (the
+// same number on every SM, so that none takes twice the FP64 work of another), with
+// at least about four particles per thread so that the per-block shuffled sums stay
+// a small share of the work
 static int red_grid(long long n)
 {
-    return (int)std::min<long long>(RED_BLOCKS, std::max<long long>(1, (n + 1023) / 1024));
+    const long long per_sm = std::max<long long>(1, std::min<long long>(8, n / (152LL * 256 * 4)));
+    return (int)std::min<long long>(RED_BLOCKS, 152 * per_sm);
 }
 
 __global__ void __launch_bounds__(256) k_stats(DevCfg dc, long long n, apr_particles p,
