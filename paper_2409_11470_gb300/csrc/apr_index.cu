@@ -1043,8 +1043,12 @@ __device__ __forceinline__ void flush_batch(int nb, bool wrapb, long long vlane,
                                            m);
 }
 
+// threads per block of the cell list kernel (a warp per cell; a block's cells are
+// consecutive in Morton order and share candidate particles in L1)
+constexpr int LIST_THREADS = 128;
+
 template <int PX, int PY, int PZ, int SYM>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(LIST_THREADS)
     k_lists(DevCfg dc, const int* __restrict__ ncell_dev, int n, long long cap,
             const int* __restrict__ cell_first,
             const int* __restrict__ cell_cnt, const int2* __restrict__ cand,
@@ -1053,10 +1057,10 @@ __global__ void __launch_bounds__(128)
             unsigned int* __restrict__ nbr, int* __restrict__ ncnt, int* __restrict__ point_q,
             int* status, int graceful)
 {
-    __shared__ int4 cq[4][LIST_BUF];
-    __shared__ float4 cf[4][LIST_BUF];
-    __shared__ unsigned long long ct[4][LIST_BUF];
-    __shared__ unsigned int cr[4][LIST_BUF];
+    __shared__ int4 cq[LIST_THREADS / 32][LIST_BUF];
+    __shared__ float4 cf[LIST_THREADS / 32][LIST_BUF];
+    __shared__ unsigned long long ct[LIST_THREADS / 32][LIST_BUF];
+    __shared__ unsigned int cr[LIST_THREADS / 32][LIST_BUF];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -1281,10 +1285,11 @@ static void launch_lists(apr_ctx* c, const int* ncell_dev, int n, bool graceful,
     Workspace& W = c->W;
     const int mask = (c->dc.periodic[0] ? 1 : 0) | (c->dc.periodic[1] ? 2 : 0) |
                      (c->dc.periodic[2] ? 4 : 0);
-    const int grid = min(nblocks((long long)n * 32, 128), 152 * 16);
+    const int grid = min(nblocks((long long)n * 32, LIST_THREADS), 152 * 16 * 128 / LIST_THREADS);
 #define APR_LISTS_CASE(M, X, Y, Z)                                                                   \
     case M:                                                                                          \
-        APR_LAUNCH(c, (k_lists<X, Y, Z, SYM>), grid, 128, c->dc, ncell_dev, n, c->cap, cell_first,   \
+        APR_LAUNCH(c, (k_lists<X, Y, Z, SYM>), grid, LIST_THREADS, c->dc, ncell_dev, n, c->cap,     \
+                   cell_first,                                                                       \
                    cell_cnt, W.cand, W.ncand, W.pk, W.sthr, W.sreach, W.nbr, W.ncnt, W.point_q,      \
                    W.status, graceful ? 1 : 0);                                                      \
         APR_LAUNCH(c, (k_lists_point<X, Y, Z, SYM>), 152 * 4, 128, c->dc, &W.status[ST_POINT_N],     \

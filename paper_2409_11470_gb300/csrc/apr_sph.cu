@@ -80,15 +80,22 @@ __device__ __forceinline__ double rel_r2<double>(const DevCfg& dc, const int*, c
 // Newton-Raphson on g(h) with a bracket over this particle's (symmetric,
 // reach-scaled) list; the first pass also finds the nearest lattice neighbour.
 // Four list entries are loaded ahead so that several gathers are in flight.
+// threads per block of the pair kernels (one particle each): a block's particles
+// are consecutive in Morton order and share most of their neighbours in L1 (float
+// force: 256 measured 2-3% faster than 128 and 512 on the shock tube; density: 128)
+constexpr int DENSITY_THREADS = 128;
+template <typename R>
+__host__ __device__ constexpr int force_threads() { return sizeof(R) == 4 ? 256 : 128; }
+
 // resident blocks per SM asked of the compiler: the float kernels are bound by
 // gather latency, so more warps in flight pay; the double kernels keep their registers
 template <typename R>
-constexpr int density_min_blocks() { return sizeof(R) == 4 ? 8 : 1; }
+constexpr int density_min_blocks() { return sizeof(R) == 4 ? 1024 / DENSITY_THREADS : 1; }
 template <typename R>
-constexpr int force_min_blocks() { return sizeof(R) == 4 ? 8 : 1; }
+constexpr int force_min_blocks() { return sizeof(R) == 4 ? 1024 / force_threads<R>() : 1; }
 
 template <typename R, int KT>
-__global__ void __launch_bounds__(128, density_min_blocks<R>())
+__global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
     k_density(DevCfg dc, long long n, long long cap, double reach, const int4* __restrict__ pk,
               const double* __restrict__ sh, const unsigned long long* __restrict__ sthr,
               const unsigned int* __restrict__ nbr, const int* __restrict__ ncnt,
@@ -273,7 +280,7 @@ apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv, con
         const double reach = DENSITY_REACH;
         const bool c2 = c->cfg.kernel == APR_KERNEL_WENDLAND_C2;
 #define APR_DENSITY(R, KT)                                                                           \
-    APR_LAUNCH(c, (k_density<R, KT>), nblocks(work, 128), 128, c->dc, n, c->cap, reach, W.pk, W.sh,  \
+    APR_LAUNCH(c, (k_density<R, KT>), nblocks(work, DENSITY_THREADS), DENSITY_THREADS, c->dc, n, c->cap, reach, W.pk, W.sh,  \
                W.sthr, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm, c->p.x, c->p.y, c->p.u, c->p.h,    \
                c->p.rho, c->p.omega, c->p.dnn, c->p.pres, c->p.cs, W.status, W.counters, active,   \
                nactive, W.retry_q[out_q], &W.status[ST_RETRY_N + out_q])
@@ -451,7 +458,7 @@ __device__ __forceinline__ void force_pair(const DevCfg& dc, const ForceSelf<R>&
 }
 
 template <typename R, int KT>
-__global__ void __launch_bounds__(128, force_min_blocks<R>())
+__global__ void __launch_bounds__(force_threads<R>(), force_min_blocks<R>())
     k_force(DevCfg dc, long long n, long long cap, const int4* __restrict__ pk,
             const void* __restrict__ Abuf, const void* __restrict__ Vbuf,
             const void* __restrict__ Bbuf, const unsigned int* __restrict__ nbr,
@@ -536,7 +543,7 @@ apr_status force_pass(apr_ctx* c, const int* active, long long nactive)
     const int ps = prof_begin(c, APR_PROF_FORCE);
     const bool c2 = c->cfg.kernel == APR_KERNEL_WENDLAND_C2;
 #define APR_FORCE(R, KT, A, V, B)                                                                    \
-    APR_LAUNCH(c, (k_force<R, KT>), nblocks(work, 128), 128, c->dc, n, c->cap, W.pk, A, V, B, W.nbr, \
+    APR_LAUNCH(c, (k_force<R, KT>), nblocks(work, force_threads<R>()), force_threads<R>(), c->dc, n, c->cap, W.pk, A, V, B, W.nbr, \
                W.ncnt, W.sx, W.sy, W.sz, W.perm, c->p.ax, c->p.ay, c->p.az, c->p.dudt, c->p.vsig,   \
                W.counters, active, nactive)
     if (c->cfg.precision == APR_PREC_FP64) {
