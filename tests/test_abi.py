@@ -45,3 +45,6 @@ def test_null_arguments_rejected():
     assert B.lib.apr_create(None, None, None) == 1
     assert B.lib.apr_workspace_size(None, 10, None) == 1
     assert B.lib.apr_sph_density(None, None) == 1
+    parts = B.Particles()
+    assert B.lib.apr_upload(None, C.byref(parts), 0) == 1
+    assert B.lib.apr_download(None, C.byref(parts), 0, None) == 1
