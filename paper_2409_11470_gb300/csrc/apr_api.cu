@@ -134,6 +134,7 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.parent_int = (int*)take(4 * C);
     w.parent_leaf = (int*)take(4 * C);
     w.visit = (int*)take(4 * C);
+    w.nlocal = (unsigned char*)take(C);
     w.nlo = (int4*)take(16 * C);
     w.nhi = (int4*)take(16 * C);
     w.nhmax = (double*)take(8 * C);

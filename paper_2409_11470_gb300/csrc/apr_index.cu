@@ -503,9 +503,14 @@ __device__ __forceinline__ int prefix_len(const unsigned long long* __restrict__
     return __clzll(a ^ b);
 }
 
+// leaves per block of the bottom-up pass (k_tree_up): a node whose leaf range lies
+// inside one such block is merged with a shared-memory arrival counter
+constexpr int TREE_UP_T = 1024;
+
 __global__ void k_tree_internal(const unsigned long long* __restrict__ k, int n,
                                 int* __restrict__ left, int* __restrict__ right,
-                                int* __restrict__ parent_int, int* __restrict__ parent_leaf)
+                                int* __restrict__ parent_int, int* __restrict__ parent_leaf,
+                                unsigned char* __restrict__ nlocal)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
@@ -525,6 +530,7 @@ __global__ void k_tree_internal(const unsigned long long* __restrict__ k, int n,
     } while (t > 1);
     int g = i + s * d + (d < 0 ? -1 : 0);
     int lo = min(i, j), hi = max(i, j);
+    nlocal[i] = lo / TREE_UP_T == hi / TREE_UP_T;
     int L = (lo == g) ? ~g : g;
     int R = (hi == g + 1) ? ~(g + 1) : g + 1;
     left[i] = L;
@@ -575,14 +581,36 @@ __device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v
     return old;
 }
 
-// bottom-up: the second child to arrive at a node merges both children
-__global__ void k_tree_up(int n, const int4* __restrict__ pk, const double* __restrict__ sh,
-                          const int* __restrict__ left, const int* __restrict__ right,
-                          const int* __restrict__ parent_int, const int* __restrict__ parent_leaf,
-                          int* __restrict__ visit, int4* nlo, int4* nhi, double* nhmax,
-                          int* status)
+__device__ __forceinline__ unsigned atom_add_acq_rel_cta_shared(unsigned* p, unsigned v)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned old;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;"
+                 : "=r"(old)
+                 : "r"(a), "r"(v)
+                 : "memory");
+    return old;
+}
+
+// bottom-up: the second child to arrive at a node merges both children.  A block
+// takes TREE_UP_T consecutive leaves; a node whose leaf range lies inside them
+// (nlocal, from the build) is reached only by this block's threads and counts
+// arrivals in shared memory, the others in global memory.  Its index is an end of
+// its range, so it falls inside the block's index window.
+__global__ void __launch_bounds__(TREE_UP_T)
+    k_tree_up(int n, const int4* __restrict__ pk, const double* __restrict__ sh,
+              const int* __restrict__ left, const int* __restrict__ right,
+              const int* __restrict__ parent_int, const int* __restrict__ parent_leaf,
+              const unsigned char* __restrict__ nlocal, int* __restrict__ visit, int4* nlo,
+              int4* nhi, double* nhmax, int* status)
+{
+    __shared__ unsigned vis[TREE_UP_T];
+    __shared__ unsigned char loc[TREE_UP_T];
+    const int b0 = blockIdx.x * TREE_UP_T;
+    vis[threadIdx.x] = 0u;
+    loc[threadIdx.x] = b0 + (int)threadIdx.x < n - 1 ? nlocal[b0 + threadIdx.x] : 0;
+    __syncthreads();
+    const int s = b0 + threadIdx.x;
     if (s >= n || n < 2) return;
     int node = parent_leaf[s];
     for (int depth = 0;; ++depth) {
@@ -591,8 +619,12 @@ __global__ void k_tree_up(int n, const int4* __restrict__ pk, const double* __re
             return;
         }
         // release: this thread's child data (stored just before) is visible to the
-        // sibling's thread; acquire: the sibling's child data is visible here
-        if (atom_add_acq_rel_u32((unsigned*)&visit[node], 1u) == 0u) return;
+        // sibling's thread; acquire: the sibling's child data is visible here (the
+        // same block's threads for a local node, any thread for the others)
+        const bool local = node >= b0 && node < b0 + TREE_UP_T && loc[node - b0];
+        const unsigned old = local ? atom_add_acq_rel_cta_shared(&vis[node - b0], 1u)
+                                   : atom_add_acq_rel_u32((unsigned*)&visit[node], 1u);
+        if (old == 0u) return;
         NodeData a = node_data(left[node], pk, sh, nlo, nhi, nhmax);
         NodeData b = node_data(right[node], pk, sh, nlo, nhi, nhmax);
         int4 lo = make_int4(min(a.lo[0], b.lo[0]), min(a.lo[1], b.lo[1]), min(a.lo[2], b.lo[2]),
@@ -613,9 +645,8 @@ static apr_status tree_up(apr_ctx* c)
     int n = (int)c->n;
     if (n < 2) return APR_OK;
     cudaMemsetAsync(W.visit, 0, sizeof(int) * (size_t)(n - 1), c->stream);
-    APR_LAUNCH(c, k_tree_up, nblocks(n, 256), 256, n, W.pk, W.sh, W.left, W.right,
-                                                      W.parent_int, W.parent_leaf, W.visit, W.nlo,
-                                                      W.nhi, W.nhmax, W.status);
+    APR_LAUNCH(c, k_tree_up, nblocks(n, TREE_UP_T), TREE_UP_T, n, W.pk, W.sh, W.left, W.right,
+               W.parent_int, W.parent_leaf, W.nlocal, W.visit, W.nlo, W.nhi, W.nhmax, W.status);
     return cuda_check(c, cudaGetLastError(), "tree up");
 }
 
@@ -654,7 +685,7 @@ apr_status index_sort(apr_ctx* c)
     ps = prof_begin(c, APR_PROF_TREE);
     if (n >= 2 && !refit)
         APR_LAUNCH(c, k_tree_internal, nblocks(n - 1, 256), 256, W.skey, (int)n, W.left, W.right,
-                                                                     W.parent_int, W.parent_leaf);
+                   W.parent_int, W.parent_leaf, W.nlocal);
     s = cuda_check(c, cudaGetLastError(), "index sort");
     if (s != APR_OK) return s;
     s = tree_up(c);

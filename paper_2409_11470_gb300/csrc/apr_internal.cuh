@@ -150,6 +150,7 @@ struct Workspace {
     int* parent_int;
     int* parent_leaf;
     int* visit;
+    unsigned char* nlocal;    // radix tree: 1 if a node's leaf range lies in one bottom-up block
     int4* nlo;                // node bbox min (x,y,z) + count
     int4* nhi;                // node bbox max (x,y,z) + first sorted slot
     double* nhmax;            // node max h
