@@ -32,12 +32,13 @@ WORKLOAD = "sod_shock_tube_3d_123480p_2level_slab"
 
 # Algorithmic FP32 work per pair, counted once from the kernel source (FMA = 2):
 # density, per pair inside 2h per Newton-Raphson iteration: relative coords 3,
-# r^2 5, sqrt 1, q 1, M4 f and f' 8, two compensated sums 11  -> 29;
+# r^2 5, sqrt 1, q 1, M4 f and f' 8, two compensated sums 11, f'' and the third
+# compensated sum (mu q^2 f'', for the step acceptance of the FP32 kernel) 10  -> 39;
 # force, per pair inside max(2h_a, 2h_b): coords/r^2/rsqrt/r/q 12, two M4
 # derivatives 8, F_a F_b 5, v.r 9, viscosity on approaching pairs (half) 6,
 # pressure term 5, three compensated components 15, energy 7, conductivity 13,
 # signal speed 3  -> 83.
-FLOPS_PER_PAIR = {"density": 29.0, "force": 83.0}
+FLOPS_PER_PAIR = {"density": 39.0, "force": 83.0}
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 

@@ -63,6 +63,25 @@ __device__ __forceinline__ void kern(int kernel, R q, R& f, R& df)
         m4<R>(q, f, df);
 }
 
+// f'' as well: M4 f'' = 3 t / 2 - 6 s; Wendland C2 f'' = -5 t^3 + 15 q t^2 / 2 (t = 1 - q/2)
+template <int KT, typename R>
+__device__ __forceinline__ void kern2_t(R q, R& f, R& df, R& ddf)
+{
+    if constexpr (KT == APR_KERNEL_WENDLAND_C2) {
+        const R t = Num<R>::max_(R(1) - R(0.5) * q, R(0));
+        const R t2 = t * t, t3 = t2 * t;
+        f = t3 * t * (R(2) * q + R(1));
+        df = R(-5) * q * t3;
+        ddf = R(-5) * t3 + R(7.5) * q * t2;
+    } else {
+        const R t = Num<R>::max_(R(2) - q, R(0)), s = Num<R>::max_(R(1) - q, R(0));
+        const R t2 = t * t, s2 = s * s;
+        f = R(0.25) * t2 * t - s2 * s;
+        df = R(3) * s2 - R(0.75) * t2;
+        ddf = R(1.5) * t - R(6) * s;
+    }
+}
+
 // the kernel fixed at compile time (KT: APR_KERNEL_M4 or APR_KERNEL_WENDLAND_C2)
 template <int KT, typename R>
 __device__ __forceinline__ void kern_t(R q, R& f, R& df)

@@ -36,16 +36,23 @@ __device__ __forceinline__ unsigned long long lattice_sq(const int d[3])
            (unsigned long long)((long long)d[2] * d[2]);
 }
 
-// one density term mu_b f(q), mu_b q f'(q) for a pair inside 2h
-template <int KT, typename R>
+// one density term mu_b f(q), mu_b q f'(q) (and with U, mu_b q^2 f''(q)) for a
+// pair inside 2h
+template <int KT, bool U2, typename R>
 __device__ __forceinline__ void density_term(R r2, R hinv, R r2max, int levb, Acc<R>& S,
-                                             Acc<R>& T, unsigned int& npair)
+                                             Acc<R>& T, Acc<R>& U, unsigned int& npair)
 {
     if (r2 >= r2max) return;
     const R q = Num<R>::root_(r2) * hinv;
-    R f, df;
-    kern_t<KT, R>(q, f, df);
     const R mub = Num<R>::mass(levb);
+    R f, df;
+    if constexpr (U2) {
+        R ddf;
+        kern2_t<KT, R>(q, f, df, ddf);
+        U.add(mub * q * q * ddf);
+    } else {
+        kern_t<KT, R>(q, f, df);
+    }
     S.add(mub * f);
     T.add(mub * q * df);
     ++npair;
@@ -109,6 +116,8 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
               const int* __restrict__ active, long long nactive, int* __restrict__ retry_q,
               int* __restrict__ retry_n)
 {
+    // FP32: Newton steps are accepted on their predicted successor (below)
+    constexpr bool ACCEPT = sizeof(R) == 4;
     // all particles, or (active != nullptr) only the queued ones of a retry
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= (active ? nactive : n)) return;
@@ -142,7 +151,7 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
     for (int it = 0; it < dc.nr_maxit; ++it) {
         const R hinv = R(1) / h;
         const R r2max = R(4) * h * h;
-        Acc<R> S, T;
+        Acc<R> S, T, U;
         const bool first_pass = it == 0;
         int k = 0;
         // the next four list entries are loaded one step ahead (clamped to the
@@ -175,10 +184,10 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
                 best = q2 < best ? q2 : best;
                 best = q3 < best ? q3 : best;
             }
-            density_term<KT, R>(rel_r2<R>(dc, d0, sx, sy, sz, a, b0), hinv, r2max, p0.w, S, T, npair);
-            density_term<KT, R>(rel_r2<R>(dc, d1, sx, sy, sz, a, b1), hinv, r2max, p1.w, S, T, npair);
-            density_term<KT, R>(rel_r2<R>(dc, d2, sx, sy, sz, a, b2), hinv, r2max, p2.w, S, T, npair);
-            density_term<KT, R>(rel_r2<R>(dc, d3, sx, sy, sz, a, b3), hinv, r2max, p3.w, S, T, npair);
+            density_term<KT, ACCEPT, R>(rel_r2<R>(dc, d0, sx, sy, sz, a, b0), hinv, r2max, p0.w, S, T, U, npair);
+            density_term<KT, ACCEPT, R>(rel_r2<R>(dc, d1, sx, sy, sz, a, b1), hinv, r2max, p1.w, S, T, U, npair);
+            density_term<KT, ACCEPT, R>(rel_r2<R>(dc, d2, sx, sy, sz, a, b2), hinv, r2max, p2.w, S, T, U, npair);
+            density_term<KT, ACCEPT, R>(rel_r2<R>(dc, d3, sx, sy, sz, a, b3), hinv, r2max, p3.w, S, T, U, npair);
         }
         for (; k < m; ++k) {
             const int b = (int)col[(long long)k * cap];
@@ -189,7 +198,7 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
                 const unsigned long long q = lattice_sq(d);
                 best = q < best ? q : best;
             }
-            density_term<KT, R>(rel_r2<R>(dc, d, sx, sy, sz, a, b), hinv, r2max, pb.w, S, T, npair);
+            density_term<KT, ACCEPT, R>(rel_r2<R>(dc, d, sx, sy, sz, a, b), hinv, r2max, pb.w, S, T, U, npair);
         }
         const R g = (S.s + mua) - target;           // pi h^3 (rho_sum - rho_h) / m0
         const R dg = -(T.s) * hinv;                   // dg/dh >= 0
@@ -197,14 +206,35 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
         if (g < R(0)) lo = h;
         else hi = h;
         R hn;
-        if (dg > R(0)) hn = h - g / dg;
+        bool newton = dg > R(0);
+        if (newton) hn = h - g / dg;
         else hn = h * R(1.25992105);
         // a Newton step that leaves the bracket is replaced by bisection (or growth)
-        if (hn < lo || (hi > R(0) && hn > hi) || !(hn == hn))
+        if (hn < lo || (hi > R(0) && hn > hi) || !(hn == hn)) {
             hn = hi > R(0) ? R(0.5) * (lo + hi) : h * R(1.25992105);
-        if (hn > R(2) * h) hn = R(2) * h;
-        if (hn < R(0.5) * h) hn = R(0.5) * h;
-        const bool done = fabs(hn - h) <= tol * h;
+            newton = false;
+        }
+        if (hn > R(2) * h) {
+            hn = R(2) * h;
+            newton = false;
+        }
+        if (hn < R(0.5) * h) {
+            hn = R(0.5) * h;
+            newton = false;
+        }
+        bool done = fabs(hn - h) <= tol * h;
+        if (ACCEPT && newton && !done) {
+            // FP32: the next Newton correction predicted from g'' = (2T + U) / h^2
+            // (g(hn) ~ g'' d^2 / 2 after the step d); a step whose successor is below
+            // a quarter of the tolerance is taken without a confirming pass, and D
+            // is carried to hn to first order (dD/dh = -(4T + U) / h)
+            const R d = hn - h;
+            const R g2 = (R(2) * T.s + U.s) * hinv * hinv;
+            if (fabs(R(0.5) * g2 * d * d) <= R(0.25) * tol * hn * dg) {
+                D -= (R(4) * T.s + U.s) * hinv * d;
+                done = true;
+            }
+        }
         if (hn > hreach) {
             // the root lies beyond this list's reach: stop at the reach; the host
             // rebuilds the lists there and the iteration continues (growth is
