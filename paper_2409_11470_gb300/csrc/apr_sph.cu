@@ -225,12 +225,13 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
         bool done = fabs(hn - h) <= tol * h;
         if (ACCEPT && newton && !done) {
             // FP32: the next Newton correction predicted from g'' = (2T + U) / h^2
-            // (g(hn) ~ g'' d^2 / 2 after the step d); a step whose successor is below
-            // a quarter of the tolerance is taken without a confirming pass, and D
-            // is carried to hn to first order (dD/dh = -(4T + U) / h)
+            // (g(hn) ~ g'' d^2 / 2 after the step d, exact to a relative O(d / h)); a
+            // step whose successor is below the tolerance is taken without a
+            // confirming pass, and D is carried to hn to first order
+            // (dD/dh = -(4T + U) / h)
             const R d = hn - h;
             const R g2 = (R(2) * T.s + U.s) * hinv * hinv;
-            if (fabs(R(0.5) * g2 * d * d) <= R(0.25) * tol * hn * dg) {
+            if (fabs(R(0.5) * g2 * d * d) <= tol * hn * dg) {
                 D -= (R(4) * T.s + U.s) * hinv * d;
                 done = true;
             }
