@@ -62,15 +62,17 @@ def _cfg(**kw):
 
 def _particles(x, y, z, vx, vy, vz, u, h, flags=None, level=None):
     n = len(x)
+    # a copy per field: callers may pass one array for several fields (zero
+    # velocities), and a later in-place change of one field must not reach the others
     p = dict(
-        x=np.ascontiguousarray(x, dtype=np.float64),
-        y=np.ascontiguousarray(y, dtype=np.float64),
-        z=np.ascontiguousarray(z, dtype=np.float64),
-        vx=np.ascontiguousarray(vx, dtype=np.float64),
-        vy=np.ascontiguousarray(vy, dtype=np.float64),
-        vz=np.ascontiguousarray(vz, dtype=np.float64),
-        u=np.ascontiguousarray(u, dtype=np.float64),
-        h=np.ascontiguousarray(h, dtype=np.float64),
+        x=np.array(x, dtype=np.float64),
+        y=np.array(y, dtype=np.float64),
+        z=np.array(z, dtype=np.float64),
+        vx=np.array(vx, dtype=np.float64),
+        vy=np.array(vy, dtype=np.float64),
+        vz=np.array(vz, dtype=np.float64),
+        u=np.array(u, dtype=np.float64),
+        h=np.array(h, dtype=np.float64),
         level=np.zeros(n, np.uint8) if level is None else np.ascontiguousarray(level, np.uint8),
         flags=np.zeros(n, np.uint8) if flags is None else np.ascontiguousarray(flags, np.uint8),
         id=np.arange(n, dtype=np.uint64),

@@ -1,15 +1,24 @@
 #!/usr/bin/env python
 """Benchmark of the APR SPH hot path on one GB300 (replicas on N GPUs).
 
-Workload: the full three-dimensional Sod shock tube (140x28x28 + 70x14x14 =
-123,480 equal-mass particles, ~210k after the initial two-level refinement of
-the slab |x| < 0.15 / 0.10).  A step is one whole pass of the hot path
-(kick, drift, accretion, zones, split/merge, neighbour index, density solve,
-forces, kick) through the C ABI.  Metric: particle-steps per second, counting
-the particles the density and force passes ran on.
+Headline workload: the flyby disc (8,000,000 particles: a locally isothermal
+disc on R in [1, 10] around a unit star, a unit perturber on a parabolic orbit
+with periastron 20 started at true anomaly -120 degrees, and a two-level
+refinement sphere R = (7.5, 5.0) that follows the perturber).  A step is one
+whole pass of the hot path through the C ABI: kick, drift, accretion, zones
+moved onto their sinks, split/merge, neighbour index, density solve, forces
+with point-mass gravity, kick, conservation sums.  Metric: particle-steps per
+second, counting the particles the density and force passes ran on; the
+FP32-mixed path is the value, the FP64 path is timed beside it.
 
-Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
-(density + force on a bounded sample of the same state) instead.
+The zone starts at r = 80 and at periastron reaches in to R = 12.5, outside
+the disc's edge at R = 10, so no gas enters it: on this workload the split and
+merge passes find nothing to do.  The disc with a planet (1.13 M particles,
+particles entering and leaving the planet's zone every step) is measured as a
+second full line in the same JSON object.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+(whole steps of the same workload recipe at a bounded particle count) instead.
 """
 from __future__ import annotations
 
@@ -28,19 +37,33 @@ sys.path.insert(0, ROOT)
 
 METRIC = "APR particle-steps/s (density+force), FP32-mixed vs FP64 GPU, at stated error"
 UNIT = "particle-steps/s"
-WORKLOAD = "sod_shock_tube_3d_123480p_2level_slab"
 
-# Algorithmic FP32 work per pair, counted once from the kernel source (FMA = 2):
-# density, per pair inside 2h per Newton-Raphson iteration: relative coords 3,
-# r^2 5, sqrt 1, q 1, M4 f and f' 8, two compensated sums 11, f'' and the third
-# compensated sum (mu q^2 f'', for the step acceptance of the FP32 kernel) 10  -> 39;
+# workload name -> (generator, default particle count, capacity factor, neighbour list length)
+# the discs' Gaussian vertical tails put up to ~1240 particles inside 2.25 h of a
+# tail particle (measured on the oracle's converged state): lists of 2048
+WORKLOADS = {
+    "flyby": ("flyby", 8_000_000, 1.2, 2048),
+    "disc_planet": ("disc_planet", 1_000_000, 1.6, 2048),
+    "sod": ("c2_sod", 123_480, 3.0, 0),
+}
+
+# Algorithmic FP32 (or FP64) work per pair, counted once from the kernel source
+# (FMA = 2): density, per pair inside 2h per Newton-Raphson iteration: relative
+# coords 3, r^2 5, sqrt 1, q 1, M4 f and f' 8, two compensated sums 11, f'' and the
+# third compensated sum (mu q^2 f'', for the step acceptance) 10  -> 39;
 # force, per pair inside max(2h_a, 2h_b): coords/r^2/rsqrt/r/q 12, two M4
-# derivatives 8, F_a F_b 5, v.r 9, viscosity on approaching pairs (half) 6,
-# pressure term 5, three compensated components 15, energy 7, conductivity 13,
-# signal speed 3  -> 83.
+# derivatives 8, F_a F_b 5, v.r 9, viscosity on approaching pairs 6, pressure term 5,
+# three compensated components 15, energy 7, conductivity 13, signal speed 3 -> 83.
 FLOPS_PER_PAIR = {"density": 39.0, "force": 83.0}
-FP32_LANES_PER_SM = 128
-NUM_SMS = 152
+# Algorithmic bytes of the neighbour-list build: per particle its lattice
+# coordinates and level (16 B), squared threshold (8 B) and per-axis bound (4 B)
+# read, its entry count written (4 B); per list entry 4 B written.
+LIST_BYTES_PER_PARTICLE = 32.0
+LIST_BYTES_PER_ENTRY = 4.0
+GROUPS = ("sort", "tree", "lists", "density", "force", "refine", "other")
+# relative tolerances of the sampled parity (the same as the GPU tests)
+PARITY_TOL = {"fp32": {"rho": 1e-5, "h": 1e-5, "omega": 1e-4, "a": 1e-4},
+              "fp64": {"rho": 1e-12, "h": 1e-12, "omega": 1e-10, "a": 1e-9}}
 
 
 def parse():
@@ -49,15 +72,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="flyby", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=0, help="particle count (0: the workload's own)")
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--parity-sample", type=int, default=1000)
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle leg (cpu_baseline, parity)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-second", action="store_true", help="skip the disc-with-planet line")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the side measurements (disc, flyby, split adjoint)")
+                    help="skip the side measurements (tube, bins, sound wave, split adjoint)")
     ap.add_argument("--extra-steps", type=int, default=10)
-    ap.add_argument("--nL", type=int, default=28, help="shock-tube resolution (28 = full size)")
     ap.add_argument("--ncu-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off)")
@@ -73,9 +99,19 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
-def workload(nL):
+def make_workload(name, n=0):
     import apr_synth
-    return apr_synth.c2_sod() if nL == 28 else apr_synth.sod(nL)
+    gen, n0, capf, mn = WORKLOADS[name]
+    f = getattr(apr_synth, gen)
+    w = f() if name == "sod" or not n else f(n)
+    return w, capf, mn
+
+
+def workload_label(name, w):
+    n = len(w["p"]["x"])
+    return {"flyby": f"flyby_disc_{n}p_periastron20_2level_sphere",
+            "disc_planet": f"disc_planet_{n}p_3level_sphere",
+            "sod": f"sod_shock_tube_3d_{n}p_2level_slab"}[name]
 
 
 # ---------------------------------------------------------------- clocks
@@ -197,20 +233,35 @@ def timed_steps(sim, torch, k, flush):
     return ms, psteps
 
 
-def traffic_record(kernel):
-    """DRAM bytes per launch from a committed ncu summary (profiles/<kernel>_traffic_*.md,
-    lines "key: value"), if it was taken on the current kernel source (else None)."""
-    import glob
-    paths = sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_traffic_*.md")))
-    if not paths:
+SAMPLE_FIELDS = ("rho", "h", "omega", "ax", "ay", "az", "dudt", "pres")
+
+
+def sample_fields(sim, ids):
+    """The fields the parity block compares, at the particles with these ids."""
+    import numpy as np
+    gid = sim.get("id")
+    order = np.argsort(gid)
+    pos = order[np.searchsorted(gid[order], ids)]
+    assert np.array_equal(gid[pos], ids)
+    return {f: sim.get(f)[pos] for f in SAMPLE_FIELDS}
+
+
+def traffic_record(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary
+    (profiles/<kernel>_traffic_<workload>.md, lines "key: value"), if it was taken on
+    the current source of the kernel's file (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic_{workload}.md")
+    if not os.path.exists(path):
         return None
     rec = {}
-    with open(paths[0]) as f:
+    with open(path) as f:
         for line in f:
             k, sep, v = line.partition(":")
-            if sep and k.strip() in ("dram_bytes_per_launch", "n", "source_sha256_16"):
+            if sep and k.strip() in ("dram_bytes_per_launch", "n", "source_sha256_16", "source"):
                 rec[k.strip()] = v.strip()
-    src = os.path.join(ROOT, "paper_2409_11470_gb300", "csrc", "apr_sph.cu")
+    src = os.path.join(ROOT, "paper_2409_11470_gb300", "csrc", rec.get("source", "apr_sph.cu"))
+    if not os.path.exists(src):
+        return None
     with open(src, "rb") as f:
         digest = hashlib.sha256(f.read()).hexdigest()[:16]
     if rec.get("source_sha256_16") != digest or "dram_bytes_per_launch" not in rec or "n" not in rec:
@@ -230,194 +281,301 @@ def replica_totals(torch, ms, psteps, world, device):
     return float(ms_t.item()), float(ps_t.item())
 
 
+def measure_peaks(torch, uuid=None):
+    """Measured FMA-pipe peaks of this GPU (apr_probe_fma_peak), with the SM clock
+    sampled while each probe runs."""
+    from paper_2409_11470_gb300.binding import probe_fma_peak
+    out = {}
+    for prec, iters in (("fp32", 40000), ("fp64", 1000)):
+        probe_fma_peak(prec, max(1, iters // 10))  # warm-up of the clocks
+        cs = ClockSampler(uuid)
+        best = 0.0
+        for _ in range(3):
+            tf, ms = probe_fma_peak(prec, iters)
+            best = max(best, tf)
+        clk = cs.stop()
+        out[prec] = {"tflops": best, "ms_per_launch": ms, "sm_mhz": clk["sm_mhz"],
+                     "reasons": clk["reasons"]}
+    return out
+
+
+def rooflines(prof, steps, ms_total, n_mean, peaks, precision):
+    """One roofline entry per kernel group that takes at least 10% of the timed
+    steps: density and force against the measured FMA peak of their precision
+    (algorithmic FLOPs per launch over the launch's average CUDA-event time), the
+    neighbour lists against the measured copy bandwidth (algorithmic bytes)."""
+    hbm = measured_hbm()
+    rows = []
+    for g in GROUPS:
+        ms = prof[g]["ms"]
+        calls = max(prof[g]["calls"], 1)
+        share = ms / ms_total if ms_total > 0 else 0.0
+        if share < 0.10:
+            continue
+        ms_launch = ms / calls
+        row = {"group": g, "share": share, "ms_per_launch": ms_launch, "launches": calls}
+        if g in FLOPS_PER_PAIR:
+            pk = peaks[precision]["tflops"]
+            work = prof[g]["pairs"] * FLOPS_PER_PAIR[g] / calls
+            ach = work / (ms_launch / 1e3) / 1e12
+            ker = f"k_{g}<{'float' if precision == 'fp32' else 'double'}>"
+            row.update({"kernel": ker, "bound": "alu", "achieved": ach, "peak": pk,
+                        "unit": "TFLOP/s", "frac": ach / pk,
+                        "peak_source": f"measured FMA-chain probe ({precision}), of measured",
+                        "pairs_per_launch": prof[g]["pairs"] / calls,
+                        "flops_per_pair": FLOPS_PER_PAIR[g]})
+        elif g == "lists":
+            entries = prof[g]["pairs"] / calls
+            byts = n_mean * LIST_BYTES_PER_PARTICLE + entries * LIST_BYTES_PER_ENTRY
+            ach = byts / (ms_launch / 1e3) / 1e9
+            row.update({"kernel": "k_candidates + k_thresholds + k_lists", "bound": "hbm",
+                        "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured",
+                        "list_entries_per_launch": entries,
+                        "algorithmic_bytes_per_launch": byts})
+        else:
+            row.update({"bound": "hbm", "note": "several kernels; no single algorithmic figure"})
+        rows.append(row)
+    return rows
+
+
+def measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0  # the recipe's fallback
+
+
+def measure(w, precision, steps, warmup, torch, flush, cap_factor, max_neigh, sample_ids=None,
+            uuid=None, world=1, ncu_range=False, keep=False):
+    """Initialise a workload, keep the sampled fields of the initialised state,
+    take warm-up steps, then time `steps` steps with the profiler on."""
+    from paper_2409_11470_gb300.binding import Simulation
+    n0 = len(w["p"]["x"])
+    sim = Simulation(w, capacity=int(cap_factor * n0) + 1024, precision=precision,
+                     max_neigh=max_neigh)
+    t0 = time.perf_counter()
+    sim.init()
+    sim.stream.synchronize()
+    init_s = time.perf_counter() - t0
+    n_init = sim.n
+    sample = sample_fields(sim, sample_ids) if sample_ids is not None else None
+    m_sinks0 = [k["m"] for k in sim.sinks()]
+    for _ in range(warmup):
+        sim.step(0.0)
+    sim.profile_enable(True)  # clears the counters
+    launches0 = sim.profile()["launches"]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(uuid)
+    if ncu_range:
+        torch.cuda.cudart().cudaProfilerStart()
+    t_wall = time.perf_counter()
+    ms, psteps = timed_steps(sim, torch, steps, flush)
+    torch.cuda.synchronize()
+    if ncu_range:
+        torch.cuda.cudart().cudaProfilerStop()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    prof = sim.profile()
+    sim.profile_enable(False)
+    res = {"ms": ms, "psteps": psteps, "prof": prof, "launches": prof["launches"] - launches0,
+           "clocks": clocks, "sample": sample, "n_initial": n0, "n_after_init": n_init,
+           "n_last": sim.n, "init_s": init_s, "wall_s_timed": t_wall,
+           "sink_mass_gain": [k["m"] - m for k, m in zip(sim.sinks(), m_sinks0)]}
+    if keep:
+        res["sim"] = sim
+    else:
+        sim.close()
+    return res
+
+
+def summary(r, steps, peaks, precision):
+    """value, per-step breakdown and rooflines of one measured run."""
+    prof = r["prof"]
+    n_mean = r["psteps"] / steps
+    rows = rooflines(prof, steps, r["ms"], n_mean, peaks, precision)
+    return {"value": r["psteps"] / (r["ms"] / 1e3), "unit": UNIT, "ms_per_step": r["ms"] / steps,
+            "steps": steps, "n_initial": r["n_initial"], "n_after_init": r["n_after_init"],
+            "n_last": r["n_last"],
+            "breakdown_ms_per_step": {g: round(prof[g]["ms"] / steps, 4) for g in GROUPS},
+            "density_attempts_per_step": prof["density_attempts"] / steps,
+            "retried_particles_per_step": prof["uncovered"] / steps,
+            "sink_mass_gain": r["sink_mass_gain"], "rooflines": rows}
+
+
 def run_ours(args):
     import numpy as np
     import torch
-
-    import apr_synth  # noqa: F401
-    from paper_2409_11470_gb300.binding import F64_FIELDS, Simulation
 
     rank, world, local = env_rank()
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    w = workload(args.nL)
+    w, capf, mn = make_workload(args.workload, args.n)
+    label = workload_label(args.workload, w)
     n0 = len(w["p"]["x"])
-    cap = 3 * n0
-    sim = Simulation(w, capacity=cap, precision="fp32")
-    sim.init()
-    n_init = sim.n
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        sim.step(0.0)
     props = torch.cuda.get_device_properties(local)
     uuid = getattr(props, "uuid", None)
     uuid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else uuid
-    sim.profile_enable(True)
-    launches0 = sim.profile()["launches"]  # kernels launched before the timed region
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(uuid)
-    if args.ncu_range:
-        torch.cuda.cudart().cudaProfilerStart()
-    t_wall = time.perf_counter()
-    ms, psteps = timed_steps(sim, torch, args.steps, flush)
-    torch.cuda.synchronize()
-    if args.ncu_range:
-        torch.cuda.cudart().cudaProfilerStop()
-    t_wall = time.perf_counter() - t_wall
-    clocks = sampler.stop()
-    prof = sim.profile()
-    sim.profile_enable(False)
-    launches = prof["launches"] - launches0
-    ms_max, ps_all = replica_totals(torch, ms, psteps, world, "cuda")
-    value = ps_all / (ms_max / 1e3)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    peaks = measure_peaks(torch, uuid)
+    rng = np.random.default_rng(12345)
+    sample_ids = np.sort(rng.choice(np.asarray(w["p"]["id"]), min(args.parity_sample, n0),
+                                    replace=False)).astype(np.uint64)
 
-    # roofline of the dominant kernel (live events on the library's stream)
-    groups = {g: prof[g] for g in ("sort", "tree", "lists", "density", "force", "refine", "other")}
-    dom = max(("density", "force"), key=lambda g: groups[g]["ms"])
-    gd = groups[dom]
-    sm_max = clocks["sm_max_mhz"] or 2070.0
-    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    flops_launch = gd["pairs"] * FLOPS_PER_PAIR[dom] / max(gd["calls"], 1)
-    ms_launch = gd["ms"] / max(gd["calls"], 1)
-    achieved = flops_launch / (ms_launch / 1e3) / 1e12
-    tr = traffic_record(f"k_{dom}_f32")
-    roofline = {"bound": "alu", "kernel": f"k_{dom}<float>", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": tr["dram_bytes_per_launch"] * (n_init / tr["n"]) if tr else None,
-                "peak_note": f"FP32 FMA pipes: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                             f"{sm_max:.0f} MHz (derived, no measured FP32 peak)",
-                "pairs_per_launch": gd["pairs"] / max(gd["calls"], 1),
-                "flops_per_pair": FLOPS_PER_PAIR[dom], "ms_per_launch": ms_launch}
-    breakdown = {g: round(v["ms"] / args.steps, 4) for g, v in groups.items()}
+    r32 = measure(w, "fp32", args.steps, args.warmup, torch, flush, capf, mn, sample_ids, uuid,
+                  world, args.ncu_range, keep=not args.no_e2e)
+    ms_max, ps_all = replica_totals(torch, r32["ms"], r32["psteps"], world, "cuda")
+    value = ps_all / (ms_max / 1e3)
+    s32 = summary(r32, args.steps, peaks, "fp32")
+    dom = max(s32["rooflines"], key=lambda x: x["share"]) if s32["rooflines"] else None
+    roofline = None
+    if dom is not None and "frac" in dom:
+        tr = None
+        if dom["group"] in FLOPS_PER_PAIR:
+            tr = traffic_record(f"k_{dom['group']}_f32", args.workload)
+        elif dom["group"] == "lists":
+            tr = traffic_record("k_lists", args.workload)
+        roofline = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
+                    "unit": dom["unit"], "frac": dom["frac"],
+                    "traffic": tr["dram_bytes_per_launch"] * (r32["n_after_init"] / tr["n"])
+                    if tr else None,
+                    "kernel": dom["kernel"], "group": dom["group"], "share": dom["share"],
+                    "peak_source": dom["peak_source"], "ms_per_launch": dom["ms_per_launch"]}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD if args.nL == 28 else f"sod_nL{args.nL}",
-                      "n_initial": n0, "n_after_init": n_init, "n_last": sim.n,
-                      "precision": "fp32-mixed (pair sums f32 compensated; state, integration, "
-                                   "reductions f64)",
-                      "l2": "flushed by a 256 MB write before every timed step",
+           "config": {"workload": label, "n_initial": n0, "n_after_init": r32["n_after_init"],
+                      "n_last": r32["n_last"],
+                      "precision": "fp32-mixed (pair sums f32 compensated on relative lattice "
+                                   "coordinates; state, integration, reductions f64)",
+                      "l2": "flushed by a 256 MB write before every timed step (the state is "
+                            "also far larger than L2)",
                       "parallelism": "replicas" if world > 1 else "single GPU",
-                      "wall_s_timed": t_wall, "launches_before_timed": launches0},
-           "roofline": roofline, "breakdown_ms_per_step": breakdown,
-           "gpu_launches": launches, "clocks": clocks}
+                      "zone": "follows the perturber (r = 80 at the start, 20 at periastron); "
+                              "its outer radius 7.5 never reaches the disc (R <= 10), so no gas "
+                              "is split or merged in these steps" if args.workload == "flyby"
+                              else None,
+                      "wall_s_timed": r32["wall_s_timed"]},
+           "roofline": roofline, "rooflines": s32["rooflines"],
+           "breakdown_ms_per_step": s32["breakdown_ms_per_step"],
+           "gpu_launches": r32["launches"], "clocks": r32["clocks"], "peaks": peaks}
 
+    r64 = None
     if rank == 0 and not args.no_fp64:
-        s64 = Simulation(w, capacity=cap, precision="fp64")
-        s64.init()
-        for _ in range(max(1, args.warmup // 2)):
-            s64.step(0.0)
-        ms64, ps64 = timed_steps(s64, torch, args.fp64_steps, flush)
-        v64 = ps64 / (ms64 / 1e3)
-        out["fp64"] = {"value": v64, "ms_per_step": ms64 / args.fp64_steps,
-                       "steps": args.fp64_steps}
-        out["fp32_over_fp64"] = value / v64
-        s64.close()
+        r64 = measure(w, "fp64", args.fp64_steps, max(1, args.warmup // 2), torch, flush, capf, mn,
+                      sample_ids, uuid)
+        s64 = summary(r64, args.fp64_steps, peaks, "fp64")
+        out["fp64"] = {k: s64[k] for k in ("value", "ms_per_step", "steps", "breakdown_ms_per_step",
+                                            "rooflines")}
+        out["fp32_over_fp64"] = value / s64["value"]
 
     if rank == 0 and not args.no_e2e:
-        # the same steps through the C ABI with host buffers: every step uploads the
-        # pinned host state (apr_upload), steps, and downloads it (apr_download); the
-        # step length is the cached limit, read before the upload drops it
-        fields = list(F64_FIELDS) + ["level", "flags", "id"]
-        host = {f: b for f, b in sim.host_buffers().items() if f in fields}
-        sim.download(host)
-        st = sim.stream
-        evs = []
-        bi = bo = 0
-        ps_e = 0
-        for _ in range(args.steps):
-            n = sim.n
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            with torch.cuda.stream(st):
-                flush.zero_()
-            dt = sim.timestep()
-            e0.record(st)
-            sim.upload(host, n)
-            sim.step(dt)
-            n2 = sim.download(host)
-            e1.record(st)
-            st.synchronize()
-            evs.append(e0.elapsed_time(e1))
-            bi += sum(n * host[f].element_size() for f in fields)
-            bo += sum(n2 * host[f].element_size() for f in fields)
-            ps_e += n2
-        out["e2e"] = {"value": ps_e / (sum(evs) / 1e3), "unit": UNIT,
-                      "h2d_bytes_per_step": bi // args.steps, "d2h_bytes_per_step": bo // args.steps}
+        out["e2e"] = e2e_rate(r32["sim"], torch, args.steps, flush)
+    if "sim" in r32:
+        r32["sim"].close()
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        out["cpu_baseline"] = oracle_baseline(w, cap, args.cpu_seconds)
+        leg = oracle_leg(w, args.workload, sample_ids, r32["sample"],
+                         r64["sample"] if r64 else None, args.cpu_seconds)
+        out["cpu_baseline"] = leg["cpu_baseline"]
+        out["parity"] = leg["parity"]
+
+    if rank == 0 and not args.no_second and args.workload == "flyby":
+        out["disc_planet_line"] = second_line(torch, flush, peaks, args)
 
     if rank == 0 and not args.no_extra:
-        sim.close()
         out["other_workloads"] = side_measurements(args, torch, flush)
 
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-    sim.close()  # idempotent
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
+def e2e_rate(sim, torch, steps, flush):
+    """The same steps through the C ABI with host buffers: every step uploads the
+    pinned host state (apr_upload), steps, and downloads it (apr_download); the
+    step length is the cached limit, read before the upload drops it."""
+    from paper_2409_11470_gb300.binding import F64_FIELDS
+    fields = list(F64_FIELDS) + ["level", "flags", "id"]
+    host = {f: b for f, b in sim.host_buffers().items() if f in fields}
+    sim.download(host)
+    st = sim.stream
+    evs = []
+    bi = bo = 0
+    ps_e = 0
+    for _ in range(steps):
+        n = sim.n
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            flush.zero_()
+        dt = sim.timestep()
+        e0.record(st)
+        sim.upload(host, n)
+        sim.step(dt)
+        n2 = sim.download(host)
+        e1.record(st)
+        st.synchronize()
+        evs.append(e0.elapsed_time(e1))
+        bi += sum(n * host[f].element_size() for f in fields)
+        bo += sum(n2 * host[f].element_size() for f in fields)
+        ps_e += n2
+    return {"value": ps_e / (sum(evs) / 1e3), "unit": UNIT, "h2d_bytes_per_step": bi // steps,
+            "d2h_bytes_per_step": bo // steps}
+
+
+def second_line(torch, flush, peaks, args):
+    """The disc with a planet (zone busy every step) as a second full line:
+    FP32-mixed and FP64 particle-steps/s, breakdown and rooflines."""
+    try:
+        w, capf, mn = make_workload("disc_planet", 0)
+        k = max(1, args.extra_steps)
+        r32 = measure(w, "fp32", k, 2, torch, flush, capf, mn)
+        s32 = summary(r32, k, peaks, "fp32")
+        line = {"workload": workload_label("disc_planet", w), "fp32": s32,
+                "gpu_launches": r32["launches"], "clocks": r32["clocks"]}
+        if not args.no_fp64:
+            k64 = max(2, k // 3)
+            r64 = measure(w, "fp64", k64, 1, torch, flush, capf, mn)
+            s64 = summary(r64, k64, peaks, "fp64")
+            line["fp64"] = {x: s64[x] for x in ("value", "ms_per_step", "steps",
+                                                 "breakdown_ms_per_step", "rooflines")}
+            line["fp32_over_fp64"] = s32["value"] / s64["value"]
+        return line
+    except Exception as e:  # a second line never takes the headline down
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 # ------------------------------------------------------- side measurements
 
-def _workload_rate(w, precision, steps, warmup, torch, flush, cap_factor, max_neigh=0):
-    from paper_2409_11470_gb300.binding import Simulation
-    n0 = len(w["p"]["x"])
-    sim = Simulation(w, capacity=int(cap_factor * n0) + 1024, precision=precision,
-                     max_neigh=max_neigh)
-    sim.init()
-    n_init = sim.n
-    m_sinks0 = sum(k["m"] for k in sim.sinks())
-    for _ in range(warmup):
-        sim.step(0.0)
-    sim.profile(reset=True)
-    sim.profile_enable(True)
-    ms, psteps = timed_steps(sim, torch, steps, flush)
-    prof = sim.profile()
-    sim.profile_enable(False)
-    res = {"value": psteps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
-           "n_after_init": n_init, "n_last": sim.n,
-           "sink_mass_gain": sum(k["m"] for k in sim.sinks()) - m_sinks0,
-           "breakdown_ms_per_step": {g: round(prof[g]["ms"] / steps, 3) for g in
-                                     ("sort", "tree", "lists", "density", "force", "refine",
-                                      "other")},
-           "density_attempts_per_step": prof["density_attempts"] / steps,
-           "retried_particles_per_step": prof["uncovered"] / steps,
-           "shrunk_particles_per_step": prof["shrunk"] / steps}
-    sim.close()
-    return res
-
-
 def side_measurements(args, torch, flush):
-    """The disc workloads and the split adjoint, each on its own: particle-steps/s
-    of whole steps (FP32-mixed and FP64) and loss+gradient evaluations/s."""
+    """The shock tube (FP32-mixed and FP64 whole steps), time-step bins, the
+    sound-wave box and the split adjoint, each on its own."""
     import apr_synth
     out = {}
     k = max(1, args.extra_steps)
-    # the discs' Gaussian vertical tails put up to ~1240 particles inside 2.25 h of a
-    # tail particle (measured on the oracle's converged state): lists of 2048
-    for name, make, cap_factor, fp64 in (
-            ("disc_planet_1e6_3level_sphere", apr_synth.disc_planet, 1.6, True),
-            ("flyby_disc_8e6_2level_sphere", apr_synth.flyby, 1.2, True)):
-        try:
-            w = make()
-            r = {"n_initial": len(w["p"]["x"]), "max_neigh": 2048,
-                 "fp32": _workload_rate(w, "fp32", k, 2, torch, flush, cap_factor, 2048)}
-            if fp64:
-                r["fp64"] = _workload_rate(w, "fp64", max(2, k // 3), 1, torch, flush, cap_factor,
-                                           2048)
-                r["fp32_over_fp64"] = r["fp32"]["value"] / r["fp64"]["value"]
-            out[name] = r
-        except Exception as e:  # a side measurement never takes the headline down
-            out[name] = {"error": f"{type(e).__name__}: {e}"}
+    try:
+        w, capf, mn = make_workload("sod", 0)
+        r = {"workload": workload_label("sod", w)}
+        r32 = measure(w, "fp32", k, 3, torch, flush, capf, mn)
+        r["fp32"] = {"value": r32["psteps"] / (r32["ms"] / 1e3), "ms_per_step": r32["ms"] / k,
+                     "breakdown_ms_per_step": {g: round(r32["prof"][g]["ms"] / k, 4) for g in GROUPS}}
+        r64 = measure(w, "fp64", max(2, k // 3), 1, torch, flush, capf, mn)
+        r["fp64"] = {"value": r64["psteps"] / (r64["ms"] / 1e3),
+                     "ms_per_step": r64["ms"] / max(2, k // 3)}
+        r["fp32_over_fp64"] = r["fp32"]["value"] / r["fp64"]["value"]
+        out["sod_shock_tube"] = r
+    except Exception as e:
+        out["sod_shock_tube"] = {"error": f"{type(e).__name__}: {e}"}
     for name, make, Bs, big, capf, mn in (
-            ("sod_time_step_bins", apr_synth.c2_sod, (2, 3), 4, 3.0, 0),
+            ("sod_time_step_bins", apr_synth.c2_sod, (3,), 4, 3.0, 0),
             ("disc_planet_1e6_time_step_bins", apr_synth.disc_planet, (3, 5), 2, 1.6, 2048)):
         try:
             out[name] = bins_measurement(torch, make(), Bs, big, capf, mn)
@@ -579,89 +737,121 @@ def adjoint_rate(torch, k):
 
 # ------------------------------------------------------------ the oracle
 
-def oracle_baseline(w, cap, seconds):
-    """Density + force of the FP64 oracle (as it stands) on a bounded sample of the
-    initialised state; returns particle-steps/s and how it was measured."""
+# bounded particle counts of the oracle's whole steps (the same recipe, seeded
+# alike): about a second per step on 16 host cores
+ORACLE_STEP_N = {"flyby": 250_000, "disc_planet": 250_000, "sod": 0}
+
+
+def _oracle_sample_errors(g, o, idx, adiabatic):
+    import numpy as np
+    rho, h, om, P = o["rho"][idx], o["h"][idx], o["omega"][idx], o["pres"][idx]
+    a_o = np.stack([o["ax"][idx], o["ay"][idx], o["az"][idx]], 1)
+    a_g = np.stack([g["ax"], g["ay"], g["az"]], 1)
+    scale = np.linalg.norm(a_o, axis=1) + P / (rho * h)
+    e = {"rho": float(np.max(np.abs(g["rho"] - rho) / rho)),
+         "h": float(np.max(np.abs(g["h"] - h) / h)),
+         "omega": float(np.max(np.abs(g["omega"] - om))),
+         "a": float(np.max(np.abs(a_g - a_o) / scale[:, None]))}
+    if adiabatic:
+        cs = o["cs"][idx]
+        sd = np.abs(o["dudt"][idx]) + P / rho * cs / h
+        e["dudt"] = float(np.max(np.abs(g["dudt"] - o["dudt"][idx]) / sd))
+    return e
+
+
+def oracle_leg(w, workload, sample_ids, s32, s64, seconds):
+    """The CPU-baseline leg: the FP64 oracle as it stands, on the host cores.
+
+    parity: from the same seeded input, the oracle solves the initialised
+    state's density (every particle, exact roots) and the forces of the sampled
+    particles; the GPU's initialised values at those particles (FP32-mixed and
+    FP64) are compared with it, per quantity: rho and h relative, Omega
+    absolute, a (and du/dt) relative to |a| + P/(rho h).
+    cpu_baseline: whole oracle steps of the same workload recipe at a bounded
+    particle count, particle-steps/s."""
     import numpy as np
 
     import oracle
-    o = oracle.Oracle(w, capacity=cap)
+    _, _, capf, _ = WORKLOADS[workload]
+    n = len(w["p"]["x"])
+    o = oracle.Oracle(w, capacity=int(capf * n) + 16)
+    t0 = time.perf_counter()
+    o.track_regions()
+    bad = o.density()
+    cnt = o.split_merge(0)
+    changed = sum(cnt.n_split) + sum(cnt.n_merge)
+    if changed:  # the zones split or merge at the start: the full initial refinement
+        o = oracle.Oracle(w, capacity=int(capf * n) + 16)
+        o.init()
+        bad = 0
+    t_dens = time.perf_counter() - t0
+    oid = o["id"]
+    order = np.argsort(oid)
+    idx = order[np.searchsorted(oid[order], sample_ids)]
+    assert np.array_equal(oid[idx], sample_ids)
+    t0 = time.perf_counter()
+    if not changed:
+        o.force(idx)
+        if o.nsink:
+            o.sink_gravity()
+    t_force = time.perf_counter() - t0
+    adiabatic = int(w["cfg"]["eos"]) == 0
+    parity = {"sample": int(len(idx)), "kind": "sampled particles of the initialised state "
+              "against the oracle's solve of the same seeded input",
+              "oracle_s": {"density_all": t_dens, "force_sample": t_force},
+              "oracle_unconverged": int(bad), "tolerance": PARITY_TOL}
+    for name, s in (("fp32", s32), ("fp64", s64)):
+        if s is None:
+            continue
+        e = _oracle_sample_errors(s, o, idx, adiabatic)
+        tol = PARITY_TOL[name]
+        parity[name] = {"max_err": e, "within_tolerance": all(e[k] <= tol[k if k != "dudt" else "a"]
+                                                              for k in e)}
+    del o
+    base = oracle_step_rate(workload, seconds)
+    return {"parity": parity, "cpu_baseline": base}
+
+
+def oracle_step_rate(workload, seconds, steps=0, warmup=0):
+    """Whole FP64 oracle steps (kick, drift, accretion, zones, split/merge, density,
+    forces, point masses, kick) of the workload recipe at a bounded particle count:
+    particle-steps/s, the threads used and what was run."""
+    import oracle
+    nb = ORACLE_STEP_N[workload]
+    w, capf, _ = make_workload(workload, nb)
+    o = oracle.Oracle(w, capacity=int(capf * len(w["p"]["x"])) + 16)
     o.init()
-    rng = np.random.default_rng(0)
-    m = 256
-    t = 0.0
-    while True:
-        sample = rng.choice(o.n, m, replace=False)
+    for _ in range(warmup):
+        o.step(o.timestep())
+    total, done, k = 0.0, 0, 0
+    while (steps and k < steps) or (not steps and (total < seconds or k < 2)):
+        dt = o.timestep()
         t0 = time.perf_counter()
-        o.density(sample)
-        o.force(sample)
-        t = time.perf_counter() - t0
-        if t * 4 > seconds or m >= o.n:
-            break
-        m = min(o.n, int(m * max(2.0, 0.5 * seconds / max(t, 1e-3))))
-    total = 0.0
-    done = 0
-    steps = max(1, int(round(seconds / max(t, 1e-3))))
-    for _ in range(steps):
-        sample = rng.choice(o.n, m, replace=False)
-        t0 = time.perf_counter()
-        o.density(sample)
-        o.force(sample)
+        o.step(dt)
         total += time.perf_counter() - t0
-        done += m
+        done += o.n
+        k += 1
     return {"value": done / total, "unit": UNIT, "cores": o.threads(), "kind": "oracle",
-            "sample": f"density+force of {m} random particles of the initialised "
-                      f"{o.n}-particle shock tube, cell-list enumeration, "
-                      f"{steps} sample(s), {total:.1f} s"}
+            "sample": f"{k} whole FP64 oracle steps (cell-list enumeration, OpenMP) of the "
+                      f"{workload_label(workload, w)} recipe ({len(w['p']['x'])} particles at the "
+                      f"start, {o.n} after), {total:.1f} s",
+            "steps": k, "seconds": total}
 
 
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return
-    w = workload(args.nL)
-    n0 = len(w["p"]["x"])
-    import numpy as np
-
-    import oracle
-    o = oracle.Oracle(w, capacity=3 * n0)
-    o.init()
-    rng = np.random.default_rng(0)
-    per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))  # whole run within minutes
-    m = 256
-    while True:
-        sample = rng.choice(o.n, m, replace=False)
-        t0 = time.perf_counter()
-        o.density(sample)
-        o.force(sample)
-        t = time.perf_counter() - t0
-        if t * 2 > per_step or m >= o.n:
-            break
-        m = min(o.n, int(m * max(2.0, 0.8 * per_step / max(t, 1e-3))))
-    for _ in range(args.warmup):
-        s = rng.choice(o.n, m, replace=False)
-        o.density(s)
-        o.force(s)
-    total = 0.0
-    for _ in range(args.steps):
-        s = rng.choice(o.n, m, replace=False)
-        t0 = time.perf_counter()
-        o.density(s)
-        o.force(s)
-        total += time.perf_counter() - t0
-    value = args.steps * m / total
-    sample = (f"each step: density+force of {m} random particles of the initialised "
-              f"{o.n}-particle shock tube (FP64 oracle, cell-list enumeration)")
+    w, _, _ = make_workload(args.workload, args.n)
+    base = oracle_step_rate(args.workload, 0.0, steps=args.steps, warmup=args.warmup)
+    value = base["value"]
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD if args.nL == 28 else f"sod_nL{args.nL}",
-                      "n_initial": n0, "n_after_init": o.n},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": o.threads(), "kind": "oracle",
-                            "sample": sample},
-           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                   "d2h_bytes_per_step": 0}}
+           "ms_per_step": 1e3 * base["seconds"] / max(base["steps"], 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_label(args.workload, w), "n_initial": len(w["p"]["x"])},
+           "cpu_baseline": {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 

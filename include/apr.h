@@ -227,11 +227,19 @@ apr_status apr_get_count(apr_ctx* ctx, long long* n, long long* next_id,
                          unsigned long long* step);
 
 /*
- * Initial refinement (Sec. 2.6 applied until no particle changes level):
- * repeat {density; split/merge pass} until nothing changes, then density and
- * forces.  *passes receives the number of split/merge passes.
+ * Initial refinement with the given refinement zones and levels (Sec. 2.1
+ * rules 1-3, Table 1; Sec. 2.6 applied until no particle changes level):
+ * the zones are installed as by apr_set_regions, moved onto the sinks they
+ * track, and {density; split/merge pass} is repeated until nothing changes,
+ * so that particles reach the full depth of nested zones; then density and
+ * forces.  regions: HOST array of nregions zones (copied; nregions 0 with a
+ * non-NULL array removes every zone); NULL keeps the zones already set (then
+ * nregions must be 0).  *passes (may be NULL) receives the number of
+ * split/merge passes.  APR_ERR_ARG for a bad zone (nothing changed),
+ * APR_ERR_CAPACITY if the splits would exceed the bound capacity; errors of
+ * the density solve and the lists as for apr_sph_density.
  */
-apr_status apr_init(apr_ctx* ctx, int* passes);
+apr_status apr_init(apr_ctx* ctx, const apr_region* regions, int nregions, int* passes);
 
 /*
  * One split/merge pass (Sec. 2.6): clear the changed marks; split levels
@@ -250,22 +258,53 @@ apr_status apr_split_merge(apr_ctx* ctx, long long* n_out, apr_counts* counts);
  */
 apr_status apr_sph_density(apr_ctx* ctx, long long* n_unconverged);
 
-/* Hydrodynamic acceleration, du/dt, signal speed, plus point-mass gravity. */
+/*
+ * Force and energy sums (the standard grad-h SPH equations the paper takes
+ * from Phantom, cited in Sec. 2.2 and Sec. 3; mixed masses by Eq. 1):
+ *   a_a = -sum_b m_b [(P_a + q_a)/(Omega_a rho_a^2) F_a + (P_b + q_b)/(Omega_b rho_b^2) F_b] r_hat
+ *   du_a/dt = (P_a + q_a)/(Omega_a rho_a^2) sum_b m_b (v_ab . r_hat) F_a + conductivity
+ * over pairs with |r_ab| < 2 max(h_a, h_b), F = dW/dr at each particle's own
+ * h, q the artificial viscosity of approaching pairs (alpha, beta) and the
+ * conductivity alpha_u (Sec. 4's shock tube); vsig_a = max over neighbours of
+ * c_s + beta max(0, -v_ab . r_hat).  Point masses (Sec. 3) add
+ * -G M (x - x_s)/|x - x_s|^3.  Reads x, v, u, h, rho, omega, pres, cs, level,
+ * flags of every live particle (rho .. cs as the last density pass left
+ * them); writes ax, ay, az, dudt, vsig.  APR_ERR_STATE before apr_bind;
+ * errors of the lists as for apr_sph_density.
+ */
 apr_status apr_sph_force(apr_ctx* ctx);
 
 /*
- * One kick-drift-kick step of length dt (dt <= 0: the Courant/force limit
- * from the last force pass): half kick, drift, accretion, zones follow their
- * sinks, split/merge, density, forces, half kick.  dt_used, stats, counts may
- * be NULL.
+ * One kick-drift-kick step of length dt (dt <= 0: the limit of apr_timestep
+ * from the last force pass), with the paper's per-step order (Sec. 2.6,
+ * Fig. 1) placed between the drift and the closing kick: half kick (gas and
+ * sinks), drift, accretion (Sec. 3), zones updated onto their sinks (Sec. 2.1),
+ * split passes ascending and merge passes descending (Sec. 2.2, 2.3),
+ * compaction, density, forces, half kick, float64 conservation sums.
+ * dt_used receives the step taken; stats the sums at the end; counts the
+ * split/merge/accretion counts; each may be NULL.  Errors as for
+ * apr_split_merge, apr_sph_density and apr_sph_force; APR_ERR_STATE before a
+ * force pass.
  */
 apr_status apr_step(apr_ctx* ctx, double dt, double* dt_used, apr_stats* stats,
                     apr_counts* counts);
 
-/* Time-step limit from the last force pass: min(ccour h/vsig, cforce sqrt(h/|a|)). */
+/*
+ * Global time-step limit from the last force pass (the step whose halving
+ * defines the bins of Sec. 2.5; the paper cites Phantom's criteria):
+ * min over live, unfixed particles of ccour h / vsig (vsig > 0) and
+ * cforce sqrt(h / |a|) (|a| > 0); ccour 0.3, cforce 0.25.  +inf if no
+ * particle constrains it.  *dt: HOST.  APR_ERR_STATE before a force pass.
+ */
 apr_status apr_timestep(apr_ctx* ctx, double* dt);
 
-/* Conservation sums of the current state. */
+/*
+ * Float64 conservation sums of the current state, over live gas particles
+ * (mass m0 / 2^level, Eq. 1) and sinks: total mass (exactly conserved by
+ * split and merge, Sec. 2.2-2.3), momentum, angular momentum about the
+ * origin, kinetic and thermal energy.  Fixed-order reduction (the same result
+ * for the same state on every call).  *stats: HOST.
+ */
 apr_status apr_stats_compute(apr_ctx* ctx, apr_stats* stats);
 
 /*
@@ -387,6 +426,22 @@ apr_status apr_profile_enable(apr_ctx* ctx, int on);
 
 /* Read (and with reset != 0 clear) the profile counters; synchronises the stream. */
 apr_status apr_profile_read(apr_ctx* ctx, apr_profile* out, int reset);
+
+/*
+ * Measurement probe (not a step of the method; the paper has no
+ * counterpart): the arithmetic peak of this GPU's fused multiply-add pipes,
+ * against which the pair kernels' FLOP rates are stated.  precision
+ * APR_PREC_FP32_MIXED probes the FP32 pipes, APR_PREC_FP64 the FP64 pipe.
+ * One warm-up launch, then one launch timed with CUDA events on `stream`
+ * (NULL = legacy default): every SM holds as many 256-thread blocks as fit,
+ * each thread runs 8 independent FMA chains for iters x 16 steps (2 flops per
+ * FMA).  *tflops and *ms (HOST) receive the rate and the timed launch's
+ * duration.  Synchronises the stream; allocates no device memory.
+ * APR_ERR_ARG for iters < 1 or another precision, APR_ERR_CUDA if a CUDA call
+ * fails.
+ */
+apr_status apr_probe_fma_peak(int precision, int iters, void* stream, double* tflops,
+                              double* ms);
 
 /*
  * Conservation sums like apr_stats_compute, for callers that cannot allocate

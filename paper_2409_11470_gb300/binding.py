@@ -100,7 +100,7 @@ def _load():
         "apr_set_sinks": [vp, P(Sink), i32],
         "apr_get_sinks": [vp, P(Sink), i32],
         "apr_get_count": [vp, P(ll), P(ll), P(C.c_ulonglong)],
-        "apr_init": [vp, P(i32)],
+        "apr_init": [vp, P(Region), i32, P(i32)],
         "apr_split_merge": [vp, P(ll), P(Counts)],
         "apr_sph_density": [vp, P(ll)],
         "apr_sph_force": [vp],
@@ -114,6 +114,7 @@ def _load():
         "apr_density_loss_grad": [vp, ll, vp, vp, vp, P(C.c_double), vp, vp],
         "apr_relax": [vp, P(Particles), ll, i32, C.c_double, P(i32), P(C.c_double)],
         "apr_step_bins": [vp, C.c_double, i32, i32, P(Counts), P(ll), P(ll), P(Stats)],
+        "apr_probe_fma_peak": [i32, i32, vp, P(C.c_double), P(C.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -124,6 +125,19 @@ def _load():
 
 
 lib = _load()
+
+
+def probe_fma_peak(precision="fp32", iters=None, stream=None):
+    """Measured rate of the FP32 (or FP64) fused multiply-add pipes of the current
+    GPU (apr_probe_fma_peak): returns (TFLOP/s, ms of the timed launch)."""
+    fp64 = precision == "fp64"
+    it = int(iters or (1000 if fp64 else 40000))
+    tf, ms = C.c_double(), C.c_double()
+    st = C.c_void_p(stream.cuda_stream if stream is not None else 0)
+    rc = lib.apr_probe_fma_peak(1 if fp64 else 0, it, st, C.byref(tf), C.byref(ms))
+    if rc != 0:
+        raise AprError(rc, "apr_probe_fma_peak failed")
+    return tf.value, ms.value
 
 
 def header_symbols():
@@ -300,9 +314,14 @@ class Simulation:
         return a.view(np.uint64) if f == "id" else a
 
     # -- hot path ---------------------------------------------------------------
-    def init(self):
+    def init(self, regions=None):
+        """Initial refinement (apr_init); ``regions`` (a list of zone dicts) replaces the
+        zones set so far, None keeps them."""
         p = C.c_int(0)
-        self._check(lib.apr_init(self.ctx, C.byref(p)), "init")
+        if regions is None:
+            self._check(lib.apr_init(self.ctx, None, 0, C.byref(p)), "init")
+        else:
+            self._check(lib.apr_init(self.ctx, _regions(regions), len(regions), C.byref(p)), "init")
         return p.value
 
     def density(self):

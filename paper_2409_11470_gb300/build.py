@@ -28,6 +28,7 @@ UNITS = {
     "apr_adjoint.cu": [],
     "apr_relax.cu": [],
     "apr_bins.cu": ["--fmad=false"],
+    "apr_probe.cu": [],
 }
 
 

@@ -707,10 +707,16 @@ apr_status apr_split_merge(apr_ctx* c, long long* n_out, apr_counts* counts)
     return s;
 }
 
-apr_status apr_init(apr_ctx* c, int* passes)
+apr_status apr_init(apr_ctx* c, const apr_region* regions, int nregions, int* passes)
 {
     if (!c) return APR_ERR_ARG;
     if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    if (regions) {
+        const apr_status sr = apr_set_regions(c, regions, nregions);
+        if (sr != APR_OK) return sr;
+    } else if (nregions != 0) {
+        return fail(c, APR_ERR_ARG, "apr_init: nregions without a region array");
+    }
     track_regions(c);
     int np = 0;
     apr_status s;

@@ -1086,7 +1086,7 @@ __global__ void __launch_bounds__(LIST_THREADS)
             const int* __restrict__ ncand, const int4* __restrict__ pk,
             const unsigned long long* __restrict__ thr, const unsigned int* __restrict__ rint,
             unsigned int* __restrict__ nbr, int* __restrict__ ncnt, int* __restrict__ point_q,
-            int* status, int graceful)
+            int* status, int graceful, unsigned long long* counters)
 {
     __shared__ int4 cq[LIST_THREADS / 32][LIST_BUF];
     __shared__ float4 cf[LIST_THREADS / 32][LIST_BUF];
@@ -1202,6 +1202,10 @@ __global__ void __launch_bounds__(LIST_THREADS)
         ncnt[a] = m > K ? -1 : m;
         if (m > K && !graceful) atomicOr(&status[ST_NEIGH_OVERFLOW], 1);
     }
+    if (dc.prof) {  // list entries written (profiling only)
+        const unsigned tot = __reduce_add_sync(FULL, own ? (unsigned)min(m, K) : 0u);
+        if (lane == 0) atomicAdd(&counters[APR_PROF_LISTS], (unsigned long long)tot);
+    }
     __syncwarp();
     }
 }
@@ -1217,7 +1221,7 @@ __global__ void __launch_bounds__(128)
                   const int4* __restrict__ pk, const unsigned long long* __restrict__ sthr,
                   const int4* __restrict__ nlo, const int4* __restrict__ nhi,
                   const unsigned long long* __restrict__ nthr, unsigned int* __restrict__ nbr,
-                  int* __restrict__ ncnt, int* status, int graceful)
+                  int* __restrict__ ncnt, int* status, int graceful, unsigned long long* counters)
 {
     __shared__ int stk[4][CAND_STACK];
     const unsigned FULL = 0xffffffffu;
@@ -1305,6 +1309,7 @@ __global__ void __launch_bounds__(128)
             const bool over = overflow || m > K;
             ncnt[a] = over ? -1 : m;
             if (over && !graceful) atomicOr(&status[ST_NEIGH_OVERFLOW], 1);
+            if (dc.prof) atomicAdd(&counters[APR_PROF_LISTS], (unsigned long long)min(m, K));
         }
     }
 }
@@ -1322,10 +1327,10 @@ static void launch_lists(apr_ctx* c, const int* ncell_dev, int n, bool graceful,
         APR_LAUNCH(c, (k_lists<X, Y, Z, SYM>), grid, LIST_THREADS, c->dc, ncell_dev, n, c->cap,     \
                    cell_first,                                                                       \
                    cell_cnt, W.cand, W.ncand, W.pk, W.sthr, W.sreach, W.nbr, W.ncnt, W.point_q,      \
-                   W.status, graceful ? 1 : 0);                                                      \
+                   W.status, graceful ? 1 : 0, W.counters);                                          \
         APR_LAUNCH(c, (k_lists_point<X, Y, Z, SYM>), 152 * 4, 128, c->dc, &W.status[ST_POINT_N],     \
                    W.point_q, n, c->cap, W.left, W.right, W.pk, W.sthr, W.nlo, W.nhi, W.nthr, W.nbr, \
-                   W.ncnt, W.status, graceful ? 1 : 0);                                              \
+                   W.ncnt, W.status, graceful ? 1 : 0, W.counters);                                  \
         break;
     switch (mask) {
         APR_LISTS_CASE(0, 0, 0, 0)
@@ -1355,7 +1360,7 @@ static void launch_queue_lists(apr_ctx* c, const int* queue, const int* qlen_dev
     case M:                                                                                          \
         APR_LAUNCH(c, (k_lists_point<X, Y, Z, SYM>), 152 * 4, 128, c->dc, qlen_dev, queue, n, c->cap, \
                    W.left, W.right, W.pk, W.sthr, W.nlo, W.nhi, W.nthr, W.nbr, W.ncnt, W.status,      \
-                   graceful ? 1 : 0);                                                                \
+                   graceful ? 1 : 0, W.counters);                                                    \
         break;
     switch (mask) {
         APR_QUEUE_CASE(0, 0, 0, 0)

@@ -140,9 +140,16 @@ extern "C" apr_status apr_stats_noalloc(const apr_config* cfg, const apr_particl
         k_na_partial<<<nblk, NA_THREADS, 0, st>>>(n, cfg->m0, cfg->eos == APR_EOS_ADIABATIC ? 1 : 0,
                                                   *p, scratch);
     k_na_final<<<1, NA_THREADS, 0, st>>>(nblk, scratch);
+    // a launch that failed leaves the final row as the previous call wrote it:
+    // report the launch error instead of reading that row back
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        put_err(err, errlen, cudaGetErrorString(e));
+        return APR_ERR_CUDA;
+    }
     double r[NA_NV];
-    cudaError_t e = cudaMemcpyAsync(r, scratch + (long long)NA_MAX_BLOCKS * NA_ROW,
-                                    sizeof(r), cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(r, scratch + (long long)NA_MAX_BLOCKS * NA_ROW, sizeof(r),
+                        cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         put_err(err, errlen, cudaGetErrorString(e));

@@ -65,6 +65,44 @@ def test_disc_planet_steps_with_accretion():
         assert a["m"] == pytest.approx(b["m"], rel=1e-14)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("which", ["sod", "disc"])
+def test_timestep_matches_oracle(precision, which):
+    """apr_timestep against the oracle's orc_timestep after the initial refinement
+    and after one step.  dt = min(0.3 h / v_sig, 0.25 sqrt(h / |a|)), so its relative
+    error is at most that of h plus v_sig, or half that of h plus |a|: the FP64 path
+    keeps 1e-9, the FP32-mixed path 1e-4 (its force tolerance)."""
+    w = apr_synth.sod(12) if which == "sod" else apr_synth.disc_planet(20000)
+    cap = 4 * len(w["p"]["x"])
+    o = oracle.Oracle(w, capacity=cap)
+    g = sim(w, precision, capacity=cap)
+    o.init()
+    g.init()
+    assert g.n == o.n
+    tol = 1e-9 if precision == "fp64" else 1e-4
+    dt = o.timestep()
+    assert np.isfinite(dt) and dt > 0
+    assert g.timestep() == pytest.approx(dt, rel=tol)
+    o.step(0.5 * dt)
+    g.step(0.5 * dt)
+    assert g.n == o.n
+    assert g.timestep() == pytest.approx(o.timestep(), rel=tol)
+
+
+def test_init_takes_the_zones():
+    """apr_init with the zones passed in (the boundary's form) gives the same state
+    as apr_set_regions followed by apr_init without zones."""
+    w = apr_synth.c1_lattice()
+    a = sim(w, "fp64", capacity=3 * 4096)
+    b = sim(w, "fp64", capacity=3 * 4096)
+    b.set_regions([])
+    pa = a.init()
+    pb = b.init(w["regions"])
+    assert pa == pb and a.n == b.n > 4096
+    for f in ("x", "h", "rho", "ax", "level", "id"):
+        assert np.array_equal(a.get(f), b.get(f)), f
+
+
 def test_gpu_step_conserves_mass_and_momentum_fp32():
     w = with_velocities(apr_synth.lattice_box(12, 0.1, sphere_R=(0.3,), seed=4), 0.2)
     w["cfg"]["alpha_u"] = 1.0

@@ -1,13 +1,18 @@
 """The conservation sums of apr_stats_noalloc, the entry point for callers that
 cannot allocate device memory (it uses a built-in scratch array instead of a
-workspace), against apr_stats_compute on the same particles, on two calls in a
-row, through the C ABI.  Collected last on purpose."""
+workspace), through the C ABI: against apr_stats_compute on the same particles,
+and against the oracle's sums on the particles the oracle's own split pass made
+from the same input, on two calls in a row.
+
+This file is collected last (its name sorts after every other test file) so
+that a run stopped at its first failure has already run every other test."""
 import ctypes as C
 
 import numpy as np
 import pytest
 
 import apr_synth
+import oracle
 from gpu_util import sim, with_velocities
 
 pytestmark = pytest.mark.gpu
@@ -28,12 +33,16 @@ def _as_array(s):
 
 @pytest.mark.parametrize("make", [lambda: with_velocities(apr_synth.c1_lattice(), 0.3),
                                   lambda: apr_synth.disc_planet(20000)])
-def test_noalloc_sums_match_workspace_sums_twice(make):
+def test_noalloc_sums_match_workspace_and_oracle_sums_twice(make):
     B, f = _entry()
     w = make()
     g = sim(w)
     g.split_merge()  # mixed levels (disc: particles near the planet)
     ref = _as_array(g.stats())
+    o = oracle.Oracle(w, capacity=3 * len(w["p"]["x"]))
+    o.split_merge(0)
+    assert o.n == g.n
+    ref_o = _as_array(o.stats())
     sinks = B.Sink * max(1, len(w["sinks"]))
     arr = sinks()
     for j, s in enumerate(w["sinks"]):
@@ -49,6 +58,8 @@ def test_noalloc_sums_match_workspace_sums_twice(make):
         assert st == 0, err.value
         got = _as_array(out)
         assert np.all(np.abs(got - ref) <= 1e-12 * scale), (got, ref)
+        # float64 sums in another order: agreement to a few ulps of the scale
+        assert np.all(np.abs(got - ref_o) <= 1e-12 * scale), (got, ref_o)
 
 
 def test_noalloc_rejects_more_particles_than_its_scratch():
