@@ -87,6 +87,10 @@ def parse():
     ap.add_argument("--ncu-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off)")
+    ap.add_argument("--table", action="store_true",
+                    help="the per-configuration table (C1-C5): GPU FP32-mixed and FP64 rates, "
+                         "the oracle's rate on the host cores, sampled errors against the "
+                         "oracle, the dominant kernel's roofline fraction; one JSON line")
     ap.add_argument("--profile-workload", choices=["disc_planet", "disc_planet_bins"], default=None,
                     help="profiling only: initialise this workload, take --warmup steps, "
                          "then --steps steps inside cudaProfilerStart/Stop (the _bins form: "
@@ -832,7 +836,7 @@ def oracle_step_rate(workload, seconds, steps=0, warmup=0):
         done += o.n
         k += 1
     return {"value": done / total, "unit": UNIT, "cores": o.threads(), "kind": "oracle",
-            "sample": f"{k} whole FP64 oracle steps (cell-list enumeration, OpenMP) of the "
+            "sample": f"{k} whole FP64 oracle steps (k-d tree enumeration, OpenMP) of the "
                       f"{workload_label(workload, w)} recipe ({len(w['p']['x'])} particles at the "
                       f"start, {o.n} after), {total:.1f} s",
             "steps": k, "seconds": total}
@@ -885,8 +889,200 @@ def run_profile_workload(args):
     sim.close()
 
 
+# --------------------------------------------------------- the C1-C5 table
+
+def _gpu_init_sample(w, precision, capf, mn, ids):
+    """GPU init of a workload and its sampled fields (the state the oracle rows
+    are compared on)."""
+    from paper_2409_11470_gb300.binding import Simulation
+    n0 = len(w["p"]["x"])
+    sim = Simulation(w, capacity=int(capf * n0) + 1024, precision=precision, max_neigh=mn)
+    sim.init()
+    out = sample_fields(sim, ids)
+    sim.close()
+    return out
+
+
+def oracle_table_leg(rows, torch):
+    """The oracle's side of the table (part of the CPU-baseline leg): per
+    configuration, its rate on the host cores and the GPU's sampled errors
+    against it (rows carry the GPU's sampled fields)."""
+    import numpy as np
+
+    import apr_synth
+    import oracle
+    from paper_2409_11470_gb300.binding import Simulation
+    out = {}
+    # C1: one split pass, then density and force of all 4376 particles (brute force and tree)
+    w = apr_synth.c1_lattice()
+    res = {}
+    for mode, enum in (("brute_force", 0), ("k_d_tree", 1)):
+        o = oracle.Oracle(w, capacity=3 * 4096, enumerate=enum)
+        o.split_merge(0)
+        t0 = time.perf_counter()
+        o.density()
+        o.force()
+        res[mode] = o.n / (time.perf_counter() - t0)
+    g = rows["C1"]["sample"]
+    errs = {p: _oracle_sample_errors(g[p], o, np.arange(o.n), False) for p in g}
+    out["C1"] = {"oracle_particle_steps_per_s": res, "cores": o.threads(),
+                 "oracle_kind": "split pass, then density + force of every particle", "errors": errs}
+    # C2, C3, C4: the oracle's whole steps; errors on the GPU's sampled initial state
+    for cname, wl in (("C2", "sod"), ("C3", "disc_planet"), ("C4", "flyby")):
+        wfull, capf, _ = make_workload(wl, 0)
+        ids = rows[cname]["ids"]
+        n = len(wfull["p"]["x"])
+        o = oracle.Oracle(wfull, capacity=int(capf * n) + 16)
+        t0 = time.perf_counter()
+        if cname == "C4":  # no particle is in the zone: density of all, forces of the sample
+            o.track_regions()
+            o.density()
+            o.split_merge(0)
+            oid = o["id"]
+            order = np.argsort(oid)
+            idx = order[np.searchsorted(oid[order], ids)]
+            o.force(idx)
+            o.sink_gravity()
+        else:
+            o.init()
+            oid = o["id"]
+            order = np.argsort(oid)
+            idx = order[np.searchsorted(oid[order], ids)]
+        t_init = time.perf_counter() - t0
+        errs = {p: _oracle_sample_errors(rows[cname]["sample"][p], o, idx,
+                                         int(wfull["cfg"]["eos"]) == 0)
+                for p in rows[cname]["sample"]}
+        if cname == "C4":
+            del o
+            rate = oracle_step_rate("flyby", 20.0)
+            rate["note"] = "the same recipe at 250,000 particles (scaled; the oracle's cost per particle-step is set by the neighbour count, the same at either size)"
+        else:
+            rate = {"value": 0.0}
+            dt = o.timestep()
+            t0 = time.perf_counter()
+            k = 0
+            while k < 2 or time.perf_counter() - t0 < 10.0:
+                o.step(dt)
+                k += 1
+            rate = {"value": k * o.n / (time.perf_counter() - t0), "steps": k, "cores": o.threads()}
+        out[cname] = {"oracle_step": rate, "oracle_init_s": t_init, "errors": errs}
+    # C5: the oracle's gradient on the 2048 splits nearest the centre
+    w = apr_synth.c5_adjoint_lattice()
+    prob = apr_synth.adjoint_problem(w)
+    t0 = time.perf_counter()
+    Jo, gdo, gho = oracle.Oracle(w).split_loss_grad(prob["parent"], prob["d"], prob["hc"],
+                                                    prob["want"])
+    t_o = time.perf_counter() - t0
+    want = prob["want"]
+    e = {}
+    for p, (J, gd, gh) in rows["C5"]["grad"].items():
+        e[p] = {"J": abs(J - Jo) / Jo,
+                "grad_d_rel_l2": float(np.linalg.norm(gd[want] - gdo[want]) / np.linalg.norm(gdo[want])),
+                "grad_h_rel_l2": float(np.linalg.norm(gh[np.repeat(want, 2)] - gho[np.repeat(want, 2)])
+                                       / np.linalg.norm(gho[np.repeat(want, 2)]))}
+    out["C5"] = {"oracle_s": t_o, "oracle_kind": "J and the gradient on the 2048-split subset "
+                 "(every child's density error enters J)", "errors": e}
+    return out
+
+
+def run_table(args):
+    """The C1-C5 table: one JSON line."""
+    import numpy as np
+    import torch
+
+    import apr_synth
+    from paper_2409_11470_gb300.binding import Simulation
+    torch.cuda.set_device(0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    peaks = measure_peaks(torch)
+    rows = {}
+    # C1: density + force after the split pass, repeated
+    w = apr_synth.c1_lattice()
+    c1 = {"config": "C1 lattice 16^3 + one split pass (4096 -> 4376)", "sample": {}}
+    for prec in ("fp32", "fp64"):
+        sim = Simulation(w, capacity=3 * 4096, precision=prec)
+        sim.split_merge()
+        sim.density()
+        sim.force()
+        st = sim.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 50
+        e0.record(st)
+        for _ in range(reps):
+            sim.density()
+            sim.force()
+        e1.record(st)
+        st.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        c1[prec] = {"value": sim.n / (ms / 1e3), "ms_per_eval": ms}
+        c1["sample"][prec] = {f: sim.get(f) for f in SAMPLE_FIELDS}
+        c1["n"] = sim.n
+        sim.close()
+    rows["C1"] = c1
+    rng = np.random.default_rng(4321)
+    for cname, wl, k in (("C2", "sod", 20), ("C3", "disc_planet", 10), ("C4", "flyby", 10)):
+        wfull, capf, mn = make_workload(wl, 0)
+        n0 = len(wfull["p"]["x"])
+        row = {"config": workload_label(wl, wfull), "sample": {}}
+        if cname == "C4":
+            ids = np.sort(rng.choice(n0, 1000, replace=False)).astype(np.uint64)
+        else:  # ids after the initial refinement: children get new ids, so sample the GPU's
+            sim = Simulation(wfull, capacity=int(capf * n0) + 1024, precision="fp64", max_neigh=mn)
+            sim.init()
+            ids = np.sort(rng.choice(sim.get("id"), 1000, replace=False))
+            sim.close()
+        row["ids"] = ids
+        for prec, steps in (("fp32", k), ("fp64", max(2, k // 4))):
+            r = measure(wfull, prec, steps, 2, torch, flush, capf, mn, ids)
+            sm = summary(r, steps, peaks, prec)
+            dom = max(sm["rooflines"], key=lambda x: x["share"]) if sm["rooflines"] else {}
+            row[prec] = {"value": sm["value"], "ms_per_step": sm["ms_per_step"],
+                         "n_after_init": sm["n_after_init"],
+                         "dominant": {x: dom.get(x) for x in ("group", "kernel", "share", "bound",
+                                                               "frac")}}
+            row["sample"][prec] = r["sample"]
+        row["fp32_over_fp64"] = row["fp32"]["value"] / row["fp64"]["value"]
+        rows[cname] = row
+    # C5: loss + gradient evaluations
+    w = apr_synth.c5_adjoint_lattice()
+    prob = apr_synth.adjoint_problem(w)
+    n, npar = len(w["p"]["x"]), len(prob["parent"])
+    c5 = {"config": "C5 126^3 lattice, split adjoint (2,000,376 particles)", "grad": {}}
+    for prec in ("fp32", "fp64"):
+        sim = Simulation(w, capacity=n + 2 * npar, precision=prec)
+        dev = sim.device
+        par = torch.as_tensor(prob["parent"], device=dev)
+        d = torch.as_tensor(prob["d"], device=dev)
+        hc = torch.as_tensor(prob["hc"], device=dev)
+        J, gd, gh = sim.density_loss_grad(par, d, hc)
+        st = sim.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5 if prec == "fp32" else 2
+        e0.record(st)
+        for _ in range(reps):
+            sim.density_loss_grad(par, d, hc)
+        e1.record(st)
+        st.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        c5[prec] = {"evals_per_s": 1e3 / ms, "ms_per_eval": ms}
+        c5["grad"][prec] = (J, gd.cpu().numpy(), gh.cpu().numpy())
+        sim.close()
+    c5["fp32_over_fp64"] = c5["fp32"]["evals_per_s"] / c5["fp64"]["evals_per_s"]
+    rows["C5"] = c5
+    orc = oracle_table_leg(rows, torch)
+    table = {}
+    for cname, row in rows.items():
+        t = {k: v for k, v in row.items() if k not in ("sample", "ids", "grad")}
+        t["oracle"] = orc[cname]
+        table[cname] = t
+    print(json.dumps({"table": table, "peaks": peaks, "unit": UNIT}), flush=True)
+
+
 def main():
     args = parse()
+    if args.table:
+        run_table(args)
+        return
     if args.profile_workload:
         run_profile_workload(args)
     elif args.impl == "reference":

@@ -354,14 +354,205 @@ static void bl_push(blist* L, long long b, double r2)
     L->n++;
 }
 
+/*
+ * k-d tree over the particles for range queries (enumeration only: a query
+ * returns exactly the particles a scan over all of them would, and every
+ * caller sorts them by index, so the tree's shape never enters a result).
+ * Each node holds the bounding box and the largest h of its live particles;
+ * internal nodes split at the median of their widest axis; leaves hold at
+ * most KD_LEAF particles.  Unlike a uniform grid it stays efficient where the
+ * particle density spans orders of magnitude (a disc's midplane and tails).
+ */
+#define KD_LEAF 16
+
+typedef struct {
+    double lo[3], hi[3];
+    double hmax;
+    long long first, count;
+    long long left, right; /* -1 for a leaf */
+} kdnode;
+
+typedef struct {
+    kdnode* node;
+    long long nnode, cap;
+    long long* items;
+} kdtree;
+
+static double coord_of(const orc_state* s, int k, long long i)
+{
+    return k == 0 ? s->x[i] : (k == 1 ? s->y[i] : s->z[i]);
+}
+
+/* rearrange it[0..n) so that it[m] holds the element of rank m along axis k,
+ * smaller-or-equal ones before it and larger-or-equal ones after (quickselect) */
+static void kd_select(const orc_state* s, int k, long long* it, long long n, long long m)
+{
+    long long lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const double pivot = coord_of(s, k, it[lo + (hi - lo) / 2]);
+        long long i = lo, j = hi;
+        while (i <= j) {
+            while (coord_of(s, k, it[i]) < pivot) ++i;
+            while (coord_of(s, k, it[j]) > pivot) --j;
+            if (i <= j) {
+                long long tmp = it[i];
+                it[i] = it[j];
+                it[j] = tmp;
+                ++i;
+                --j;
+            }
+        }
+        if (m <= j) hi = j;
+        else if (m >= i) lo = i;
+        else break;
+    }
+}
+
+static long long kd_build_node(kdtree* t, const orc_state* s, long long first, long long count)
+{
+    long long id;
+#pragma omp atomic capture
+    id = t->nnode++;
+    kdnode* nd = &t->node[id];
+    nd->first = first;
+    nd->count = count;
+    nd->left = nd->right = -1;
+    nd->hmax = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        nd->lo[k] = INFINITY;
+        nd->hi[k] = -INFINITY;
+    }
+    for (long long q = first; q < first + count; ++q) {
+        long long i = t->items[q];
+        for (int k = 0; k < 3; ++k) {
+            double v = coord_of(s, k, i);
+            if (v < nd->lo[k]) nd->lo[k] = v;
+            if (v > nd->hi[k]) nd->hi[k] = v;
+        }
+        if (s->h[i] > nd->hmax) nd->hmax = s->h[i];
+    }
+    if (count <= KD_LEAF) return id;
+    int axis = 0;
+    for (int k = 1; k < 3; ++k)
+        if (nd->hi[k] - nd->lo[k] > nd->hi[axis] - nd->lo[axis]) axis = k;
+    const long long m = count / 2;
+    kd_select(s, axis, t->items + first, count, m);
+    long long l, r;
+    if (count > 65536) {
+#pragma omp task shared(l)
+        l = kd_build_node(t, s, first, m);
+#pragma omp task shared(r)
+        r = kd_build_node(t, s, first + m, count - m);
+#pragma omp taskwait
+    } else {
+        l = kd_build_node(t, s, first, m);
+        r = kd_build_node(t, s, first + m, count - m);
+    }
+    t->node[id].left = l;
+    t->node[id].right = r;
+    return id;
+}
+
+/* a tree over the live particles of s */
+static void kd_build(const orc_state* s, kdtree* t)
+{
+    long long n = 0;
+    for (long long i = 0; i < s->n; ++i)
+        if (is_live(s, i)) ++n;
+    t->items = (long long*)malloc(sizeof(long long) * (size_t)(n ? n : 1));
+    n = 0;
+    for (long long i = 0; i < s->n; ++i)
+        if (is_live(s, i)) t->items[n++] = i;
+    /* leaves hold at least KD_LEAF / 2 particles: fewer than 4 n / KD_LEAF + 1 nodes */
+    t->cap = 4 * n / KD_LEAF + 2;
+    t->node = (kdnode*)malloc(sizeof(kdnode) * (size_t)t->cap);
+    t->nnode = 0;
+    if (n == 0) return;
+#pragma omp parallel
+#pragma omp single
+    kd_build_node(t, s, 0, n);
+}
+
+static void kd_free(kdtree* t)
+{
+    free(t->node);
+    free(t->items);
+}
+
+/* squared distance from p to the node's box, the smallest over periodic images
+ * (never more than the computed separation of p from a particle inside it) */
+static double kd_gap2(const orc_cfg* c, const double p[3], const kdnode* nd)
+{
+    double s2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double g = 0.0;
+        if (p[k] < nd->lo[k]) g = nd->lo[k] - p[k];
+        else if (p[k] > nd->hi[k]) g = p[k] - nd->hi[k];
+        if (c->periodic[k] && g > 0.0) {
+            const double L = box_len(c, k);
+            for (int img = -1; img <= 1; img += 2) {
+                const double v = p[k] + img * L;
+                double gi = 0.0;
+                if (v < nd->lo[k]) gi = nd->lo[k] - v;
+                else if (v > nd->hi[k]) gi = v - nd->hi[k];
+                if (gi < g) g = gi;
+            }
+        }
+        s2 += g * g;
+    }
+    return s2;
+}
+
+/*
+ * Every live b with |x_a - x_b| < R (sym = 0), or a superset of the b with
+ * |x_a - x_b| < 2 max(h_a, h_b) (sym = 1: nodes whose box is farther than
+ * 2 max(h_a, largest h inside) are skipped), appended to out unsorted with
+ * their squared separations.  A node is skipped only when its box gap exceeds
+ * the radius by a relative 1e-9, far above the rounding of either distance.
+ */
+static void kd_query(const orc_cfg* c, const orc_state* s, const kdtree* t, long long a, double R,
+                     int sym, blist* out)
+{
+    if (t->nnode == 0) return;
+    const double p[3] = {s->x[a], s->y[a], s->z[a]};
+    long long stack[128];
+    int sp = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        const kdnode* nd = &t->node[stack[--sp]];
+        double Rn = R;
+        if (sym) Rn = 2.0 * (s->h[a] > nd->hmax ? s->h[a] : nd->hmax);
+        if (kd_gap2(c, p, nd) > Rn * Rn * (1.0 + 1e-9)) continue;
+        if (nd->left < 0) {
+            const double R2 = Rn * Rn;
+            for (long long q = nd->first; q < nd->first + nd->count; ++q) {
+                long long b = t->items[q];
+                double d[3];
+                sep64(c, s, a, b, d);
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (r2 < R2) bl_push(out, b, r2);
+            }
+        } else {
+            stack[sp++] = nd->right;
+            stack[sp++] = nd->left;
+        }
+    }
+}
+
+
 static int cmp_ll(const void* a, const void* b)
 {
     long long x = *(const long long*)a, y = *(const long long*)b;
     return (x > y) - (x < y);
 }
 
-/* all live b (b may equal a) with |x_a - x_b| < R, sorted by index */
-static void gather_within(const orc_cfg* c, const orc_state* s, const cellgrid* g, long long a,
+/* sort a gathered list by particle index, so that sums do not depend on the
+ * enumeration */
+static void sort_gathered(const orc_cfg* c, const orc_state* s, long long a, blist* out);
+
+/* all live b (b may equal a) with |x_a - x_b| < R, sorted by index (g == NULL:
+ * a scan over every particle; else the k-d tree) */
+static void gather_within(const orc_cfg* c, const orc_state* s, const kdtree* g, long long a,
                           double R, blist* out)
 {
     out->n = 0;
@@ -376,40 +567,25 @@ static void gather_within(const orc_cfg* c, const orc_state* s, const cellgrid* 
         }
         return;
     }
-    long long ca[3] = {cell_coord(c, g, 0, s->x[a]), cell_coord(c, g, 1, s->y[a]),
-                       cell_coord(c, g, 2, s->z[a])};
-    long long lo[3], hi[3];
-    for (int k = 0; k < 3; ++k) {
-        long long m = (long long)ceil(R / g->cw[k]);
-        if (c->periodic[k]) {
-            if (2 * m + 1 >= g->nc[k]) {
-                lo[k] = 0;
-                hi[k] = g->nc[k] - 1;
-            } else {
-                lo[k] = ca[k] - m;
-                hi[k] = ca[k] + m;
-            }
-        } else {
-            lo[k] = ca[k] - m < 0 ? 0 : ca[k] - m;
-            hi[k] = ca[k] + m >= g->nc[k] ? g->nc[k] - 1 : ca[k] + m;
-        }
+    kd_query(c, s, g, a, R, 0, out);
+    sort_gathered(c, s, a, out);
+}
+
+/* a superset, sorted by index, of the live b with |x_a - x_b| < 2 max(h_a, h_b) */
+static void gather_symmetric(const orc_cfg* c, const orc_state* s, const kdtree* g, long long a,
+                             double hmax, blist* out)
+{
+    if (!g) {
+        gather_within(c, s, NULL, a, 2.0 * (s->h[a] > hmax ? s->h[a] : hmax), out);
+        return;
     }
-    for (long long i = lo[0]; i <= hi[0]; ++i)
-        for (long long j = lo[1]; j <= hi[1]; ++j)
-            for (long long k = lo[2]; k <= hi[2]; ++k) {
-                long long ii = (i % g->nc[0] + g->nc[0]) % g->nc[0];
-                long long jj = (j % g->nc[1] + g->nc[1]) % g->nc[1];
-                long long kk = (k % g->nc[2] + g->nc[2]) % g->nc[2];
-                long long cell = (ii * g->nc[1] + jj) * g->nc[2] + kk;
-                for (long long t = g->head[cell]; t < g->head[cell + 1]; ++t) {
-                    long long b = g->items[t];
-                    if (!is_live(s, b)) continue;
-                    double d[3];
-                    sep64(c, s, a, b, d);
-                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    if (r2 < R2) bl_push(out, b, r2);
-                }
-            }
+    out->n = 0;
+    kd_query(c, s, g, a, 0.0, 1, out);
+    sort_gathered(c, s, a, out);
+}
+
+static void sort_gathered(const orc_cfg* c, const orc_state* s, long long a, blist* out)
+{
     /* sort by particle index so that sums do not depend on the enumeration */
     long long* key = (long long*)malloc(sizeof(long long) * (size_t)(out->n ? out->n : 1));
     for (long long t = 0; t < out->n; ++t) key[t] = out->idx[t];
@@ -525,7 +701,7 @@ static void eos(const orc_cfg* c, const orc_state* s, long long a, double rho, d
 }
 
 /* density, h, Omega, nearest-neighbour distance, pressure and sound speed of particle a */
-static int density_one(const orc_cfg* c, orc_state* s, const cellgrid* g, const long long* xi,
+static int density_one(const orc_cfg* c, orc_state* s, const kdtree* g, const long long* xi,
                        long long a, blist* L, double** rbuf, double** mbuf, long long* bufcap)
 {
     double ma = mass_of(c, s->level[a]);
@@ -611,10 +787,10 @@ long long orc_density(const orc_cfg* c, orc_state* s, const long long* sample, l
     long long n = s->n;
     long long* xi = (long long*)malloc(sizeof(long long) * 3 * (size_t)(n ? n : 1));
     orc_quantise(c, n, s->x, s->y, s->z, xi);
-    cellgrid grid, *g = NULL;
+    kdtree tree, *g = NULL;
     if (c->enumerate == 1 && n > 0) {
-        grid_build(c, s, 0.5 * max_live_h(s), &grid);
-        g = &grid;
+        kd_build(s, &tree);
+        g = &tree;
     }
     long long m = sample ? nsample : n;
     long long bad = 0;
@@ -635,7 +811,7 @@ long long orc_density(const orc_cfg* c, orc_state* s, const long long* sample, l
         free(L.idx);
         free(L.r2);
     }
-    if (g) grid_free(g);
+    if (g) kd_free(g);
     free(xi);
     return bad;
 }
@@ -728,10 +904,10 @@ void orc_force(const orc_cfg* c, orc_state* s, const long long* sample, long lon
 {
     long long n = s->n;
     double hmax = max_live_h(s);
-    cellgrid grid, *g = NULL;
+    kdtree tree, *g = NULL;
     if (c->enumerate == 1 && n > 0) {
-        grid_build(c, s, 0.5 * hmax, &grid);
-        g = &grid;
+        kd_build(s, &tree);
+        g = &tree;
     }
     set_threads(c);
     if (sample) {
@@ -742,13 +918,13 @@ void orc_force(const orc_cfg* c, orc_state* s, const long long* sample, long lon
             for (long long t = 0; t < nsample; ++t) {
                 long long a = sample[t];
                 if (!is_live(s, a)) continue;
-                gather_within(c, s, g, a, 2.0 * (s->h[a] > hmax ? s->h[a] : hmax), &L);
+                gather_symmetric(c, s, g, a, hmax, &L);
                 force_sum(c, s, a, L.idx, L.n);
             }
             free(L.idx);
             free(L.r2);
         }
-        if (g) grid_free(g);
+        if (g) kd_free(g);
         return;
     }
     /* gather lists G_a (ascending), then reverse lists R_b = {a : b in G_a} (ascending) */
@@ -812,7 +988,7 @@ void orc_force(const orc_cfg* c, orc_state* s, const long long* sample, long lon
     free(roff);
     free(rlist);
     free(fill);
-    if (g) grid_free(g);
+    if (g) kd_free(g);
 }
 
 /* point-mass gravity: sinks on gas (added to a), gas and sinks on sinks */
@@ -1530,10 +1706,10 @@ int orc_split_loss_grad(const orc_cfg* c, const orc_state* s, long long npar,
     double hmax = 0.0;
     for (long long i = 0; i < nt; ++i)
         if (role[i] && T.h[i] > hmax) hmax = T.h[i];
-    cellgrid grid, *g = NULL;
+    kdtree tree, *g = NULL;
     if (c->enumerate && nt > 0) {
-        grid_build(c, &T, 2.0 * hmax, &grid);
-        g = &grid;
+        kd_build(&T, &tree);
+        g = &tree;
     }
     double* e = (double*)calloc(sz, sizeof(double));
     set_threads(c);
@@ -1621,7 +1797,7 @@ int orc_split_loss_grad(const orc_cfg* c, const orc_state* s, long long npar,
         free(L.idx);
         free(L.r2);
     }
-    if (g) grid_free(g);
+    if (g) kd_free(g);
     free(e);
     free(role);
     free_state_arrays(&T);

@@ -249,6 +249,11 @@ static apr_status check_cfg(const apr_config* cfg, DevCfg* dc, std::string* why)
         dc->inv_delta = mant == 0.5 ? std::ldexp(1.0, 1 - ex) : 0.0;
     }
     dc->alpha_avf = (float)cfg->alpha_av;
+    dc->hfactf = (float)cfg->hfact;
+    dc->gammaf = (float)cfg->gamma;
+    dc->cs0f = (float)cfg->cs0;
+    dc->qcsf = (float)cfg->qcs;
+    dc->m0f = (float)cfg->m0;
     dc->beta_avf = (float)cfg->beta_av;
     dc->alpha_uf = (float)cfg->alpha_u;
     dc->hfact = cfg->hfact;
@@ -304,6 +309,7 @@ static apr_status check_overflow(apr_ctx* c)
 
 static apr_status run_density(apr_ctx* c, long long* noconv_out)
 {
+    c->force_data_fresh = false;
     apr_status s = index_sort(c);
     if (s != APR_OK) return s;
     long long unc = 0, noconv = 0, shrinks = 0;
@@ -315,19 +321,20 @@ static apr_status run_density(apr_ctx* c, long long* noconv_out)
             // also hold every force pair, r < 2 max(h_a, h_b)
             s = index_lists(c, 1, DENSITY_REACH, true);
             if (s != APR_OK) return s;
-            s = density_pass(c, &unc, &noconv, nullptr, 0, q);
+            s = density_pass(c, &unc, &noconv, nullptr, 0, q, true);
         } else {
             // only the particles queued by the last pass: their gather lists by a
             // per-particle tree walk at their new h, then their Newton-Raphson
             // (the symmetric lists the force needs are rebuilt after the last attempt)
             s = relist_mark(c, c->W.retry_q[q], &c->W.status[ST_RETRY_N + q], attempt == 1);
-            if (s == APR_OK) s = index_refresh_sh(c);
+            if (s == APR_OK)
+                s = index_refresh_sh_queue(c, c->W.retry_q[q], &c->W.status[ST_RETRY_N + q]);
             if (s != APR_OK) return s;
             s = index_lists_queue(c, c->W.retry_q[q], &c->W.status[ST_RETRY_N + q], DENSITY_REACH,
                                   true, false);
             if (s != APR_OK) return s;
             const long long nq = unc;
-            s = density_pass(c, &unc, &noconv, c->W.retry_q[q], nq, q ^ 1);
+            s = density_pass(c, &unc, &noconv, c->W.retry_q[q], nq, q ^ 1, true);
             q ^= 1;
         }
         if (s != APR_OK) return s;
@@ -352,6 +359,8 @@ static apr_status run_density(apr_ctx* c, long long* noconv_out)
         return fail(c, APR_ERR_NEIGH_OVERFLOW,
                     "neighbour lists cannot hold the particles within reach: raise max_neigh");
     if (unc) return fail(c, APR_ERR_NR_NOCONV, "smoothing lengths kept outgrowing their lists");
+    // every slot's force records were written by the pass that settled its h
+    c->force_data_fresh = true;
     if (noconv) return fail(c, APR_ERR_NR_NOCONV, "h-rho iteration did not converge everywhere");
     return APR_OK;
 }
@@ -375,10 +384,13 @@ static apr_status run_force(apr_ctx* c, bool reuse_density_lists)
         if (s != APR_OK) return s;
         c->lists_fresh = true;
     }
-    int ps = prof_begin(c, APR_PROF_OTHER);
-    s = gather_force_data(c);
-    prof_end(c, ps);
-    if (s != APR_OK) return s;
+    if (!(reuse_density_lists && c->force_data_fresh)) {
+        int ps = prof_begin(c, APR_PROF_OTHER);
+        s = gather_force_data(c);
+        prof_end(c, ps);
+        if (s != APR_OK) return s;
+    }
+    c->force_data_fresh = false;
     s = force_pass(c);
     if (s != APR_OK) return s;
     // lists the density pass built and checked need no second read of the status
@@ -387,7 +399,7 @@ static apr_status run_force(apr_ctx* c, bool reuse_density_lists)
         if (s != APR_OK) return s;
         c->lists_unchecked = false;
     }
-    ps = prof_begin(c, APR_PROF_OTHER);
+    int ps = prof_begin(c, APR_PROF_OTHER);
     s = sink_gravity(c);
     prof_end(c, ps);
     if (s != APR_OK) return s;
@@ -435,6 +447,7 @@ apr_status apr_create(apr_ctx** out, const apr_config* cfg, void* stream)
     c->have_force = false;
     c->coop_blocks = 0;
     c->lists_fresh = false;
+    c->force_data_fresh = false;
     c->prof_attempts = c->prof_unc = c->prof_shrink = 0;
     c->n = c->cap = c->next_id = 0;
     c->step = 0;
@@ -621,6 +634,7 @@ apr_status apr_upload(apr_ctx* c, const apr_particles* host, long long n)
     c->n = n;
     c->dt_valid = false;
     c->lists_fresh = false;
+    c->force_data_fresh = false;
     return APR_OK;
 }
 
@@ -849,6 +863,7 @@ apr_status apr_neighbour_lists(apr_ctx* c, int mode, long long* offsets, int* id
 static apr_status run_density_active(apr_ctx* c, long long nq, bool all)
 {
     Workspace& W = c->W;
+    c->force_data_fresh = false;
     long long unc = 0, noconv = 0, shrinks = 0;
     int attempts = 0, q = 0;
     apr_status s = APR_OK;
@@ -861,7 +876,7 @@ static apr_status run_density_active(apr_ctx* c, long long nq, bool all)
             if (s == APR_OK) s = density_pass(c, &unc, &noconv, W.active_q, nq, q);
         } else {
             s = relist_mark(c, W.retry_q[q], &W.status[ST_RETRY_N + q], attempt == 1);
-            if (s == APR_OK) s = index_refresh_sh(c);
+            if (s == APR_OK) s = index_refresh_sh_queue(c, W.retry_q[q], &W.status[ST_RETRY_N + q]);
             if (s == APR_OK)
                 s = index_lists_queue(c, W.retry_q[q], &W.status[ST_RETRY_N + q], DENSITY_REACH,
                                       true, false);
@@ -979,6 +994,7 @@ apr_status apr_step_bins(apr_ctx* c, double dt_max, int B, int init_bins, apr_co
     }
     c->dt_valid = false;
     c->lists_fresh = false;
+    c->force_data_fresh = false;
     if (s != APR_OK) return s;
     int sat = 0;
     cudaMemcpyAsync(c->hbuf, &W.status[ST_SATURATED], sizeof(int), cudaMemcpyDeviceToHost, c->stream);
@@ -1079,6 +1095,7 @@ apr_status apr_density_loss_grad(apr_ctx* c, long long npar, const long long* pa
     c->have_force = false;
     c->dt_valid = false;
     c->lists_fresh = false;
+    c->force_data_fresh = false;
     return s;
 }
 

@@ -492,6 +492,19 @@ __global__ void k_gather_h(long long n, const unsigned int* __restrict__ perm,
     if (s < n) sh[s] = h[perm[s]];
 }
 
+// the same for the queued slots only (the h of no other slot has changed since it
+// was last needed: between the attempts of a density solve only the queued
+// particles are listed and iterated, and the rebuild after them refreshes all)
+__global__ void k_gather_h_queue(const int* __restrict__ queue, const int* __restrict__ qlen,
+                                 long long n, const unsigned int* __restrict__ perm,
+                                 const double* __restrict__ h, double* __restrict__ sh)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= min((long long)*qlen, n)) return;
+    const int a = queue[i];
+    if (a >= 0 && a < n) sh[a] = h[perm[a]];
+}
+
 // ------------------------------------------------------------ radix tree
 
 __device__ __forceinline__ int prefix_len(const unsigned long long* __restrict__ k, int n, int i,
@@ -709,6 +722,16 @@ apr_status index_refresh_sh(apr_ctx* c)
     return cuda_check(c, cudaGetLastError(), "refresh sh");
 }
 
+apr_status index_refresh_sh_queue(apr_ctx* c, const int* queue, const int* qlen_dev)
+{
+    if (c->n <= 0) return APR_OK;
+    int ps = prof_begin(c, APR_PROF_TREE);
+    APR_LAUNCH(c, k_gather_h_queue, nblocks(c->n, 256), 256, queue, qlen_dev, c->n, c->W.perm,
+               c->p.h, c->W.sh);
+    prof_end(c, ps);
+    return cuda_check(c, cudaGetLastError(), "refresh sh (queue)");
+}
+
 apr_status index_refresh_h(apr_ctx* c)
 {
     if (c->n <= 0) return APR_OK;
@@ -922,6 +945,24 @@ __global__ void k_thresholds(DevCfg dc, long long n, double reach, const double*
     rint[s] = r > 0xffffffffULL ? 0xffffffffu : (unsigned)r;
 }
 
+// thresholds of the queued slots only (gather lists of a queue read no other slot's)
+__global__ void k_thresholds_queue(DevCfg dc, const int* __restrict__ queue,
+                                   const int* __restrict__ qlen, long long n, double reach,
+                                   const double* __restrict__ sh, unsigned long long* __restrict__ thr,
+                                   unsigned int* __restrict__ rint)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= min((long long)*qlen, n)) return;
+    const int s = queue[i];
+    if (s < 0 || s >= n) return;
+    const unsigned long long t = lattice_threshold(dc, reach * sh[s]);
+    thr[s] = t;
+    unsigned long long r = (unsigned long long)ceilf(sqrtf((float)t));
+    while (r > 0 && (r - 1) * (r - 1) >= t) --r;
+    while (r * r < t) ++r;
+    rint[s] = r > 0xffffffffULL ? 0xffffffffu : (unsigned)r;
+}
+
 // exact lists: warp per cell.  The particles of each candidate cell are culled
 // against the cell's bounding box first (exact: a particle whose squared gap to
 // the box is >= the larger threshold reaches no particle inside it), moved to
@@ -1025,25 +1066,58 @@ __device__ __forceinline__ void list_batch_fast(int nb, const int4* __restrict__
                                                 long long cap, unsigned int* __restrict__ nbr,
                                                 int& m)
 {
+    // Per chunk of 32 staged candidates: first the float tests of every
+    // candidate into two bit masks (inside the band's lower edge: a hit; inside
+    // the band: undecided), with no branch or store; then the exact tests of
+    // the undecided ones (rare: only when some lane of the warp has one); then
+    // the hits written in candidate order.  The entries and their order are
+    // those of a test-and-write loop over the candidates.  Idle lanes carry NaN
+    // coordinates, so none of their tests passes.
     const float lo_k = 1.0f - FILTER_EPS, hi_k = 1.0f + FILTER_EPS;
-    for (int l = 0; l < nb; ++l) {
-        const float4 f = cf[l];
-        const float dx = pfx - f.x, dy = pfy - f.y, dz = pfz - f.z;
-        const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        float thf = tfa;  // -1 on idle lanes: nothing passes
-        if (SYM && own) thf = fmaxf(thf, f.w);
-        bool hit;
-        if (r2f < thf * lo_k) {
-            hit = cq[l].w != a;
-        } else if (r2f <= thf * hi_k) {
-            hit = exact_pair<PX, PY, PZ, SYM, false>(cq[l], SYM ? ct[l] : 0ULL, SYM ? cr[l] : 0u, pa,
-                                                     a, own, ta, Ra, Lx, Ly, Lz);
+    for (int base = 0; base < nb; base += 32) {
+        const int cnt = min(32, nb - base);
+        unsigned hit = 0u, band = 0u;
+        if (cnt == 32) {
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j) {
+                const float4 f = cf[base + j];
+                const float dx = pfx - f.x, dy = pfy - f.y, dz = pfz - f.z;
+                const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                const float thf = SYM ? fmaxf(tfa, f.w) : tfa;
+                const float lo = thf * lo_k, hi = thf * hi_k;
+                hit |= (r2f < lo ? 1u : 0u) << j;
+                band |= (r2f >= lo && r2f <= hi ? 1u : 0u) << j;
+            }
         } else {
-            continue;
+            for (int j = 0; j < cnt; ++j) {
+                const float4 f = cf[base + j];
+                const float dx = pfx - f.x, dy = pfy - f.y, dz = pfz - f.z;
+                const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                const float thf = SYM ? fmaxf(tfa, f.w) : tfa;
+                const float lo = thf * lo_k, hi = thf * hi_k;
+                hit |= (r2f < lo ? 1u : 0u) << j;
+                band |= (r2f >= lo && r2f <= hi ? 1u : 0u) << j;
+            }
         }
-        if (hit) {
-            if (m < K) nbr[(long long)m * cap + a] = (unsigned)cq[l].w;
-            ++m;
+        if (__any_sync(0xffffffffu, band != 0u)) {
+            unsigned bm = band;
+            while (bm) {
+                const int j = __ffs(bm) - 1;
+                bm &= bm - 1u;
+                const int l = base + j;
+                if (exact_pair<PX, PY, PZ, SYM, false>(cq[l], SYM ? ct[l] : 0ULL, SYM ? cr[l] : 0u,
+                                                       pa, a, own, ta, Ra, Lx, Ly, Lz))
+                    hit |= 1u << j;
+            }
+        }
+        while (hit) {
+            const int j = __ffs(hit) - 1;
+            hit &= hit - 1u;
+            const int b = cq[base + j].w;
+            if (b != a) {
+                if (m < K) nbr[(long long)m * cap + a] = (unsigned)b;
+                ++m;
+            }
         }
     }
 }
@@ -1131,7 +1205,10 @@ __global__ void __launch_bounds__(LIST_THREADS)
     // the float filter: this lane's coordinates relative to the centre, the float
     // threshold (-1: idle lane), the smallest own R and the largest relative
     // coordinate so far (own particles: at most half the box, rounded up)
-    const float pfx = (float)(pa.x - cx), pfy = (float)(pa.y - cy), pfz = (float)(pa.z - cz);
+    // idle lanes: NaN coordinates (no float test passes) and no threshold
+    const float nan = __int_as_float(0x7fc00000);
+    const float pfx = own ? (float)(pa.x - cx) : nan, pfy = own ? (float)(pa.y - cy) : nan,
+                pfz = own ? (float)(pa.z - cz) : nan;
     const float tfa = own ? (float)ta : -1.0f;
     const unsigned int rmin = __reduce_min_sync(FULL, own ? Ra : 0xffffffffu);
     const long long vown = max(max(hix - lox, hiy - loy), hiz - loz) / 2 + 1;
@@ -1382,13 +1459,17 @@ apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, 
     const int n = (int)c->n;
     if (n <= 0) return APR_OK;
     int ps = prof_begin(c, APR_PROF_LISTS);
-    APR_LAUNCH(c, k_thresholds, nblocks(n, 256), 256, c->dc, n, reach, W.sh, W.sthr, W.sreach,
-               W.status);
     if (sym) {
+        // symmetric lists read every slot's threshold and the nodes' largest h
+        APR_LAUNCH(c, k_thresholds, nblocks(n, 256), 256, c->dc, n, reach, W.sh, W.sthr, W.sreach,
+                   W.status);
         if (n >= 2)
             APR_LAUNCH(c, k_node_thr, nblocks(n - 1, 256), 256, c->dc, n, reach, W.nhmax, W.nthr);
         launch_queue_lists<1>(c, queue, qlen_dev, n, graceful);
     } else {
+        // gather lists read only the queued slots' own thresholds
+        APR_LAUNCH(c, k_thresholds_queue, nblocks(n, 256), 256, c->dc, queue, qlen_dev, n, reach,
+                   W.sh, W.sthr, W.sreach);
         launch_queue_lists<0>(c, queue, qlen_dev, n, graceful);
     }
     prof_end(c, ps);

@@ -22,7 +22,11 @@ constexpr int SORT_SWEEP_MAX_TILES = 256;     // Morton sort: single-sweep passe
 constexpr int SCAN_BLOCK = 1024;             // items per scan block (256 x 4)
 constexpr int RED_BLOCKS = 1216;             // 8 x 152 SMs: fixed-shape f64 reductions
 constexpr int DEFAULT_MAX_NEIGH = 512;
-constexpr float DENSITY_REACH = 1.125f;      // density lists cover r < 2 * 1.125 * h
+// density lists cover r < 2 * 1.06 * h: room for the h-rho iteration to grow h by 6%
+// without a new list (a particle whose root lies farther is retried with a list at
+// its new h); 1.06 measured faster than 1.125 (fewer list entries for the density and
+// force passes to skip) and than 1.03 (more retries) on the tube and both discs
+constexpr float DENSITY_REACH = 1.06f;
 
 // status words written by kernels (device, read back by the host)
 enum {
@@ -85,6 +89,7 @@ struct DevCfg {
     double cs0, qcs;
     double alpha_av, beta_av, alpha_u;
     float alpha_avf, beta_avf, alpha_uf;  // the same in float for the FP32 pair loops
+    float hfactf, gammaf, cs0f, qcsf, m0f;  // float copies for the FP32-mixed density epilogue
     double rsep_fac, dnn_cap;
     double m0;
     int lmax;
@@ -228,6 +233,7 @@ struct apr_ctx {
     int coop_blocks;          // co-resident blocks of the pairing-tree kernel (0: unknown)
     long long prof_attempts, prof_unc, prof_shrink;  // density-solve counters
     bool lists_fresh;         // the current lists hold every pair at the current h
+    bool force_data_fresh;    // the last density solve wrote every slot's force records
     bool lists_unchecked;     // lists were built after the last read of the status words
     bool quiet_pass;          // the last split/merge pass changed nothing
     bool order_valid;         // the kept Morton order is a permutation of the current set
@@ -333,10 +339,14 @@ apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, 
 apr_status index_lists_cells_of(apr_ctx* c, const int* queue, const int* qlen_dev, double reach,
                                 bool graceful);
 apr_status index_refresh_sh(apr_ctx* c);     // re-gather h only (no node h maxima)
+// re-gather the h of the queued slots only
+apr_status index_refresh_sh_queue(apr_ctx* c, const int* queue, const int* qlen_dev);
 
 // SPH passes (apr_sph.cu)
+// force_data: also write the force pass's per-slot records of the iterated particles
 apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv,
-                        const int* active = nullptr, long long nactive = 0, int out_q = 0);
+                        const int* active = nullptr, long long nactive = 0, int out_q = 0,
+                        bool force_data = false);
 apr_status force_pass(apr_ctx* c, const int* active = nullptr, long long nactive = 0);
 apr_status gather_force_data(apr_ctx* c);
 

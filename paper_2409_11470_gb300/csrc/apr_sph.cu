@@ -101,6 +101,42 @@ constexpr int density_min_blocks() { return sizeof(R) == 4 ? 1024 / DENSITY_THRE
 template <typename R>
 constexpr int force_min_blocks() { return sizeof(R) == 4 ? 1024 / force_threads<R>() : 1; }
 
+// one slot's force records: A = (1/h, P/(Omega rho^2), c_s, rho), V = (v, u),
+// B = (P, 1/(Omega rho), h, mass factor).  FP32-mixed: float4, every quotient
+// formed in float from the float values the density solve settled (the gather
+// below forms the same from the stored values, which are exact widenings of
+// them); FP64: four doubles each.
+__device__ __forceinline__ void store_force_data_f(void* A, void* V, void* B, long long s, float h,
+                                                   float r, float om, float P, float cs, double vx,
+                                                   double vy, double vz, double u, int level)
+{
+    ((float4*)A)[s] = make_float4(1.0f / h, P / (om * r * r), cs, r);
+    ((float4*)V)[s] = make_float4((float)vx, (float)vy, (float)vz, (float)u);
+    ((float4*)B)[s] = make_float4(P, 1.0f / (om * r), h, level_mass_f(level));
+}
+
+__device__ __forceinline__ void store_force_data_d(void* A, void* V, void* B, long long s, double h,
+                                                   double r, double om, double P, double cs,
+                                                   double vx, double vy, double vz, double u,
+                                                   int level)
+{
+    double* a = (double*)A + 4 * s;
+    double* v = (double*)V + 4 * s;
+    double* b = (double*)B + 4 * s;
+    a[0] = 1.0 / h;
+    a[1] = P / (om * r * r);
+    a[2] = cs;
+    a[3] = r;
+    v[0] = vx;
+    v[1] = vy;
+    v[2] = vz;
+    v[3] = u;
+    b[0] = P;
+    b[1] = 1.0 / (om * r);
+    b[2] = h;
+    b[3] = level_mass_d(level);
+}
+
 template <typename R, int KT>
 __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
     k_density(DevCfg dc, long long n, long long cap, double reach, const int4* __restrict__ pk,
@@ -114,7 +150,9 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
               double* __restrict__ dnn_out, double* __restrict__ pres_out,
               double* __restrict__ cs_out, int* status, unsigned long long* counters,
               const int* __restrict__ active, long long nactive, int* __restrict__ retry_q,
-              int* __restrict__ retry_n)
+              int* __restrict__ retry_n, const double* __restrict__ vx,
+              const double* __restrict__ vy, const double* __restrict__ vz,
+              void* __restrict__ fA, void* __restrict__ fV, void* __restrict__ fB)
 {
     // FP32: Newton steps are accepted on their predicted successor (below)
     constexpr bool ACCEPT = sizeof(R) == 4;
@@ -264,23 +302,34 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
     // the reach, so the overall nearest counts iff it lies inside 2h
     const unsigned long long thr = lattice_threshold(dc, hd);
     dnn_out[i] = best < thr ? sqrt((double)best) * dc.delta : (double)INFINITY;
-    const double hr = dc.hfact / hd;
-    const double rho = dc.m0 * (double)level_mass_d(pa.w) * hr * hr * hr;
-    rho_out[i] = rho;
-    omega_out[i] = 1.0 - (double)D / (3.0 * (double)target);
-    double P, cs;
     if constexpr (sizeof(R) == 4) {
-        // FP32-mixed: the sound speed at the pair sums' precision (FP64 square
-        // roots, quotients and powers are slow on this part); c_s^2 = gamma (gamma - 1) u
+        // FP32-mixed: density, Omega, pressure, sound speed and the force records
+        // at the pair sums' precision (this part's FP64 unit runs at a small
+        // fraction of the FP32 rate, and float64 quotients and roots here cost
+        // more than the rest of the epilogue); the results are widened on store
+        const float hr = dc.hfactf / h;
+        const float rho = dc.m0f * level_mass_f(pa.w) * hr * hr * hr;
+        const float om = 1.0f - D / (3.0f * target);
+        float P, cs;
         if (dc.eos == APR_EOS_ADIABATIC) {
-            P = (dc.gamma - 1.0) * rho * u[i];
-            cs = (double)sqrtf((float)(dc.gamma * (dc.gamma - 1.0) * u[i]));
+            const float uf = (float)u[i];
+            P = (dc.gammaf - 1.0f) * rho * uf;
+            cs = sqrtf(dc.gammaf * (dc.gammaf - 1.0f) * uf);
         } else {
-            const float Rc = sqrtf((float)(x[i] * x[i] + y[i] * y[i]));
-            cs = (double)((float)dc.cs0 * powf(Rc, -(float)dc.qcs));
+            const float xf = (float)x[i], yf = (float)y[i];
+            cs = dc.cs0f * powf(sqrtf(xf * xf + yf * yf), -dc.qcsf);
             P = cs * cs * rho;
         }
+        rho_out[i] = (double)rho;
+        omega_out[i] = (double)om;
+        pres_out[i] = (double)P;
+        cs_out[i] = (double)cs;
+        if (fA) store_force_data_f(fA, fV, fB, a, h, rho, om, P, cs, vx[i], vy[i], vz[i], u[i], pa.w);
     } else {
+        const double hr = dc.hfact / hd;
+        const double rho = dc.m0 * (double)level_mass_d(pa.w) * hr * hr * hr;
+        const double om = 1.0 - (double)D / (3.0 * (double)target);
+        double P, cs;
         if (dc.eos == APR_EOS_ADIABATIC) {
             P = (dc.gamma - 1.0) * rho * u[i];
             cs = sqrt(dc.gamma * P / rho);
@@ -289,15 +338,18 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
             cs = dc.cs0 * pow(Rc, -dc.qcs);
             P = cs * cs * rho;
         }
+        rho_out[i] = rho;
+        omega_out[i] = om;
+        pres_out[i] = P;
+        cs_out[i] = cs;
+        if (fA) store_force_data_d(fA, fV, fB, a, hd, rho, om, P, cs, vx[i], vy[i], vz[i], u[i], pa.w);
     }
-    pres_out[i] = P;
-    cs_out[i] = cs;
 }
 
 // one Newton-Raphson pass over all particles (active == nullptr) or over the
 // nactive queued ones; particles that need another attempt go to retry_q[out_q]
 apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv, const int* active,
-                        long long nactive, int out_q)
+                        long long nactive, int out_q, bool force_data)
 {
     Workspace& W = c->W;
     const long long n = c->n;
@@ -310,11 +362,16 @@ apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv, con
     if (work > 0) {
         const double reach = DENSITY_REACH;
         const bool c2 = c->cfg.kernel == APR_KERNEL_WENDLAND_C2;
+        const bool f64 = c->cfg.precision == APR_PREC_FP64;
+        void* fa = f64 ? (void*)W.dA : (void*)W.fA;
+        void* fv = f64 ? (void*)W.dV : (void*)W.fV;
+        void* fb = f64 ? (void*)W.dB : (void*)W.fB;
 #define APR_DENSITY(R, KT)                                                                           \
     APR_LAUNCH(c, (k_density<R, KT>), nblocks(work, DENSITY_THREADS), DENSITY_THREADS, c->dc, n, c->cap, reach, W.pk, W.sh,  \
                W.sthr, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm, c->p.x, c->p.y, c->p.u, c->p.h,    \
                c->p.rho, c->p.omega, c->p.dnn, c->p.pres, c->p.cs, W.status, W.counters, active,   \
-               nactive, W.retry_q[out_q], &W.status[ST_RETRY_N + out_q])
+               nactive, W.retry_q[out_q], &W.status[ST_RETRY_N + out_q], c->p.vx, c->p.vy, c->p.vz, \
+               force_data ? fa : nullptr, fv, fb)
         if (c->cfg.precision == APR_PREC_FP64) {
             if (c2) APR_DENSITY(double, APR_KERNEL_WENDLAND_C2);
             else APR_DENSITY(double, APR_KERNEL_M4);
@@ -356,10 +413,10 @@ __global__ void k_gather_force_f32(long long n, const unsigned int* __restrict__
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     unsigned i = perm[s];
-    double r = rho[i], om = omega[i], P = pres[i];
-    A[s] = make_float4((float)(1.0 / h[i]), (float)(P / (om * r * r)), (float)cs[i], (float)r);
-    V[s] = make_float4((float)vx[i], (float)vy[i], (float)vz[i], (float)u[i]);
-    B[s] = make_float4((float)P, (float)(1.0 / (om * r)), (float)h[i], level_mass_f(pk[s].w));
+    // the FP32-mixed density solve stores float values widened to double: the
+    // narrowing is exact, and the records equal the ones it writes itself
+    store_force_data_f(A, V, B, s, (float)h[i], (float)rho[i], (float)omega[i], (float)pres[i],
+                       (float)cs[i], vx[i], vy[i], vz[i], u[i], pk[s].w);
 }
 
 __global__ void k_gather_force_f64(long long n, const unsigned int* __restrict__ perm,
@@ -374,19 +431,8 @@ __global__ void k_gather_force_f64(long long n, const unsigned int* __restrict__
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     unsigned i = perm[s];
-    double r = rho[i], om = omega[i], P = pres[i];
-    A[4 * s + 0] = 1.0 / h[i];
-    A[4 * s + 1] = P / (om * r * r);
-    A[4 * s + 2] = cs[i];
-    A[4 * s + 3] = r;
-    V[4 * s + 0] = vx[i];
-    V[4 * s + 1] = vy[i];
-    V[4 * s + 2] = vz[i];
-    V[4 * s + 3] = u[i];
-    B[4 * s + 0] = P;
-    B[4 * s + 1] = 1.0 / (om * r);
-    B[4 * s + 2] = h[i];
-    B[4 * s + 3] = level_mass_d(pk[s].w);
+    store_force_data_d(A, V, B, s, h[i], rho[i], omega[i], pres[i], cs[i], vx[i], vy[i], vz[i], u[i],
+                       pk[s].w);
 }
 
 apr_status gather_force_data(apr_ctx* c)

@@ -87,16 +87,29 @@ def test_omega_matches_finite_difference_of_density_sum():
         assert abs(omega_fd - o["omega"][a]) < 1e-7
 
 
-def test_enumeration_modes_give_identical_results():
-    w = apr_synth.c1_lattice()
+@pytest.mark.parametrize("make", [apr_synth.c1_lattice, lambda: apr_synth.flyby(3000),
+                                  lambda: apr_synth.sod(6)])
+def test_enumeration_modes_give_identical_results(make):
+    """Brute force and the k-d tree find the same neighbour sets (sorted by index
+    before any sum): on a lattice, on a disc whose h spans two orders of magnitude
+    (midplane to vertical tails; also the sampled force path, which prunes tree
+    nodes by their largest h), and on a periodic tube."""
+    w = make()
     res = []
+    rng = np.random.default_rng(3)
     for mode in (0, 1):
         o = oracle.Oracle(w, enumerate=mode)
         o.density()
         o.force()
-        res.append({f: o[f].copy() for f in ("h", "rho", "omega", "dnn", "ax", "ay", "dudt")})
+        full = {f: o[f].copy() for f in ("h", "rho", "omega", "dnn", "ax", "ay", "dudt", "vsig")}
+        sample = rng.choice(o.n, 50, replace=False) if mode == 0 else sample
+        o["ax"][:] = 0.0
+        o.force(sample)
+        full["ax_sample"] = o["ax"][sample].copy()
+        res.append(full)
     for f in res[0]:
         assert np.array_equal(res[0][f], res[1][f]), f
+    assert np.array_equal(res[1]["ax_sample"], res[1]["ax"][sample])
 
 
 def _float_pairs(x, y, z, h, L=1.0):
