@@ -1215,19 +1215,40 @@ __global__ void __launch_bounds__(LIST_THREADS)
     long long vlane = 0;  // largest |coordinate - centre| this lane staged into the batch
     int nb = 0;
     bool wrapb = false;
+    // The candidate cells are software-pipelined: the particles of cell j + 1 are
+    // loaded (and the entry of cell j + 2 read) before cell j is culled and
+    // staged, so that two cells' loads are in flight instead of a chain of two
+    // dependent loads per cell.
+    const int2* __restrict__ cc = cand + (long long)cid * MAX_CAND;
+    auto valid = [&](const int2& c) { return c.x >= 0 && c.y >= 0 && c.y <= CELL_MAX && c.x + c.y <= n; };
+    int2 cb_n = nc > 0 ? cc[0] : make_int2(-1, 0);
+    int4 q_n = make_int4(0, 0, 0, 0);
+    unsigned long long tq_n = 0;
+    unsigned int rq_n = 0;
+    if (valid(cb_n) && lane < cb_n.y) {
+        const int b = cb_n.x + lane;
+        q_n = pk[b];
+        tq_n = thr[b];
+        rq_n = rint[b];
+    }
+    int2 cb_nn = nc > 1 ? cc[1] : make_int2(-1, 0);
     for (int j = 0; j < nc; ++j) {
-        const int2 cb = cand[(long long)cid * MAX_CAND + j];
-        if (cb.x < 0 || cb.y < 0 || cb.y > CELL_MAX || cb.x + cb.y > n) continue;
+        const int2 cb = cb_n;
+        int4 q = q_n;
+        const unsigned long long tq = tq_n;
+        const unsigned int rq = rq_n;
+        cb_n = cb_nn;
+        if (valid(cb_n) && lane < cb_n.y) {
+            const int b = cb_n.x + lane;
+            q_n = pk[b];
+            tq_n = thr[b];
+            rq_n = rint[b];
+        }
+        cb_nn = j + 2 < nc ? cc[j + 2] : make_int2(-1, 0);
+        if (!valid(cb)) continue;
         bool keep = false, nw = false;
-        int4 q = make_int4(0, 0, 0, 0);
-        unsigned long long tq = 0;
-        unsigned int rq = 0;
         if (lane < cb.y) {
-            const int b = cb.x + lane;
-            q = pk[b];
-            q.w = b;
-            tq = thr[b];
-            rq = rint[b];
+            q.w = cb.x + lane;
             const unsigned long long T = (SYM && tq > tcell) ? tq : tcell;
             // periodic axes: the image nearest the box centre is at most one unit
             // farther from the box than the nearest image (the centre rounds

@@ -1,11 +1,13 @@
 """The periodic sound-wave box of the paper's appendix tests on the GPU: steps
 against the oracle (a small box, the circular zone active from the start), and
-at the paper's size the two quantities the paper reports for it, the density
-blip at the zone and the width of the mixed-level transition.  Measured here
-(M4, no relaxing): a blip of about 7.6% of the initial density at t = 2 (the
-paper: below 5%) and a transition of about 0.4 h; the zone's mean density keeps
-falling after the split, the wave away from the zone is unaffected.  The
-bounds below are set on those measurements with margin."""
+the two quantities the paper reports for it, the density blip at the zone and
+the width of the mixed-level transition.
+
+The paper's bound (a blip below 5% of the initial density) is asserted at 32
+particles across, where the FP64 oracle meets it too (3.8%).  At the paper's 64
+across neither the oracle (8.2%, or 7.3% with the children r_sep apart instead
+of each r_sep from its parent) nor the GPU (about 7.4%) does; there the test
+guards against regressions only, with a bound of twice the paper's."""
 import numpy as np
 import pytest
 
@@ -64,6 +66,17 @@ def run_wave(w, t_end, zone):
     return g, rho0
 
 
+def test_sound_wave_blip_at_32_across_within_the_paper_bound():
+    need_gpu()
+    w = apr_synth.sound_wave_box(32)
+    ref, rho_ic = run_wave(w, 2.0, zone=False)
+    apr, _ = run_wave(w, 2.0, zone=True)
+    assert apr.n > ref.n
+    _, pr = apr_synth.wave_profile(ref.get("x"), ref.get("y"), ref.get("rho"), w["Ly"], nbins=32)
+    _, pa = apr_synth.wave_profile(apr.get("x"), apr.get("y"), apr.get("rho"), w["Ly"], nbins=32)
+    assert np.max(np.abs(pa - pr)) / rho_ic < 0.05
+
+
 @pytest.mark.slow
 def test_sound_wave_blip_and_transition_width():
     need_gpu()
@@ -74,7 +87,7 @@ def test_sound_wave_blip_and_transition_width():
     _, pr = apr_synth.wave_profile(ref.get("x"), ref.get("y"), ref.get("rho"), w["Ly"])
     _, pa = apr_synth.wave_profile(apr.get("x"), apr.get("y"), apr.get("rho"), w["Ly"])
     blip = np.max(np.abs(pa - pr)) / rho_ic
-    assert blip < 0.10
+    assert blip < 0.10  # regression guard: twice the paper's bound (see above)
     fuzz = apr_synth.zone_fuzz(apr.get("x"), apr.get("y"), apr.get("level"), apr.get("h"))
     assert fuzz < 0.5
     # away from the zone the wave is that of the run without it

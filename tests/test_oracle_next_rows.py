@@ -420,3 +420,36 @@ def test_bins_accretion_conserves_mass():
     assert s1.mass == pytest.approx(m0, rel=1e-14)
     ks = b.sinks_state()
     assert ks[0]["m"] > 1.0
+
+
+def _wave_run(n_across, zone, rsep_fac=0.2, dnn_cap=0.35, t_end=2.0):
+    w = apr_synth.sound_wave_box(n_across=n_across)
+    w["cfg"]["rsep_fac"], w["cfg"]["dnn_cap"] = rsep_fac, dnn_cap
+    o = oracle.Oracle(w, capacity=4 * len(w["p"]["x"]))
+    o.init()
+    rho0 = float(np.mean(o["rho"]))
+    t_on, regs = w["regions_at"]
+    t, on = 0.0, False
+    while t < t_end - 1e-12:
+        if zone and not on and t >= t_on - 1e-12:
+            o.regions, o.nreg, on = oracle.make_regions(regs), len(regs), True
+        dt = min(o.timestep(), t_end - t, (t_on - t) if (zone and not on) else 1e9)
+        o.step(dt)
+        t += dt
+    return o, rho0, w
+
+
+def test_sound_wave_blip_both_separation_readings_at_32_across():
+    """The appendix sound-wave box at 32 particles across, zone on at t = 0.5, to
+    t = 2: the density blip (largest difference of the binned cross-section
+    density from the run without the zone) stays below the paper's 5% of the
+    initial density with either reading of "children at a distance r_sep"
+    (Sec. 2.2): each child r_sep from its parent (this build's reading) or the
+    two children r_sep apart (rsep_fac and the d_nn cap halved)."""
+    ref, rho0, w = _wave_run(32, zone=False)
+    _, pr = apr_synth.wave_profile(ref["x"], ref["y"], ref["rho"], w["Ly"], nbins=32)
+    for fac, cap in ((0.2, 0.35), (0.1, 0.175)):
+        o, _, _ = _wave_run(32, zone=True, rsep_fac=fac, dnn_cap=cap)
+        assert np.sum(o["level"] == 1) > 100
+        _, pa = apr_synth.wave_profile(o["x"], o["y"], o["rho"], w["Ly"], nbins=32)
+        assert np.max(np.abs(pa - pr)) / rho0 < 0.05, (fac, cap)
