@@ -443,7 +443,7 @@ def run_ours(args):
         if dom["group"] in FLOPS_PER_PAIR:
             tr = traffic_record(f"k_{dom['group']}_f32", args.workload)
         elif dom["group"] == "lists":
-            tr = traffic_record("k_lists", args.workload)
+            tr = traffic_record("lists", args.workload)
         roofline = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
                     "unit": dom["unit"], "frac": dom["frac"],
                     "traffic": tr["dram_bytes_per_launch"] * (r32["n_after_init"] / tr["n"])

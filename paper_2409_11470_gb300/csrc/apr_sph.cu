@@ -84,6 +84,30 @@ __device__ __forceinline__ double rel_r2<double>(const DevCfg& dc, const int*, c
     return d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
 }
 
+// The nearest lattice neighbour (the exact integer minimum of the squared lattice
+// distance over the list).  FP64: every entry's exact square.  FP32: the exact
+// square only of entries whose float r^2 lies within a relative 2^-20 of the
+// smallest float r^2 seen so far.  This is the exact minimum: the float r^2 of any
+// entry is its exact lattice r^2 times the (power-of-two) unit squared, to a
+// relative 5 u (u = 2^-24: three conversions, three products, two sums), so the
+// exact nearest's float r^2 is within a relative 10.1 u of the smallest float
+// r^2 of the list, hence within 2^-20 = 16 u of the running minimum when it is
+// met; the entries skipped are farther than it.
+template <typename R>
+__device__ __forceinline__ void near_update(R r2f, const int d[3], R& bestf, unsigned long long& best)
+{
+    if constexpr (sizeof(R) == 4) {
+        if (r2f <= bestf * (1.0f + 1.0f / (1 << 20))) {
+            const unsigned long long q = lattice_sq(d);
+            best = q < best ? q : best;
+            bestf = fminf(bestf, r2f);
+        }
+    } else {
+        const unsigned long long q = lattice_sq(d);
+        best = q < best ? q : best;
+    }
+}
+
 // Newton-Raphson on g(h) with a bracket over this particle's (symmetric,
 // reach-scaled) list; the first pass also finds the nearest lattice neighbour.
 // Four list entries are loaded ahead so that several gathers are in flight.
@@ -110,9 +134,22 @@ __device__ __forceinline__ void store_force_data_f(void* A, void* V, void* B, lo
                                                    float r, float om, float P, float cs, double vx,
                                                    double vy, double vz, double u, int level)
 {
-    ((float4*)A)[s] = make_float4(1.0f / h, P / (om * r * r), cs, r);
+    if (B) {
+        ((float4*)A)[s] = make_float4(1.0f / h, P / (om * r * r), cs, r);
+        ((float4*)B)[s] = make_float4(P, 1.0f / (om * r), h, level_mass_f(level));
+    } else {
+        // without conductivity the force needs of B only 1/(Omega rho) (here in A's
+        // last slot) and the mass (from the level): two records per slot
+        ((float4*)A)[s] = make_float4(1.0f / h, P / (om * r * r), cs, 1.0f / (om * r));
+    }
     ((float4*)V)[s] = make_float4((float)vx, (float)vy, (float)vz, (float)u);
-    ((float4*)B)[s] = make_float4(P, 1.0f / (om * r), h, level_mass_f(level));
+}
+
+// the FP32-mixed force records use the two-record layout (A, V) unless the run
+// has artificial conductivity, which needs pressure and density of the neighbour
+__host__ __device__ inline bool force_two_records(const DevCfg& dc)
+{
+    return !(dc.eos == APR_EOS_ADIABATIC && dc.alpha_u > 0.0);
 }
 
 __device__ __forceinline__ void store_force_data_d(void* A, void* V, void* B, long long s, double h,
@@ -186,6 +223,8 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
     bool conv = false, uncovered = false;
     unsigned int npair = 0;
     unsigned long long best = ~0ULL;
+    // FP32: the nearest lattice neighbour through the float r^2 (see near_update)
+    R bestf = R(INFINITY);
     for (int it = 0; it < dc.nr_maxit; ++it) {
         const R hinv = R(1) / h;
         const R r2max = R(4) * h * h;
@@ -213,30 +252,28 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
             lattice_d(dc, pa, p1, d1);
             lattice_d(dc, pa, p2, d2);
             lattice_d(dc, pa, p3, d3);
+            const R r0 = rel_r2<R>(dc, d0, sx, sy, sz, a, b0), r1 = rel_r2<R>(dc, d1, sx, sy, sz, a, b1);
+            const R r2 = rel_r2<R>(dc, d2, sx, sy, sz, a, b2), r3 = rel_r2<R>(dc, d3, sx, sy, sz, a, b3);
             if (first_pass) {
                 // the nearest lattice neighbour, on the first pass only
-                const unsigned long long q0 = lattice_sq(d0), q1 = lattice_sq(d1);
-                const unsigned long long q2 = lattice_sq(d2), q3 = lattice_sq(d3);
-                best = q0 < best ? q0 : best;
-                best = q1 < best ? q1 : best;
-                best = q2 < best ? q2 : best;
-                best = q3 < best ? q3 : best;
+                near_update<R>(r0, d0, bestf, best);
+                near_update<R>(r1, d1, bestf, best);
+                near_update<R>(r2, d2, bestf, best);
+                near_update<R>(r3, d3, bestf, best);
             }
-            density_term<KT, ACCEPT, R>(rel_r2<R>(dc, d0, sx, sy, sz, a, b0), hinv, r2max, p0.w, S, T, U, npair);
-            density_term<KT, ACCEPT, R>(rel_r2<R>(dc, d1, sx, sy, sz, a, b1), hinv, r2max, p1.w, S, T, U, npair);
-            density_term<KT, ACCEPT, R>(rel_r2<R>(dc, d2, sx, sy, sz, a, b2), hinv, r2max, p2.w, S, T, U, npair);
-            density_term<KT, ACCEPT, R>(rel_r2<R>(dc, d3, sx, sy, sz, a, b3), hinv, r2max, p3.w, S, T, U, npair);
+            density_term<KT, ACCEPT, R>(r0, hinv, r2max, p0.w, S, T, U, npair);
+            density_term<KT, ACCEPT, R>(r1, hinv, r2max, p1.w, S, T, U, npair);
+            density_term<KT, ACCEPT, R>(r2, hinv, r2max, p2.w, S, T, U, npair);
+            density_term<KT, ACCEPT, R>(r3, hinv, r2max, p3.w, S, T, U, npair);
         }
         for (; k < m; ++k) {
             const int b = (int)col[(long long)k * cap];
             const int4 pb = pk[b];
             int d[3];
             lattice_d(dc, pa, pb, d);
-            if (first_pass) {
-                const unsigned long long q = lattice_sq(d);
-                best = q < best ? q : best;
-            }
-            density_term<KT, ACCEPT, R>(rel_r2<R>(dc, d, sx, sy, sz, a, b), hinv, r2max, pb.w, S, T, U, npair);
+            const R rb = rel_r2<R>(dc, d, sx, sy, sz, a, b);
+            if (first_pass) near_update<R>(rb, d, bestf, best);
+            density_term<KT, ACCEPT, R>(rb, hinv, r2max, pb.w, S, T, U, npair);
         }
         const R g = (S.s + mua) - target;           // pi h^3 (rho_sum - rho_h) / m0
         const R dg = -(T.s) * hinv;                   // dg/dh >= 0
@@ -324,7 +361,9 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
         omega_out[i] = (double)om;
         pres_out[i] = (double)P;
         cs_out[i] = (double)cs;
-        if (fA) store_force_data_f(fA, fV, fB, a, h, rho, om, P, cs, vx[i], vy[i], vz[i], u[i], pa.w);
+        if (fA)
+            store_force_data_f(fA, fV, force_two_records(dc) ? nullptr : fB, a, h, rho, om, P, cs, vx[i],
+                               vy[i], vz[i], u[i], pa.w);
     } else {
         const double hr = dc.hfact / hd;
         const double rho = dc.m0 * (double)level_mass_d(pa.w) * hr * hr * hr;
@@ -416,7 +455,7 @@ __global__ void k_gather_force_f32(long long n, const unsigned int* __restrict__
     // the FP32-mixed density solve stores float values widened to double: the
     // narrowing is exact, and the records equal the ones it writes itself
     store_force_data_f(A, V, B, s, (float)h[i], (float)rho[i], (float)omega[i], (float)pres[i],
-                       (float)cs[i], vx[i], vy[i], vz[i], u[i], pk[s].w);
+                       (float)cs[i], vx[i], vy[i], vz[i], u[i], pk[s].w);  // B null: two records
 }
 
 __global__ void k_gather_force_f64(long long n, const unsigned int* __restrict__ perm,
@@ -447,7 +486,7 @@ apr_status gather_force_data(apr_ctx* c)
     else
         APR_LAUNCH(c, k_gather_force_f32, nblocks(n, 256), 256, 
             n, W.perm, W.pk, c->p.h, c->p.rho, c->p.omega, c->p.pres, c->p.cs, c->p.vx, c->p.vy,
-            c->p.vz, c->p.u, W.fA, W.fV, W.fB);
+            c->p.vz, c->p.u, W.fA, W.fV, force_two_records(c->dc) ? nullptr : W.fB);
     return cuda_check(c, cudaGetLastError(), "gather force data");
 }
 
@@ -478,12 +517,15 @@ struct ForceSelf {
     R hinv, h4, pro, cs, rho, P, ior, vx, vy, vz, u;
 };
 
-// one pair of the force / energy sums (pairs outside both supports add nothing)
-template <int KT, typename R>
+// one pair of the force / energy sums (pairs outside both supports add nothing);
+// B2: the two-record layout (1/(Omega rho) in A's last slot, mass from the level,
+// no conductivity)
+template <int KT, typename R, bool B2>
 __device__ __forceinline__ void force_pair(const DevCfg& dc, const ForceSelf<R>& A, const R d[3],
                                            const F4<R>& Ab, const F4<R>& Vb, const F4<R>& Bb,
-                                           bool adiabatic, bool cond, Acc<R>& fx, Acc<R>& fy,
-                                           Acc<R>& fz, Acc<R>& du, R& vsig, unsigned int& npair)
+                                           int levb, bool adiabatic, bool cond, Acc<R>& fx,
+                                           Acc<R>& fy, Acc<R>& fz, Acc<R>& du, R& vsig,
+                                           unsigned int& npair)
 {
     const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     const R rinv = Num<R>::rsqrt_(r2);
@@ -514,16 +556,16 @@ __device__ __forceinline__ void force_pair(const DevCfg& dc, const ForceSelf<R>&
         const R vsa = alpha * A.cs - beta * vr;
         const R vsb = alpha * Ab.z - beta * vr;
         ta -= R(0.5) * vsa * vr * A.ior;
-        tb -= R(0.5) * vsb * vr * Bb.y;
+        tb -= R(0.5) * vsb * vr * (B2 ? Ab.w : Bb.y);
     }
-    const R mub = Bb.w;
+    const R mub = B2 ? Num<R>::mass(levb) : Bb.w;
     const R fac = mub * (ta * Fa + tb * Fb) * rinv;
     fx.add(-fac * d[0]);
     fy.add(-fac * d[1]);
     fz.add(-fac * d[2]);
     if (adiabatic) {
         R e = mub * ta * vr * Fa;
-        if (cond) {
+        if (!B2 && cond) {
             const R dP = A.P - Bb.x;
             const R vsu = Num<R>::sqrt_(fabs(dP) / (R(0.5) * (A.rho + Ab.w)));
             e += mub * alpha_u * vsu * (A.u - Vb.w) * R(0.5) * (Fa * A.ior + Fb * Bb.y);
@@ -534,7 +576,8 @@ __device__ __forceinline__ void force_pair(const DevCfg& dc, const ForceSelf<R>&
     vsig = vs > vsig ? vs : vsig;
 }
 
-template <typename R, int KT>
+// B2: the two-record layout (A, V) of runs without conductivity (FP32-mixed)
+template <typename R, int KT, bool B2>
 __global__ void __launch_bounds__(force_threads<R>(), force_min_blocks<R>())
     k_force(DevCfg dc, long long n, long long cap, const int4* __restrict__ pk,
             const void* __restrict__ Abuf, const void* __restrict__ Vbuf,
@@ -552,7 +595,8 @@ __global__ void __launch_bounds__(force_threads<R>(), force_min_blocks<R>())
     const int a = active ? active[s] : (int)s;
     if (a < 0 || a >= n) return;
     const int4 pa = pk[a];
-    const F4<R> Aa = ld4<R>(Abuf, a), Va = ld4<R>(Vbuf, a), Ba = ld4<R>(Bbuf, a);
+    const F4<R> Aa = ld4<R>(Abuf, a), Va = ld4<R>(Vbuf, a);
+    const F4<R> Ba = B2 ? F4<R>{R(0), R(0), R(0), R(0)} : ld4<R>(Bbuf, a);
     ForceSelf<R> A;
     A.hinv = Aa.x;
     A.h4 = Aa.x * Aa.x * Aa.x * Aa.x;
@@ -560,7 +604,7 @@ __global__ void __launch_bounds__(force_threads<R>(), force_min_blocks<R>())
     A.cs = Aa.z;
     A.rho = Aa.w;
     A.P = Ba.x;
-    A.ior = Ba.y;
+    A.ior = B2 ? Aa.w : Ba.y;
     A.vx = Va.x;
     A.vy = Va.y;
     A.vz = Va.z;
@@ -580,26 +624,27 @@ __global__ void __launch_bounds__(force_threads<R>(), force_min_blocks<R>())
         n0 = col[0];
         n1 = col[cap];
     }
+    const F4<R> zero{R(0), R(0), R(0), R(0)};
     for (; k + 2 <= m; k += 2) {
         const int b0 = (int)n0, b1 = (int)n1;
         n0 = col[(long long)min(k + 2, m - 1) * cap];
         n1 = col[(long long)min(k + 3, m - 1) * cap];
         const int4 p0 = pk[b0], p1 = pk[b1];
-        const F4<R> A0 = ld4<R>(Abuf, b0), V0 = ld4<R>(Vbuf, b0), B0 = ld4<R>(Bbuf, b0);
-        const F4<R> A1 = ld4<R>(Abuf, b1), V1 = ld4<R>(Vbuf, b1), B1 = ld4<R>(Bbuf, b1);
+        const F4<R> A0 = ld4<R>(Abuf, b0), V0 = ld4<R>(Vbuf, b0), B0 = B2 ? zero : ld4<R>(Bbuf, b0);
+        const F4<R> A1 = ld4<R>(Abuf, b1), V1 = ld4<R>(Vbuf, b1), B1 = B2 ? zero : ld4<R>(Bbuf, b1);
         R d0[3], d1[3];
         Rel<R>::get(dc, pa, p0, sx, sy, sz, a, b0, d0);
         Rel<R>::get(dc, pa, p1, sx, sy, sz, a, b1, d1);
-        force_pair<KT, R>(dc, A, d0, A0, V0, B0, adiabatic, cond, fx, fy, fz, du, vsig, npair);
-        force_pair<KT, R>(dc, A, d1, A1, V1, B1, adiabatic, cond, fx, fy, fz, du, vsig, npair);
+        force_pair<KT, R, B2>(dc, A, d0, A0, V0, B0, p0.w, adiabatic, cond, fx, fy, fz, du, vsig, npair);
+        force_pair<KT, R, B2>(dc, A, d1, A1, V1, B1, p1.w, adiabatic, cond, fx, fy, fz, du, vsig, npair);
     }
     for (; k < m; ++k) {
         const int b = (int)col[(long long)k * cap];
         const int4 pb = pk[b];
-        const F4<R> Ab = ld4<R>(Abuf, b), Vb = ld4<R>(Vbuf, b), Bb = ld4<R>(Bbuf, b);
+        const F4<R> Ab = ld4<R>(Abuf, b), Vb = ld4<R>(Vbuf, b), Bb = B2 ? zero : ld4<R>(Bbuf, b);
         R d[3];
         Rel<R>::get(dc, pa, pb, sx, sy, sz, a, b, d);
-        force_pair<KT, R>(dc, A, d, Ab, Vb, Bb, adiabatic, cond, fx, fy, fz, du, vsig, npair);
+        force_pair<KT, R, B2>(dc, A, d, Ab, Vb, Bb, pb.w, adiabatic, cond, fx, fy, fz, du, vsig, npair);
     }
     if (dc.prof) atomicAdd(&counters[APR_PROF_FORCE], (unsigned long long)npair);
     const double scale = dc.m0_knorm;
@@ -619,16 +664,19 @@ apr_status force_pass(apr_ctx* c, const int* active, long long nactive)
     if (n <= 0 || work <= 0) return APR_OK;
     const int ps = prof_begin(c, APR_PROF_FORCE);
     const bool c2 = c->cfg.kernel == APR_KERNEL_WENDLAND_C2;
-#define APR_FORCE(R, KT, A, V, B)                                                                    \
-    APR_LAUNCH(c, (k_force<R, KT>), nblocks(work, force_threads<R>()), force_threads<R>(), c->dc, n, c->cap, W.pk, A, V, B, W.nbr, \
+#define APR_FORCE(R, KT, B2, A, V, B)                                                                \
+    APR_LAUNCH(c, (k_force<R, KT, B2>), nblocks(work, force_threads<R>()), force_threads<R>(), c->dc, n, c->cap, W.pk, A, V, B, W.nbr, \
                W.ncnt, W.sx, W.sy, W.sz, W.perm, c->p.ax, c->p.ay, c->p.az, c->p.dudt, c->p.vsig,   \
                W.counters, active, nactive)
     if (c->cfg.precision == APR_PREC_FP64) {
-        if (c2) APR_FORCE(double, APR_KERNEL_WENDLAND_C2, W.dA, W.dV, W.dB);
-        else APR_FORCE(double, APR_KERNEL_M4, W.dA, W.dV, W.dB);
+        if (c2) APR_FORCE(double, APR_KERNEL_WENDLAND_C2, false, W.dA, W.dV, W.dB);
+        else APR_FORCE(double, APR_KERNEL_M4, false, W.dA, W.dV, W.dB);
+    } else if (force_two_records(c->dc)) {
+        if (c2) APR_FORCE(float, APR_KERNEL_WENDLAND_C2, true, W.fA, W.fV, W.fB);
+        else APR_FORCE(float, APR_KERNEL_M4, true, W.fA, W.fV, W.fB);
     } else {
-        if (c2) APR_FORCE(float, APR_KERNEL_WENDLAND_C2, W.fA, W.fV, W.fB);
-        else APR_FORCE(float, APR_KERNEL_M4, W.fA, W.fV, W.fB);
+        if (c2) APR_FORCE(float, APR_KERNEL_WENDLAND_C2, false, W.fA, W.fV, W.fB);
+        else APR_FORCE(float, APR_KERNEL_M4, false, W.fA, W.fV, W.fB);
     }
 #undef APR_FORCE
     prof_end(c, ps);
