@@ -1474,7 +1474,7 @@ static void launch_queue_lists(apr_ctx* c, const int* queue, const int* qlen_dev
 }
 
 apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, double reach,
-                             bool graceful, bool sym)
+                             bool graceful, bool sym, double node_reach)
 {
     Workspace& W = c->W;
     const int n = (int)c->n;
@@ -1485,7 +1485,8 @@ apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, 
         APR_LAUNCH(c, k_thresholds, nblocks(n, 256), 256, c->dc, n, reach, W.sh, W.sthr, W.sreach,
                    W.status);
         if (n >= 2)
-            APR_LAUNCH(c, k_node_thr, nblocks(n - 1, 256), 256, c->dc, n, reach, W.nhmax, W.nthr);
+            APR_LAUNCH(c, k_node_thr, nblocks(n - 1, 256), 256, c->dc, n,
+                       node_reach > 0.0 ? node_reach : reach, W.nhmax, W.nthr);
         launch_queue_lists<1>(c, queue, qlen_dev, n, graceful);
     } else {
         // gather lists read only the queued slots' own thresholds
@@ -1577,6 +1578,32 @@ apr_status relist_mark(apr_ctx* c, const int* queue, const int* qlen_dev, bool f
     return cuda_check(c, cudaGetLastError(), "relist mark");
 }
 
+// After a density solve with retries, the radix tree's largest h per node is
+// brought up to date without a bottom-up pass over the whole tree: a particle that
+// converged on its first list ended within that list's reach, reach x its h at the
+// build, so reach x the build's node maximum bounds it; a retried particle raises
+// its ancestors' maxima itself.  The values are stored in build units (h / reach,
+// rounded up) and compared as their float64 bit patterns, which order like the
+// values for positive numbers; an ancestor already at or above the value stops
+// the walk (every ancestor of a node holds at least its maximum).
+__global__ void k_hmax_raise(const int* __restrict__ queue, const int* __restrict__ qlen, int n,
+                             const double* __restrict__ sh, const int* __restrict__ parent_leaf,
+                             const int* __restrict__ parent_int, double* nhmax, double inv_reach)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= min(*qlen, n) || n < 2) return;
+    const int s = queue[i];
+    if (s < 0 || s >= n) return;
+    const double v = sh[s] * inv_reach * (1.0 + 0x1p-50);
+    const unsigned long long vb = (unsigned long long)__double_as_longlong(v);
+    int node = parent_leaf[s];
+    for (int depth = 0; depth < 4 * 64 && node >= 0 && node < n - 1; ++depth) {
+        const unsigned long long old = atomicMax((unsigned long long*)&nhmax[node], vb);
+        if (old >= vb || node == 0) break;
+        node = parent_int[node];
+    }
+}
+
 apr_status relist_finish(apr_ctx* c)
 {
     Workspace& W = c->W;
@@ -1589,9 +1616,17 @@ apr_status relist_finish(apr_ctx* c)
                &W.status[ST_RETRIED_N], W.nbr, W.ncnt, W.pk, W.perm, c->p.h, W.sthr0, W.qmark,
                W.relist_q, &W.status[ST_RELIST_N]);
     prof_end(c, ps);
-    apr_status s = index_refresh_h(c);
+    apr_status s = index_refresh_sh(c);
     if (s != APR_OK) return s;
-    return index_lists_queue(c, W.relist_q, &W.status[ST_RELIST_N], 1.0, false);
+    ps = prof_begin(c, APR_PROF_TREE);
+    // the retried particles are the first ST_RETRIED_N entries of the relist queue
+    APR_LAUNCH(c, k_hmax_raise, nblocks(n, 256), 256, W.relist_q, &W.status[ST_RETRIED_N], n, W.sh,
+               W.parent_leaf, W.parent_int, W.nhmax, 1.0 / (double)DENSITY_REACH);
+    prof_end(c, ps);
+    s = cuda_check(c, cudaGetLastError(), "node h raise");
+    if (s != APR_OK) return s;
+    return index_lists_queue(c, W.relist_q, &W.status[ST_RELIST_N], 1.0, false, true,
+                             (double)DENSITY_REACH);
 }
 
 apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful)

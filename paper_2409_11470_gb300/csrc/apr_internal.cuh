@@ -332,9 +332,10 @@ apr_status relist_finish(apr_ctx* c);
 // graceful: an overflowing list is marked (count -1) instead of flagged as an error.
 apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful = false);
 // lists of the queued particles only, by a per-particle tree walk: symmetric
-// (sym) or gather lists
+// (sym) or gather lists; node_reach > 0: the nodes' largest h are in units of
+// h / node_reach (see relist_finish)
 apr_status index_lists_queue(apr_ctx* c, const int* queue, const int* qlen_dev, double reach,
-                             bool graceful = true, bool sym = true);
+                             bool graceful = true, bool sym = true, double node_reach = -1.0);
 // symmetric lists of every particle in a cell that holds a queued particle
 apr_status index_lists_cells_of(apr_ctx* c, const int* queue, const int* qlen_dev, double reach,
                                 bool graceful);
