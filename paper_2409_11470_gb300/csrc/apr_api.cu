@@ -149,7 +149,7 @@ size_t workspace_layout(const apr_config& cfg, long long cap, char* base, Worksp
     w.acell_cnt = (int*)take(4 * C);
     w.acell_node = (int*)take(4 * C);
     w.amark = (unsigned char*)take(C);
-    w.cand = (int2*)take(8 * (size_t)MAX_CAND * C);
+    w.cand = (int2*)take(8 * (size_t)max_cand_of((int)K) * C);
     w.ncand = (int*)take(4 * C);
     w.point_q = (int*)take(4 * C);
     w.retry_q[0] = (int*)take(4 * C);
@@ -277,6 +277,7 @@ static apr_status check_cfg(const apr_config* cfg, DevCfg* dc, std::string* why)
                                    : (cfg->precision == APR_PREC_FP64 ? 1e-12 : 1e-6);
     dc->nr_maxit = cfg->nr_maxit > 0 ? cfg->nr_maxit : 50;
     dc->max_neigh = cfg->max_neigh > 0 ? cfg->max_neigh : DEFAULT_MAX_NEIGH;
+    dc->max_cand = max_cand_of(dc->max_neigh);
     return APR_OK;
 }
 

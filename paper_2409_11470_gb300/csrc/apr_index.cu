@@ -903,7 +903,7 @@ __global__ void __launch_bounds__(128)
             const unsigned cm = __ballot_sync(0xffffffffu, pass && cell);
             if (pass && cell) {
                 const int pos = k + __popc(cm & lt);
-                if (pos < MAX_CAND) cand[(long long)cid * MAX_CAND + pos] = make_int2(first, count);
+                if (pos < dc.max_cand) cand[(long long)cid * dc.max_cand + pos] = make_int2(first, count);
             }
             k += __popc(cm);
             const unsigned im = __ballot_sync(0xffffffffu, pass && !cell);
@@ -921,7 +921,7 @@ __global__ void __launch_bounds__(128)
             sp += 2 * nint;
             __syncwarp();
         }
-        overflow = overflow || k > MAX_CAND;
+        overflow = overflow || k > dc.max_cand;
         // an overflowed cell is not an error: its particles take the per-particle search
         if (lane == 0) ncand[cid] = overflow ? -1 : k;
     }
@@ -1219,7 +1219,7 @@ __global__ void __launch_bounds__(LIST_THREADS)
     // loaded (and the entry of cell j + 2 read) before cell j is culled and
     // staged, so that two cells' loads are in flight instead of a chain of two
     // dependent loads per cell.
-    const int2* __restrict__ cc = cand + (long long)cid * MAX_CAND;
+    const int2* __restrict__ cc = cand + (long long)cid * dc.max_cand;
     auto valid = [&](const int2& c) { return c.x >= 0 && c.y >= 0 && c.y <= CELL_MAX && c.x + c.y <= n; };
     int2 cb_n = nc > 0 ? cc[0] : make_int2(-1, 0);
     int4 q_n = make_int4(0, 0, 0, 0);

@@ -16,12 +16,20 @@ constexpr int COORD_BITS = 30;               // lattice coordinates are in [0, 2
 constexpr long long COORD_MAX = (1LL << COORD_BITS) - 1;
 constexpr int CELL_MAX = 32;                 // particles per cell (one warp)
 constexpr int KEY_BITS = 16;                 // Morton key bits per axis (48-bit keys, 6 passes)
-constexpr int MAX_CAND = 128;                // candidate cells per cell
+// candidate cells per cell: 128, or 256 for runs with neighbour lists longer than
+// the default (discs, whose sparse vertical tails have large h: more of their cells
+// keep their candidates instead of falling back to per-particle tree walks; on the
+// uniform shock tube 256 cost 11% of the list time, on the flyby it saved 6%)
+constexpr int MAX_CAND_SMALL = 128, MAX_CAND_LARGE = 256;
 constexpr int RADIX_TILE = 2048;             // items per radix-sort block (256 x 8)
 constexpr int SORT_SWEEP_MAX_TILES = 256;     // Morton sort: single-sweep passes up to this many tiles
 constexpr int SCAN_BLOCK = 1024;             // items per scan block (256 x 4)
 constexpr int RED_BLOCKS = 1216;             // 8 x 152 SMs: fixed-shape f64 reductions
 constexpr int DEFAULT_MAX_NEIGH = 512;
+inline int max_cand_of(int max_neigh)
+{
+    return max_neigh > DEFAULT_MAX_NEIGH ? MAX_CAND_LARGE : MAX_CAND_SMALL;
+}
 // density lists cover r < 2 * 1.06 * h: room for the h-rho iteration to grow h by 6%
 // without a new list (a particle whose root lies farther is retried with a list at
 // its new h); 1.06 measured faster than 1.125 (fewer list entries for the density and
@@ -31,7 +39,7 @@ constexpr float DENSITY_REACH = 1.06f;
 // status words written by kernels (device, read back by the host)
 enum {
     ST_NEIGH_OVERFLOW = 0,   // a particle's list exceeded max_neigh
-    ST_CAND_OVERFLOW = 1,    // a cell's candidate list exceeded MAX_CAND
+    ST_CAND_OVERFLOW = 1,    // a cell's candidate list exceeded max_cand
     ST_UNCOVERED = 2,        // density: h grew beyond the list's reach
     ST_NOCONV = 3,           // density: Newton-Raphson not converged
     ST_COUNT_A = 4,          // generic counters for split/merge passes
@@ -98,6 +106,7 @@ struct DevCfg {
     double nr_tol;
     int nr_maxit;
     int max_neigh;
+    int max_cand;              // candidate cells per cell (MAX_CAND_SMALL or _LARGE)
     int prof;                  // count pair evaluations into Workspace::counters
     int kernel;                // APR_KERNEL_M4 or APR_KERNEL_WENDLAND_C2
     double knorm_inv;          // W = f(q) / (knorm_inv h^3): pi (M4), 16 pi / 21 (Wendland C2)
@@ -171,7 +180,7 @@ struct Workspace {
     int* acell_cnt;
     int* acell_node;
     unsigned char* amark;     // per sorted slot: queued
-    int2* cand;               // MAX_CAND (first slot, count) per cell
+    int2* cand;               // max_cand (first slot, count) per cell
     int* ncand;
     int* point_q;             // particles of cells whose candidate list overflowed
     int* retry_q[2];          // density: particles that need another attempt
