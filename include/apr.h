@@ -308,6 +308,21 @@ apr_status apr_timestep(apr_ctx* ctx, double* dt);
 apr_status apr_stats_compute(apr_ctx* ctx, apr_stats* stats);
 
 /*
+ * Memory layout, no counterpart in the paper: permutes every bound particle
+ * array (all fields of apr_particles, bin too when bound) in place into the
+ * order of the index's last Morton sort (sorting first if the particle set
+ * changed since), so that particles close in space sit close in memory and the
+ * passes' gathers through the sort read consecutive addresses.  Ids travel with
+ * their particles; indices the caller kept from before (apr_merge_pairs, the
+ * parents of apr_density_loss_grad) name other particles afterwards.  Later
+ * results are those without the call, except for the order of equal Morton
+ * keys in the next sort and hence the summation order of sums.  The
+ * neighbour-list memory is its scratch, so the next pass rebuilds the lists.
+ * Errors: APR_ERR_STATE before apr_bind; APR_ERR_CUDA on a launch error.
+ */
+apr_status apr_reorder(apr_ctx* ctx);
+
+/*
  * Debug / parity: neighbour lists on the quantised lattice at the current h,
  * into HOST buffers in CSR form (offsets[n+1], idx[total]; particle indices
  * in the caller's order; order within a list unspecified).  mode 0: b != a

@@ -107,6 +107,7 @@ def _load():
         "apr_step": [vp, C.c_double, P(C.c_double), P(Stats), P(Counts)],
         "apr_timestep": [vp, P(C.c_double)],
         "apr_stats_compute": [vp, P(Stats)],
+        "apr_reorder": [vp],
         "apr_neighbour_lists": [vp, i32, P(ll), P(i32), ll, P(ll)],
         "apr_merge_pairs": [vp, i32, P(ll), ll, P(ll), P(ll)],
         "apr_profile_enable": [vp, i32],
@@ -362,6 +363,11 @@ class Simulation:
         st = Stats()
         self._check(lib.apr_stats_compute(self.ctx, C.byref(st)), "stats")
         return st
+
+    def reorder(self):
+        """Permute the bound arrays into the index's Morton order (apr_reorder);
+        ids travel with their particles."""
+        self._check(lib.apr_reorder(self.ctx), "reorder")
 
     def neighbour_lists(self, mode=0, cap=None):
         n = self.n

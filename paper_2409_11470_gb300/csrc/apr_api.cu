@@ -693,6 +693,13 @@ apr_status apr_get_count(apr_ctx* c, long long* n, long long* next_id, unsigned 
     return APR_OK;
 }
 
+apr_status apr_reorder(apr_ctx* c)
+{
+    if (!c) return APR_ERR_ARG;
+    if (!c->bound) return fail(c, APR_ERR_STATE, "apr_bind first");
+    return reorder(c);
+}
+
 apr_status apr_sph_density(apr_ctx* c, long long* n_unconverged)
 {
     if (!c) return APR_ERR_ARG;

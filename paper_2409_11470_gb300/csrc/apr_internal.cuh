@@ -396,6 +396,7 @@ apr_status adjoint_children(apr_ctx* c, long long npar, const long long* parent,
 apr_status adjoint_sums(apr_ctx* c, long long n, long long npar, double* loss, double* grad_d,
                         double* grad_hc);
 apr_status compact(apr_ctx* c, long long* removed);
+apr_status reorder(apr_ctx* c);  // bound arrays into the index's Morton order
 
 inline int nblocks(long long n, int bs) { return (int)((n + bs - 1) / bs); }
 

@@ -1435,6 +1435,52 @@ apr_status compact(apr_ctx* c, long long* removed)
     return cuda_check(c, cudaGetLastError(), "compaction");
 }
 
+// every field of the particle in canonical slot perm[j] to position j of the scratch:
+// scattered reads, coalesced writes; k_compact_back then writes the fields back in order
+__global__ void k_reorder_out(long long n, long long cap, FieldPtrs f,
+                              const unsigned int* __restrict__ perm, double* __restrict__ tmp)
+{
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const long long i = perm[j];
+    for (int k = 0; k < 18; ++k) tmp[k * cap + j] = f.d[k][i];
+    ((unsigned long long*)(tmp + 18 * cap))[j] = f.id[i];
+    unsigned char* b = (unsigned char*)(tmp + 19 * cap);
+    b[j] = f.level[i];
+    b[cap + j] = f.flags[i];
+    if (f.bin) b[2 * cap + j] = f.bin[i];
+}
+
+__global__ void k_iota(long long n, unsigned int* __restrict__ out)
+{
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[j] = (unsigned int)j;
+}
+
+// The bound arrays permuted into the index's Morton order.  The sorted order, the
+// radix tree over it and the force records keep their meaning (slot j now holds
+// canonical particle j), so the kept order stays valid with the identity as its
+// permutation and every later gather through it reads consecutive addresses.
+apr_status reorder(apr_ctx* c)
+{
+    const long long n = c->n;
+    if (n < 2) return APR_OK;
+    if (!(c->order_valid && c->order_n == n)) {
+        apr_status s = index_sort(c);
+        if (s != APR_OK) return s;
+    }
+    Workspace& W = c->W;
+    const FieldPtrs f = field_ptrs(c->p);
+    double* tmp = (double*)W.nbr;  // 20 x cap x 8 bytes <= the list memory
+    APR_LAUNCH(c, k_reorder_out, nblocks(n, 256), 256, n, c->cap, f, W.perm_keep, tmp);
+    APR_LAUNCH(c, k_compact_back, nblocks(n, 256), 256, n, c->cap, f, tmp);
+    APR_LAUNCH(c, k_iota, nblocks(n, 256), 256, n, W.perm_keep);
+    W.perm = W.perm_keep;
+    c->lists_fresh = false;  // the scratch overwrote them
+    c->force_data_fresh = false;
+    return cuda_check(c, cudaGetLastError(), "reorder");
+}
+
 // ------------------------------------------------------- split/merge pass
 
 __global__ void k_clear_changed(long long n, unsigned char* flags)
