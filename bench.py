@@ -887,13 +887,14 @@ def run_profile_workload(args):
     n0 = len(w["p"]["x"])
     sim = Simulation(w, capacity=int(1.6 * n0) + 1024, precision="fp32", max_neigh=2048)
     sim.init()
+    sim.reorder()
     bins = args.profile_workload.endswith("_bins")
 
     def one(first):
         if bins:
             sim.step_bins(32 * sim.timestep(), 5, init_bins=first)
         else:
-            sim.step(0.0)
+            advance(sim)
 
     for k in range(args.warmup):
         one(k == 0)

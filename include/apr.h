@@ -21,8 +21,9 @@
  *  - Errors are status codes; no exception crosses the ABI.  apr_last_error
  *    returns a text for the last failing call on that context.
  *  - Particle order is the caller's: indices are stable except that split
- *    children are appended at the end (slot n + rank) and merged-away or
- *    accreted particles are removed by a stable compaction.
+ *    children are appended at the end (slot n + rank), merged-away or
+ *    accreted particles are removed by a stable compaction, and apr_reorder
+ *    permutes every array into spatial order when the caller asks for it.
  */
 #ifndef APR_H
 #define APR_H
@@ -481,8 +482,10 @@ apr_status apr_probe_fma_peak(int precision, int iters, void* stream, double* tf
  * buffer for a message (empty on success).
  *
  * The first call on each device looks up the device address of the built-in
- * array (with that device current); make that first call before any stream
- * capture.  Every call overwrites the whole scratch it uses, so nothing
+ * array (with that device current).  No call may run on a stream under
+ * capture: every call reads its result back to host memory and synchronises
+ * the stream, so a call on a capturing stream returns APR_ERR_ARG without
+ * launching anything.  Every call overwrites the whole scratch it uses, so nothing
  * carries over between calls, but two calls that overlap on the GPU (from
  * different streams or threads) share the array and race.
  */

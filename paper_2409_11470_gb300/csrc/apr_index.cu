@@ -1073,7 +1073,12 @@ __device__ __forceinline__ void list_batch_fast(int nb, const int4* __restrict__
     // the hits written in candidate order.  The entries and their order are
     // those of a test-and-write loop over the candidates.  Idle lanes carry NaN
     // coordinates, so none of their tests passes.
-    const float lo_k = 1.0f - FILTER_EPS, hi_k = 1.0f + FILTER_EPS;
+    // the band's lower edge th (1 - eps) comes scaled with the thresholds (the
+    // staged candidates' too: fl(max(a, b) k) = max(fl(a k), fl(b k))), its upper
+    // edge is that times (1 + eps)/(1 - eps); below the upper edge and not a hit
+    // is the band
+    const float lo_k = 1.0f - FILTER_EPS, hl_k = (1.0f + FILTER_EPS) / (1.0f - FILTER_EPS);
+    const float tfl = tfa * lo_k;
     for (int base = 0; base < nb; base += 32) {
         const int cnt = min(32, nb - base);
         unsigned hit = 0u, band = 0u;
@@ -1083,22 +1088,21 @@ __device__ __forceinline__ void list_batch_fast(int nb, const int4* __restrict__
                 const float4 f = cf[base + j];
                 const float dx = pfx - f.x, dy = pfy - f.y, dz = pfz - f.z;
                 const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                const float thf = SYM ? fmaxf(tfa, f.w) : tfa;
-                const float lo = thf * lo_k, hi = thf * hi_k;
+                const float lo = SYM ? fmaxf(tfl, f.w) : tfl;
                 hit |= (r2f < lo ? 1u : 0u) << j;
-                band |= (r2f >= lo && r2f <= hi ? 1u : 0u) << j;
+                band |= (r2f <= lo * hl_k ? 1u : 0u) << j;
             }
         } else {
             for (int j = 0; j < cnt; ++j) {
                 const float4 f = cf[base + j];
                 const float dx = pfx - f.x, dy = pfy - f.y, dz = pfz - f.z;
                 const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                const float thf = SYM ? fmaxf(tfa, f.w) : tfa;
-                const float lo = thf * lo_k, hi = thf * hi_k;
+                const float lo = SYM ? fmaxf(tfl, f.w) : tfl;
                 hit |= (r2f < lo ? 1u : 0u) << j;
-                band |= (r2f >= lo && r2f <= hi ? 1u : 0u) << j;
+                band |= (r2f <= lo * hl_k ? 1u : 0u) << j;
             }
         }
+        band &= ~hit;
         if (__any_sync(0xffffffffu, band != 0u)) {
             unsigned bm = band;
             while (bm) {
@@ -1274,7 +1278,8 @@ __global__ void __launch_bounds__(LIST_THREADS)
             const int pos = nb + __popc(km & lt);
             const int rx = q.x - cx, ry = q.y - cy, rz = q.z - cz;
             cq[w][pos] = q;
-            cf[w][pos] = make_float4((float)rx, (float)ry, (float)rz, (float)tq);
+            cf[w][pos] = make_float4((float)rx, (float)ry, (float)rz,
+                                     (float)tq * (1.0f - FILTER_EPS));
             vlane = max(vlane, (long long)max(max(abs(rx), abs(ry)), abs(rz)));
             if (SYM) {
                 ct[w][pos] = tq;

@@ -119,6 +119,17 @@ extern "C" apr_status apr_stats_noalloc(const apr_config* cfg, const apr_particl
         put_err(err, errlen, "apr_stats_noalloc: no current CUDA device");
         return APR_ERR_CUDA;
     }
+    {
+        // every call reads its result back and synchronises the stream, neither of
+        // which a stream under capture allows
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess ||
+            cs != cudaStreamCaptureStatusNone) {
+            (void)cudaGetLastError();
+            put_err(err, errlen, "apr_stats_noalloc: the stream is under capture (or invalid)");
+            return APR_ERR_ARG;
+        }
+    }
     double* scratch;
     {
         // once per device, with that device current: the device address of the array
