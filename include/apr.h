@@ -78,6 +78,11 @@ enum { APR_KERNEL_M4 = 0, APR_KERNEL_WENDLAND_C2 = 1 };
  * for level k, the maximum over zones); L >= 1 derefines (every point asks for
  * level L, a point inside k boundaries for L - k, the minimum over zones), the
  * mode Sec. 2.1 and Sec. 4 describe for zones of lower resolution.
+ * fused_density: 1 lets the FP32-mixed path take the first Newton-Raphson
+ * pass of a step's density solve inside the neighbour-list build, from the
+ * candidates staged in shared memory (the same terms in the same order, hence
+ * the same results); 0 (default, faster on GB300) runs every pass in the
+ * density kernel.  The FP64 path always does the latter.
  */
 typedef struct {
     double box_lo[3], box_hi[3];
@@ -98,6 +103,7 @@ typedef struct {
     int max_neigh;
     int kernel;
     int level_default;
+    int fused_density;
 } apr_config;
 
 /*

@@ -35,7 +35,8 @@ class Config(C.Structure):
                 ("lmax", C.c_int), ("seed", C.c_ulonglong), ("ccour", C.c_double),
                 ("cforce", C.c_double), ("G", C.c_double), ("precision", C.c_int),
                 ("nr_tol", C.c_double), ("nr_maxit", C.c_int), ("max_neigh", C.c_int),
-                ("kernel", C.c_int), ("level_default", C.c_int)]
+                ("kernel", C.c_int), ("level_default", C.c_int),
+                ("fused_density", C.c_int)]
 
 
 class Region(C.Structure):
@@ -167,6 +168,7 @@ def make_config(cfg, precision="fp32", nr_tol=0.0, nr_maxit=0, max_neigh=0):
     c.max_neigh = int(max_neigh)
     c.kernel = int(cfg.get("kernel", 0))
     c.level_default = int(cfg.get("level_default", 0))
+    c.fused_density = int(cfg.get("fused_density", 0))
     return c
 
 

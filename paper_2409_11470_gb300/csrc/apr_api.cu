@@ -9,6 +9,7 @@
 #include <new>
 #include <vector>
 
+#include "apr_density.cuh"
 #include "apr_internal.cuh"
 
 namespace apr {
@@ -320,9 +321,23 @@ static apr_status run_density(apr_ctx* c, long long* noconv_out)
         if (attempt == 0) {
             // symmetric lists at the reach: if every h converges within it, they
             // also hold every force pair, r < 2 max(h_a, h_b)
-            s = index_lists(c, 1, DENSITY_REACH, true);
-            if (s != APR_OK) return s;
-            s = density_pass(c, &unc, &noconv, nullptr, 0, q, true);
+            if (c->cfg.precision == APR_PREC_FP32_MIXED && c->cfg.fused_density) {
+                // the first pass inside the list build; the particles it does not
+                // settle (queued in retry_q[1]) take the density kernel from the start
+                int* dq_n = &c->W.status[ST_RETRY_N + 1];
+                cudaMemsetAsync(dq_n, 0, sizeof(int), c->stream);
+                const FuseArgs fz{c->W.sh, (double)DENSITY_REACH, density_io(c, true), c->W.retry_q[1],
+                                  dq_n};
+                s = index_lists(c, 1, DENSITY_REACH, true, &fz);
+                int nq = 0;
+                if (s == APR_OK) s = read_status(c, ST_RETRY_N + 1, 1, &nq);
+                if (s != APR_OK) return s;
+                s = density_pass(c, &unc, &noconv, c->W.retry_q[1], (long long)nq, q, true);
+            } else {
+                s = index_lists(c, 1, DENSITY_REACH, true);
+                if (s != APR_OK) return s;
+                s = density_pass(c, &unc, &noconv, nullptr, 0, q, true);
+            }
         } else {
             // only the particles queued by the last pass: their gather lists by a
             // per-particle tree walk at their new h, then their Newton-Raphson

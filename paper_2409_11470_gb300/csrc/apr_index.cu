@@ -13,7 +13,9 @@
 // Every membership decision is an exact integer comparison, so the lists are
 // bit-identical to a brute-force search on the same lattice.
 #include <cstdio>
+#include <type_traits>
 
+#include "apr_density.cuh"
 #include "apr_internal.cuh"
 
 namespace apr {
@@ -981,6 +983,50 @@ __device__ __forceinline__ int wrap_near(int d, int L)
     return 2 * d > L ? d - L : (2 * d < -L ? d + L : d);
 }
 
+// The first Newton-Raphson pass of the density solve fused into the list build
+// (FuseArgs): the per-lane sums of that pass, or nothing.
+
+template <int KT>
+struct FusedLane {
+    static constexpr bool on = true;
+    const unsigned char* lev;  // the staged candidates' levels (their .w holds the slot)
+    float unit, hinv, r2max, bestf;
+    Acc<float> S, T, U;
+    unsigned long long best;
+    unsigned int npair;
+    __device__ __forceinline__ void init(float h, float delta_f)
+    {
+        unit = delta_f;
+        hinv = 1.0f / h;
+        r2max = 4.0f * h * h;
+        bestf = INFINITY;
+        best = ~0ULL;
+        npair = 0;
+    }
+    // a list entry of lane particle pa: the staged candidate l, q its coordinates as
+    // staged (periodic axes: the image nearest the cell; the minimum image is taken
+    // again per axis)
+    template <int PX, int PY, int PZ>
+    __device__ __forceinline__ void hit(const int4& pa, const int4& q, int l, int Lx, int Ly, int Lz)
+    {
+        int d[3] = {pa.x - q.x, pa.y - q.y, pa.z - q.z};
+        if (PX) d[0] = wrap_near(d[0], Lx);
+        if (PY) d[1] = wrap_near(d[1], Ly);
+        if (PZ) d[2] = wrap_near(d[2], Lz);
+        const float r2 = lattice_r2f(unit, d);
+        near_update<float>(r2, d, bestf, best);
+        density_term<KT, true, float>(r2, hinv, r2max, (int)lev[l], S, T, U, npair);
+    }
+};
+
+struct NoFuse {
+    static constexpr bool on = false;
+    template <int PX, int PY, int PZ>
+    __device__ __forceinline__ void hit(const int4&, const int4&, int, int, int, int)
+    {
+    }
+};
+
 // gap from coordinate v to [lo, hi], minimum over the periodic images when P
 template <int P>
 __device__ __forceinline__ long long axis_gap(int v, int lo, int hi, int L)
@@ -1027,13 +1073,13 @@ __device__ __forceinline__ bool exact_pair(const int4& q, unsigned long long tq,
     return r2 < th;
 }
 
-template <int PX, int PY, int PZ, int SYM, bool WRAP>
+template <int PX, int PY, int PZ, int SYM, bool WRAP, class FZ>
 __device__ __forceinline__ void list_batch(int nb, const int4* __restrict__ cq,
                                            const unsigned long long* __restrict__ ct,
                                            const unsigned int* __restrict__ cr, const int4& pa,
                                            int a, bool own, unsigned long long ta, unsigned int Ra,
                                            int Lx, int Ly, int Lz, int K, long long cap,
-                                           unsigned int* __restrict__ nbr, int& m)
+                                           unsigned int* __restrict__ nbr, int& m, FZ& fz)
 {
     for (int l = 0; l < nb; ++l) {
         const int4 q = cq[l];
@@ -1041,6 +1087,7 @@ __device__ __forceinline__ void list_batch(int nb, const int4* __restrict__ cq,
                                              Ra, Lx, Ly, Lz)) {
             if (m < K) nbr[(long long)m * cap + a] = (unsigned)q.w;
             ++m;
+            fz.template hit<PX, PY, PZ>(pa, q, l, Lx, Ly, Lz);
         }
     }
 }
@@ -1055,7 +1102,7 @@ __device__ __forceinline__ void list_batch(int nb, const int4* __restrict__ cq,
 constexpr float FILTER_EPS = 1.0f / 1024.0f;
 constexpr long long FILTER_SPAN = 256;
 
-template <int PX, int PY, int PZ, int SYM>
+template <int PX, int PY, int PZ, int SYM, class FZ>
 __device__ __forceinline__ void list_batch_fast(int nb, const int4* __restrict__ cq,
                                                 const float4* __restrict__ cf,
                                                 const unsigned long long* __restrict__ ct,
@@ -1064,7 +1111,7 @@ __device__ __forceinline__ void list_batch_fast(int nb, const int4* __restrict__
                                                 float tfa, int a, bool own, unsigned long long ta,
                                                 unsigned int Ra, int Lx, int Ly, int Lz, int K,
                                                 long long cap, unsigned int* __restrict__ nbr,
-                                                int& m)
+                                                int& m, FZ& fz)
 {
     // Per chunk of 32 staged candidates: first the float tests of every
     // candidate into two bit masks (inside the band's lower edge: a hit; inside
@@ -1083,7 +1130,8 @@ __device__ __forceinline__ void list_batch_fast(int nb, const int4* __restrict__
         const int cnt = min(32, nb - base);
         unsigned hit = 0u, band = 0u;
         if (cnt == 32) {
-#pragma unroll 8
+            // fully unrolled: every bit position is a constant
+#pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const float4 f = cf[base + j];
                 const float dx = pfx - f.x, dy = pfy - f.y, dz = pfz - f.z;
@@ -1117,10 +1165,19 @@ __device__ __forceinline__ void list_batch_fast(int nb, const int4* __restrict__
         while (hit) {
             const int j = __ffs(hit) - 1;
             hit &= hit - 1u;
-            const int b = cq[base + j].w;
-            if (b != a) {
-                if (m < K) nbr[(long long)m * cap + a] = (unsigned)b;
-                ++m;
+            if constexpr (FZ::on) {
+                const int4 q = cq[base + j];
+                if (q.w != a) {
+                    if (m < K) nbr[(long long)m * cap + a] = (unsigned)q.w;
+                    ++m;
+                    fz.template hit<PX, PY, PZ>(pa, q, base + j, Lx, Ly, Lz);
+                }
+            } else {
+                const int b = cq[base + j].w;
+                if (b != a) {
+                    if (m < K) nbr[(long long)m * cap + a] = (unsigned)b;
+                    ++m;
+                }
             }
         }
     }
@@ -1129,34 +1186,35 @@ __device__ __forceinline__ void list_batch_fast(int nb, const int4* __restrict__
 // one staged batch: the float filter when the batch's relative coordinates stay
 // within FILTER_SPAN times the smallest own R (R - 1 <= sqrt(threshold)), else,
 // and for batches that need the per-pair minimum image, the exact tests
-template <int PX, int PY, int PZ, int SYM>
+template <int PX, int PY, int PZ, int SYM, class FZ>
 __device__ __forceinline__ void flush_batch(int nb, bool wrapb, long long vlane, long long vown,
                                             unsigned int rmin, const int4* cq, const float4* cf,
                                             const unsigned long long* ct, const unsigned int* cr,
                                             const int4& pa, float pfx, float pfy, float pfz,
                                             float tfa, int a, bool own, unsigned long long ta,
                                             unsigned int Ra, int Lx, int Ly, int Lz, int K,
-                                            long long cap, unsigned int* nbr, int& m)
+                                            long long cap, unsigned int* nbr, int& m, FZ& fz)
 {
     const long long v = max(vown, (long long)__reduce_max_sync(0xffffffffu, (unsigned)vlane));
     const bool fast = !wrapb && rmin >= 2u && rmin != 0xffffffffu &&
                       v <= FILTER_SPAN * (long long)(rmin - 1u);
     if (wrapb)
         list_batch<PX, PY, PZ, SYM, true>(nb, cq, ct, cr, pa, a, own, ta, Ra, Lx, Ly, Lz, K, cap, nbr,
-                                          m);
+                                          m, fz);
     else if (fast)
         list_batch_fast<PX, PY, PZ, SYM>(nb, cq, cf, ct, cr, pa, pfx, pfy, pfz, tfa, a, own, ta, Ra, Lx,
-                                         Ly, Lz, K, cap, nbr, m);
+                                         Ly, Lz, K, cap, nbr, m, fz);
     else
         list_batch<PX, PY, PZ, SYM, false>(nb, cq, ct, cr, pa, a, own, ta, Ra, Lx, Ly, Lz, K, cap, nbr,
-                                           m);
+                                           m, fz);
 }
 
 // threads per block of the cell list kernel (a warp per cell; a block's cells are
 // consecutive in Morton order and share candidate particles in L1)
 constexpr int LIST_THREADS = 128;
 
-template <int PX, int PY, int PZ, int SYM>
+// FUSE: 0, or 1 + the kernel type of a fused first density pass (FuseArgs)
+template <int PX, int PY, int PZ, int SYM, int FUSE>
 __global__ void __launch_bounds__(LIST_THREADS)
     k_lists(DevCfg dc, const int* __restrict__ ncell_dev, int n, long long cap,
             const int* __restrict__ cell_first,
@@ -1164,12 +1222,14 @@ __global__ void __launch_bounds__(LIST_THREADS)
             const int* __restrict__ ncand, const int4* __restrict__ pk,
             const unsigned long long* __restrict__ thr, const unsigned int* __restrict__ rint,
             unsigned int* __restrict__ nbr, int* __restrict__ ncnt, int* __restrict__ point_q,
-            int* status, int graceful, unsigned long long* counters)
+            int* status, int graceful, unsigned long long* counters, FuseArgs fa)
 {
+    using FZ = typename std::conditional<FUSE != 0, FusedLane<FUSE - 1>, NoFuse>::type;
     __shared__ int4 cq[LIST_THREADS / 32][LIST_BUF];
     __shared__ float4 cf[LIST_THREADS / 32][LIST_BUF];
     __shared__ unsigned long long ct[LIST_THREADS / 32][LIST_BUF];
     __shared__ unsigned int cr[LIST_THREADS / 32][LIST_BUF];
+    __shared__ unsigned char clev[LIST_THREADS / 32][FUSE != 0 ? LIST_BUF : 1];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -1191,8 +1251,16 @@ __global__ void __launch_bounds__(LIST_THREADS)
         if (own) {
             const int q = atomicAdd(&status[ST_POINT_N], 1);
             if (q < n) point_q[q] = a;
+            if constexpr (FUSE != 0) fa.dq[atomicAdd(fa.dq_n, 1)] = a;
         }
         continue;
+    }
+    FZ fz;
+    double hlist = 1.0;
+    if constexpr (FUSE != 0) {
+        if (own) hlist = fa.sh[a];
+        fz.init((float)hlist, dc.deltaf);
+        fz.lev = clev[w];
     }
     // the cell's box, largest threshold and largest R
     const int lox = __reduce_min_sync(FULL, own ? pa.x : INT_MAX);
@@ -1251,6 +1319,7 @@ __global__ void __launch_bounds__(LIST_THREADS)
         cb_nn = j + 2 < nc ? cc[j + 2] : make_int2(-1, 0);
         if (!valid(cb)) continue;
         bool keep = false, nw = false;
+        const int lev = q.w;  // pk's fourth word: the level (the staged copy holds the slot)
         if (lane < cb.y) {
             q.w = cb.x + lane;
             const unsigned long long T = (SYM && tq > tcell) ? tq : tcell;
@@ -1278,6 +1347,7 @@ __global__ void __launch_bounds__(LIST_THREADS)
             const int pos = nb + __popc(km & lt);
             const int rx = q.x - cx, ry = q.y - cy, rz = q.z - cz;
             cq[w][pos] = q;
+            if constexpr (FUSE != 0) clev[w][pos] = (unsigned char)lev;
             cf[w][pos] = make_float4((float)rx, (float)ry, (float)rz,
                                      (float)tq * (1.0f - FILTER_EPS));
             vlane = max(vlane, (long long)max(max(abs(rx), abs(ry)), abs(rz)));
@@ -1291,7 +1361,7 @@ __global__ void __launch_bounds__(LIST_THREADS)
         if (nb >= 32) {
             flush_batch<PX, PY, PZ, SYM>(nb, wrapb, vlane, vown, rmin, cq[w], cf[w], ct[w], cr[w], pa,
                                          pfx, pfy, pfz, tfa, a, own, ta, Ra, Lx, Ly, Lz, K, cap, nbr,
-                                         m);
+                                         m, fz);
             nb = 0;
             wrapb = false;
             vlane = 0;
@@ -1300,10 +1370,29 @@ __global__ void __launch_bounds__(LIST_THREADS)
     }
     if (nb > 0)
         flush_batch<PX, PY, PZ, SYM>(nb, wrapb, vlane, vown, rmin, cq[w], cf[w], ct[w], cr[w], pa, pfx,
-                                     pfy, pfz, tfa, a, own, ta, Ra, Lx, Ly, Lz, K, cap, nbr, m);
+                                     pfy, pfz, tfa, a, own, ta, Ra, Lx, Ly, Lz, K, cap, nbr, m, fz);
     if (own) {
         ncnt[a] = m > K ? -1 : m;
         if (m > K && !graceful) atomicOr(&status[ST_NEIGH_OVERFLOW], 1);
+    }
+    if constexpr (FUSE != 0) {
+        // the pass's Newton-Raphson update, as the density kernel's first iteration
+        if (own) {
+            bool settled = false;
+            if (m <= K) {
+                const float mua = level_mass_f(pa.w);
+                const float target = float(dc.knorm_inv) * mua * float(dc.hfact * dc.hfact * dc.hfact);
+                NRState<float> st{(float)hlist, 0.0f, 0.0f, 0.0f, false, false};
+                const float hreach = round_down<float>(fa.reach * hlist);
+                if (nr_update<float, true>(st, fz.S.s, fz.T.s, fz.U.s, mua, target, (float)dc.nr_tol,
+                                           hreach) &&
+                    st.conv) {
+                    density_store<float>(dc, fa.io, a, pa, st.h, st.D, target, fz.best);
+                    settled = true;
+                }
+            }
+            if (!settled) fa.dq[atomicAdd(fa.dq_n, 1)] = a;
+        }
     }
     if (dc.prof) {  // list entries written (profiling only)
         const unsigned tot = __reduce_add_sync(FULL, own ? (unsigned)min(m, K) : 0u);
@@ -1417,9 +1506,9 @@ __global__ void __launch_bounds__(128)
     }
 }
 
-template <int SYM>
-static void launch_lists(apr_ctx* c, const int* ncell_dev, int n, bool graceful,
-                         const int* cell_first, const int* cell_cnt)
+template <int SYM, int FUSE>
+static void launch_lists_t(apr_ctx* c, const int* ncell_dev, int n, bool graceful,
+                           const int* cell_first, const int* cell_cnt, const FuseArgs& fa)
 {
     Workspace& W = c->W;
     const int mask = (c->dc.periodic[0] ? 1 : 0) | (c->dc.periodic[1] ? 2 : 0) |
@@ -1427,10 +1516,10 @@ static void launch_lists(apr_ctx* c, const int* ncell_dev, int n, bool graceful,
     const int grid = min(nblocks((long long)n * 32, LIST_THREADS), 152 * 16 * 128 / LIST_THREADS);
 #define APR_LISTS_CASE(M, X, Y, Z)                                                                   \
     case M:                                                                                          \
-        APR_LAUNCH(c, (k_lists<X, Y, Z, SYM>), grid, LIST_THREADS, c->dc, ncell_dev, n, c->cap,     \
+        APR_LAUNCH(c, (k_lists<X, Y, Z, SYM, FUSE>), grid, LIST_THREADS, c->dc, ncell_dev, n, c->cap, \
                    cell_first,                                                                       \
                    cell_cnt, W.cand, W.ncand, W.pk, W.sthr, W.sreach, W.nbr, W.ncnt, W.point_q,      \
-                   W.status, graceful ? 1 : 0, W.counters);                                          \
+                   W.status, graceful ? 1 : 0, W.counters, fa);                                      \
         APR_LAUNCH(c, (k_lists_point<X, Y, Z, SYM>), 152 * 4, 128, c->dc, &W.status[ST_POINT_N],     \
                    W.point_q, n, c->cap, W.left, W.right, W.pk, W.sthr, W.nlo, W.nhi, W.nthr, W.nbr, \
                    W.ncnt, W.status, graceful ? 1 : 0, W.counters);                                  \
@@ -1446,6 +1535,25 @@ static void launch_lists(apr_ctx* c, const int* ncell_dev, int n, bool graceful,
         APR_LISTS_CASE(7, 1, 1, 1)
     }
 #undef APR_LISTS_CASE
+}
+
+// fz: the fused first density pass (symmetric lists only), or null
+template <int SYM>
+static void launch_lists(apr_ctx* c, const int* ncell_dev, int n, bool graceful,
+                         const int* cell_first, const int* cell_cnt, const FuseArgs* fz = nullptr)
+{
+    if constexpr (SYM == 1) {
+        if (fz) {
+            if (c->cfg.kernel == APR_KERNEL_WENDLAND_C2)
+                launch_lists_t<1, 1 + APR_KERNEL_WENDLAND_C2>(c, ncell_dev, n, graceful, cell_first,
+                                                              cell_cnt, *fz);
+            else
+                launch_lists_t<1, 1 + APR_KERNEL_M4>(c, ncell_dev, n, graceful, cell_first, cell_cnt,
+                                                     *fz);
+            return;
+        }
+    }
+    launch_lists_t<SYM, 0>(c, ncell_dev, n, graceful, cell_first, cell_cnt, FuseArgs{});
 }
 
 // lists (graceful: an overflow marks the list, the density pass shrinks h) of the
@@ -1634,7 +1742,7 @@ apr_status relist_finish(apr_ctx* c)
                              (double)DENSITY_REACH);
 }
 
-apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful)
+apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful, const FuseArgs* fz)
 {
     Workspace& W = c->W;
     int n = (int)c->n;
@@ -1664,7 +1772,7 @@ apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful)
     if (mode == 0)
         launch_lists<0>(c, ncell_dev, n, graceful, W.cell_first, W.cell_cnt);
     else
-        launch_lists<1>(c, ncell_dev, n, graceful, W.cell_first, W.cell_cnt);
+        launch_lists<1>(c, ncell_dev, n, graceful, W.cell_first, W.cell_cnt, fz);
     prof_end(c, ps);
     return cuda_check(c, cudaGetLastError(), "lists");
 }

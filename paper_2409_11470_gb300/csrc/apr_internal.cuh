@@ -339,7 +339,9 @@ apr_status relist_mark(apr_ctx* c, const int* queue, const int* qlen_dev, bool f
 apr_status relist_finish(apr_ctx* c);
 // mode 0: gather lists (r < 2 reach h_a); mode 1: symmetric lists (r < 2 reach max(h_a, h_b)).
 // graceful: an overflowing list is marked (count -1) instead of flagged as an error.
-apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful = false);
+struct FuseArgs;
+apr_status index_lists(apr_ctx* c, int mode, double reach, bool graceful = false,
+                       const FuseArgs* fz = nullptr);
 // lists of the queued particles only, by a per-particle tree walk: symmetric
 // (sym) or gather lists; node_reach > 0: the nodes' largest h are in units of
 // h / node_reach (see relist_finish)

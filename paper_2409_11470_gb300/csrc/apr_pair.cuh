@@ -29,6 +29,31 @@ struct Num<double> {
     __device__ static double mass(int level) { return level_mass_d(level); }
 };
 
+// Float arithmetic that rounds the same whether or not its unit is compiled with
+// multiply-add contraction: every product that feeds a sum is either an explicit
+// fused multiply-add or a separately rounded product (these intrinsics are never
+// contracted).  The kernel functions and the density terms are written with it,
+// so that the list kernel (a unit compiled without contraction) and the density
+// kernel give the same bits for the same terms.
+template <typename R>
+struct Rn;
+template <>
+struct Rn<float> {
+    __device__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+    __device__ static float add(float a, float b) { return __fadd_rn(a, b); }
+    __device__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+    __device__ static float fma(float a, float b, float c) { return fmaf(a, b, c); }
+};
+// double: the plain operators, contracted as the compiler sees fit (only the density
+// kernel's unit evaluates these in double, and its FP64 pipe is the limit there)
+template <>
+struct Rn<double> {
+    __device__ static double mul(double a, double b) { return a * b; }
+    __device__ static double add(double a, double b) { return a + b; }
+    __device__ static double sub(double a, double b) { return a - b; }
+    __device__ static double fma(double a, double b, double c) { return ::fma(a, b, c); }
+};
+
 // M4 cubic spline: f(q) and f'(q), zero for q >= 2.  Without branches: with
 // t = max(2 - q, 0) and s = max(1 - q, 0), f = t^3 / 4 - s^3 and
 // f' = 3 s^2 - 3 t^2 / 4 (for q < 1 this expands to 1 - 3q^2/2 + 3q^3/4 and
@@ -36,10 +61,11 @@ struct Num<double> {
 template <typename R>
 __device__ __forceinline__ void m4(R q, R& f, R& df)
 {
-    const R t = Num<R>::max_(R(2) - q, R(0)), s = Num<R>::max_(R(1) - q, R(0));
-    const R t2 = t * t, s2 = s * s;
-    f = R(0.25) * t2 * t - s2 * s;
-    df = R(3) * s2 - R(0.75) * t2;
+    using O = Rn<R>;
+    const R t = Num<R>::max_(O::sub(R(2), q), R(0)), s = Num<R>::max_(O::sub(R(1), q), R(0));
+    const R t2 = O::mul(t, t), s2 = O::mul(s, s);
+    f = O::fma(O::mul(R(0.25), t2), t, -O::mul(s2, s));
+    df = O::fma(R(3), s2, -O::mul(R(0.75), t2));
 }
 
 // Wendland C2 (support 2h): f(q) = (1 - q/2)^4 (2q + 1), f'(q) = -5 q (1 - q/2)^3,
@@ -47,10 +73,11 @@ __device__ __forceinline__ void m4(R q, R& f, R& df)
 template <typename R>
 __device__ __forceinline__ void wendland_c2(R q, R& f, R& df)
 {
-    const R t = Num<R>::max_(R(1) - R(0.5) * q, R(0));
-    const R t3 = t * t * t;
-    f = t3 * t * (R(2) * q + R(1));
-    df = R(-5) * q * t3;
+    using O = Rn<R>;
+    const R t = Num<R>::max_(O::fma(R(-0.5), q, R(1)), R(0));
+    const R t3 = O::mul(O::mul(t, t), t);
+    f = O::mul(O::mul(t3, t), O::fma(R(2), q, R(1)));
+    df = O::mul(O::mul(R(-5), q), t3);
 }
 
 // the configured kernel (the branch is uniform across the grid)
@@ -67,18 +94,19 @@ __device__ __forceinline__ void kern(int kernel, R q, R& f, R& df)
 template <int KT, typename R>
 __device__ __forceinline__ void kern2_t(R q, R& f, R& df, R& ddf)
 {
+    using O = Rn<R>;
     if constexpr (KT == APR_KERNEL_WENDLAND_C2) {
-        const R t = Num<R>::max_(R(1) - R(0.5) * q, R(0));
-        const R t2 = t * t, t3 = t2 * t;
-        f = t3 * t * (R(2) * q + R(1));
-        df = R(-5) * q * t3;
-        ddf = R(-5) * t3 + R(7.5) * q * t2;
+        const R t = Num<R>::max_(O::fma(R(-0.5), q, R(1)), R(0));
+        const R t2 = O::mul(t, t), t3 = O::mul(t2, t);
+        f = O::mul(O::mul(t3, t), O::fma(R(2), q, R(1)));
+        df = O::mul(O::mul(R(-5), q), t3);
+        ddf = O::fma(O::mul(R(7.5), q), t2, O::mul(R(-5), t3));
     } else {
-        const R t = Num<R>::max_(R(2) - q, R(0)), s = Num<R>::max_(R(1) - q, R(0));
-        const R t2 = t * t, s2 = s * s;
-        f = R(0.25) * t2 * t - s2 * s;
-        df = R(3) * s2 - R(0.75) * t2;
-        ddf = R(1.5) * t - R(6) * s;
+        const R t = Num<R>::max_(O::sub(R(2), q), R(0)), s = Num<R>::max_(O::sub(R(1), q), R(0));
+        const R t2 = O::mul(t, t), s2 = O::mul(s, s);
+        f = O::fma(O::mul(R(0.25), t2), t, -O::mul(s2, s));
+        df = O::fma(R(3), s2, -O::mul(R(0.75), t2));
+        ddf = O::fma(R(1.5), t, -O::mul(R(6), s));
     }
 }
 

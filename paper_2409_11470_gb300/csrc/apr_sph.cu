@@ -14,6 +14,7 @@
 // FP64: the same kernels in double on the float64 coordinates.
 #include <cfloat>
 
+#include "apr_density.cuh"
 #include "apr_internal.cuh"
 #include "apr_pair.cuh"
 
@@ -29,42 +30,6 @@ __device__ __forceinline__ void lattice_d(const DevCfg& dc, const int4& pa, cons
     d[2] = min_image32(pa.z - pb.z, dc.periodic[2], (int)dc.Lint[2]);
 }
 
-// its exact square
-__device__ __forceinline__ unsigned long long lattice_sq(const int d[3])
-{
-    return (unsigned long long)((long long)d[0] * d[0]) + (unsigned long long)((long long)d[1] * d[1]) +
-           (unsigned long long)((long long)d[2] * d[2]);
-}
-
-// one density term mu_b f(q), mu_b q f'(q) (and with U, mu_b q^2 f''(q)) for a
-// pair inside 2h
-template <int KT, bool U2, typename R>
-__device__ __forceinline__ void density_term(R r2, R hinv, R r2max, int levb, Acc<R>& S,
-                                             Acc<R>& T, Acc<R>& U, unsigned int& npair)
-{
-    if (r2 >= r2max) return;
-    const R q = Num<R>::root_(r2) * hinv;
-    const R mub = Num<R>::mass(levb);
-    R f, df;
-    if constexpr (U2) {
-        R ddf;
-        kern2_t<KT, R>(q, f, df, ddf);
-        U.add(mub * q * q * ddf);
-    } else {
-        kern_t<KT, R>(q, f, df);
-    }
-    S.add(mub * f);
-    T.add(mub * q * df);
-    ++npair;
-}
-
-template <typename R>
-__device__ __forceinline__ R round_down(double x);
-template <>
-__device__ __forceinline__ float round_down<float>(double x) { return __double2float_rd(x); }
-template <>
-__device__ __forceinline__ double round_down<double>(double x) { return x; }
-
 template <typename R>
 __device__ __forceinline__ R rel_r2(const DevCfg& dc, const int d[3], const double* sx,
                                     const double* sy, const double* sz, int a, int b);
@@ -72,8 +37,7 @@ template <>
 __device__ __forceinline__ float rel_r2<float>(const DevCfg& dc, const int d[3], const double*,
                                                const double*, const double*, int, int)
 {
-    const float x = (float)d[0] * dc.deltaf, y = (float)d[1] * dc.deltaf, z = (float)d[2] * dc.deltaf;
-    return x * x + y * y + z * z;
+    return lattice_r2f(dc.deltaf, d);
 }
 template <>
 __device__ __forceinline__ double rel_r2<double>(const DevCfg& dc, const int*, const double* sx,
@@ -82,30 +46,6 @@ __device__ __forceinline__ double rel_r2<double>(const DevCfg& dc, const int*, c
     double d[3];
     Rel<double>::get(dc, int4(), int4(), sx, sy, sz, a, b, d);
     return d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-}
-
-// The nearest lattice neighbour (the exact integer minimum of the squared lattice
-// distance over the list).  FP64: every entry's exact square.  FP32: the exact
-// square only of entries whose float r^2 lies within a relative 2^-20 of the
-// smallest float r^2 seen so far.  This is the exact minimum: the float r^2 of any
-// entry is its exact lattice r^2 times the (power-of-two) unit squared, to a
-// relative 5 u (u = 2^-24: three conversions, three products, two sums), so the
-// exact nearest's float r^2 is within a relative 10.1 u of the smallest float
-// r^2 of the list, hence within 2^-20 = 16 u of the running minimum when it is
-// met; the entries skipped are farther than it.
-template <typename R>
-__device__ __forceinline__ void near_update(R r2f, const int d[3], R& bestf, unsigned long long& best)
-{
-    if constexpr (sizeof(R) == 4) {
-        if (r2f <= bestf * (1.0f + 1.0f / (1 << 20))) {
-            const unsigned long long q = lattice_sq(d);
-            best = q < best ? q : best;
-            bestf = fminf(bestf, r2f);
-        }
-    } else {
-        const unsigned long long q = lattice_sq(d);
-        best = q < best ? q : best;
-    }
 }
 
 // Newton-Raphson on g(h) with a bracket over this particle's (symmetric,
@@ -125,73 +65,16 @@ constexpr int density_min_blocks() { return sizeof(R) == 4 ? 1024 / DENSITY_THRE
 template <typename R>
 constexpr int force_min_blocks() { return sizeof(R) == 4 ? 1024 / force_threads<R>() : 1; }
 
-// one slot's force records: A = (1/h, P/(Omega rho^2), c_s, rho), V = (v, u),
-// B = (P, 1/(Omega rho), h, mass factor).  FP32-mixed: float4, every quotient
-// formed in float from the float values the density solve settled (the gather
-// below forms the same from the stored values, which are exact widenings of
-// them); FP64: four doubles each.
-__device__ __forceinline__ void store_force_data_f(void* A, void* V, void* B, long long s, float h,
-                                                   float r, float om, float P, float cs, double vx,
-                                                   double vy, double vz, double u, int level)
-{
-    if (B) {
-        ((float4*)A)[s] = make_float4(1.0f / h, P / (om * r * r), cs, r);
-        ((float4*)B)[s] = make_float4(P, 1.0f / (om * r), h, level_mass_f(level));
-    } else {
-        // without conductivity the force needs of B only 1/(Omega rho) (here in A's
-        // last slot) and the mass (from the level): two records per slot
-        ((float4*)A)[s] = make_float4(1.0f / h, P / (om * r * r), cs, 1.0f / (om * r));
-    }
-    ((float4*)V)[s] = make_float4((float)vx, (float)vy, (float)vz, (float)u);
-}
-
-// the FP32-mixed force records use the two-record layout (A, V) unless the run
-// has artificial conductivity, which needs pressure and density of the neighbour
-__host__ __device__ inline bool force_two_records(const DevCfg& dc)
-{
-    return !(dc.eos == APR_EOS_ADIABATIC && dc.alpha_u > 0.0);
-}
-
-__device__ __forceinline__ void store_force_data_d(void* A, void* V, void* B, long long s, double h,
-                                                   double r, double om, double P, double cs,
-                                                   double vx, double vy, double vz, double u,
-                                                   int level)
-{
-    double* a = (double*)A + 4 * s;
-    double* v = (double*)V + 4 * s;
-    double* b = (double*)B + 4 * s;
-    a[0] = 1.0 / h;
-    a[1] = P / (om * r * r);
-    a[2] = cs;
-    a[3] = r;
-    v[0] = vx;
-    v[1] = vy;
-    v[2] = vz;
-    v[3] = u;
-    b[0] = P;
-    b[1] = 1.0 / (om * r);
-    b[2] = h;
-    b[3] = level_mass_d(level);
-}
-
 template <typename R, int KT>
 __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
     k_density(DevCfg dc, long long n, long long cap, double reach, const int4* __restrict__ pk,
-              const double* __restrict__ sh, const unsigned long long* __restrict__ sthr,
-              const unsigned int* __restrict__ nbr, const int* __restrict__ ncnt,
-              const double* __restrict__ sx, const double* __restrict__ sy,
-              const double* __restrict__ sz, const unsigned int* __restrict__ perm,
-              const double* __restrict__ x, const double* __restrict__ y,
-              const double* __restrict__ u, double* __restrict__ h_out,
-              double* __restrict__ rho_out, double* __restrict__ omega_out,
-              double* __restrict__ dnn_out, double* __restrict__ pres_out,
-              double* __restrict__ cs_out, int* status, unsigned long long* counters,
-              const int* __restrict__ active, long long nactive, int* __restrict__ retry_q,
-              int* __restrict__ retry_n, const double* __restrict__ vx,
-              const double* __restrict__ vy, const double* __restrict__ vz,
-              void* __restrict__ fA, void* __restrict__ fV, void* __restrict__ fB)
+              const double* __restrict__ sh, const unsigned int* __restrict__ nbr,
+              const int* __restrict__ ncnt, const double* __restrict__ sx,
+              const double* __restrict__ sy, const double* __restrict__ sz, DensityIO io,
+              int* status, unsigned long long* counters, const int* __restrict__ active,
+              long long nactive, int* __restrict__ retry_q, int* __restrict__ retry_n)
 {
-    // FP32: Newton steps are accepted on their predicted successor (below)
+    // FP32: Newton steps are accepted on their predicted successor (nr_update)
     constexpr bool ACCEPT = sizeof(R) == 4;
     // all particles, or (active != nullptr) only the queued ones of a retry
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -204,7 +87,7 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
     if (m < 0) {
         // the list at this h overflowed (e.g. an initial h far too large at a
         // density jump): shrink h and let the host rebuild the lists
-        h_out[perm[a]] = 0.8 * hlist;
+        io.h_out[io.perm[a]] = 0.8 * hlist;
         atomicAdd(&status[ST_UNCOVERED], 1);
         atomicAdd(&status[ST_SHRINK], 1);
         retry_q[atomicAdd(retry_n, 1)] = a;
@@ -213,21 +96,18 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
     const R mua = Num<R>::mass(pa.w);
     const R target = R(dc.knorm_inv) * mua * R(dc.hfact * dc.hfact * dc.hfact);
     const unsigned int* col = nbr + a;  // this particle's list: col[k * cap]
-    R h = (R)hlist;
     // the list's reach (float: rounded down, so that h stays inside it) and the
     // convergence tolerance at the iteration's precision
     const R hreach = round_down<R>(reach * hlist);
     const R tol = (R)dc.nr_tol;
-    R lo = R(0), hi = R(0);  // bracket of the root; hi == 0: none yet
-    R D = R(0);              // sum mu_b (3 f + q f') at the last evaluated h
-    bool conv = false, uncovered = false;
+    NRState<R> st{(R)hlist, R(0), R(0), R(0), false, false};
     unsigned int npair = 0;
     unsigned long long best = ~0ULL;
     // FP32: the nearest lattice neighbour through the float r^2 (see near_update)
     R bestf = R(INFINITY);
     for (int it = 0; it < dc.nr_maxit; ++it) {
-        const R hinv = R(1) / h;
-        const R r2max = R(4) * h * h;
+        const R hinv = R(1) / st.h;
+        const R r2max = R(4) * st.h * st.h;
         Acc<R> S, T, U;
         const bool first_pass = it == 0;
         int k = 0;
@@ -275,114 +155,29 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
             if (first_pass) near_update<R>(rb, d, bestf, best);
             density_term<KT, ACCEPT, R>(rb, hinv, r2max, pb.w, S, T, U, npair);
         }
-        const R g = (S.s + mua) - target;           // pi h^3 (rho_sum - rho_h) / m0
-        const R dg = -(T.s) * hinv;                   // dg/dh >= 0
-        D = R(3) * (S.s + mua) + T.s;
-        if (g < R(0)) lo = h;
-        else hi = h;
-        R hn;
-        bool newton = dg > R(0);
-        if (newton) hn = h - g / dg;
-        else hn = h * R(1.25992105);
-        // a Newton step that leaves the bracket is replaced by bisection (or growth)
-        if (hn < lo || (hi > R(0) && hn > hi) || !(hn == hn)) {
-            hn = hi > R(0) ? R(0.5) * (lo + hi) : h * R(1.25992105);
-            newton = false;
-        }
-        if (hn > R(2) * h) {
-            hn = R(2) * h;
-            newton = false;
-        }
-        if (hn < R(0.5) * h) {
-            hn = R(0.5) * h;
-            newton = false;
-        }
-        bool done = fabs(hn - h) <= tol * h;
-        if (ACCEPT && newton && !done) {
-            // FP32: the next Newton correction predicted from g'' = (2T + U) / h^2
-            // (g(hn) ~ g'' d^2 / 2 after the step d, exact to a relative O(d / h)); a
-            // step whose successor is below the tolerance is taken without a
-            // confirming pass, and D is carried to hn to first order
-            // (dD/dh = -(4T + U) / h)
-            const R d = hn - h;
-            const R g2 = (R(2) * T.s + U.s) * hinv * hinv;
-            if (fabs(R(0.5) * g2 * d * d) <= tol * hn * dg) {
-                D -= (R(4) * T.s + U.s) * hinv * d;
-                done = true;
-            }
-        }
-        if (hn > hreach) {
-            // the root lies beyond this list's reach: stop at the reach; the host
-            // rebuilds the lists there and the iteration continues (growth is
-            // bounded per attempt, so lists stay short)
-            h = hreach;
-            uncovered = true;
-            break;
-        }
-        h = hn;
-        if (done) {
-            conv = true;
-            break;
-        }
+        if (nr_update<R, ACCEPT>(st, S.s, T.s, U.s, mua, target, tol, hreach)) break;
     }
     if (dc.prof) atomicAdd(&counters[APR_PROF_DENSITY], (unsigned long long)npair);
-    const unsigned i = perm[a];
-    const double hd = (double)h;
-    h_out[i] = hd;
-    if (uncovered) {
+    if (st.uncovered) {
+        io.h_out[io.perm[a]] = (double)st.h;
         atomicAdd(&status[ST_UNCOVERED], 1);
         retry_q[atomicAdd(retry_n, 1)] = a;
         return;
     }
-    if (!conv) atomicAdd(&status[ST_NOCONV], 1);
-    // nearest lattice neighbour within 2h: the list holds every particle within
-    // the reach, so the overall nearest counts iff it lies inside 2h
-    const unsigned long long thr = lattice_threshold(dc, hd);
-    dnn_out[i] = best < thr ? sqrt((double)best) * dc.delta : (double)INFINITY;
-    if constexpr (sizeof(R) == 4) {
-        // FP32-mixed: density, Omega, pressure, sound speed and the force records
-        // at the pair sums' precision (this part's FP64 unit runs at a small
-        // fraction of the FP32 rate, and float64 quotients and roots here cost
-        // more than the rest of the epilogue); the results are widened on store
-        const float hr = dc.hfactf / h;
-        const float rho = dc.m0f * level_mass_f(pa.w) * hr * hr * hr;
-        const float om = 1.0f - D / (3.0f * target);
-        float P, cs;
-        if (dc.eos == APR_EOS_ADIABATIC) {
-            const float uf = (float)u[i];
-            P = (dc.gammaf - 1.0f) * rho * uf;
-            cs = sqrtf(dc.gammaf * (dc.gammaf - 1.0f) * uf);
-        } else {
-            const float xf = (float)x[i], yf = (float)y[i];
-            cs = dc.cs0f * powf(sqrtf(xf * xf + yf * yf), -dc.qcsf);
-            P = cs * cs * rho;
-        }
-        rho_out[i] = (double)rho;
-        omega_out[i] = (double)om;
-        pres_out[i] = (double)P;
-        cs_out[i] = (double)cs;
-        if (fA)
-            store_force_data_f(fA, fV, force_two_records(dc) ? nullptr : fB, a, h, rho, om, P, cs, vx[i],
-                               vy[i], vz[i], u[i], pa.w);
-    } else {
-        const double hr = dc.hfact / hd;
-        const double rho = dc.m0 * (double)level_mass_d(pa.w) * hr * hr * hr;
-        const double om = 1.0 - (double)D / (3.0 * (double)target);
-        double P, cs;
-        if (dc.eos == APR_EOS_ADIABATIC) {
-            P = (dc.gamma - 1.0) * rho * u[i];
-            cs = sqrt(dc.gamma * P / rho);
-        } else {
-            double Rc = sqrt(x[i] * x[i] + y[i] * y[i]);
-            cs = dc.cs0 * pow(Rc, -dc.qcs);
-            P = cs * cs * rho;
-        }
-        rho_out[i] = rho;
-        omega_out[i] = om;
-        pres_out[i] = P;
-        cs_out[i] = cs;
-        if (fA) store_force_data_d(fA, fV, fB, a, hd, rho, om, P, cs, vx[i], vy[i], vz[i], u[i], pa.w);
-    }
+    if (!st.conv) atomicAdd(&status[ST_NOCONV], 1);
+    density_store<R>(dc, io, a, pa, st.h, st.D, target, best);
+}
+
+DensityIO density_io(apr_ctx* c, bool force_data)
+{
+    Workspace& W = c->W;
+    const bool f64 = c->cfg.precision == APR_PREC_FP64;
+    void* fa = f64 ? (void*)W.dA : (void*)W.fA;
+    void* fv = f64 ? (void*)W.dV : (void*)W.fV;
+    void* fb = f64 ? (void*)W.dB : (void*)W.fB;
+    return DensityIO{W.perm,     c->p.x,     c->p.y,   c->p.u,    c->p.vx,  c->p.vy,
+                     c->p.vz,    c->p.h,     c->p.rho, c->p.omega, c->p.dnn, c->p.pres,
+                     c->p.cs,    force_data ? fa : nullptr, fv, fb};
 }
 
 // one Newton-Raphson pass over all particles (active == nullptr) or over the
@@ -401,16 +196,11 @@ apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv, con
     if (work > 0) {
         const double reach = DENSITY_REACH;
         const bool c2 = c->cfg.kernel == APR_KERNEL_WENDLAND_C2;
-        const bool f64 = c->cfg.precision == APR_PREC_FP64;
-        void* fa = f64 ? (void*)W.dA : (void*)W.fA;
-        void* fv = f64 ? (void*)W.dV : (void*)W.fV;
-        void* fb = f64 ? (void*)W.dB : (void*)W.fB;
+        const DensityIO io = density_io(c, force_data);
 #define APR_DENSITY(R, KT)                                                                           \
     APR_LAUNCH(c, (k_density<R, KT>), nblocks(work, DENSITY_THREADS), DENSITY_THREADS, c->dc, n, c->cap, reach, W.pk, W.sh,  \
-               W.sthr, W.nbr, W.ncnt, W.sx, W.sy, W.sz, W.perm, c->p.x, c->p.y, c->p.u, c->p.h,    \
-               c->p.rho, c->p.omega, c->p.dnn, c->p.pres, c->p.cs, W.status, W.counters, active,   \
-               nactive, W.retry_q[out_q], &W.status[ST_RETRY_N + out_q], c->p.vx, c->p.vy, c->p.vz, \
-               force_data ? fa : nullptr, fv, fb)
+               W.nbr, W.ncnt, W.sx, W.sy, W.sz, io, W.status, W.counters, active, nactive,         \
+               W.retry_q[out_q], &W.status[ST_RETRY_N + out_q])
         if (c->cfg.precision == APR_PREC_FP64) {
             if (c2) APR_DENSITY(double, APR_KERNEL_WENDLAND_C2);
             else APR_DENSITY(double, APR_KERNEL_M4);
