@@ -84,6 +84,19 @@ __device__ __forceinline__ void near_update(R r2f, const int d[3], R& bestf, uns
     }
 }
 
+// the largest growth of h in one density attempt beyond its list's reach, allowed to
+// a particle whose list fills at most an eighth of its capacity (the list around the
+// grown h holds about (1.4 x 1.06)^3 = 3.3 times as many entries)
+constexpr double RETRY_GROWTH = 1.4;
+
+// where an uncovered step may stop: RETRY_GROWTH times the reach for a short list
+// (m entries of capacity K), else the reach itself
+template <typename R>
+__device__ __forceinline__ R retry_cap(R hreach, int m, int K)
+{
+    return 8LL * m <= (long long)K ? R(RETRY_GROWTH) * hreach : hreach;
+}
+
 // one particle's iteration state between passes over its list
 template <typename R>
 struct NRState {
@@ -99,7 +112,7 @@ struct NRState {
 // tolerance is taken without a confirming pass.
 template <typename R, bool ACCEPT>
 __device__ __forceinline__ bool nr_update(NRState<R>& st, R S, R T, R U, R mua, R target, R tol,
-                                          R hreach)
+                                          R hreach, R hcap)
 {
     using O = Rn<R>;
     const R h = st.h;
@@ -142,9 +155,10 @@ __device__ __forceinline__ bool nr_update(NRState<R>& st, R S, R T, R U, R mua, 
         }
     }
     if (hn > hreach) {
-        // the root lies beyond this list's reach: stop at the reach; the host
-        // rebuilds the lists there and the iteration continues
-        st.h = hreach;
+        // the step leaves this list's reach: stop at its target, but at most at hcap
+        // (retry_cap); the host builds the particle's list at the reach around it
+        // and the iteration continues there
+        st.h = hn < hcap ? hn : hcap;
         st.uncovered = true;
         return true;
     }

@@ -1385,7 +1385,7 @@ __global__ void __launch_bounds__(LIST_THREADS)
                 NRState<float> st{(float)hlist, 0.0f, 0.0f, 0.0f, false, false};
                 const float hreach = round_down<float>(fa.reach * hlist);
                 if (nr_update<float, true>(st, fz.S.s, fz.T.s, fz.U.s, mua, target, (float)dc.nr_tol,
-                                           hreach) &&
+                                           hreach, retry_cap<float>(hreach, m, K)) &&
                     st.conv) {
                     density_store<float>(dc, fa.io, a, pa, st.h, st.D, target, fz.best);
                     settled = true;

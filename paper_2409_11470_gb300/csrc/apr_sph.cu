@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
     // the list's reach (float: rounded down, so that h stays inside it) and the
     // convergence tolerance at the iteration's precision
     const R hreach = round_down<R>(reach * hlist);
+    const R hcap = retry_cap<R>(hreach, m, dc.max_neigh);
     const R tol = (R)dc.nr_tol;
     NRState<R> st{(R)hlist, R(0), R(0), R(0), false, false};
     unsigned int npair = 0;
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
             if (first_pass) near_update<R>(rb, d, bestf, best);
             density_term<KT, ACCEPT, R>(rb, hinv, r2max, pb.w, S, T, U, npair);
         }
-        if (nr_update<R, ACCEPT>(st, S.s, T.s, U.s, mua, target, tol, hreach)) break;
+        if (nr_update<R, ACCEPT>(st, S.s, T.s, U.s, mua, target, tol, hreach, hcap)) break;
     }
     if (dc.prof) atomicAdd(&counters[APR_PROF_DENSITY], (unsigned long long)npair);
     if (st.uncovered) {
