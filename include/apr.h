@@ -71,7 +71,8 @@ enum { APR_KERNEL_M4 = 0, APR_KERNEL_WENDLAND_C2 = 1 };
  * precision: APR_PREC_FP32_MIXED (pair sums in float on relative lattice
  * coordinates, compensated; state, integration and global sums in double) or
  * APR_PREC_FP64.  nr_tol, nr_maxit: h-rho Newton-Raphson stopping rule.
- * max_neigh: capacity of one particle's neighbour list (0 = default 512).
+ * max_neigh: capacity of one particle's neighbour list (0 = default 512; else a
+ * positive multiple of 4, the lists being written and read 16 bytes at a time).
  * kernel: APR_KERNEL_M4 (cubic spline, h_fact 1.2) or APR_KERNEL_WENDLAND_C2
  * (the applications' kernel of Sec. 3, h_fact 1.3); both have support 2h.
  * level_default: 0 refines (a point inside k nested boundaries of a zone asks

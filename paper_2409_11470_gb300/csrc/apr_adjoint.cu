@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(ADJ_THREADS)
         Sn.add(xa.mu);  // self, f(0) = 1
         const int m = ncnt[a];
         for (int k = 0; k < m; ++k) {
-            const int b = (int)nbr[(long long)k * cap + a];
+            const int b = (int)nbr[(long long)a * dc.max_neigh + k];
             const AdjSlot<R> xb = X[b];
             if (!(xb.role & (ROLE_NEW | ROLE_REF))) continue;
             R d[3];
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(ADJ_THREADS)
     dh.add(R(-3) * xa.mu);  // self: -(3 f(0) + 0)
     const int m = ncnt[a];
     for (int k = 0; k < m; ++k) {
-        const int b = (int)nbr[(long long)k * cap + a];
+        const int b = (int)nbr[(long long)a * dc.max_neigh + k];
         const AdjSlot<R> xb = X[b];
         if (!xb.role) continue;
         R d[3];

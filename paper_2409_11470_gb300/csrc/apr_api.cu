@@ -277,6 +277,10 @@ static apr_status check_cfg(const apr_config* cfg, DevCfg* dc, std::string* why)
     dc->nr_tol = cfg->nr_tol > 0.0 ? cfg->nr_tol
                                    : (cfg->precision == APR_PREC_FP64 ? 1e-12 : 1e-6);
     dc->nr_maxit = cfg->nr_maxit > 0 ? cfg->nr_maxit : 50;
+    if (cfg->max_neigh < 0 || cfg->max_neigh % 4 != 0) {
+        *why = "max_neigh must be 0 (the default) or a positive multiple of 4";
+        return APR_ERR_ARG;
+    }
     dc->max_neigh = cfg->max_neigh > 0 ? cfg->max_neigh : DEFAULT_MAX_NEIGH;
     dc->max_cand = max_cand_of(dc->max_neigh);
     return APR_OK;
@@ -861,8 +865,7 @@ apr_status apr_neighbour_lists(apr_ctx* c, int mode, long long* offsets, int* id
     if (n > 0) {
         cudaMemcpyAsync(perm.data(), c->W.perm, 4 * n, cudaMemcpyDeviceToHost, c->stream);
         cudaMemcpyAsync(cnt.data(), c->W.ncnt, 4 * n, cudaMemcpyDeviceToHost, c->stream);
-        cudaMemcpy2DAsync(nb.data(), 4 * n, c->W.nbr, 4 * c->cap, 4 * n, K, cudaMemcpyDeviceToHost,
-                          c->stream);
+        cudaMemcpyAsync(nb.data(), c->W.nbr, 4 * (size_t)K * n, cudaMemcpyDeviceToHost, c->stream);
     }
     s = cuda_check(c, cudaStreamSynchronize(c->stream), "neighbour lists");
     if (s != APR_OK) return s;
@@ -875,7 +878,7 @@ apr_status apr_neighbour_lists(apr_ctx* c, int mode, long long* offsets, int* id
     if (tot > cap || (tot > 0 && !idx)) return fail(c, APR_ERR_NEIGH_OVERFLOW, "idx too small");
     for (long long sl = 0; sl < n; ++sl) {
         long long a = perm[sl], o = offsets[a];
-        for (int k = 0; k < cnt[sl]; ++k) idx[o + k] = (int)perm[nb[(size_t)k * n + sl]];
+        for (int k = 0; k < cnt[sl]; ++k) idx[o + k] = (int)perm[nb[(size_t)sl * K + k]];
     }
     return APR_OK;
 }

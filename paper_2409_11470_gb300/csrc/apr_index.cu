@@ -1073,20 +1073,48 @@ __device__ __forceinline__ bool exact_pair(const int4& q, unsigned long long tq,
     return r2 < th;
 }
 
+// A lane's list: slot a's entries go to its row nbr[a * K ...] four at a time (one
+// 16-byte store per four entries; K is a multiple of four); entries past K are
+// counted but not kept (the list then reads as overflowed)
+struct RowWriter {
+    unsigned e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+    __device__ __forceinline__ void push(unsigned* __restrict__ row, int& m, int K, unsigned v)
+    {
+        if (m < K) {
+            const int c = m & 3;
+            e0 = c == 0 ? v : e0;
+            e1 = c == 1 ? v : e1;
+            e2 = c == 2 ? v : e2;
+            e3 = c == 3 ? v : e3;
+            if (c == 3) *reinterpret_cast<uint4*>(row + (m - 3)) = make_uint4(e0, e1, e2, e3);
+        }
+        ++m;
+    }
+    // the last one to three entries kept
+    __device__ __forceinline__ void finish(unsigned* __restrict__ row, int m, int K) const
+    {
+        const int mw = m < K ? m : K;
+        const int c = mw & 3, base = mw - c;
+        if (c > 0) row[base] = e0;
+        if (c > 1) row[base + 1] = e1;
+        if (c > 2) row[base + 2] = e2;
+    }
+};
+
 template <int PX, int PY, int PZ, int SYM, bool WRAP, class FZ>
 __device__ __forceinline__ void list_batch(int nb, const int4* __restrict__ cq,
                                            const unsigned long long* __restrict__ ct,
                                            const unsigned int* __restrict__ cr, const int4& pa,
                                            int a, bool own, unsigned long long ta, unsigned int Ra,
-                                           int Lx, int Ly, int Lz, int K, long long cap,
-                                           unsigned int* __restrict__ nbr, int& m, FZ& fz)
+                                           int Lx, int Ly, int Lz, int K,
+                                           unsigned int* __restrict__ row, RowWriter& wr, int& m,
+                                           FZ& fz)
 {
     for (int l = 0; l < nb; ++l) {
         const int4 q = cq[l];
         if (exact_pair<PX, PY, PZ, SYM, WRAP>(q, SYM ? ct[l] : 0ULL, SYM ? cr[l] : 0u, pa, a, own, ta,
                                              Ra, Lx, Ly, Lz)) {
-            if (m < K) nbr[(long long)m * cap + a] = (unsigned)q.w;
-            ++m;
+            wr.push(row, m, K, (unsigned)q.w);
             fz.template hit<PX, PY, PZ>(pa, q, l, Lx, Ly, Lz);
         }
     }
@@ -1110,7 +1138,7 @@ __device__ __forceinline__ void list_batch_fast(int nb, const int4* __restrict__
                                                 const int4& pa, float pfx, float pfy, float pfz,
                                                 float tfa, int a, bool own, unsigned long long ta,
                                                 unsigned int Ra, int Lx, int Ly, int Lz, int K,
-                                                long long cap, unsigned int* __restrict__ nbr,
+                                                unsigned int* __restrict__ row, RowWriter& wr,
                                                 int& m, FZ& fz)
 {
     // Per chunk of 32 staged candidates: first the float tests of every
@@ -1168,16 +1196,12 @@ __device__ __forceinline__ void list_batch_fast(int nb, const int4* __restrict__
             if constexpr (FZ::on) {
                 const int4 q = cq[base + j];
                 if (q.w != a) {
-                    if (m < K) nbr[(long long)m * cap + a] = (unsigned)q.w;
-                    ++m;
+                    wr.push(row, m, K, (unsigned)q.w);
                     fz.template hit<PX, PY, PZ>(pa, q, base + j, Lx, Ly, Lz);
                 }
             } else {
                 const int b = cq[base + j].w;
-                if (b != a) {
-                    if (m < K) nbr[(long long)m * cap + a] = (unsigned)b;
-                    ++m;
-                }
+                if (b != a) wr.push(row, m, K, (unsigned)b);
             }
         }
     }
@@ -1193,19 +1217,19 @@ __device__ __forceinline__ void flush_batch(int nb, bool wrapb, long long vlane,
                                             const int4& pa, float pfx, float pfy, float pfz,
                                             float tfa, int a, bool own, unsigned long long ta,
                                             unsigned int Ra, int Lx, int Ly, int Lz, int K,
-                                            long long cap, unsigned int* nbr, int& m, FZ& fz)
+                                            unsigned int* row, RowWriter& wr, int& m, FZ& fz)
 {
     const long long v = max(vown, (long long)__reduce_max_sync(0xffffffffu, (unsigned)vlane));
     const bool fast = !wrapb && rmin >= 2u && rmin != 0xffffffffu &&
                       v <= FILTER_SPAN * (long long)(rmin - 1u);
     if (wrapb)
-        list_batch<PX, PY, PZ, SYM, true>(nb, cq, ct, cr, pa, a, own, ta, Ra, Lx, Ly, Lz, K, cap, nbr,
+        list_batch<PX, PY, PZ, SYM, true>(nb, cq, ct, cr, pa, a, own, ta, Ra, Lx, Ly, Lz, K, row, wr,
                                           m, fz);
     else if (fast)
         list_batch_fast<PX, PY, PZ, SYM>(nb, cq, cf, ct, cr, pa, pfx, pfy, pfz, tfa, a, own, ta, Ra, Lx,
-                                         Ly, Lz, K, cap, nbr, m, fz);
+                                         Ly, Lz, K, row, wr, m, fz);
     else
-        list_batch<PX, PY, PZ, SYM, false>(nb, cq, ct, cr, pa, a, own, ta, Ra, Lx, Ly, Lz, K, cap, nbr,
+        list_batch<PX, PY, PZ, SYM, false>(nb, cq, ct, cr, pa, a, own, ta, Ra, Lx, Ly, Lz, K, row, wr,
                                            m, fz);
 }
 
@@ -1255,6 +1279,9 @@ __global__ void __launch_bounds__(LIST_THREADS)
         }
         continue;
     }
+    // this lane's list row (idle lanes find no entry and write nothing)
+    unsigned int* const row = nbr + (long long)a * K;
+    RowWriter wr;
     FZ fz;
     double hlist = 1.0;
     if constexpr (FUSE != 0) {
@@ -1360,7 +1387,7 @@ __global__ void __launch_bounds__(LIST_THREADS)
         __syncwarp();
         if (nb >= 32) {
             flush_batch<PX, PY, PZ, SYM>(nb, wrapb, vlane, vown, rmin, cq[w], cf[w], ct[w], cr[w], pa,
-                                         pfx, pfy, pfz, tfa, a, own, ta, Ra, Lx, Ly, Lz, K, cap, nbr,
+                                         pfx, pfy, pfz, tfa, a, own, ta, Ra, Lx, Ly, Lz, K, row, wr,
                                          m, fz);
             nb = 0;
             wrapb = false;
@@ -1370,8 +1397,9 @@ __global__ void __launch_bounds__(LIST_THREADS)
     }
     if (nb > 0)
         flush_batch<PX, PY, PZ, SYM>(nb, wrapb, vlane, vown, rmin, cq[w], cf[w], ct[w], cr[w], pa, pfx,
-                                     pfy, pfz, tfa, a, own, ta, Ra, Lx, Ly, Lz, K, cap, nbr, m, fz);
+                                     pfy, pfz, tfa, a, own, ta, Ra, Lx, Ly, Lz, K, row, wr, m, fz);
     if (own) {
+        wr.finish(row, m, K);
         ncnt[a] = m > K ? -1 : m;
         if (m > K && !graceful) atomicOr(&status[ST_NEIGH_OVERFLOW], 1);
     }
@@ -1478,7 +1506,7 @@ __global__ void __launch_bounds__(128)
                 const unsigned hm = __ballot_sync(FULL, hit);
                 if (hit) {
                     const int pos = m + __popc(hm & lt);
-                    if (pos < K) nbr[(long long)pos * cap + a] = (unsigned)b;
+                    if (pos < K) nbr[(long long)a * K + pos] = (unsigned)b;
                 }
                 m += __popc(hm);
             }
@@ -1658,7 +1686,7 @@ __global__ void k_relist_mark_reach(DevCfg dc, int n, long long cap, int K,
         const unsigned long long tf = lattice_threshold(dc, h[perm[b]]);
         const unsigned long long tb0 = sthr0[b];
         for (int k = lane; k < m; k += 32) {
-            const int y = (int)nbr[(long long)k * cap + b];
+            const int y = (int)nbr[(long long)b * K + k];
             if (y < 0 || y >= n) continue;
             const int4 py = pk[y];
             const long long dx = min_image32(pb.x - py.x, dc.periodic[0], Lx);

@@ -188,7 +188,8 @@ struct Workspace {
     int* relist_q;            // density retries: retried slots, then their list partners
     unsigned int* qmark;      // per slot: 2 retried, 1 in a retried particle's list
     unsigned long long* sthr0; // density retries: the first list build's thresholds
-    // neighbour lists, transposed: nbr[k * cap + sorted slot]
+    // neighbour lists, a row per sorted slot: nbr[slot * max_neigh + k] (a lane writes
+    // and reads its own list four entries, 16 bytes, at a time)
     unsigned int* nbr;
     int* ncnt;
     // status words and profile counters

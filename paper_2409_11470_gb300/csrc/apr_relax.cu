@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(128)
     Acc<R> gx, gy, gz;
     const int m = ncnt[a];
     for (int k = 0; k < m; ++k) {
-        const int b = (int)nbr[(long long)k * cap + a];
+        const int b = (int)nbr[(long long)a * dc.max_neigh + k];
         const unsigned j = perm[b];
         if (role[j] != RELAX_REF) continue;
         R d[3];

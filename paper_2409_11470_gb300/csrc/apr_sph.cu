@@ -95,7 +95,10 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
     }
     const R mua = Num<R>::mass(pa.w);
     const R target = R(dc.knorm_inv) * mua * R(dc.hfact * dc.hfact * dc.hfact);
-    const unsigned int* col = nbr + a;  // this particle's list: col[k * cap]
+    // this particle's list: a row of max_neigh entries (a multiple of 4), the first m
+    // kept; mpad = m rounded up to 4 (<= max_neigh) bounds the 16-byte loads
+    const unsigned int* row = nbr + (long long)a * dc.max_neigh;
+    const int mpad = (m + 3) & ~3;
     // the list's reach (float: rounded down, so that h stays inside it) and the
     // convergence tolerance at the iteration's precision
     const R hreach = round_down<R>(reach * hlist);
@@ -112,21 +115,13 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
         Acc<R> S, T, U;
         const bool first_pass = it == 0;
         int k = 0;
-        // the next four list entries are loaded one step ahead (clamped to the
-        // last entry), so that only the gathers of a step wait on memory
-        unsigned int n0 = 0, n1 = 0, n2 = 0, n3 = 0;
-        if (m >= 4) {
-            n0 = col[0];
-            n1 = col[cap];
-            n2 = col[2 * cap];
-            n3 = col[3 * cap];
-        }
+        // the next four list entries are loaded one step ahead (one 16-byte load), so
+        // that only the gathers of a step wait on memory
+        uint4 nx = make_uint4(0u, 0u, 0u, 0u);
+        if (m >= 4) nx = *reinterpret_cast<const uint4*>(row);
         for (; k + 4 <= m; k += 4) {
-            const int b0 = (int)n0, b1 = (int)n1, b2 = (int)n2, b3 = (int)n3;
-            n0 = col[(long long)min(k + 4, m - 1) * cap];
-            n1 = col[(long long)min(k + 5, m - 1) * cap];
-            n2 = col[(long long)min(k + 6, m - 1) * cap];
-            n3 = col[(long long)min(k + 7, m - 1) * cap];
+            const int b0 = (int)nx.x, b1 = (int)nx.y, b2 = (int)nx.z, b3 = (int)nx.w;
+            if (k + 8 <= mpad) nx = *reinterpret_cast<const uint4*>(row + k + 4);
             const int4 p0 = pk[b0], p1 = pk[b1], p2 = pk[b2], p3 = pk[b3];
             int d0[3], d1[3], d2[3], d3[3];
             lattice_d(dc, pa, p0, d0);
@@ -148,7 +143,7 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
             density_term<KT, ACCEPT, R>(r3, hinv, r2max, p3.w, S, T, U, npair);
         }
         for (; k < m; ++k) {
-            const int b = (int)col[(long long)k * cap];
+            const int b = (int)row[k];
             const int4 pb = pk[b];
             int d[3];
             lattice_d(dc, pa, pb, d);
@@ -406,20 +401,18 @@ __global__ void __launch_bounds__(force_threads<R>(), force_min_blocks<R>())
     R vsig = A.cs;
     unsigned int npair = 0;
     const int m = ncnt[a];
-    const unsigned int* col = nbr + a;
+    // this particle's list row; mpad = m rounded up to 2 bounds the 8-byte loads
+    const unsigned int* row = nbr + (long long)a * dc.max_neigh;
+    const int mpad = (m + 1) & ~1;
     int k = 0;
-    // the next two list entries are loaded one step ahead (clamped to the last
-    // entry), so that only the gathers of a step wait on memory
-    unsigned int n0 = 0, n1 = 0;
-    if (m >= 2) {
-        n0 = col[0];
-        n1 = col[cap];
-    }
+    // the next two list entries are loaded one step ahead (one 8-byte load), so that
+    // only the gathers of a step wait on memory
+    uint2 nx = make_uint2(0u, 0u);
+    if (m >= 2) nx = *reinterpret_cast<const uint2*>(row);
     const F4<R> zero{R(0), R(0), R(0), R(0)};
     for (; k + 2 <= m; k += 2) {
-        const int b0 = (int)n0, b1 = (int)n1;
-        n0 = col[(long long)min(k + 2, m - 1) * cap];
-        n1 = col[(long long)min(k + 3, m - 1) * cap];
+        const int b0 = (int)nx.x, b1 = (int)nx.y;
+        if (k + 4 <= mpad) nx = *reinterpret_cast<const uint2*>(row + k + 2);
         const int4 p0 = pk[b0], p1 = pk[b1];
         const F4<R> A0 = ld4<R>(Abuf, b0), V0 = ld4<R>(Vbuf, b0), B0 = B2 ? zero : ld4<R>(Bbuf, b0);
         const F4<R> A1 = ld4<R>(Abuf, b1), V1 = ld4<R>(Vbuf, b1), B1 = B2 ? zero : ld4<R>(Bbuf, b1);
@@ -430,7 +423,7 @@ __global__ void __launch_bounds__(force_threads<R>(), force_min_blocks<R>())
         force_pair<KT, R, B2>(dc, A, d1, A1, V1, B1, p1.w, adiabatic, cond, fx, fy, fz, du, vsig, npair);
     }
     for (; k < m; ++k) {
-        const int b = (int)col[(long long)k * cap];
+        const int b = (int)row[k];
         const int4 pb = pk[b];
         const F4<R> Ab = ld4<R>(Abuf, b), Vb = ld4<R>(Vbuf, b), Bb = B2 ? zero : ld4<R>(Bbuf, b);
         R d[3];
