@@ -401,18 +401,22 @@ __global__ void __launch_bounds__(force_threads<R>(), force_min_blocks<R>())
     R vsig = A.cs;
     unsigned int npair = 0;
     const int m = ncnt[a];
-    // this particle's list row; mpad = m rounded up to 2 bounds the 8-byte loads
+    // this particle's list row; mpad = m rounded up to 4 (<= max_neigh) bounds the
+    // 16-byte loads
     const unsigned int* row = nbr + (long long)a * dc.max_neigh;
-    const int mpad = (m + 1) & ~1;
+    const int mpad = (m + 3) & ~3;
     int k = 0;
-    // the next two list entries are loaded one step ahead (one 8-byte load), so that
-    // only the gathers of a step wait on memory
-    uint2 nx = make_uint2(0u, 0u);
-    if (m >= 2) nx = *reinterpret_cast<const uint2*>(row);
+    // the list entries come four at a time (one 16-byte load), the next four while the
+    // second pair of the current ones is evaluated, so that only the gathers of a step
+    // wait on memory (two at a time measured slower on the shock tube, whose
+    // conductivity adds a third record per neighbour to what L1 holds)
+    uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
+    if (m >= 2) w4 = *reinterpret_cast<const uint4*>(row);
     const F4<R> zero{R(0), R(0), R(0), R(0)};
     for (; k + 2 <= m; k += 2) {
-        const int b0 = (int)nx.x, b1 = (int)nx.y;
-        if (k + 4 <= mpad) nx = *reinterpret_cast<const uint2*>(row + k + 2);
+        const bool upper = (k & 2) != 0;
+        const int b0 = (int)(upper ? w4.z : w4.x), b1 = (int)(upper ? w4.w : w4.y);
+        if (upper && k + 6 <= mpad) w4 = *reinterpret_cast<const uint4*>(row + k + 2);
         const int4 p0 = pk[b0], p1 = pk[b1];
         const F4<R> A0 = ld4<R>(Abuf, b0), V0 = ld4<R>(Vbuf, b0), B0 = B2 ? zero : ld4<R>(Bbuf, b0);
         const F4<R> A1 = ld4<R>(Abuf, b1), V1 = ld4<R>(Vbuf, b1), B1 = B2 ? zero : ld4<R>(Bbuf, b1);

@@ -35,9 +35,12 @@ def test_create_rejects_bad_configs_before_touching_the_gpu():
     bad.append(c)
     c = dict(base, delta=2.0 ** -31)  # more than 2^30 lattice units
     bad.append(c)
-    for cfg in bad:
+    cfgs = [B.make_config(cfg) for cfg in bad]
+    # list capacities must be multiples of 4 (rows written 16 bytes at a time)
+    cfgs += [B.make_config(base, max_neigh=6), B.make_config(base, max_neigh=-4)]
+    for cfg in cfgs:
         ctx = C.c_void_p()
-        st = B.lib.apr_create(C.byref(ctx), C.byref(B.make_config(cfg)), None)
+        st = B.lib.apr_create(C.byref(ctx), C.byref(cfg), None)
         assert st == 1 and not ctx.value
 
 

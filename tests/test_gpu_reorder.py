@@ -37,10 +37,14 @@ def _mean_hop(g):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_reorder_permutes_fields_by_id(precision):
+    import torch
     w = apr_synth.disc_planet(20000)
     g = sim(w, precision, capacity=4 * 20000)
     g.init()
     g.step(0.01)
+    # time-step bins travel with their particles too
+    g.t["bin"][: g.n] = torch.randint(0, 6, (g.n,), dtype=torch.uint8, device=g.t["bin"].device)
+    bins0 = g.get("bin")[np.argsort(g.get("id"))]
     ids0, s0 = _by_id(g)
     order0 = g.get("id").copy()
     hop0 = _mean_hop(g)
@@ -48,6 +52,7 @@ def test_reorder_permutes_fields_by_id(precision):
     ids1, s1 = _by_id(g)
     assert np.array_equal(ids0, ids1)
     _same_bits(s0, s1)
+    assert np.array_equal(g.get("bin")[np.argsort(g.get("id"))], bins0)
     order1 = g.get("id").copy()
     assert not np.array_equal(order0, order1)
     # the generator's order is random in space; the Morton order is not
