@@ -84,6 +84,15 @@ __device__ __forceinline__ void near_update(R r2f, const int d[3], R& bestf, uns
     }
 }
 
+// a profiling count added once per warp (the threads present at the call; one
+// atomic per thread on a single word would serialise on it)
+__device__ __forceinline__ void count_warp(unsigned long long* counter, unsigned int v)
+{
+    const unsigned mask = __activemask();
+    const unsigned tot = __reduce_add_sync(mask, v);
+    if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(counter, (unsigned long long)tot);
+}
+
 // the largest growth of h in one density attempt beyond its list's reach, allowed to
 // a particle whose list fills at most an eighth of its capacity (the list around the
 // grown h holds about (1.4 x 1.06)^3 = 3.3 times as many entries)

@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
         }
         if (nr_update<R, ACCEPT>(st, S.s, T.s, U.s, mua, target, tol, hreach, hcap)) break;
     }
-    if (dc.prof) atomicAdd(&counters[APR_PROF_DENSITY], (unsigned long long)npair);
+    if (dc.prof) count_warp(&counters[APR_PROF_DENSITY], npair);
     if (st.uncovered) {
         io.h_out[io.perm[a]] = (double)st.h;
         atomicAdd(&status[ST_UNCOVERED], 1);
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(force_threads<R>(), force_min_blocks<R>())
         Rel<R>::get(dc, pa, pb, sx, sy, sz, a, b, d);
         force_pair<KT, R, B2>(dc, A, d, Ab, Vb, Bb, pb.w, adiabatic, cond, fx, fy, fz, du, vsig, npair);
     }
-    if (dc.prof) atomicAdd(&counters[APR_PROF_FORCE], (unsigned long long)npair);
+    if (dc.prof) count_warp(&counters[APR_PROF_FORCE], npair);
     const double scale = dc.m0_knorm;
     const unsigned i = perm[a];
     ax_out[i] = scale * ((double)fx.s - (double)fx.c);
