@@ -32,8 +32,8 @@ __device__ __forceinline__ float lattice_r2f(float unit, const int d[3])
 // one density term mu_b f(q), mu_b q f'(q) (and with U2, mu_b q^2 f''(q)) for a
 // pair inside 2h
 template <int KT, bool U2, typename R>
-__device__ __forceinline__ void density_term(R r2, R hinv, R r2max, int levb, Acc<R>& S,
-                                             Acc<R>& T, Acc<R>& U, unsigned int& npair)
+__device__ __forceinline__ void density_term(R r2, R hinv, R r2max, int levb, AccB<R>& S,
+                                             AccB<R>& T, AccB<R>& U, unsigned int& npair)
 {
     using O = Rn<R>;
     if (r2 >= r2max) return;
@@ -44,12 +44,12 @@ __device__ __forceinline__ void density_term(R r2, R hinv, R r2max, int levb, Ac
     if constexpr (U2) {
         R ddf;
         kern2_t<KT, R>(q, f, df, ddf);
-        U.add(O::mul(O::mul(mq, q), ddf));
+        U.add_prod(O::mul(mq, q), ddf);
     } else {
         kern_t<KT, R>(q, f, df);
     }
-    S.add(O::mul(mub, f));
-    T.add(O::mul(mq, df));
+    S.add_prod(mub, f);
+    T.add_prod(mq, df);
     ++npair;
 }
 

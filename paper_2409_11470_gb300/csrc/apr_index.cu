@@ -991,9 +991,9 @@ struct FusedLane {
     static constexpr bool on = true;
     const unsigned char* lev;  // the staged candidates' levels (their .w holds the slot)
     float unit, hinv, r2max, bestf;
-    Acc<float> S, T, U;
+    AccB<float> S, T, U;  // flushed every four entries, as the density kernel does
     unsigned long long best;
-    unsigned int npair;
+    unsigned int npair, nent;
     __device__ __forceinline__ void init(float h, float delta_f)
     {
         unit = delta_f;
@@ -1002,6 +1002,13 @@ struct FusedLane {
         bestf = INFINITY;
         best = ~0ULL;
         npair = 0;
+        nent = 0;
+    }
+    __device__ __forceinline__ void flush()
+    {
+        S.flush();
+        T.flush();
+        U.flush();
     }
     // a list entry of lane particle pa: the staged candidate l, q its coordinates as
     // staged (periodic axes: the image nearest the cell; the minimum image is taken
@@ -1016,6 +1023,7 @@ struct FusedLane {
         const float r2 = lattice_r2f(unit, d);
         near_update<float>(r2, d, bestf, best);
         density_term<KT, true, float>(r2, hinv, r2max, (int)lev[l], S, T, U, npair);
+        if ((++nent & 3u) == 0u) flush();
     }
 };
 
@@ -1411,6 +1419,7 @@ __global__ void __launch_bounds__(LIST_THREADS)
                 const float mua = level_mass_f(pa.w);
                 const float target = float(dc.knorm_inv) * mua * float(dc.hfact * dc.hfact * dc.hfact);
                 NRState<float> st{(float)hlist, 0.0f, 0.0f, 0.0f, false, false};
+                fz.flush();
                 const float hreach = round_down<float>(fa.reach * hlist);
                 if (nr_update<float, true>(st, fz.S.s, fz.T.s, fz.U.s, mua, target, (float)dc.nr_tol,
                                            hreach, retry_cap<float>(hreach, m, K)) &&

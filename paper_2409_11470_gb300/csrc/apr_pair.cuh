@@ -134,6 +134,27 @@ struct Acc {
     }
 };
 
+// compensated by groups: the terms of a group summed plainly (products fused into
+// the sum), each group's sum added to the total with Kahan's compensation at
+// flush(); the pair kernels flush every four terms, so the rounding error is that of
+// a compensated sum of the group sums plus a few units in the last place of each
+// group (one compensation step per four terms instead of one per term)
+template <typename R>
+struct AccB {
+    R s, c, g;
+    __device__ __forceinline__ AccB() : s(0), c(0), g(0) {}
+    __device__ __forceinline__ void add(R x) { g += x; }  // (a product may fuse into it)
+    __device__ __forceinline__ void add_prod(R a, R b) { g = Rn<R>::fma(a, b, g); }
+    __device__ __forceinline__ void flush()
+    {
+        R y = g - c;
+        R t = s + y;
+        c = (t - s) - y;
+        s = t;
+        g = R(0);
+    }
+};
+
 // relative position a - b of two sorted particles
 template <typename R>
 struct Rel;

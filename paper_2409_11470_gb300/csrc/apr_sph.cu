@@ -10,7 +10,8 @@
 // monotone, so a bracket can safeguard every step.
 //
 // FP32-mixed: pair sums in float on relative lattice coordinates
-// (dx = float(dx_lattice) * D), Kahan-compensated; results widened to double.
+// (dx = float(dx_lattice) * D), compensated (Kahan) by groups of four terms; results
+// widened to double.
 // FP64: the same kernels in double on the float64 coordinates.
 #include <cfloat>
 
@@ -112,7 +113,8 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
     for (int it = 0; it < dc.nr_maxit; ++it) {
         const R hinv = R(1) / st.h;
         const R r2max = R(4) * st.h * st.h;
-        Acc<R> S, T, U;
+        // compensated by groups of four list entries (AccB)
+        AccB<R> S, T, U;
         const bool first_pass = it == 0;
         int k = 0;
         // the next four list entries are loaded one step ahead (one 16-byte load), so
@@ -141,6 +143,9 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
             density_term<KT, ACCEPT, R>(r1, hinv, r2max, p1.w, S, T, U, npair);
             density_term<KT, ACCEPT, R>(r2, hinv, r2max, p2.w, S, T, U, npair);
             density_term<KT, ACCEPT, R>(r3, hinv, r2max, p3.w, S, T, U, npair);
+            S.flush();
+            T.flush();
+            U.flush();
         }
         for (; k < m; ++k) {
             const int b = (int)row[k];
@@ -151,6 +156,9 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
             if (first_pass) near_update<R>(rb, d, bestf, best);
             density_term<KT, ACCEPT, R>(rb, hinv, r2max, pb.w, S, T, U, npair);
         }
+        S.flush();
+        T.flush();
+        U.flush();
         if (nr_update<R, ACCEPT>(st, S.s, T.s, U.s, mua, target, tol, hreach, hcap)) break;
     }
     if (dc.prof) count_warp(&counters[APR_PROF_DENSITY], npair);
@@ -309,8 +317,8 @@ struct ForceSelf {
 template <int KT, typename R, bool B2>
 __device__ __forceinline__ void force_pair(const DevCfg& dc, const ForceSelf<R>& A, const R d[3],
                                            const F4<R>& Ab, const F4<R>& Vb, const F4<R>& Bb,
-                                           int levb, bool adiabatic, bool cond, Acc<R>& fx,
-                                           Acc<R>& fy, Acc<R>& fz, Acc<R>& du, R& vsig,
+                                           int levb, bool adiabatic, bool cond, AccB<R>& fx,
+                                           AccB<R>& fy, AccB<R>& fz, AccB<R>& du, R& vsig,
                                            unsigned int& npair)
 {
     const R r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -397,7 +405,7 @@ __global__ void __launch_bounds__(force_threads<R>(), force_min_blocks<R>())
     A.u = Va.w;
     const bool adiabatic = dc.eos == APR_EOS_ADIABATIC;
     const bool cond = adiabatic && dc.alpha_u > 0.0;
-    Acc<R> fx, fy, fz, du;
+    AccB<R> fx, fy, fz, du;  // compensated by groups of four pairs
     R vsig = A.cs;
     unsigned int npair = 0;
     const int m = ncnt[a];
@@ -425,6 +433,12 @@ __global__ void __launch_bounds__(force_threads<R>(), force_min_blocks<R>())
         Rel<R>::get(dc, pa, p1, sx, sy, sz, a, b1, d1);
         force_pair<KT, R, B2>(dc, A, d0, A0, V0, B0, p0.w, adiabatic, cond, fx, fy, fz, du, vsig, npair);
         force_pair<KT, R, B2>(dc, A, d1, A1, V1, B1, p1.w, adiabatic, cond, fx, fy, fz, du, vsig, npair);
+        if (upper) {
+            fx.flush();
+            fy.flush();
+            fz.flush();
+            du.flush();
+        }
     }
     for (; k < m; ++k) {
         const int b = (int)row[k];
@@ -434,6 +448,10 @@ __global__ void __launch_bounds__(force_threads<R>(), force_min_blocks<R>())
         Rel<R>::get(dc, pa, pb, sx, sy, sz, a, b, d);
         force_pair<KT, R, B2>(dc, A, d, Ab, Vb, Bb, pb.w, adiabatic, cond, fx, fy, fz, du, vsig, npair);
     }
+    fx.flush();
+    fy.flush();
+    fz.flush();
+    du.flush();
     if (dc.prof) count_warp(&counters[APR_PROF_FORCE], npair);
     const double scale = dc.m0_knorm;
     const unsigned i = perm[a];
