@@ -296,6 +296,11 @@ __device__ __forceinline__ long long min_image(long long d, int periodic, long l
     return d;
 }
 
+inline bool any_periodic(const DevCfg& dc)
+{
+    return dc.periodic[0] || dc.periodic[1] || dc.periodic[2];
+}
+
 __device__ __forceinline__ int min_image32(int d, int periodic, int L)
 {
     if (periodic) {

@@ -155,17 +155,22 @@ struct AccB {
     }
 };
 
-// relative position a - b of two sorted particles
+// relative position a - b of two sorted particles; PER false: no axis is periodic
+// (the minimum-image tests are compiled out)
 template <typename R>
 struct Rel;
 template <>
 struct Rel<float> {
+    template <bool PER = true>
     __device__ static void get(const DevCfg& dc, const int4& pa, const int4& pb, const double*,
                                const double*, const double*, int, int, float d[3])
     {
-        int dx = min_image32(pa.x - pb.x, dc.periodic[0], (int)dc.Lint[0]);
-        int dy = min_image32(pa.y - pb.y, dc.periodic[1], (int)dc.Lint[1]);
-        int dz = min_image32(pa.z - pb.z, dc.periodic[2], (int)dc.Lint[2]);
+        int dx = pa.x - pb.x, dy = pa.y - pb.y, dz = pa.z - pb.z;
+        if constexpr (PER) {
+            dx = min_image32(dx, dc.periodic[0], (int)dc.Lint[0]);
+            dy = min_image32(dy, dc.periodic[1], (int)dc.Lint[1]);
+            dz = min_image32(dz, dc.periodic[2], (int)dc.Lint[2]);
+        }
         d[0] = (float)dx * dc.deltaf;
         d[1] = (float)dy * dc.deltaf;
         d[2] = (float)dz * dc.deltaf;
@@ -173,6 +178,7 @@ struct Rel<float> {
 };
 template <>
 struct Rel<double> {
+    template <bool PER = true>
     __device__ static void get(const DevCfg& dc, const int4&, const int4&, const double* sx,
                                const double* sy, const double* sz, int a, int b, double d[3])
     {
@@ -181,7 +187,7 @@ struct Rel<double> {
         d[2] = sz[a] - sz[b];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-            if (dc.periodic[k]) {
+            if (PER && dc.periodic[k]) {
                 if (d[k] > 0.5 * dc.L[k]) d[k] -= dc.L[k];
                 else if (d[k] < -0.5 * dc.L[k]) d[k] += dc.L[k];
             }

@@ -23,12 +23,18 @@ namespace apr {
 
 // ----------------------------------------------------------------- density
 
-// exact lattice separation (minimum image)
+// exact lattice separation (minimum image; PER false: no axis is periodic)
+template <bool PER>
 __device__ __forceinline__ void lattice_d(const DevCfg& dc, const int4& pa, const int4& pb, int d[3])
 {
-    d[0] = min_image32(pa.x - pb.x, dc.periodic[0], (int)dc.Lint[0]);
-    d[1] = min_image32(pa.y - pb.y, dc.periodic[1], (int)dc.Lint[1]);
-    d[2] = min_image32(pa.z - pb.z, dc.periodic[2], (int)dc.Lint[2]);
+    d[0] = pa.x - pb.x;
+    d[1] = pa.y - pb.y;
+    d[2] = pa.z - pb.z;
+    if constexpr (PER) {
+        d[0] = min_image32(d[0], dc.periodic[0], (int)dc.Lint[0]);
+        d[1] = min_image32(d[1], dc.periodic[1], (int)dc.Lint[1]);
+        d[2] = min_image32(d[2], dc.periodic[2], (int)dc.Lint[2]);
+    }
 }
 
 template <typename R>
@@ -45,7 +51,7 @@ __device__ __forceinline__ double rel_r2<double>(const DevCfg& dc, const int*, c
                                                  const double* sy, const double* sz, int a, int b)
 {
     double d[3];
-    Rel<double>::get(dc, int4(), int4(), sx, sy, sz, a, b, d);
+    Rel<double>::get<true>(dc, int4(), int4(), sx, sy, sz, a, b, d);
     return d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
 }
 
@@ -66,7 +72,8 @@ constexpr int density_min_blocks() { return sizeof(R) == 4 ? 1024 / DENSITY_THRE
 template <typename R>
 constexpr int force_min_blocks() { return sizeof(R) == 4 ? 1024 / force_threads<R>() : 1; }
 
-template <typename R, int KT>
+// PER false: no periodic axis (minimum-image tests compiled out)
+template <typename R, int KT, bool PER>
 __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
     k_density(DevCfg dc, long long n, long long cap, double reach, const int4* __restrict__ pk,
               const double* __restrict__ sh, const unsigned int* __restrict__ nbr,
@@ -126,10 +133,10 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
             if (k + 8 <= mpad) nx = *reinterpret_cast<const uint4*>(row + k + 4);
             const int4 p0 = pk[b0], p1 = pk[b1], p2 = pk[b2], p3 = pk[b3];
             int d0[3], d1[3], d2[3], d3[3];
-            lattice_d(dc, pa, p0, d0);
-            lattice_d(dc, pa, p1, d1);
-            lattice_d(dc, pa, p2, d2);
-            lattice_d(dc, pa, p3, d3);
+            lattice_d<PER>(dc, pa, p0, d0);
+            lattice_d<PER>(dc, pa, p1, d1);
+            lattice_d<PER>(dc, pa, p2, d2);
+            lattice_d<PER>(dc, pa, p3, d3);
             const R r0 = rel_r2<R>(dc, d0, sx, sy, sz, a, b0), r1 = rel_r2<R>(dc, d1, sx, sy, sz, a, b1);
             const R r2 = rel_r2<R>(dc, d2, sx, sy, sz, a, b2), r3 = rel_r2<R>(dc, d3, sx, sy, sz, a, b3);
             if (first_pass) {
@@ -151,7 +158,7 @@ __global__ void __launch_bounds__(DENSITY_THREADS, density_min_blocks<R>())
             const int b = (int)row[k];
             const int4 pb = pk[b];
             int d[3];
-            lattice_d(dc, pa, pb, d);
+            lattice_d<PER>(dc, pa, pb, d);
             const R rb = rel_r2<R>(dc, d, sx, sy, sz, a, b);
             if (first_pass) near_update<R>(rb, d, bestf, best);
             density_term<KT, ACCEPT, R>(rb, hinv, r2max, pb.w, S, T, U, npair);
@@ -201,10 +208,15 @@ apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv, con
         const double reach = DENSITY_REACH;
         const bool c2 = c->cfg.kernel == APR_KERNEL_WENDLAND_C2;
         const DensityIO io = density_io(c, force_data);
-#define APR_DENSITY(R, KT)                                                                           \
-    APR_LAUNCH(c, (k_density<R, KT>), nblocks(work, DENSITY_THREADS), DENSITY_THREADS, c->dc, n, c->cap, reach, W.pk, W.sh,  \
+#define APR_DENSITY_P(R, KT, P)                                                                      \
+    APR_LAUNCH(c, (k_density<R, KT, P>), nblocks(work, DENSITY_THREADS), DENSITY_THREADS, c->dc, n, c->cap, reach, W.pk, W.sh,  \
                W.nbr, W.ncnt, W.sx, W.sy, W.sz, io, W.status, W.counters, active, nactive,         \
                W.retry_q[out_q], &W.status[ST_RETRY_N + out_q])
+#define APR_DENSITY(R, KT)                                                                           \
+    do {                                                                                             \
+        if (any_periodic(c->dc)) APR_DENSITY_P(R, KT, true);                                         \
+        else APR_DENSITY_P(R, KT, false);                                                            \
+    } while (0)
         if (c->cfg.precision == APR_PREC_FP64) {
             if (c2) APR_DENSITY(double, APR_KERNEL_WENDLAND_C2);
             else APR_DENSITY(double, APR_KERNEL_M4);
@@ -213,6 +225,7 @@ apr_status density_pass(apr_ctx* c, long long* uncovered, long long* noconv, con
             else APR_DENSITY(float, APR_KERNEL_M4);
         }
 #undef APR_DENSITY
+#undef APR_DENSITY_P
     }
     prof_end(c, ps);
     // one read-back for the index status words and the density counters
@@ -470,6 +483,8 @@ apr_status force_pass(apr_ctx* c, const int* active, long long nactive)
     if (n <= 0 || work <= 0) return APR_OK;
     const int ps = prof_begin(c, APR_PROF_FORCE);
     const bool c2 = c->cfg.kernel == APR_KERNEL_WENDLAND_C2;
+// (the force kernel keeps the run-time minimum-image tests: compiled out they made it
+// slower on the flyby and the disc, 3.14 -> 3.22 and 0.70 -> 0.74 ms)
 #define APR_FORCE(R, KT, B2, A, V, B)                                                                \
     APR_LAUNCH(c, (k_force<R, KT, B2>), nblocks(work, force_threads<R>()), force_threads<R>(), c->dc, n, c->cap, W.pk, A, V, B, W.nbr, \
                W.ncnt, W.sx, W.sy, W.sz, W.perm, c->p.ax, c->p.ay, c->p.az, c->p.dudt, c->p.vsig,   \
