@@ -412,12 +412,21 @@ def measure(w, precision, steps, warmup, torch, flush, cap_factor, max_neigh, sa
     return res
 
 
+DF_GROUPS = ("sort", "tree", "lists", "density", "force")
+
+
 def summary(r, steps, peaks, precision):
     """value, per-step breakdown and rooflines of one measured run."""
     prof = r["prof"]
     n_mean = r["psteps"] / steps
     rows = rooflines(prof, steps, r["ms"], n_mean, peaks, precision)
+    # the index, density and force alone (quantise and sort, radix tree, cells and
+    # lists, density solve, forces): the groups' device time per step
+    df_ms = sum(prof[g]["ms"] for g in DF_GROUPS)
     return {"value": r["psteps"] / (r["ms"] / 1e3), "unit": UNIT, "ms_per_step": r["ms"] / steps,
+            "density_force_only": {"value": r["psteps"] / (df_ms / 1e3) if df_ms > 0 else None,
+                                   "unit": UNIT, "ms_per_step": df_ms / steps,
+                                   "groups": list(DF_GROUPS)},
             "steps": steps, "n_initial": r["n_initial"], "n_after_init": r["n_after_init"],
             "n_last": r["n_last"],
             "breakdown_ms_per_step": {g: round(prof[g]["ms"] / steps, 4) for g in GROUPS},
@@ -486,6 +495,7 @@ def run_ours(args):
                       "wall_s_timed": r32["wall_s_timed"]},
            "roofline": roofline, "rooflines": s32["rooflines"],
            "breakdown_ms_per_step": s32["breakdown_ms_per_step"],
+           "density_force_only": s32["density_force_only"],
            "gpu_launches": r32["launches"], "clocks": r32["clocks"], "peaks": peaks}
 
     r64 = None
@@ -494,7 +504,7 @@ def run_ours(args):
                       sample_ids, uuid)
         s64 = summary(r64, args.fp64_steps, peaks, "fp64")
         out["fp64"] = {k: s64[k] for k in ("value", "ms_per_step", "steps", "breakdown_ms_per_step",
-                                            "rooflines")}
+                                            "density_force_only", "rooflines")}
         out["fp32_over_fp64"] = value / s64["value"]
 
     if rank == 0 and not args.no_e2e:
@@ -568,7 +578,8 @@ def second_line(torch, flush, peaks, args):
             r64 = measure(w, "fp64", k64, 1, torch, flush, capf, mn)
             s64 = summary(r64, k64, peaks, "fp64")
             line["fp64"] = {x: s64[x] for x in ("value", "ms_per_step", "steps",
-                                                 "breakdown_ms_per_step", "rooflines")}
+                                                 "breakdown_ms_per_step", "density_force_only",
+                                                 "rooflines")}
             line["fp32_over_fp64"] = s32["value"] / s64["value"]
         return line
     except Exception as e:  # a second line never takes the headline down
