@@ -203,3 +203,26 @@ def test_density_recovers_from_a_far_too_large_initial_h():
     g = sim(w, max_neigh=256)
     g.density()
     assert rel(g.get("rho"), o["rho"]).max() < 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("which", ["lattice", "disc"])
+def test_profile_pair_counts_match_the_lists(precision, which):
+    """The profiler's force pair count (pairs inside max(2 h_a, 2 h_b), counted once per
+    warp) equals the total of the symmetric neighbour lists at the same h, which the
+    list tests tie to the oracle; the density count covers about one pass or more over
+    every particle's pairs inside 2 h_a (each pass at the h it evaluated, within a few
+    percent of the final one)."""
+    w = (with_velocities(apr_synth.c1_lattice(), 0.3) if which == "lattice"
+         else apr_synth.disc_planet(20000))
+    g = sim(w, precision, capacity=2 * len(w["p"]["x"]), max_neigh=0 if which == "lattice" else 2048)
+    g.profile_enable(True)
+    g.density()
+    dens_pairs = g.profile(reset=True)["density"]["pairs"]
+    g.force()
+    force_pairs = g.profile()["force"]["pairs"]
+    off1, _ = g.neighbour_lists(mode=1)
+    off0, _ = g.neighbour_lists(mode=0)
+    # float q < 2 against the exact lattice test: at most a few pairs on the boundary
+    assert abs(force_pairs - off1[-1]) <= max(2, 1e-5 * off1[-1])
+    assert dens_pairs >= 0.9 * off0[-1]
