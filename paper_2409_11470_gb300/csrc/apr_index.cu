@@ -893,9 +893,15 @@ __global__ void __launch_bounds__(128)
             const int node = have ? stk[w][sp - 1 - lane] : 0;
             sp -= take;
             bool pass = false, cell = false;
-            int first = 0, count = 0;
+            int first = 0, count = 0, lc = 0, rc = 0;
             if (have) {
                 const NodeBox o = node_box(node, pk, sthr, nlo, nhi, nthr);
+                // the children's indices in the same round trip as the node's box (needed
+                // only if it passes, but a second dependent load per round costs more)
+                if (node >= 0) {
+                    lc = __ldg(&left[node]);
+                    rc = __ldg(&right[node]);
+                }
                 const unsigned long long thr = (mode == 0 || o.thr < thr_self) ? thr_self : o.thr;
                 pass = box_dist2(dc, me.lo, me.hi, o.lo, o.hi) < thr;
                 cell = o.count <= CELL_MAX;
@@ -917,8 +923,8 @@ __global__ void __launch_bounds__(128)
             }
             if (pass && !cell) {
                 const int pos = sp + 2 * __popc(im & lt);
-                stk[w][pos] = __ldg(&right[node]);
-                stk[w][pos + 1] = __ldg(&left[node]);
+                stk[w][pos] = rc;
+                stk[w][pos + 1] = lc;
             }
             sp += 2 * nint;
             __syncwarp();
@@ -1476,9 +1482,13 @@ __global__ void __launch_bounds__(128)
             const int node = have ? stk[w][sp - 1 - lane] : 0;
             sp -= take;
             bool pass = false, cell = false;
-            int first = 0, count = 0;
+            int first = 0, count = 0, lc = 0, rc = 0;
             if (have) {
                 const NodeBox o = node_box(node, pk, sthr, nlo, nhi, nthr);
+                if (node >= 0) {  // children with the box (see k_candidates)
+                    lc = __ldg(&left[node]);
+                    rc = __ldg(&right[node]);
+                }
                 const unsigned long long T = (SYM && o.thr > ta) ? o.thr : ta;
                 const long long gx = axis_gap<PX>(pa.x, o.lo[0], o.hi[0], Lx);
                 const long long gy = axis_gap<PY>(pa.y, o.lo[1], o.hi[1], Ly);
@@ -1528,8 +1538,8 @@ __global__ void __launch_bounds__(128)
             }
             if (pass && !cell) {
                 const int pos = sp + 2 * __popc(im & lt);
-                stk[w][pos] = __ldg(&right[node]);
-                stk[w][pos + 1] = __ldg(&left[node]);
+                stk[w][pos] = rc;
+                stk[w][pos + 1] = lc;
             }
             sp += 2 * nint;
             __syncwarp();
