@@ -633,6 +633,10 @@ __global__ void __launch_bounds__(TREE_UP_T)
             atomicOr(&status[ST_TREE_BAD], 1);
             return;
         }
+        // the topology (written by the build, read-only here) loads with the arrival
+        // count instead of after it
+        const int lcn = __ldg(&left[node]), rcn = __ldg(&right[node]);
+        const int par = __ldg(&parent_int[node]);
         // release: this thread's child data (stored just before) is visible to the
         // sibling's thread; acquire: the sibling's child data is visible here (the
         // same block's threads for a local node, any thread for the others)
@@ -640,8 +644,8 @@ __global__ void __launch_bounds__(TREE_UP_T)
         const unsigned old = local ? atom_add_acq_rel_cta_shared(&vis[node - b0], 1u)
                                    : atom_add_acq_rel_u32((unsigned*)&visit[node], 1u);
         if (old == 0u) return;
-        NodeData a = node_data(left[node], pk, sh, nlo, nhi, nhmax);
-        NodeData b = node_data(right[node], pk, sh, nlo, nhi, nhmax);
+        NodeData a = node_data(lcn, pk, sh, nlo, nhi, nhmax);
+        NodeData b = node_data(rcn, pk, sh, nlo, nhi, nhmax);
         int4 lo = make_int4(min(a.lo[0], b.lo[0]), min(a.lo[1], b.lo[1]), min(a.lo[2], b.lo[2]),
                             a.count + b.count);
         int4 hi = make_int4(max(a.hi[0], b.hi[0]), max(a.hi[1], b.hi[1]), max(a.hi[2], b.hi[2]),
@@ -650,7 +654,7 @@ __global__ void __launch_bounds__(TREE_UP_T)
         __stcg(&nhi[node], hi);
         __stcg(&nhmax[node], fmax(a.hmax, b.hmax));
         if (node == 0) return;
-        node = parent_int[node];
+        node = par;
     }
 }
 
