@@ -70,3 +70,25 @@ def test_noalloc_rejects_more_particles_than_its_scratch():
     st = f(C.byref(g.cfg), C.byref(g.parts), 16_777_217, None, 0,
            C.c_void_p(g.stream.cuda_stream), C.byref(out), err, 256)
     assert st == 1 and b"16,777,216" in err.value
+
+
+def test_noalloc_refuses_a_stream_under_capture():
+    """Every call reads its result back and synchronises its stream, which a stream
+    under capture does not allow: the call returns APR_ERR_ARG before it launches
+    anything, and the capture ends normally (an empty graph)."""
+    import torch
+    B, f = _entry()
+    g = sim(apr_synth.c1_lattice())
+    out = B.Stats()
+    err = C.create_string_buffer(256)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph, stream=s):
+        st = f(C.byref(g.cfg), C.byref(g.parts), g.n, None, 0, C.c_void_p(s.cuda_stream),
+               C.byref(out), err, 256)
+    assert st == 1 and b"capture" in err.value
+    # the entry works again once the capture has ended
+    st = f(C.byref(g.cfg), C.byref(g.parts), g.n, None, 0, C.c_void_p(g.stream.cuda_stream),
+           C.byref(out), err, 256)
+    assert st == 0, err.value
