@@ -886,6 +886,7 @@ __global__ void __launch_bounds__(128)
     for (int cid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; cid < ncell; cid += nwarps) {
         const NodeBox me = node_box(cell_node[cid], pk, sthr, nlo, nhi, nthr);
         const unsigned long long thr_self = me.thr;
+        const bool nonper = !(dc.periodic[0] || dc.periodic[1] || dc.periodic[2]);
         __syncwarp();
         if (lane == 0) stk[w][0] = n >= 2 ? 0 : ~0;
         __syncwarp();
@@ -907,7 +908,16 @@ __global__ void __launch_bounds__(128)
                     rc = __ldg(&right[node]);
                 }
                 const unsigned long long thr = (mode == 0 || o.thr < thr_self) ? thr_self : o.thr;
-                pass = box_dist2(dc, me.lo, me.hi, o.lo, o.hi) < thr;
+                if (nonper) {
+                    // in float, widened by 2^-16 relative: a superset of the exact test
+                    // (the list kernel culls every staged candidate exactly)
+                    const float gx = (float)max(0, max(o.lo[0] - me.hi[0], me.lo[0] - o.hi[0]));
+                    const float gy = (float)max(0, max(o.lo[1] - me.hi[1], me.lo[1] - o.hi[1]));
+                    const float gz = (float)max(0, max(o.lo[2] - me.hi[2], me.lo[2] - o.hi[2]));
+                    pass = fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < (float)thr * (1.0f + 1.0f / 65536.0f);
+                } else {
+                    pass = box_dist2(dc, me.lo, me.hi, o.lo, o.hi) < thr;
+                }
                 cell = o.count <= CELL_MAX;
                 first = o.first;
                 count = o.count;
