@@ -996,7 +996,11 @@ __global__ void k_thresholds_queue(DevCfg dc, const int* __restrict__ queue,
 // minimum image differs from the shifted one is then at least
 // L/2 - ceil(w/2) >= R apart on that axis, so both readings reject it.
 // Batches holding a particle that breaks this take the per-pair minimum image.
-constexpr int LIST_BUF = 64;
+// A batch is tested once it holds LIST_FLUSH candidates (a candidate cell adds at
+// most 32): three or four chunks of 32 per batch, so that a batch's ragged last
+// chunk and fixed costs are shared by more candidates than with batches of 32.
+constexpr int LIST_FLUSH = 96;
+constexpr int LIST_BUF = LIST_FLUSH + 32;
 
 __device__ __forceinline__ int wrap_near(int d, int L)
 {
@@ -1109,13 +1113,23 @@ struct RowWriter {
     __device__ __forceinline__ void push(unsigned* __restrict__ row, int& m, int K, unsigned v)
     {
         if (m < K) {
-            const int c = m & 3;
-            e0 = c == 0 ? v : e0;
-            e1 = c == 1 ? v : e1;
-            e2 = c == 2 ? v : e2;
-            e3 = c == 3 ? v : e3;
-            if (c == 3) *reinterpret_cast<uint4*>(row + (m - 3)) = make_uint4(e0, e1, e2, e3);
+            // the last four entries, newest in e3
+            e0 = e1;
+            e1 = e2;
+            e2 = e3;
+            e3 = v;
+            if ((m & 3) == 3) *reinterpret_cast<uint4*>(row + (m - 3)) = make_uint4(e0, e1, e2, e3);
         }
+        ++m;
+    }
+    // the same with m < K known
+    __device__ __forceinline__ void push_room(unsigned* __restrict__ row, int& m, unsigned v)
+    {
+        e0 = e1;
+        e1 = e2;
+        e2 = e3;
+        e3 = v;
+        if ((m & 3) == 3) *reinterpret_cast<uint4*>(row + (m - 3)) = make_uint4(e0, e1, e2, e3);
         ++m;
     }
     // the last one to three entries kept
@@ -1123,9 +1137,16 @@ struct RowWriter {
     {
         const int mw = m < K ? m : K;
         const int c = mw & 3, base = mw - c;
-        if (c > 0) row[base] = e0;
-        if (c > 1) row[base + 1] = e1;
-        if (c > 2) row[base + 2] = e2;
+        if (c == 1) row[base] = e3;
+        if (c == 2) {
+            row[base] = e2;
+            row[base + 1] = e3;
+        }
+        if (c == 3) {
+            row[base] = e1;
+            row[base + 1] = e2;
+            row[base + 2] = e3;
+        }
     }
 };
 
@@ -1216,6 +1237,15 @@ __device__ __forceinline__ void list_batch_fast(int nb, const int4* __restrict__
                 if (exact_pair<PX, PY, PZ, SYM, false>(cq[l], SYM ? ct[l] : 0ULL, SYM ? cr[l] : 0u,
                                                        pa, a, own, ta, Ra, Lx, Ly, Lz))
                     hit |= 1u << j;
+            }
+        }
+        if (!FZ::on && m + __popc(hit) <= K) {
+            // room for every hit of the chunk: no per-entry bound test
+            while (hit) {
+                const int j = __ffs(hit) - 1;
+                hit &= hit - 1u;
+                const int b = cq[base + j].w;
+                if (b != a) wr.push_room(row, m, (unsigned)b);
             }
         }
         while (hit) {
@@ -1413,7 +1443,7 @@ __global__ void __launch_bounds__(LIST_THREADS)
         }
         nb += __popc(km);
         __syncwarp();
-        if (nb >= 32) {
+        if (nb >= LIST_FLUSH) {
             flush_batch<PX, PY, PZ, SYM>(nb, wrapb, vlane, vown, rmin, cq[w], cf[w], ct[w], cr[w], pa,
                                          pfx, pfy, pfz, tfa, a, own, ta, Ra, Lx, Ly, Lz, K, row, wr,
                                          m, fz);
