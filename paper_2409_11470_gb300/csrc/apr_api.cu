@@ -840,7 +840,9 @@ apr_status apr_step(apr_ctx* c, double dt, double* dt_used, apr_stats* stats,
     // conservation sums and the next step's limit)
     kick_sinks(c, hdt);
     apr_stats st_local;
+    ps = prof_begin(c, APR_PROF_OTHER);
     s = compute_stats_dt(c, stats ? stats : &st_local, &c->dt_next, hdt);
+    prof_end(c, ps);
     if (s != APR_OK) return s;
     c->dt_valid = true;
     return APR_OK;

@@ -1714,6 +1714,30 @@ static int red_grid(long long n)
     return (int)std::min<long long>(RED_BLOCKS, 152 * per_sm);
 }
 
+// one particle's terms of the conservation sums in units of m0 (the host scales
+// them): w = 2^-level makes every product with it exact
+__device__ __forceinline__ void stats_terms(const DevCfg& dc, const apr_particles& p, long long i,
+                                            double w, double vx, double vy, double vz, double* v)
+{
+    const double mx = w * vx, my = w * vy, mz = w * vz;
+    const double x = p.x[i], y = p.y[i], z = p.z[i];
+    v[0] += w;
+    v[1] += mx;
+    v[2] += my;
+    v[3] += mz;
+    v[4] = fma(-z, my, fma(y, mz, v[4]));
+    v[5] = fma(-x, mz, fma(z, mx, v[5]));
+    v[6] = fma(-y, mx, fma(x, my, v[6]));
+    v[7] = fma(mz, vz, fma(my, vy, fma(mx, vx, v[7])));
+    if (dc.eos == APR_EOS_ADIABATIC) v[8] = fma(w, p.u[i], v[8]);
+}
+
+// the sums' units: m0 for all, m0 / 2 for the kinetic energy (slot 7)
+static void stats_scale(const apr_ctx* c, double* r)
+{
+    for (int k = 0; k < 9; ++k) r[k] *= k == 7 ? 0.5 * c->dc.m0 : c->dc.m0;
+}
+
 __global__ void __launch_bounds__(256) k_stats(DevCfg dc, long long n, apr_particles p,
                                                double* partials)
 {
@@ -1721,17 +1745,7 @@ __global__ void __launch_bounds__(256) k_stats(DevCfg dc, long long n, apr_parti
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         if (p.flags[i] & APR_FLAG_DEAD) continue;
-        double m = dc.m0 * level_mass_d(p.level[i]);
-        double vx = p.vx[i], vy = p.vy[i], vz = p.vz[i];
-        v[0] += m;
-        v[1] += m * vx;
-        v[2] += m * vy;
-        v[3] += m * vz;
-        v[4] += m * (p.y[i] * vz - p.z[i] * vy);
-        v[5] += m * (p.z[i] * vx - p.x[i] * vz);
-        v[6] += m * (p.x[i] * vy - p.y[i] * vx);
-        v[7] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
-        if (dc.eos == APR_EOS_ADIABATIC) v[8] += m * p.u[i];
+        stats_terms(dc, p, i, level_mass_d(p.level[i]), p.vx[i], p.vy[i], p.vz[i], v);
     }
     block_reduce_store<9>(v, partials);
 }
@@ -1742,10 +1756,54 @@ __global__ void __launch_bounds__(256) k_stats(DevCfg dc, long long n, apr_parti
 // criterion keeps its best (numerator, denominator) pair, compared by cross
 // products (h / |a| compares as h^2 / a^2); the winner's quotient is formed once
 // per block with the same expressions as per particle
+// The high word of a positive normal double, read as an integer, is 2^20 (log2 x +
+// 1023) less at most 2^20 max_f (log2(1 + f) - f) + 1 < 90,253 (the mantissa's
+// linear reading of log2 and its truncation to 20 bits): a key compared in this
+// log domain with that error on both sides settles most candidates with integer
+// arithmetic only.
+constexpr long long HL_ERR = 90300;
+constexpr long long HL_LOG3 = 1662000;  // 2^20 log2 3, rounded up
+__device__ __forceinline__ bool hl_normal(int hi) { return hi >= 0x00100000 && hi < 0x7ff00000; }
+constexpr long long HL_NONE = 1LL << 60;  // no log-domain key: no candidate is skipped
+
 struct DtMin {
     double cn = 0.0, cd = 0.0;  // courant: h, v_sig (cd == 0: none yet)
     double fn = 0.0, fd = 0.0;  // force: h^2, a^2 (fd == 0: none yet)
     double fh = 0.0;            // the force winner's h
+    // log-domain keys of the winners (HL_NONE: none, or not normal)
+    long long ck = HL_NONE, fk = HL_NONE;
+    // add() for a particle whose courant key h / v_sig or force key h^2 / |a|^2 is
+    // certainly larger than the winner's skips that criterion's float64 test: with
+    // a_max the largest |a| component, |a|^2 lies in [a_max^2, 3 a_max^2], so the
+    // log-domain key 2 (H(h) - H(a_max)) is within 2 HL_ERR + 2^20 log2 3 of the
+    // key's log; a skip needs the two keys' logs apart by at least 2^-19, far
+    // beyond the rounding of the float64 cross products, which then never prefer it
+    __device__ __forceinline__ void add_keyed(double h, double vsig, double ax, double ay, double az)
+    {
+        const int Ah = __double2hiint(h), Av = __double2hiint(vsig);
+        const bool nh = hl_normal(Ah);
+        const long long kc = (nh && hl_normal(Av)) ? (long long)Ah - Av : HL_NONE;
+        if (!(kc != HL_NONE && kc > ck + 2 * HL_ERR + 2)) {
+            if (vsig > 0.0 && (cd == 0.0 || h * cd < cn * vsig)) {
+                cn = h;
+                cd = vsig;
+                ck = kc;
+            }
+        }
+        const int Am = max(max(__double2hiint(ax) & 0x7fffffff, __double2hiint(ay) & 0x7fffffff),
+                           __double2hiint(az) & 0x7fffffff);
+        const long long kf = (nh && hl_normal(Am)) ? 2 * ((long long)Ah - Am) : HL_NONE;
+        if (!(kf != HL_NONE && kf > fk + 4 * HL_ERR + HL_LOG3 + 2)) {
+            const double a2 = ax * ax + ay * ay + az * az;
+            const double h2 = h * h;
+            if (a2 > 0.0 && (fd == 0.0 || h2 * fd < fn * a2)) {
+                fn = h2;
+                fd = a2;
+                fh = h;
+                fk = kf;
+            }
+        }
+    }
     __device__ void add(double h, double vsig, double a2)
     {
         if (vsig > 0.0 && (cd == 0.0 || h * cd < cn * vsig)) {
@@ -1800,7 +1858,7 @@ __global__ void __launch_bounds__(256) k_stats_dt(DevCfg dc, long long n, apr_pa
          i += (long long)gridDim.x * blockDim.x) {
         const unsigned char fl = p.flags[i];
         if (fl & APR_FLAG_DEAD) continue;
-        double m = dc.m0 * level_mass_d(p.level[i]);
+        const double w = level_mass_d(p.level[i]);
         double vx = p.vx[i], vy = p.vy[i], vz = p.vz[i];
         if (hdt != 0.0 && !(fl & APR_FLAG_FIXED)) {
             vx += hdt * p.ax[i];
@@ -1811,17 +1869,9 @@ __global__ void __launch_bounds__(256) k_stats_dt(DevCfg dc, long long n, apr_pa
             p.vz[i] = vz;
             if (dc.eos == APR_EOS_ADIABATIC) p.u[i] += hdt * p.dudt[i];
         }
-        v[0] += m;
-        v[1] += m * vx;
-        v[2] += m * vy;
-        v[3] += m * vz;
-        v[4] += m * (p.y[i] * vz - p.z[i] * vy);
-        v[5] += m * (p.z[i] * vx - p.x[i] * vz);
-        v[6] += m * (p.x[i] * vy - p.y[i] * vx);
-        v[7] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
-        if (dc.eos == APR_EOS_ADIABATIC) v[8] += m * p.u[i];
+        stats_terms(dc, p, i, w, vx, vy, vz, v);
         if (fl & APR_FLAG_FIXED) continue;
-        best.add(p.h[i], p.vsig[i], p.ax[i] * p.ax[i] + p.ay[i] * p.ay[i] + p.az[i] * p.az[i]);
+        best.add_keyed(p.h[i], p.vsig[i], p.ax[i], p.ay[i], p.az[i]);
     }
     __shared__ double sm[10][8];
     __shared__ DtMin sd[8];
@@ -1879,6 +1929,7 @@ apr_status compute_stats_dt(apr_ctx* c, apr_stats* st, double* dt, double kick_h
     double r[10];
     apr_status s = reduce_readback_n(c, nblk, 10, 1u << 9, r);
     if (s != APR_OK) return s;
+    stats_scale(c, r);
     stats_from(c, r, st);
     *dt = r[9];
     return APR_OK;
@@ -1891,6 +1942,7 @@ apr_status compute_stats(apr_ctx* c, apr_stats* st)
     double r[9];
     apr_status s = reduce_readback_n(c, nblk, 9, 0u, r);
     if (s != APR_OK) return s;
+    stats_scale(c, r);
     st->mass = r[0];
     for (int k = 0; k < 3; ++k) {
         st->mom[k] = r[1 + k];
