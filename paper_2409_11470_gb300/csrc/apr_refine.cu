@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "apr_internal.cuh"
+#include "apr_pair.cuh"
 
 namespace apr {
 
@@ -2010,21 +2011,25 @@ __device__ __forceinline__ double rsqrt_newton(double x)
 // the particles whose step ends at substep boundary `sub` take their pull.
 // NS bounds the number of point masses (the per-block sums are 3 NS wide).  F32
 // (the FP32-mixed path): the separation is formed in FP64 and the pull evaluated
-// in FP32, like the pair sums; the point masses' sums stay FP64.
+// in FP32, like the pair sums; the point masses' sums are compensated in FP32 per
+// thread and added in FP64 across threads.
 template <int NS, bool F32>
 __global__ void __launch_bounds__(256) k_sink_gravity(DevCfg dc, DevSinks sk, long long n,
                                                       apr_particles p, int B, long long sub,
                                                       double* partials)
 {
     if constexpr (F32) {
-        double v[3 * NS];
-        for (int k = 0; k < 3 * NS; ++k) v[k] = 0.0;
+        // the point masses' pull by this thread's particles, compensated in float
+        // like the pair sums (the FP64 pipe is narrow on this part); the threads'
+        // sums are added in float64
+        Acc<float> w[3 * NS];
         const int ns = sk.n < NS ? sk.n : NS;
         const float G = (float)dc.G;
         for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
              i += (long long)gridDim.x * blockDim.x) {
             if (p.flags[i] & APR_FLAG_DEAD) continue;
-            const float mi = (float)(dc.m0 * level_mass_d(p.level[i]));
+            // float(m0 2^-level) = float(m0) 2^-level: a power of two scales exactly
+            const float mi = dc.m0f * level_mass_f(p.level[i]);
             const bool pulled = B < 0 || sub % ((1LL << B) >> p.bin[i]) == 0;
             float ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
@@ -2040,9 +2045,9 @@ __global__ void __launch_bounds__(256) k_sink_gravity(DevCfg dc, DevSinks sk, lo
                 ay -= fm * dy;
                 az -= fm * dz;
                 const float fi = f * mi;
-                v[3 * j + 0] += (double)(fi * dx);
-                v[3 * j + 1] += (double)(fi * dy);
-                v[3 * j + 2] += (double)(fi * dz);
+                w[3 * j + 0].add(fi * dx);
+                w[3 * j + 1].add(fi * dy);
+                w[3 * j + 2].add(fi * dz);
             }
             if (pulled) {
                 p.ax[i] += (double)ax;
@@ -2050,6 +2055,8 @@ __global__ void __launch_bounds__(256) k_sink_gravity(DevCfg dc, DevSinks sk, lo
                 p.az[i] += (double)az;
             }
         }
+        double v[3 * NS];
+        for (int k = 0; k < 3 * NS; ++k) v[k] = (double)w[k].s - (double)w[k].c;
         block_reduce_store<3 * NS>(v, partials);
         return;
     }
