@@ -248,6 +248,7 @@ static apr_status check_cfg(const apr_config* cfg, DevCfg* dc, std::string* why)
         int ex = 0;
         const double mant = std::frexp(cfg->delta, &ex);
         dc->inv_delta = mant == 0.5 ? std::ldexp(1.0, 1 - ex) : 0.0;
+        dc->inv_delta2 = 2.0 * dc->inv_delta;
     }
     dc->alpha_avf = (float)cfg->alpha_av;
     dc->hfactf = (float)cfg->hfact;

@@ -958,10 +958,12 @@ __global__ void k_thresholds(DevCfg dc, long long n, double reach, const double*
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s == 0) status[ST_POINT_N] = 0;  // the per-particle queue of this list build
     if (s >= n) return;
-    const unsigned long long t = lattice_threshold(dc, reach * sh[s]);
+    const double rad = lattice_radius(dc, reach * sh[s]);
+    const unsigned long long t = lattice_threshold_t(rad);
     thr[s] = t;
-    // a float root as the start, made exact by the integer steps below
-    unsigned long long r = (unsigned long long)ceilf(sqrtf((float)t));
+    // ceil(|radius|) as the start (its square is at least radius^2, so it lies at
+    // most a step or two from the root), made exact by the integer steps below
+    unsigned long long r = t >= 4611686018427387904ULL ? 2147483648ULL : ceil_bits(rad);
     while (r > 0 && (r - 1) * (r - 1) >= t) --r;
     while (r * r < t) ++r;
     rint[s] = r > 0xffffffffULL ? 0xffffffffu : (unsigned)r;
@@ -977,9 +979,12 @@ __global__ void k_thresholds_queue(DevCfg dc, const int* __restrict__ queue,
     if (i >= min((long long)*qlen, n)) return;
     const int s = queue[i];
     if (s < 0 || s >= n) return;
-    const unsigned long long t = lattice_threshold(dc, reach * sh[s]);
+    const double rad = lattice_radius(dc, reach * sh[s]);
+    const unsigned long long t = lattice_threshold_t(rad);
     thr[s] = t;
-    unsigned long long r = (unsigned long long)ceilf(sqrtf((float)t));
+    // ceil(|radius|) as the start (its square is at least radius^2, so it lies at
+    // most a step or two from the root), made exact by the integer steps below
+    unsigned long long r = t >= 4611686018427387904ULL ? 2147483648ULL : ceil_bits(rad);
     while (r > 0 && (r - 1) * (r - 1) >= t) --r;
     while (r * r < t) ++r;
     rint[s] = r > 0xffffffffULL ? 0xffffffffu : (unsigned)r;

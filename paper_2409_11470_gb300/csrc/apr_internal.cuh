@@ -92,6 +92,7 @@ struct DevCfg {
     double delta;
     float deltaf;
     double inv_delta;          // 1 / delta when delta is a power of two (exact), else 0
+    double inv_delta2;         // 2 inv_delta (exact; 0 with inv_delta)
     double hfact, gamma;
     int eos;
     double cs0, qcs;
@@ -279,12 +280,41 @@ __host__ __device__ inline unsigned long long neighbour_threshold(double h, doub
 
 // the same threshold with dc's lattice unit: a multiplication where the unit is a
 // power of two (then x * (1/delta) equals x / delta exactly), else the division
+// ceil(|d|) of a double with |d| < 2^62 as an integer, read off its bits with
+// integer operations (the FP64 pipe, which rounds and converts, is narrow on this part)
+__device__ __forceinline__ unsigned long long ceil_bits(double d)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d) & 0x7fffffffffffffffULL;
+    const int e = (int)(b >> 52) - 1023;
+    if (e < 0) return b != 0ULL ? 1ULL : 0ULL;
+    const unsigned long long m = (b & ((1ULL << 52) - 1ULL)) | (1ULL << 52);
+    if (e >= 52) return m << (e - 52);
+    const unsigned long long ip = m >> (52 - e);
+    return ip + ((m & ((1ULL << (52 - e)) - 1ULL)) != 0ULL ? 1ULL : 0ULL);
+}
+
+// the lattice radius 2 h / delta (as the oracle forms it: with a power-of-two unit
+// (2 h) inv_delta = h (2 inv_delta), both one rounding of the same product)
+__device__ __forceinline__ double lattice_radius(const DevCfg& dc, double h)
+{
+    return dc.inv_delta > 0.0 ? h * dc.inv_delta2 : (2.0 * h) / dc.delta;
+}
+
+// ceil(t^2) of t = lattice_radius, capped at 2^62; t^2 in [0, 4.6e18) (compared as
+// bits: for non-negative doubles the bit patterns order as the values, and a NaN's
+// lie above) takes ceil_bits
+__device__ __forceinline__ unsigned long long lattice_threshold_t(double t)
+{
+    const double t2 = t * t;
+    if (!((unsigned long long)__double_as_longlong(t2) <
+          (unsigned long long)__double_as_longlong(4.6e18)))
+        return 4611686018427387904ULL;
+    return ceil_bits(t2);
+}
+
 __device__ __forceinline__ unsigned long long lattice_threshold(const DevCfg& dc, double h)
 {
-    double t = dc.inv_delta > 0.0 ? (2.0 * h) * dc.inv_delta : (2.0 * h) / dc.delta;
-    double t2 = t * t;
-    if (!(t2 < 4.6e18)) return 4611686018427387904ULL;
-    return (unsigned long long)ceil(t2);
+    return lattice_threshold_t(lattice_radius(dc, h));
 }
 
 __device__ __forceinline__ long long min_image(long long d, int periodic, long long L)
