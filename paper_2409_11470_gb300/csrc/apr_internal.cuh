@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <string>
 
@@ -280,11 +281,20 @@ __host__ __device__ inline unsigned long long neighbour_threshold(double h, doub
 
 // the same threshold with dc's lattice unit: a multiplication where the unit is a
 // power of two (then x * (1/delta) equals x / delta exactly), else the division
+// the bits of a double (host and device: the threshold arithmetic below is also
+// compiled for the host by a test)
+__host__ __device__ __forceinline__ unsigned long long dbits(double d)
+{
+    unsigned long long b;
+    memcpy(&b, &d, sizeof b);
+    return b;
+}
+
 // ceil(|d|) of a double with |d| < 2^62 as an integer, read off its bits with
 // integer operations (the FP64 pipe, which rounds and converts, is narrow on this part)
-__device__ __forceinline__ unsigned long long ceil_bits(double d)
+__host__ __device__ __forceinline__ unsigned long long ceil_bits(double d)
 {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(d) & 0x7fffffffffffffffULL;
+    const unsigned long long b = dbits(d) & 0x7fffffffffffffffULL;
     const int e = (int)(b >> 52) - 1023;
     if (e < 0) return b != 0ULL ? 1ULL : 0ULL;
     const unsigned long long m = (b & ((1ULL << 52) - 1ULL)) | (1ULL << 52);
@@ -295,7 +305,7 @@ __device__ __forceinline__ unsigned long long ceil_bits(double d)
 
 // the lattice radius 2 h / delta (as the oracle forms it: with a power-of-two unit
 // (2 h) inv_delta = h (2 inv_delta), both one rounding of the same product)
-__device__ __forceinline__ double lattice_radius(const DevCfg& dc, double h)
+__host__ __device__ __forceinline__ double lattice_radius(const DevCfg& dc, double h)
 {
     return dc.inv_delta > 0.0 ? h * dc.inv_delta2 : (2.0 * h) / dc.delta;
 }
@@ -303,11 +313,10 @@ __device__ __forceinline__ double lattice_radius(const DevCfg& dc, double h)
 // ceil(t^2) of t = lattice_radius, capped at 2^62; t^2 in [0, 4.6e18) (compared as
 // bits: for non-negative doubles the bit patterns order as the values, and a NaN's
 // lie above) takes ceil_bits
-__device__ __forceinline__ unsigned long long lattice_threshold_t(double t)
+__host__ __device__ __forceinline__ unsigned long long lattice_threshold_t(double t)
 {
     const double t2 = t * t;
-    if (!((unsigned long long)__double_as_longlong(t2) <
-          (unsigned long long)__double_as_longlong(4.6e18)))
+    if (!(dbits(t2) < dbits(4.6e18)))
         return 4611686018427387904ULL;
     return ceil_bits(t2);
 }
