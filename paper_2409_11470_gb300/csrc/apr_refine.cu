@@ -20,6 +20,7 @@
 
 #include "apr_internal.cuh"
 #include "apr_dtmin.cuh"
+#include "apr_sinkpre.cuh"
 #include "apr_pair.cuh"
 
 namespace apr {
@@ -2040,27 +2041,17 @@ __global__ void __launch_bounds__(256) k_accrete(DevCfg dc, DevSinks sk, long lo
     double v[7 * APR_MAXSINK];
     for (int k = 0; k < 7 * APR_MAXSINK; ++k) v[k] = 0.0;
     int cnt = 0;
-    // a float pre-test: with v_f the float of a double v, |v_f - v| <= |v_f| 2^-24, so
-    // |d_k| >= |x_f - s_f| - (|x_f| + |s_f|) 2^-22 bounds every axis's separation from
-    // below (the factor covers both conversions and the float difference); a particle
-    // whose bound lies outside every accretion radius needs no float64 test
-    float sxf[APR_MAXSINK][3], rf2[APR_MAXSINK];
+    // a particle certainly outside every accretion radius by the float pre-test
+    // (SinkPre) needs no float64 test
+    SinkPre pre[APR_MAXSINK];
     const int ns = sk.n < APR_MAXSINK ? sk.n : APR_MAXSINK;
-    for (int j = 0; j < ns; ++j) {
-        for (int k = 0; k < 3; ++k) sxf[j][k] = (float)sk.x[j][k];
-        rf2[j] = (float)(sk.racc[j] * sk.racc[j]) * (1.0f + 1.0f / 1048576.0f);
-    }
+    for (int j = 0; j < ns; ++j) pre[j].set(sk.x[j], sk.racc[j]);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         if (p.flags[i] & (APR_FLAG_DEAD | APR_FLAG_FIXED)) continue;
         const float xf = (float)p.x[i], yf = (float)p.y[i], zf = (float)p.z[i];
         bool near = false;
-        for (int j = 0; j < ns; ++j) {
-            const float gx = fmaxf(0.0f, fabsf(xf - sxf[j][0]) - (fabsf(xf) + fabsf(sxf[j][0])) * (1.0f / 4194304.0f));
-            const float gy = fmaxf(0.0f, fabsf(yf - sxf[j][1]) - (fabsf(yf) + fabsf(sxf[j][1])) * (1.0f / 4194304.0f));
-            const float gz = fmaxf(0.0f, fabsf(zf - sxf[j][2]) - (fabsf(zf) + fabsf(sxf[j][2])) * (1.0f / 4194304.0f));
-            near = near || fmaf(gz, gz, fmaf(gy, gy, gx * gx)) * (1.0f - 1.0f / 1048576.0f) < rf2[j];
-        }
+        for (int j = 0; j < ns; ++j) near = near || pre[j].maybe_inside(xf, yf, zf);
         if (!near) continue;
         for (int j = 0; j < sk.n; ++j) {
             double dx = p.x[i] - sk.x[j][0], dy = p.y[i] - sk.x[j][1], dz = p.z[i] - sk.x[j][2];
